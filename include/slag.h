@@ -1,0 +1,184 @@
+/*
+ * slag.h -- C ABI of the B300 lifting library (libslag.so).
+ *
+ * The library implements the "Semantic Embedding" stage of SLAG (Method
+ * section): 2D language features, one embedding per image segment, are lifted
+ * onto the Gaussians of a 3D Gaussian-splatting scene without a loss
+ * function. Every Gaussian k receives the normalised weighted average
+ *
+ *     E_k = sum_i sum_j sum_{p in M_j} w_{k,p} E_j  /  sum_i sum_j sum_{p in M_j} w_{k,p}
+ *
+ * (Aggregation step), where i runs over views, j over the segments (masks) of
+ * view i, p over the pixels of segment j, and w_{k,p} is the weight the
+ * rasterizer assigns to Gaussian k at pixel p (Rasterizer_SLAG statement and
+ * Eq. 2). Queries are cosine similarity searches over the resulting N x D
+ * tensor ("Query processing for inference").
+ *
+ * Conventions shared by every entry point:
+ *   - All compute runs on the CUDA device current at slag_create, in the
+ *     stream given in slag_options (NULL = the legacy default stream).
+ *   - The caller owns every buffer it passes. Inputs flagged on_device are
+ *     read asynchronously in the context's stream and must stay valid until
+ *     that stream has passed the call; host inputs are consumed before the
+ *     call returns. Outputs are caller-allocated.
+ *   - No call throws; each returns a slag_status. slag_last_error() gives a
+ *     one-line description of the last failure of a context.
+ *   - A context is not thread-safe: one host thread at a time.
+ *   - Gaussian indices in every output are the caller's original indices.
+ */
+#ifndef SLAG_H
+#define SLAG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slag_ctx slag_ctx;
+
+typedef enum {
+    SLAG_OK = 0,
+    SLAG_ERR_INVALID_ARG = 1, /* bad pointer, size, non-finite input, segment id outside [-1, M) */
+    SLAG_ERR_STATE = 2,       /* call not allowed now (e.g. query before finalize) */
+    SLAG_ERR_OOM = 3,         /* device or pinned host allocation failed */
+    SLAG_ERR_CUDA = 4,        /* a CUDA runtime call failed; see slag_last_error */
+    SLAG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    SLAG_ERR_CAPACITY = 6     /* an internal bound was exceeded (see the entry point) */
+} slag_status;
+
+/* Weight recorded per (Gaussian, pixel):
+ *   SLAG_WEIGHT_ALPHA_T: the front-to-back compositing weight w = alpha * T,
+ *     alpha = min(0.99, opacity * exp(-q/2)), T = prod over earlier
+ *     contributors of (1 - alpha); the weights of a pixel sum to 1 - T_final.
+ *   SLAG_WEIGHT_KERNEL: the raw splat kernel exp(-q/2) of Eq. 2, recorded
+ *     for the same contributing set.
+ * In both modes a Gaussian contributes to a pixel when alpha >= 1/255 and the
+ * transmittance after it stays >= 1e-4 (the first Gaussian that would push it
+ * below 1e-4 ends the pixel and is not counted). */
+enum { SLAG_WEIGHT_ALPHA_T = 0, SLAG_WEIGHT_KERNEL = 1 };
+
+/* Arithmetic of the aggregation. FP32: weights, features and sums in float32. */
+enum { SLAG_PREC_FP32 = 0 };
+
+/* The Gaussian set G = {G_1..G_N} (Method, Rasterizer_SLAG statement). */
+typedef struct {
+    int64_t n;               /* number of Gaussians, 1 <= n < 2^31 */
+    const float *means;      /* n x 3, world space */
+    const float *scales;     /* n x 3, linear standard deviations (>= 0) */
+    const float *quats;      /* n x 4, rotation (w, x, y, z), any non-zero norm */
+    const float *opacities;  /* n, activated, in [0, 1] */
+    int32_t on_device;       /* 1: the four pointers are device pointers */
+} slag_gaussians;
+
+/* Pinhole camera (K_i, R_i, t_i). OpenCV axes: x right, y down, z forward.
+ * A world point X maps to x_c = R X + t and to pixel (fx x/z + cx, fy y/z + cy);
+ * pixel (u, v) covers [u, u+1) x [v, v+1), its centre is (u + 0.5, v + 0.5). */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;   /* 1 .. 65535 */
+    float R[9];              /* world -> camera rotation, row-major */
+    float t[3];
+    float near_z, far_z;     /* a Gaussian is kept when near_z < z_c < far_z; near_z > 0 */
+} slag_camera;
+
+typedef struct {
+    int32_t dim;             /* D: embedding width, a multiple of 128, 128 .. 4096 */
+    int32_t precision;       /* SLAG_PREC_FP32 */
+    int32_t weight_mode;     /* SLAG_WEIGHT_ALPHA_T (default) or SLAG_WEIGHT_KERNEL */
+    int32_t reserved;        /* must be 0 */
+    void *cuda_stream;       /* cudaStream_t, NULL = legacy default stream */
+} slag_options;
+
+typedef struct {
+    int64_t views;           /* views added since create / reset */
+    int64_t pairs;           /* sum over views of Gaussian-tile pairs P */
+    int64_t contributions;   /* sum over views of composited (Gaussian, pixel) pairs */
+    int64_t triples;         /* stored (Gaussian, view-segment, W) entries */
+    int64_t columns;         /* sum over views of M (segment embeddings kept) */
+    int64_t last_pairs;      /* P of the last view */
+    int64_t last_contributions;
+    int64_t touched;         /* Gaussians with sum w > 0 at the last finalize */
+} slag_stats;
+
+/* Create a context over the Gaussian set (Method, Rasterizer_SLAG statement:
+ * G is fixed while views are added). Copies and reorders the Gaussians into
+ * device memory and allocates the workspace. Errors: INVALID_ARG for a NULL
+ * pointer, n out of range, a non-finite value, a zero quaternion, a negative
+ * scale or an opacity outside [0, 1], bad options; OOM; CUDA. *out is set only
+ * on success. */
+slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_ctx **out);
+
+/* Add one view (Method: Rasterization, Parameter Masking and the view's share
+ * of the Aggregation sums). seg_ids: height x width int32, row-major, the
+ * segment id of each pixel in [0, M) or -1 for a pixel in no segment (the
+ * masks M_j of the view as a partition); seg_table: M x dim float32,
+ * row-major, the embedding E_j of segment j. A pixel may belong to several
+ * overlapping masks by adding the same camera again with a second id map.
+ * Runs projection, tile binning, the two sorts, compositing, masking and the
+ * per-view reduction; synchronises the stream once, to size the view's
+ * workspace. Errors: INVALID_ARG (NULL pointer, camera not finite or out of
+ * range, M < 1 or M >= 2^24, a segment id outside [-1, M): the view is then
+ * not added); CAPACITY (more than 2^31 - 1 Gaussian-tile pairs in the view);
+ * OOM; CUDA. */
+slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *seg_ids,
+                          const float *seg_table, int32_t M, int32_t on_device);
+
+/* Normalise (Aggregation step, E_k formula) and make the embeddings
+ * queryable. out_emb: n x dim float32 (nullable), E_k in the caller's
+ * Gaussian order; a Gaussian no view touched (sum w = 0) gets the zero
+ * vector. out_wsum: n float32 (nullable), the denominator sum w. on_device
+ * says where the two outputs live. May be called again after more views.
+ * Errors: STATE before any view; CAPACITY when the per-view reduction
+ * overflowed its bound in some view; OOM; CUDA. */
+slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device);
+
+/* Cosine top-k of one query vector q (dim float32, host) over the finalized
+ * embeddings ("Query processing for inference"). Candidates are Gaussians
+ * with sum w > 0 and a non-zero embedding; scores are q . E_k / |E_k| (q is
+ * used as given: pass a unit vector for cosine). Results are ordered by
+ * descending score, ties to the lower Gaussian index. out_ids (int64) and
+ * out_scores (float) hold k entries on the host; *out_count (nullable)
+ * receives min(k, candidates); unused slots get id -1. Errors: STATE before
+ * finalize; INVALID_ARG for k < 1 or k > 1024. */
+slag_status slag_query(slag_ctx *ctx, const float *q, int32_t k, int64_t *out_ids,
+                       float *out_scores, int32_t *out_count);
+
+/* Batched form of slag_query: Q is B x dim float32 row-major; out_ids and
+ * out_scores are B x k, out_count is B (nullable). on_device says where Q and
+ * the outputs live. Same ordering, candidates and errors as slag_query. */
+slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k, int64_t *out_ids,
+                             float *out_scores, int32_t *out_count, int32_t on_device);
+
+/* Drop every added view (sums, stored triples and segment embeddings); keep
+ * the Gaussians and the workspace. */
+slag_status slag_reset(slag_ctx *ctx);
+
+slag_status slag_get_stats(const slag_ctx *ctx, slag_stats *out);
+const char *slag_last_error(const slag_ctx *ctx);
+void slag_destroy(slag_ctx *ctx);
+
+/* ---- diagnostics: the integer stages and per-pixel compositing state ---- */
+
+/* Tile binning of one view without compositing. out_touched: n uint32 (host,
+ * nullable), tiles touched per Gaussian in the caller's order (0 = culled);
+ * *out_P: number of Gaussian-tile pairs; out_list (host, nullable, list_cap
+ * entries): the Gaussian of each pair, grouped by tile in row-major tile
+ * order, each tile's Gaussians in ascending (float32 depth, Gaussian index);
+ * out_ranges (host, nullable): tiles x 2 int64 [start, end) into out_list.
+ * Errors: CAPACITY when out_list is given and list_cap < P (nothing written
+ * to out_list). */
+slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_touched,
+                          int64_t *out_P, int32_t *out_list, int64_t list_cap, int64_t *out_ranges);
+
+/* Composite one view without adding it: per pixel (height x width, host,
+ * each nullable) the final transmittance, the sum of the recorded weights
+ * over every contributing Gaussian and the number of contributors. */
+slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_T, float *out_wsum,
+                              int32_t *out_count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLAG_H */

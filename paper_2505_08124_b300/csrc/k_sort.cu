@@ -1,0 +1,402 @@
+// Stable LSD radix sort and exclusive scan (no CUB).
+//
+// Radix sort, one pass per digit of <= 8 bits, three kernels per pass:
+//   1. rs_hist:    each CTA counts the digits of its 4096-item tile
+//                  (warp-aggregated with match.any into per-warp histograms);
+//                  writes hist[digit][tile] and adds the digit totals.
+//   2. rs_offsets: one CTA per digit scans hist[digit][*] into global
+//                  output offsets (digit start + earlier tiles' counts).
+//   3. rs_scatter: each CTA ranks its tile stably (warp w owns items
+//                  [w*512, w*512+512) of the tile, in 16 rounds of 32, so
+//                  (warp, round, lane) order is input order), stages the tile
+//                  in shared memory in digit order and writes each digit's run
+//                  contiguously.
+// Exclusive scan of uint32: per-tile sums, a single-CTA scan of the sums, and
+// a per-tile scan with the carried offset.
+#include "slag_internal.cuh"
+
+namespace slag {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTileItems = kThreads * kItems;   // 4096
+constexpr int kWarps = kThreads / 32;
+constexpr int kWarpItems = kTileItems / kWarps; // 512
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) rs_hist(const K *__restrict__ keys, int64_t n, int shift,
+                                                    uint32_t mask, uint32_t *__restrict__ hist,
+                                                    uint32_t *__restrict__ digit_tot, int ntiles) {
+    __shared__ uint32_t h[kWarps][256];
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < kWarps * 256; i += kThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)w * kWarpItems;
+    for (int r = 0; r < kItems; ++r) {
+        int64_t i = base + r * 32 + lane;
+        bool valid = i < n;
+        uint32_t act = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            uint32_t d = (uint32_t)(keys[i] >> shift) & mask;
+            uint32_t peers = __match_any_sync(act, d);
+            if (lane == __ffs(peers) - 1) h[w][d] += __popc(peers);
+        }
+    }
+    __syncthreads();
+    for (int d = tid; d < 256; d += kThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) s += h[q][d];
+        hist[(int64_t)d * ntiles + blockIdx.x] = s;
+        if (s) atomicAdd(&digit_tot[d], s);
+    }
+}
+
+// One CTA per digit: offs[d][t] = sum_{d' < d} total[d'] + sum_{t' < t} hist[d][t'].
+__global__ void __launch_bounds__(1024) rs_offsets(uint32_t *__restrict__ hist,
+                                                   const uint32_t *__restrict__ digit_tot, int ntiles) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry_s;
+    const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid < 32) {
+        uint32_t s = 0;
+        for (int q = lane; q < d; q += 32) s += digit_tot[q];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) carry_s = s;
+    }
+    __syncthreads();
+    uint32_t carry = carry_s;
+    uint32_t *row = hist + (int64_t)d * ntiles;
+    for (int base = 0; base < ntiles; base += 1024) {
+        int i = base + tid;
+        uint32_t v = i < ntiles ? row[i] : 0;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t ws = warp_sums[lane];
+            uint32_t wx = ws;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, wx, o);
+                if (lane >= o) wx += y;
+            }
+            warp_sums[lane] = wx - ws;   // exclusive prefix of warp sums
+        }
+        __syncthreads();
+        uint32_t excl = carry + warp_sums[w] + x - v;
+        if (i < ntiles) row[i] = excl;
+        __syncthreads();
+        // carry for the next chunk: the last thread's exclusive value plus its own count
+        if (tid == 1023) carry_s = excl + v;
+        __syncthreads();
+        carry = carry_s;
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                       K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                       int64_t n, int shift, uint32_t mask,
+                                                       const uint32_t *__restrict__ offs, int ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t(*cnt)[256] = reinterpret_cast<uint32_t(*)[256]>(smem_raw);          // kWarps x 256
+    uint32_t *lstart = reinterpret_cast<uint32_t *>(smem_raw + kWarps * 256 * 4); // 256
+    uint32_t *gbase = lstart + 256;                                                // 256
+    uint32_t *wsum = gbase + 256;                                                  // 8
+    K *skeys = reinterpret_cast<K *>(smem_raw + kWarps * 256 * 4 + 3 * 256 * 4 + 64);
+    uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + kTileItems);
+
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < kWarps * 256; i += kThreads) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+
+    const int64_t tile_base = (int64_t)blockIdx.x * kTileItems;
+    const int64_t base = tile_base + (int64_t)w * kWarpItems;
+    K key[kItems];
+    uint32_t val[kItems];
+    uint32_t pos[kItems];
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        int64_t i = base + r * 32 + lane;
+        bool valid = i < n;
+        uint32_t act = __ballot_sync(0xffffffffu, valid);
+        pos[r] = 0xffffffffu;
+        key[r] = 0;
+        val[r] = 0;
+        if (valid) {
+            key[r] = kin[i];
+            val[r] = vin[i];
+            uint32_t d = (uint32_t)(key[r] >> shift) & mask;
+            uint32_t peers = __match_any_sync(act, d);
+            uint32_t c = cnt[w][d];
+            __syncwarp(act);
+            if (lane == __ffs(peers) - 1) cnt[w][d] = c + __popc(peers);
+            pos[r] = c + __popc(peers & lt);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, tile total
+    uint32_t tot;
+    {
+        const int d = tid;
+        uint32_t s = 0;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) {
+            uint32_t t = cnt[q][d];
+            cnt[q][d] = s;
+            s += t;
+        }
+        tot = s;
+        gbase[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+    }
+    // exclusive scan of tot over the 256 digits -> lstart
+    {
+        uint32_t x = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int q = 0; q < w; ++q) before += wsum[q];
+        lstart[tid] = before + x - tot;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        if (pos[r] != 0xffffffffu) {
+            uint32_t d = (uint32_t)(key[r] >> shift) & mask;
+            uint32_t lp = lstart[d] + cnt[w][d] + pos[r];
+            skeys[lp] = key[r];
+            svals[lp] = val[r];
+        }
+    }
+    __syncthreads();
+    int64_t rem = n - tile_base;
+    int tile_n = rem < kTileItems ? (int)rem : kTileItems;
+    for (int j = tid; j < tile_n; j += kThreads) {
+        K k = skeys[j];
+        uint32_t d = (uint32_t)(k >> shift) & mask;
+        uint32_t gp = gbase[d] + (uint32_t)j - lstart[d];
+        kout[gp] = k;
+        vout[gp] = svals[j];
+    }
+}
+
+template <typename K>
+size_t scatter_smem() {
+    return (size_t)kWarps * 256 * 4 + 3 * 256 * 4 + 64 + (size_t)kTileItems * (sizeof(K) + 4);
+}
+
+template <typename K>
+bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                     const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st) {
+    if (n <= 0 || npass <= 0) return false;
+    const int ntiles = (int)((n + kTileItems - 1) / kTileItems);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem<K>());
+        attr_set = true;
+    }
+    K *ki = keys, *ko = keys_alt;
+    uint32_t *vi = vals, *vo = vals_alt;
+    for (int p = 0; p < npass; ++p) {
+        uint32_t mask = (widths[p] >= 32) ? 0xffffffffu : ((1u << widths[p]) - 1u);
+        cudaMemsetAsync(s.digit_tot, 0, 256 * sizeof(uint32_t), st);
+        rs_hist<K><<<ntiles, kThreads, 0, st>>>(ki, n, shifts[p], mask, s.hist, s.digit_tot, ntiles);
+        rs_offsets<<<256, 1024, 0, st>>>(s.hist, s.digit_tot, ntiles);
+        rs_scatter<K><<<ntiles, kThreads, scatter_smem<K>(), st>>>(ki, vi, ko, vo, n, shifts[p], mask,
+                                                                    s.hist, ntiles);
+        K *tk = ki; ki = ko; ko = tk;
+        uint32_t *tv = vi; vi = vo; vo = tv;
+    }
+    return (npass & 1) != 0;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, uint32_t &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t ws = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        uint32_t wx = ws;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wx, o);
+            if (lane >= o) wx += y;
+        }
+        wsum[lane] = wx - ws;
+        if (lane == 31) wsum[32] = wx;
+    }
+    __syncthreads();
+    uint32_t r = wsum[w] + x - v;
+    total = wsum[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kThreads) scan_partials(const uint32_t *__restrict__ in, int64_t n,
+                                                          uint32_t *__restrict__ partials) {
+    const int64_t base = (int64_t)blockIdx.x * kTileItems;
+    uint32_t s = 0;
+    for (int j = threadIdx.x; j < kTileItems; j += kThreads) {
+        int64_t i = base + j;
+        if (i < n) s += in[i];
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ uint32_t ws[kWarps];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int q = 0; q < kWarps; ++q) t += ws[q];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// Single CTA: in-place exclusive scan of the per-tile sums; total to *d_total.
+__global__ void __launch_bounds__(1024) scan_spine(uint32_t *__restrict__ partials, int64_t np,
+                                                   unsigned long long *__restrict__ d_total) {
+    __shared__ uint32_t wsum[33];
+    unsigned long long carry = 0;
+    for (int64_t base = 0; base < np; base += 1024) {
+        int64_t i = base + threadIdx.x;
+        uint32_t v = i < np ? partials[i] : 0;
+        uint32_t tot;
+        uint32_t e = block_excl_scan(v, wsum, tot);
+        if (i < np) partials[i] = (uint32_t)(carry + e);
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
+// buffer index with one pad word per 32, so that thread t reading its 16
+// consecutive items hits distinct banks
+__device__ __forceinline__ int padded(int j) { return j + (j >> 5); }
+
+__global__ void __launch_bounds__(kThreads) scan_tiles(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                       int64_t n, const uint32_t *__restrict__ partials) {
+    __shared__ uint32_t buf[kTileItems + kTileItems / 32];
+    __shared__ uint32_t wsum[33];
+    const int64_t base = (int64_t)blockIdx.x * kTileItems;
+    for (int j = threadIdx.x; j < kTileItems; j += kThreads) {
+        int64_t i = base + j;
+        buf[padded(j)] = i < n ? in[i] : 0;
+    }
+    __syncthreads();
+    uint32_t v[kItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+        v[q] = buf[padded(threadIdx.x * kItems + q)];
+        s += v[q];
+    }
+    uint32_t tot;
+    uint32_t e = block_excl_scan(s, wsum, tot) + partials[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+        buf[padded(threadIdx.x * kItems + q)] = e;
+        e += v[q];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kTileItems; j += kThreads) {
+        int64_t i = base + j;
+        if (i < n) out[i] = buf[padded(j)];
+    }
+}
+
+}  // namespace
+
+cudaError_t scratch_reserve(SortScratch &s, int64_t n) {
+    int64_t tiles = (n + kTileItems - 1) / kTileItems + 1;
+    size_t need_hist = (size_t)256 * tiles;
+    if (!s.digit_tot) {
+        cudaError_t e = cudaMalloc(&s.digit_tot, 256 * sizeof(uint32_t));
+        if (e != cudaSuccess) return e;
+    }
+    if (need_hist > s.hist_cap) {
+        cudaFree(s.hist);
+        s.hist = nullptr;
+        s.hist_cap = 0;
+        cudaError_t e = cudaMalloc(&s.hist, need_hist * sizeof(uint32_t));
+        if (e != cudaSuccess) return e;
+        s.hist_cap = need_hist;
+    }
+    if ((size_t)tiles > s.partials_cap) {
+        cudaFree(s.partials);
+        s.partials = nullptr;
+        s.partials_cap = 0;
+        cudaError_t e = cudaMalloc(&s.partials, (size_t)tiles * sizeof(uint32_t));
+        if (e != cudaSuccess) return e;
+        s.partials_cap = (size_t)tiles;
+    }
+    return cudaSuccess;
+}
+
+void scratch_free(SortScratch &s) {
+    cudaFree(s.hist);
+    cudaFree(s.digit_tot);
+    cudaFree(s.partials);
+    s = SortScratch{};
+}
+
+int digit_passes(int lo, int bits, int *shifts, int *widths) {
+    if (bits <= 0) return 0;
+    int np = (bits + 7) / 8;
+    int base = bits / np, extra = bits % np, at = lo;
+    for (int p = 0; p < np; ++p) {
+        int wdt = base + (p < extra ? 1 : 0);
+        shifts[p] = at;
+        widths[p] = wdt;
+        at += wdt;
+    }
+    return np;
+}
+
+bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                    const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st) {
+    return radix_sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st);
+}
+
+bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                    const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st) {
+    return radix_sort_impl<uint64_t>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st);
+}
+
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *d_total,
+                        SortScratch &s, cudaStream_t st) {
+    if (n <= 0) {
+        if (d_total) cudaMemsetAsync(d_total, 0, sizeof(unsigned long long), st);
+        return;
+    }
+    int64_t tiles = (n + kTileItems - 1) / kTileItems;
+    scan_partials<<<(unsigned)tiles, kThreads, 0, st>>>(in, n, s.partials);
+    scan_spine<<<1, 1024, 0, st>>>(s.partials, tiles, d_total);
+    scan_tiles<<<(unsigned)tiles, kThreads, 0, st>>>(in, out, n, s.partials);
+}
+
+}  // namespace slag

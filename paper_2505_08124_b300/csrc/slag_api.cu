@@ -1,0 +1,716 @@
+// C ABI of libslag: context management and the per-call pipelines.
+//
+// slag_add_view (Method, "Semantic Embedding": Rasterization, Parameter
+// Masking, the view's share of Aggregation):
+//   project -> depth sort (stable, caller index breaks ties) -> gather records
+//   in depth-rank order -> scan tile counts -> [one stream sync: read the pair
+//   count P and the error flags] -> emit (tile, rank) pairs -> stable sort by
+//   tile -> tile ranges -> composite + mask + in-tile segment binning ->
+//   consume the per-view (segment, weight) tables into the triple log.
+// slag_finalize (Aggregation, E_k formula): sort the log by
+//   (block, column, Gaussian) -> distinct columns per block -> blocked
+//   contraction with the stored segment embeddings -> divide by sum w.
+// slag_query ("Query processing for inference"): cosine scores + top-k.
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <string>
+
+#include "slag_internal.cuh"
+
+using namespace slag;
+
+struct slag_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0;
+    int32_t D = 0;
+    int32_t weight_mode = 0;
+    std::string err;
+
+    // Gaussians, internal (Morton) order
+    float4 *mean_op = nullptr, *cov_a = nullptr;
+    float2 *cov_b = nullptr;
+    uint32_t *orig_of_int = nullptr, *int_of_orig = nullptr;
+
+    // per-view, n-sized
+    uint32_t *dkey[2] = {nullptr, nullptr}, *dval[2] = {nullptr, nullptr};
+    float4 *rec_a = nullptr, *rec_b = nullptr, *srec_a = nullptr, *srec_b = nullptr;
+    uint2 *rect = nullptr, *srect = nullptr;
+    uint32_t *stouched = nullptr, *offsets = nullptr;
+    HashEntry *hash = nullptr;
+    float *s_hi = nullptr, *s_lo = nullptr, *s_ovf = nullptr;
+
+    // per-view, P-sized and image-sized
+    uint32_t *pkey[2] = {nullptr, nullptr}, *pval[2] = {nullptr, nullptr};
+    int64_t p_cap = 0;
+    uint2 *ranges = nullptr;
+    int64_t ranges_cap = 0;
+    int32_t *seg_buf = nullptr;
+    int64_t seg_cap = 0;
+    float *dbg_T = nullptr, *dbg_wsum = nullptr;
+    int32_t *dbg_count = nullptr;
+    int64_t dbg_cap = 0;
+
+    ViewCounters *ctr = nullptr;             // device, reset per view
+    unsigned long long *totals = nullptr;    // device: [0] triples in the log, [1] contributions,
+                                             // [2] low word: log overflow flag
+    unsigned long long *log_count = nullptr; // = totals
+    unsigned long long *contrib = nullptr;   // = totals + 1
+    struct HostCounters {
+        ViewCounters v;
+        unsigned long long totals[3];
+        unsigned long long touched;
+    } *hc = nullptr;                         // pinned host
+    unsigned long long contrib_before_last = 0;
+
+    // triple log + finalize scratch
+    uint64_t *log_key = nullptr, *log_key_alt = nullptr;
+    float *log_w = nullptr, *log_w_alt = nullptr;
+    int64_t log_cap = 0;
+    uint32_t *flags = nullptr, *uidx = nullptr, *ucol = nullptr, *ustart = nullptr;
+    int64_t fin_cap = 0;
+    uint32_t *bstart = nullptr, *bend = nullptr;
+    bool log_overflowed = false;
+
+    // stored segment embeddings (columns x D)
+    float *table = nullptr;
+    int64_t table_rows = 0, table_cap = 0;
+
+    // outputs
+    float *E = nullptr, *inv_norm = nullptr, *wsum = nullptr;
+    unsigned long long *touched = nullptr;
+    bool finalized = false;
+
+    // queries
+    float *qbuf = nullptr;
+    int64_t qbuf_cap = 0;
+    float *cand_s = nullptr;
+    uint32_t *cand_i = nullptr;
+    int64_t cand_cap = 0;
+    int64_t *qids = nullptr;
+    float *qscores = nullptr;
+    int32_t *qcount = nullptr;
+    int64_t qout_cap = 0;
+
+    SortScratch scratch;
+    slag_stats stats{};
+};
+
+namespace {
+
+slag_status fail(slag_ctx *c, slag_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? SLAG_ERR_OOM : SLAG_ERR_CUDA,       \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+        }                                                                                          \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * (size_t)count);
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+// Grows a device buffer to at least `need` elements (x1.5 headroom); keeps
+// the first `keep` elements when asked.
+template <typename T>
+cudaError_t grow(T *&p, int64_t &cap, int64_t need, cudaStream_t st, int64_t keep = 0) {
+    if (need <= cap) return cudaSuccess;
+    int64_t nc = need + need / 2 + 1024;
+    T *q = nullptr;
+    cudaError_t e = dalloc(&q, nc);
+    if (e != cudaSuccess) return e;
+    if (keep > 0 && p) {
+        e = cudaMemcpyAsync(q, p, sizeof(T) * (size_t)keep, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { cudaFree(q); return e; }
+        cudaStreamSynchronize(st);
+    }
+    if (p) cudaFree(p);
+    p = q;
+    cap = nc;
+    return cudaSuccess;
+}
+
+bool finite_camera(const slag_camera *c) {
+    const float *f = &c->fx;
+    for (int i = 0; i < 4; ++i)
+        if (!std::isfinite(f[i])) return false;
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(c->R[i])) return false;
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(c->t[i])) return false;
+    return std::isfinite(c->near_z) && std::isfinite(c->far_z);
+}
+
+slag_status check_camera(slag_ctx *ctx, const slag_camera *cam) {
+    if (!cam) return fail(ctx, SLAG_ERR_INVALID_ARG, "camera is NULL");
+    if (!finite_camera(cam)) return fail(ctx, SLAG_ERR_INVALID_ARG, "camera has a non-finite value");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 65535 || cam->height > 65535)
+        return fail(ctx, SLAG_ERR_INVALID_ARG, "camera width/height outside 1..65535");
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(ctx, SLAG_ERR_INVALID_ARG, "camera fx/fy must be > 0");
+    if (!(cam->near_z > 0.f) || !(cam->far_z > cam->near_z))
+        return fail(ctx, SLAG_ERR_INVALID_ARG, "camera needs 0 < near_z < far_z");
+    return SLAG_OK;
+}
+
+CamParams cam_params(const slag_camera *c) {
+    CamParams p;
+    p.fx = c->fx; p.fy = c->fy; p.cx = c->cx; p.cy = c->cy;
+    p.width = c->width; p.height = c->height;
+    memcpy(p.R, c->R, sizeof(p.R));
+    memcpy(p.t, c->t, sizeof(p.t));
+    p.near_z = c->near_z; p.far_z = c->far_z;
+    p.tiles_x = (c->width + kTile - 1) / kTile;
+    p.tiles_y = (c->height + kTile - 1) / kTile;
+    return p;
+}
+
+int ceil_log2(uint64_t v) {
+    int b = 0;
+    while ((1ull << b) < v) ++b;
+    return b;
+}
+
+// Projection through the tile ranges of one view: leaves the depth-sorted
+// records, the tile-sorted pair list and ranges in the workspace; returns the
+// pair count in *P_out and the list buffer in *list_out.
+slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_t **keys_out,
+                     uint32_t **list_out, const int32_t *seg_check, int32_t M) {
+    cudaStream_t st = ctx->stream;
+    const int64_t n = ctx->n;
+    CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
+    if (seg_check) launch_check_seg(seg_check, (int64_t)cp.width * cp.height, M, ctx->ctr, st);
+    launch_project(cp, ctx->mean_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, ctx->dkey[0], ctx->dval[0],
+                   ctx->rec_a, ctx->rec_b, ctx->rect, ctx->ctr, st);
+    int shifts[8], widths[8];
+    int np = digit_passes(0, 32, shifts, widths);
+    bool alt = radix_sort_u32(ctx->dkey[0], ctx->dkey[1], ctx->dval[0], ctx->dval[1], n, shifts, widths, np,
+                              ctx->scratch, st);
+    const uint32_t *sorted_vals = ctx->dval[alt ? 1 : 0];
+    launch_gather_sorted(sorted_vals, n, ctx->ctr, ctx->rec_a, ctx->rec_b, ctx->rect, ctx->srec_a, ctx->srec_b,
+                         ctx->srect, ctx->stouched, st);
+    exclusive_scan_u32(ctx->stouched, ctx->offsets, n, &ctx->ctr->P, ctx->scratch, st);
+    CK(cudaMemcpyAsync(&ctx->hc->v, ctx->ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->hc->totals, ctx->totals, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (ctx->hc->v.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
+    const int64_t P = (int64_t)ctx->hc->v.P;
+    if (P > 0x7fffffffLL) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^31-1 Gaussian-tile pairs in one view");
+    if (P > ctx->p_cap) {
+        int64_t cap = ctx->p_cap;
+        for (int b = 0; b < 2; ++b) {
+            int64_t c1 = cap, c2 = cap;
+            CK(grow(ctx->pkey[b], c1, P, st));
+            CK(grow(ctx->pval[b], c2, P, st));
+            ctx->p_cap = c1;
+        }
+        CK(scratch_reserve(ctx->scratch, ctx->p_cap));
+    }
+    const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
+    CK(grow(ctx->ranges, ctx->ranges_cap, tiles, st));
+    CK(cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)tiles, st));
+    uint32_t nv = ctx->hc->v.n_visible;
+    launch_emit(ctx->srect, ctx->offsets, nv, cp.tiles_x, ctx->pkey[0], ctx->pval[0], st);
+    np = digit_passes(0, ceil_log2((uint64_t)tiles), shifts, widths);
+    alt = radix_sort_u32(ctx->pkey[0], ctx->pkey[1], ctx->pval[0], ctx->pval[1], P, shifts, widths, np,
+                         ctx->scratch, st);
+    uint32_t *keys = ctx->pkey[alt ? 1 : 0];
+    launch_ranges(keys, P, ctx->ranges, st);
+    *P_out = P;
+    *keys_out = keys;
+    *list_out = ctx->pval[alt ? 1 : 0];
+    return SLAG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_ctx **out) {
+    if (!out) return SLAG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!g || !opt) return SLAG_ERR_INVALID_ARG;
+    if (g->n < 1 || g->n >= (1LL << 31)) return SLAG_ERR_INVALID_ARG;
+    if (!g->means || !g->scales || !g->quats || !g->opacities) return SLAG_ERR_INVALID_ARG;
+    if (opt->dim < 128 || opt->dim > 4096 || opt->dim % 128 != 0) return SLAG_ERR_INVALID_ARG;
+    if (opt->precision != SLAG_PREC_FP32) return SLAG_ERR_INVALID_ARG;
+    if (opt->weight_mode != SLAG_WEIGHT_ALPHA_T && opt->weight_mode != SLAG_WEIGHT_KERNEL) return SLAG_ERR_INVALID_ARG;
+    if (opt->reserved != 0) return SLAG_ERR_INVALID_ARG;
+
+    slag_ctx *ctx = new (std::nothrow) slag_ctx();
+    if (!ctx) return SLAG_ERR_OOM;
+    float *dm = nullptr, *ds = nullptr, *dq = nullptr, *dop = nullptr;
+    uint32_t *bb = nullptr;
+    auto free_inputs = [&]() { dfree(dm); dfree(ds); dfree(dq); dfree(dop); dfree(bb); };
+    auto bail = [&](slag_status s) {
+        free_inputs();
+        slag_destroy(ctx);
+        return s;
+    };
+    const int64_t n = g->n;
+    ctx->n = n;
+    ctx->D = opt->dim;
+    ctx->weight_mode = opt->weight_mode;
+    ctx->stream = (cudaStream_t)opt->cuda_stream;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(SLAG_ERR_CUDA);
+    cudaStream_t st = ctx->stream;
+
+#define CA(call)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess)                                        \
+            return bail(e_ == cudaErrorMemoryAllocation ? SLAG_ERR_OOM : SLAG_ERR_CUDA); \
+    } while (0)
+
+    // inputs on the device
+    const float *im = g->means, *is = g->scales, *iq = g->quats, *io = g->opacities;
+    if (!g->on_device) {
+        CA(dalloc(&dm, 3 * n)); CA(dalloc(&ds, 3 * n)); CA(dalloc(&dq, 4 * n)); CA(dalloc(&dop, n));
+        CA(cudaMemcpyAsync(dm, g->means, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
+        CA(cudaMemcpyAsync(ds, g->scales, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
+        CA(cudaMemcpyAsync(dq, g->quats, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, st));
+        CA(cudaMemcpyAsync(dop, g->opacities, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+        im = dm; is = ds; iq = dq; io = dop;
+    }
+    CA(cudaMallocHost((void **)&ctx->hc, sizeof(slag_ctx::HostCounters)));
+    CA(dalloc(&ctx->ctr, 1));
+    CA(dalloc(&ctx->totals, 3));
+    ctx->log_count = ctx->totals;
+    ctx->contrib = ctx->totals + 1;
+    CA(dalloc(&ctx->touched, 1));
+    CA(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
+    CA(cudaMemsetAsync(ctx->totals, 0, 3 * sizeof(unsigned long long), st));
+    CA(scratch_reserve(ctx->scratch, n));
+
+    // validation
+    launch_check_gaussians(im, is, iq, io, n, &ctx->ctr->bad_seg, st);
+    CA(cudaMemcpyAsync(&ctx->hc->v, ctx->ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
+    CA(cudaStreamSynchronize(st));
+    CA(cudaGetLastError());
+    if (ctx->hc->v.bad_seg) return bail(SLAG_ERR_INVALID_ARG);
+
+    // Morton order
+    CA(dalloc(&ctx->orig_of_int, n)); CA(dalloc(&ctx->int_of_orig, n));
+    for (int b = 0; b < 2; ++b) { CA(dalloc(&ctx->dkey[b], n)); CA(dalloc(&ctx->dval[b], n)); }
+    CA(dalloc(&ctx->stouched, n));
+    CA(dalloc(&ctx->offsets, n));
+    CA(dalloc(&bb, 6));
+    launch_bbox(im, n, bb, st);
+    launch_morton(im, n, bb, ctx->dkey[0], ctx->dval[0], st);
+    int shifts[8], widths[8];
+    int np = digit_passes(0, 30, shifts, widths);
+    bool alt = radix_sort_u32(ctx->dkey[0], ctx->dkey[1], ctx->dval[0], ctx->dval[1], n, shifts, widths, np,
+                              ctx->scratch, st);
+    CA(cudaMemcpyAsync(ctx->orig_of_int, ctx->dval[alt ? 1 : 0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+    CA(dalloc(&ctx->mean_op, n)); CA(dalloc(&ctx->cov_a, n)); CA(dalloc(&ctx->cov_b, n));
+    launch_pack_gaussians(im, is, iq, io, n, ctx->orig_of_int, ctx->mean_op, ctx->cov_a, ctx->cov_b,
+                          ctx->int_of_orig, st);
+
+    // per-view workspace
+    CA(dalloc(&ctx->rec_a, n)); CA(dalloc(&ctx->rec_b, n)); CA(dalloc(&ctx->srec_a, n)); CA(dalloc(&ctx->srec_b, n));
+    CA(dalloc(&ctx->rect, n)); CA(dalloc(&ctx->srect, n));
+    CA(dalloc(&ctx->hash, n));
+    CA(dalloc(&ctx->s_hi, n)); CA(dalloc(&ctx->s_lo, n)); CA(dalloc(&ctx->s_ovf, n));
+    CA(dalloc(&ctx->E, n * (int64_t)ctx->D)); CA(dalloc(&ctx->inv_norm, n)); CA(dalloc(&ctx->wsum, n));
+    CA(dalloc(&ctx->bstart, (n + kBlockG - 1) / kBlockG)); CA(dalloc(&ctx->bend, (n + kBlockG - 1) / kBlockG));
+    launch_hash_init(ctx->hash, n, st);
+    CA(cudaMemsetAsync(ctx->s_hi, 0, sizeof(float) * n, st));
+    CA(cudaMemsetAsync(ctx->s_lo, 0, sizeof(float) * n, st));
+    CA(cudaMemsetAsync(ctx->s_ovf, 0, sizeof(float) * n, st));
+    CA(cudaStreamSynchronize(st));
+    CA(cudaGetLastError());
+    free_inputs();
+#undef CA
+    *out = ctx;
+    return SLAG_OK;
+}
+
+slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *seg_ids, const float *seg_table,
+                          int32_t M, int32_t on_device) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    slag_status s = check_camera(ctx, cam);
+    if (s != SLAG_OK) return s;
+    if (!seg_ids || !seg_table) return fail(ctx, SLAG_ERR_INVALID_ARG, "seg_ids / seg_table is NULL");
+    if (M < 1 || M >= (1 << 24)) return fail(ctx, SLAG_ERR_INVALID_ARG, "M outside [1, 2^24)");
+    if (ctx->table_rows + M >= (1LL << 32)) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^32 segment columns");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const CamParams cp = cam_params(cam);
+    const int64_t npx = (int64_t)cam->width * cam->height;
+    const int64_t D = ctx->D;
+
+    // segment embeddings -> rows [table_rows, table_rows + M) of the column store
+    CK(grow(ctx->table, ctx->table_cap, (ctx->table_rows + M) * D, st, ctx->table_rows * D));
+    CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    const int32_t *seg = seg_ids;
+    if (!on_device) {
+        CK(grow(ctx->seg_buf, ctx->seg_cap, npx, st));
+        CK(cudaMemcpyAsync(ctx->seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, cudaMemcpyHostToDevice, st));
+        seg = ctx->seg_buf;
+    }
+    int64_t P = 0;
+    uint32_t *keys = nullptr, *list = nullptr;
+    s = bin_view(ctx, cp, &P, &keys, &list, seg, M);
+    if (s != SLAG_OK) return s;
+
+    // room in the triple log: at most kHashSlots per Gaussian from the consume
+    // pass plus the overflow appends of this view
+    const unsigned long long used = ctx->hc->totals[0];
+    ctx->contrib_before_last = ctx->hc->totals[1];
+    const int64_t need = (int64_t)used + ctx->n * kHashSlots + 2 * P + (1 << 20);
+    if (need > ctx->log_cap) {
+        int64_t c1 = ctx->log_cap, c2 = ctx->log_cap;
+        CK(grow(ctx->log_key, c1, need, st, (int64_t)used));
+        CK(grow(ctx->log_w, c2, need, st, (int64_t)used));
+        ctx->log_cap = c1;
+    }
+    CompositeArgs a;
+    a.cam = cp;
+    a.ranges = ctx->ranges;
+    a.list = list;
+    a.srec_a = ctx->srec_a;
+    a.srec_b = ctx->srec_b;
+    a.seg = seg;
+    a.view_base = (int32_t)ctx->table_rows;
+    a.weight_mode = ctx->weight_mode;
+    a.hash = ctx->hash;
+    a.log_count = ctx->log_count;
+    a.log_cap = (unsigned long long)ctx->log_cap;
+    a.log_key = ctx->log_key;
+    a.log_w = ctx->log_w;
+    a.s_ovf = ctx->s_ovf;
+    a.ctr = ctx->ctr;
+    a.overflow = reinterpret_cast<uint32_t *>(ctx->totals + 2);
+    a.contrib = ctx->contrib;
+    a.dbg_T = a.dbg_wsum = nullptr;
+    a.dbg_count = nullptr;
+    a.accumulate = 1;
+    launch_composite(a, st);
+    launch_consume(ctx->hash, ctx->n, (int32_t)ctx->table_rows, ctx->s_hi, ctx->s_lo, ctx->log_count,
+                   (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
+                   reinterpret_cast<uint32_t *>(ctx->totals + 2), st);
+    CK(cudaGetLastError());
+    ctx->table_rows += M;
+    ctx->stats.views += 1;
+    ctx->stats.pairs += P;
+    ctx->stats.last_pairs = P;
+    ctx->stats.columns = ctx->table_rows;
+    ctx->finalized = false;
+    return SLAG_OK;
+}
+
+slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    if (ctx->stats.views == 0) return fail(ctx, SLAG_ERR_STATE, "finalize before any view");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->hc->totals, ctx->totals, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    ctx->stats.contributions = (int64_t)ctx->hc->totals[1];
+    ctx->stats.last_contributions = (int64_t)(ctx->hc->totals[1] - ctx->contrib_before_last);
+    if (ctx->hc->totals[2]) ctx->log_overflowed = true;
+    if (ctx->log_overflowed) return fail(ctx, SLAG_ERR_CAPACITY, "the triple log overflowed in some view");
+    const int64_t Z = (int64_t)ctx->hc->totals[0];
+    ctx->stats.triples = Z;
+    const int64_t n = ctx->n;
+    const int64_t nblocks = (n + kBlockG - 1) / kBlockG;
+    CK(cudaMemsetAsync(ctx->bstart, 0, sizeof(uint32_t) * nblocks, st));
+    CK(cudaMemsetAsync(ctx->bend, 0, sizeof(uint32_t) * nblocks, st));
+    CK(cudaMemsetAsync(ctx->touched, 0, sizeof(unsigned long long), st));
+    if (Z > 0) {
+        if (Z > ctx->fin_cap) {
+            int64_t c = ctx->fin_cap;
+            int64_t c1 = c, c2 = c, c3 = c, c4 = c, c5 = c, c6 = c;
+            CK(grow(ctx->log_key_alt, c1, Z, st));
+            CK(grow(ctx->log_w_alt, c2, Z, st));
+            CK(grow(ctx->flags, c3, Z, st));
+            CK(grow(ctx->uidx, c4, Z, st));
+            CK(grow(ctx->ucol, c5, Z, st));
+            CK(grow(ctx->ustart, c6, Z, st));
+            ctx->fin_cap = c1;
+            CK(scratch_reserve(ctx->scratch, Z));
+        }
+        // sort by (block, column, Gaussian): bits [0, 7 + col_bits) then [39, 39 + block_bits)
+        int shifts[16], widths[16];
+        int np = digit_passes(0, 7 + ceil_log2((uint64_t)ctx->table_rows), shifts, widths);
+        np += digit_passes(39, ceil_log2((uint64_t)nblocks), shifts + np, widths + np);
+        bool alt = radix_sort_u64(ctx->log_key, ctx->log_key_alt, reinterpret_cast<uint32_t *>(ctx->log_w),
+                                  reinterpret_cast<uint32_t *>(ctx->log_w_alt), Z, shifts, widths, np,
+                                  ctx->scratch, st);
+        if (alt) {
+            // the sorted log becomes the log (its order is free); capacities follow the buffers
+            std::swap(ctx->log_key, ctx->log_key_alt);
+            std::swap(ctx->log_w, ctx->log_w_alt);
+            std::swap(ctx->log_cap, ctx->fin_cap);
+            // fin_cap must cover every finalize buffer: take the smaller of the two
+            if (ctx->fin_cap > ctx->log_cap) ctx->fin_cap = ctx->log_cap;
+        }
+        launch_unique_flags(ctx->log_key, Z, ctx->flags, st);
+        exclusive_scan_u32(ctx->flags, ctx->uidx, Z, nullptr, ctx->scratch, st);
+        launch_uniques(ctx->log_key, ctx->flags, ctx->uidx, Z, ctx->ucol, ctx->ustart, ctx->bstart, ctx->bend, st);
+    }
+    AggArgs g;
+    g.keys = ctx->log_key;
+    g.w = ctx->log_w;
+    g.uidx = ctx->uidx;
+    g.ucol = ctx->ucol;
+    g.ustart = ctx->ustart;
+    g.bstart = ctx->bstart;
+    g.bend = ctx->bend;
+    g.table = ctx->table;
+    g.s_hi = ctx->s_hi;
+    g.s_lo = ctx->s_lo;
+    g.s_ovf = ctx->s_ovf;
+    g.orig_of_int = ctx->orig_of_int;
+    g.n = n;
+    g.D = ctx->D;
+    g.E = ctx->E;
+    g.inv_norm = ctx->inv_norm;
+    g.wsum = ctx->wsum;
+    g.touched = ctx->touched;
+    launch_aggregate(g, nblocks, st);
+    CK(cudaGetLastError());
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (out_emb) CK(cudaMemcpyAsync(out_emb, ctx->E, sizeof(float) * (size_t)(n * ctx->D), kind, st));
+    if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, kind, st));
+    CK(cudaMemcpyAsync(&ctx->hc->touched, ctx->touched, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->stats.touched = (int64_t)ctx->hc->touched;
+    ctx->finalized = true;
+    return SLAG_OK;
+}
+
+slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k, int64_t *out_ids,
+                             float *out_scores, int32_t *out_count, int32_t on_device) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    if (!ctx->finalized) return fail(ctx, SLAG_ERR_STATE, "query before finalize");
+    if (!Q || !out_ids || !out_scores) return fail(ctx, SLAG_ERR_INVALID_ARG, "NULL query or output");
+    if (k < 1 || k > kMaxK) return fail(ctx, SLAG_ERR_INVALID_ARG, "k outside [1, 1024]");
+    if (B < 1) return fail(ctx, SLAG_ERR_INVALID_ARG, "B < 1");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int64_t D = ctx->D;
+    const float *dQ = Q;
+    if (!on_device) {
+        CK(grow(ctx->qbuf, ctx->qbuf_cap, (int64_t)B * D, st));
+        CK(cudaMemcpyAsync(ctx->qbuf, Q, sizeof(float) * (size_t)(B * D), cudaMemcpyHostToDevice, st));
+        dQ = ctx->qbuf;
+    }
+    const int64_t nc = (int64_t)query_cand_entries(B, ctx->n, k);
+    if (nc > ctx->cand_cap) {
+        int64_t c1 = ctx->cand_cap, c2 = ctx->cand_cap;
+        CK(grow(ctx->cand_s, c1, nc, st));
+        CK(grow(ctx->cand_i, c2, nc, st));
+        ctx->cand_cap = c1;
+    }
+    int64_t *ids = out_ids;
+    float *scores = out_scores;
+    int32_t *cnt = out_count;
+    if (!on_device) {
+        if ((int64_t)B * k > ctx->qout_cap) {
+            int64_t c1 = ctx->qout_cap, c2 = ctx->qout_cap, c3 = ctx->qout_cap;
+            CK(grow(ctx->qids, c1, (int64_t)B * k, st));
+            CK(grow(ctx->qscores, c2, (int64_t)B * k, st));
+            CK(grow(ctx->qcount, c3, (int64_t)B * k, st));
+            ctx->qout_cap = c1;
+        }
+        ids = ctx->qids;
+        scores = ctx->qscores;
+        cnt = ctx->qcount;
+    }
+    launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i, ids, scores, cnt,
+                      st);
+    CK(cudaGetLastError());
+    if (!on_device) {
+        CK(cudaMemcpyAsync(out_ids, ids, sizeof(int64_t) * (size_t)B * k, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(out_scores, scores, sizeof(float) * (size_t)B * k, cudaMemcpyDeviceToHost, st));
+        if (out_count) CK(cudaMemcpyAsync(out_count, cnt, sizeof(int32_t) * (size_t)B, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return SLAG_OK;
+}
+
+slag_status slag_query(slag_ctx *ctx, const float *q, int32_t k, int64_t *out_ids, float *out_scores,
+                       int32_t *out_count) {
+    return slag_query_batch(ctx, q, 1, k, out_ids, out_scores, out_count, 0);
+}
+
+slag_status slag_reset(slag_ctx *ctx) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int64_t n = ctx->n;
+    launch_hash_init(ctx->hash, n, st);
+    CK(cudaMemsetAsync(ctx->s_hi, 0, sizeof(float) * n, st));
+    CK(cudaMemsetAsync(ctx->s_lo, 0, sizeof(float) * n, st));
+    CK(cudaMemsetAsync(ctx->s_ovf, 0, sizeof(float) * n, st));
+    CK(cudaMemsetAsync(ctx->totals, 0, 3 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
+    CK(cudaGetLastError());
+    ctx->contrib_before_last = 0;
+    ctx->table_rows = 0;
+    ctx->log_overflowed = false;
+    ctx->finalized = false;
+    ctx->hc->v = ViewCounters{};
+    ctx->stats = slag_stats{};
+    return SLAG_OK;
+}
+
+slag_status slag_get_stats(const slag_ctx *ctx, slag_stats *out) {
+    if (!ctx || !out) return SLAG_ERR_INVALID_ARG;
+    *out = ctx->stats;
+    return SLAG_OK;
+}
+
+const char *slag_last_error(const slag_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+void slag_destroy(slag_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
+    dfree(ctx->mean_op); dfree(ctx->cov_a); dfree(ctx->cov_b); dfree(ctx->orig_of_int); dfree(ctx->int_of_orig);
+    for (int b = 0; b < 2; ++b) { dfree(ctx->dkey[b]); dfree(ctx->dval[b]); dfree(ctx->pkey[b]); dfree(ctx->pval[b]); }
+    dfree(ctx->rec_a); dfree(ctx->rec_b); dfree(ctx->srec_a); dfree(ctx->srec_b); dfree(ctx->rect); dfree(ctx->srect);
+    dfree(ctx->stouched); dfree(ctx->offsets); dfree(ctx->hash); dfree(ctx->s_hi); dfree(ctx->s_lo); dfree(ctx->s_ovf);
+    dfree(ctx->ranges); dfree(ctx->seg_buf); dfree(ctx->dbg_T); dfree(ctx->dbg_wsum); dfree(ctx->dbg_count);
+    dfree(ctx->ctr); dfree(ctx->totals); dfree(ctx->touched);
+    dfree(ctx->log_key); dfree(ctx->log_key_alt); dfree(ctx->log_w); dfree(ctx->log_w_alt);
+    dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
+    dfree(ctx->table); dfree(ctx->E); dfree(ctx->inv_norm); dfree(ctx->wsum);
+    dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);
+    scratch_free(ctx->scratch);
+    if (ctx->hc) cudaFreeHost(ctx->hc);
+    delete ctx;
+}
+
+slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_touched, int64_t *out_P,
+                          int32_t *out_list, int64_t list_cap, int64_t *out_ranges) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    slag_status s = check_camera(ctx, cam);
+    if (s != SLAG_OK) return s;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const CamParams cp = cam_params(cam);
+    int64_t P = 0;
+    uint32_t *keys = nullptr, *list = nullptr;
+    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0);
+    if (s != SLAG_OK) return s;
+    if (out_P) *out_P = P;
+    const int64_t n = ctx->n;
+    const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
+    if (out_touched) {
+        // tiles touched per Gaussian, caller order: depth-sorted values hold internal indices
+        uint32_t *h_orig = (uint32_t *)malloc(sizeof(uint32_t) * n);
+        uint2 *h_rect = (uint2 *)malloc(sizeof(uint2) * n);
+        if (!h_orig || !h_rect) {
+            free(h_orig); free(h_rect);
+            return fail(ctx, SLAG_ERR_OOM, "host allocation");
+        }
+        CK(cudaMemcpyAsync(h_rect, ctx->rect, sizeof(uint2) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_orig, ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int64_t gI = 0; gI < n; ++gI) {
+            const uint2 rc = h_rect[gI];
+            out_touched[h_orig[gI]] = ((rc.x >> 16) - (rc.x & 0xffffu)) * ((rc.y >> 16) - (rc.y & 0xffffu));
+        }
+        free(h_orig); free(h_rect);
+    }
+    if (out_list) {
+        if (list_cap < P) return fail(ctx, SLAG_ERR_CAPACITY, "list_cap < P");
+        // list holds depth ranks; map rank -> internal -> caller index on the host
+        uint32_t *h_list = (uint32_t *)malloc(sizeof(uint32_t) * (P > 0 ? P : 1));
+        uint32_t *h_orig = (uint32_t *)malloc(sizeof(uint32_t) * n);
+        float4 *h_recb = (float4 *)malloc(sizeof(float4) * n);
+        if (!h_list || !h_orig || !h_recb) {
+            free(h_list); free(h_orig); free(h_recb);
+            return fail(ctx, SLAG_ERR_OOM, "host allocation");
+        }
+        if (P > 0) CK(cudaMemcpyAsync(h_list, list, sizeof(uint32_t) * P, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_recb, ctx->srec_b, sizeof(float4) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_orig, ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < P; ++i) {
+            uint32_t gI;
+            memcpy(&gI, &h_recb[h_list[i]].z, 4);
+            out_list[i] = (int32_t)h_orig[gI];
+        }
+        free(h_list); free(h_orig); free(h_recb);
+    }
+    if (out_ranges) {
+        uint2 *h_r = (uint2 *)malloc(sizeof(uint2) * tiles);
+        if (!h_r) return fail(ctx, SLAG_ERR_OOM, "host allocation");
+        CK(cudaMemcpyAsync(h_r, ctx->ranges, sizeof(uint2) * tiles, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int64_t t = 0; t < tiles; ++t) { out_ranges[2 * t] = h_r[t].x; out_ranges[2 * t + 1] = h_r[t].y; }
+        free(h_r);
+    }
+    (void)keys;
+    return SLAG_OK;
+}
+
+slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_T, float *out_wsum,
+                              int32_t *out_count) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    slag_status s = check_camera(ctx, cam);
+    if (s != SLAG_OK) return s;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const CamParams cp = cam_params(cam);
+    const int64_t npx = (int64_t)cam->width * cam->height;
+    int64_t P = 0;
+    uint32_t *keys = nullptr, *list = nullptr;
+    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0);
+    if (s != SLAG_OK) return s;
+    if (npx > ctx->dbg_cap) {
+        int64_t c1 = ctx->dbg_cap, c2 = ctx->dbg_cap, c3 = ctx->dbg_cap;
+        CK(grow(ctx->dbg_T, c1, npx, st));
+        CK(grow(ctx->dbg_wsum, c2, npx, st));
+        CK(grow(ctx->dbg_count, c3, npx, st));
+        ctx->dbg_cap = c1;
+    }
+    CompositeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.cam = cp;
+    a.ranges = ctx->ranges;
+    a.list = list;
+    a.srec_a = ctx->srec_a;
+    a.srec_b = ctx->srec_b;
+    a.seg = nullptr;
+    a.weight_mode = ctx->weight_mode;
+    a.ctr = ctx->ctr;
+    a.overflow = reinterpret_cast<uint32_t *>(&ctx->ctr->pad[0]);
+    a.contrib = &ctx->ctr->contributions;
+    a.dbg_T = ctx->dbg_T;
+    a.dbg_wsum = ctx->dbg_wsum;
+    a.dbg_count = ctx->dbg_count;
+    a.accumulate = 0;
+    launch_composite(a, st);
+    CK(cudaGetLastError());
+    if (out_T) CK(cudaMemcpyAsync(out_T, ctx->dbg_T, sizeof(float) * npx, cudaMemcpyDeviceToHost, st));
+    if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->dbg_wsum, sizeof(float) * npx, cudaMemcpyDeviceToHost, st));
+    if (out_count) CK(cudaMemcpyAsync(out_count, ctx->dbg_count, sizeof(int32_t) * npx, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    (void)keys;
+    return SLAG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Internal declarations shared by the CUDA translation units of libslag.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/slag.h"
+
+namespace slag {
+
+constexpr int kTile = 16;          // screen tile edge in pixels
+constexpr int kBlockG = 128;       // Gaussians per aggregation block (key packs g & 127)
+constexpr int kHashSlots = 4;      // per-view (segment, weight) slots per Gaussian
+constexpr int kMaxK = 1024;        // largest top-k
+constexpr uint32_t kCulled = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// device-side records
+// ---------------------------------------------------------------------------
+
+// Per-view (segment, weight) table of one Gaussian. seg = -1 marks a free slot.
+struct __align__(16) HashEntry {
+    int32_t seg[kHashSlots];
+    float w[kHashSlots];
+};
+
+// Per-view counters written by kernels and read back once per view.
+struct ViewCounters {
+    uint32_t n_visible;
+    uint32_t bad_seg;                 // non-zero: a segment id outside [-1, M)
+    unsigned long long P;             // Gaussian-tile pairs
+    unsigned long long contributions; // composited (Gaussian, pixel) pairs (diagnostic render)
+    uint32_t pad[2];
+};
+
+struct CamParams {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float R[9];
+    float t[3];
+    float near_z, far_z;
+    int32_t tiles_x, tiles_y;
+};
+
+// ---------------------------------------------------------------------------
+// primitives (k_sort.cu)
+// ---------------------------------------------------------------------------
+
+// Scratch for radix sorts and scans; grows on demand.
+struct SortScratch {
+    uint32_t *hist = nullptr;      // 256 x tiles
+    size_t hist_cap = 0;
+    uint32_t *digit_tot = nullptr; // 256
+    uint32_t *partials = nullptr;  // scan partials
+    size_t partials_cap = 0;
+};
+
+cudaError_t scratch_reserve(SortScratch &s, int64_t n);
+void scratch_free(SortScratch &s);
+
+// Stable LSD radix sort of (key, value) pairs over the bit ranges listed in
+// shifts/widths (each width <= 8, applied in order). Ping-pongs between the
+// two buffers; returns true when the result is in the *_alt buffers.
+bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
+                    int64_t n, const int *shifts, const int *widths, int npass, SortScratch &s,
+                    cudaStream_t st);
+bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
+                    int64_t n, const int *shifts, const int *widths, int npass, SortScratch &s,
+                    cudaStream_t st);
+
+// Exclusive prefix sum of n uint32 values; writes the total to *d_total (may be null).
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *d_total,
+                        SortScratch &s, cudaStream_t st);
+
+// Splits [lo, lo + bits) into passes of at most 8 bits; returns the pass count.
+int digit_passes(int lo, int bits, int *shifts, int *widths);
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+// k_project.cu
+void launch_check_gaussians(const float *means, const float *scales, const float *quats,
+                            const float *opac, int64_t n, uint32_t *d_flag, cudaStream_t st);
+void launch_bbox(const float *means, int64_t n, uint32_t *d_bbox6, cudaStream_t st);
+void launch_morton(const float *means, int64_t n, const uint32_t *d_bbox6, uint32_t *codes,
+                   uint32_t *idx, cudaStream_t st);
+void launch_pack_gaussians(const float *means, const float *scales, const float *quats,
+                           const float *opac, int64_t n, const uint32_t *orig_of_int,
+                           float4 *mean_op, float4 *cov_a, float2 *cov_b, uint32_t *int_of_orig,
+                           cudaStream_t st);
+void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *cov_a,
+                    const float2 *cov_b, int64_t n, const uint32_t *orig_of_int, uint32_t *dkey_orig,
+                    uint32_t *dval_orig, float4 *rec_a, float4 *rec_b, uint2 *rect,
+                    ViewCounters *ctr, cudaStream_t st);
+void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, const ViewCounters *ctr,
+                          const float4 *rec_a, const float4 *rec_b, const uint2 *rect,
+                          float4 *srec_a, float4 *srec_b, uint2 *srect, uint32_t *stouched,
+                          cudaStream_t st);
+void launch_check_seg(const int32_t *seg, int64_t npx, int32_t M, ViewCounters *ctr, cudaStream_t st);
+
+// k_bin.cu
+void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int tiles_x,
+                 uint32_t *keys, uint32_t *vals, cudaStream_t st);
+void launch_ranges(const uint32_t *keys, int64_t P, uint2 *ranges, cudaStream_t st);
+
+// k_composite.cu
+struct CompositeArgs {
+    CamParams cam;
+    const uint2 *ranges;
+    const uint32_t *list;          // sorted values: depth rank of each pair
+    const float4 *srec_a, *srec_b; // records in depth-rank order
+    const int32_t *seg;            // H x W
+    int32_t view_base;             // column of segment 0 of this view
+    int32_t weight_mode;
+    HashEntry *hash;               // n entries (internal order)
+    unsigned long long *log_count;
+    unsigned long long log_cap;
+    uint64_t *log_key;
+    float *log_w;
+    float *s_ovf;                  // per-Gaussian weight of overflow triples
+    ViewCounters *ctr;
+    uint32_t *overflow;            // set when the triple log is full (never reset by a view)
+    unsigned long long *contrib;   // running count of composited (Gaussian, pixel) pairs
+    float *dbg_T, *dbg_wsum;       // nullable, H x W
+    int32_t *dbg_count;            // nullable
+    int accumulate;                // 0: compositing only (diagnostics)
+};
+void launch_composite(const CompositeArgs &a, cudaStream_t st);
+
+// k_accum.cu
+void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st);
+void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
+                    unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key,
+                    float *log_w, uint32_t *overflow, cudaStream_t st);
+void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaStream_t st);
+void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z,
+                    uint32_t *ucol, uint32_t *ustart, uint32_t *bstart, uint32_t *bend,
+                    cudaStream_t st);
+struct AggArgs {
+    const uint64_t *keys;
+    const float *w;
+    const uint32_t *uidx, *ucol, *ustart, *bstart, *bend;
+    const float *table;            // columns x D
+    const float *s_hi, *s_lo, *s_ovf;
+    const uint32_t *orig_of_int;
+    int64_t n;
+    int32_t D;
+    float *E;                      // n x D, caller order
+    float *inv_norm;               // n, caller order
+    float *wsum;                   // n, caller order
+    unsigned long long *touched;
+};
+void launch_aggregate(const AggArgs &a, int64_t nblocks, cudaStream_t st);
+
+// k_query.cu
+size_t query_cand_entries(int32_t B, int64_t n, int32_t k);
+void launch_query_topk(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n,
+                       int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
+                       float *out_scores, int32_t *out_count, cudaStream_t st);
+
+}  // namespace slag
