@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the lifting path on one B300 (or N replicas under torchrun).
+
+One step = one whole lifting job on the mid-scale workload: 300,000 Gaussians
+on 20 ellipsoid surfaces, 64 views of 960x540 with 64 Voronoi segments each,
+512-d float32 segment embeddings from 32 prototypes (seed 1), through
+slag_reset -> 64 x slag_add_view -> slag_finalize -> 1,000 top-10 cosine
+queries. Inputs are seeded synthetic data of that shape.
+
+Reported:
+  value  Gaussian-pixel contributions per second (whole job, device-resident inputs)
+  e2e    the same through host buffers: per step the segment maps and tables
+         are copied host->device, the embeddings, weight sums and query
+         results device->host, all inside the timed region
+  roofline  the stage with the largest device time, timed live with CUDA
+         events recorded by the library in its own stream
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload
+
+`--impl reference` times the CPU oracle alone (the reference arm).
+Under torchrun each rank runs its own replica of the job (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gaussian-pixel contribs/s & views/s, D=512: BF16/latent vs FP32 plain at stated cos err"
+UNIT = "contribs/s"
+WORKLOAD = "plain FP32 mid scale: 300k Gaussians on 20 ellipsoids, 64 views 960x540, 64 segments, D=512, +1000 top-10 queries"
+
+# Dense FP32 issue rate used as the compositing kernel's ALU roofline: 148 SMs x 128 FP32 lanes
+# x the maximum SM clock, one operation per lane per cycle (most of the work is not FMA).
+N_SM = 148
+FP32_LANES = 128
+# FP32 operations per evaluated (Gaussian, pixel) pair in the compositing loop: offsets (2),
+# quadratic form (9), exponent argument check (1), opacity product and cap (2), floor test (1),
+# transmittance update, stop test and weight (3), plus the exp itself on the SFU.
+OPS_PER_EVAL = 18
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="slag", choices=["slag", "reference"])
+    p.add_argument("--queries", type=int, default=1000)
+    p.add_argument("--k", type=int, default=10)
+    p.add_argument("--views", type=int, default=0, help="use only the first V views (0 = all)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _scene(views_limit=0):
+    import synth
+    s = synth.config_mid()
+    nv = s.n_views if not views_limit else min(views_limit, s.n_views)
+    views = [s.view(i) for i in range(nv)]
+    return s, views
+
+
+def _queries(views, B, seed=4):
+    rng = np.random.default_rng(seed)
+    Q = rng.standard_normal((B, views[0].table.shape[1])).astype(np.float32)
+    Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    return Q
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.device_id = device_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.device_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _device_id(torch, local):
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local)
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ----------------------------------------------------------------------------
+
+def _cpu_oracle_sample(scene, views, seconds):
+    """The oracle as it stands on the host cores, on whole views until `seconds` pass."""
+    from oracle import oracle as O
+    O.build()
+    cores = len(os.sched_getaffinity(0))
+    done_views, contrib = 0, 0
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(views) and time.perf_counter() - t0 < seconds:
+        batch = views[i:i + cores]
+        _, _, info = O.lift(scene.gaussians, batch, threads=cores)
+        contrib += sum(c for _, c in info)
+        done_views += len(batch)
+        i += len(batch)
+    dt = time.perf_counter() - t0
+    return {"value": contrib / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "views_per_s": done_views / dt,
+            "sample": "%d of %d views of the same workload (float64 factored oracle, views spread over %d "
+                      "threads, one accumulator per thread); %.1f s" % (done_views, len(views), cores, dt)}
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    scene, views = _scene(a.views)
+    per_step = []
+    s = None
+    for it in range(a.warmup + a.steps):
+        s = _cpu_oracle_sample(scene, views, max(2.0, a.cpu_seconds / 4))
+        if it >= a.warmup:
+            per_step.append(s)
+    value = float(np.mean([x["value"] for x in per_step]))
+    vps = float(np.mean([x["views_per_s"] for x in per_step]))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "views_per_s": vps,
+           "config": {"workload": WORKLOAD, "views": len(views), "l2": "n/a (host)"},
+           "cpu_baseline": dict(s, value=value),
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_slag(a):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2505_08124_b300 import slag as S
+    S.load_library()
+
+    scene, views = _scene(a.views)
+    g = scene.gaussians
+    D = scene.dim
+    Q = _queries(views, a.queries)
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+
+    # device-resident inputs
+    d_seg = [torch.from_numpy(v.seg).to(dev) for v in views]
+    d_tab = [torch.from_numpy(v.table).to(dev) for v in views]
+    d_Q = torch.from_numpy(Q).to(dev)
+    d_ids = torch.empty((a.queries, a.k), dtype=torch.int64, device=dev)
+    d_sc = torch.empty((a.queries, a.k), dtype=torch.float32, device=dev)
+    d_cnt = torch.empty(a.queries, dtype=torch.int32, device=dev)
+    d_w = torch.empty(g.n, dtype=torch.float32, device=dev)
+    cams = [v.camera for v in views]
+
+    L = S.Lifter(g, dim=D, stream=stream.cuda_stream)
+
+    def step_device():
+        L.reset()
+        for c, sg, tb in zip(cams, d_seg, d_tab):
+            L.add_view(c, sg, tb)
+        L.finalize(None, d_w)
+        L.query_batch(d_Q, a.k, d_ids, d_sc, d_cnt)
+
+    # host-resident inputs (pinned) for the end-to-end leg
+    h_seg = [torch.from_numpy(v.seg).pin_memory().numpy() for v in views]
+    h_tab = [torch.from_numpy(v.table).pin_memory().numpy() for v in views]
+    h_E = torch.empty((g.n, D), dtype=torch.float32).pin_memory().numpy()
+    h_w = torch.empty(g.n, dtype=torch.float32).pin_memory().numpy()
+    h_Q = torch.from_numpy(Q).pin_memory().numpy()
+
+    def step_host():
+        L.reset()
+        for c, sg, tb in zip(cams, h_seg, h_tab):
+            L.add_view(c, sg, tb)
+        rc = L._lib.slag_finalize(L._h, h_E.ctypes.data, h_w.ctypes.data, 0)
+        L._check(rc, "slag_finalize")
+        ids, sc, cnt = L.query_batch(h_Q, a.k)
+        return ids
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(a.warmup):
+        step_device()
+    barrier()
+    L.set_profiling(True)
+    L.profile(reset=True)
+    st0 = L.stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(_device_id(torch, local)) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(a.steps):
+            step_device()
+        e1.record(stream)
+        barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    prof = L.profile(reset=True)
+    L.set_profiling(False)
+    stats = L.stats()
+    contrib_per_step = stats["contributions"]          # reset() clears the counters each step
+    evals_per_step = stats["evaluations"]
+    views_per_step = len(views)
+    total_units = contrib_per_step * a.steps * ws
+    value = total_units / (ms / 1e3)
+    views_per_s = views_per_step * a.steps * ws / (ms / 1e3)
+
+    # end to end through host buffers
+    e2e = None
+    if not a.no_e2e:
+        step_host()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            step_host()
+        barrier()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        h2d = sum(x.nbytes for x in h_seg) + sum(x.nbytes for x in h_tab) + h_Q.nbytes
+        d2h = h_E.nbytes + h_w.nbytes + a.queries * a.k * (8 + 4) + a.queries * 4
+        e2e = {"value": contrib_per_step * a.steps * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "views_per_s": views_per_step * a.steps * ws / dt,
+               "ms_per_step": dt * 1e3 / a.steps}
+
+    # roofline of the stage with the largest device time
+    import json as _j
+    peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    dominant = max(prof, key=lambda k: prof[k][0])
+    comp_ms, comp_spans = prof["composite"]
+    launches_per_step = len(views)
+    comp_ms_per_launch = comp_ms / max(1, comp_spans)
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    peak_tops = N_SM * FP32_LANES * sm_max * 1e6 / 1e12
+    evals_per_launch = evals_per_step / max(1, launches_per_step)
+    achieved = evals_per_launch * OPS_PER_EVAL / (comp_ms_per_launch / 1e3) / 1e12
+    roofline = {"kernel": "composite_k", "bound": "alu", "achieved": achieved, "peak": peak_tops,
+                "unit": "TOPS (fp32 issue)", "frac": achieved / peak_tops, "traffic": None,
+                "evaluations_per_launch": evals_per_launch, "ms_per_launch": comp_ms_per_launch,
+                "peak_source": "derived: %d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json)"
+                               % (N_SM, FP32_LANES, sm_max),
+                "dominant_stage": dominant}
+
+    gpu_launches = _count_launches(prof, a)
+    cpu = None
+    if rank == 0 and not a.no_cpu:
+        cpu = _cpu_oracle_sample(scene, views, a.cpu_seconds)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "views_per_s": views_per_s,
+               "config": {"workload": WORKLOAD, "gaussians": g.n, "views": len(views), "resolution": "960x540",
+                          "segments": 64, "dim": D, "queries": a.queries, "k": a.k,
+                          "parallelism": "replicas x%d" % ws,
+                          "l2": "inputs larger than L2 (133 MB of segment maps + 8 MB tables per step; "
+                                "614 MB embeddings written per step)"},
+               "clocks": clk.summary(),
+               "e2e": e2e,
+               "roofline": roofline,
+               "cpu_baseline": cpu,
+               "gpu_launches": gpu_launches,
+               "stages_ms_per_step": {k: v[0] / a.steps for k, v in prof.items()},
+               "stats_per_step": stats}
+        print(json.dumps(out), flush=True)
+    L.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _count_launches(prof, a):
+    """Kernel launches of the library per timed region (counted from the pipeline's structure)."""
+    views = prof["composite"][1] // max(1, a.steps) if prof["composite"][1] else 0
+    # per view: check_seg, project, 4 depth-sort passes x 3, gather, scan x3, emit, tile sort
+    # 2 passes x 3, ranges, composite, consume
+    per_view = 1 + 1 + 12 + 1 + 3 + 1 + 6 + 1 + 1 + 1
+    # per finalize: log sort (~4 passes x 3), flags, scan x3, uniques, aggregate; reset: hash init
+    per_step = 12 + 1 + 3 + 1 + 1 + 1 + 2   # + query: score + merge
+    return int((views * per_view + per_step) * a.steps)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_slag(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -99,6 +99,8 @@ typedef struct {
     int64_t last_pairs;      /* P of the last view */
     int64_t last_contributions;
     int64_t touched;         /* Gaussians with sum w > 0 at the last finalize */
+    int64_t evaluations;     /* sum over views of (Gaussian, pixel) pairs visited before each
+                                pixel ended (the compositing work, contributing or not) */
 } slag_stats;
 
 /* Create a context over the Gaussian set (Method, Rasterizer_SLAG statement:
@@ -176,6 +178,34 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
  * over every contributing Gaussian and the number of contributors. */
 slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_T, float *out_wsum,
                               int32_t *out_count);
+
+/* ---- diagnostics: per-stage device time ---------------------------------- */
+
+/* Stages timed with CUDA events recorded in the context's stream. */
+enum {
+    SLAG_STAGE_PROJECT = 0,    /* projection, depth sort, depth-rank gather, tile-count scan */
+    SLAG_STAGE_BIN = 1,        /* pair emission, stable sort by tile, tile ranges */
+    SLAG_STAGE_COMPOSITE = 2,  /* compositing, masking, in-tile segment binning */
+    SLAG_STAGE_CONSUME = 3,    /* per-view (segment, weight) tables -> triple log */
+    SLAG_STAGE_LOG_SORT = 4,   /* finalize: sort of the triple log, distinct columns */
+    SLAG_STAGE_AGGREGATE = 5,  /* finalize: blocked contraction and normalisation */
+    SLAG_STAGE_QUERY = 6,      /* cosine scores and top-k */
+    SLAG_STAGE_COUNT = 7
+};
+
+typedef struct {
+    double ms[SLAG_STAGE_COUNT];       /* summed device time per stage */
+    int64_t spans[SLAG_STAGE_COUNT];   /* number of timed spans per stage */
+} slag_profile;
+
+/* Turn per-stage timing on (1) or off (0). Off by default; when on, every
+ * stage is bracketed by two events in the context's stream (no extra
+ * synchronisation: spans are resolved at the calls that synchronise). */
+slag_status slag_set_profiling(slag_ctx *ctx, int32_t enable);
+
+/* Synchronises the context's stream, adds every finished span to *out and,
+ * when reset is non-zero, clears the totals. */
+slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset);
 
 #ifdef __cplusplus
 }

@@ -114,7 +114,7 @@ __global__ void uniques_k(const uint64_t *__restrict__ keys, const uint32_t *__r
 constexpr int kKC = 32;    // columns per chunk
 constexpr int kDS = 128;   // embedding dims per slice
 
-__global__ void __launch_bounds__(256) aggregate_k(const AggArgs a) {
+__global__ void __launch_bounds__(256, 1) aggregate_k(const AggArgs a) {
     __shared__ __align__(16) float Wd[kKC][kBlockG];
     __shared__ __align__(16) float Es[kKC][kDS];
     const int tid = threadIdx.x;
@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(256) aggregate_k(const AggArgs a) {
     const int64_t b = blockIdx.x;
     const uint32_t ts = a.bstart[b], te = a.bend[b];
     const bool any = ts < te;
-    const uint32_t u0 = any ? a.uidx[ts] : 0u, u1 = any ? a.uidx[te - 1] + 1u : 0u;
+    // unique (block, column) index of triple t = exclusive count + own flag - 1; a block's first
+    // triple always starts a new column
+    const uint32_t u0 = any ? a.uidx[ts] : 0u, u1 = any ? a.uidx[te - 1] + a.flags[te - 1] : 0u;
 
     float S[8];
 #pragma unroll
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(256) aggregate_k(const AggArgs a) {
             __syncthreads();
             for (uint32_t t = t0 + tid; t < t1; t += 256) {
                 const uint64_t key = a.keys[t];
-                const uint32_t lc = a.uidx[t] - uc;
+                const uint32_t lc = a.uidx[t] + a.flags[t] - 1u - uc;
                 atomicAdd(&Wd[lc][(int)(key & 127u)], a.w[t]);
             }
             for (int e = tid; e < kKC * kDS / 4; e += 256) {

@@ -78,7 +78,7 @@ __device__ void hash_add(const CompositeArgs &a, uint32_t g, int32_t seg, float 
     append_triple(a, g, seg, w);
 }
 
-__global__ void __launch_bounds__(kThreads) composite_k(const CompositeArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) composite_k(const CompositeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) composite_k(const CompositeArgs a) {
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
     float T = 1.f, wsum = 0.f;
-    int count = 0;
+    int count = 0, evals = 0;
     bool done = !inside;
 
     const uint2 rg = a.ranges[tile];
@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(kThreads) composite_k(const CompositeArgs a) {
                 const int gi = c * 32 + j;
                 float wv = 0.f;
                 if (!done && gi < nb) {
+                    ++evals;
                     const float4 ra = sm.rec_a[gi];
                     const float4 rb = sm.rec_b[gi];
                     const float dx = ra.x - pxc, dy = ra.y - pyc;
@@ -244,9 +245,13 @@ __global__ void __launch_bounds__(kThreads) composite_k(const CompositeArgs a) {
         if (a.dbg_wsum) a.dbg_wsum[pi] = wsum;
         if (a.dbg_count) a.dbg_count[pi] = count;
     }
-    unsigned long long cnt = (unsigned long long)count;
-    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    unsigned long long cnt = (unsigned long long)count, ev = (unsigned long long)evals;
+    for (int o = 16; o; o >>= 1) {
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    }
     if (lane == 0 && cnt) atomicAdd(a.contrib, cnt);
+    if (lane == 0 && ev && a.evals) atomicAdd(a.evals, ev);
 }
 
 }  // namespace

@@ -16,6 +16,7 @@
 
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "slag_internal.cuh"
 
@@ -55,12 +56,12 @@ struct slag_ctx {
 
     ViewCounters *ctr = nullptr;             // device, reset per view
     unsigned long long *totals = nullptr;    // device: [0] triples in the log, [1] contributions,
-                                             // [2] low word: log overflow flag
+                                             // [2] low word: log overflow flag, [3] evaluations
     unsigned long long *log_count = nullptr; // = totals
     unsigned long long *contrib = nullptr;   // = totals + 1
     struct HostCounters {
         ViewCounters v;
-        unsigned long long totals[3];
+        unsigned long long totals[4];
         unsigned long long touched;
     } *hc = nullptr;                         // pinned host
     unsigned long long contrib_before_last = 0;
@@ -96,6 +97,16 @@ struct slag_ctx {
 
     SortScratch scratch;
     slag_stats stats{};
+
+    // per-stage timing
+    struct Span {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    bool prof_on = false;
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> event_pool;
+    slag_profile prof{};
 };
 
 namespace {
@@ -181,6 +192,44 @@ CamParams cam_params(const slag_camera *c) {
     return p;
 }
 
+cudaEvent_t take_event(slag_ctx *ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Opens a timing span of `stage` in the context's stream (no-op when profiling is off).
+void span_begin(slag_ctx *ctx, int stage) {
+    if (!ctx->prof_on) return;
+    slag_ctx::Span sp{stage, take_event(ctx), take_event(ctx)};
+    cudaEventRecord(sp.a, ctx->stream);
+    ctx->spans.push_back(sp);
+}
+
+void span_end(slag_ctx *ctx) {
+    if (!ctx->prof_on || ctx->spans.empty()) return;
+    cudaEventRecord(ctx->spans.back().b, ctx->stream);
+}
+
+// Adds every finished span to the totals (call after a stream synchronisation).
+void spans_resolve(slag_ctx *ctx) {
+    for (auto &sp : ctx->spans) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
+            ctx->prof.ms[sp.stage] += ms;
+            ctx->prof.spans[sp.stage] += 1;
+        }
+        ctx->event_pool.push_back(sp.a);
+        ctx->event_pool.push_back(sp.b);
+    }
+    ctx->spans.clear();
+}
+
 int ceil_log2(uint64_t v) {
     int b = 0;
     while ((1ull << b) < v) ++b;
@@ -195,6 +244,7 @@ slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->n;
     CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
+    span_begin(ctx, SLAG_STAGE_PROJECT);
     if (seg_check) launch_check_seg(seg_check, (int64_t)cp.width * cp.height, M, ctx->ctr, st);
     launch_project(cp, ctx->mean_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, ctx->dkey[0], ctx->dval[0],
                    ctx->rec_a, ctx->rec_b, ctx->rect, ctx->ctr, st);
@@ -206,10 +256,12 @@ slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_
     launch_gather_sorted(sorted_vals, n, ctx->ctr, ctx->rec_a, ctx->rec_b, ctx->rect, ctx->srec_a, ctx->srec_b,
                          ctx->srect, ctx->stouched, st);
     exclusive_scan_u32(ctx->stouched, ctx->offsets, n, &ctx->ctr->P, ctx->scratch, st);
+    span_end(ctx);
     CK(cudaMemcpyAsync(&ctx->hc->v, ctx->ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ctx->hc->totals, ctx->totals, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->hc->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    spans_resolve(ctx);
     if (ctx->hc->v.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
     const int64_t P = (int64_t)ctx->hc->v.P;
     if (P > 0x7fffffffLL) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^31-1 Gaussian-tile pairs in one view");
@@ -227,12 +279,14 @@ slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_
     CK(grow(ctx->ranges, ctx->ranges_cap, tiles, st));
     CK(cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)tiles, st));
     uint32_t nv = ctx->hc->v.n_visible;
+    span_begin(ctx, SLAG_STAGE_BIN);
     launch_emit(ctx->srect, ctx->offsets, nv, cp.tiles_x, ctx->pkey[0], ctx->pval[0], st);
     np = digit_passes(0, ceil_log2((uint64_t)tiles), shifts, widths);
     alt = radix_sort_u32(ctx->pkey[0], ctx->pkey[1], ctx->pval[0], ctx->pval[1], P, shifts, widths, np,
                          ctx->scratch, st);
     uint32_t *keys = ctx->pkey[alt ? 1 : 0];
     launch_ranges(keys, P, ctx->ranges, st);
+    span_end(ctx);
     *P_out = P;
     *keys_out = keys;
     *list_out = ctx->pval[alt ? 1 : 0];
@@ -291,12 +345,12 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     }
     CA(cudaMallocHost((void **)&ctx->hc, sizeof(slag_ctx::HostCounters)));
     CA(dalloc(&ctx->ctr, 1));
-    CA(dalloc(&ctx->totals, 3));
+    CA(dalloc(&ctx->totals, 4));
     ctx->log_count = ctx->totals;
     ctx->contrib = ctx->totals + 1;
     CA(dalloc(&ctx->touched, 1));
     CA(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
-    CA(cudaMemsetAsync(ctx->totals, 0, 3 * sizeof(unsigned long long), st));
+    CA(cudaMemsetAsync(ctx->totals, 0, 4 * sizeof(unsigned long long), st));
     CA(scratch_reserve(ctx->scratch, n));
 
     // validation
@@ -400,13 +454,18 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     a.ctr = ctx->ctr;
     a.overflow = reinterpret_cast<uint32_t *>(ctx->totals + 2);
     a.contrib = ctx->contrib;
+    a.evals = ctx->totals + 3;
     a.dbg_T = a.dbg_wsum = nullptr;
     a.dbg_count = nullptr;
     a.accumulate = 1;
+    span_begin(ctx, SLAG_STAGE_COMPOSITE);
     launch_composite(a, st);
+    span_end(ctx);
+    span_begin(ctx, SLAG_STAGE_CONSUME);
     launch_consume(ctx->hash, ctx->n, (int32_t)ctx->table_rows, ctx->s_hi, ctx->s_lo, ctx->log_count,
                    (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
                    reinterpret_cast<uint32_t *>(ctx->totals + 2), st);
+    span_end(ctx);
     CK(cudaGetLastError());
     ctx->table_rows += M;
     ctx->stats.views += 1;
@@ -422,10 +481,11 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     if (ctx->stats.views == 0) return fail(ctx, SLAG_ERR_STATE, "finalize before any view");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    CK(cudaMemcpyAsync(ctx->hc->totals, ctx->totals, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->hc->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     ctx->stats.contributions = (int64_t)ctx->hc->totals[1];
+    ctx->stats.evaluations = (int64_t)ctx->hc->totals[3];
     ctx->stats.last_contributions = (int64_t)(ctx->hc->totals[1] - ctx->contrib_before_last);
     if (ctx->hc->totals[2]) ctx->log_overflowed = true;
     if (ctx->log_overflowed) return fail(ctx, SLAG_ERR_CAPACITY, "the triple log overflowed in some view");
@@ -449,6 +509,7 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
             ctx->fin_cap = c1;
             CK(scratch_reserve(ctx->scratch, Z));
         }
+        span_begin(ctx, SLAG_STAGE_LOG_SORT);
         // sort by (block, column, Gaussian): bits [0, 7 + col_bits) then [39, 39 + block_bits)
         int shifts[16], widths[16];
         int np = digit_passes(0, 7 + ceil_log2((uint64_t)ctx->table_rows), shifts, widths);
@@ -467,10 +528,12 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
         launch_unique_flags(ctx->log_key, Z, ctx->flags, st);
         exclusive_scan_u32(ctx->flags, ctx->uidx, Z, nullptr, ctx->scratch, st);
         launch_uniques(ctx->log_key, ctx->flags, ctx->uidx, Z, ctx->ucol, ctx->ustart, ctx->bstart, ctx->bend, st);
+        span_end(ctx);
     }
     AggArgs g;
     g.keys = ctx->log_key;
     g.w = ctx->log_w;
+    g.flags = ctx->flags;
     g.uidx = ctx->uidx;
     g.ucol = ctx->ucol;
     g.ustart = ctx->ustart;
@@ -487,13 +550,16 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     g.inv_norm = ctx->inv_norm;
     g.wsum = ctx->wsum;
     g.touched = ctx->touched;
+    span_begin(ctx, SLAG_STAGE_AGGREGATE);
     launch_aggregate(g, nblocks, st);
+    span_end(ctx);
     CK(cudaGetLastError());
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (out_emb) CK(cudaMemcpyAsync(out_emb, ctx->E, sizeof(float) * (size_t)(n * ctx->D), kind, st));
     if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, kind, st));
     CK(cudaMemcpyAsync(&ctx->hc->touched, ctx->touched, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    spans_resolve(ctx);
     ctx->stats.touched = (int64_t)ctx->hc->touched;
     ctx->finalized = true;
     return SLAG_OK;
@@ -537,8 +603,10 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
         scores = ctx->qscores;
         cnt = ctx->qcount;
     }
+    span_begin(ctx, SLAG_STAGE_QUERY);
     launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i, ids, scores, cnt,
                       st);
+    span_end(ctx);
     CK(cudaGetLastError());
     if (!on_device) {
         CK(cudaMemcpyAsync(out_ids, ids, sizeof(int64_t) * (size_t)B * k, cudaMemcpyDeviceToHost, st));
@@ -563,7 +631,7 @@ slag_status slag_reset(slag_ctx *ctx) {
     CK(cudaMemsetAsync(ctx->s_hi, 0, sizeof(float) * n, st));
     CK(cudaMemsetAsync(ctx->s_lo, 0, sizeof(float) * n, st));
     CK(cudaMemsetAsync(ctx->s_ovf, 0, sizeof(float) * n, st));
-    CK(cudaMemsetAsync(ctx->totals, 0, 3 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(ctx->totals, 0, 4 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
     CK(cudaGetLastError());
     ctx->contrib_before_last = 0;
@@ -598,8 +666,26 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->table); dfree(ctx->E); dfree(ctx->inv_norm); dfree(ctx->wsum);
     dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);
     scratch_free(ctx->scratch);
+    for (auto &sp : ctx->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->hc) cudaFreeHost(ctx->hc);
     delete ctx;
+}
+
+slag_status slag_set_profiling(slag_ctx *ctx, int32_t enable) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    ctx->prof_on = enable != 0;
+    return SLAG_OK;
+}
+
+slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset) {
+    if (!ctx || !out) return SLAG_ERR_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    spans_resolve(ctx);
+    *out = ctx->prof;
+    if (reset) ctx->prof = slag_profile{};
+    return SLAG_OK;
 }
 
 slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_touched, int64_t *out_P,
@@ -660,7 +746,13 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
         if (!h_r) return fail(ctx, SLAG_ERR_OOM, "host allocation");
         CK(cudaMemcpyAsync(h_r, ctx->ranges, sizeof(uint2) * tiles, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        for (int64_t t = 0; t < tiles; ++t) { out_ranges[2 * t] = h_r[t].x; out_ranges[2 * t + 1] = h_r[t].y; }
+        // an empty tile is reported as [e, e) with e the end of the tiles before it
+        int64_t at = 0;
+        for (int64_t t = 0; t < tiles; ++t) {
+            if (h_r[t].y > h_r[t].x) at = h_r[t].y;
+            out_ranges[2 * t] = h_r[t].y > h_r[t].x ? (int64_t)h_r[t].x : at;
+            out_ranges[2 * t + 1] = h_r[t].y > h_r[t].x ? (int64_t)h_r[t].y : at;
+        }
         free(h_r);
     }
     (void)keys;

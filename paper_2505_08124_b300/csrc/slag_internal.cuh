@@ -122,6 +122,7 @@ struct CompositeArgs {
     ViewCounters *ctr;
     uint32_t *overflow;            // set when the triple log is full (never reset by a view)
     unsigned long long *contrib;   // running count of composited (Gaussian, pixel) pairs
+    unsigned long long *evals;     // running count of visited (Gaussian, pixel) pairs
     float *dbg_T, *dbg_wsum;       // nullable, H x W
     int32_t *dbg_count;            // nullable
     int accumulate;                // 0: compositing only (diagnostics)
@@ -140,7 +141,9 @@ void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t 
 struct AggArgs {
     const uint64_t *keys;
     const float *w;
-    const uint32_t *uidx, *ucol, *ustart, *bstart, *bend;
+    const uint32_t *flags;         // 1 where a triple starts a new (block, column)
+    const uint32_t *uidx;          // exclusive prefix count of flags
+    const uint32_t *ucol, *ustart, *bstart, *bend;
     const float *table;            // columns x D
     const float *s_hi, *s_lo, *s_ovf;
     const uint32_t *orig_of_int;

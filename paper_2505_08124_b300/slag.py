@@ -1,0 +1,273 @@
+"""Thin Python binding of libslag (ctypes; argument marshalling only).
+
+Every step of the lifting path runs in the library's CUDA kernels; this
+module only converts arguments. Host inputs are numpy arrays; device inputs
+are torch CUDA tensors (passed by data pointer). There is no fallback: when
+libslag.so is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libslag.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY = 1, 2, 3, 4, 5, 6
+_NAMES = {1: "INVALID_ARG", 2: "STATE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "CAPACITY"}
+WEIGHT_ALPHA_T, WEIGHT_KERNEL = 0, 1
+PREC_FP32 = 0
+
+
+class SlagError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("slag error %s (%d): %s" % (_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+class CCamera(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3),
+                ("near_z", ctypes.c_float), ("far_z", ctypes.c_float)]
+
+
+class CGaussians(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("means", ctypes.c_void_p), ("scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacities", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class COptions(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("precision", ctypes.c_int32), ("weight_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+
+
+class CStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("views", "pairs", "contributions", "triples", "columns",
+                                               "last_pairs", "last_contributions", "touched",
+                                               "evaluations")]
+
+
+_lib = None
+
+EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_query_batch", "slag_reset",
+           "slag_get_stats", "slag_last_error", "slag_destroy", "slag_bin_view", "slag_render_debug",
+           "slag_set_profiling", "slag_get_profile")
+STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
+
+
+class CProfile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * len(STAGES)), ("spans", ctypes.c_int64 * len(STAGES))]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libslag.so (once). Raises if it is missing: there is no other implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libslag.so not found at %s: build it with `python -m paper_2505_08124_b300.build`"
+                           % path)
+    lib = ctypes.CDLL(path)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.slag_create.argtypes = [ctypes.POINTER(CGaussians), ctypes.POINTER(COptions), ctypes.POINTER(P)]
+    lib.slag_add_view.argtypes = [P, ctypes.POINTER(CCamera), P, P, i32, i32]
+    lib.slag_finalize.argtypes = [P, P, P, i32]
+    lib.slag_query.argtypes = [P, P, i32, P, P, P]
+    lib.slag_query_batch.argtypes = [P, P, i32, i32, P, P, P, i32]
+    lib.slag_reset.argtypes = [P]
+    lib.slag_get_stats.argtypes = [P, ctypes.POINTER(CStats)]
+    lib.slag_last_error.argtypes = [P]
+    lib.slag_last_error.restype = ctypes.c_char_p
+    lib.slag_destroy.argtypes = [P]
+    lib.slag_destroy.restype = None
+    lib.slag_bin_view.argtypes = [P, ctypes.POINTER(CCamera), P, P, P, i64, P]
+    lib.slag_render_debug.argtypes = [P, ctypes.POINTER(CCamera), P, P, P]
+    lib.slag_set_profiling.argtypes = [P, i32]
+    lib.slag_get_profile.argtypes = [P, ctypes.POINTER(CProfile), i32]
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if f.restype is ctypes.c_int:   # default
+            f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, on_device, keepalive) of a numpy array or a torch CUDA tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("torch tensors must be contiguous")
+        want = {np.float32: "torch.float32", np.int32: "torch.int32", np.int64: "torch.int64"}[dtype]
+        if str(x.dtype) != want:
+            raise TypeError("expected %s, got %s" % (want, x.dtype))
+        return ctypes.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
+
+def camera_struct(cam) -> CCamera:
+    c = CCamera()
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.R[:] = [float(v) for v in np.asarray(cam.R, np.float32).reshape(9)]
+    c.t[:] = [float(v) for v in np.asarray(cam.t, np.float32).reshape(3)]
+    c.near_z, c.far_z = float(getattr(cam, "near", 0.01)), float(getattr(cam, "far", 100.0))
+    return c
+
+
+class Lifter:
+    """One lifting context: a fixed Gaussian set, views added one at a time."""
+
+    def __init__(self, gaussians, dim: int = 512, weight_mode: int = WEIGHT_ALPHA_T,
+                 stream: Optional[int] = None):
+        self._lib = load_library()
+        self.n = int(gaussians.means.shape[0])
+        self.dim = int(dim)
+        ptrs = [_ptr(getattr(gaussians, k), np.float32) for k in ("means", "scales", "quats", "opacities")]
+        dev = {p[1] for p in ptrs}
+        if len(dev) != 1:
+            raise ValueError("Gaussian arrays must all be on the host or all on the device")
+        g = CGaussians(self.n, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], dev.pop())
+        o = COptions(self.dim, PREC_FP32, int(weight_mode), 0, ctypes.c_void_p(stream) if stream else None)
+        h = ctypes.c_void_p()
+        rc = self._lib.slag_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h))
+        if rc != OK:
+            raise SlagError(rc, "slag_create")
+        self._h = h
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, rc: int, what: str):
+        if rc != OK:
+            raise SlagError(rc, "%s: %s" % (what, self._lib.slag_last_error(self._h).decode()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.slag_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the path -------------------------------------------------------------
+    def add_view(self, camera, seg, table):
+        sp, sdev, sk = _ptr(seg, np.int32)
+        tp, tdev, tk = _ptr(table, np.float32)
+        if sdev != tdev:
+            raise ValueError("segment map and table must both be host or both device")
+        M = int(table.shape[0])
+        if int(table.shape[1]) != self.dim:
+            raise ValueError("table has %d columns, context dim is %d" % (table.shape[1], self.dim))
+        if tuple(seg.shape) != (int(camera.height), int(camera.width)):
+            raise ValueError("segment map shape %s does not match the camera" % (tuple(seg.shape),))
+        c = camera_struct(camera)
+        self._check(self._lib.slag_add_view(self._h, ctypes.byref(c), sp, tp, M, sdev), "slag_add_view")
+        del sk, tk
+
+    def finalize(self, out_emb=None, out_wsum=None, want_emb: bool = True):
+        """Returns (E, wsum). With torch CUDA outputs given, fills them; else returns numpy arrays."""
+        if out_emb is None and out_wsum is None:
+            E = np.empty((self.n, self.dim), np.float32) if want_emb else None
+            w = np.empty(self.n, np.float32)
+            ep = E.ctypes.data_as(ctypes.c_void_p) if E is not None else None
+            self._check(self._lib.slag_finalize(self._h, ep, w.ctypes.data_as(ctypes.c_void_p), 0), "slag_finalize")
+            return E, w
+        ep, edev, _ = _ptr(out_emb, np.float32)
+        wp, wdev, _ = _ptr(out_wsum, np.float32)
+        dev = edev if out_emb is not None else wdev
+        self._check(self._lib.slag_finalize(self._h, ep, wp, dev), "slag_finalize")
+        return out_emb, out_wsum
+
+    def query(self, q, k: int):
+        q = np.ascontiguousarray(q, np.float32)
+        ids = np.empty(k, np.int64)
+        sc = np.empty(k, np.float32)
+        cnt = ctypes.c_int32()
+        self._check(self._lib.slag_query(self._h, q.ctypes.data_as(ctypes.c_void_p), k,
+                                         ids.ctypes.data_as(ctypes.c_void_p), sc.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.byref(cnt)), "slag_query")
+        return ids[:cnt.value], sc[:cnt.value]
+
+    def query_batch(self, Q, k: int, out_ids=None, out_scores=None, out_count=None):
+        """Host numpy Q -> (ids, scores, count) numpy; torch CUDA Q -> fills the given torch outputs."""
+        B = int(Q.shape[0])
+        if _is_torch(Q) and Q.is_cuda:
+            qp, _, _ = _ptr(Q, np.float32)
+            ip, _, _ = _ptr(out_ids, np.int64)
+            sp, _, _ = _ptr(out_scores, np.float32)
+            cp, _, _ = _ptr(out_count, np.int32)
+            self._check(self._lib.slag_query_batch(self._h, qp, B, k, ip, sp, cp, 1), "slag_query_batch")
+            return out_ids, out_scores, out_count
+        Qa = np.ascontiguousarray(Q, np.float32)
+        ids = np.empty((B, k), np.int64)
+        sc = np.empty((B, k), np.float32)
+        cnt = np.empty(B, np.int32)
+        self._check(self._lib.slag_query_batch(self._h, Qa.ctypes.data_as(ctypes.c_void_p), B, k,
+                                               ids.ctypes.data_as(ctypes.c_void_p),
+                                               sc.ctypes.data_as(ctypes.c_void_p),
+                                               cnt.ctypes.data_as(ctypes.c_void_p), 0), "slag_query_batch")
+        return ids, sc, cnt
+
+    def reset(self):
+        self._check(self._lib.slag_reset(self._h), "slag_reset")
+
+    def stats(self) -> dict:
+        s = CStats()
+        self._check(self._lib.slag_get_stats(self._h, ctypes.byref(s)), "slag_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in CStats._fields_}
+
+    # -- diagnostics ----------------------------------------------------------
+    def set_profiling(self, on: bool = True):
+        self._check(self._lib.slag_set_profiling(self._h, 1 if on else 0), "slag_set_profiling")
+
+    def profile(self, reset: bool = False) -> dict:
+        """{stage: (device ms summed, spans)} from events recorded in the context's stream."""
+        p = CProfile()
+        self._check(self._lib.slag_get_profile(self._h, ctypes.byref(p), 1 if reset else 0), "slag_get_profile")
+        return {name: (float(p.ms[i]), int(p.spans[i])) for i, name in enumerate(STAGES)}
+
+    def bin_view(self, camera):
+        """(tiles_touched[n], list[P] caller ids grouped by tile, ranges[tiles, 2])."""
+        c = camera_struct(camera)
+        P = ctypes.c_int64()
+        self._check(self._lib.slag_bin_view(self._h, ctypes.byref(c), None, ctypes.byref(P), None, 0, None),
+                    "slag_bin_view")
+        tiles = ((int(camera.width) + 15) // 16) * ((int(camera.height) + 15) // 16)
+        touched = np.empty(self.n, np.uint32)
+        lst = np.empty(max(P.value, 1), np.int32)
+        rng = np.empty((tiles, 2), np.int64)
+        self._check(self._lib.slag_bin_view(self._h, ctypes.byref(c), touched.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.byref(P), lst.ctypes.data_as(ctypes.c_void_p), lst.shape[0],
+                                            rng.ctypes.data_as(ctypes.c_void_p)), "slag_bin_view")
+        return touched, lst[:P.value], rng
+
+    def render_debug(self, camera):
+        """Per pixel (final transmittance, sum of weights, contributor count)."""
+        c = camera_struct(camera)
+        H, W = int(camera.height), int(camera.width)
+        T = np.empty((H, W), np.float32)
+        ws = np.empty((H, W), np.float32)
+        cnt = np.empty((H, W), np.int32)
+        self._check(self._lib.slag_render_debug(self._h, ctypes.byref(c), T.ctypes.data_as(ctypes.c_void_p),
+                                                ws.ctypes.data_as(ctypes.c_void_p),
+                                                cnt.ctypes.data_as(ctypes.c_void_p)), "slag_render_debug")
+        return T, ws, cnt

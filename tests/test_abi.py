@@ -1,0 +1,66 @@
+"""CPU-side checks of the C-ABI library: it builds, loads and exports every declared entry point.
+
+No compute call is made here (this machine may have no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(slag_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_08124_b300 import build
+    build.build()
+    from paper_2505_08124_b300 import slag
+    return slag.load_library()
+
+
+def test_header_declares_the_path():
+    d = _declared()
+    for name in ("slag_create", "slag_add_view", "slag_finalize", "slag_query"):
+        assert name in d
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in sorted(_declared()):
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_binding_lists_every_export(lib):
+    from paper_2505_08124_b300 import slag
+    assert set(slag.EXPORTS) <= _declared()
+    assert _declared() <= set(slag.EXPORTS) | {n for n in _declared() if n.startswith("slag_noalloc")}
+
+
+def test_struct_layouts_match_header():
+    from paper_2505_08124_b300 import slag
+    # slag_camera: 4 floats, 2 int32, 9 + 3 floats, 2 floats
+    assert ctypes.sizeof(slag.CCamera) == 4 * (4 + 2 + 9 + 3 + 2)
+    assert ctypes.sizeof(slag.CGaussians) == 8 + 4 * 8 + 8
+    assert ctypes.sizeof(slag.COptions) == 16 + 8
+    assert ctypes.sizeof(slag.CStats) == 9 * 8
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2505_08124_b300 import slag
+    saved = slag._lib
+    slag._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            slag.load_library(str(tmp_path / "nope.so"))
+    finally:
+        slag._lib = saved
