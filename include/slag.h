@@ -146,6 +146,38 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
 slag_status slag_query(slag_ctx *ctx, const float *q, int32_t k, int64_t *out_ids,
                        float *out_scores, int32_t *out_count);
 
+/* Allocation-free cosine top-k over embeddings the caller holds on the
+ * device. The paper has no counterpart: this entry point exists for callers
+ * that must not allocate device memory once running -- a query service on a
+ * robot or embedded board that reserves its memory at start-up (cudaMalloc can
+ * synchronise the device and take unbounded time), or an application whose
+ * device memory is owned by its own allocator. It runs the same scoring and
+ * selection kernels as slag_query_batch and allocates nothing: its scratch is
+ * one 16 MiB array inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   E: n x dim float32 row-major (device, 16-byte aligned), e.g. the output of
+ *   slag_finalize; wsum: n float32 (device, nullable) -- rows with wsum <= 0
+ *   are not candidates; rows with a zero norm never are. Q: B x dim float32
+ *   (device, 16-byte aligned). Outputs (device): out_ids B x k int64,
+ *   out_scores B x k float32, out_count B int32 (nullable), with the ordering,
+ *   candidates and -1 padding of slag_query_batch. dim: a multiple of 16 in
+ *   16..4096; 1 <= k <= 1024.
+ *   Work is enqueued in cuda_stream (NULL = legacy default stream); the
+ *   outputs are ready when that stream has passed the call.
+ *   Size limit: 4 n + 8 B ceil(n / 128) min(k, 128) bytes (each of the three
+ *   parts rounded up to 256) must not exceed 16 MiB; larger requests return
+ *   SLAG_ERR_CAPACITY without launching anything (split the queries).
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture. Every call uses the same array: nothing in it needs to start at
+ *   zero (each call writes all it reads), but calls that overlap on the GPU --
+ *   in different streams or from different threads -- race on it.
+ * Errors: INVALID_ARG (NULL pointer, sizes out of range, misaligned E or Q);
+ * CAPACITY (see above); CUDA. */
+slag_status slag_noalloc_query_topk(const float *E, int64_t n, int32_t dim, const float *wsum,
+                                    const float *Q, int32_t B, int32_t k, int64_t *out_ids,
+                                    float *out_scores, int32_t *out_count, void *cuda_stream);
+
 /* Batched form of slag_query: Q is B x dim float32 row-major; out_ids and
  * out_scores are B x k, out_count is B (nullable). on_device says where Q and
  * the outputs live. Same ordering, candidates and errors as slag_query. */

@@ -56,7 +56,7 @@ _lib = None
 
 EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_query_batch", "slag_reset",
            "slag_get_stats", "slag_last_error", "slag_destroy", "slag_bin_view", "slag_render_debug",
-           "slag_set_profiling", "slag_get_profile")
+           "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
     lib.slag_render_debug.argtypes = [P, ctypes.POINTER(CCamera), P, P, P]
     lib.slag_set_profiling.argtypes = [P, i32]
     lib.slag_get_profile.argtypes = [P, ctypes.POINTER(CProfile), i32]
+    lib.slag_noalloc_query_topk.argtypes = [P, i64, i32, P, P, i32, i32, P, P, P, P]
     for name in EXPORTS:
         f = getattr(lib, name)
         if f.restype is ctypes.c_int:   # default
@@ -124,6 +125,24 @@ def camera_struct(cam) -> CCamera:
     c.t[:] = [float(v) for v in np.asarray(cam.t, np.float32).reshape(3)]
     c.near_z, c.far_z = float(getattr(cam, "near", 0.01)), float(getattr(cam, "far", 100.0))
     return c
+
+
+def noalloc_query_topk(E, wsum, Q, k: int, out_ids, out_scores, out_count=None, stream: Optional[int] = None):
+    """Allocation-free cosine top-k on torch CUDA tensors (see slag_noalloc_query_topk).
+
+    Fills out_ids (B x k int64), out_scores (B x k float32) and out_count (B int32, optional)
+    asynchronously in `stream`; returns the status code."""
+    lib = load_library()
+    n, dim = int(E.shape[0]), int(E.shape[1])
+    B = int(Q.shape[0])
+    ep, _, _ = _ptr(E, np.float32)
+    wp, _, _ = _ptr(wsum, np.float32)
+    qp, _, _ = _ptr(Q, np.float32)
+    ip, _, _ = _ptr(out_ids, np.int64)
+    sp, _, _ = _ptr(out_scores, np.float32)
+    cp, _, _ = _ptr(out_count, np.int32)
+    return lib.slag_noalloc_query_topk(ep, n, dim, wp, qp, B, int(k), ip, sp, cp,
+                                       ctypes.c_void_p(stream) if stream else None)
 
 
 class Lifter:
