@@ -14,11 +14,18 @@
 // One CTA (256 threads) per 16x16 tile:
 //   * the tile's pixels are reordered by segment ("slot"), so that each warp's
 //     32 pixels usually share one segment;
-//   * records of 256 Gaussians at a time are staged in shared memory;
-//   * a warp composites its 32 pixels against 32 Gaussians, storing the
-//     32 x 32 weights in a padded shared buffer, then reads the buffer
-//     transposed: lane j sums Gaussian j over the warp's pixels per slot and
-//     adds the partial into a shared (slot x Gaussian) table;
+//   * records of 256 Gaussians at a time are staged in shared memory; a
+//     record holds mu', the conic scaled by -log2(e)/2 (so that alpha =
+//     min(0.99, 2^(q2 + log2 opacity)) needs one SFU exp2 and the alpha
+//     floor is tested on the exponent before it), and the half extents of
+//     the alpha >= 1/255 ellipse;
+//   * per chunk of 32 Gaussians, each warp keeps (ballot) only those whose
+//     alpha >= 1/255 ellipse box meets the box of its 32 pixel centres --
+//     the others cannot contribute to any of its pixels -- composites its
+//     32 pixels against them, storing the weights in a padded shared 32 x 32
+//     buffer, then reads the buffer transposed: lane j sums Gaussian j over
+//     the warp's pixels per slot and adds the partial into a shared
+//     (slot x Gaussian) table;
 //   * after each batch the non-zero table entries go into the per-view
 //     (segment, weight) table of each Gaussian in global memory (4 slots per
 //     Gaussian; further segments are appended directly as triples).
@@ -30,12 +37,14 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kBatch = 256;
-constexpr int kSmemSlots = 16;
+constexpr int kSmemSlots = 8;
 constexpr int kWStride = 33;
+constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2(1/255)
 
 struct Smem {
-    float4 rec_a[kBatch];
-    float4 rec_b[kBatch];
+    float4 rec_a[kBatch];                 // (mu'x, mu'y, a', b')
+    float4 rec_b[kBatch];                 // (c', log2 opacity, ex, ey)
+    uint32_t gid[kBatch];                 // internal Gaussian index
     float wb[kSmemSlots][kBatch];         // per (slot, Gaussian of the batch)
     float wbuf[kThreads / 32][32 * kWStride];
     uint32_t keys[kThreads];
@@ -44,6 +53,12 @@ struct Smem {
     int32_t group_slot[kThreads / 32];    // slot shared by a warp's 32 positions, -2 = mixed
     int32_t scalar[4];
 };
+
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 __device__ __forceinline__ uint64_t pack_key(uint32_t g, uint32_t col) {
     return ((uint64_t)(g >> 7) << 39) | ((uint64_t)col << 7) | (uint64_t)(g & 127u);
@@ -78,7 +93,12 @@ __device__ void hash_add(const CompositeArgs &a, uint32_t g, int32_t seg, float 
     append_triple(a, g, seg, w);
 }
 
-__global__ void __launch_bounds__(kThreads, 2) composite_k(const CompositeArgs a) {
+__device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int slot, int gi, float acc) {
+    if (slot < kSmemSlots) atomicAdd(&sm.wb[slot][gi], acc);
+    else hash_add(a, sm.gid[gi], sm.seg_of_slot[slot], acc);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) composite_k(const CompositeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -140,13 +160,22 @@ __global__ void __launch_bounds__(kThreads, 2) composite_k(const CompositeArgs a
     const int px = tx * kTile + (pix & 15), py = ty * kTile + (pix >> 4);
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    // bounding box of this warp's pixel centres (culling of Gaussians per warp)
+    float wx0 = inside ? pxc : INFINITY, wx1 = inside ? pxc : -INFINITY;
+    float wy0 = inside ? pyc : INFINITY, wy1 = inside ? pyc : -INFINITY;
+    for (int o = 16; o; o >>= 1) {
+        wx0 = fminf(wx0, __shfl_xor_sync(0xffffffffu, wx0, o));
+        wx1 = fmaxf(wx1, __shfl_xor_sync(0xffffffffu, wx1, o));
+        wy0 = fminf(wy0, __shfl_xor_sync(0xffffffffu, wy0, o));
+        wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
+    }
     float T = 1.f, wsum = 0.f;
     int count = 0, evals = 0;
     bool done = !inside;
+    const bool kernel_mode = a.weight_mode == SLAG_WEIGHT_KERNEL;
 
     const uint2 rg = a.ranges[tile];
     const int start = (int)rg.x, end = (int)rg.y;
-    const float alpha_min = 1.f / 255.f;
     float *wb_warp = sm.wbuf[w];
 
     for (int b = start; b < end; b += kBatch) {
@@ -154,39 +183,51 @@ __global__ void __launch_bounds__(kThreads, 2) composite_k(const CompositeArgs a
         if (live == 0) break;
         const int nb = min(kBatch, end - b);
         if (tid < nb) {
-            uint32_t r = a.list[b + tid];
+            const uint32_t r = a.list[b + tid];
             sm.rec_a[tid] = a.srec_a[r];
             sm.rec_b[tid] = a.srec_b[r];
+            sm.gid[tid] = a.sgid[r];
         }
         for (int s = 0; s < ns_smem; ++s) sm.wb[s][tid] = 0.f;
         __syncthreads();
         const int gs = sm.group_slot[w];
         for (int c = 0; c * 32 < nb; ++c) {
             if (!__any_sync(0xffffffffu, !done)) break;
-            // A: composite 32 Gaussians for this thread's pixel
-#pragma unroll 4
-            for (int j = 0; j < 32; ++j) {
-                const int gi = c * 32 + j;
+            const int nvalid = min(32, nb - c * 32);
+            // which of the chunk's Gaussians can reach alpha >= 1/255 inside this warp's pixels
+            bool hit = false;
+            if (lane < nvalid) {
+                const float4 ra = sm.rec_a[c * 32 + lane];
+                const float4 rb = sm.rec_b[c * 32 + lane];
+                hit = (ra.x - rb.z <= wx1) && (ra.x + rb.z >= wx0) && (ra.y - rb.w <= wy1) && (ra.y + rb.w >= wy0);
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, hit);
+            if (!done) evals += nvalid;
+            if (mask == 0) continue;
+            // A: composite the surviving Gaussians for this thread's pixel
+            uint32_t m = mask;
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
                 float wv = 0.f;
-                if (!done && gi < nb) {
-                    ++evals;
-                    const float4 ra = sm.rec_a[gi];
-                    const float4 rb = sm.rec_b[gi];
+                if (!done) {
+                    const float4 ra = sm.rec_a[c * 32 + j];
+                    const float4 rb = sm.rec_b[c * 32 + j];
                     const float dx = ra.x - pxc, dy = ra.y - pyc;
-                    const float power = -0.5f * (ra.z * dx * dx + rb.x * dy * dy) - ra.w * dx * dy;
-                    if (power <= 0.f) {
-                        const float kern = __expf(power);
-                        const float alpha = fminf(0.99f, rb.y * kern);
-                        if (alpha >= alpha_min) {
-                            const float Tn = T * (1.f - alpha);
-                            if (Tn < 1e-4f) {
-                                done = true;
-                            } else {
-                                wv = a.weight_mode == SLAG_WEIGHT_KERNEL ? kern : alpha * T;
-                                T = Tn;
-                                wsum += wv;
-                                ++count;
-                            }
+                    const float u = fmaf(ra.z, dx, ra.w * dy);
+                    const float q2 = fmaf(u, dx, rb.x * dy * dy);
+                    const float e = q2 + rb.y;
+                    if (q2 <= 0.f && e >= kLog2AlphaMin) {
+                        const float alpha = fminf(0.99f, fast_exp2(e));
+                        const float Tn = T - alpha * T;
+                        if (Tn < 1e-4f) {
+                            done = true;
+                            evals -= nvalid - 1 - j;
+                        } else {
+                            wv = kernel_mode ? fast_exp2(q2) : alpha * T;
+                            T = Tn;
+                            wsum += wv;
+                            ++count;
                         }
                     }
                 }
@@ -194,36 +235,27 @@ __global__ void __launch_bounds__(kThreads, 2) composite_k(const CompositeArgs a
             }
             __syncwarp();
             // B: lane = Gaussian c*32+lane, sum over this warp's 32 positions per slot
-            if (a.accumulate && gs != -1) {
+            if (a.accumulate && gs != -1 && ((mask >> lane) & 1u)) {
                 const float *row = wb_warp + lane * kWStride;
                 const int gi = c * 32 + lane;
                 if (gs >= 0) {
                     float acc = 0.f;
 #pragma unroll
                     for (int q = 0; q < 32; ++q) acc += row[q];
-                    if (acc != 0.f) {
-                        if (gs < kSmemSlots) atomicAdd(&sm.wb[gs][gi], acc);
-                        else hash_add(a, __float_as_uint(sm.rec_b[gi].z), sm.seg_of_slot[gs], acc);
-                    }
+                    if (acc != 0.f) flush_slot(a, sm, gs, gi, acc);
                 } else {
                     int cur = sm.slot_of_pos[w * 32];
                     float acc = 0.f;
                     for (int q = 0; q < 32; ++q) {
                         const int sl = sm.slot_of_pos[w * 32 + q];
                         if (sl != cur) {
-                            if (cur >= 0 && acc != 0.f) {
-                                if (cur < kSmemSlots) atomicAdd(&sm.wb[cur][gi], acc);
-                                else hash_add(a, __float_as_uint(sm.rec_b[gi].z), sm.seg_of_slot[cur], acc);
-                            }
+                            if (cur >= 0 && acc != 0.f) flush_slot(a, sm, cur, gi, acc);
                             acc = 0.f;
                             cur = sl;
                         }
                         acc += row[q];
                     }
-                    if (cur >= 0 && acc != 0.f) {
-                        if (cur < kSmemSlots) atomicAdd(&sm.wb[cur][gi], acc);
-                        else hash_add(a, __float_as_uint(sm.rec_b[gi].z), sm.seg_of_slot[cur], acc);
-                    }
+                    if (cur >= 0 && acc != 0.f) flush_slot(a, sm, cur, gi, acc);
                 }
             }
             __syncwarp();
@@ -231,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 2) composite_k(const CompositeArgs a
         __syncthreads();
         // C: per Gaussian of the batch, push the non-zero (segment, sum) entries
         if (a.accumulate && tid < nb) {
-            const uint32_t g = __float_as_uint(sm.rec_b[tid].z);
+            const uint32_t g = sm.gid[tid];
             for (int s = 0; s < ns_smem; ++s) {
                 const float v = sm.wb[s][tid];
                 if (v != 0.f) hash_add(a, g, sm.seg_of_slot[s], v);

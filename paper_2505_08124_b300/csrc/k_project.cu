@@ -215,9 +215,23 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
                 if (x0 < x1 && y0 < y1) {
                     visible = true;
                     rc = make_uint2(x0 | (x1 << 16), y0 | (y1 << 16));
-                    float inv = FD(1.f, det);
-                    ra = make_float4(px, py, FM(c11, inv), -FM(c01, inv));
-                    rb = make_float4(FM(c00, inv), mo.w, __uint_as_float((uint32_t)g), 0.f);
+                    // compositing record: the exponent of alpha in base 2 is
+                    //   q2 + log2(o),  q2 = a' dx^2 + b' dx dy + c' dy^2  (d = mu' - pixel)
+                    // with (a', b', c') = log2(e) * (-A/2, -B, -C/2) for the conic (A, B, C);
+                    // (ex, ey): half extents of the alpha >= 1/255 ellipse q <= 2 ln(255 o)
+                    // (with a small safety margin), -inf when no pixel can reach the floor.
+                    const float kLog2e = 1.4426950408889634f;
+                    const float inv = 1.f / det;
+                    const float A = c11 * inv, B = -c01 * inv, C = c00 * inv;
+                    const float op = mo.w;
+                    const float tau = 2.f * logf(255.f * op);
+                    float ex = -INFINITY, ey = -INFINITY;
+                    if (tau >= 0.f) {
+                        ex = sqrtf(tau * c00) * 1.001f + 0.01f;
+                        ey = sqrtf(tau * c11) * 1.001f + 0.01f;
+                    }
+                    ra = make_float4(px, py, -0.5f * kLog2e * A, -kLog2e * B);
+                    rb = make_float4(-0.5f * kLog2e * C, op > 0.f ? log2f(op) : -INFINITY, ex, ey);
                 }
             }
         }

@@ -1,16 +1,19 @@
 // Stable LSD radix sort and exclusive scan (no CUB).
 //
-// Radix sort, one pass per digit of <= 8 bits, three kernels per pass:
-//   1. rs_hist:    each CTA counts the digits of its 4096-item tile
-//                  (warp-aggregated with match.any into per-warp histograms);
-//                  writes hist[digit][tile] and adds the digit totals.
+// Radix sort, one pass per digit of <= 8 bits, three kernels per pass, over
+// tiles of 256 x ITEMS items (ITEMS = 16, or 4 below ~2M items so that the
+// grid still covers the GPU):
+//   1. rs_hist:    each CTA counts the digits of its tile into per-warp
+//                  shared histograms (shared-memory atomics); writes
+//                  hist[digit][tile] and adds the digit totals.
 //   2. rs_offsets: one CTA per digit scans hist[digit][*] into global
 //                  output offsets (digit start + earlier tiles' counts).
 //   3. rs_scatter: each CTA ranks its tile stably (warp w owns items
-//                  [w*512, w*512+512) of the tile, in 16 rounds of 32, so
-//                  (warp, round, lane) order is input order), stages the tile
-//                  in shared memory in digit order and writes each digit's run
-//                  contiguously.
+//                  [w*32*ITEMS, (w+1)*32*ITEMS) of the tile in rounds of 32,
+//                  so (warp, round, lane) order is input order; equal digits
+//                  within a round are found with one ballot per digit bit),
+//                  stages the tile in shared memory in digit order and writes
+//                  each digit's run contiguously.
 // Exclusive scan of uint32: per-tile sums, a single-CTA scan of the sums, and
 // a per-tile scan with the carried offset.
 #include "slag_internal.cuh"
@@ -31,7 +34,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-template <typename K>
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kThreads) rs_hist(const K *__restrict__ keys, int64_t n, int shift,
                                                     uint32_t mask, uint32_t *__restrict__ hist,
                                                     uint32_t *__restrict__ digit_tot, int ntiles) {
@@ -39,16 +42,11 @@ __global__ void __launch_bounds__(kThreads) rs_hist(const K *__restrict__ keys, 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kWarps * 256; i += kThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kTileItems + (int64_t)w * kWarpItems;
-    for (int r = 0; r < kItems; ++r) {
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * ITEMS) + (int64_t)w * (32 * ITEMS);
+#pragma unroll 4
+    for (int r = 0; r < ITEMS; ++r) {
         int64_t i = base + r * 32 + lane;
-        bool valid = i < n;
-        uint32_t act = __ballot_sync(0xffffffffu, valid);
-        if (valid) {
-            uint32_t d = (uint32_t)(keys[i] >> shift) & mask;
-            uint32_t peers = __match_any_sync(act, d);
-            if (lane == __ffs(peers) - 1) h[w][d] += __popc(peers);
-        }
+        if (i < n) atomicAdd(&h[w][(uint32_t)(keys[i] >> shift) & mask], 1u);
     }
     __syncthreads();
     for (int d = tid; d < 256; d += kThreads) {
@@ -105,47 +103,59 @@ __global__ void __launch_bounds__(1024) rs_offsets(uint32_t *__restrict__ hist,
     }
 }
 
-template <typename K>
+// Lanes of the warp whose digit equals this lane's: one ballot per digit bit.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, int width, bool valid) {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    for (int b = 0; b < width; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t ones = __ballot_sync(0xffffffffu, valid && bit);
+        peers &= bit ? ones : ~ones;
+    }
+    return peers;
+}
+
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                        K *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                       int64_t n, int shift, uint32_t mask,
+                                                       int64_t n, int shift, uint32_t mask, int width,
                                                        const uint32_t *__restrict__ offs, int ntiles) {
+    constexpr int kTileN = kThreads * ITEMS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t(*cnt)[256] = reinterpret_cast<uint32_t(*)[256]>(smem_raw);          // kWarps x 256
     uint32_t *lstart = reinterpret_cast<uint32_t *>(smem_raw + kWarps * 256 * 4); // 256
     uint32_t *gbase = lstart + 256;                                                // 256
     uint32_t *wsum = gbase + 256;                                                  // 8
     K *skeys = reinterpret_cast<K *>(smem_raw + kWarps * 256 * 4 + 3 * 256 * 4 + 64);
-    uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + kTileItems);
+    uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + kTileN);
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kWarps * 256; i += kThreads) (&cnt[0][0])[i] = 0;
     __syncthreads();
 
-    const int64_t tile_base = (int64_t)blockIdx.x * kTileItems;
-    const int64_t base = tile_base + (int64_t)w * kWarpItems;
-    K key[kItems];
-    uint32_t val[kItems];
-    uint32_t pos[kItems];
+    const int64_t tile_base = (int64_t)blockIdx.x * kTileN;
+    const int64_t base = tile_base + (int64_t)w * (32 * ITEMS);
+    K key[ITEMS];
+    uint32_t val[ITEMS];
+    uint32_t pos[ITEMS];
     const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        int64_t i = base + r * 32 + lane;
-        bool valid = i < n;
-        uint32_t act = __ballot_sync(0xffffffffu, valid);
-        pos[r] = 0xffffffffu;
-        key[r] = 0;
-        val[r] = 0;
-        if (valid) {
-            key[r] = kin[i];
-            val[r] = vin[i];
-            uint32_t d = (uint32_t)(key[r] >> shift) & mask;
-            uint32_t peers = __match_any_sync(act, d);
-            uint32_t c = cnt[w][d];
-            __syncwarp(act);
-            if (lane == __ffs(peers) - 1) cnt[w][d] = c + __popc(peers);
-            pos[r] = c + __popc(peers & lt);
-        }
+    for (int r = 0; r < ITEMS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : (K)0;
+        val[r] = valid ? vin[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
+        const uint32_t peers = digit_peers(d, width, valid);
+        uint32_t c = 0;
+        if (valid) c = cnt[w][d];
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) cnt[w][d] = c + __popc(peers);
+        pos[r] = valid ? c + __popc(peers & lt) : 0xffffffffu;
         __syncwarp();
     }
     __syncthreads();
@@ -178,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
+    for (int r = 0; r < ITEMS; ++r) {
         if (pos[r] != 0xffffffffu) {
             uint32_t d = (uint32_t)(key[r] >> shift) & mask;
             uint32_t lp = lstart[d] + cnt[w][d] + pos[r];
@@ -188,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
     }
     __syncthreads();
     int64_t rem = n - tile_base;
-    int tile_n = rem < kTileItems ? (int)rem : kTileItems;
+    int tile_n = rem < kTileN ? (int)rem : kTileN;
     for (int j = tid; j < tile_n; j += kThreads) {
         K k = skeys[j];
         uint32_t d = (uint32_t)(k >> shift) & mask;
@@ -198,20 +208,20 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
     }
 }
 
-template <typename K>
+template <typename K, int ITEMS>
 size_t scatter_smem() {
-    return (size_t)kWarps * 256 * 4 + 3 * 256 * 4 + 64 + (size_t)kTileItems * (sizeof(K) + 4);
+    return (size_t)kWarps * 256 * 4 + 3 * 256 * 4 + 64 + (size_t)kThreads * ITEMS * (sizeof(K) + 4);
 }
 
-template <typename K>
-bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
-                     const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st) {
-    if (n <= 0 || npass <= 0) return false;
-    const int ntiles = (int)((n + kTileItems - 1) / kTileItems);
+template <typename K, int ITEMS>
+bool radix_sort_tiles(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, const int *shifts,
+                      const int *widths, int npass, SortScratch &s, cudaStream_t st) {
+    constexpr int kTileN = kThreads * ITEMS;
+    const int ntiles = (int)((n + kTileN - 1) / kTileN);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)scatter_smem<K>());
+        cudaFuncSetAttribute(rs_scatter<K, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem<K, ITEMS>());
         attr_set = true;
     }
     K *ki = keys, *ko = keys_alt;
@@ -219,14 +229,24 @@ bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, i
     for (int p = 0; p < npass; ++p) {
         uint32_t mask = (widths[p] >= 32) ? 0xffffffffu : ((1u << widths[p]) - 1u);
         cudaMemsetAsync(s.digit_tot, 0, 256 * sizeof(uint32_t), st);
-        rs_hist<K><<<ntiles, kThreads, 0, st>>>(ki, n, shifts[p], mask, s.hist, s.digit_tot, ntiles);
+        rs_hist<K, ITEMS><<<ntiles, kThreads, 0, st>>>(ki, n, shifts[p], mask, s.hist, s.digit_tot, ntiles);
         rs_offsets<<<256, 1024, 0, st>>>(s.hist, s.digit_tot, ntiles);
-        rs_scatter<K><<<ntiles, kThreads, scatter_smem<K>(), st>>>(ki, vi, ko, vo, n, shifts[p], mask,
-                                                                    s.hist, ntiles);
+        rs_scatter<K, ITEMS><<<ntiles, kThreads, scatter_smem<K, ITEMS>(), st>>>(ki, vi, ko, vo, n, shifts[p], mask,
+                                                                                  widths[p], s.hist, ntiles);
         K *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
     }
     return (npass & 1) != 0;
+}
+
+// Inputs below ~2M items use 1024-item tiles so that the grid still covers the GPU.
+template <typename K>
+bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
+                     const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st) {
+    if (n <= 0 || npass <= 0) return false;
+    if (n < (1 << 21))
+        return radix_sort_tiles<K, 4>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st);
+    return radix_sort_tiles<K, kItems>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -332,7 +352,8 @@ __global__ void __launch_bounds__(kThreads) scan_tiles(const uint32_t *__restric
 }  // namespace
 
 cudaError_t scratch_reserve(SortScratch &s, int64_t n) {
-    int64_t tiles = (n + kTileItems - 1) / kTileItems + 1;
+    // the finest tiling used (1024 items) sets the size of the histogram array
+    int64_t tiles = (n + 1023) / 1024 + 1;
     size_t need_hist = (size_t)256 * tiles;
     if (!s.digit_tot) {
         cudaError_t e = cudaMalloc(&s.digit_tot, 256 * sizeof(uint32_t));

@@ -240,7 +240,7 @@ int ceil_log2(uint64_t v) {
 // records, the tile-sorted pair list and ranges in the workspace; returns the
 // pair count in *P_out and the list buffer in *list_out.
 slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_t **keys_out,
-                     uint32_t **list_out, const int32_t *seg_check, int32_t M) {
+                     uint32_t **list_out, const int32_t *seg_check, int32_t M, const uint32_t **sgid_out) {
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->n;
     CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
@@ -253,6 +253,7 @@ slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_
     bool alt = radix_sort_u32(ctx->dkey[0], ctx->dkey[1], ctx->dval[0], ctx->dval[1], n, shifts, widths, np,
                               ctx->scratch, st);
     const uint32_t *sorted_vals = ctx->dval[alt ? 1 : 0];
+    *sgid_out = sorted_vals;
     launch_gather_sorted(sorted_vals, n, ctx->ctr, ctx->rec_a, ctx->rec_b, ctx->rect, ctx->srec_a, ctx->srec_b,
                          ctx->srect, ctx->stouched, st);
     exclusive_scan_u32(ctx->stouched, ctx->offsets, n, &ctx->ctr->P, ctx->scratch, st);
@@ -422,7 +423,8 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     }
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
-    s = bin_view(ctx, cp, &P, &keys, &list, seg, M);
+    const uint32_t *sgid = nullptr;
+    s = bin_view(ctx, cp, &P, &keys, &list, seg, M, &sgid);
     if (s != SLAG_OK) return s;
 
     // room in the triple log: at most kHashSlots per Gaussian from the consume
@@ -442,6 +444,7 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     a.list = list;
     a.srec_a = ctx->srec_a;
     a.srec_b = ctx->srec_b;
+    a.sgid = sgid;
     a.seg = seg;
     a.view_base = (int32_t)ctx->table_rows;
     a.weight_mode = ctx->weight_mode;
@@ -698,7 +701,8 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
     const CamParams cp = cam_params(cam);
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
-    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0);
+    const uint32_t *sgid = nullptr;
+    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0, &sgid);
     if (s != SLAG_OK) return s;
     if (out_P) *out_P = P;
     const int64_t n = ctx->n;
@@ -725,21 +729,17 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
         // list holds depth ranks; map rank -> internal -> caller index on the host
         uint32_t *h_list = (uint32_t *)malloc(sizeof(uint32_t) * (P > 0 ? P : 1));
         uint32_t *h_orig = (uint32_t *)malloc(sizeof(uint32_t) * n);
-        float4 *h_recb = (float4 *)malloc(sizeof(float4) * n);
-        if (!h_list || !h_orig || !h_recb) {
-            free(h_list); free(h_orig); free(h_recb);
+        uint32_t *h_gid = (uint32_t *)malloc(sizeof(uint32_t) * n);
+        if (!h_list || !h_orig || !h_gid) {
+            free(h_list); free(h_orig); free(h_gid);
             return fail(ctx, SLAG_ERR_OOM, "host allocation");
         }
         if (P > 0) CK(cudaMemcpyAsync(h_list, list, sizeof(uint32_t) * P, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(h_recb, ctx->srec_b, sizeof(float4) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_gid, sgid, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(h_orig, ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        for (int64_t i = 0; i < P; ++i) {
-            uint32_t gI;
-            memcpy(&gI, &h_recb[h_list[i]].z, 4);
-            out_list[i] = (int32_t)h_orig[gI];
-        }
-        free(h_list); free(h_orig); free(h_recb);
+        for (int64_t i = 0; i < P; ++i) out_list[i] = (int32_t)h_orig[h_gid[h_list[i]]];
+        free(h_list); free(h_orig); free(h_gid);
     }
     if (out_ranges) {
         uint2 *h_r = (uint2 *)malloc(sizeof(uint2) * tiles);
@@ -770,7 +770,8 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     const int64_t npx = (int64_t)cam->width * cam->height;
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
-    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0);
+    const uint32_t *sgid = nullptr;
+    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0, &sgid);
     if (s != SLAG_OK) return s;
     if (npx > ctx->dbg_cap) {
         int64_t c1 = ctx->dbg_cap, c2 = ctx->dbg_cap, c3 = ctx->dbg_cap;
@@ -786,6 +787,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.list = list;
     a.srec_a = ctx->srec_a;
     a.srec_b = ctx->srec_b;
+    a.sgid = sgid;
     a.seg = nullptr;
     a.weight_mode = ctx->weight_mode;
     a.ctr = ctx->ctr;

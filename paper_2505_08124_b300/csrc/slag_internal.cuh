@@ -110,6 +110,7 @@ struct CompositeArgs {
     const uint2 *ranges;
     const uint32_t *list;          // sorted values: depth rank of each pair
     const float4 *srec_a, *srec_b; // records in depth-rank order
+    const uint32_t *sgid;          // internal Gaussian index of each depth rank
     const int32_t *seg;            // H x W
     int32_t view_base;             // column of segment 0 of this view
     int32_t weight_mode;
