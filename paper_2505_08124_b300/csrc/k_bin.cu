@@ -1,5 +1,7 @@
-// Tile binning: emit one (tile, depth rank) pair per Gaussian-tile overlap,
-// and find each tile's range in the tile-sorted pairs.
+// Tile binning: emit one (bin, depth rank) pair per Gaussian-bin overlap, and
+// find each bin's range in the bin-sorted pairs. A bin is a 16x16 tile (the
+// flat lists of the integer-stage diagnostics) or a 4x4-tile super-tile (the
+// lists the compositing kernel filters per tile, see k_composite.cu).
 //
 // Pairs are emitted in depth-rank order (rank = position in the stable sort
 // by (float32 depth, caller index)), each Gaussian's tiles in row-major order.
@@ -13,24 +15,28 @@ namespace slag {
 
 namespace {
 
-// One warp per Gaussian: the lanes write consecutive pairs of its rectangle.
+// One thread per Gaussian (in depth-rank order): the pairs of the bins its tile
+// rectangle meets, row-major; a bin is a 2^shift x 2^shift square of tiles.
 __global__ void __launch_bounds__(256) emit_k(const uint2 *__restrict__ srect, const uint32_t *__restrict__ offsets,
-                                              uint32_t n_visible, int tiles_x, uint32_t *__restrict__ keys,
+                                              uint32_t n_visible, int shift, int bins_x, uint32_t *__restrict__ keys,
                                               uint32_t *__restrict__ vals) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t r = warp; r < n_visible; r += nwarps) {
-        uint2 rc = srect[r];
-        uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
-        uint32_t wdt = x1 - x0, cnt = wdt * (y1 - y0);
-        uint32_t off = offsets[r];
-        for (uint32_t i = lane; i < cnt; i += 32) {
-            uint32_t y = y0 + i / wdt, x = x0 + i % wdt;
-            keys[off + i] = y * (uint32_t)tiles_x + x;
-            vals[off + i] = r;
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_visible) return;
+    const uint2 rc = srect[r];
+    const uint32_t x0 = (rc.x & 0xffffu) >> shift, x1 = (((rc.x >> 16) - 1) >> shift) + 1;
+    const uint32_t y0 = (rc.y & 0xffffu) >> shift, y1 = (((rc.y >> 16) - 1) >> shift) + 1;
+    uint32_t off = offsets[r];
+    for (uint32_t y = y0; y < y1; ++y)
+        for (uint32_t x = x0; x < x1; ++x, ++off) {
+            keys[off] = y * (uint32_t)bins_x + x;
+            vals[off] = r;
         }
-    }
+}
+
+__global__ void pair_rect_k(const uint32_t *__restrict__ list, int64_t P, const uint2 *__restrict__ srect,
+                            uint2 *__restrict__ prect) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) prect[i] = srect[list[i]];
 }
 
 __global__ void ranges_k(const uint32_t *__restrict__ keys, int64_t P, uint2 *__restrict__ ranges) {
@@ -41,14 +47,59 @@ __global__ void ranges_k(const uint32_t *__restrict__ keys, int64_t P, uint2 *__
     if (i == P - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
+// One CTA: order = tiles grouped by descending floor(log2(pair count + 1)), so
+// that compositing starts the longest lists first (order within a group is
+// the order in which the threads claim places).
+__device__ __forceinline__ uint2 bin_range(const uint2 *ranges, int t, int tiles_x, int shift) {
+    const int tx = t % tiles_x, ty = t / tiles_x;
+    const int bins_x = ((tiles_x - 1) >> shift) + 1;
+    return ranges[(ty >> shift) * bins_x + (tx >> shift)];
+}
+
+__global__ void __launch_bounds__(1024) tile_order_k(const uint2 *__restrict__ ranges, int tiles_x, int tiles,
+                                                     int shift, uint32_t *__restrict__ order) {
+    __shared__ uint32_t cnt[33], start[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = bin_range(ranges, t, tiles_x, shift);
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        atomicAdd(&cnt[32 - __clz(len + 1u)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int b = 32; b >= 0; --b) {
+            start[b] = acc;
+            acc += cnt[b];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = bin_range(ranges, t, tiles_x, shift);
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        order[atomicAdd(&start[32 - __clz(len + 1u)], 1u)] = (uint32_t)t;
+    }
+}
+
 }  // namespace
 
-void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int tiles_x, uint32_t *keys,
-                 uint32_t *vals, cudaStream_t st) {
+void launch_tile_order(const uint2 *ranges, int tiles_x, int tiles_y, int shift, uint32_t *order,
+                       cudaStream_t st) {
+    const int tiles = tiles_x * tiles_y;
+    if (tiles <= 0) return;
+    tile_order_k<<<1, 1024, 0, st>>>(ranges, tiles_x, tiles, shift, order);
+}
+
+void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int shift, int bins_x,
+                 uint32_t *keys, uint32_t *vals, cudaStream_t st) {
     if (n_visible == 0) return;
-    int64_t blocks = ((int64_t)n_visible * 32 + 255) / 256;
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    emit_k<<<(unsigned)blocks, 256, 0, st>>>(srect, offsets, n_visible, tiles_x, keys, vals);
+    emit_k<<<(n_visible + 255) / 256, 256, 0, st>>>(srect, offsets, n_visible, shift, bins_x, keys, vals);
+}
+
+void launch_pair_rects(const uint32_t *list, int64_t P, const uint2 *srect, uint2 *prect, cudaStream_t st) {
+    if (P <= 0) return;
+    pair_rect_k<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(list, P, srect, prect);
 }
 
 void launch_ranges(const uint32_t *keys, int64_t P, uint2 *ranges, cudaStream_t st) {

@@ -35,8 +35,11 @@ namespace slag {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kBatch = 256;
+constexpr int kRows = 4;                              // tile rows per CTA: a 16x16 tile = 4 CTAs
+constexpr int kThreads = kTile * kRows;               // 64: one pixel per thread
+constexpr int kSubTiles = kTile / kRows;
+constexpr int kRound = 128;                           // candidates examined per fill round
+constexpr int kBatch = 64 + kRound;                   // record capacity of a batch
 constexpr int kSmemSlots = 8;
 constexpr int kWStride = 33;
 constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2(1/255)
@@ -45,6 +48,7 @@ struct Smem {
     float4 rec_a[kBatch];                 // (mu'x, mu'y, a', b')
     float4 rec_b[kBatch];                 // (c', log2 opacity, ex, ey)
     uint32_t gid[kBatch];                 // internal Gaussian index
+    int32_t fill[4];                      // per-warp hit counts of a fill round
     float wb[kSmemSlots][kBatch];         // per (slot, Gaussian of the batch)
     float wbuf[kThreads / 32][32 * kWStride];
     uint32_t keys[kThreads];
@@ -59,6 +63,20 @@ __device__ __forceinline__ float fast_exp2(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ uint64_t pack_key(uint32_t g, uint32_t col) {
     return ((uint64_t)(g >> 7) << 39) | ((uint64_t)col << 7) | (uint64_t)(g & 127u);
@@ -98,23 +116,31 @@ __device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int
     else hash_add(a, sm.gid[gi], sm.seg_of_slot[slot], acc);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) composite_k(const CompositeArgs a) {
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x;
+    const int tile = (int)a.tile_order[blockIdx.x / kSubTiles];
+    const int row0 = (int)(blockIdx.x % kSubTiles) * kRows;    // first tile row of this CTA
     const int tx = tile % a.cam.tiles_x, ty = tile / a.cam.tiles_x;
     const int W = a.cam.width, H = a.cam.height;
 
     // ---- segment of each pixel, slot-sorted positions --------------------------------
     int32_t s_nat;
     {
-        int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+        int px = tx * kTile + (tid & 15), py = ty * kTile + row0 + (tid >> 4);
         bool inside = px < W && py < H;
         s_nat = (inside && a.seg && a.accumulate) ? a.seg[(int64_t)py * W + px] : -1;
         if (s_nat < -1) s_nat = -1;
         sm.keys[tid] = ((uint32_t)(s_nat + 1) << 8) | (uint32_t)tid;
     }
+    // (pixel index within the CTA fits in the low 8 bits of a key)
     if (tid == 0) sm.scalar[0] = s_nat;
     __syncthreads();
     const bool uniform = __syncthreads_and(s_nat == sm.scalar[0]);
@@ -157,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 4) composite_k(const CompositeArgs a
     }
     const int ns_smem = nslots < kSmemSlots ? nslots : kSmemSlots;
 
-    const int px = tx * kTile + (pix & 15), py = ty * kTile + (pix >> 4);
+    const int px = tx * kTile + (pix & 15), py = ty * kTile + row0 + (pix >> 4);
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
     // bounding box of this warp's pixel centres (culling of Gaussians per warp)
@@ -174,64 +200,144 @@ __global__ void __launch_bounds__(kThreads, 4) composite_k(const CompositeArgs a
     bool done = !inside;
     const bool kernel_mode = a.weight_mode == SLAG_WEIGHT_KERNEL;
 
-    const uint2 rg = a.ranges[tile];
-    const int start = (int)rg.x, end = (int)rg.y;
+    // this tile's candidates: the depth-ordered list of its bin (a 2^shift x
+    // 2^shift square of tiles); the Gaussians whose tile rectangle holds this tile
+    // form, in the same order, the tile's own list
+    const uint2 rg = a.ranges[(ty >> a.bin_shift) * a.bins_x + (tx >> a.bin_shift)];
+    const int end = (int)rg.y;
+    int cursor = (int)rg.x;
     float *wb_warp = sm.wbuf[w];
+    const uint32_t lt = lanemask_lt();
 
-    for (int b = start; b < end; b += kBatch) {
+    // candidates of the next fill round, prefetched into registers
+    constexpr int kPer = kRound / kThreads;
+    uint32_t r_nx[kPer];
+    uint2 rc_nx[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int c = cursor + k * kThreads + tid;
+        r_nx[k] = c < end ? a.list[c] : 0u;
+        rc_nx[k] = c < end ? a.prect[c] : make_uint2(0u, 0u);
+    }
+
+    while (true) {
         int live = __syncthreads_count(!done);   // also: the previous batch is fully consumed
-        if (live == 0) break;
-        const int nb = min(kBatch, end - b);
-        if (tid < nb) {
-            const uint32_t r = a.list[b + tid];
-            sm.rec_a[tid] = a.srec_a[r];
-            sm.rec_b[tid] = a.srec_b[r];
-            sm.gid[tid] = a.sgid[r];
+        if (live == 0 || cursor >= end) break;
+        // fill: rounds of kRound candidates until at least 64 records are staged; the
+        // records of the hits are copied asynchronously, the next round's candidates
+        // are loaded while this round is compacted
+        int nb = 0;
+        while (nb < kBatch - kRound && cursor < end) {
+            uint32_t r[kPer];
+            bool hit[kPer];
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int c = cursor + k * kThreads + tid;
+                r[k] = r_nx[k];
+                const uint2 rc = rc_nx[k];
+                hit[k] = c < end && (uint32_t)tx >= (rc.x & 0xffffu) && (uint32_t)tx < (rc.x >> 16) &&
+                         (uint32_t)ty >= (rc.y & 0xffffu) && (uint32_t)ty < (rc.y >> 16);
+                const int cn = c + kRound;
+                r_nx[k] = cn < end ? a.list[cn] : 0u;
+                rc_nx[k] = cn < end ? a.prect[cn] : make_uint2(0u, 0u);
+            }
+            // stable compaction: candidate order is (k, warp, lane)
+            uint32_t bal[kPer];
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                bal[k] = __ballot_sync(0xffffffffu, hit[k]);
+                if (lane == 0) sm.fill[k * (kThreads / 32) + w] = __popc(bal[k]);
+            }
+            __syncthreads();
+            int before = 0, nh = 0;
+            for (int q = 0; q < kPer * (kThreads / 32); ++q) nh += sm.fill[q];
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                int bk = 0;
+                for (int q = 0; q < k * (kThreads / 32) + w; ++q) bk += sm.fill[q];
+                if (hit[k]) {
+                    const int pos = nb + bk + __popc(bal[k] & lt);
+                    cp_async16(&sm.rec_a[pos], a.srec_a + r[k]);
+                    cp_async16(&sm.rec_b[pos], a.srec_b + r[k]);
+                    cp_async4(&sm.gid[pos], a.sgid + r[k]);
+                }
+            }
+            (void)before;
+            nb += nh;
+            cursor += kRound;
+            __syncthreads();
         }
-        for (int s = 0; s < ns_smem; ++s) sm.wb[s][tid] = 0.f;
+        cp_async_wait_all();
         __syncthreads();
+        if (nb == 0) continue;
+        if (tid < kBatch)
+            for (int s2 = 0; s2 < ns_smem; ++s2) sm.wb[s2][tid] = 0.f;
+        for (int i = tid + kThreads; i < nb; i += kThreads)
+            for (int s2 = 0; s2 < ns_smem; ++s2) sm.wb[s2][i] = 0.f;
+        __syncthreads();
+        const float4 *rec_a = sm.rec_a;
+        const float4 *rec_b = sm.rec_b;
         const int gs = sm.group_slot[w];
         for (int c = 0; c * 32 < nb; ++c) {
             if (!__any_sync(0xffffffffu, !done)) break;
             const int nvalid = min(32, nb - c * 32);
             // which of the chunk's Gaussians can reach alpha >= 1/255 inside this warp's pixels
-            bool hit = false;
+            bool hitw = false;
             if (lane < nvalid) {
-                const float4 ra = sm.rec_a[c * 32 + lane];
-                const float4 rb = sm.rec_b[c * 32 + lane];
-                hit = (ra.x - rb.z <= wx1) && (ra.x + rb.z >= wx0) && (ra.y - rb.w <= wy1) && (ra.y + rb.w >= wy0);
+                const float4 ra = rec_a[c * 32 + lane];
+                const float4 rb = rec_b[c * 32 + lane];
+                hitw = (ra.x - rb.z <= wx1) && (ra.x + rb.z >= wx0) && (ra.y - rb.w <= wy1) && (ra.y + rb.w >= wy0);
             }
-            const uint32_t mask = __ballot_sync(0xffffffffu, hit);
+            const uint32_t mask = __ballot_sync(0xffffffffu, hitw);
             if (!done) evals += nvalid;
             if (mask == 0) continue;
-            // A: composite the surviving Gaussians for this thread's pixel
+            // A: composite the surviving Gaussians for this thread's pixel, four at a time:
+            // the exponents and exp2 of a group are independent; only the transmittance
+            // updates run in order
             uint32_t m = mask;
             while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                float wv = 0.f;
-                if (!done) {
-                    const float4 ra = sm.rec_a[c * 32 + j];
-                    const float4 rb = sm.rec_b[c * 32 + j];
-                    const float dx = ra.x - pxc, dy = ra.y - pyc;
-                    const float u = fmaf(ra.z, dx, ra.w * dy);
-                    const float q2 = fmaf(u, dx, rb.x * dy * dy);
-                    const float e = q2 + rb.y;
-                    if (q2 <= 0.f && e >= kLog2AlphaMin) {
-                        const float alpha = fminf(0.99f, fast_exp2(e));
-                        const float Tn = T - alpha * T;
+                int jj[4];
+                float al[4], kq[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    jj[k] = m ? __ffs(m) - 1 : -1;
+                    m &= m ? m - 1 : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    al[k] = 0.f;
+                    kq[k] = 0.f;
+                    if (jj[k] >= 0) {
+                        const float4 ra = rec_a[c * 32 + jj[k]];
+                        const float4 rb = rec_b[c * 32 + jj[k]];
+                        const float dx = ra.x - pxc, dy = ra.y - pyc;
+                        const float u = fmaf(ra.z, dx, ra.w * dy);
+                        const float q2 = fmaf(u, dx, rb.x * dy * dy);
+                        const float e = q2 + rb.y;
+                        if (q2 <= 0.f && e >= kLog2AlphaMin) {
+                            al[k] = fminf(0.99f, fast_exp2(e));
+                            kq[k] = q2;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (jj[k] < 0) break;
+                    float wv = 0.f;
+                    if (!done && al[k] > 0.f) {
+                        const float Tn = T - al[k] * T;
                         if (Tn < 1e-4f) {
                             done = true;
-                            evals -= nvalid - 1 - j;
+                            evals -= nvalid - 1 - jj[k];
                         } else {
-                            wv = kernel_mode ? fast_exp2(q2) : alpha * T;
+                            wv = kernel_mode ? fast_exp2(kq[k]) : al[k] * T;
                             T = Tn;
                             wsum += wv;
                             ++count;
                         }
                     }
+                    wb_warp[jj[k] * kWStride + lane] = wv;
                 }
-                wb_warp[j * kWStride + lane] = wv;
             }
             __syncwarp();
             // B: lane = Gaussian c*32+lane, sum over this warp's 32 positions per slot
@@ -239,9 +345,15 @@ __global__ void __launch_bounds__(kThreads, 4) composite_k(const CompositeArgs a
                 const float *row = wb_warp + lane * kWStride;
                 const int gi = c * 32 + lane;
                 if (gs >= 0) {
-                    float acc = 0.f;
+                    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) acc += row[q];
+                    for (int q = 0; q < 32; q += 4) {
+                        p0 += row[q];
+                        p1 += row[q + 1];
+                        p2 += row[q + 2];
+                        p3 += row[q + 3];
+                    }
+                    const float acc = (p0 + p1) + (p2 + p3);
                     if (acc != 0.f) flush_slot(a, sm, gs, gi, acc);
                 } else {
                     int cur = sm.slot_of_pos[w * 32];
@@ -262,13 +374,14 @@ __global__ void __launch_bounds__(kThreads, 4) composite_k(const CompositeArgs a
         }
         __syncthreads();
         // C: per Gaussian of the batch, push the non-zero (segment, sum) entries
-        if (a.accumulate && tid < nb) {
-            const uint32_t g = sm.gid[tid];
-            for (int s = 0; s < ns_smem; ++s) {
-                const float v = sm.wb[s][tid];
-                if (v != 0.f) hash_add(a, g, sm.seg_of_slot[s], v);
+        if (a.accumulate)
+            for (int i = tid; i < nb; i += kThreads) {
+                const uint32_t g = sm.gid[i];
+                for (int s2 = 0; s2 < ns_smem; ++s2) {
+                    const float v = sm.wb[s2][i];
+                    if (v != 0.f) hash_add(a, g, sm.seg_of_slot[s2], v);
+                }
             }
-        }
     }
 
     if (inside) {
@@ -295,7 +408,7 @@ void launch_composite(const CompositeArgs &a, cudaStream_t st) {
         attr_set = true;
     }
     const int tiles = a.cam.tiles_x * a.cam.tiles_y;
-    composite_k<<<tiles, kThreads, sizeof(Smem), st>>>(a);
+    composite_k<<<tiles * kSubTiles, kThreads, sizeof(Smem), st>>>(a);
 }
 
 }  // namespace slag

@@ -247,24 +247,31 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
 }
 
 // r < n_visible: records, rectangle and tile count of the Gaussian of depth rank r.
-__global__ void gather_sorted_k(const uint32_t *__restrict__ sorted_vals, int64_t n,
-                                const ViewCounters *__restrict__ ctr, const float4 *__restrict__ rec_a,
-                                const float4 *__restrict__ rec_b, const uint2 *__restrict__ rect,
-                                float4 *__restrict__ srec_a, float4 *__restrict__ srec_b,
-                                uint2 *__restrict__ srect, uint32_t *__restrict__ stouched) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    uint32_t nv = ctr->n_visible;
-    if (r < nv) {
-        uint32_t g = sorted_vals[r];
-        srec_a[r] = rec_a[g];
-        srec_b[r] = rec_b[g];
-        uint2 rc = rect[g];
-        srect[r] = rc;
-        stouched[r] = ((rc.x >> 16) - (rc.x & 0xffffu)) * ((rc.y >> 16) - (rc.y & 0xffffu));
-    } else {
-        stouched[r] = 0;
+__global__ void gather_sorted_k(const uint32_t *__restrict__ sorted_vals, int64_t n, ViewCounters *ctr,
+                                const float4 *__restrict__ rec_a, const float4 *__restrict__ rec_b,
+                                const uint2 *__restrict__ rect, float4 *__restrict__ srec_a,
+                                float4 *__restrict__ srec_b, uint2 *__restrict__ srect,
+                                uint32_t *__restrict__ stouched, int shift) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t tiles = 0;
+    if (r < n) {
+        const uint32_t nv = ctr->n_visible;
+        if (r < nv) {
+            const uint32_t g = sorted_vals[r];
+            srec_a[r] = rec_a[g];
+            srec_b[r] = rec_b[g];
+            const uint2 rc = rect[g];
+            srect[r] = rc;
+            const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
+            tiles = (x1 - x0) * (y1 - y0);
+            stouched[r] = ((((x1 - 1) >> shift) - (x0 >> shift)) + 1) * ((((y1 - 1) >> shift) - (y0 >> shift)) + 1);
+        } else {
+            stouched[r] = 0;
+        }
     }
+    unsigned long long t = tiles;
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(&ctr->P_tiles, t);
 }
 
 __global__ void check_seg_k(const int32_t *__restrict__ seg, int64_t npx, int32_t M, ViewCounters *ctr) {
@@ -313,11 +320,11 @@ void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *c
                                                   dval_orig, rec_a, rec_b, rect, ctr);
 }
 
-void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, const ViewCounters *ctr, const float4 *rec_a,
+void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, ViewCounters *ctr, const float4 *rec_a,
                           const float4 *rec_b, const uint2 *rect, float4 *srec_a, float4 *srec_b, uint2 *srect,
-                          uint32_t *stouched, cudaStream_t st) {
+                          uint32_t *stouched, int shift, cudaStream_t st) {
     gather_sorted_k<<<blocks_for(n, 256), 256, 0, st>>>(sorted_vals, n, ctr, rec_a, rec_b, rect, srec_a, srec_b,
-                                                        srect, stouched);
+                                                        srect, stouched, shift);
 }
 
 void launch_check_seg(const int32_t *seg, int64_t npx, int32_t M, ViewCounters *ctr, cudaStream_t st) {

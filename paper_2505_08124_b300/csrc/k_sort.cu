@@ -1,14 +1,14 @@
 // Stable LSD radix sort and exclusive scan (no CUB).
 //
-// Radix sort, one pass per digit of <= 8 bits, three kernels per pass, over
-// tiles of 256 x ITEMS items (ITEMS = 16, or 4 below ~2M items so that the
-// grid still covers the GPU):
+// Radix sort, one pass per digit of <= 11 bits (256 or 2048 bins), three
+// kernels per pass, over tiles of 256 x ITEMS items (ITEMS = 16, or 4 below
+// ~2M items so that the grid still covers the GPU):
 //   1. rs_hist:    each CTA counts the digits of its tile into per-warp
-//                  shared histograms (shared-memory atomics); writes
-//                  hist[digit][tile] and adds the digit totals.
-//   2. rs_offsets: one CTA per digit scans hist[digit][*] into global
-//                  output offsets (digit start + earlier tiles' counts).
-//   3. rs_scatter: each CTA ranks its tile stably (warp w owns items
+//                  shared histograms (one add per distinct digit of a warp
+//                  round); writes hist[digit][tile] and adds the digit totals.
+//   2. rs_offsets: one CTA per digit scans hist[digit][*] over the tiles and
+//                  writes the digit's total.
+//   3. rs_scatter: each CTA scans the digit totals (digit starts), ranks its tile stably (warp w owns items
 //                  [w*32*ITEMS, (w+1)*32*ITEMS) of the tile in rounds of 32,
 //                  so (warp, round, lane) order is input order; equal digits
 //                  within a round are found with one ballot per digit bit),
@@ -34,46 +34,58 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-template <typename K, int ITEMS>
+// Lanes of the warp whose digit equals this lane's: one ballot per digit bit.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, int width, bool valid) {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    for (int b = 0; b < width; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t ones = __ballot_sync(0xffffffffu, valid && bit);
+        peers &= bit ? ones : ~ones;
+    }
+    return peers;
+}
+
+// Per-tile digit counts: per-warp shared histograms, one add per distinct digit of
+// each 32-item round (the round's leader adds the popcount of its peers).
+template <typename K, int ITEMS, int BINS>
 __global__ void __launch_bounds__(kThreads) rs_hist(const K *__restrict__ keys, int64_t n, int shift,
-                                                    uint32_t mask, uint32_t *__restrict__ hist,
-                                                    uint32_t *__restrict__ digit_tot, int ntiles) {
-    __shared__ uint32_t h[kWarps][256];
+                                                    uint32_t mask, int width, uint32_t *__restrict__ hist,
+                                                    int ntiles) {
+    extern __shared__ __align__(16) uint32_t hsm[];   // kWarps x BINS
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < kWarps * 256; i += kThreads) (&h[0][0])[i] = 0;
+    for (int i = tid; i < kWarps * BINS; i += kThreads) hsm[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * (kThreads * ITEMS) + (int64_t)w * (32 * ITEMS);
+    uint32_t *h = hsm + w * BINS;
 #pragma unroll 4
     for (int r = 0; r < ITEMS; ++r) {
-        int64_t i = base + r * 32 + lane;
-        if (i < n) atomicAdd(&h[w][(uint32_t)(keys[i] >> shift) & mask], 1u);
+        const int64_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t d = valid ? (uint32_t)(keys[i] >> shift) & mask : 0u;
+        const uint32_t peers = digit_peers(d, width, valid);
+        if (valid && lane == __ffs(peers) - 1) h[d] += __popc(peers);
+        __syncwarp();
     }
     __syncthreads();
-    for (int d = tid; d < 256; d += kThreads) {
+    for (int d = tid; d < BINS; d += kThreads) {
         uint32_t s = 0;
 #pragma unroll
-        for (int q = 0; q < kWarps; ++q) s += h[q][d];
+        for (int q = 0; q < kWarps; ++q) s += hsm[q * BINS + d];
         hist[(int64_t)d * ntiles + blockIdx.x] = s;
-        if (s) atomicAdd(&digit_tot[d], s);
     }
 }
 
-// One CTA per digit: offs[d][t] = sum_{d' < d} total[d'] + sum_{t' < t} hist[d][t'].
-__global__ void __launch_bounds__(1024) rs_offsets(uint32_t *__restrict__ hist,
-                                                   const uint32_t *__restrict__ digit_tot, int ntiles) {
+// One CTA per digit: exclusive scan of hist[d][*] over the tiles, in place;
+// the row total goes to digit_tot[d].
+__global__ void __launch_bounds__(1024) rs_offsets(uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_tot,
+                                                  int ntiles) {
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t carry_s;
     const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid < 32) {
-        uint32_t s = 0;
-        for (int q = lane; q < d; q += 32) s += digit_tot[q];
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) carry_s = s;
-    }
-    __syncthreads();
-    uint32_t carry = carry_s;
+    const int nw = blockDim.x >> 5;
+    uint32_t carry = 0;
     uint32_t *row = hist + (int64_t)d * ntiles;
-    for (int base = 0; base < ntiles; base += 1024) {
+    for (int base = 0; base < ntiles; base += blockDim.x) {
         int i = base + tid;
         uint32_t v = i < ntiles ? row[i] : 0;
         uint32_t x = v;
@@ -84,7 +96,7 @@ __global__ void __launch_bounds__(1024) rs_offsets(uint32_t *__restrict__ hist,
         if (lane == 31) warp_sums[w] = x;
         __syncthreads();
         if (w == 0) {
-            uint32_t ws = warp_sums[lane];
+            uint32_t ws = lane < nw ? warp_sums[lane] : 0u;
             uint32_t wx = ws;
             for (int o = 1; o < 32; o <<= 1) {
                 uint32_t y = __shfl_up_sync(0xffffffffu, wx, o);
@@ -97,39 +109,32 @@ __global__ void __launch_bounds__(1024) rs_offsets(uint32_t *__restrict__ hist,
         if (i < ntiles) row[i] = excl;
         __syncthreads();
         // carry for the next chunk: the last thread's exclusive value plus its own count
-        if (tid == 1023) carry_s = excl + v;
+        if (tid == (int)blockDim.x - 1) carry_s = excl + v;
         __syncthreads();
         carry = carry_s;
     }
+    if (tid == 0) digit_tot[d] = carry;
 }
 
-// Lanes of the warp whose digit equals this lane's: one ballot per digit bit.
-__device__ __forceinline__ uint32_t digit_peers(uint32_t d, int width, bool valid) {
-    uint32_t peers = __ballot_sync(0xffffffffu, valid);
-    for (int b = 0; b < width; ++b) {
-        const bool bit = (d >> b) & 1u;
-        const uint32_t ones = __ballot_sync(0xffffffffu, valid && bit);
-        peers &= bit ? ones : ~ones;
-    }
-    return peers;
-}
-
-template <typename K, int ITEMS>
+template <typename K, int ITEMS, int BINS>
 __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                        K *__restrict__ kout, uint32_t *__restrict__ vout,
                                                        int64_t n, int shift, uint32_t mask, int width,
-                                                       const uint32_t *__restrict__ offs, int ntiles) {
+                                                       const uint32_t *__restrict__ offs,
+                                                       const uint32_t *__restrict__ digit_tot, int ntiles,
+                                                       uint2 *__restrict__ ranges, int nranges) {
     constexpr int kTileN = kThreads * ITEMS;
+    constexpr int kPer = BINS / kThreads;              // digits per thread in the per-tile scans
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t(*cnt)[256] = reinterpret_cast<uint32_t(*)[256]>(smem_raw);          // kWarps x 256
-    uint32_t *lstart = reinterpret_cast<uint32_t *>(smem_raw + kWarps * 256 * 4); // 256
-    uint32_t *gbase = lstart + 256;                                                // 256
-    uint32_t *wsum = gbase + 256;                                                  // 8
-    K *skeys = reinterpret_cast<K *>(smem_raw + kWarps * 256 * 4 + 3 * 256 * 4 + 64);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem_raw);              // kWarps x BINS
+    uint32_t *lstart = cnt + kWarps * BINS;                              // BINS
+    uint32_t *gbase = lstart + BINS;                                     // BINS
+    uint32_t *wsum = gbase + BINS;                                       // 16
+    K *skeys = reinterpret_cast<K *>(wsum + 16);
     uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + kTileN);
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < kWarps * 256; i += kThreads) (&cnt[0][0])[i] = 0;
+    for (int i = tid; i < kWarps * BINS; i += kThreads) cnt[i] = 0;
     __syncthreads();
 
     const int64_t tile_base = (int64_t)blockIdx.x * kTileN;
@@ -138,6 +143,7 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
     uint32_t val[ITEMS];
     uint32_t pos[ITEMS];
     const uint32_t lt = lanemask_lt();
+    uint32_t *cw = cnt + w * BINS;
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         const int64_t i = base + r * 32 + lane;
@@ -152,30 +158,23 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
         const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
         const uint32_t peers = digit_peers(d, width, valid);
         uint32_t c = 0;
-        if (valid) c = cnt[w][d];
+        if (valid) c = cw[d];
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) cnt[w][d] = c + __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) cw[d] = c + __popc(peers);
         pos[r] = valid ? c + __popc(peers & lt) : 0xffffffffu;
         __syncwarp();
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps, tile total
-    uint32_t tot;
+    // global start of each digit: exclusive scan of the digit totals (kept in gbase)
     {
-        const int d = tid;
-        uint32_t s = 0;
+        uint32_t dt[kPer];
+        uint32_t dsum = 0;
 #pragma unroll
-        for (int q = 0; q < kWarps; ++q) {
-            uint32_t t = cnt[q][d];
-            cnt[q][d] = s;
-            s += t;
+        for (int k = 0; k < kPer; ++k) {
+            dt[k] = digit_tot[tid * kPer + k];
+            dsum += dt[k];
         }
-        tot = s;
-        gbase[d] = offs[(int64_t)d * ntiles + blockIdx.x];
-    }
-    // exclusive scan of tot over the 256 digits -> lstart
-    {
-        uint32_t x = tot;
+        uint32_t x = dsum;
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
@@ -184,69 +183,119 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
         __syncthreads();
         uint32_t before = 0;
         for (int q = 0; q < w; ++q) before += wsum[q];
-        lstart[tid] = before + x - tot;
+        uint32_t run = before + x - dsum;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int d = tid * kPer + k;
+            gbase[d] = run + offs[(int64_t)d * ntiles + blockIdx.x];
+            if (ranges && blockIdx.x == 0 && d < nranges) ranges[d] = make_uint2(run, run + dt[k]);
+            run += dt[k];
+        }
+        __syncthreads();
+    }
+    // per digit: exclusive prefix over warps (in place) and the tile's digit total
+    uint32_t tot[kPer];
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int d = tid * kPer + k;
+        uint32_t s = 0;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) {
+            const uint32_t t = cnt[q * BINS + d];
+            cnt[q * BINS + d] = s;
+            s += t;
+        }
+        tot[k] = s;
+        tsum += s;
+    }
+    // exclusive scan of the digit totals over the tile -> lstart
+    {
+        uint32_t x = tsum;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int q = 0; q < w; ++q) before += wsum[q];
+        uint32_t run = before + x - tsum;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            lstart[tid * kPer + k] = run;
+            run += tot[k];
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         if (pos[r] != 0xffffffffu) {
-            uint32_t d = (uint32_t)(key[r] >> shift) & mask;
-            uint32_t lp = lstart[d] + cnt[w][d] + pos[r];
+            const uint32_t d = (uint32_t)(key[r] >> shift) & mask;
+            const uint32_t lp = lstart[d] + cw[d] + pos[r];
             skeys[lp] = key[r];
             svals[lp] = val[r];
         }
     }
     __syncthreads();
-    int64_t rem = n - tile_base;
-    int tile_n = rem < kTileN ? (int)rem : kTileN;
+    const int64_t rem = n - tile_base;
+    const int tile_n = rem < kTileN ? (int)rem : kTileN;
     for (int j = tid; j < tile_n; j += kThreads) {
-        K k = skeys[j];
-        uint32_t d = (uint32_t)(k >> shift) & mask;
-        uint32_t gp = gbase[d] + (uint32_t)j - lstart[d];
+        const K k = skeys[j];
+        const uint32_t d = (uint32_t)(k >> shift) & mask;
+        const uint32_t gp = gbase[d] + (uint32_t)j - lstart[d];
         kout[gp] = k;
         vout[gp] = svals[j];
     }
 }
 
-template <typename K, int ITEMS>
+template <typename K, int ITEMS, int BINS>
 size_t scatter_smem() {
-    return (size_t)kWarps * 256 * 4 + 3 * 256 * 4 + 64 + (size_t)kThreads * ITEMS * (sizeof(K) + 4);
+    return (size_t)(kWarps + 2) * BINS * 4 + 64 + (size_t)kThreads * ITEMS * (sizeof(K) + 4);
 }
 
-template <typename K, int ITEMS>
-bool radix_sort_tiles(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, const int *shifts,
-                      const int *widths, int npass, SortScratch &s, cudaStream_t st) {
+template <typename K, int ITEMS, int BINS>
+void radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, int64_t n, int shift, int width, SortScratch &s,
+                cudaStream_t st, uint2 *ranges, int nranges) {
     constexpr int kTileN = kThreads * ITEMS;
     const int ntiles = (int)((n + kTileN - 1) / kTileN);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(rs_scatter<K, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)scatter_smem<K, ITEMS>());
+        cudaFuncSetAttribute(rs_scatter<K, ITEMS, BINS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem<K, ITEMS, BINS>());
+        cudaFuncSetAttribute(rs_hist<K, ITEMS, BINS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kWarps * BINS * 4);
         attr_set = true;
     }
+    const uint32_t mask = (width >= 32) ? 0xffffffffu : ((1u << width) - 1u);
+    rs_hist<K, ITEMS, BINS><<<ntiles, kThreads, kWarps * BINS * 4, st>>>(ki, n, shift, mask, width, s.hist, ntiles);
+    rs_offsets<<<BINS, ntiles >= 1024 ? 1024 : (ntiles >= 256 ? 256 : 64), 0, st>>>(s.hist, s.digit_tot, ntiles);
+    rs_scatter<K, ITEMS, BINS><<<ntiles, kThreads, scatter_smem<K, ITEMS, BINS>(), st>>>(
+        ki, vi, ko, vo, n, shift, mask, width, s.hist, s.digit_tot, ntiles, ranges, nranges);
+}
+
+// Inputs below ~2M items use 1024-item tiles so that the grid still covers the GPU;
+// passes wider than 8 bits use 2048 bins.
+template <typename K>
+bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, const int *shifts,
+                     const int *widths, int npass, SortScratch &s, cudaStream_t st, uint2 *ranges, int nranges) {
+    if (n <= 0 || npass <= 0) return false;
+    const bool small = n < (1 << 21);
     K *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < npass; ++p) {
-        uint32_t mask = (widths[p] >= 32) ? 0xffffffffu : ((1u << widths[p]) - 1u);
-        cudaMemsetAsync(s.digit_tot, 0, 256 * sizeof(uint32_t), st);
-        rs_hist<K, ITEMS><<<ntiles, kThreads, 0, st>>>(ki, n, shifts[p], mask, s.hist, s.digit_tot, ntiles);
-        rs_offsets<<<256, 1024, 0, st>>>(s.hist, s.digit_tot, ntiles);
-        rs_scatter<K, ITEMS><<<ntiles, kThreads, scatter_smem<K, ITEMS>(), st>>>(ki, vi, ko, vo, n, shifts[p], mask,
-                                                                                  widths[p], s.hist, ntiles);
+        uint2 *rg = (npass == 1) ? ranges : nullptr;
+        if (widths[p] > 8) {
+            if (small) radix_pass<K, 4, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges);
+            else radix_pass<K, kItems, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges);
+        } else {
+            if (small) radix_pass<K, 4, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges);
+            else radix_pass<K, kItems, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges);
+        }
         K *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
     }
     return (npass & 1) != 0;
-}
-
-// Inputs below ~2M items use 1024-item tiles so that the grid still covers the GPU.
-template <typename K>
-bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
-                     const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st) {
-    if (n <= 0 || npass <= 0) return false;
-    if (n < (1 << 21))
-        return radix_sort_tiles<K, 4>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st);
-    return radix_sort_tiles<K, kItems>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -352,11 +401,11 @@ __global__ void __launch_bounds__(kThreads) scan_tiles(const uint32_t *__restric
 }  // namespace
 
 cudaError_t scratch_reserve(SortScratch &s, int64_t n) {
-    // the finest tiling used (1024 items) sets the size of the histogram array
-    int64_t tiles = (n + 1023) / 1024 + 1;
-    size_t need_hist = (size_t)256 * tiles;
+    // 2048 bins x the tile count of the tiling used for n items (1024-item tiles below 2M)
+    const int64_t tiles = n < (1 << 21) ? (n + 1023) / 1024 + 1 : (n + kTileItems - 1) / kTileItems + 1;
+    size_t need_hist = (size_t)2048 * tiles;
     if (!s.digit_tot) {
-        cudaError_t e = cudaMalloc(&s.digit_tot, 256 * sizeof(uint32_t));
+        cudaError_t e = cudaMalloc(&s.digit_tot, 2048 * sizeof(uint32_t));
         if (e != cudaSuccess) return e;
     }
     if (need_hist > s.hist_cap) {
@@ -367,13 +416,14 @@ cudaError_t scratch_reserve(SortScratch &s, int64_t n) {
         if (e != cudaSuccess) return e;
         s.hist_cap = need_hist;
     }
-    if ((size_t)tiles > s.partials_cap) {
+    const int64_t scan_tiles_n = (n + kTileItems - 1) / kTileItems + 1;
+    if ((size_t)scan_tiles_n > s.partials_cap) {
         cudaFree(s.partials);
         s.partials = nullptr;
         s.partials_cap = 0;
-        cudaError_t e = cudaMalloc(&s.partials, (size_t)tiles * sizeof(uint32_t));
+        cudaError_t e = cudaMalloc(&s.partials, (size_t)scan_tiles_n * sizeof(uint32_t));
         if (e != cudaSuccess) return e;
-        s.partials_cap = (size_t)tiles;
+        s.partials_cap = (size_t)scan_tiles_n;
     }
     return cudaSuccess;
 }
@@ -385,9 +435,11 @@ void scratch_free(SortScratch &s) {
     s = SortScratch{};
 }
 
-int digit_passes(int lo, int bits, int *shifts, int *widths) {
+int digit_passes(int lo, int bits, int *shifts, int *widths, int64_t n) {
     if (bits <= 0) return 0;
-    int np = (bits + 7) / 8;
+    // 2048-bin passes pay off only on large inputs; small ones use 8-bit digits
+    const int maxw = n >= (1 << 21) ? 11 : 8;
+    int np = (bits + maxw - 1) / maxw;
     int base = bits / np, extra = bits % np, at = lo;
     for (int p = 0; p < np; ++p) {
         int wdt = base + (p < extra ? 1 : 0);
@@ -399,13 +451,15 @@ int digit_passes(int lo, int bits, int *shifts, int *widths) {
 }
 
 bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
-                    const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st) {
-    return radix_sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st);
+                    const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st,
+                    uint2 *ranges, int nranges) {
+    return radix_sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st, ranges,
+                                     nranges);
 }
 
 bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                     const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st) {
-    return radix_sort_impl<uint64_t>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st);
+    return radix_sort_impl<uint64_t>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st, nullptr, 0);
 }
 
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *d_total,

@@ -46,8 +46,12 @@ struct slag_ctx {
     // per-view, P-sized and image-sized
     uint32_t *pkey[2] = {nullptr, nullptr}, *pval[2] = {nullptr, nullptr};
     int64_t p_cap = 0;
+    uint2 *prect = nullptr;
+    int64_t prect_cap = 0;
     uint2 *ranges = nullptr;
     int64_t ranges_cap = 0;
+    uint32_t *tile_order = nullptr;
+    int64_t order_cap = 0;
     int32_t *seg_buf = nullptr;
     int64_t seg_cap = 0;
     float *dbg_T = nullptr, *dbg_wsum = nullptr;
@@ -240,7 +244,8 @@ int ceil_log2(uint64_t v) {
 // records, the tile-sorted pair list and ranges in the workspace; returns the
 // pair count in *P_out and the list buffer in *list_out.
 slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_t **keys_out,
-                     uint32_t **list_out, const int32_t *seg_check, int32_t M, const uint32_t **sgid_out) {
+                     uint32_t **list_out, const int32_t *seg_check, int32_t M, const uint32_t **sgid_out,
+                     int shift) {
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->n;
     CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
@@ -249,13 +254,13 @@ slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_
     launch_project(cp, ctx->mean_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, ctx->dkey[0], ctx->dval[0],
                    ctx->rec_a, ctx->rec_b, ctx->rect, ctx->ctr, st);
     int shifts[8], widths[8];
-    int np = digit_passes(0, 32, shifts, widths);
+    int np = digit_passes(0, 32, shifts, widths, n);
     bool alt = radix_sort_u32(ctx->dkey[0], ctx->dkey[1], ctx->dval[0], ctx->dval[1], n, shifts, widths, np,
                               ctx->scratch, st);
     const uint32_t *sorted_vals = ctx->dval[alt ? 1 : 0];
     *sgid_out = sorted_vals;
     launch_gather_sorted(sorted_vals, n, ctx->ctr, ctx->rec_a, ctx->rec_b, ctx->rect, ctx->srec_a, ctx->srec_b,
-                         ctx->srect, ctx->stouched, st);
+                         ctx->srect, ctx->stouched, shift, st);
     exclusive_scan_u32(ctx->stouched, ctx->offsets, n, &ctx->ctr->P, ctx->scratch, st);
     span_end(ctx);
     CK(cudaMemcpyAsync(&ctx->hc->v, ctx->ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
@@ -264,8 +269,9 @@ slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_
     CK(cudaGetLastError());
     spans_resolve(ctx);
     if (ctx->hc->v.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
-    const int64_t P = (int64_t)ctx->hc->v.P;
-    if (P > 0x7fffffffLL) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^31-1 Gaussian-tile pairs in one view");
+    const int64_t P = (int64_t)ctx->hc->v.P;   // pairs at the binning granularity
+    if (P > 0x7fffffffLL || ctx->hc->v.P_tiles > 0x7fffffffULL)
+        return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^31-1 Gaussian-tile pairs in one view");
     if (P > ctx->p_cap) {
         int64_t cap = ctx->p_cap;
         for (int b = 0; b < 2; ++b) {
@@ -276,17 +282,34 @@ slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_
         }
         CK(scratch_reserve(ctx->scratch, ctx->p_cap));
     }
+    const int bins_x = ((cp.tiles_x - 1) >> shift) + 1, bins_y = ((cp.tiles_y - 1) >> shift) + 1;
+    const int64_t bins = (int64_t)bins_x * bins_y;
     const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
-    CK(grow(ctx->ranges, ctx->ranges_cap, tiles, st));
-    CK(cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)tiles, st));
+    CK(grow(ctx->ranges, ctx->ranges_cap, bins, st));
     uint32_t nv = ctx->hc->v.n_visible;
     span_begin(ctx, SLAG_STAGE_BIN);
-    launch_emit(ctx->srect, ctx->offsets, nv, cp.tiles_x, ctx->pkey[0], ctx->pval[0], st);
-    np = digit_passes(0, ceil_log2((uint64_t)tiles), shifts, widths);
-    alt = radix_sort_u32(ctx->pkey[0], ctx->pkey[1], ctx->pval[0], ctx->pval[1], P, shifts, widths, np,
-                         ctx->scratch, st);
-    uint32_t *keys = ctx->pkey[alt ? 1 : 0];
-    launch_ranges(keys, P, ctx->ranges, st);
+    launch_emit(ctx->srect, ctx->offsets, nv, shift, bins_x, ctx->pkey[0], ctx->pval[0], st);
+    np = digit_passes(0, ceil_log2((uint64_t)bins), shifts, widths, P);
+    uint32_t *keys = ctx->pkey[0];
+    alt = false;
+    if (P > 0 && np == 1) {
+        // one pass: its digit is the bin id, and the pass's offsets give the ranges
+        alt = radix_sort_u32(ctx->pkey[0], ctx->pkey[1], ctx->pval[0], ctx->pval[1], P, shifts, widths, np,
+                             ctx->scratch, st, ctx->ranges, (int)bins);
+        keys = ctx->pkey[alt ? 1 : 0];
+    } else {
+        CK(cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)bins, st));
+        alt = radix_sort_u32(ctx->pkey[0], ctx->pkey[1], ctx->pval[0], ctx->pval[1], P, shifts, widths, np,
+                             ctx->scratch, st);
+        keys = ctx->pkey[alt ? 1 : 0];
+        launch_ranges(keys, P, ctx->ranges, st);
+    }
+    CK(grow(ctx->tile_order, ctx->order_cap, tiles, st));
+    launch_tile_order(ctx->ranges, cp.tiles_x, cp.tiles_y, shift, ctx->tile_order, st);
+    if (shift > 0) {
+        CK(grow(ctx->prect, ctx->prect_cap, P, st));
+        launch_pair_rects(ctx->pval[alt ? 1 : 0], P, ctx->srect, ctx->prect, st);
+    }
     span_end(ctx);
     *P_out = P;
     *keys_out = keys;
@@ -370,7 +393,7 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     launch_bbox(im, n, bb, st);
     launch_morton(im, n, bb, ctx->dkey[0], ctx->dval[0], st);
     int shifts[8], widths[8];
-    int np = digit_passes(0, 30, shifts, widths);
+    int np = digit_passes(0, 30, shifts, widths, n);
     bool alt = radix_sort_u32(ctx->dkey[0], ctx->dkey[1], ctx->dval[0], ctx->dval[1], n, shifts, widths, np,
                               ctx->scratch, st);
     CA(cudaMemcpyAsync(ctx->orig_of_int, ctx->dval[alt ? 1 : 0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
@@ -424,14 +447,14 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, cp, &P, &keys, &list, seg, M, &sgid);
+    s = bin_view(ctx, cp, &P, &keys, &list, seg, M, &sgid, kSuperShift);
     if (s != SLAG_OK) return s;
 
     // room in the triple log: at most kHashSlots per Gaussian from the consume
     // pass plus the overflow appends of this view
     const unsigned long long used = ctx->hc->totals[0];
     ctx->contrib_before_last = ctx->hc->totals[1];
-    const int64_t need = (int64_t)used + ctx->n * kHashSlots + 2 * P + (1 << 20);
+    const int64_t need = (int64_t)used + ctx->n * kHashSlots + 2 * (int64_t)ctx->hc->v.P_tiles + (1 << 20);
     if (need > ctx->log_cap) {
         int64_t c1 = ctx->log_cap, c2 = ctx->log_cap;
         CK(grow(ctx->log_key, c1, need, st, (int64_t)used));
@@ -441,7 +464,11 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     CompositeArgs a;
     a.cam = cp;
     a.ranges = ctx->ranges;
+    a.bin_shift = kSuperShift;
+    a.bins_x = ((cp.tiles_x - 1) >> kSuperShift) + 1;
+    a.tile_order = ctx->tile_order;
     a.list = list;
+    a.prect = ctx->prect;
     a.srec_a = ctx->srec_a;
     a.srec_b = ctx->srec_b;
     a.sgid = sgid;
@@ -472,8 +499,8 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     CK(cudaGetLastError());
     ctx->table_rows += M;
     ctx->stats.views += 1;
-    ctx->stats.pairs += P;
-    ctx->stats.last_pairs = P;
+    ctx->stats.pairs += (int64_t)ctx->hc->v.P_tiles;
+    ctx->stats.last_pairs = (int64_t)ctx->hc->v.P_tiles;
     ctx->stats.columns = ctx->table_rows;
     ctx->finalized = false;
     return SLAG_OK;
@@ -515,8 +542,8 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
         span_begin(ctx, SLAG_STAGE_LOG_SORT);
         // sort by (block, column, Gaussian): bits [0, 7 + col_bits) then [39, 39 + block_bits)
         int shifts[16], widths[16];
-        int np = digit_passes(0, 7 + ceil_log2((uint64_t)ctx->table_rows), shifts, widths);
-        np += digit_passes(39, ceil_log2((uint64_t)nblocks), shifts + np, widths + np);
+        int np = digit_passes(0, 7 + ceil_log2((uint64_t)ctx->table_rows), shifts, widths, Z);
+        np += digit_passes(39, ceil_log2((uint64_t)nblocks), shifts + np, widths + np, Z);
         bool alt = radix_sort_u64(ctx->log_key, ctx->log_key_alt, reinterpret_cast<uint32_t *>(ctx->log_w),
                                   reinterpret_cast<uint32_t *>(ctx->log_w_alt), Z, shifts, widths, np,
                                   ctx->scratch, st);
@@ -662,7 +689,7 @@ void slag_destroy(slag_ctx *ctx) {
     for (int b = 0; b < 2; ++b) { dfree(ctx->dkey[b]); dfree(ctx->dval[b]); dfree(ctx->pkey[b]); dfree(ctx->pval[b]); }
     dfree(ctx->rec_a); dfree(ctx->rec_b); dfree(ctx->srec_a); dfree(ctx->srec_b); dfree(ctx->rect); dfree(ctx->srect);
     dfree(ctx->stouched); dfree(ctx->offsets); dfree(ctx->hash); dfree(ctx->s_hi); dfree(ctx->s_lo); dfree(ctx->s_ovf);
-    dfree(ctx->ranges); dfree(ctx->seg_buf); dfree(ctx->dbg_T); dfree(ctx->dbg_wsum); dfree(ctx->dbg_count);
+    dfree(ctx->ranges); dfree(ctx->prect); dfree(ctx->tile_order); dfree(ctx->seg_buf); dfree(ctx->dbg_T); dfree(ctx->dbg_wsum); dfree(ctx->dbg_count);
     dfree(ctx->ctr); dfree(ctx->totals); dfree(ctx->touched);
     dfree(ctx->log_key); dfree(ctx->log_key_alt); dfree(ctx->log_w); dfree(ctx->log_w_alt);
     dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
@@ -702,7 +729,7 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0, &sgid);
+    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0, &sgid, 0);
     if (s != SLAG_OK) return s;
     if (out_P) *out_P = P;
     const int64_t n = ctx->n;
@@ -771,7 +798,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0, &sgid);
+    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0, &sgid, kSuperShift);
     if (s != SLAG_OK) return s;
     if (npx > ctx->dbg_cap) {
         int64_t c1 = ctx->dbg_cap, c2 = ctx->dbg_cap, c3 = ctx->dbg_cap;
@@ -784,7 +811,11 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     memset(&a, 0, sizeof(a));
     a.cam = cp;
     a.ranges = ctx->ranges;
+    a.bin_shift = kSuperShift;
+    a.bins_x = ((cp.tiles_x - 1) >> kSuperShift) + 1;
+    a.tile_order = ctx->tile_order;
     a.list = list;
+    a.prect = ctx->prect;
     a.srec_a = ctx->srec_a;
     a.srec_b = ctx->srec_b;
     a.sgid = sgid;

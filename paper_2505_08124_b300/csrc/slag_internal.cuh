@@ -11,6 +11,7 @@ namespace slag {
 constexpr int kTile = 16;          // screen tile edge in pixels
 constexpr int kBlockG = 128;       // Gaussians per aggregation block (key packs g & 127)
 constexpr int kHashSlots = 4;      // per-view (segment, weight) slots per Gaussian
+constexpr int kSuperShift = 2;     // compositing lists are binned per 4x4-tile super-tile
 constexpr int kMaxK = 1024;        // largest top-k
 constexpr uint32_t kCulled = 0xFFFFFFFFu;
 
@@ -28,7 +29,8 @@ struct __align__(16) HashEntry {
 struct ViewCounters {
     uint32_t n_visible;
     uint32_t bad_seg;                 // non-zero: a segment id outside [-1, M)
-    unsigned long long P;             // Gaussian-tile pairs
+    unsigned long long P;             // pairs at the binning granularity (tiles or super-tiles)
+    unsigned long long P_tiles;       // Gaussian-tile pairs
     unsigned long long contributions; // composited (Gaussian, pixel) pairs (diagnostic render)
     uint32_t pad[2];
 };
@@ -59,11 +61,13 @@ cudaError_t scratch_reserve(SortScratch &s, int64_t n);
 void scratch_free(SortScratch &s);
 
 // Stable LSD radix sort of (key, value) pairs over the bit ranges listed in
-// shifts/widths (each width <= 8, applied in order). Ping-pongs between the
-// two buffers; returns true when the result is in the *_alt buffers.
+// shifts/widths (each width <= 11, applied in order). Ping-pongs between the
+// two buffers; returns true when the result is in the *_alt buffers. For a
+// single pass whose digit is the whole key, `ranges` (nullable) receives each
+// key value's [start, end) in the output for key values < nranges.
 bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                     int64_t n, const int *shifts, const int *widths, int npass, SortScratch &s,
-                    cudaStream_t st);
+                    cudaStream_t st, uint2 *ranges = nullptr, int nranges = 0);
 bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                     int64_t n, const int *shifts, const int *widths, int npass, SortScratch &s,
                     cudaStream_t st);
@@ -72,8 +76,9 @@ bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *d_total,
                         SortScratch &s, cudaStream_t st);
 
-// Splits [lo, lo + bits) into passes of at most 8 bits; returns the pass count.
-int digit_passes(int lo, int bits, int *shifts, int *widths);
+// Splits [lo, lo + bits) into passes for a sort of n items (at most 11 bits
+// per pass from 2M items up, 8 below); returns the pass count.
+int digit_passes(int lo, int bits, int *shifts, int *widths, int64_t n);
 
 // ---------------------------------------------------------------------------
 // launchers
@@ -93,22 +98,34 @@ void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *c
                     const float2 *cov_b, int64_t n, const uint32_t *orig_of_int, uint32_t *dkey_orig,
                     uint32_t *dval_orig, float4 *rec_a, float4 *rec_b, uint2 *rect,
                     ViewCounters *ctr, cudaStream_t st);
-void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, const ViewCounters *ctr,
+// Records, rectangles and bin counts in depth-rank order. With shift s > 0 the
+// count is of 2^s x 2^s-tile super-tiles; the tile-pair total goes to ctr->P_tiles.
+void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, ViewCounters *ctr,
                           const float4 *rec_a, const float4 *rec_b, const uint2 *rect,
                           float4 *srec_a, float4 *srec_b, uint2 *srect, uint32_t *stouched,
-                          cudaStream_t st);
+                          int shift, cudaStream_t st);
 void launch_check_seg(const int32_t *seg, int64_t npx, int32_t M, ViewCounters *ctr, cudaStream_t st);
 
 // k_bin.cu
-void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int tiles_x,
+// One (bin, depth rank) pair per Gaussian-bin overlap; bins are 2^shift-tile squares,
+// bins_x of them per row.
+void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int shift, int bins_x,
                  uint32_t *keys, uint32_t *vals, cudaStream_t st);
 void launch_ranges(const uint32_t *keys, int64_t P, uint2 *ranges, cudaStream_t st);
+// prect[i] = srect[list[i]]: the tile rectangle of each sorted pair's Gaussian.
+void launch_pair_rects(const uint32_t *list, int64_t P, const uint2 *srect, uint2 *prect, cudaStream_t st);
+// Tiles grouped by descending floor(log2(list length + 1)) of their bin.
+void launch_tile_order(const uint2 *ranges, int tiles_x, int tiles_y, int shift, uint32_t *order,
+                       cudaStream_t st);
 
 // k_composite.cu
 struct CompositeArgs {
     CamParams cam;
-    const uint2 *ranges;
+    const uint2 *ranges;           // per bin (tile, or super-tile when bin_shift > 0)
+    int32_t bin_shift, bins_x;
+    const uint32_t *tile_order;    // CTAs of tile_order[i] come i-th
     const uint32_t *list;          // sorted values: depth rank of each pair
+    const uint2 *prect;            // tile rectangle of the Gaussian of each sorted pair
     const float4 *srec_a, *srec_b; // records in depth-rank order
     const uint32_t *sgid;          // internal Gaussian index of each depth rank
     const int32_t *seg;            // H x W
