@@ -184,6 +184,11 @@ size_t query_cand_entries(int32_t B, int64_t n, int32_t k) {
     return (size_t)B * (size_t)ntiles * (size_t)kk;
 }
 
+void launch_query_merge(const float *cand_s, const uint32_t *cand_i, int64_t per_query, int32_t B, int32_t k,
+                        int64_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t st) {
+    merge_k<<<B, 256, 0, st>>>(cand_s, cand_i, per_query, k, out_ids, out_scores, out_count);
+}
+
 void launch_query_topk(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n, int32_t D,
                        int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids, float *out_scores,
                        int32_t *out_count, cudaStream_t st) {

@@ -1,0 +1,374 @@
+// Cosine top-k on the 5th-generation tensor cores ("Query processing for
+// inference": score_k = q . E_k / |E_k|, top-k by descending score, ties to
+// the lower Gaussian index).
+//
+// A CTA scores 256 queries x 256 Gaussians per tile as two tcgen05.mma
+// accumulators of M = 128 TMEM lanes (queries) x N = 256 TMEM columns
+// (Gaussians), fp32, over K = D in chunks of 16. Float32 accuracy comes from
+// the three-term TF32 split x = hi + lo (hi = x rounded to TF32, lo = the
+// rest rounded to TF32): q.e ~ q_hi.e_hi + q_hi.e_lo + q_lo.e_hi, so each
+// chunk issues 2 accumulators x 2 K-steps x 3 MMAs of K = 8. The CTA's 512
+// threads stage operands into shared memory in the canonical no-swizzle
+// K-major layout (core matrices of 8 rows x 16 bytes; K-adjacent core
+// matrices 128 bytes apart, 8-row groups 512 bytes apart), three stages deep
+// against the MMAs (mbarriers), with the next chunk's global loads in flight
+// while the current one is converted. After a tile's last chunk, the first 8
+// warps read one query's 256 scores each from TMEM (tcgen05.ld 32x32b),
+// scale them by 1/|E_k| and keep a running top-16 in registers. A grid of
+// (query tiles x Gaussian splits) writes per-split candidates that the merge
+// kernel of k_query.cu reduces to the final top-k.
+//
+// Every wait on an mbarrier is bounded (about one second of globaltimer);
+// on timeout the kernel sets *err, stops issuing work and releases its TMEM.
+#include "slag_internal.cuh"
+
+namespace slag {
+
+namespace {
+
+constexpr int kM = 256;          // queries per CTA tile: two accumulators of 128 TMEM lanes
+constexpr int kMmaM = 128;       // M of one MMA (TMEM lanes of one accumulator)
+constexpr int kN = 256;          // Gaussians per tile (TMEM columns of one accumulator)
+constexpr int kKC = 16;          // K per staged chunk
+constexpr int kStages = 3;
+constexpr int kThreadsTC = 512;
+constexpr int kTopTC = 16;       // running top-k kept per query
+constexpr uint32_t kTmemCols = 512;
+
+// byte sizes of one stage
+constexpr int kABytes = kM * kKC * 4;   // 16 KB
+constexpr int kBBytes = kN * kKC * 4;   // 16 KB
+constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
+constexpr int kSBO = (kKC / 4) * 128;   // bytes between 8-row groups
+constexpr int kLoadsPerThread = (kM + kN) * (kKC / 4) / kThreadsTC;   // float4 per thread per chunk
+
+struct __align__(8) TcCtl {
+    uint64_t bar[kStages];
+    uint32_t tmem_addr;
+    uint32_t abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete; false after ~1 s.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (gtimer() - t0 > 1000000000ull) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major canonical layout.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of the 5th-generation tensor cores
+    return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                            ((uint32_t)(kMmaM >> 4) << 24);
+static_assert(kMmaM == 128 && kN % 16 == 0 && kN <= 256, "cta_group::1 tf32 MMA shape");
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ bool better(float s, uint32_t i, float s2, uint32_t i2) {
+    return s > s2 || (s == s2 && i < i2);
+}
+
+// Byte offset of element (row, 4-element group kq) of a [rows x kKC] K-major tile.
+__device__ __forceinline__ uint32_t core_off(int row, int kq) {
+    return (uint32_t)(((row >> 3) * (kKC / 4) + kq) * 128 + (row & 7) * 16);
+}
+
+__device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo, uint32_t off, float4 v) {
+    float4 h, l;
+    h.x = to_tf32(v.x); l.x = to_tf32(v.x - h.x);
+    h.y = to_tf32(v.y); l.y = to_tf32(v.y - h.y);
+    h.z = to_tf32(v.z); l.z = to_tf32(v.z - h.z);
+    h.w = to_tf32(v.w); l.w = to_tf32(v.w - h.w);
+    *reinterpret_cast<float4 *>(hi + off) = h;
+    *reinterpret_cast<float4 *>(lo + off) = l;
+}
+
+__global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restrict__ Q, int32_t B,
+                                                            const float *__restrict__ E,
+                                                            const float *__restrict__ inv_norm, int64_t n,
+                                                            int32_t D, int32_t k, int32_t nsplit,
+                                                            float *__restrict__ cand_s,
+                                                            uint32_t *__restrict__ cand_i, uint32_t *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *stage0 = smem_raw;
+    TcCtl *ctl = reinterpret_cast<TcCtl *>(smem_raw + kStages * kStageBytes);
+    float *sinv = reinterpret_cast<float *>(smem_raw + kStages * kStageBytes + 64);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q0 = blockIdx.x * kM;
+    const int split = blockIdx.y;
+    const int64_t ntile_g = (n + kN - 1) / kN;
+    const int64_t per = (ntile_g + nsplit - 1) / nsplit;
+    const int64_t t_begin = split * per;
+    const int64_t t_end = min(ntile_g, t_begin + per);
+    const int nchunk = D / kKC;
+    const int64_t total_chunks = t_end > t_begin ? (t_end - t_begin) * nchunk : 0;
+
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) mbar_init(&ctl->bar[i], 1);
+        ctl->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_addr)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = ctl->tmem_addr;
+
+    float bs[kTopTC];
+    uint32_t bi[kTopTC];
+#pragma unroll
+    for (int i = 0; i < kTopTC; ++i) {
+        bs[i] = -INFINITY;
+        bi[i] = 0xffffffffu;
+    }
+
+    // this thread's share of a chunk: kLoadsPerThread float4, A rows first then B rows
+    auto fetch = [&](int64_t gc, float4 (&v)[kLoadsPerThread]) {
+        const int64_t t = t_begin + gc / nchunk;
+        const int d0 = (int)(gc % nchunk) * kKC;
+        const int64_t g0 = t * kN;
+#pragma unroll
+        for (int j = 0; j < kLoadsPerThread; ++j) {
+            const int i = tid + j * kThreadsTC;          // 0 .. (kM + kN) * 4
+            const int row = i >> 2, kq = i & 3;
+            v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < kM) {
+                if (q0 + row < B) v[j] = __ldg(reinterpret_cast<const float4 *>(Q + (int64_t)(q0 + row) * D + d0 + kq * 4));
+            } else {
+                const int64_t g = g0 + (row - kM);
+                if (g < n) v[j] = __ldg(reinterpret_cast<const float4 *>(E + g * D + d0 + kq * 4));
+            }
+        }
+    };
+
+    float4 pf[kLoadsPerThread];
+    if (total_chunks > 0) fetch(0, pf);
+    bool ok = true;
+    int64_t gc = 0;
+    for (; gc < total_chunks; ++gc) {
+        const int st = (int)(gc % kStages);
+        unsigned char *A_hi = stage0 + st * kStageBytes;
+        unsigned char *A_lo = A_hi + kABytes;
+        unsigned char *B_hi = A_lo + kABytes;
+        unsigned char *B_lo = B_hi + kBBytes;
+        const int c = (int)(gc % nchunk);
+        // the MMAs that last read this stage (chunk gc - kStages) must be done
+        if (gc >= kStages) {
+            if (!mbar_wait(&ctl->bar[st], (uint32_t)((gc - kStages) / kStages) & 1u)) ok = false;
+        }
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+#pragma unroll
+        for (int j = 0; j < kLoadsPerThread; ++j) {
+            const int i = tid + j * kThreadsTC;
+            const int row = i >> 2, kq = i & 3;
+            if (row < kM) split_store(A_hi, A_lo, core_off(row, kq), pf[j]);
+            else split_store(B_hi, B_lo, core_off(row - kM, kq), pf[j]);
+        }
+        if (gc + 1 < total_chunks) fetch(gc + 1, pf);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(A_hi), a_lo = smem_u32(A_lo);
+            const uint32_t b_hi = smem_u32(B_hi), b_lo = smem_u32(B_lo);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t ah = a_hi + h * 16 * kSBO, al = a_lo + h * 16 * kSBO;   // rows 128h..
+                const uint32_t dt = tmem + (uint32_t)(h * kN);                         // columns 256h..
+#pragma unroll
+                for (int s2 = 0; s2 < kKC / 8; ++s2) {
+                    const uint32_t ko = s2 * 256;   // two core matrices of K = 4 per MMA of K = 8
+                    const uint64_t dah = smem_desc(ah + ko, 128, kSBO), dal = smem_desc(al + ko, 128, kSBO);
+                    const uint64_t dbh = smem_desc(b_hi + ko, 128, kSBO), dbl = smem_desc(b_lo + ko, 128, kSBO);
+                    mma_tf32(dt, dah, dbh, (c > 0 || s2 > 0) ? 1u : 0u);
+                    mma_tf32(dt, dah, dbl, 1u);
+                    mma_tf32(dt, dal, dbh, 1u);
+                }
+            }
+            mma_commit(&ctl->bar[st]);
+        }
+        if (c != nchunk - 1) continue;
+        // epilogue of the tile: its last commit follows every earlier MMA
+        if (!mbar_wait(&ctl->bar[st], (uint32_t)(gc / kStages) & 1u)) ok = false;
+        if (__syncthreads_or(!ok)) { ok = false; ++gc; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int64_t g0 = (t_begin + gc / nchunk) * kN;
+        for (int i = tid; i < kN; i += kThreadsTC) {
+            const int64_t g = g0 + i;
+            sinv[i] = g < n ? inv_norm[g] : 0.f;
+        }
+        __syncthreads();
+        if (warp < 8) {
+            // warp w: accumulator w / 4, TMEM lanes 32 (w % 4) ..
+            const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * kN);
+            for (int cb = 0; cb < kN; cb += 32) {
+                float v[32];
+                tmem_ld32(base + (uint32_t)cb, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float inv = sinv[cb + j];
+                    if (inv > 0.f) {
+                        float sc = v[j] * inv;
+                        uint32_t gi = (uint32_t)(g0 + cb + j);
+                        if (better(sc, gi, bs[kTopTC - 1], bi[kTopTC - 1])) {
+#pragma unroll
+                            for (int p = 0; p < kTopTC; ++p) {
+                                if (better(sc, gi, bs[p], bi[p])) {
+                                    const float ts = bs[p];
+                                    const uint32_t ti = bi[p];
+                                    bs[p] = sc;
+                                    bi[p] = gi;
+                                    sc = ts;
+                                    gi = ti;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();   // every thread has read the accumulators before the next tile overwrites them
+    }
+
+    if (!ok) {
+        if (tid == 0) atomicOr(err, 1u);
+        // let MMAs in flight finish (bounded) before TMEM is released
+        if (gc > 0) {
+            const int64_t last = gc - 1;
+            mbar_wait(&ctl->bar[last % kStages], (uint32_t)(last / kStages) & 1u);
+        }
+    }
+    // this query's candidates of this split
+    if (warp < 8) {
+        const int q = q0 + (warp >> 2) * 128 + (warp & 3) * 32 + lane;
+        if (q < B) {
+            const int kk = k < kTopTC ? k : kTopTC;
+            float *cs = cand_s + ((int64_t)q * nsplit + split) * kk;
+            uint32_t *ci = cand_i + ((int64_t)q * nsplit + split) * kk;
+#pragma unroll
+            for (int p = 0; p < kTopTC; ++p)
+                if (p < kk) {
+                    cs[p] = bs[p];
+                    ci[p] = bs[p] == -INFINITY ? 0xffffffffu : bi[p];
+                }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+size_t tc_smem() { return (size_t)kStages * kStageBytes + 64 + kN * 4; }
+
+}  // namespace
+
+bool query_tc_supported(int32_t D, int32_t k) { return k >= 1 && k <= kTopTC && D % kKC == 0; }
+
+int32_t query_tc_splits(int32_t B, int64_t n) {
+    const int64_t qt = (B + kM - 1) / kM;
+    const int64_t nt = (n + kN - 1) / kN;
+    int64_t s = 148 / qt;
+    if (s < 1) s = 1;
+    if (s > nt) s = nt;
+    return (int32_t)s;
+}
+
+void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n, int32_t D,
+                          int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids, float *out_scores,
+                          int32_t *out_count, uint32_t *err, cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(query_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem());
+        attr_set = true;
+    }
+    const int32_t nsplit = query_tc_splits(B, n);
+    dim3 grid((unsigned)((B + kM - 1) / kM), (unsigned)nsplit);
+    query_tc_k<<<grid, kThreadsTC, tc_smem(), st>>>(Q, B, E, inv_norm, n, D, k, nsplit, cand_s, cand_i, err);
+    const int32_t kk = k < kTopTC ? k : kTopTC;
+    launch_query_merge(cand_s, cand_i, (int64_t)nsplit * kk, B, k, out_ids, out_scores, out_count, st);
+}
+
+}  // namespace slag

@@ -67,7 +67,10 @@ struct slag_ctx {
         ViewCounters v;
         unsigned long long totals[4];
         unsigned long long touched;
+        uint32_t tc_err;
+        uint32_t pad;
     } *hc = nullptr;                         // pinned host
+    uint32_t *tc_err = nullptr;              // device: a tensor-core query kernel gave up waiting
     unsigned long long contrib_before_last = 0;
 
     // triple log + finalize scratch
@@ -373,6 +376,8 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     ctx->log_count = ctx->totals;
     ctx->contrib = ctx->totals + 1;
     CA(dalloc(&ctx->touched, 1));
+    CA(dalloc(&ctx->tc_err, 1));
+    CA(cudaMemsetAsync(ctx->tc_err, 0, sizeof(uint32_t), st));
     CA(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
     CA(cudaMemsetAsync(ctx->totals, 0, 4 * sizeof(unsigned long long), st));
     CA(scratch_reserve(ctx->scratch, n));
@@ -611,7 +616,10 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
         CK(cudaMemcpyAsync(ctx->qbuf, Q, sizeof(float) * (size_t)(B * D), cudaMemcpyHostToDevice, st));
         dQ = ctx->qbuf;
     }
-    const int64_t nc = (int64_t)query_cand_entries(B, ctx->n, k);
+    if (((uintptr_t)dQ & 15u) != 0) return fail(ctx, SLAG_ERR_INVALID_ARG, "Q must be 16-byte aligned");
+    const bool tc = query_tc_supported(ctx->D, k);
+    const int64_t nc = tc ? (int64_t)B * query_tc_splits(B, ctx->n) * (k < 16 ? k : 16)
+                          : (int64_t)query_cand_entries(B, ctx->n, k);
     if (nc > ctx->cand_cap) {
         int64_t c1 = ctx->cand_cap, c2 = ctx->cand_cap;
         CK(grow(ctx->cand_s, c1, nc, st));
@@ -634,15 +642,21 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
         cnt = ctx->qcount;
     }
     span_begin(ctx, SLAG_STAGE_QUERY);
-    launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i, ids, scores, cnt,
-                      st);
+    if (tc)
+        launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i, ids, scores,
+                             cnt, ctx->tc_err, st);
+    else
+        launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i, ids, scores,
+                          cnt, st);
     span_end(ctx);
     CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&ctx->hc->tc_err, ctx->tc_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     if (!on_device) {
         CK(cudaMemcpyAsync(out_ids, ids, sizeof(int64_t) * (size_t)B * k, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(out_scores, scores, sizeof(float) * (size_t)B * k, cudaMemcpyDeviceToHost, st));
         if (out_count) CK(cudaMemcpyAsync(out_count, cnt, sizeof(int32_t) * (size_t)B, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        if (ctx->hc->tc_err) return fail(ctx, SLAG_ERR_TIMEOUT, "a tensor-core query kernel gave up waiting");
     }
     return SLAG_OK;
 }
@@ -690,7 +704,7 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->rec_a); dfree(ctx->rec_b); dfree(ctx->srec_a); dfree(ctx->srec_b); dfree(ctx->rect); dfree(ctx->srect);
     dfree(ctx->stouched); dfree(ctx->offsets); dfree(ctx->hash); dfree(ctx->s_hi); dfree(ctx->s_lo); dfree(ctx->s_ovf);
     dfree(ctx->ranges); dfree(ctx->prect); dfree(ctx->tile_order); dfree(ctx->seg_buf); dfree(ctx->dbg_T); dfree(ctx->dbg_wsum); dfree(ctx->dbg_count);
-    dfree(ctx->ctr); dfree(ctx->totals); dfree(ctx->touched);
+    dfree(ctx->ctr); dfree(ctx->totals); dfree(ctx->touched); dfree(ctx->tc_err);
     dfree(ctx->log_key); dfree(ctx->log_key_alt); dfree(ctx->log_w); dfree(ctx->log_w_alt);
     dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
     dfree(ctx->table); dfree(ctx->E); dfree(ctx->inv_norm); dfree(ctx->wsum);

@@ -176,8 +176,18 @@ void launch_aggregate(const AggArgs &a, int64_t nblocks, cudaStream_t st);
 
 // k_query.cu
 size_t query_cand_entries(int32_t B, int64_t n, int32_t k);
+// per query: the best k of `per_query` candidates (score, index; index 0xffffffff = none)
+void launch_query_merge(const float *cand_s, const uint32_t *cand_i, int64_t per_query, int32_t B, int32_t k,
+                        int64_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t st);
 void launch_query_topk(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n,
                        int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
                        float *out_scores, int32_t *out_count, cudaStream_t st);
+
+// k_query_tc.cu: tensor-core scores (3xTF32 on tcgen05) for k <= 16 and D % 32 == 0
+bool query_tc_supported(int32_t D, int32_t k);
+int32_t query_tc_splits(int32_t B, int64_t n);
+void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n, int32_t D,
+                          int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids, float *out_scores,
+                          int32_t *out_count, uint32_t *err, cudaStream_t st);
 
 }  // namespace slag
