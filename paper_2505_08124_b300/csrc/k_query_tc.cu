@@ -2,18 +2,19 @@
 // inference": score_k = q . E_k / |E_k|, top-k by descending score, ties to
 // the lower Gaussian index).
 //
-// A CTA scores 256 queries x 256 Gaussians per tile as two tcgen05.mma
-// accumulators of M = 128 TMEM lanes (queries) x N = 256 TMEM columns
-// (Gaussians), fp32, over K = D in chunks of 16. Float32 accuracy comes from
+// A CTA scores 256 queries x 128 Gaussians per tile as two tcgen05.mma
+// accumulators of M = 128 TMEM lanes (queries) x N = 128 TMEM columns
+// (Gaussians), fp32, over K = D in chunks of 32. Float32 accuracy comes from
 // the three-term TF32 split x = hi + lo (hi = x rounded to TF32, lo = the
 // rest rounded to TF32): q.e ~ q_hi.e_hi + q_hi.e_lo + q_lo.e_hi, so each
-// chunk issues 2 accumulators x 2 K-steps x 3 MMAs of K = 8. The CTA's 512
-// threads stage operands into shared memory in the canonical no-swizzle
-// K-major layout (core matrices of 8 rows x 16 bytes; K-adjacent core
-// matrices 128 bytes apart, 8-row groups 512 bytes apart), three stages deep
+// chunk issues 2 accumulators x 4 K-steps x 3 MMAs of K = 8. The CTA's 512
+// threads stage operands into shared memory in the 128-byte-swizzled K-major
+// layout (atoms of 8 rows x 128 bytes = 32 TF32 values per row, the 16-byte
+// chunk c of row r stored at chunk c ^ (r mod 8), atoms 1024 bytes apart; a
+// K-step of 8 advances the descriptor start by 32 bytes), two stages deep
 // against the MMAs (mbarriers), with the next chunk's global loads in flight
 // while the current one is converted. After a tile's last chunk, the first 8
-// warps read one query's 256 scores each from TMEM (tcgen05.ld 32x32b),
+// warps read one query's 128 scores each from TMEM (tcgen05.ld 32x32b),
 // scale them by 1/|E_k| and keep a running top-16 in registers. A grid of
 // (query tiles x Gaussian splits) writes per-split candidates that the merge
 // kernel of k_query.cu reduces to the final top-k.
@@ -28,18 +29,18 @@ namespace {
 
 constexpr int kM = 256;          // queries per CTA tile: two accumulators of 128 TMEM lanes
 constexpr int kMmaM = 128;       // M of one MMA (TMEM lanes of one accumulator)
-constexpr int kN = 256;          // Gaussians per tile (TMEM columns of one accumulator)
-constexpr int kKC = 16;          // K per staged chunk
-constexpr int kStages = 3;
+constexpr int kN = 128;          // Gaussians per tile (TMEM columns of one accumulator)
+constexpr int kKC = 32;          // K per staged chunk: one 128-byte swizzle atom row of TF32
+constexpr int kStages = 2;
 constexpr int kThreadsTC = 512;
 constexpr int kTopTC = 16;       // running top-k kept per query
-constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kTmemCols = 256;
 
 // byte sizes of one stage
-constexpr int kABytes = kM * kKC * 4;   // 16 KB
+constexpr int kABytes = kM * kKC * 4;   // 32 KB
 constexpr int kBBytes = kN * kKC * 4;   // 16 KB
 constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr int kSBO = (kKC / 4) * 128;   // bytes between 8-row groups
+constexpr int kSBO = 1024;              // bytes between 8-row swizzle atoms
 constexpr int kLoadsPerThread = (kM + kN) * (kKC / 4) / kThreadsTC;   // float4 per thread per chunk
 
 struct __align__(8) TcCtl {
@@ -90,20 +91,24 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-// Shared-memory matrix descriptor: no swizzle, K-major canonical layout.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle (layout type 2),
+// atoms 1024-byte aligned (base offset 0); the leading offset is unused for
+// swizzled K-major operands and set to 16 bytes.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;   // descriptor version of the 5th-generation tensor cores
-    return d;                 // base offset 0, layout type 0 (no swizzle)
+    d |= (uint64_t)2 << 61;   // 128-byte swizzle
+    return d;
 }
 
-// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, N = 256, M = 128.
+// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, N = kN, M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kMmaM >> 4) << 24);
 static_assert(kMmaM == 128 && kN % 16 == 0 && kN <= 256, "cta_group::1 tf32 MMA shape");
+static_assert(kKC * 4 == 128, "a chunk row is one 128-byte swizzle row");
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
     asm volatile(
@@ -141,9 +146,9 @@ __device__ __forceinline__ bool better(float s, uint32_t i, float s2, uint32_t i
     return s > s2 || (s == s2 && i < i2);
 }
 
-// Byte offset of element (row, 4-element group kq) of a [rows x kKC] K-major tile.
+// Byte offset of the 16-byte chunk kq (4 TF32 values) of a row in a 128-byte-swizzled K-major tile.
 __device__ __forceinline__ uint32_t core_off(int row, int kq) {
-    return (uint32_t)(((row >> 3) * (kKC / 4) + kq) * 128 + (row & 7) * 16);
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((kq ^ (row & 7)) << 4));
 }
 
 __device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo, uint32_t off, float4 v) {
@@ -154,6 +159,20 @@ __device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo
     h.w = to_tf32(v.w); l.w = to_tf32(v.w - h.w);
     *reinterpret_cast<float4 *>(hi + off) = h;
     *reinterpret_cast<float4 *>(lo + off) = l;
+}
+
+// v[j] for a lane-varying j, by a binary tree of selects (no local memory)
+__device__ __forceinline__ float select32(const float (&v)[32], int j) {
+    float a[16], b[8], c[4], d[2];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) a[t] = (j & 1) ? v[2 * t + 1] : v[2 * t];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) b[t] = (j & 2) ? a[2 * t + 1] : a[2 * t];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) c[t] = (j & 4) ? b[2 * t + 1] : b[2 * t];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) d[t] = (j & 8) ? c[2 * t + 1] : c[2 * t];
+    return (j & 16) ? d[1] : d[0];
 }
 
 __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restrict__ Q, int32_t B,
@@ -200,6 +219,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
         bs[i] = -INFINITY;
         bi[i] = 0xffffffffu;
     }
+    // Running threshold: the split's k-th best score so far. Columns arrive in
+    // increasing Gaussian index, so a score equal to the k-th best never ranks
+    // above it and the test is strict. Rows past the last query take none.
+    const int kk = k < kTopTC ? k : kTopTC;
+    float thr_run = -INFINITY;
+    if (warp < 8 && q0 + (warp >> 2) * 128 + (warp & 3) * 32 + lane >= B) thr_run = INFINITY;
 
     // this thread's share of a chunk: kLoadsPerThread float4, A rows first then B rows
     auto fetch = [&](int64_t gc, float4 (&v)[kLoadsPerThread]) {
@@ -208,8 +233,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
         const int64_t g0 = t * kN;
 #pragma unroll
         for (int j = 0; j < kLoadsPerThread; ++j) {
-            const int i = tid + j * kThreadsTC;          // 0 .. (kM + kN) * 4
-            const int row = i >> 2, kq = i & 3;
+            const int i = tid + j * kThreadsTC;          // 0 .. (kM + kN) * 8
+            const int row = i >> 3, kq = i & 7;
             v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (row < kM) {
                 if (q0 + row < B) v[j] = __ldg(reinterpret_cast<const float4 *>(Q + (int64_t)(q0 + row) * D + d0 + kq * 4));
@@ -239,7 +264,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
 #pragma unroll
         for (int j = 0; j < kLoadsPerThread; ++j) {
             const int i = tid + j * kThreadsTC;
-            const int row = i >> 2, kq = i & 3;
+            const int row = i >> 3, kq = i & 7;
             if (row < kM) split_store(A_hi, A_lo, core_off(row, kq), pf[j]);
             else split_store(B_hi, B_lo, core_off(row - kM, kq), pf[j]);
         }
@@ -253,12 +278,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t ah = a_hi + h * 16 * kSBO, al = a_lo + h * 16 * kSBO;   // rows 128h..
-                const uint32_t dt = tmem + (uint32_t)(h * kN);                         // columns 256h..
+                const uint32_t dt = tmem + (uint32_t)(h * kN);                         // columns 128h..
 #pragma unroll
                 for (int s2 = 0; s2 < kKC / 8; ++s2) {
-                    const uint32_t ko = s2 * 256;   // two core matrices of K = 4 per MMA of K = 8
-                    const uint64_t dah = smem_desc(ah + ko, 128, kSBO), dal = smem_desc(al + ko, 128, kSBO);
-                    const uint64_t dbh = smem_desc(b_hi + ko, 128, kSBO), dbl = smem_desc(b_lo + ko, 128, kSBO);
+                    const uint32_t ko = s2 * 32;    // K = 8 TF32 = 32 bytes along the swizzled row
+                    const uint64_t dah = smem_desc(ah + ko), dal = smem_desc(al + ko);
+                    const uint64_t dbh = smem_desc(b_hi + ko), dbl = smem_desc(b_lo + ko);
                     mma_tf32(dt, dah, dbh, (c > 0 || s2 > 0) ? 1u : 0u);
                     mma_tf32(dt, dah, dbl, 1u);
                     mma_tf32(dt, dal, dbh, 1u);
@@ -274,7 +299,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
         const int64_t g0 = (t_begin + gc / nchunk) * kN;
         for (int i = tid; i < kN; i += kThreadsTC) {
             const int64_t g = g0 + i;
-            sinv[i] = g < n ? inv_norm[g] : 0.f;
+            const float inv = g < n ? inv_norm[g] : 0.f;
+            sinv[i] = inv > 0.f ? inv : __int_as_float(0x7fc00000);   // NaN: never passes a threshold
         }
         __syncthreads();
         if (warp < 8) {
@@ -283,26 +309,37 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
             for (int cb = 0; cb < kN; cb += 32) {
                 float v[32];
                 tmem_ld32(base + (uint32_t)cb, v);
+                uint32_t mask = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float inv = sinv[cb + j];
-                    if (inv > 0.f) {
-                        float sc = v[j] * inv;
-                        uint32_t gi = (uint32_t)(g0 + cb + j);
-                        if (better(sc, gi, bs[kTopTC - 1], bi[kTopTC - 1])) {
-#pragma unroll
-                            for (int p = 0; p < kTopTC; ++p) {
-                                if (better(sc, gi, bs[p], bi[p])) {
-                                    const float ts = bs[p];
-                                    const uint32_t ti = bi[p];
-                                    bs[p] = sc;
-                                    bi[p] = gi;
-                                    sc = ts;
-                                    gi = ti;
-                                }
-                            }
-                        }
+                    v[j] *= sinv[cb + j];
+                    mask |= (v[j] > thr_run ? 1u : 0u) << j;
+                }
+                // candidates at or above the running threshold, one per lane per round, so that
+                // the lanes of the warp insert together
+                while (__any_sync(0xffffffffu, mask != 0u)) {
+                    float sc = -INFINITY;
+                    uint32_t gi = 0xffffffffu;
+                    if (mask) {
+                        const int j = __ffs(mask) - 1;
+                        mask &= mask - 1u;
+                        sc = select32(v, j);
+                        gi = (uint32_t)(g0 + cb + j);
                     }
+#pragma unroll
+                    for (int p = 0; p < kTopTC; ++p) {
+                        const bool b = better(sc, gi, bs[p], bi[p]);
+                        const float ts = b ? bs[p] : sc;
+                        const uint32_t ti = b ? bi[p] : gi;
+                        bs[p] = b ? sc : bs[p];
+                        bi[p] = b ? gi : bi[p];
+                        sc = ts;
+                        gi = ti;
+                    }
+                    float kth = bs[0];
+#pragma unroll
+                    for (int p = 1; p < kTopTC; ++p) kth = p == kk - 1 ? bs[p] : kth;
+                    thr_run = kth;
                 }
             }
         }
@@ -322,7 +359,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
     if (warp < 8) {
         const int q = q0 + (warp >> 2) * 128 + (warp & 3) * 32 + lane;
         if (q < B) {
-            const int kk = k < kTopTC ? k : kTopTC;
             float *cs = cand_s + ((int64_t)q * nsplit + split) * kk;
             uint32_t *ci = cand_i + ((int64_t)q * nsplit + split) * kk;
 #pragma unroll

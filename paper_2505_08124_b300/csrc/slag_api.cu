@@ -643,8 +643,8 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
     }
     span_begin(ctx, SLAG_STAGE_QUERY);
     if (tc)
-        launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i, ids, scores,
-                             cnt, ctx->tc_err, st);
+        launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i,
+                             ids, scores, cnt, ctx->tc_err, st);
     else
         launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i, ids, scores,
                           cnt, st);
