@@ -40,8 +40,12 @@ __global__ void __launch_bounds__(256) consume_k(HashEntry *__restrict__ hash, i
                                                  float *__restrict__ s_hi, float *__restrict__ s_lo,
                                                  unsigned long long *log_count, unsigned long long log_cap,
                                                  uint64_t *__restrict__ log_key, float *__restrict__ log_w,
-                                                 uint32_t *overflow_flag) {
+                                                 uint32_t *overflow_flag,
+                                                 const unsigned long long *__restrict__ view_contrib,
+                                                 unsigned long long *total_contrib) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the view's composited pairs join the running total (the view's composite has finished)
+    if (g == 0 && view_contrib) atomicAdd(total_contrib, *view_contrib);
     const int lane = threadIdx.x & 31;
     HashEntry e;
     int cnt = 0;
@@ -224,9 +228,10 @@ void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st) {
 
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
                     unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key, float *log_w,
-                    uint32_t *overflow, cudaStream_t st) {
+                    uint32_t *overflow, const unsigned long long *view_contrib, unsigned long long *total_contrib,
+                    cudaStream_t st) {
     consume_k<<<blocks_for(n, 256), 256, 0, st>>>(hash, n, view_base, s_hi, s_lo, log_count, log_cap, log_key,
-                                                  log_w, overflow);
+                                                  log_w, overflow, view_contrib, total_contrib);
 }
 
 void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaStream_t st) {

@@ -3,10 +3,19 @@
 // slag_add_view (Method, "Semantic Embedding": Rasterization, Parameter
 // Masking, the view's share of Aggregation):
 //   project -> depth sort (stable, caller index breaks ties) -> gather records
-//   in depth-rank order -> scan tile counts -> [one stream sync: read the pair
-//   count P and the error flags] -> emit (tile, rank) pairs -> stable sort by
-//   tile -> tile ranges -> composite + mask + in-tile segment binning ->
+//   in depth-rank order -> scan tile counts -> [host waits for this part only:
+//   the pair count P and the error flags] -> emit (bin, rank) pairs -> stable
+//   sort by bin -> bin ranges -> composite + mask + in-tile segment binning ->
 //   consume the per-view (segment, weight) tables into the triple log.
+//
+// Views are pipelined over kSlots sets of per-view buffers. The front half
+// (projection through binning) runs on one high-priority internal stream, the
+// back half (composite, consume) on the slot's own stream, so that the next
+// view's front half and the start of its composite fill the SMs that a
+// composite's last, longest tiles leave idle. Consumes keep view order (they
+// update the compensated per-Gaussian sums without atomics) through an event
+// chain. Every entry point that reads results or reuses buffers first makes
+// the caller's stream wait for all views in flight.
 // slag_finalize (Aggregation, E_k formula): sort the log by
 //   (block, column, Gaussian) -> distinct columns per block -> blocked
 //   contraction with the stored segment embeddings -> divide by sum w.
@@ -22,6 +31,44 @@
 
 using namespace slag;
 
+namespace {
+
+constexpr int kSlots = 2;   // views in flight
+
+// Buffers of one view in flight. The front stream fills them; the slot's back
+// stream composites from them; the front stream reuses them for the view
+// kSlots later once ev_done has fired.
+struct ViewSlot {
+    // n-sized
+    uint32_t *dkey[2] = {nullptr, nullptr}, *dval[2] = {nullptr, nullptr};
+    float4 *rec_a = nullptr, *rec_b = nullptr, *srec_a = nullptr, *srec_b = nullptr;
+    uint2 *rect = nullptr, *srect = nullptr;
+    uint32_t *stouched = nullptr, *offsets = nullptr;
+    HashEntry *hash = nullptr;             // per-view (segment, weight) slots; consume clears them
+    // pair-, bin- and image-sized
+    uint32_t *pkey[2] = {nullptr, nullptr}, *pval[2] = {nullptr, nullptr};
+    int64_t p_cap = 0;
+    uint2 *prect = nullptr;
+    int64_t prect_cap = 0;
+    uint2 *ranges = nullptr;
+    int64_t ranges_cap = 0;
+    uint32_t *tile_order = nullptr;
+    int64_t order_cap = 0;
+    int32_t *seg_buf = nullptr;            // the view's segment map (always copied: the caller's buffer
+    int64_t seg_cap = 0;                   // is free once slag_add_view returns)
+    ViewCounters *ctr = nullptr;           // device
+    struct Host {
+        ViewCounters v;
+        unsigned long long totals[4];
+    } *h = nullptr;                        // pinned host copy read at the front sync
+    cudaStream_t back = nullptr;
+    cudaEvent_t ev_bin = nullptr;          // front work of the slot's view done
+    cudaEvent_t ev_done = nullptr;         // back work of the slot's view done
+    int64_t log_bound = 0;                 // triples the slot's view may append after its front sync
+};
+
+}  // namespace
+
 struct slag_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -35,43 +82,30 @@ struct slag_ctx {
     float2 *cov_b = nullptr;
     uint32_t *orig_of_int = nullptr, *int_of_orig = nullptr;
 
-    // per-view, n-sized
-    uint32_t *dkey[2] = {nullptr, nullptr}, *dval[2] = {nullptr, nullptr};
-    float4 *rec_a = nullptr, *rec_b = nullptr, *srec_a = nullptr, *srec_b = nullptr;
-    uint2 *rect = nullptr, *srect = nullptr;
-    uint32_t *stouched = nullptr, *offsets = nullptr;
-    HashEntry *hash = nullptr;
+    // views in flight
+    ViewSlot slot[kSlots];
+    cudaStream_t front = nullptr;            // projection through binning of every view
+    cudaEvent_t ev_in = nullptr;             // caller's stream at the start of a call
+    cudaEvent_t ev_front = nullptr;          // front stream after a view's front work
+    cudaEvent_t ev_consumed = nullptr;       // the last enqueued consume
+    int64_t views_enqueued = 0;              // views since create / reset (slot = count % kSlots)
     float *s_hi = nullptr, *s_lo = nullptr, *s_ovf = nullptr;
-
-    // per-view, P-sized and image-sized
-    uint32_t *pkey[2] = {nullptr, nullptr}, *pval[2] = {nullptr, nullptr};
-    int64_t p_cap = 0;
-    uint2 *prect = nullptr;
-    int64_t prect_cap = 0;
-    uint2 *ranges = nullptr;
-    int64_t ranges_cap = 0;
-    uint32_t *tile_order = nullptr;
-    int64_t order_cap = 0;
-    int32_t *seg_buf = nullptr;
-    int64_t seg_cap = 0;
     float *dbg_T = nullptr, *dbg_wsum = nullptr;
     int32_t *dbg_count = nullptr;
     int64_t dbg_cap = 0;
 
-    ViewCounters *ctr = nullptr;             // device, reset per view
     unsigned long long *totals = nullptr;    // device: [0] triples in the log, [1] contributions,
                                              // [2] low word: log overflow flag, [3] evaluations
     unsigned long long *log_count = nullptr; // = totals
     unsigned long long *contrib = nullptr;   // = totals + 1
     struct HostCounters {
-        ViewCounters v;
+        ViewCounters v;                      // validation at create, the last view at finalize
         unsigned long long totals[4];
         unsigned long long touched;
         uint32_t tc_err;
         uint32_t pad;
     } *hc = nullptr;                         // pinned host
     uint32_t *tc_err = nullptr;              // device: a tensor-core query kernel gave up waiting
-    unsigned long long contrib_before_last = 0;
 
     // triple log + finalize scratch
     uint64_t *log_key = nullptr, *log_key_alt = nullptr;
@@ -210,22 +244,30 @@ cudaEvent_t take_event(slag_ctx *ctx) {
     return e;
 }
 
-// Opens a timing span of `stage` in the context's stream (no-op when profiling is off).
-void span_begin(slag_ctx *ctx, int stage) {
+// Opens a timing span of `stage` in stream `st` (no-op when profiling is off).
+// Spans of views in flight overlap, so stage totals add device time per
+// stream, not wall time.
+void span_begin(slag_ctx *ctx, int stage, cudaStream_t st) {
     if (!ctx->prof_on) return;
     slag_ctx::Span sp{stage, take_event(ctx), take_event(ctx)};
-    cudaEventRecord(sp.a, ctx->stream);
+    cudaEventRecord(sp.a, st);
     ctx->spans.push_back(sp);
 }
 
-void span_end(slag_ctx *ctx) {
+void span_end(slag_ctx *ctx, cudaStream_t st) {
     if (!ctx->prof_on || ctx->spans.empty()) return;
-    cudaEventRecord(ctx->spans.back().b, ctx->stream);
+    cudaEventRecord(ctx->spans.back().b, st);
 }
 
-// Adds every finished span to the totals (call after a stream synchronisation).
+// Adds every finished span to the totals; spans still in flight stay.
 void spans_resolve(slag_ctx *ctx) {
-    for (auto &sp : ctx->spans) {
+    size_t keep = 0;
+    for (size_t i = 0; i < ctx->spans.size(); ++i) {
+        auto &sp = ctx->spans[i];
+        if (cudaEventQuery(sp.b) != cudaSuccess) {
+            ctx->spans[keep++] = sp;
+            continue;
+        }
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
             ctx->prof.ms[sp.stage] += ms;
@@ -234,7 +276,23 @@ void spans_resolve(slag_ctx *ctx) {
         ctx->event_pool.push_back(sp.a);
         ctx->event_pool.push_back(sp.b);
     }
-    ctx->spans.clear();
+    ctx->spans.resize(keep);
+    (void)cudaGetLastError();   // clears cudaErrorNotReady left by the queries
+}
+
+// The caller's stream waits for every view in flight and for the front stream.
+cudaError_t join_views(slag_ctx *ctx) {
+    cudaError_t e = cudaEventRecord(ctx->ev_front, ctx->front);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_front, 0);
+    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->stream, ctx->slot[i].ev_done, 0);
+    return e;
+}
+
+// Host waits for every internal stream (the caller's stream is not waited for).
+cudaError_t drain_views(slag_ctx *ctx) {
+    cudaError_t e = cudaStreamSynchronize(ctx->front);
+    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaStreamSynchronize(ctx->slot[i].back);
+    return e;
 }
 
 int ceil_log2(uint64_t v) {
@@ -243,81 +301,115 @@ int ceil_log2(uint64_t v) {
     return b;
 }
 
-// Projection through the tile ranges of one view: leaves the depth-sorted
-// records, the tile-sorted pair list and ranges in the workspace; returns the
-// pair count in *P_out and the list buffer in *list_out.
-slag_status bin_view(slag_ctx *ctx, const CamParams &cp, int64_t *P_out, uint32_t **keys_out,
-                     uint32_t **list_out, const int32_t *seg_check, int32_t M, const uint32_t **sgid_out,
-                     int shift) {
-    cudaStream_t st = ctx->stream;
+// Projection through the bin ranges of one view, into slot `vs` on stream
+// `st`: leaves the depth-sorted records, the bin-sorted pair list and ranges
+// in the slot; returns the pair count in *P_out and the list buffer in
+// *list_out. The host waits for `st` once (pair count, error flags) and
+// copies the log's fill level of that moment into vs.h->totals.
+slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int64_t *P_out,
+                     uint32_t **keys_out, uint32_t **list_out, const int32_t *seg_check, int32_t M,
+                     const uint32_t **sgid_out, int shift) {
     const int64_t n = ctx->n;
-    CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
-    span_begin(ctx, SLAG_STAGE_PROJECT);
-    if (seg_check) launch_check_seg(seg_check, (int64_t)cp.width * cp.height, M, ctx->ctr, st);
-    launch_project(cp, ctx->mean_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, ctx->dkey[0], ctx->dval[0],
-                   ctx->rec_a, ctx->rec_b, ctx->rect, ctx->ctr, st);
+    CK(cudaMemsetAsync(vs.ctr, 0, sizeof(ViewCounters), st));
+    span_begin(ctx, SLAG_STAGE_PROJECT, st);
+    if (seg_check) launch_check_seg(seg_check, (int64_t)cp.width * cp.height, M, vs.ctr, st);
+    launch_project(cp, ctx->mean_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, vs.dkey[0], vs.dval[0],
+                   vs.rec_a, vs.rec_b, vs.rect, vs.ctr, st);
     int shifts[8], widths[8];
     int np = digit_passes(0, 32, shifts, widths, n);
-    bool alt = radix_sort_u32(ctx->dkey[0], ctx->dkey[1], ctx->dval[0], ctx->dval[1], n, shifts, widths, np,
+    bool alt = radix_sort_u32(vs.dkey[0], vs.dkey[1], vs.dval[0], vs.dval[1], n, shifts, widths, np,
                               ctx->scratch, st);
-    const uint32_t *sorted_vals = ctx->dval[alt ? 1 : 0];
+    const uint32_t *sorted_vals = vs.dval[alt ? 1 : 0];
     *sgid_out = sorted_vals;
-    launch_gather_sorted(sorted_vals, n, ctx->ctr, ctx->rec_a, ctx->rec_b, ctx->rect, ctx->srec_a, ctx->srec_b,
-                         ctx->srect, ctx->stouched, shift, st);
-    exclusive_scan_u32(ctx->stouched, ctx->offsets, n, &ctx->ctr->P, ctx->scratch, st);
-    span_end(ctx);
-    CK(cudaMemcpyAsync(&ctx->hc->v, ctx->ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ctx->hc->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    launch_gather_sorted(sorted_vals, n, vs.ctr, vs.rec_a, vs.rec_b, vs.rect, vs.srec_a, vs.srec_b,
+                         vs.srect, vs.stouched, shift, st);
+    exclusive_scan_u32(vs.stouched, vs.offsets, n, &vs.ctr->P, ctx->scratch, st);
+    span_end(ctx, st);
+    CK(cudaMemcpyAsync(&vs.h->v, vs.ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(vs.h->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     spans_resolve(ctx);
-    if (ctx->hc->v.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
-    const int64_t P = (int64_t)ctx->hc->v.P;   // pairs at the binning granularity
-    if (P > 0x7fffffffLL || ctx->hc->v.P_tiles > 0x7fffffffULL)
+    if (vs.h->v.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
+    const int64_t P = (int64_t)vs.h->v.P;   // pairs at the binning granularity
+    if (P > 0x7fffffffLL || vs.h->v.P_tiles > 0x7fffffffULL)
         return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^31-1 Gaussian-tile pairs in one view");
-    if (P > ctx->p_cap) {
-        int64_t cap = ctx->p_cap;
+    if (P > vs.p_cap) {
+        int64_t cap = vs.p_cap;
         for (int b = 0; b < 2; ++b) {
             int64_t c1 = cap, c2 = cap;
-            CK(grow(ctx->pkey[b], c1, P, st));
-            CK(grow(ctx->pval[b], c2, P, st));
-            ctx->p_cap = c1;
+            CK(grow(vs.pkey[b], c1, P, st));
+            CK(grow(vs.pval[b], c2, P, st));
+            vs.p_cap = c1;
         }
-        CK(scratch_reserve(ctx->scratch, ctx->p_cap));
+        CK(scratch_reserve(ctx->scratch, vs.p_cap));
     }
     const int bins_x = ((cp.tiles_x - 1) >> shift) + 1, bins_y = ((cp.tiles_y - 1) >> shift) + 1;
     const int64_t bins = (int64_t)bins_x * bins_y;
     const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
-    CK(grow(ctx->ranges, ctx->ranges_cap, bins, st));
-    uint32_t nv = ctx->hc->v.n_visible;
-    span_begin(ctx, SLAG_STAGE_BIN);
-    launch_emit(ctx->srect, ctx->offsets, nv, shift, bins_x, ctx->pkey[0], ctx->pval[0], st);
+    CK(grow(vs.ranges, vs.ranges_cap, bins, st));
+    uint32_t nv = vs.h->v.n_visible;
+    span_begin(ctx, SLAG_STAGE_BIN, st);
+    launch_emit(vs.srect, vs.offsets, nv, shift, bins_x, vs.pkey[0], vs.pval[0], st);
     np = digit_passes(0, ceil_log2((uint64_t)bins), shifts, widths, P);
-    uint32_t *keys = ctx->pkey[0];
+    uint32_t *keys = vs.pkey[0];
     alt = false;
     if (P > 0 && np == 1) {
         // one pass: its digit is the bin id, and the pass's offsets give the ranges
-        alt = radix_sort_u32(ctx->pkey[0], ctx->pkey[1], ctx->pval[0], ctx->pval[1], P, shifts, widths, np,
-                             ctx->scratch, st, ctx->ranges, (int)bins);
-        keys = ctx->pkey[alt ? 1 : 0];
+        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np,
+                             ctx->scratch, st, vs.ranges, (int)bins);
+        keys = vs.pkey[alt ? 1 : 0];
     } else {
-        CK(cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)bins, st));
-        alt = radix_sort_u32(ctx->pkey[0], ctx->pkey[1], ctx->pval[0], ctx->pval[1], P, shifts, widths, np,
+        CK(cudaMemsetAsync(vs.ranges, 0, sizeof(uint2) * (size_t)bins, st));
+        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np,
                              ctx->scratch, st);
-        keys = ctx->pkey[alt ? 1 : 0];
-        launch_ranges(keys, P, ctx->ranges, st);
+        keys = vs.pkey[alt ? 1 : 0];
+        launch_ranges(keys, P, vs.ranges, st);
     }
-    CK(grow(ctx->tile_order, ctx->order_cap, tiles, st));
-    launch_tile_order(ctx->ranges, cp.tiles_x, cp.tiles_y, shift, ctx->tile_order, st);
+    CK(grow(vs.tile_order, vs.order_cap, tiles, st));
+    launch_tile_order(vs.ranges, cp.tiles_x, cp.tiles_y, shift, vs.tile_order, st);
     if (shift > 0) {
-        CK(grow(ctx->prect, ctx->prect_cap, P, st));
-        launch_pair_rects(ctx->pval[alt ? 1 : 0], P, ctx->srect, ctx->prect, st);
+        CK(grow(vs.prect, vs.prect_cap, P, st));
+        launch_pair_rects(vs.pval[alt ? 1 : 0], P, vs.srect, vs.prect, st);
     }
-    span_end(ctx);
+    span_end(ctx, st);
     *P_out = P;
     *keys_out = keys;
-    *list_out = ctx->pval[alt ? 1 : 0];
+    *list_out = vs.pval[alt ? 1 : 0];
     return SLAG_OK;
+}
+
+cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
+    cudaError_t e = cudaSuccess;
+#define SA(call) do { if (e == cudaSuccess) e = (call); } while (0)
+    for (int b = 0; b < 2; ++b) { SA(dalloc(&vs.dkey[b], n)); SA(dalloc(&vs.dval[b], n)); }
+    SA(dalloc(&vs.rec_a, n)); SA(dalloc(&vs.rec_b, n)); SA(dalloc(&vs.srec_a, n)); SA(dalloc(&vs.srec_b, n));
+    SA(dalloc(&vs.rect, n)); SA(dalloc(&vs.srect, n));
+    SA(dalloc(&vs.stouched, n)); SA(dalloc(&vs.offsets, n));
+    SA(dalloc(&vs.hash, n));
+    SA(dalloc(&vs.ctr, 1));
+    SA(cudaMallocHost((void **)&vs.h, sizeof(ViewSlot::Host)));
+    int lo = 0, hi = 0;
+    SA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    SA(cudaStreamCreateWithPriority(&vs.back, cudaStreamNonBlocking, lo));
+    SA(cudaEventCreateWithFlags(&vs.ev_bin, cudaEventDisableTiming));
+    SA(cudaEventCreateWithFlags(&vs.ev_done, cudaEventDisableTiming));
+#undef SA
+    if (e == cudaSuccess && vs.h) memset(vs.h, 0, sizeof(ViewSlot::Host));
+    return e;
+}
+
+void slot_free(ViewSlot &vs) {
+    for (int b = 0; b < 2; ++b) { dfree(vs.dkey[b]); dfree(vs.dval[b]); dfree(vs.pkey[b]); dfree(vs.pval[b]); }
+    dfree(vs.rec_a); dfree(vs.rec_b); dfree(vs.srec_a); dfree(vs.srec_b); dfree(vs.rect); dfree(vs.srect);
+    dfree(vs.stouched); dfree(vs.offsets); dfree(vs.hash);
+    dfree(vs.prect); dfree(vs.ranges); dfree(vs.tile_order); dfree(vs.seg_buf); dfree(vs.ctr);
+    if (vs.h) cudaFreeHost(vs.h);
+    vs.h = nullptr;
+    if (vs.back) cudaStreamDestroy(vs.back);
+    if (vs.ev_bin) cudaEventDestroy(vs.ev_bin);
+    if (vs.ev_done) cudaEventDestroy(vs.ev_done);
+    vs.back = nullptr; vs.ev_bin = vs.ev_done = nullptr;
 }
 
 }  // namespace
@@ -371,49 +463,53 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
         im = dm; is = ds; iq = dq; io = dop;
     }
     CA(cudaMallocHost((void **)&ctx->hc, sizeof(slag_ctx::HostCounters)));
-    CA(dalloc(&ctx->ctr, 1));
+    for (int i = 0; i < kSlots; ++i) CA(slot_alloc(ctx->slot[i], n));
+    {
+        int lo = 0, hi = 0;
+        CA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CA(cudaStreamCreateWithPriority(&ctx->front, cudaStreamNonBlocking, hi));
+    }
+    CA(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+    CA(cudaEventCreateWithFlags(&ctx->ev_front, cudaEventDisableTiming));
+    CA(cudaEventCreateWithFlags(&ctx->ev_consumed, cudaEventDisableTiming));
     CA(dalloc(&ctx->totals, 4));
     ctx->log_count = ctx->totals;
     ctx->contrib = ctx->totals + 1;
     CA(dalloc(&ctx->touched, 1));
     CA(dalloc(&ctx->tc_err, 1));
+    ViewCounters *vctr = ctx->slot[0].ctr;
     CA(cudaMemsetAsync(ctx->tc_err, 0, sizeof(uint32_t), st));
-    CA(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
+    CA(cudaMemsetAsync(vctr, 0, sizeof(ViewCounters), st));
     CA(cudaMemsetAsync(ctx->totals, 0, 4 * sizeof(unsigned long long), st));
     CA(scratch_reserve(ctx->scratch, n));
 
     // validation
-    launch_check_gaussians(im, is, iq, io, n, &ctx->ctr->bad_seg, st);
-    CA(cudaMemcpyAsync(&ctx->hc->v, ctx->ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
+    launch_check_gaussians(im, is, iq, io, n, &vctr->bad_seg, st);
+    CA(cudaMemcpyAsync(&ctx->hc->v, vctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
     CA(cudaStreamSynchronize(st));
     CA(cudaGetLastError());
     if (ctx->hc->v.bad_seg) return bail(SLAG_ERR_INVALID_ARG);
 
     // Morton order
     CA(dalloc(&ctx->orig_of_int, n)); CA(dalloc(&ctx->int_of_orig, n));
-    for (int b = 0; b < 2; ++b) { CA(dalloc(&ctx->dkey[b], n)); CA(dalloc(&ctx->dval[b], n)); }
-    CA(dalloc(&ctx->stouched, n));
-    CA(dalloc(&ctx->offsets, n));
     CA(dalloc(&bb, 6));
+    ViewSlot &s0 = ctx->slot[0];
     launch_bbox(im, n, bb, st);
-    launch_morton(im, n, bb, ctx->dkey[0], ctx->dval[0], st);
+    launch_morton(im, n, bb, s0.dkey[0], s0.dval[0], st);
     int shifts[8], widths[8];
     int np = digit_passes(0, 30, shifts, widths, n);
-    bool alt = radix_sort_u32(ctx->dkey[0], ctx->dkey[1], ctx->dval[0], ctx->dval[1], n, shifts, widths, np,
+    bool alt = radix_sort_u32(s0.dkey[0], s0.dkey[1], s0.dval[0], s0.dval[1], n, shifts, widths, np,
                               ctx->scratch, st);
-    CA(cudaMemcpyAsync(ctx->orig_of_int, ctx->dval[alt ? 1 : 0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+    CA(cudaMemcpyAsync(ctx->orig_of_int, s0.dval[alt ? 1 : 0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
     CA(dalloc(&ctx->mean_op, n)); CA(dalloc(&ctx->cov_a, n)); CA(dalloc(&ctx->cov_b, n));
     launch_pack_gaussians(im, is, iq, io, n, ctx->orig_of_int, ctx->mean_op, ctx->cov_a, ctx->cov_b,
                           ctx->int_of_orig, st);
 
-    // per-view workspace
-    CA(dalloc(&ctx->rec_a, n)); CA(dalloc(&ctx->rec_b, n)); CA(dalloc(&ctx->srec_a, n)); CA(dalloc(&ctx->srec_b, n));
-    CA(dalloc(&ctx->rect, n)); CA(dalloc(&ctx->srect, n));
-    CA(dalloc(&ctx->hash, n));
+    // accumulators and outputs
     CA(dalloc(&ctx->s_hi, n)); CA(dalloc(&ctx->s_lo, n)); CA(dalloc(&ctx->s_ovf, n));
     CA(dalloc(&ctx->E, n * (int64_t)ctx->D)); CA(dalloc(&ctx->inv_norm, n)); CA(dalloc(&ctx->wsum, n));
     CA(dalloc(&ctx->bstart, (n + kBlockG - 1) / kBlockG)); CA(dalloc(&ctx->bend, (n + kBlockG - 1) / kBlockG));
-    launch_hash_init(ctx->hash, n, st);
+    for (int i = 0; i < kSlots; ++i) launch_hash_init(ctx->slot[i].hash, n, st);
     CA(cudaMemsetAsync(ctx->s_hi, 0, sizeof(float) * n, st));
     CA(cudaMemsetAsync(ctx->s_lo, 0, sizeof(float) * n, st));
     CA(cudaMemsetAsync(ctx->s_ovf, 0, sizeof(float) * n, st));
@@ -434,78 +530,110 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     if (M < 1 || M >= (1 << 24)) return fail(ctx, SLAG_ERR_INVALID_ARG, "M outside [1, 2^24)");
     if (ctx->table_rows + M >= (1LL << 32)) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^32 segment columns");
     CK(cudaSetDevice(ctx->device));
-    cudaStream_t st = ctx->stream;
+    ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
+    cudaStream_t fr = ctx->front;
     const CamParams cp = cam_params(cam);
     const int64_t npx = (int64_t)cam->width * cam->height;
     const int64_t D = ctx->D;
 
-    // segment embeddings -> rows [table_rows, table_rows + M) of the column store
-    CK(grow(ctx->table, ctx->table_cap, (ctx->table_rows + M) * D, st, ctx->table_rows * D));
-    CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D),
-                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    const int32_t *seg = seg_ids;
-    if (!on_device) {
-        CK(grow(ctx->seg_buf, ctx->seg_cap, npx, st));
-        CK(cudaMemcpyAsync(ctx->seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, cudaMemcpyHostToDevice, st));
-        seg = ctx->seg_buf;
+    // the front stream starts after the caller's work so far (inputs written
+    // on the caller's stream) and after the slot's previous view has been
+    // composited and consumed
+    CK(cudaEventRecord(ctx->ev_in, ctx->stream));
+    CK(cudaStreamWaitEvent(fr, ctx->ev_in, 0));
+    CK(cudaStreamWaitEvent(fr, vs.ev_done, 0));
+
+    // segment embeddings -> rows [table_rows, table_rows + M) of the column store;
+    // the segment map -> the slot (both read on the front stream before the host
+    // sync below, so the caller's buffers are free when this call returns)
+    if (ctx->table_rows + M > ctx->table_cap / D) {
+        CK(drain_views(ctx));   // growing frees the old store
+        CK(grow(ctx->table, ctx->table_cap, (ctx->table_rows + M) * D, fr, ctx->table_rows * D));
     }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D), kind, fr));
+    if (npx > vs.seg_cap) CK(grow(vs.seg_buf, vs.seg_cap, npx, fr));
+    CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, fr));
+    const int32_t *seg = vs.seg_buf;
+
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, cp, &P, &keys, &list, seg, M, &sgid, kSuperShift);
+    s = bin_view(ctx, vs, fr, cp, &P, &keys, &list, seg, M, &sgid, kSuperShift);
     if (s != SLAG_OK) return s;
+    CK(cudaEventRecord(vs.ev_bin, fr));
 
-    // room in the triple log: at most kHashSlots per Gaussian from the consume
-    // pass plus the overflow appends of this view
-    const unsigned long long used = ctx->hc->totals[0];
-    ctx->contrib_before_last = ctx->hc->totals[1];
-    const int64_t need = (int64_t)used + ctx->n * kHashSlots + 2 * (int64_t)ctx->hc->v.P_tiles + (1 << 20);
+    // room in the triple log: its fill level at the front sync, plus what the
+    // other views in flight may still append, plus this view's bound (at most
+    // kHashSlots per Gaussian from the consume pass and the composite's
+    // overflow appends)
+    vs.log_bound = ctx->n * kHashSlots + 2 * (int64_t)vs.h->v.P_tiles + (1 << 20);
+    int64_t need = (int64_t)vs.h->totals[0] + vs.log_bound;
+    for (int i = 0; i < kSlots; ++i)
+        if (&ctx->slot[i] != &vs) need += ctx->slot[i].log_bound;
     if (need > ctx->log_cap) {
+        // no view may append while the log moves: wait for all, then read the exact fill level
+        CK(drain_views(ctx));
+        CK(cudaMemcpyAsync(vs.h->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, fr));
+        CK(cudaStreamSynchronize(fr));
+        for (int i = 0; i < kSlots; ++i)
+            if (&ctx->slot[i] != &vs) ctx->slot[i].log_bound = 0;
+        const int64_t used = (int64_t)vs.h->totals[0];
+        need = used + vs.log_bound;
         int64_t c1 = ctx->log_cap, c2 = ctx->log_cap;
-        CK(grow(ctx->log_key, c1, need, st, (int64_t)used));
-        CK(grow(ctx->log_w, c2, need, st, (int64_t)used));
+        CK(grow(ctx->log_key, c1, need, fr, used));
+        CK(grow(ctx->log_w, c2, need, fr, used));
         ctx->log_cap = c1;
     }
+
+    // back half on the slot's stream
+    cudaStream_t bk = vs.back;
+    CK(cudaStreamWaitEvent(bk, vs.ev_bin, 0));
     CompositeArgs a;
     a.cam = cp;
-    a.ranges = ctx->ranges;
+    a.ranges = vs.ranges;
     a.bin_shift = kSuperShift;
     a.bins_x = ((cp.tiles_x - 1) >> kSuperShift) + 1;
-    a.tile_order = ctx->tile_order;
+    a.tile_order = vs.tile_order;
     a.list = list;
-    a.prect = ctx->prect;
-    a.srec_a = ctx->srec_a;
-    a.srec_b = ctx->srec_b;
+    a.prect = vs.prect;
+    a.srec_a = vs.srec_a;
+    a.srec_b = vs.srec_b;
     a.sgid = sgid;
     a.seg = seg;
     a.view_base = (int32_t)ctx->table_rows;
     a.weight_mode = ctx->weight_mode;
-    a.hash = ctx->hash;
+    a.hash = vs.hash;
     a.log_count = ctx->log_count;
     a.log_cap = (unsigned long long)ctx->log_cap;
     a.log_key = ctx->log_key;
     a.log_w = ctx->log_w;
     a.s_ovf = ctx->s_ovf;
-    a.ctr = ctx->ctr;
+    a.ctr = vs.ctr;
     a.overflow = reinterpret_cast<uint32_t *>(ctx->totals + 2);
-    a.contrib = ctx->contrib;
+    a.contrib = &vs.ctr->contributions;
     a.evals = ctx->totals + 3;
     a.dbg_T = a.dbg_wsum = nullptr;
     a.dbg_count = nullptr;
     a.accumulate = 1;
-    span_begin(ctx, SLAG_STAGE_COMPOSITE);
-    launch_composite(a, st);
-    span_end(ctx);
-    span_begin(ctx, SLAG_STAGE_CONSUME);
-    launch_consume(ctx->hash, ctx->n, (int32_t)ctx->table_rows, ctx->s_hi, ctx->s_lo, ctx->log_count,
+    span_begin(ctx, SLAG_STAGE_COMPOSITE, bk);
+    launch_composite(a, bk);
+    span_end(ctx, bk);
+    // consumes in view order: the compensated sums are updated without atomics
+    CK(cudaStreamWaitEvent(bk, ctx->ev_consumed, 0));
+    span_begin(ctx, SLAG_STAGE_CONSUME, bk);
+    launch_consume(vs.hash, ctx->n, (int32_t)ctx->table_rows, ctx->s_hi, ctx->s_lo, ctx->log_count,
                    (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
-                   reinterpret_cast<uint32_t *>(ctx->totals + 2), st);
-    span_end(ctx);
+                   reinterpret_cast<uint32_t *>(ctx->totals + 2), &vs.ctr->contributions, ctx->contrib, bk);
+    span_end(ctx, bk);
+    CK(cudaEventRecord(ctx->ev_consumed, bk));
+    CK(cudaEventRecord(vs.ev_done, bk));
     CK(cudaGetLastError());
+    ctx->views_enqueued += 1;
     ctx->table_rows += M;
     ctx->stats.views += 1;
-    ctx->stats.pairs += (int64_t)ctx->hc->v.P_tiles;
-    ctx->stats.last_pairs = (int64_t)ctx->hc->v.P_tiles;
+    ctx->stats.pairs += (int64_t)vs.h->v.P_tiles;
+    ctx->stats.last_pairs = (int64_t)vs.h->v.P_tiles;
     ctx->stats.columns = ctx->table_rows;
     ctx->finalized = false;
     return SLAG_OK;
@@ -516,12 +644,15 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     if (ctx->stats.views == 0) return fail(ctx, SLAG_ERR_STATE, "finalize before any view");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
+    CK(join_views(ctx));
+    const ViewSlot &last = ctx->slot[(ctx->views_enqueued + kSlots - 1) % kSlots];
     CK(cudaMemcpyAsync(ctx->hc->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ctx->hc->v, last.ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     ctx->stats.contributions = (int64_t)ctx->hc->totals[1];
     ctx->stats.evaluations = (int64_t)ctx->hc->totals[3];
-    ctx->stats.last_contributions = (int64_t)(ctx->hc->totals[1] - ctx->contrib_before_last);
+    ctx->stats.last_contributions = (int64_t)ctx->hc->v.contributions;
     if (ctx->hc->totals[2]) ctx->log_overflowed = true;
     if (ctx->log_overflowed) return fail(ctx, SLAG_ERR_CAPACITY, "the triple log overflowed in some view");
     const int64_t Z = (int64_t)ctx->hc->totals[0];
@@ -544,7 +675,7 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
             ctx->fin_cap = c1;
             CK(scratch_reserve(ctx->scratch, Z));
         }
-        span_begin(ctx, SLAG_STAGE_LOG_SORT);
+        span_begin(ctx, SLAG_STAGE_LOG_SORT, st);
         // sort by (block, column, Gaussian): bits [0, 7 + col_bits) then [39, 39 + block_bits)
         int shifts[16], widths[16];
         int np = digit_passes(0, 7 + ceil_log2((uint64_t)ctx->table_rows), shifts, widths, Z);
@@ -563,7 +694,7 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
         launch_unique_flags(ctx->log_key, Z, ctx->flags, st);
         exclusive_scan_u32(ctx->flags, ctx->uidx, Z, nullptr, ctx->scratch, st);
         launch_uniques(ctx->log_key, ctx->flags, ctx->uidx, Z, ctx->ucol, ctx->ustart, ctx->bstart, ctx->bend, st);
-        span_end(ctx);
+        span_end(ctx, st);
     }
     AggArgs g;
     g.keys = ctx->log_key;
@@ -585,9 +716,9 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     g.inv_norm = ctx->inv_norm;
     g.wsum = ctx->wsum;
     g.touched = ctx->touched;
-    span_begin(ctx, SLAG_STAGE_AGGREGATE);
+    span_begin(ctx, SLAG_STAGE_AGGREGATE, st);
     launch_aggregate(g, nblocks, st);
-    span_end(ctx);
+    span_end(ctx, st);
     CK(cudaGetLastError());
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (out_emb) CK(cudaMemcpyAsync(out_emb, ctx->E, sizeof(float) * (size_t)(n * ctx->D), kind, st));
@@ -641,14 +772,14 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
         scores = ctx->qscores;
         cnt = ctx->qcount;
     }
-    span_begin(ctx, SLAG_STAGE_QUERY);
+    span_begin(ctx, SLAG_STAGE_QUERY, st);
     if (tc)
         launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i,
                              ids, scores, cnt, ctx->tc_err, st);
     else
         launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i, ids, scores,
                           cnt, st);
-    span_end(ctx);
+    span_end(ctx, st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&ctx->hc->tc_err, ctx->tc_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     if (!on_device) {
@@ -671,14 +802,19 @@ slag_status slag_reset(slag_ctx *ctx) {
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->n;
-    launch_hash_init(ctx->hash, n, st);
+    CK(join_views(ctx));
+    // a view that failed after its front sync can leave entries in its slot's table
+    for (int i = 0; i < kSlots; ++i) {
+        launch_hash_init(ctx->slot[i].hash, n, st);
+        CK(cudaMemsetAsync(ctx->slot[i].ctr, 0, sizeof(ViewCounters), st));
+        ctx->slot[i].log_bound = 0;
+    }
     CK(cudaMemsetAsync(ctx->s_hi, 0, sizeof(float) * n, st));
     CK(cudaMemsetAsync(ctx->s_lo, 0, sizeof(float) * n, st));
     CK(cudaMemsetAsync(ctx->s_ovf, 0, sizeof(float) * n, st));
     CK(cudaMemsetAsync(ctx->totals, 0, 4 * sizeof(unsigned long long), st));
-    CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(ViewCounters), st));
     CK(cudaGetLastError());
-    ctx->contrib_before_last = 0;
+    ctx->views_enqueued = 0;
     ctx->table_rows = 0;
     ctx->log_overflowed = false;
     ctx->finalized = false;
@@ -699,12 +835,18 @@ void slag_destroy(slag_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
+    if (ctx->front) cudaStreamSynchronize(ctx->front);
+    for (int i = 0; i < kSlots; ++i)
+        if (ctx->slot[i].back) cudaStreamSynchronize(ctx->slot[i].back);
+    for (int i = 0; i < kSlots; ++i) slot_free(ctx->slot[i]);
+    if (ctx->front) cudaStreamDestroy(ctx->front);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_front) cudaEventDestroy(ctx->ev_front);
+    if (ctx->ev_consumed) cudaEventDestroy(ctx->ev_consumed);
     dfree(ctx->mean_op); dfree(ctx->cov_a); dfree(ctx->cov_b); dfree(ctx->orig_of_int); dfree(ctx->int_of_orig);
-    for (int b = 0; b < 2; ++b) { dfree(ctx->dkey[b]); dfree(ctx->dval[b]); dfree(ctx->pkey[b]); dfree(ctx->pval[b]); }
-    dfree(ctx->rec_a); dfree(ctx->rec_b); dfree(ctx->srec_a); dfree(ctx->srec_b); dfree(ctx->rect); dfree(ctx->srect);
-    dfree(ctx->stouched); dfree(ctx->offsets); dfree(ctx->hash); dfree(ctx->s_hi); dfree(ctx->s_lo); dfree(ctx->s_ovf);
-    dfree(ctx->ranges); dfree(ctx->prect); dfree(ctx->tile_order); dfree(ctx->seg_buf); dfree(ctx->dbg_T); dfree(ctx->dbg_wsum); dfree(ctx->dbg_count);
-    dfree(ctx->ctr); dfree(ctx->totals); dfree(ctx->touched); dfree(ctx->tc_err);
+    dfree(ctx->s_hi); dfree(ctx->s_lo); dfree(ctx->s_ovf);
+    dfree(ctx->dbg_T); dfree(ctx->dbg_wsum); dfree(ctx->dbg_count);
+    dfree(ctx->totals); dfree(ctx->touched); dfree(ctx->tc_err);
     dfree(ctx->log_key); dfree(ctx->log_key_alt); dfree(ctx->log_w); dfree(ctx->log_w_alt);
     dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
     dfree(ctx->table); dfree(ctx->E); dfree(ctx->inv_norm); dfree(ctx->wsum);
@@ -726,6 +868,7 @@ slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset) {
     if (!ctx || !out) return SLAG_ERR_INVALID_ARG;
     CK(cudaSetDevice(ctx->device));
     CK(cudaStreamSynchronize(ctx->stream));
+    CK(drain_views(ctx));
     spans_resolve(ctx);
     *out = ctx->prof;
     if (reset) ctx->prof = slag_profile{};
@@ -739,11 +882,13 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
     if (s != SLAG_OK) return s;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
+    CK(join_views(ctx));
+    ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
     const CamParams cp = cam_params(cam);
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0, &sgid, 0);
+    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, nullptr, 0, &sgid, 0);
     if (s != SLAG_OK) return s;
     if (out_P) *out_P = P;
     const int64_t n = ctx->n;
@@ -756,7 +901,7 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
             free(h_orig); free(h_rect);
             return fail(ctx, SLAG_ERR_OOM, "host allocation");
         }
-        CK(cudaMemcpyAsync(h_rect, ctx->rect, sizeof(uint2) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_rect, vs.rect, sizeof(uint2) * n, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(h_orig, ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         for (int64_t gI = 0; gI < n; ++gI) {
@@ -785,7 +930,7 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
     if (out_ranges) {
         uint2 *h_r = (uint2 *)malloc(sizeof(uint2) * tiles);
         if (!h_r) return fail(ctx, SLAG_ERR_OOM, "host allocation");
-        CK(cudaMemcpyAsync(h_r, ctx->ranges, sizeof(uint2) * tiles, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_r, vs.ranges, sizeof(uint2) * tiles, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         // an empty tile is reported as [e, e) with e the end of the tiles before it
         int64_t at = 0;
@@ -807,12 +952,14 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     if (s != SLAG_OK) return s;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
+    CK(join_views(ctx));
+    ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
     const CamParams cp = cam_params(cam);
     const int64_t npx = (int64_t)cam->width * cam->height;
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, cp, &P, &keys, &list, nullptr, 0, &sgid, kSuperShift);
+    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, nullptr, 0, &sgid, kSuperShift);
     if (s != SLAG_OK) return s;
     if (npx > ctx->dbg_cap) {
         int64_t c1 = ctx->dbg_cap, c2 = ctx->dbg_cap, c3 = ctx->dbg_cap;
@@ -824,20 +971,20 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     CompositeArgs a;
     memset(&a, 0, sizeof(a));
     a.cam = cp;
-    a.ranges = ctx->ranges;
+    a.ranges = vs.ranges;
     a.bin_shift = kSuperShift;
     a.bins_x = ((cp.tiles_x - 1) >> kSuperShift) + 1;
-    a.tile_order = ctx->tile_order;
+    a.tile_order = vs.tile_order;
     a.list = list;
-    a.prect = ctx->prect;
-    a.srec_a = ctx->srec_a;
-    a.srec_b = ctx->srec_b;
+    a.prect = vs.prect;
+    a.srec_a = vs.srec_a;
+    a.srec_b = vs.srec_b;
     a.sgid = sgid;
     a.seg = nullptr;
     a.weight_mode = ctx->weight_mode;
-    a.ctr = ctx->ctr;
-    a.overflow = reinterpret_cast<uint32_t *>(&ctx->ctr->pad[0]);
-    a.contrib = &ctx->ctr->contributions;
+    a.ctr = vs.ctr;
+    a.overflow = reinterpret_cast<uint32_t *>(&vs.ctr->pad[0]);
+    a.contrib = &vs.ctr->contributions;
     a.dbg_T = ctx->dbg_T;
     a.dbg_wsum = ctx->dbg_wsum;
     a.dbg_count = ctx->dbg_count;

@@ -151,7 +151,8 @@ void launch_composite(const CompositeArgs &a, cudaStream_t st);
 void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st);
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
                     unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key,
-                    float *log_w, uint32_t *overflow, cudaStream_t st);
+                    float *log_w, uint32_t *overflow, const unsigned long long *view_contrib,
+                    unsigned long long *total_contrib, cudaStream_t st);
 void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaStream_t st);
 void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z,
                     uint32_t *ucol, uint32_t *ustart, uint32_t *bstart, uint32_t *bend,
