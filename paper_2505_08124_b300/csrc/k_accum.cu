@@ -20,10 +20,6 @@ namespace slag {
 
 namespace {
 
-__device__ __forceinline__ uint64_t pack_key(uint32_t g, uint32_t col) {
-    return ((uint64_t)(g >> 7) << 39) | ((uint64_t)col << 7) | (uint64_t)(g & 127u);
-}
-
 __global__ void hash_init_k(HashEntry *h, int64_t n) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
@@ -34,6 +30,20 @@ __global__ void hash_init_k(HashEntry *h, int64_t n) {
         e.w[s] = 0.f;
     }
     h[g] = e;
+}
+
+// Grid-stride over the view's records; many records per SM in flight hide the
+// latency of the table probes.
+__global__ void __launch_bounds__(256) combine_k(const WeightRecord *__restrict__ recs,
+                                                 const unsigned long long *__restrict__ rec_count,
+                                                 unsigned long long rec_cap, const HashSink sink) {
+    unsigned long long nr = *rec_count;
+    if (nr > rec_cap) nr = rec_cap;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < nr;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const WeightRecord r = recs[i];
+        sink_add(sink, r.g, r.seg, r.w);
+    }
 }
 
 __global__ void __launch_bounds__(256) consume_k(HashEntry *__restrict__ hash, int64_t n, int32_t view_base,
@@ -224,6 +234,18 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st) {
     hash_init_k<<<blocks_for(n, 256), 256, 0, st>>>(hash, n);
+}
+
+void launch_combine(const WeightRecord *recs, const unsigned long long *rec_count, unsigned long long rec_cap,
+                    const HashSink &sink, cudaStream_t st) {
+    if (rec_cap == 0) return;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    unsigned blocks = (unsigned)sms * 8u;
+    const unsigned long long need = (rec_cap + 255) / 256;
+    if (need < blocks) blocks = (unsigned)need;
+    combine_k<<<blocks, 256, 0, st>>>(recs, rec_count, rec_cap, sink);
 }
 
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,

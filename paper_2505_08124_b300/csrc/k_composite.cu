@@ -11,10 +11,12 @@
 // a segment carries the same embedding E_j, the D-wide product B . E is
 // deferred to the aggregation (this view only emits B).
 //
-// One CTA (256 threads) per 16x16 tile:
-//   * the tile's pixels are reordered by segment ("slot"), so that each warp's
-//     32 pixels usually share one segment;
-//   * records of 256 Gaussians at a time are staged in shared memory; a
+// One CTA (64 threads, one pixel each) per 16x4 quarter of a 16x16 tile; the
+// tile's Gaussians are those of its bin's list (a 4x4-tile super-tile) whose
+// tile rectangle holds the tile, taken in list order:
+//   * the quarter's pixels are reordered by segment ("slot"), so that each
+//     warp's 32 pixels usually share one segment;
+//   * records of up to 192 Gaussians at a time are staged in shared memory; a
 //     record holds mu', the conic scaled by -log2(e)/2 (so that alpha =
 //     min(0.99, 2^(q2 + log2 opacity)) needs one SFU exp2 and the alpha
 //     floor is tested on the exponent before it), and the half extents of
@@ -26,9 +28,12 @@
 //     buffer, then reads the buffer transposed: lane j sums Gaussian j over
 //     the warp's pixels per slot and adds the partial into a shared
 //     (slot x Gaussian) table;
-//   * after each batch the non-zero table entries go into the per-view
-//     (segment, weight) table of each Gaussian in global memory (4 slots per
-//     Gaussian; further segments are appended directly as triples).
+//   * after each batch the non-zero table entries are queued in shared memory
+//     and moved, a block at a time, to the view's record list; a separate
+//     combine pass (many records in flight per SM) adds them to the per-view
+//     (segment, weight) table of each Gaussian (4 slots per Gaussian; further
+//     segments are appended directly as triples). Probing the tables here
+//     would leave each CTA waiting on a dependent chain of L2 round trips.
 #include "slag_internal.cuh"
 
 namespace slag {
@@ -40,7 +45,9 @@ constexpr int kThreads = kTile * kRows;               // 64: one pixel per threa
 constexpr int kSubTiles = kTile / kRows;
 constexpr int kRound = 128;                           // candidates examined per fill round
 constexpr int kBatch = 64 + kRound;                   // record capacity of a batch
-constexpr int kSmemSlots = 8;
+constexpr int kSmemSlots = 4;
+constexpr int kRecBuf = 256;                          // queued (Gaussian, slot) sums of a CTA
+constexpr int kRecFlush = 128;                        // queue level that triggers a flush after a batch
 constexpr int kWStride = 33;
 constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2(1/255)
 
@@ -56,7 +63,14 @@ struct Smem {
     int32_t seg_of_slot[kThreads];
     int32_t group_slot[kThreads / 32];    // slot shared by a warp's 32 positions, -2 = mixed
     int32_t scalar[4];
+    uint32_t rec_g[kRecBuf];              // queued sums: Gaussian, weight, shared slot
+    float rec_w[kRecBuf];
+    uint8_t rec_s[kRecBuf];
+    int32_t nrec;
+    unsigned long long rec_base;
 };
+// 10 CTAs per SM (228 KB of shared memory, 1 KB of it reserved per CTA)
+static_assert(sizeof(Smem) + 1024 <= 233472 / 10, "composite shared memory above the 10-CTA budget");
 
 __device__ __forceinline__ float fast_exp2(float x) {
     float y;
@@ -78,42 +92,39 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-__device__ __forceinline__ uint64_t pack_key(uint32_t g, uint32_t col) {
-    return ((uint64_t)(g >> 7) << 39) | ((uint64_t)col << 7) | (uint64_t)(g & 127u);
-}
-
-__device__ void append_triple(const CompositeArgs &a, uint32_t g, int32_t seg, float w) {
-    unsigned long long idx = atomicAdd(a.log_count, 1ull);
-    if (idx < a.log_cap) {
-        a.log_key[idx] = pack_key(g, (uint32_t)(a.view_base + seg));
-        a.log_w[idx] = w;
-        atomicAdd(&a.s_ovf[g], w);
-    } else {
-        atomicOr(a.overflow, 1u);
-    }
-}
-
-// Adds w to the (segment, weight) slot of Gaussian g, claiming a free slot if needed.
-__device__ void hash_add(const CompositeArgs &a, uint32_t g, int32_t seg, float w) {
-    HashEntry *h = a.hash + g;
-#pragma unroll
-    for (int s = 0; s < kHashSlots; ++s) {
-        int32_t cur = *((volatile int32_t *)&h->seg[s]);
-        if (cur == -1) {
-            cur = atomicCAS(&h->seg[s], -1, seg);
-            if (cur == -1) cur = seg;
-        }
-        if (cur == seg) {
-            atomicAdd(&h->w[s], w);
-            return;
-        }
-    }
-    append_triple(a, g, seg, w);
+__device__ __forceinline__ HashSink sink_of(const CompositeArgs &a) {
+    return HashSink{a.hash, a.log_count, a.log_cap, a.log_key, a.log_w, a.s_ovf, a.overflow, a.view_base};
 }
 
 __device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int slot, int gi, float acc) {
     if (slot < kSmemSlots) atomicAdd(&sm.wb[slot][gi], acc);
-    else hash_add(a, sm.gid[gi], sm.seg_of_slot[slot], acc);
+    else sink_add(sink_of(a), sm.gid[gi], sm.seg_of_slot[slot], acc);
+}
+
+// Moves the queued records to the view's record list: one reservation for
+// all of them. Every thread of the CTA calls it (after a barrier).
+__device__ void flush_queue(const CompositeArgs &a, Smem &sm, int tid) {
+    const int nr = min(sm.nrec, kRecBuf);
+    if (tid == 0) sm.rec_base = nr ? atomicAdd(a.rec_count, (unsigned long long)nr) : 0ull;
+    __syncthreads();
+    const unsigned long long base = sm.rec_base;
+    for (int k = tid; k < nr; k += kThreads) {
+        const uint32_t g = sm.rec_g[k];
+        const int32_t seg = sm.seg_of_slot[sm.rec_s[k]];
+        const float w = sm.rec_w[k];
+        if (base + (unsigned long long)k < a.rec_cap) {
+            WeightRecord r;
+            r.g = g;
+            r.seg = seg;
+            r.w = w;
+            r.pad = 0u;
+            a.recs[base + k] = r;
+        } else {
+            sink_add(sink_of(a), g, seg, w);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) sm.nrec = 0;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -141,7 +152,10 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
         sm.keys[tid] = ((uint32_t)(s_nat + 1) << 8) | (uint32_t)tid;
     }
     // (pixel index within the CTA fits in the low 8 bits of a key)
-    if (tid == 0) sm.scalar[0] = s_nat;
+    if (tid == 0) {
+        sm.scalar[0] = s_nat;
+        sm.nrec = 0;
+    }
     __syncthreads();
     const bool uniform = __syncthreads_and(s_nat == sm.scalar[0]);
     int pos;
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
                 if (lane == 0) sm.fill[k * (kThreads / 32) + w] = __popc(bal[k]);
             }
             __syncthreads();
-            int before = 0, nh = 0;
+            int nh = 0;
             for (int q = 0; q < kPer * (kThreads / 32); ++q) nh += sm.fill[q];
 #pragma unroll
             for (int k = 0; k < kPer; ++k) {
@@ -262,7 +276,6 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
                     cp_async4(&sm.gid[pos], a.sgid + r[k]);
                 }
             }
-            (void)before;
             nb += nh;
             cursor += kRound;
             __syncthreads();
@@ -373,16 +386,40 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
             __syncwarp();
         }
         __syncthreads();
-        // C: per Gaussian of the batch, push the non-zero (segment, sum) entries
-        if (a.accumulate)
-            for (int i = tid; i < nb; i += kThreads) {
-                const uint32_t g = sm.gid[i];
+        // C: per Gaussian of the batch, the non-zero (segment, sum) entries are queued;
+        // the queue goes to the view's record list in blocks, and the combine pass
+        // adds the records to the per-Gaussian tables
+        if (a.accumulate) {
+            for (int i0 = 0; i0 < nb; i0 += kThreads) {
+                const int i = i0 + tid;
+                const bool valid = i < nb;
+                const uint32_t g = valid ? sm.gid[i] : 0u;
                 for (int s2 = 0; s2 < ns_smem; ++s2) {
-                    const float v = sm.wb[s2][i];
-                    if (v != 0.f) hash_add(a, g, sm.seg_of_slot[s2], v);
+                    const float v = valid ? sm.wb[s2][i] : 0.f;
+                    const uint32_t bal = __ballot_sync(0xffffffffu, v != 0.f);
+                    if (bal == 0u) continue;
+                    // one queue reservation per warp; without room (or without a record
+                    // list) the sum goes to the Gaussian's table directly
+                    int base = kRecBuf;
+                    if (lane == 0 && a.recs) base = atomicAdd(&sm.nrec, __popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (v != 0.f) {
+                        const int k = base + __popc(bal & lt);
+                        if (k < kRecBuf) {
+                            sm.rec_g[k] = g;
+                            sm.rec_w[k] = v;
+                            sm.rec_s[k] = (uint8_t)s2;
+                        } else {
+                            sink_add(sink_of(a), g, sm.seg_of_slot[s2], v);
+                        }
+                    }
                 }
             }
+            __syncthreads();
+            if (sm.nrec >= kRecFlush) flush_queue(a, sm, tid);
+        }
     }
+    if (a.accumulate && a.recs) flush_queue(a, sm, tid);
 
     if (inside) {
         const int64_t pi = (int64_t)py * W + px;

@@ -26,7 +26,6 @@ constexpr int kThreads = 256;
 constexpr int kItems = 16;
 constexpr int kTileItems = kThreads * kItems;   // 4096
 constexpr int kWarps = kThreads / 32;
-constexpr int kWarpItems = kTileItems / kWarps; // 512
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;

@@ -56,6 +56,9 @@ struct ViewSlot {
     int64_t order_cap = 0;
     int32_t *seg_buf = nullptr;            // the view's segment map (always copied: the caller's buffer
     int64_t seg_cap = 0;                   // is free once slag_add_view returns)
+    WeightRecord *recs = nullptr;          // the composite's (Gaussian, segment, weight) sums
+    int64_t rec_cap = 0;
+    unsigned long long *rec_count = nullptr;
     ViewCounters *ctr = nullptr;           // device
     struct Host {
         ViewCounters v;
@@ -388,6 +391,7 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
     SA(dalloc(&vs.stouched, n)); SA(dalloc(&vs.offsets, n));
     SA(dalloc(&vs.hash, n));
     SA(dalloc(&vs.ctr, 1));
+    SA(dalloc(&vs.rec_count, 1));
     SA(cudaMallocHost((void **)&vs.h, sizeof(ViewSlot::Host)));
     int lo = 0, hi = 0;
     SA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -404,6 +408,7 @@ void slot_free(ViewSlot &vs) {
     dfree(vs.rec_a); dfree(vs.rec_b); dfree(vs.srec_a); dfree(vs.srec_b); dfree(vs.rect); dfree(vs.srect);
     dfree(vs.stouched); dfree(vs.offsets); dfree(vs.hash);
     dfree(vs.prect); dfree(vs.ranges); dfree(vs.tile_order); dfree(vs.seg_buf); dfree(vs.ctr);
+    dfree(vs.recs); dfree(vs.rec_count);
     if (vs.h) cudaFreeHost(vs.h);
     vs.h = nullptr;
     if (vs.back) cudaStreamDestroy(vs.back);
@@ -568,27 +573,34 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     // kHashSlots per Gaussian from the consume pass and the composite's
     // overflow appends)
     vs.log_bound = ctx->n * kHashSlots + 2 * (int64_t)vs.h->v.P_tiles + (1 << 20);
-    int64_t need = (int64_t)vs.h->totals[0] + vs.log_bound;
+    int64_t others = 0;
     for (int i = 0; i < kSlots; ++i)
-        if (&ctx->slot[i] != &vs) need += ctx->slot[i].log_bound;
-    if (need > ctx->log_cap) {
-        // no view may append while the log moves: wait for all, then read the exact fill level
+        if (&ctx->slot[i] != &vs) others += ctx->slot[i].log_bound;
+    if ((int64_t)vs.h->totals[0] + others + vs.log_bound > ctx->log_cap) {
+        // no view may append while the log moves: wait for all, then read the exact
+        // fill level; the new capacity keeps room for a full pipeline of views, so
+        // that the next views pass this test without waiting
         CK(drain_views(ctx));
         CK(cudaMemcpyAsync(vs.h->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, fr));
         CK(cudaStreamSynchronize(fr));
-        for (int i = 0; i < kSlots; ++i)
-            if (&ctx->slot[i] != &vs) ctx->slot[i].log_bound = 0;
         const int64_t used = (int64_t)vs.h->totals[0];
-        need = used + vs.log_bound;
+        const int64_t need = used + others + vs.log_bound;
         int64_t c1 = ctx->log_cap, c2 = ctx->log_cap;
         CK(grow(ctx->log_key, c1, need, fr, used));
         CK(grow(ctx->log_w, c2, need, fr, used));
         ctx->log_cap = c1;
     }
 
+    // record list of the composite: one record per (Gaussian, 16x4 quarter tile,
+    // segment) with a non-zero sum; sums beyond the capacity go to the tables
+    // directly, so the capacity only bounds the fast path
+    const int64_t rec_need = (int64_t)vs.h->v.P_tiles + ctx->n;
+    if (rec_need > vs.rec_cap) CK(grow(vs.recs, vs.rec_cap, rec_need, fr));
+
     // back half on the slot's stream
     cudaStream_t bk = vs.back;
     CK(cudaStreamWaitEvent(bk, vs.ev_bin, 0));
+    CK(cudaMemsetAsync(vs.rec_count, 0, sizeof(unsigned long long), bk));
     CompositeArgs a;
     a.cam = cp;
     a.ranges = vs.ranges;
@@ -616,8 +628,16 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     a.dbg_T = a.dbg_wsum = nullptr;
     a.dbg_count = nullptr;
     a.accumulate = 1;
+    a.recs = vs.recs;
+    a.rec_count = vs.rec_count;
+    a.rec_cap = (unsigned long long)vs.rec_cap;
     span_begin(ctx, SLAG_STAGE_COMPOSITE, bk);
     launch_composite(a, bk);
+    span_end(ctx, bk);
+    const HashSink sink{vs.hash, ctx->log_count, (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
+                        ctx->s_ovf, reinterpret_cast<uint32_t *>(ctx->totals + 2), (int32_t)ctx->table_rows};
+    span_begin(ctx, SLAG_STAGE_CONSUME, bk);
+    launch_combine(vs.recs, vs.rec_count, (unsigned long long)vs.rec_cap, sink, bk);
     span_end(ctx, bk);
     // consumes in view order: the compensated sums are updated without atomics
     CK(cudaStreamWaitEvent(bk, ctx->ev_consumed, 0));
@@ -989,6 +1009,9 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.dbg_wsum = ctx->dbg_wsum;
     a.dbg_count = ctx->dbg_count;
     a.accumulate = 0;
+    a.recs = nullptr;
+    a.rec_count = nullptr;
+    a.rec_cap = 0;
     launch_composite(a, st);
     CK(cudaGetLastError());
     if (out_T) CK(cudaMemcpyAsync(out_T, ctx->dbg_T, sizeof(float) * npx, cudaMemcpyDeviceToHost, st));

@@ -118,6 +118,64 @@ void launch_pair_rects(const uint32_t *list, int64_t P, const uint2 *srect, uint
 void launch_tile_order(const uint2 *ranges, int tiles_x, int tiles_y, int shift, uint32_t *order,
                        cudaStream_t st);
 
+// Where a view's per-Gaussian (segment, weight) sums go: the Gaussian's
+// kHashSlots-entry table, or, once its slots hold other segments, a triple
+// (Gaussian, column, weight) appended to the log, whose weight also goes to
+// the Gaussian's overflow sum.
+struct HashSink {
+    HashEntry *hash;               // n entries (internal order)
+    unsigned long long *log_count;
+    unsigned long long log_cap;
+    uint64_t *log_key;
+    float *log_w;
+    float *s_ovf;                  // per-Gaussian weight of overflow triples
+    uint32_t *overflow;            // set when the triple log is full (never reset by a view)
+    int32_t view_base;             // column of segment 0 of this view
+};
+
+// Log key of (internal Gaussian g, column col): block of 128 Gaussians, column, offset in the block.
+__device__ __forceinline__ uint64_t pack_key(uint32_t g, uint32_t col) {
+    return ((uint64_t)(g >> 7) << 39) | ((uint64_t)col << 7) | (uint64_t)(g & 127u);
+}
+
+__device__ __forceinline__ void sink_append(const HashSink &k, uint32_t g, int32_t seg, float w) {
+    const unsigned long long idx = atomicAdd(k.log_count, 1ull);
+    if (idx < k.log_cap) {
+        k.log_key[idx] = pack_key(g, (uint32_t)(k.view_base + seg));
+        k.log_w[idx] = w;
+        atomicAdd(&k.s_ovf[g], w);
+    } else {
+        atomicOr(k.overflow, 1u);
+    }
+}
+
+// Adds w to the (segment, weight) slot of Gaussian g, claiming a free slot if needed.
+__device__ __forceinline__ void sink_add(const HashSink &k, uint32_t g, int32_t seg, float w) {
+    HashEntry *h = k.hash + g;
+#pragma unroll
+    for (int s = 0; s < kHashSlots; ++s) {
+        int32_t cur = *((volatile int32_t *)&h->seg[s]);
+        if (cur == -1) {
+            cur = atomicCAS(&h->seg[s], -1, seg);
+            if (cur == -1) cur = seg;
+        }
+        if (cur == seg) {
+            atomicAdd(&h->w[s], w);
+            return;
+        }
+    }
+    sink_append(k, g, seg, w);
+}
+
+// One per-(Gaussian, sub-tile, segment) sum of a view, on its way from the
+// compositing kernel to the combine pass.
+struct __align__(16) WeightRecord {
+    uint32_t g;                    // internal Gaussian index
+    int32_t seg;
+    float w;
+    uint32_t pad;
+};
+
 // k_composite.cu
 struct CompositeArgs {
     CamParams cam;
@@ -144,11 +202,17 @@ struct CompositeArgs {
     float *dbg_T, *dbg_wsum;       // nullable, H x W
     int32_t *dbg_count;            // nullable
     int accumulate;                // 0: compositing only (diagnostics)
+    WeightRecord *recs;            // record list of the view (nullable: sums go to the tables directly)
+    unsigned long long *rec_count; // records written (zeroed before the launch)
+    unsigned long long rec_cap;
 };
 void launch_composite(const CompositeArgs &a, cudaStream_t st);
 
 // k_accum.cu
 void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st);
+// Adds the view's records (the first min(*rec_count, rec_cap)) to the per-Gaussian tables.
+void launch_combine(const WeightRecord *recs, const unsigned long long *rec_count, unsigned long long rec_cap,
+                    const HashSink &sink, cudaStream_t st);
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
                     unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key,
                     float *log_w, uint32_t *overflow, const unsigned long long *view_contrib,
