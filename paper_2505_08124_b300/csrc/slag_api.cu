@@ -8,7 +8,7 @@
 //   sort by bin -> bin ranges -> composite + mask + in-tile segment binning ->
 //   consume the per-view (segment, weight) tables into the triple log.
 //
-// Views are pipelined over kSlots sets of per-view buffers. The front half
+// Views are pipelined over kSlots (6) sets of per-view buffers. The front half
 // (projection through binning) runs on one high-priority internal stream, the
 // back half (composite, consume) on the slot's own stream, so that the next
 // view's front half and the start of its composite fill the SMs that a
@@ -33,7 +33,7 @@ using namespace slag;
 
 namespace {
 
-constexpr int kSlots = 2;   // views in flight
+constexpr int kSlots = 6;   // views in flight
 
 // Buffers of one view in flight. The front stream fills them; the slot's back
 // stream composites from them; the front stream reuses them for the view
