@@ -12,8 +12,11 @@ Reported:
   e2e    the same through host buffers: per step the segment maps and tables
          are copied host->device, the embeddings, weight sums and query
          results device->host, all inside the timed region
-  roofline  the stage with the largest device time, timed live with CUDA
-         events recorded by the library in its own stream
+  roofline  the compositing kernel (the largest share of device time): its
+         algorithmic operations over the time at least one composite was
+         running, from CUDA events the library records in the streams that
+         launch it (views in flight overlap, so summed launch spans would
+         count shared time more than once)
   cpu_baseline  the CPU oracle on a bounded sample of the same workload
 
 `--impl reference` times the CPU oracle alone (the reference arm).
@@ -46,6 +49,10 @@ FP32_LANES = 128
 # quadratic form (9), exponent argument check (1), opacity product and cap (2), floor test (1),
 # transmittance update, stop test and weight (3), plus the exp itself on the SFU.
 OPS_PER_EVAL = 18
+# DRAM bytes (read + write) per launch of composite_k from one ncu capture on this workload, valid
+# while the kernel source has the recorded SHA-256 (otherwise the roofline reports traffic: null).
+COMPOSITE_TRAFFIC = {"bytes_per_launch": 15488000,   # 15.465 MB read + 0.023 MB written
+                     "source_sha256": "2227b9a2011f3c5211231097a4edfc7d095baaebaf9f8024f1f22cf60c07a09f"}
 
 
 def _args():
@@ -68,6 +75,21 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x, dist=None, device=None):
+    """Max of x over the ranks of the default process group (x itself without one)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world_size, seconds):
+    """Whole-job throughput: every rank processed units_per_rank in the (max-over-ranks) time."""
+    return units_per_rank * world_size / seconds
 
 
 def _scene(views_limit=0):
@@ -195,7 +217,9 @@ def run_reference(a):
            "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "views_per_s": vps,
-           "config": {"workload": WORKLOAD, "views": len(views), "l2": "n/a (host)"},
+           "config": {"workload": WORKLOAD, "gaussians": scene.gaussians.n, "views": len(views),
+                      "resolution": "960x540", "segments": 64, "dim": scene.dim, "queries": a.queries, "k": a.k,
+                      "parallelism": "rank 0 on host cores", "l2": "n/a (host)"},
            "cpu_baseline": dict(s, value=value),
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -263,12 +287,8 @@ def run_slag(a):
         if dist:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x):
+        return max_over_ranks(x, dist, dev)
 
     for _ in range(a.warmup):
         step_device()
@@ -280,21 +300,22 @@ def run_slag(a):
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(_device_id(torch, local)) as clk:
         barrier()
+        n_launch0 = S.kernel_launches()
         e0.record(stream)
         for _ in range(a.steps):
             step_device()
         e1.record(stream)
         barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1))
-    prof = L.profile(reset=True)
+        gpu_launches = S.kernel_launches() - n_launch0
+    ms = rank_max(e0.elapsed_time(e1))
+    prof = L.profile_busy(reset=True)
     L.set_profiling(False)
     stats = L.stats()
     contrib_per_step = stats["contributions"]          # reset() clears the counters each step
     evals_per_step = stats["evaluations"]
     views_per_step = len(views)
-    total_units = contrib_per_step * a.steps * ws
-    value = total_units / (ms / 1e3)
-    views_per_s = views_per_step * a.steps * ws / (ms / 1e3)
+    value = job_rate(contrib_per_step * a.steps, ws, ms / 1e3)
+    views_per_s = job_rate(views_per_step * a.steps, ws, ms / 1e3)
 
     # end to end through host buffers
     e2e = None
@@ -305,33 +326,39 @@ def run_slag(a):
         for _ in range(a.steps):
             step_host()
         barrier()
-        dt = max_over_ranks(time.perf_counter() - t0)
+        dt = rank_max(time.perf_counter() - t0)
         h2d = sum(x.nbytes for x in h_seg) + sum(x.nbytes for x in h_tab) + h_Q.nbytes
         d2h = h_E.nbytes + h_w.nbytes + a.queries * a.k * (8 + 4) + a.queries * 4
-        e2e = {"value": contrib_per_step * a.steps * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "views_per_s": views_per_step * a.steps * ws / dt,
+        e2e = {"value": job_rate(contrib_per_step * a.steps, ws, dt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "views_per_s": job_rate(views_per_step * a.steps, ws, dt),
                "ms_per_step": dt * 1e3 / a.steps}
 
     # roofline of the stage with the largest device time
     import json as _j
     peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    dominant = max(prof, key=lambda k: prof[k][0])
-    comp_ms, comp_spans = prof["composite"]
-    launches_per_step = len(views)
-    comp_ms_per_launch = comp_ms / max(1, comp_spans)
+    dominant = max(prof, key=lambda k: prof[k][2])
+    comp_ms, comp_spans, comp_busy = prof["composite"]
+    launches = max(1, comp_spans)
+    busy_per_launch = comp_busy / launches          # composite-busy time per launch (ms)
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     peak_tops = N_SM * FP32_LANES * sm_max * 1e6 / 1e12
-    evals_per_launch = evals_per_step / max(1, launches_per_step)
-    achieved = evals_per_launch * OPS_PER_EVAL / (comp_ms_per_launch / 1e3) / 1e12
+    evals_per_launch = evals_per_step * a.steps / launches
+    achieved = evals_per_launch * OPS_PER_EVAL / (busy_per_launch / 1e3) / 1e12
+    traffic = None
+    if COMPOSITE_TRAFFIC["bytes_per_launch"] is not None:
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_2505_08124_b300", "csrc", "k_composite.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() == COMPOSITE_TRAFFIC["source_sha256"]:
+            traffic = COMPOSITE_TRAFFIC["bytes_per_launch"]
     roofline = {"kernel": "composite_k", "bound": "alu", "achieved": achieved, "peak": peak_tops,
-                "unit": "TOPS (fp32 issue)", "frac": achieved / peak_tops, "traffic": None,
-                "evaluations_per_launch": evals_per_launch, "ms_per_launch": comp_ms_per_launch,
+                "unit": "TOPS (fp32 issue)", "frac": achieved / peak_tops, "traffic": traffic,
+                "evaluations_per_launch": evals_per_launch,
+                "busy_ms_per_launch": busy_per_launch, "span_ms_per_launch": comp_ms / launches,
                 "peak_source": "derived: %d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json)"
                                % (N_SM, FP32_LANES, sm_max),
                 "dominant_stage": dominant}
 
-    gpu_launches = _count_launches(prof, a)
     cpu = None
     if rank == 0 and not a.no_cpu:
         cpu = _cpu_oracle_sample(scene, views, a.cpu_seconds)
@@ -351,23 +378,13 @@ def run_slag(a):
                "roofline": roofline,
                "cpu_baseline": cpu,
                "gpu_launches": gpu_launches,
-               "stages_ms_per_step": {k: v[0] / a.steps for k, v in prof.items()},
+               "stages_busy_ms_per_step": {k: v[2] / a.steps for k, v in prof.items()},
+               "stages_span_ms_per_step": {k: v[0] / a.steps for k, v in prof.items()},
                "stats_per_step": stats}
         print(json.dumps(out), flush=True)
     L.close()
     if dist:
         dist.destroy_process_group()
-
-
-def _count_launches(prof, a):
-    """Kernel launches of the library per timed region (counted from the pipeline's structure)."""
-    views = prof["composite"][1] // max(1, a.steps) if prof["composite"][1] else 0
-    # per view: check_seg, project, 4 depth-sort passes x 3, gather, scan x3, emit, tile sort
-    # 2 passes x 3, ranges, composite, consume
-    per_view = 1 + 1 + 12 + 1 + 3 + 1 + 6 + 1 + 1 + 1
-    # per finalize: log sort (~4 passes x 3), flags, scan x3, uniques, aggregate; reset: hash init
-    per_step = 12 + 1 + 3 + 1 + 1 + 1 + 2   # + query: score + merge
-    return int((views * per_view + per_step) * a.steps)
 
 
 def main():

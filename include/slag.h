@@ -213,12 +213,12 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
 
 /* ---- diagnostics: per-stage device time ---------------------------------- */
 
-/* Stages timed with CUDA events recorded in the context's stream. */
+/* Stages timed with CUDA events recorded in the streams that run them. */
 enum {
     SLAG_STAGE_PROJECT = 0,    /* projection, depth sort, depth-rank gather, tile-count scan */
-    SLAG_STAGE_BIN = 1,        /* pair emission, stable sort by tile, tile ranges */
+    SLAG_STAGE_BIN = 1,        /* pair emission, stable sort by bin, bin ranges */
     SLAG_STAGE_COMPOSITE = 2,  /* compositing, masking, in-tile segment binning */
-    SLAG_STAGE_CONSUME = 3,    /* per-view (segment, weight) tables -> triple log */
+    SLAG_STAGE_CONSUME = 3,    /* combine pass, per-view (segment, weight) tables -> triple log */
     SLAG_STAGE_LOG_SORT = 4,   /* finalize: sort of the triple log, distinct columns */
     SLAG_STAGE_AGGREGATE = 5,  /* finalize: blocked contraction and normalisation */
     SLAG_STAGE_QUERY = 6,      /* cosine scores and top-k */
@@ -226,8 +226,10 @@ enum {
 };
 
 typedef struct {
-    double ms[SLAG_STAGE_COUNT];       /* summed device time per stage */
+    double ms[SLAG_STAGE_COUNT];       /* summed duration of the stage's spans */
     int64_t spans[SLAG_STAGE_COUNT];   /* number of timed spans per stage */
+    double busy_ms[SLAG_STAGE_COUNT];  /* time covered by at least one span of the stage: views in
+                                          flight overlap, so ms can exceed it */
 } slag_profile;
 
 /* Turn per-stage timing on (1) or off (0). Off by default; when on, every
@@ -235,9 +237,15 @@ typedef struct {
  * synchronisation: spans are resolved at the calls that synchronise). */
 slag_status slag_set_profiling(slag_ctx *ctx, int32_t enable);
 
-/* Synchronises the context's stream, adds every finished span to *out and,
- * when reset is non-zero, clears the totals. */
+/* Synchronises the context's streams, adds every finished span to *out and,
+ * when reset is non-zero, clears the totals. busy_ms covers the spans
+ * resolved since profiling was enabled or last reset. */
 slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset);
+
+/* Kernel launches issued by the library so far, over every context and
+ * device of the process (a running count; differences give the launches of
+ * a region of work). */
+uint64_t slag_kernel_launches(void);
 
 #ifdef __cplusplus
 }

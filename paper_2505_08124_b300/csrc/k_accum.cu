@@ -233,7 +233,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st) {
-    hash_init_k<<<blocks_for(n, 256), 256, 0, st>>>(hash, n);
+    hash_init_k<<<blocks_for(n, 256), 256, 0, st>>>(hash, n); note_launch();
 }
 
 void launch_combine(const WeightRecord *recs, const unsigned long long *rec_count, unsigned long long rec_cap,
@@ -245,7 +245,7 @@ void launch_combine(const WeightRecord *recs, const unsigned long long *rec_coun
     unsigned blocks = (unsigned)sms * 8u;
     const unsigned long long need = (rec_cap + 255) / 256;
     if (need < blocks) blocks = (unsigned)need;
-    combine_k<<<blocks, 256, 0, st>>>(recs, rec_count, rec_cap, sink);
+    combine_k<<<blocks, 256, 0, st>>>(recs, rec_count, rec_cap, sink); note_launch();
 }
 
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
@@ -253,23 +253,23 @@ void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, 
                     uint32_t *overflow, const unsigned long long *view_contrib, unsigned long long *total_contrib,
                     cudaStream_t st) {
     consume_k<<<blocks_for(n, 256), 256, 0, st>>>(hash, n, view_base, s_hi, s_lo, log_count, log_cap, log_key,
-                                                  log_w, overflow, view_contrib, total_contrib);
+                                                  log_w, overflow, view_contrib, total_contrib); note_launch();
 }
 
 void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaStream_t st) {
     if (Z <= 0) return;
-    unique_flags_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys, Z, flags);
+    unique_flags_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys, Z, flags); note_launch();
 }
 
 void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z, uint32_t *ucol,
                     uint32_t *ustart, uint32_t *bstart, uint32_t *bend, cudaStream_t st) {
     if (Z <= 0) return;
-    uniques_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys, flags, uidx, Z, ucol, ustart, bstart, bend);
+    uniques_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys, flags, uidx, Z, ucol, ustart, bstart, bend); note_launch();
 }
 
 void launch_aggregate(const AggArgs &a, int64_t nblocks, cudaStream_t st) {
     if (nblocks <= 0) return;
-    aggregate_k<<<(unsigned)nblocks, 256, 0, st>>>(a);
+    aggregate_k<<<(unsigned)nblocks, 256, 0, st>>>(a); note_launch();
 }
 
 }  // namespace slag

@@ -88,23 +88,23 @@ void launch_tile_order(const uint2 *ranges, int tiles_x, int tiles_y, int shift,
                        cudaStream_t st) {
     const int tiles = tiles_x * tiles_y;
     if (tiles <= 0) return;
-    tile_order_k<<<1, 1024, 0, st>>>(ranges, tiles_x, tiles, shift, order);
+    tile_order_k<<<1, 1024, 0, st>>>(ranges, tiles_x, tiles, shift, order); note_launch();
 }
 
 void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int shift, int bins_x,
                  uint32_t *keys, uint32_t *vals, cudaStream_t st) {
     if (n_visible == 0) return;
-    emit_k<<<(n_visible + 255) / 256, 256, 0, st>>>(srect, offsets, n_visible, shift, bins_x, keys, vals);
+    emit_k<<<(n_visible + 255) / 256, 256, 0, st>>>(srect, offsets, n_visible, shift, bins_x, keys, vals); note_launch();
 }
 
 void launch_pair_rects(const uint32_t *list, int64_t P, const uint2 *srect, uint2 *prect, cudaStream_t st) {
     if (P <= 0) return;
-    pair_rect_k<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(list, P, srect, prect);
+    pair_rect_k<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(list, P, srect, prect); note_launch();
 }
 
 void launch_ranges(const uint32_t *keys, int64_t P, uint2 *ranges, cudaStream_t st) {
     if (P <= 0) return;
-    ranges_k<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(keys, P, ranges);
+    ranges_k<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(keys, P, ranges); note_launch();
 }
 
 }  // namespace slag

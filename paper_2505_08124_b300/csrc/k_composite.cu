@@ -445,7 +445,7 @@ void launch_composite(const CompositeArgs &a, cudaStream_t st) {
         attr_set = true;
     }
     const int tiles = a.cam.tiles_x * a.cam.tiles_y;
-    composite_k<<<tiles * kSubTiles, kThreads, sizeof(Smem), st>>>(a);
+    composite_k<<<tiles * kSubTiles, kThreads, sizeof(Smem), st>>>(a); note_launch();
 }
 
 }  // namespace slag

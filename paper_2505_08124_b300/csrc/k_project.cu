@@ -290,7 +290,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 void launch_check_gaussians(const float *means, const float *scales, const float *quats, const float *opac,
                             int64_t n, uint32_t *d_flag, cudaStream_t st) {
-    check_gaussians_k<<<blocks_for(n, 256), 256, 0, st>>>(means, scales, quats, opac, n, d_flag);
+    check_gaussians_k<<<blocks_for(n, 256), 256, 0, st>>>(means, scales, quats, opac, n, d_flag); note_launch();
 }
 
 void launch_bbox(const float *means, int64_t n, uint32_t *d_bbox6, cudaStream_t st) {
@@ -298,39 +298,39 @@ void launch_bbox(const float *means, int64_t n, uint32_t *d_bbox6, cudaStream_t 
     cudaMemcpyAsync(d_bbox6, init, sizeof(init), cudaMemcpyHostToDevice, st);
     unsigned nb = blocks_for(n, 256);
     if (nb > 1184) nb = 1184;
-    bbox_k<<<nb, 256, 0, st>>>(means, n, d_bbox6);
+    bbox_k<<<nb, 256, 0, st>>>(means, n, d_bbox6); note_launch();
 }
 
 void launch_morton(const float *means, int64_t n, const uint32_t *d_bbox6, uint32_t *codes, uint32_t *idx,
                    cudaStream_t st) {
-    morton_k<<<blocks_for(n, 256), 256, 0, st>>>(means, n, d_bbox6, codes, idx);
+    morton_k<<<blocks_for(n, 256), 256, 0, st>>>(means, n, d_bbox6, codes, idx); note_launch();
 }
 
 void launch_pack_gaussians(const float *means, const float *scales, const float *quats, const float *opac,
                            int64_t n, const uint32_t *orig_of_int, float4 *mean_op, float4 *cov_a,
                            float2 *cov_b, uint32_t *int_of_orig, cudaStream_t st) {
     pack_k<<<blocks_for(n, 256), 256, 0, st>>>(means, scales, quats, opac, n, orig_of_int, mean_op, cov_a,
-                                               cov_b, int_of_orig);
+                                               cov_b, int_of_orig); note_launch();
 }
 
 void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *cov_a, const float2 *cov_b,
                     int64_t n, const uint32_t *orig_of_int, uint32_t *dkey_orig, uint32_t *dval_orig,
                     float4 *rec_a, float4 *rec_b, uint2 *rect, ViewCounters *ctr, cudaStream_t st) {
     project_k<<<blocks_for(n, 256), 256, 0, st>>>(cam, mean_op, cov_a, cov_b, n, orig_of_int, dkey_orig,
-                                                  dval_orig, rec_a, rec_b, rect, ctr);
+                                                  dval_orig, rec_a, rec_b, rect, ctr); note_launch();
 }
 
 void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, ViewCounters *ctr, const float4 *rec_a,
                           const float4 *rec_b, const uint2 *rect, float4 *srec_a, float4 *srec_b, uint2 *srect,
                           uint32_t *stouched, int shift, cudaStream_t st) {
     gather_sorted_k<<<blocks_for(n, 256), 256, 0, st>>>(sorted_vals, n, ctr, rec_a, rec_b, rect, srec_a, srec_b,
-                                                        srect, stouched, shift);
+                                                        srect, stouched, shift); note_launch();
 }
 
 void launch_check_seg(const int32_t *seg, int64_t npx, int32_t M, ViewCounters *ctr, cudaStream_t st) {
     unsigned nb = blocks_for(npx, 256);
     if (nb > 2368) nb = 2368;
-    check_seg_k<<<nb, 256, 0, st>>>(seg, npx, M, ctr);
+    check_seg_k<<<nb, 256, 0, st>>>(seg, npx, M, ctr); note_launch();
 }
 
 }  // namespace slag

@@ -186,7 +186,7 @@ size_t query_cand_entries(int32_t B, int64_t n, int32_t k) {
 
 void launch_query_merge(const float *cand_s, const uint32_t *cand_i, int64_t per_query, int32_t B, int32_t k,
                         int64_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t st) {
-    merge_k<<<B, 256, 0, st>>>(cand_s, cand_i, per_query, k, out_ids, out_scores, out_count);
+    merge_k<<<B, 256, 0, st>>>(cand_s, cand_i, per_query, k, out_ids, out_scores, out_count); note_launch();
 }
 
 void launch_query_topk(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n, int32_t D,
@@ -195,8 +195,8 @@ void launch_query_topk(const float *Q, int32_t B, const float *E, const float *i
     const int64_t ntiles = (n + kGB - 1) / kGB;
     const int32_t kk = k < kGB ? k : kGB;
     dim3 grid((unsigned)ntiles, (unsigned)((B + kQB - 1) / kQB));
-    score_tile_k<<<grid, 256, 0, st>>>(Q, B, E, inv_norm, n, D, kk, cand_s, cand_i, (int32_t)ntiles);
-    merge_k<<<B, 256, 0, st>>>(cand_s, cand_i, ntiles * kk, k, out_ids, out_scores, out_count);
+    score_tile_k<<<grid, 256, 0, st>>>(Q, B, E, inv_norm, n, D, kk, cand_s, cand_i, (int32_t)ntiles); note_launch();
+    merge_k<<<B, 256, 0, st>>>(cand_s, cand_i, ntiles * kk, k, out_ids, out_scores, out_count); note_launch();
 }
 
 }  // namespace slag

@@ -402,7 +402,7 @@ void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float
     }
     const int32_t nsplit = query_tc_splits(B, n);
     dim3 grid((unsigned)((B + kM - 1) / kM), (unsigned)nsplit);
-    query_tc_k<<<grid, kThreadsTC, tc_smem(), st>>>(Q, B, E, inv_norm, n, D, k, nsplit, cand_s, cand_i, err);
+    query_tc_k<<<grid, kThreadsTC, tc_smem(), st>>>(Q, B, E, inv_norm, n, D, k, nsplit, cand_s, cand_i, err); note_launch();
     const int32_t kk = k < kTopTC ? k : kTopTC;
     launch_query_merge(cand_s, cand_i, (int64_t)nsplit * kk, B, k, out_ids, out_scores, out_count, st);
 }

@@ -267,10 +267,10 @@ void radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, int64_t n,
         attr_set = true;
     }
     const uint32_t mask = (width >= 32) ? 0xffffffffu : ((1u << width) - 1u);
-    rs_hist<K, ITEMS, BINS><<<ntiles, kThreads, kWarps * BINS * 4, st>>>(ki, n, shift, mask, width, s.hist, ntiles);
-    rs_offsets<<<BINS, ntiles >= 1024 ? 1024 : (ntiles >= 256 ? 256 : 64), 0, st>>>(s.hist, s.digit_tot, ntiles);
+    rs_hist<K, ITEMS, BINS><<<ntiles, kThreads, kWarps * BINS * 4, st>>>(ki, n, shift, mask, width, s.hist, ntiles); note_launch();
+    rs_offsets<<<BINS, ntiles >= 1024 ? 1024 : (ntiles >= 256 ? 256 : 64), 0, st>>>(s.hist, s.digit_tot, ntiles); note_launch();
     rs_scatter<K, ITEMS, BINS><<<ntiles, kThreads, scatter_smem<K, ITEMS, BINS>(), st>>>(
-        ki, vi, ko, vo, n, shift, mask, width, s.hist, s.digit_tot, ntiles, ranges, nranges);
+        ki, vi, ko, vo, n, shift, mask, width, s.hist, s.digit_tot, ntiles, ranges, nranges); note_launch();
 }
 
 // Inputs below ~2M items use 1024-item tiles so that the grid still covers the GPU;
@@ -468,9 +468,9 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, unsigned l
         return;
     }
     int64_t tiles = (n + kTileItems - 1) / kTileItems;
-    scan_partials<<<(unsigned)tiles, kThreads, 0, st>>>(in, n, s.partials);
-    scan_spine<<<1, 1024, 0, st>>>(s.partials, tiles, d_total);
-    scan_tiles<<<(unsigned)tiles, kThreads, 0, st>>>(in, out, n, s.partials);
+    scan_partials<<<(unsigned)tiles, kThreads, 0, st>>>(in, n, s.partials); note_launch();
+    scan_spine<<<1, 1024, 0, st>>>(s.partials, tiles, d_total); note_launch();
+    scan_tiles<<<(unsigned)tiles, kThreads, 0, st>>>(in, out, n, s.partials); note_launch();
 }
 
 }  // namespace slag

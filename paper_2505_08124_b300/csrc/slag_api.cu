@@ -23,13 +23,23 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "slag_internal.cuh"
 
 using namespace slag;
+
+namespace slag {
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace slag
 
 namespace {
 
@@ -151,6 +161,8 @@ struct slag_ctx {
     std::vector<Span> spans;
     std::vector<cudaEvent_t> event_pool;
     slag_profile prof{};
+    cudaEvent_t prof_base = nullptr;                       // origin of the span intervals
+    std::vector<std::pair<float, float>> busy[SLAG_STAGE_COUNT];
 };
 
 namespace {
@@ -275,6 +287,10 @@ void spans_resolve(slag_ctx *ctx) {
         if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
             ctx->prof.ms[sp.stage] += ms;
             ctx->prof.spans[sp.stage] += 1;
+            float t0 = 0.f, t1 = 0.f;
+            if (ctx->prof_base && cudaEventElapsedTime(&t0, ctx->prof_base, sp.a) == cudaSuccess &&
+                cudaEventElapsedTime(&t1, ctx->prof_base, sp.b) == cudaSuccess)
+                ctx->busy[sp.stage].push_back({t0, t1});
         }
         ctx->event_pool.push_back(sp.a);
         ctx->event_pool.push_back(sp.b);
@@ -843,6 +859,8 @@ slag_status slag_reset(slag_ctx *ctx) {
     return SLAG_OK;
 }
 
+uint64_t slag_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
+
 slag_status slag_get_stats(const slag_ctx *ctx, slag_stats *out) {
     if (!ctx || !out) return SLAG_ERR_INVALID_ARG;
     *out = ctx->stats;
@@ -874,12 +892,19 @@ void slag_destroy(slag_ctx *ctx) {
     scratch_free(ctx->scratch);
     for (auto &sp : ctx->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->prof_base) cudaEventDestroy(ctx->prof_base);
     if (ctx->hc) cudaFreeHost(ctx->hc);
     delete ctx;
 }
 
 slag_status slag_set_profiling(slag_ctx *ctx, int32_t enable) {
     if (!ctx) return SLAG_ERR_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    if (enable && !ctx->prof_on) {
+        if (!ctx->prof_base) CK(cudaEventCreate(&ctx->prof_base));
+        CK(cudaEventRecord(ctx->prof_base, ctx->stream));
+        for (auto &b : ctx->busy) b.clear();
+    }
     ctx->prof_on = enable != 0;
     return SLAG_OK;
 }
@@ -890,8 +915,29 @@ slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset) {
     CK(cudaStreamSynchronize(ctx->stream));
     CK(drain_views(ctx));
     spans_resolve(ctx);
+    for (int s = 0; s < SLAG_STAGE_COUNT; ++s) {
+        // union of the stage's intervals
+        auto &v = ctx->busy[s];
+        std::sort(v.begin(), v.end());
+        double total = 0.0, lo = 0.0, hi = -1.0;
+        for (const auto &iv : v) {
+            if (iv.first > hi) {
+                if (hi > lo) total += hi - lo;
+                lo = iv.first;
+                hi = iv.second;
+            } else if (iv.second > hi) {
+                hi = iv.second;
+            }
+        }
+        if (hi > lo) total += hi - lo;
+        ctx->prof.busy_ms[s] = total;
+    }
     *out = ctx->prof;
-    if (reset) ctx->prof = slag_profile{};
+    if (reset) {
+        ctx->prof = slag_profile{};
+        for (auto &b : ctx->busy) b.clear();
+        if (ctx->prof_base) CK(cudaEventRecord(ctx->prof_base, ctx->stream));
+    }
     return SLAG_OK;
 }
 

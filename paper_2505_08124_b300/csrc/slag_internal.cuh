@@ -8,6 +8,9 @@
 
 namespace slag {
 
+// Counts the kernel launches of the library (process-wide, every device).
+void note_launch();
+
 constexpr int kTile = 16;          // screen tile edge in pixels
 constexpr int kBlockG = 128;       // Gaussians per aggregation block (key packs g & 127)
 constexpr int kHashSlots = 4;      // per-view (segment, weight) slots per Gaussian

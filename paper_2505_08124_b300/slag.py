@@ -56,12 +56,13 @@ _lib = None
 
 EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_query_batch", "slag_reset",
            "slag_get_stats", "slag_last_error", "slag_destroy", "slag_bin_view", "slag_render_debug",
-           "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk")
+           "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk", "slag_kernel_launches")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
 class CProfile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * len(STAGES)), ("spans", ctypes.c_int64 * len(STAGES))]
+    _fields_ = [("ms", ctypes.c_double * len(STAGES)), ("spans", ctypes.c_int64 * len(STAGES)),
+                ("busy_ms", ctypes.c_double * len(STAGES))]
 
 
 def load_library(path: str = LIB_PATH):
@@ -89,6 +90,8 @@ def load_library(path: str = LIB_PATH):
     lib.slag_render_debug.argtypes = [P, ctypes.POINTER(CCamera), P, P, P]
     lib.slag_set_profiling.argtypes = [P, i32]
     lib.slag_get_profile.argtypes = [P, ctypes.POINTER(CProfile), i32]
+    lib.slag_kernel_launches.argtypes = []
+    lib.slag_kernel_launches.restype = ctypes.c_uint64
     lib.slag_noalloc_query_topk.argtypes = [P, i64, i32, P, P, i32, i32, P, P, P, P]
     for name in EXPORTS:
         f = getattr(lib, name)
@@ -259,10 +262,15 @@ class Lifter:
         self._check(self._lib.slag_set_profiling(self._h, 1 if on else 0), "slag_set_profiling")
 
     def profile(self, reset: bool = False) -> dict:
-        """{stage: (device ms summed, spans)} from events recorded in the context's stream."""
+        """{stage: (summed span ms, spans)} from events recorded in the streams that run each stage."""
+        return {k: v[:2] for k, v in self.profile_busy(reset).items()}
+
+    def profile_busy(self, reset: bool = False) -> dict:
+        """{stage: (summed span ms, spans, busy ms)}; busy ms is the union of the stage's spans
+        (overlapping views make the summed ms larger than it)."""
         p = CProfile()
         self._check(self._lib.slag_get_profile(self._h, ctypes.byref(p), 1 if reset else 0), "slag_get_profile")
-        return {name: (float(p.ms[i]), int(p.spans[i])) for i, name in enumerate(STAGES)}
+        return {name: (float(p.ms[i]), int(p.spans[i]), float(p.busy_ms[i])) for i, name in enumerate(STAGES)}
 
     def bin_view(self, camera):
         """(tiles_touched[n], list[P] caller ids grouped by tile, ranges[tiles, 2])."""
@@ -290,3 +298,8 @@ class Lifter:
                                                 ws.ctypes.data_as(ctypes.c_void_p),
                                                 cnt.ctypes.data_as(ctypes.c_void_p)), "slag_render_debug")
         return T, ws, cnt
+
+
+def kernel_launches() -> int:
+    """Kernel launches issued by libslag so far (process-wide running count)."""
+    return int(load_library().slag_kernel_launches())

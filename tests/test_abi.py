@@ -53,6 +53,15 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(slag.CGaussians) == 8 + 4 * 8 + 8
     assert ctypes.sizeof(slag.COptions) == 16 + 8
     assert ctypes.sizeof(slag.CStats) == 9 * 8
+    # slag_profile: ms, spans, busy_ms per stage
+    assert ctypes.sizeof(slag.CProfile) == 3 * 7 * 8
+
+
+def test_launch_counter_reads_without_a_gpu(lib):
+    # a running count of the library's kernel launches: plain host state
+    from paper_2505_08124_b300 import slag
+    n = slag.kernel_launches()
+    assert isinstance(n, int) and n >= 0
 
 
 def test_missing_library_fails_loudly(tmp_path):
