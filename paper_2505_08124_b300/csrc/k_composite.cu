@@ -11,20 +11,24 @@
 // a segment carries the same embedding E_j, the D-wide product B . E is
 // deferred to the aggregation (this view only emits B).
 //
-// One CTA (64 threads, one pixel each) per 16x4 quarter of a 16x16 tile; the
+// One CTA (64 threads, two pixels each) per 16x8 half of a 16x16 tile; the
 // tile's Gaussians are those of its bin's list (a 4x4-tile super-tile) whose
 // tile rectangle holds the tile, taken in list order:
-//   * the quarter's pixels are reordered by segment ("slot"), so that each
-//     warp's 32 pixels usually share one segment;
+//   * the half tile's pixels are reordered by segment ("slot"); a thread takes
+//     two neighbours in that order (almost always one segment), so each warp's
+//     64 pixels usually share one segment, and the record loads, culling and
+//     bookkeeping of a Gaussian serve two pixels with independent
+//     transmittance chains;
 //   * records of up to 192 Gaussians at a time are staged in shared memory; a
 //     record holds mu', the conic scaled by -log2(e)/2 (so that alpha =
 //     min(0.99, 2^(q2 + log2 opacity)) needs one SFU exp2 and the alpha
 //     floor is tested on the exponent before it), and the half extents of
 //     the alpha >= 1/255 ellipse;
 //   * per chunk of 32 Gaussians, each warp keeps (ballot) only those whose
-//     alpha >= 1/255 ellipse box meets the box of its 32 pixel centres --
+//     alpha >= 1/255 ellipse box meets the box of its 64 pixel centres --
 //     the others cannot contribute to any of its pixels -- composites its
-//     32 pixels against them, storing the weights in a padded shared 32 x 32
+//     pixels against them, storing each lane's weight (its two pixels' sum)
+//     in a padded shared 32 x 32
 //     buffer, then reads the buffer transposed: lane j sums Gaussian j over
 //     the warp's pixels per slot and adds the partial into a shared
 //     (slot x Gaussian) table;
@@ -40,8 +44,9 @@ namespace slag {
 
 namespace {
 
-constexpr int kRows = 4;                              // tile rows per CTA: a 16x16 tile = 4 CTAs
-constexpr int kThreads = kTile * kRows;               // 64: one pixel per thread
+constexpr int kRows = 8;                              // tile rows per CTA: a 16x16 tile = 2 CTAs
+constexpr int kPix = kTile * kRows;                   // 128 pixels per CTA
+constexpr int kThreads = kPix / 2;                    // 64: two pixels per thread
 constexpr int kSubTiles = kTile / kRows;
 constexpr int kRound = 128;                           // candidates examined per fill round
 constexpr int kBatch = 64 + kRound;                   // record capacity of a batch
@@ -58,10 +63,11 @@ struct Smem {
     int32_t fill[4];                      // per-warp hit counts of a fill round
     float wb[kSmemSlots][kBatch];         // per (slot, Gaussian of the batch)
     float wbuf[kThreads / 32][32 * kWStride];
-    uint32_t keys[kThreads];
-    int32_t slot_of_pos[kThreads];
-    int32_t seg_of_slot[kThreads];
-    int32_t group_slot[kThreads / 32];    // slot shared by a warp's 32 positions, -2 = mixed
+    uint32_t keys[kPix];
+    int32_t slot_lane[kThreads];          // slot of the sums each lane stores (its first pixel's)
+    int32_t seg_of_slot[kPix];
+    int32_t group_slot[kThreads / 32];    // slot shared by all of a warp's pixels, -2 = mixed
+    int32_t warp_tot[kThreads / 32];
     int32_t scalar[4];
     uint32_t rec_g[kRecBuf];              // queued sums: Gaussian, weight, shared slot
     float rec_w[kRecBuf];
@@ -133,7 +139,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-__global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs a) {
+__global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -142,76 +148,92 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
     const int tx = tile % a.cam.tiles_x, ty = tile / a.cam.tiles_x;
     const int W = a.cam.width, H = a.cam.height;
 
-    // ---- segment of each pixel, slot-sorted positions --------------------------------
-    int32_t s_nat;
-    {
-        int px = tx * kTile + (tid & 15), py = ty * kTile + row0 + (tid >> 4);
-        bool inside = px < W && py < H;
-        s_nat = (inside && a.seg && a.accumulate) ? a.seg[(int64_t)py * W + px] : -1;
-        if (s_nat < -1) s_nat = -1;
-        sm.keys[tid] = ((uint32_t)(s_nat + 1) << 8) | (uint32_t)tid;
+    // ---- segment of each of the CTA's 128 pixels; positions sorted by segment --------
+    // (thread t reads pixels t and t + 64; a pixel index fits in the low 8 bits of a key)
+    int32_t s_nat[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int p = tid + h * kThreads;
+        const int px = tx * kTile + (p & 15), py = ty * kTile + row0 + (p >> 4);
+        const bool inside = px < W && py < H;
+        int32_t sg = (inside && a.seg && a.accumulate) ? a.seg[(int64_t)py * W + px] : -1;
+        if (sg < -1) sg = -1;
+        s_nat[h] = sg;
+        sm.keys[p] = ((uint32_t)(sg + 1) << 8) | (uint32_t)p;
     }
-    // (pixel index within the CTA fits in the low 8 bits of a key)
     if (tid == 0) {
-        sm.scalar[0] = s_nat;
+        sm.scalar[0] = s_nat[0];
         sm.nrec = 0;
     }
     __syncthreads();
-    const bool uniform = __syncthreads_and(s_nat == sm.scalar[0]);
-    int pos;
-    if (uniform) {
-        pos = tid;
-    } else {
-        const uint32_t mine = sm.keys[tid];
-        int rank = 0;
+    const bool uniform = __syncthreads_and(s_nat[0] == sm.scalar[0] && s_nat[1] == sm.scalar[0]);
+    int pos0 = tid, pos1 = tid + kThreads;
+    if (!uniform) {
+        const uint32_t m0 = sm.keys[tid], m1 = sm.keys[tid + kThreads];
+        int r0 = 0, r1 = 0;
 #pragma unroll 8
-        for (int q = 0; q < kThreads; ++q) rank += sm.keys[q] < mine ? 1 : 0;
-        pos = rank;
+        for (int q = 0; q < kPix; ++q) {
+            const uint32_t kq = sm.keys[q];
+            r0 += kq < m0 ? 1 : 0;
+            r1 += kq < m1 ? 1 : 0;
+        }
+        pos0 = r0;
+        pos1 = r1;
     }
     __syncthreads();
-    sm.keys[pos] = ((uint32_t)(s_nat + 1) << 8) | (uint32_t)tid;   // position -> (segment, pixel)
+    sm.keys[pos0] = ((uint32_t)(s_nat[0] + 1) << 8) | (uint32_t)tid;
+    sm.keys[pos1] = ((uint32_t)(s_nat[1] + 1) << 8) | (uint32_t)(tid + kThreads);
     __syncthreads();
-    // my position is tid from here on
-    const uint32_t kp = sm.keys[tid];
-    const int pix = (int)(kp & 255u);
-    const int32_t my_seg = (int32_t)(kp >> 8) - 1;
-    bool is_new = my_seg >= 0 && (tid == 0 || (int32_t)(sm.keys[tid - 1] >> 8) - 1 != my_seg);
-    // inclusive prefix count of is_new over positions
-    uint32_t bal = __ballot_sync(0xffffffffu, is_new);
-    if (lane == 0) sm.group_slot[w] = __popc(bal);
-    __syncthreads();
-    int before = 0, nslots = 0;
-    for (int q = 0; q < kThreads / 32; ++q) {
-        int c = sm.group_slot[q];
-        if (q < w) before += c;
-        nslots += c;
+    // this thread's pixels: positions 2 tid and 2 tid + 1 (adjacent in segment order, so
+    // they almost always share a segment)
+    const uint32_t k0 = sm.keys[2 * tid], k1 = sm.keys[2 * tid + 1];
+    const int pix0 = (int)(k0 & 255u), pix1 = (int)(k1 & 255u);
+    const int32_t seg0 = (int32_t)(k0 >> 8) - 1, seg1 = (int32_t)(k1 >> 8) - 1;
+    // slots: the distinct segments in position order
+    const int32_t seg_before = tid > 0 ? (int32_t)(sm.keys[2 * tid - 1] >> 8) - 1 : -2;
+    const int new0 = (seg0 >= 0 && seg0 != seg_before) ? 1 : 0;
+    const int new1 = (seg1 >= 0 && seg1 != seg0) ? 1 : 0;
+    int incl = new0 + new1;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
-    const int my_slot = my_seg >= 0 ? before + __popc(bal & ((2u << lane) - 1u)) - 1 : -1;
+    if (lane == 31) sm.warp_tot[w] = incl;
     __syncthreads();
-    sm.slot_of_pos[tid] = my_slot;
-    if (is_new) sm.seg_of_slot[my_slot] = my_seg;
+    const int before = (w == 1 ? sm.warp_tot[0] : 0) + incl - new0 - new1;
+    const int nslots = sm.warp_tot[0] + sm.warp_tot[1];
+    const int slot0 = seg0 >= 0 ? before + new0 - 1 : -1;
+    const int slot1 = seg1 >= 0 ? before + new0 + new1 - 1 : -1;
+    if (new0) sm.seg_of_slot[slot0] = seg0;
+    if (new1) sm.seg_of_slot[slot1] = seg1;
+    sm.slot_lane[tid] = slot0;   // the slot of the sums this lane stores
+    const bool pair_same = slot0 == slot1;
     {
-        int first = __shfl_sync(0xffffffffu, my_slot, 0);
-        bool same = __all_sync(0xffffffffu, my_slot == first);
+        const int first = __shfl_sync(0xffffffffu, slot0, 0);
+        const bool same = __all_sync(0xffffffffu, slot0 == first && slot1 == first);
         if (lane == 0) sm.group_slot[w] = same ? first : -2;
     }
     const int ns_smem = nslots < kSmemSlots ? nslots : kSmemSlots;
 
-    const int px = tx * kTile + (pix & 15), py = ty * kTile + row0 + (pix >> 4);
-    const bool inside = px < W && py < H;
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const int px0 = tx * kTile + (pix0 & 15), py0 = ty * kTile + row0 + (pix0 >> 4);
+    const int px1 = tx * kTile + (pix1 & 15), py1 = ty * kTile + row0 + (pix1 >> 4);
+    const bool inside0 = px0 < W && py0 < H, inside1 = px1 < W && py1 < H;
+    const float pxc0 = (float)px0 + 0.5f, pyc0 = (float)py0 + 0.5f;
+    const float pxc1 = (float)px1 + 0.5f, pyc1 = (float)py1 + 0.5f;
     // bounding box of this warp's pixel centres (culling of Gaussians per warp)
-    float wx0 = inside ? pxc : INFINITY, wx1 = inside ? pxc : -INFINITY;
-    float wy0 = inside ? pyc : INFINITY, wy1 = inside ? pyc : -INFINITY;
+    float wx0 = fminf(inside0 ? pxc0 : INFINITY, inside1 ? pxc1 : INFINITY);
+    float wx1 = fmaxf(inside0 ? pxc0 : -INFINITY, inside1 ? pxc1 : -INFINITY);
+    float wy0 = fminf(inside0 ? pyc0 : INFINITY, inside1 ? pyc1 : INFINITY);
+    float wy1 = fmaxf(inside0 ? pyc0 : -INFINITY, inside1 ? pyc1 : -INFINITY);
     for (int o = 16; o; o >>= 1) {
         wx0 = fminf(wx0, __shfl_xor_sync(0xffffffffu, wx0, o));
         wx1 = fmaxf(wx1, __shfl_xor_sync(0xffffffffu, wx1, o));
         wy0 = fminf(wy0, __shfl_xor_sync(0xffffffffu, wy0, o));
         wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
     }
-    float T = 1.f, wsum = 0.f;
-    int count = 0, evals = 0;
-    bool done = !inside;
+    float T0 = 1.f, T1 = 1.f, wsum0 = 0.f, wsum1 = 0.f;
+    int count0 = 0, count1 = 0, evals = 0;
+    bool done0 = !inside0, done1 = !inside1;
     const bool kernel_mode = a.weight_mode == SLAG_WEIGHT_KERNEL;
 
     // this tile's candidates: the depth-ordered list of its bin (a 2^shift x
@@ -235,11 +257,11 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
     }
 
     while (true) {
-        int live = __syncthreads_count(!done);   // also: the previous batch is fully consumed
+        int live = __syncthreads_count(!(done0 && done1));   // also: the previous batch is consumed
         if (live == 0 || cursor >= end) break;
-        // fill: rounds of kRound candidates until at least 64 records are staged; the
-        // records of the hits are copied asynchronously, the next round's candidates
-        // are loaded while this round is compacted
+        // fill: rounds of kRound candidates until at least kBatch - kRound records are
+        // staged; the records of the hits are copied asynchronously, the next round's
+        // candidates are loaded while this round is compacted
         int nb = 0;
         while (nb < kBatch - kRound && cursor < end) {
             uint32_t r[kPer];
@@ -292,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
         const float4 *rec_b = sm.rec_b;
         const int gs = sm.group_slot[w];
         for (int c = 0; c * 32 < nb; ++c) {
-            if (!__any_sync(0xffffffffu, !done)) break;
+            if (!__any_sync(0xffffffffu, !(done0 && done1))) break;
             const int nvalid = min(32, nb - c * 32);
             // which of the chunk's Gaussians can reach alpha >= 1/255 inside this warp's pixels
             bool hitw = false;
@@ -302,58 +324,86 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
                 hitw = (ra.x - rb.z <= wx1) && (ra.x + rb.z >= wx0) && (ra.y - rb.w <= wy1) && (ra.y + rb.w >= wy0);
             }
             const uint32_t mask = __ballot_sync(0xffffffffu, hitw);
-            if (!done) evals += nvalid;
+            evals += nvalid * ((done0 ? 0 : 1) + (done1 ? 0 : 1));
             if (mask == 0) continue;
-            // A: composite the surviving Gaussians for this thread's pixel, four at a time:
-            // the exponents and exp2 of a group are independent; only the transmittance
-            // updates run in order
+            // A: composite the surviving Gaussians for this thread's two pixels, two
+            // Gaussians at a time: the four exponents and exp2 of a group are independent;
+            // only each pixel's transmittance updates run in order
             uint32_t m = mask;
             while (m) {
-                int jj[4];
-                float al[4], kq[4];
+                int jj[2];
+                float al0[2], al1[2], kq0[2], kq1[2];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < 2; ++k) {
                     jj[k] = m ? __ffs(m) - 1 : -1;
                     m &= m ? m - 1 : 0u;
                 }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    al[k] = 0.f;
-                    kq[k] = 0.f;
+                for (int k = 0; k < 2; ++k) {
+                    al0[k] = al1[k] = 0.f;
+                    kq0[k] = kq1[k] = 0.f;
                     if (jj[k] >= 0) {
                         const float4 ra = rec_a[c * 32 + jj[k]];
                         const float4 rb = rec_b[c * 32 + jj[k]];
-                        const float dx = ra.x - pxc, dy = ra.y - pyc;
-                        const float u = fmaf(ra.z, dx, ra.w * dy);
-                        const float q2 = fmaf(u, dx, rb.x * dy * dy);
-                        const float e = q2 + rb.y;
-                        if (q2 <= 0.f && e >= kLog2AlphaMin) {
-                            al[k] = fminf(0.99f, fast_exp2(e));
-                            kq[k] = q2;
+                        {
+                            const float dx = ra.x - pxc0, dy = ra.y - pyc0;
+                            const float u = fmaf(ra.z, dx, ra.w * dy);
+                            const float q2 = fmaf(u, dx, rb.x * dy * dy);
+                            const float e = q2 + rb.y;
+                            if (q2 <= 0.f && e >= kLog2AlphaMin) {
+                                al0[k] = fminf(0.99f, fast_exp2(e));
+                                kq0[k] = q2;
+                            }
+                        }
+                        {
+                            const float dx = ra.x - pxc1, dy = ra.y - pyc1;
+                            const float u = fmaf(ra.z, dx, ra.w * dy);
+                            const float q2 = fmaf(u, dx, rb.x * dy * dy);
+                            const float e = q2 + rb.y;
+                            if (q2 <= 0.f && e >= kLog2AlphaMin) {
+                                al1[k] = fminf(0.99f, fast_exp2(e));
+                                kq1[k] = q2;
+                            }
                         }
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < 2; ++k) {
                     if (jj[k] < 0) break;
-                    float wv = 0.f;
-                    if (!done && al[k] > 0.f) {
-                        const float Tn = T - al[k] * T;
+                    float w0 = 0.f, w1 = 0.f;
+                    if (!done0 && al0[k] > 0.f) {
+                        const float Tn = T0 - al0[k] * T0;
                         if (Tn < 1e-4f) {
-                            done = true;
+                            done0 = true;
                             evals -= nvalid - 1 - jj[k];
                         } else {
-                            wv = kernel_mode ? fast_exp2(kq[k]) : al[k] * T;
-                            T = Tn;
-                            wsum += wv;
-                            ++count;
+                            w0 = kernel_mode ? fast_exp2(kq0[k]) : al0[k] * T0;
+                            T0 = Tn;
+                            wsum0 += w0;
+                            ++count0;
                         }
                     }
-                    wb_warp[jj[k] * kWStride + lane] = wv;
+                    if (!done1 && al1[k] > 0.f) {
+                        const float Tn = T1 - al1[k] * T1;
+                        if (Tn < 1e-4f) {
+                            done1 = true;
+                            evals -= nvalid - 1 - jj[k];
+                        } else {
+                            w1 = kernel_mode ? fast_exp2(kq1[k]) : al1[k] * T1;
+                            T1 = Tn;
+                            wsum1 += w1;
+                            ++count1;
+                        }
+                    }
+                    wb_warp[jj[k] * kWStride + lane] = pair_same ? w0 + w1 : w0;
+                    // the second pixel of a pair that straddles a segment boundary adds
+                    // its weight to its own slot directly
+                    if (!pair_same && w1 != 0.f && slot1 >= 0 && a.accumulate)
+                        flush_slot(a, sm, slot1, c * 32 + jj[k], w1);
                 }
             }
             __syncwarp();
-            // B: lane = Gaussian c*32+lane, sum over this warp's 32 positions per slot
+            // B: lane = Gaussian c*32+lane, sum over this warp's 32 lanes per slot
             if (a.accumulate && gs != -1 && ((mask >> lane) & 1u)) {
                 const float *row = wb_warp + lane * kWStride;
                 const int gi = c * 32 + lane;
@@ -369,10 +419,10 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
                     const float acc = (p0 + p1) + (p2 + p3);
                     if (acc != 0.f) flush_slot(a, sm, gs, gi, acc);
                 } else {
-                    int cur = sm.slot_of_pos[w * 32];
+                    int cur = sm.slot_lane[w * 32];
                     float acc = 0.f;
                     for (int q = 0; q < 32; ++q) {
-                        const int sl = sm.slot_of_pos[w * 32 + q];
+                        const int sl = sm.slot_lane[w * 32 + q];
                         if (sl != cur) {
                             if (cur >= 0 && acc != 0.f) flush_slot(a, sm, cur, gi, acc);
                             acc = 0.f;
@@ -421,13 +471,19 @@ __global__ void __launch_bounds__(kThreads, 14) composite_k(const CompositeArgs 
     }
     if (a.accumulate && a.recs) flush_queue(a, sm, tid);
 
-    if (inside) {
-        const int64_t pi = (int64_t)py * W + px;
-        if (a.dbg_T) a.dbg_T[pi] = T;
-        if (a.dbg_wsum) a.dbg_wsum[pi] = wsum;
-        if (a.dbg_count) a.dbg_count[pi] = count;
+    if (inside0) {
+        const int64_t pi = (int64_t)py0 * W + px0;
+        if (a.dbg_T) a.dbg_T[pi] = T0;
+        if (a.dbg_wsum) a.dbg_wsum[pi] = wsum0;
+        if (a.dbg_count) a.dbg_count[pi] = count0;
     }
-    unsigned long long cnt = (unsigned long long)count, ev = (unsigned long long)evals;
+    if (inside1) {
+        const int64_t pi = (int64_t)py1 * W + px1;
+        if (a.dbg_T) a.dbg_T[pi] = T1;
+        if (a.dbg_wsum) a.dbg_wsum[pi] = wsum1;
+        if (a.dbg_count) a.dbg_count[pi] = count1;
+    }
+    unsigned long long cnt = (unsigned long long)(count0 + count1), ev = (unsigned long long)evals;
     for (int o = 16; o; o >>= 1) {
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         ev += __shfl_xor_sync(0xffffffffu, ev, o);
