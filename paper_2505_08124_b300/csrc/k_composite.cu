@@ -139,6 +139,9 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// kKernel: record Eq. 2's kernel exp(-q/2) instead of alpha * T; kDebug: keep the
+// per-pixel weight sums and counts of the diagnostic render.
+template <bool kKernel, bool kDebug>
 __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
@@ -234,7 +237,6 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
     float T0 = 1.f, T1 = 1.f, wsum0 = 0.f, wsum1 = 0.f;
     int count0 = 0, count1 = 0, evals = 0;
     bool done0 = !inside0, done1 = !inside1;
-    const bool kernel_mode = a.weight_mode == SLAG_WEIGHT_KERNEL;
 
     // this tile's candidates: the depth-ordered list of its bin (a 2^shift x
     // 2^shift square of tiles); the Gaussians whose tile rectangle holds this tile
@@ -370,30 +372,27 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (jj[k] < 0) break;
-                    float w0 = 0.f, w1 = 0.f;
-                    if (!done0 && al0[k] > 0.f) {
-                        const float Tn = T0 - al0[k] * T0;
-                        if (Tn < 1e-4f) {
-                            done0 = true;
-                            evals -= nvalid - 1 - jj[k];
-                        } else {
-                            w0 = kernel_mode ? fast_exp2(kq0[k]) : al0[k] * T0;
-                            T0 = Tn;
-                            wsum0 += w0;
-                            ++count0;
-                        }
-                    }
-                    if (!done1 && al1[k] > 0.f) {
-                        const float Tn = T1 - al1[k] * T1;
-                        if (Tn < 1e-4f) {
-                            done1 = true;
-                            evals -= nvalid - 1 - jj[k];
-                        } else {
-                            w1 = kernel_mode ? fast_exp2(kq1[k]) : al1[k] * T1;
-                            T1 = Tn;
-                            wsum1 += w1;
-                            ++count1;
-                        }
+                    // predicated, branch-free: a Gaussian contributes unless the pixel has
+                    // stopped or alpha is below the floor; the one whose (1 - alpha) would
+                    // take T below 1e-4 stops the pixel and contributes nothing
+                    const float Tn0 = T0 - al0[k] * T0, Tn1 = T1 - al1[k] * T1;
+                    const bool act0 = !done0 && al0[k] > 0.f, act1 = !done1 && al1[k] > 0.f;
+                    const bool stop0 = act0 && Tn0 < 1e-4f, stop1 = act1 && Tn1 < 1e-4f;
+                    const bool take0 = act0 && !stop0, take1 = act1 && !stop1;
+                    float w0 = kKernel ? fast_exp2(kq0[k]) : al0[k] * T0;
+                    float w1 = kKernel ? fast_exp2(kq1[k]) : al1[k] * T1;
+                    w0 = take0 ? w0 : 0.f;
+                    w1 = take1 ? w1 : 0.f;
+                    T0 = take0 ? Tn0 : T0;
+                    T1 = take1 ? Tn1 : T1;
+                    done0 = done0 || stop0;
+                    done1 = done1 || stop1;
+                    count0 += take0 ? 1 : 0;
+                    count1 += take1 ? 1 : 0;
+                    evals -= ((stop0 ? 1 : 0) + (stop1 ? 1 : 0)) * (nvalid - 1 - jj[k]);
+                    if (kDebug) {
+                        wsum0 += w0;
+                        wsum1 += w1;
                     }
                     wb_warp[jj[k] * kWStride + lane] = pair_same ? w0 + w1 : w0;
                     // the second pixel of a pair that straddles a segment boundary adds
@@ -497,11 +496,18 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
 void launch_composite(const CompositeArgs &a, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(composite_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+        cudaFuncSetAttribute(composite_k<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+        cudaFuncSetAttribute(composite_k<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+        cudaFuncSetAttribute(composite_k<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+        cudaFuncSetAttribute(composite_k<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         attr_set = true;
     }
     const int tiles = a.cam.tiles_x * a.cam.tiles_y;
-    composite_k<<<tiles * kSubTiles, kThreads, sizeof(Smem), st>>>(a); note_launch();
+    const bool kernel = a.weight_mode == SLAG_WEIGHT_KERNEL;
+    const bool debug = a.dbg_T || a.dbg_wsum || a.dbg_count;
+    auto *kfn = kernel ? (debug ? composite_k<true, true> : composite_k<true, false>)
+                       : (debug ? composite_k<false, true> : composite_k<false, false>);
+    kfn<<<tiles * kSubTiles, kThreads, sizeof(Smem), st>>>(a); note_launch();
 }
 
 }  // namespace slag
