@@ -2,6 +2,10 @@
 // over the Gaussians with sum w > 0 and a non-zero embedding; results by
 // descending score, ties to the lower Gaussian index.
 //
+// The candidates are rows rows[0..n) of E when a row list is given (the
+// touched Gaussians in increasing order, so ties still go to the lower
+// Gaussian index), else rows 0..n; results are row numbers of E.
+//
 // Stage 1: a CTA scores 64 queries x 128 Gaussians (K = D in steps of 16,
 // a 4 x 8 register tile per thread) and keeps, per query, the best
 // min(k, 128) of its 128 Gaussians as candidates. Stage 2: one CTA per query
@@ -25,7 +29,8 @@ __device__ __forceinline__ bool better(float s, uint32_t i, float s2, uint32_t i
 
 __global__ void __launch_bounds__(256) score_tile_k(const float *__restrict__ Q, int32_t B,
                                                     const float *__restrict__ E, const float *__restrict__ inv_norm,
-                                                    int64_t n, int32_t D, int32_t kk, float *__restrict__ cand_s,
+                                                    const uint32_t *__restrict__ rows, int64_t n, int32_t D,
+                                                    int32_t kk, float *__restrict__ cand_s,
                                                     uint32_t *__restrict__ cand_i, int32_t ntiles) {
     __shared__ __align__(16) float Qs[kKD][kQB + 4];
     __shared__ __align__(16) float Es[kKD][kGB + 4];
@@ -55,7 +60,10 @@ __global__ void __launch_bounds__(256) score_tile_k(const float *__restrict__ Q,
             const int e = tid + r * 256;
             const int gl = e >> 2, d4 = e & 3;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (g0 + gl < n) v = *reinterpret_cast<const float4 *>(E + (g0 + gl) * D + d0 + d4 * 4);
+            if (g0 + gl < n) {
+                const int64_t row = rows ? (int64_t)rows[g0 + gl] : g0 + gl;
+                v = *reinterpret_cast<const float4 *>(E + row * D + d0 + d4 * 4);
+            }
             Es[d4 * 4 + 0][gl] = v.x;
             Es[d4 * 4 + 1][gl] = v.y;
             Es[d4 * 4 + 2][gl] = v.z;
@@ -80,7 +88,7 @@ __global__ void __launch_bounds__(256) score_tile_k(const float *__restrict__ Q,
     for (int j = 0; j < 8; ++j) {
         const int gl = j < 4 ? tg * 4 + j : 64 + tg * 4 + (j - 4);
         const int64_t g = g0 + gl;
-        const float inv = g < n ? inv_norm[g] : 0.f;
+        const float inv = g < n ? inv_norm[rows ? (int64_t)rows[g] : g] : 0.f;
 #pragma unroll
         for (int i = 0; i < 4; ++i) Sc[tq * 4 + i][gl] = inv > 0.f ? acc[i][j] * inv : -INFINITY;
     }
@@ -120,7 +128,8 @@ __global__ void __launch_bounds__(256) score_tile_k(const float *__restrict__ Q,
 }
 
 __global__ void __launch_bounds__(256) merge_k(const float *__restrict__ cand_s, const uint32_t *__restrict__ cand_i,
-                                               int64_t per_query, int32_t k, int64_t *__restrict__ out_ids,
+                                               int64_t per_query, int32_t k, const uint32_t *__restrict__ rows,
+                                               int64_t *__restrict__ out_ids,
                                                float *__restrict__ out_scores, int32_t *__restrict__ out_count) {
     __shared__ float ws[8];
     __shared__ uint32_t wi[8];
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(256) merge_k(const float *__restrict__ cand_s,
                 if (better(ws[c], wi[c], s, i)) { s = ws[c]; i = wi[c]; }
             last_s = s;
             last_i = i;
-            out_ids[(int64_t)q * k + r] = i == 0xffffffffu ? -1 : (int64_t)i;
+            out_ids[(int64_t)q * k + r] = i == 0xffffffffu ? -1 : (rows ? (int64_t)rows[i] : (int64_t)i);
             out_scores[(int64_t)q * k + r] = i == 0xffffffffu ? 0.f : s;
         }
         __syncthreads();
@@ -185,18 +194,45 @@ size_t query_cand_entries(int32_t B, int64_t n, int32_t k) {
 }
 
 void launch_query_merge(const float *cand_s, const uint32_t *cand_i, int64_t per_query, int32_t B, int32_t k,
-                        int64_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t st) {
-    merge_k<<<B, 256, 0, st>>>(cand_s, cand_i, per_query, k, out_ids, out_scores, out_count); note_launch();
+                        const uint32_t *rows, int64_t *out_ids, float *out_scores, int32_t *out_count,
+                        cudaStream_t st) {
+    merge_k<<<B, 256, 0, st>>>(cand_s, cand_i, per_query, k, rows, out_ids, out_scores, out_count); note_launch();
 }
 
-void launch_query_topk(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n, int32_t D,
-                       int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids, float *out_scores,
-                       int32_t *out_count, cudaStream_t st) {
+void launch_query_topk(const float *Q, int32_t B, const float *E, const float *inv_norm, const uint32_t *rows,
+                       int64_t n, int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
+                       float *out_scores, int32_t *out_count, cudaStream_t st) {
     const int64_t ntiles = (n + kGB - 1) / kGB;
     const int32_t kk = k < kGB ? k : kGB;
-    dim3 grid((unsigned)ntiles, (unsigned)((B + kQB - 1) / kQB));
-    score_tile_k<<<grid, 256, 0, st>>>(Q, B, E, inv_norm, n, D, kk, cand_s, cand_i, (int32_t)ntiles); note_launch();
-    merge_k<<<B, 256, 0, st>>>(cand_s, cand_i, ntiles * kk, k, out_ids, out_scores, out_count); note_launch();
+    if (ntiles > 0) {
+        dim3 grid((unsigned)ntiles, (unsigned)((B + kQB - 1) / kQB));
+        score_tile_k<<<grid, 256, 0, st>>>(Q, B, E, inv_norm, rows, n, D, kk, cand_s, cand_i, (int32_t)ntiles); note_launch();
+    }
+    merge_k<<<B, 256, 0, st>>>(cand_s, cand_i, ntiles * kk, k, rows, out_ids, out_scores, out_count); note_launch();
+}
+
+namespace {
+
+__global__ void touched_flags_k(const float *__restrict__ inv_norm, int64_t n, uint32_t *__restrict__ flags) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) flags[g] = inv_norm[g] > 0.f ? 1u : 0u;
+}
+
+__global__ void touched_rows_k(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos, int64_t n,
+                               uint32_t *__restrict__ rows) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n && flags[g]) rows[pos[g]] = (uint32_t)g;
+}
+
+}  // namespace
+
+void launch_touched_rows(const float *inv_norm, int64_t n, uint32_t *flags, uint32_t *pos, uint32_t *rows,
+                         unsigned long long *d_count, SortScratch &scratch, cudaStream_t st) {
+    if (n <= 0) return;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    touched_flags_k<<<blocks, 256, 0, st>>>(inv_norm, n, flags); note_launch();
+    exclusive_scan_u32(flags, pos, n, d_count, scratch, st);
+    touched_rows_k<<<blocks, 256, 0, st>>>(flags, pos, n, rows); note_launch();
 }
 
 }  // namespace slag

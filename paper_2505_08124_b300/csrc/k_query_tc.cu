@@ -177,7 +177,8 @@ __device__ __forceinline__ float select32(const float (&v)[32], int j) {
 
 __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restrict__ Q, int32_t B,
                                                             const float *__restrict__ E,
-                                                            const float *__restrict__ inv_norm, int64_t n,
+                                                            const float *__restrict__ inv_norm,
+                                                            const uint32_t *__restrict__ rows, int64_t n,
                                                             int32_t D, int32_t k, int32_t nsplit,
                                                             float *__restrict__ cand_s,
                                                             uint32_t *__restrict__ cand_i, uint32_t *err) {
@@ -240,7 +241,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
                 if (q0 + row < B) v[j] = __ldg(reinterpret_cast<const float4 *>(Q + (int64_t)(q0 + row) * D + d0 + kq * 4));
             } else {
                 const int64_t g = g0 + (row - kM);
-                if (g < n) v[j] = __ldg(reinterpret_cast<const float4 *>(E + g * D + d0 + kq * 4));
+                if (g < n) {
+                    const int64_t er = rows ? (int64_t)__ldg(rows + g) : g;
+                    v[j] = __ldg(reinterpret_cast<const float4 *>(E + er * D + d0 + kq * 4));
+                }
             }
         }
     };
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
         const int64_t g0 = (t_begin + gc / nchunk) * kN;
         for (int i = tid; i < kN; i += kThreadsTC) {
             const int64_t g = g0 + i;
-            const float inv = g < n ? inv_norm[g] : 0.f;
+            const float inv = g < n ? inv_norm[rows ? (int64_t)rows[g] : g] : 0.f;
             sinv[i] = inv > 0.f ? inv : __int_as_float(0x7fc00000);   // NaN: never passes a threshold
         }
         __syncthreads();
@@ -392,19 +396,23 @@ int32_t query_tc_splits(int32_t B, int64_t n) {
     return (int32_t)s;
 }
 
-void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n, int32_t D,
-                          int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids, float *out_scores,
-                          int32_t *out_count, uint32_t *err, cudaStream_t st) {
+void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, const uint32_t *rows,
+                          int64_t n, int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
+                          float *out_scores, int32_t *out_count, uint32_t *err, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(query_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem());
         attr_set = true;
     }
+    const int32_t kk = k < kTopTC ? k : kTopTC;
+    if (n <= 0) {   // no candidates: every query gets an empty result
+        launch_query_merge(cand_s, cand_i, 0, B, k, rows, out_ids, out_scores, out_count, st);
+        return;
+    }
     const int32_t nsplit = query_tc_splits(B, n);
     dim3 grid((unsigned)((B + kM - 1) / kM), (unsigned)nsplit);
-    query_tc_k<<<grid, kThreadsTC, tc_smem(), st>>>(Q, B, E, inv_norm, n, D, k, nsplit, cand_s, cand_i, err); note_launch();
-    const int32_t kk = k < kTopTC ? k : kTopTC;
-    launch_query_merge(cand_s, cand_i, (int64_t)nsplit * kk, B, k, out_ids, out_scores, out_count, st);
+    query_tc_k<<<grid, kThreadsTC, tc_smem(), st>>>(Q, B, E, inv_norm, rows, n, D, k, nsplit, cand_s, cand_i, err); note_launch();
+    launch_query_merge(cand_s, cand_i, (int64_t)nsplit * kk, B, k, rows, out_ids, out_scores, out_count, st);
 }
 
 }  // namespace slag

@@ -115,6 +115,7 @@ struct slag_ctx {
         ViewCounters v;                      // validation at create, the last view at finalize
         unsigned long long totals[4];
         unsigned long long touched;
+        unsigned long long n_q;              // query candidates (touched rows)
         uint32_t tc_err;
         uint32_t pad;
     } *hc = nullptr;                         // pinned host
@@ -136,6 +137,9 @@ struct slag_ctx {
     // outputs
     float *E = nullptr, *inv_norm = nullptr, *wsum = nullptr;
     unsigned long long *touched = nullptr;
+    uint32_t *qrows = nullptr, *qflags = nullptr, *qpos = nullptr;   // query candidates: touched rows of E
+    unsigned long long *d_nq = nullptr;
+    int64_t n_q = 0;
     bool finalized = false;
 
     // queries
@@ -529,6 +533,7 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     // accumulators and outputs
     CA(dalloc(&ctx->s_hi, n)); CA(dalloc(&ctx->s_lo, n)); CA(dalloc(&ctx->s_ovf, n));
     CA(dalloc(&ctx->E, n * (int64_t)ctx->D)); CA(dalloc(&ctx->inv_norm, n)); CA(dalloc(&ctx->wsum, n));
+    CA(dalloc(&ctx->qrows, n)); CA(dalloc(&ctx->qflags, n)); CA(dalloc(&ctx->qpos, n)); CA(dalloc(&ctx->d_nq, 1));
     CA(dalloc(&ctx->bstart, (n + kBlockG - 1) / kBlockG)); CA(dalloc(&ctx->bend, (n + kBlockG - 1) / kBlockG));
     for (int i = 0; i < kSlots; ++i) launch_hash_init(ctx->slot[i].hash, n, st);
     CA(cudaMemsetAsync(ctx->s_hi, 0, sizeof(float) * n, st));
@@ -754,15 +759,19 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     g.touched = ctx->touched;
     span_begin(ctx, SLAG_STAGE_AGGREGATE, st);
     launch_aggregate(g, nblocks, st);
+    // query candidates: the rows of E with a non-zero embedding, in caller order
+    launch_touched_rows(ctx->inv_norm, n, ctx->qflags, ctx->qpos, ctx->qrows, ctx->d_nq, ctx->scratch, st);
     span_end(ctx, st);
     CK(cudaGetLastError());
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (out_emb) CK(cudaMemcpyAsync(out_emb, ctx->E, sizeof(float) * (size_t)(n * ctx->D), kind, st));
     if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, kind, st));
     CK(cudaMemcpyAsync(&ctx->hc->touched, ctx->touched, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ctx->hc->n_q, ctx->d_nq, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     spans_resolve(ctx);
     ctx->stats.touched = (int64_t)ctx->hc->touched;
+    ctx->n_q = (int64_t)ctx->hc->n_q;
     ctx->finalized = true;
     return SLAG_OK;
 }
@@ -785,8 +794,9 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
     }
     if (((uintptr_t)dQ & 15u) != 0) return fail(ctx, SLAG_ERR_INVALID_ARG, "Q must be 16-byte aligned");
     const bool tc = query_tc_supported(ctx->D, k);
-    const int64_t nc = tc ? (int64_t)B * query_tc_splits(B, ctx->n) * (k < 16 ? k : 16)
-                          : (int64_t)query_cand_entries(B, ctx->n, k);
+    const int64_t nq = ctx->n_q;
+    const int64_t nc = tc ? (int64_t)B * (nq > 0 ? query_tc_splits(B, nq) : 0) * (k < 16 ? k : 16)
+                          : (int64_t)query_cand_entries(B, nq, k);
     if (nc > ctx->cand_cap) {
         int64_t c1 = ctx->cand_cap, c2 = ctx->cand_cap;
         CK(grow(ctx->cand_s, c1, nc, st));
@@ -810,11 +820,11 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
     }
     span_begin(ctx, SLAG_STAGE_QUERY, st);
     if (tc)
-        launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i,
+        launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s, ctx->cand_i,
                              ids, scores, cnt, ctx->tc_err, st);
     else
-        launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->n, ctx->D, k, ctx->cand_s, ctx->cand_i, ids, scores,
-                          cnt, st);
+        launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s, ctx->cand_i, ids,
+                          scores, cnt, st);
     span_end(ctx, st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&ctx->hc->tc_err, ctx->tc_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -888,6 +898,7 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->log_key); dfree(ctx->log_key_alt); dfree(ctx->log_w); dfree(ctx->log_w_alt);
     dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
     dfree(ctx->table); dfree(ctx->E); dfree(ctx->inv_norm); dfree(ctx->wsum);
+    dfree(ctx->qrows); dfree(ctx->qflags); dfree(ctx->qpos); dfree(ctx->d_nq);
     dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);
     scratch_free(ctx->scratch);
     for (auto &sp : ctx->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }

@@ -244,18 +244,24 @@ void launch_aggregate(const AggArgs &a, int64_t nblocks, cudaStream_t st);
 
 // k_query.cu
 size_t query_cand_entries(int32_t B, int64_t n, int32_t k);
-// per query: the best k of `per_query` candidates (score, index; index 0xffffffff = none)
+// per query: the best k of `per_query` candidates (score, index; index 0xffffffff = none);
+// with a row list, result ids are rows[index]
 void launch_query_merge(const float *cand_s, const uint32_t *cand_i, int64_t per_query, int32_t B, int32_t k,
-                        int64_t *out_ids, float *out_scores, int32_t *out_count, cudaStream_t st);
-void launch_query_topk(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n,
-                       int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
+                        const uint32_t *rows, int64_t *out_ids, float *out_scores, int32_t *out_count,
+                        cudaStream_t st);
+// The candidates are rows rows[0..n) of E (rows nullable: rows 0..n); ids returned are E rows.
+void launch_query_topk(const float *Q, int32_t B, const float *E, const float *inv_norm, const uint32_t *rows,
+                       int64_t n, int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
                        float *out_scores, int32_t *out_count, cudaStream_t st);
+// rows[0..*d_count) = the Gaussians with inv_norm > 0, in increasing order (flags, pos: n each)
+void launch_touched_rows(const float *inv_norm, int64_t n, uint32_t *flags, uint32_t *pos, uint32_t *rows,
+                         unsigned long long *d_count, SortScratch &scratch, cudaStream_t st);
 
 // k_query_tc.cu: tensor-core scores (3xTF32 on tcgen05) for k <= 16 and D % 32 == 0
 bool query_tc_supported(int32_t D, int32_t k);
 int32_t query_tc_splits(int32_t B, int64_t n);
-void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, int64_t n, int32_t D,
-                          int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids, float *out_scores,
-                          int32_t *out_count, uint32_t *err, cudaStream_t st);
+void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, const uint32_t *rows,
+                          int64_t n, int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
+                          float *out_scores, int32_t *out_count, uint32_t *err, cudaStream_t st);
 
 }  // namespace slag

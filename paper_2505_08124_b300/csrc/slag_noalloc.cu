@@ -79,7 +79,7 @@ extern "C" slag_status slag_noalloc_query_topk(const float *E, int64_t n, int32_
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int64_t threads = n * 32;
     row_inv_norm_k<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(E, wsum, n, dim, inv_norm); slag::note_launch();
-    slag::launch_query_topk(Q, B, E, inv_norm, n, dim, k, cand_s, cand_i, out_ids, out_scores, out_count, st);
+    slag::launch_query_topk(Q, B, E, inv_norm, nullptr, n, dim, k, cand_s, cand_i, out_ids, out_scores, out_count, st);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SLAG_OK : SLAG_ERR_CUDA;
 }

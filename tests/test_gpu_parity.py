@@ -250,6 +250,22 @@ def test_query_more_than_candidates(slag):
         assert len(set(ids.tolist())) == n_valid
 
 
+@pytest.mark.parametrize("k", [5, 300])   # tensor-core path and CUDA-core path
+def test_query_without_candidates(slag, k):
+    # a view whose pixels all lie outside every segment touches no Gaussian: every
+    # query has an empty result
+    s = synth.small_scene(23, 500, 1, 64, 64, 3, dim=128)
+    v = s.view(0)
+    with slag.Lifter(s.gaussians, dim=128) as L:
+        L.add_view(v.camera, np.full_like(v.seg, -1), v.table)
+        E, w = L.finalize()
+        assert not w.any() and not E.any()
+        Q = np.tile(v.table[:1] / np.linalg.norm(v.table[0]), (3, 1)).astype(np.float32)
+        ids, sc, cnt = L.query_batch(Q, k)
+        assert (cnt == 0).all()
+        assert (ids == -1).all()
+
+
 # ----------------------------------------------------------------------------
 # errors
 # ----------------------------------------------------------------------------
