@@ -9,11 +9,9 @@
 //
 // At finalize, the log is sorted by (Gaussian block of 128, column,
 // Gaussian), so that each block of 128 spatially adjacent Gaussians (Morton
-// order) sees its distinct columns in order. The numerator of a block is the
-// dense contraction W_block (128 x K_block) x E (K_block x D), computed here
-// in chunks of 32 columns; rows are then divided by the denominator and
-// written in the caller's Gaussian order, with the inverse row norm kept for
-// cosine queries.
+// order) sees its distinct columns in order; the distinct columns of each
+// block are listed here. The contraction itself (W_block x E_cols on the
+// tensor cores) is in k_aggregate_tc.cu.
 #include "slag_internal.cuh"
 
 namespace slag {
@@ -125,109 +123,6 @@ __global__ void uniques_k(const uint64_t *__restrict__ keys, const uint32_t *__r
     if (i == Z - 1 || (uint32_t)(keys[i + 1] >> 39) != blk) bend[blk] = (uint32_t)(i + 1);
 }
 
-constexpr int kKC = 32;    // columns per chunk
-constexpr int kDS = 128;   // embedding dims per slice
-
-__global__ void __launch_bounds__(256, 1) aggregate_k(const AggArgs a) {
-    __shared__ __align__(16) float Wd[kKC][kBlockG];
-    __shared__ __align__(16) float Es[kKC][kDS];
-    const int tid = threadIdx.x;
-    const int ty = tid >> 4, tx = tid & 15;
-    const int64_t b = blockIdx.x;
-    const uint32_t ts = a.bstart[b], te = a.bend[b];
-    const bool any = ts < te;
-    // unique (block, column) index of triple t = exclusive count + own flag - 1; a block's first
-    // triple always starts a new column
-    const uint32_t u0 = any ? a.uidx[ts] : 0u, u1 = any ? a.uidx[te - 1] + a.flags[te - 1] : 0u;
-
-    float S[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int64_t g = b * kBlockG + ty * 8 + i;
-        S[i] = g < a.n ? (a.s_hi[g] + a.s_lo[g]) + a.s_ovf[g] : 0.f;
-    }
-    float norm2[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) norm2[i] = 0.f;
-
-    for (int ds = 0; ds < a.D; ds += kDS) {
-        float acc[8][8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-        for (uint32_t uc = u0; uc < u1; uc += kKC) {
-            const uint32_t nk = min((uint32_t)kKC, u1 - uc);
-            const uint32_t t0 = a.ustart[uc];
-            const uint32_t t1 = (uc + kKC < u1) ? a.ustart[uc + kKC] : te;
-            float4 *wz = reinterpret_cast<float4 *>(&Wd[0][0]);
-            for (int e = tid; e < kKC * kBlockG / 4; e += 256) wz[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-            __syncthreads();
-            for (uint32_t t = t0 + tid; t < t1; t += 256) {
-                const uint64_t key = a.keys[t];
-                const uint32_t lc = a.uidx[t] + a.flags[t] - 1u - uc;
-                atomicAdd(&Wd[lc][(int)(key & 127u)], a.w[t]);
-            }
-            for (int e = tid; e < kKC * kDS / 4; e += 256) {
-                const int lc = e >> 5, d4 = e & 31;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if ((uint32_t)lc < nk) {
-                    const float *row = a.table + (int64_t)a.ucol[uc + lc] * a.D + ds;
-                    v = reinterpret_cast<const float4 *>(row)[d4];
-                }
-                reinterpret_cast<float4 *>(&Es[lc][0])[d4] = v;
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int k = 0; k < kKC; ++k) {
-                const float4 a0 = *reinterpret_cast<const float4 *>(&Wd[k][ty * 8]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&Wd[k][ty * 8 + 4]);
-                const float4 b0 = *reinterpret_cast<const float4 *>(&Es[k][tx * 4]);
-                const float4 b1 = *reinterpret_cast<const float4 *>(&Es[k][64 + tx * 4]);
-                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t g = b * kBlockG + ty * 8 + i;
-            if (g >= a.n) continue;
-            const float inv = S[i] > 0.f ? 1.f / S[i] : 0.f;
-            float v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                v[j] = acc[i][j] * inv;
-                norm2[i] = fmaf(v[j], v[j], norm2[i]);
-            }
-            float *row = a.E + (int64_t)a.orig_of_int[g] * a.D + ds;
-            reinterpret_cast<float4 *>(row)[tx] = make_float4(v[0], v[1], v[2], v[3]);
-            reinterpret_cast<float4 *>(row + 64)[tx] = make_float4(v[4], v[5], v[6], v[7]);
-        }
-    }
-    // row norms: the 16 threads sharing rows ty*8.. are lanes (ty & 1) * 16 + tx of one warp
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        for (int o = 8; o; o >>= 1) norm2[i] += __shfl_xor_sync(0xffffffffu, norm2[i], o);
-    if (tx == 0) {
-        unsigned long long touched = 0;
-        for (int i = 0; i < 8; ++i) {
-            const int64_t g = b * kBlockG + ty * 8 + i;
-            if (g >= a.n) continue;
-            const uint32_t o = a.orig_of_int[g];
-            const bool ok = S[i] > 0.f && norm2[i] > 0.f;
-            a.inv_norm[o] = ok ? 1.f / sqrtf(norm2[i]) : 0.f;
-            a.wsum[o] = S[i];
-            touched += S[i] > 0.f ? 1 : 0;
-        }
-        if (touched) atomicAdd(a.touched, touched);
-    }
-}
-
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -265,11 +160,6 @@ void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t 
                     uint32_t *ustart, uint32_t *bstart, uint32_t *bend, cudaStream_t st) {
     if (Z <= 0) return;
     uniques_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys, flags, uidx, Z, ucol, ustart, bstart, bend); note_launch();
-}
-
-void launch_aggregate(const AggArgs &a, int64_t nblocks, cudaStream_t st) {
-    if (nblocks <= 0) return;
-    aggregate_k<<<(unsigned)nblocks, 256, 0, st>>>(a); note_launch();
 }
 
 }  // namespace slag

@@ -22,6 +22,7 @@
 // Every wait on an mbarrier is bounded (about one second of globaltimer);
 // on timeout the kernel sets *err, stops issuing work and releases its TMEM.
 #include "slag_internal.cuh"
+#include "tc_util.cuh"
 
 namespace slag {
 
@@ -40,7 +41,7 @@ constexpr uint32_t kTmemCols = 256;
 constexpr int kABytes = kM * kKC * 4;   // 32 KB
 constexpr int kBBytes = kN * kKC * 4;   // 16 KB
 constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr int kSBO = 1024;              // bytes between 8-row swizzle atoms
+constexpr int kSBO = tc::kSBO;          // bytes between 8-row swizzle atoms
 constexpr int kLoadsPerThread = (kM + kN) * (kKC / 4) / kThreadsTC;   // float4 per thread per chunk
 
 struct __align__(8) TcCtl {
@@ -49,116 +50,26 @@ struct __align__(8) TcCtl {
     uint32_t abort;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using tc::core_off;
+using tc::gtimer;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::mma_commit;
+using tc::smem_desc;
+using tc::smem_u32;
+using tc::split_store;
+using tc::tmem_ld32;
 
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase of `parity` to complete; false after ~1 s.
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (gtimer() - t0 > 1000000000ull) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle (layout type 2),
-// atoms 1024-byte aligned (base offset 0); the leading offset is unused for
-// swizzled K-major operands and set to 16 bytes.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version of the 5th-generation tensor cores
-    d |= (uint64_t)2 << 61;   // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, N = kN, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                            ((uint32_t)(kMmaM >> 4) << 24);
-static_assert(kMmaM == 128 && kN % 16 == 0 && kN <= 256, "cta_group::1 tf32 MMA shape");
+constexpr uint32_t kIdesc = tc::idesc_tf32<kN>();
+static_assert(kMmaM == 128, "cta_group::1 tf32 MMA shape");
 static_assert(kKC * 4 == 128, "a chunk row is one 128-byte swizzle row");
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
-        "}\n" ::"r"(tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    tc::mma_tf32(tmem, adesc, bdesc, kIdesc, accum);
 }
 
 __device__ __forceinline__ bool better(float s, uint32_t i, float s2, uint32_t i2) {
     return s > s2 || (s == s2 && i < i2);
-}
-
-// Byte offset of the 16-byte chunk kq (4 TF32 values) of a row in a 128-byte-swizzled K-major tile.
-__device__ __forceinline__ uint32_t core_off(int row, int kq) {
-    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((kq ^ (row & 7)) << 4));
-}
-
-__device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo, uint32_t off, float4 v) {
-    float4 h, l;
-    h.x = to_tf32(v.x); l.x = to_tf32(v.x - h.x);
-    h.y = to_tf32(v.y); l.y = to_tf32(v.y - h.y);
-    h.z = to_tf32(v.z); l.z = to_tf32(v.z - h.z);
-    h.w = to_tf32(v.w); l.w = to_tf32(v.w - h.w);
-    *reinterpret_cast<float4 *>(hi + off) = h;
-    *reinterpret_cast<float4 *>(lo + off) = l;
 }
 
 // v[j] for a lane-varying j, by a binary tree of selects (no local memory)

@@ -119,7 +119,7 @@ struct slag_ctx {
         uint32_t tc_err;
         uint32_t pad;
     } *hc = nullptr;                         // pinned host
-    uint32_t *tc_err = nullptr;              // device: a tensor-core query kernel gave up waiting
+    uint32_t *tc_err = nullptr;              // device: a tensor-core kernel gave up waiting
 
     // triple log + finalize scratch
     uint64_t *log_key = nullptr, *log_key_alt = nullptr;
@@ -758,7 +758,7 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     g.wsum = ctx->wsum;
     g.touched = ctx->touched;
     span_begin(ctx, SLAG_STAGE_AGGREGATE, st);
-    launch_aggregate(g, nblocks, st);
+    launch_aggregate(g, nblocks, ctx->tc_err, st);
     // query candidates: the rows of E with a non-zero embedding, in caller order
     launch_touched_rows(ctx->inv_norm, n, ctx->qflags, ctx->qpos, ctx->qrows, ctx->d_nq, ctx->scratch, st);
     span_end(ctx, st);
@@ -768,7 +768,9 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, kind, st));
     CK(cudaMemcpyAsync(&ctx->hc->touched, ctx->touched, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&ctx->hc->n_q, ctx->d_nq, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ctx->hc->tc_err, ctx->tc_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (ctx->hc->tc_err) return fail(ctx, SLAG_ERR_TIMEOUT, "the tensor-core aggregation gave up waiting");
     spans_resolve(ctx);
     ctx->stats.touched = (int64_t)ctx->hc->touched;
     ctx->n_q = (int64_t)ctx->hc->n_q;

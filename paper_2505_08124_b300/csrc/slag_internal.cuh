@@ -240,7 +240,9 @@ struct AggArgs {
     float *wsum;                   // n, caller order
     unsigned long long *touched;
 };
-void launch_aggregate(const AggArgs &a, int64_t nblocks, cudaStream_t st);
+// k_aggregate_tc.cu: one CTA per block of 128 Gaussians on the tensor cores; *err is set
+// when a bounded wait gives up
+void launch_aggregate(const AggArgs &a, int64_t nblocks, uint32_t *err, cudaStream_t st);
 
 // k_query.cu
 size_t query_cand_entries(int32_t B, int64_t n, int32_t k);
