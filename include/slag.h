@@ -58,8 +58,15 @@ typedef enum {
  * below 1e-4 ends the pixel and is not counted). */
 enum { SLAG_WEIGHT_ALPHA_T = 0, SLAG_WEIGHT_KERNEL = 1 };
 
-/* Arithmetic of the aggregation. FP32: weights, features and sums in float32. */
-enum { SLAG_PREC_FP32 = 0 };
+/* Arithmetic of the aggregation (Aggregation, E_k formula): the per-view
+ * weights are always composited in float32 and Sum w is a compensated float32
+ * sum. FP32: the contraction of the weights with the segment embeddings runs
+ * at float32 accuracy (three-term TF32 split on the tensor cores). BF16: the
+ * weights and the segment embeddings enter the tensor cores as bfloat16 with
+ * float32 accumulation; the error against float64 is stated per result by the
+ * tests (cosine >= 1 - 1e-3 per touched Gaussian at the tested scales). No
+ * float64 is used on the GPU in either form. */
+enum { SLAG_PREC_FP32 = 0, SLAG_PREC_BF16 = 1 };
 
 /* The Gaussian set G = {G_1..G_N} (Method, Rasterizer_SLAG statement). */
 typedef struct {
@@ -84,7 +91,7 @@ typedef struct {
 
 typedef struct {
     int32_t dim;             /* D: embedding width, a multiple of 128, 128 .. 4096 */
-    int32_t precision;       /* SLAG_PREC_FP32 */
+    int32_t precision;       /* SLAG_PREC_FP32 or SLAG_PREC_BF16 */
     int32_t weight_mode;     /* SLAG_WEIGHT_ALPHA_T (default) or SLAG_WEIGHT_KERNEL */
     int32_t reserved;        /* must be 0 */
     void *cuda_stream;       /* cudaStream_t, NULL = legacy default stream */

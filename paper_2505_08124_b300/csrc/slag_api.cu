@@ -88,6 +88,7 @@ struct slag_ctx {
     int64_t n = 0;
     int32_t D = 0;
     int32_t weight_mode = 0;
+    int32_t precision = 0;
     std::string err;
 
     // Gaussians, internal (Morton) order
@@ -448,7 +449,7 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     if (g->n < 1 || g->n >= (1LL << 31)) return SLAG_ERR_INVALID_ARG;
     if (!g->means || !g->scales || !g->quats || !g->opacities) return SLAG_ERR_INVALID_ARG;
     if (opt->dim < 128 || opt->dim > 4096 || opt->dim % 128 != 0) return SLAG_ERR_INVALID_ARG;
-    if (opt->precision != SLAG_PREC_FP32) return SLAG_ERR_INVALID_ARG;
+    if (opt->precision != SLAG_PREC_FP32 && opt->precision != SLAG_PREC_BF16) return SLAG_ERR_INVALID_ARG;
     if (opt->weight_mode != SLAG_WEIGHT_ALPHA_T && opt->weight_mode != SLAG_WEIGHT_KERNEL) return SLAG_ERR_INVALID_ARG;
     if (opt->reserved != 0) return SLAG_ERR_INVALID_ARG;
 
@@ -466,6 +467,7 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     ctx->n = n;
     ctx->D = opt->dim;
     ctx->weight_mode = opt->weight_mode;
+    ctx->precision = opt->precision;
     ctx->stream = (cudaStream_t)opt->cuda_stream;
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(SLAG_ERR_CUDA);
     cudaStream_t st = ctx->stream;
@@ -757,6 +759,7 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     g.inv_norm = ctx->inv_norm;
     g.wsum = ctx->wsum;
     g.touched = ctx->touched;
+    g.bf16 = ctx->precision == SLAG_PREC_BF16 ? 1 : 0;
     span_begin(ctx, SLAG_STAGE_AGGREGATE, st);
     launch_aggregate(g, nblocks, ctx->tc_err, st);
     // query candidates: the rows of E with a non-zero embedding, in caller order

@@ -239,6 +239,7 @@ struct AggArgs {
     float *inv_norm;               // n, caller order
     float *wsum;                   // n, caller order
     unsigned long long *touched;
+    int bf16;                      // BF16 operands (FP32 accumulation) instead of the 3xTF32 split
 };
 // k_aggregate_tc.cu: one CTA per block of 128 Gaussians on the tensor cores; *err is set
 // when a bounded wait gives up

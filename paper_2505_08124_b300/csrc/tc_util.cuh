@@ -90,6 +90,27 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t
         : "memory");
 }
 
+// Instruction descriptor, kind::f16 with BF16 A and B (same type, as the MMA requires): D f32,
+// both K-major, M = 128, N.
+template <int N>
+constexpr uint32_t idesc_bf16() {
+    static_assert(N % 16 == 0 && N >= 16 && N <= 256, "cta_group::1 M = 128 MMA: N in [16, 256], multiple of 16");
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// K = 16 BF16 values (32 bytes of a 128-byte swizzled row) per MMA.
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");

@@ -21,6 +21,7 @@ ERR_INVALID_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY = 1, 2,
 _NAMES = {1: "INVALID_ARG", 2: "STATE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "CAPACITY"}
 WEIGHT_ALPHA_T, WEIGHT_KERNEL = 0, 1
 PREC_FP32 = 0
+PREC_BF16 = 1
 
 
 class SlagError(RuntimeError):
@@ -152,7 +153,7 @@ class Lifter:
     """One lifting context: a fixed Gaussian set, views added one at a time."""
 
     def __init__(self, gaussians, dim: int = 512, weight_mode: int = WEIGHT_ALPHA_T,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, precision: int = PREC_FP32):
         self._lib = load_library()
         self.n = int(gaussians.means.shape[0])
         self.dim = int(dim)
@@ -161,7 +162,7 @@ class Lifter:
         if len(dev) != 1:
             raise ValueError("Gaussian arrays must all be on the host or all on the device")
         g = CGaussians(self.n, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], dev.pop())
-        o = COptions(self.dim, PREC_FP32, int(weight_mode), 0, ctypes.c_void_p(stream) if stream else None)
+        o = COptions(self.dim, int(precision), int(weight_mode), 0, ctypes.c_void_p(stream) if stream else None)
         h = ctypes.c_void_p()
         rc = self._lib.slag_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h))
         if rc != OK:
