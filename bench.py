@@ -65,6 +65,7 @@ def _args():
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--views", type=int, default=0, help="use only the first V views (0 = all)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the BF16 form's line")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
@@ -359,6 +360,10 @@ def run_slag(a):
                                % (N_SM, FP32_LANES, sm_max),
                 "dominant_stage": dominant}
 
+    forms = None
+    if not a.no_forms:
+        forms = {"bf16": _bf16_form(S, torch, L, g, D, cams, d_seg, d_tab, d_Q, a, stream, dev, rank_max, ws)}
+
     cpu = None
     if rank == 0 and not a.no_cpu:
         cpu = _cpu_oracle_sample(scene, views, a.cpu_seconds)
@@ -378,6 +383,7 @@ def run_slag(a):
                "roofline": roofline,
                "cpu_baseline": cpu,
                "gpu_launches": gpu_launches,
+               "forms": forms,
                "stages_busy_ms_per_step": {k: v[2] / a.steps for k, v in prof.items()},
                "stages_span_ms_per_step": {k: v[0] / a.steps for k, v in prof.items()},
                "stats_per_step": stats}
@@ -385,6 +391,64 @@ def run_slag(a):
     L.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _bf16_form(S, torch, L, g, D, cams, d_seg, d_tab, d_Q, a, stream, dev, rank_max, ws):
+    """The BF16 form on the same workload: the same step with the contraction of the weights
+    and the segment embeddings in bfloat16 (float32 accumulation); its error is stated against
+    the float32 path's embeddings of the same job (1 - cosine per Gaussian with sum w >= 1e-3)
+    and its top-10 answers against the float32 path's (strict overlap, and tie-tolerant: an id
+    counts when its float32 cosine is within 1e-3 of the float32 10th best)."""
+    n = g.n
+    Lb = S.Lifter(g, dim=D, stream=stream.cuda_stream, precision=S.PREC_BF16)
+    ids_b = torch.empty((a.queries, a.k), dtype=torch.int64, device=dev)
+    sc_b = torch.empty((a.queries, a.k), dtype=torch.float32, device=dev)
+    cnt_b = torch.empty(a.queries, dtype=torch.int32, device=dev)
+    w_b = torch.empty(n, dtype=torch.float32, device=dev)
+
+    def step(lift, E_out, w_out, ids, sc, cnt):
+        lift.reset()
+        for c, sg, tb in zip(cams, d_seg, d_tab):
+            lift.add_view(c, sg, tb)
+        lift.finalize(E_out, w_out)
+        lift.query_batch(d_Q, a.k, ids, sc, cnt)
+
+    for _ in range(max(1, a.warmup)):
+        step(Lb, None, w_b, ids_b, sc_b, cnt_b)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step(Lb, None, w_b, ids_b, sc_b, cnt_b)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = rank_max(e0.elapsed_time(e1))
+    contrib = Lb.stats()["contributions"]
+
+    # error against the float32 path on this job
+    E_b = torch.empty((n, D), dtype=torch.float32, device=dev)
+    E_f = torch.empty((n, D), dtype=torch.float32, device=dev)
+    w_f = torch.empty(n, dtype=torch.float32, device=dev)
+    ids_f = torch.empty_like(ids_b)
+    step(Lb, E_b, w_b, ids_b, sc_b, cnt_b)
+    step(L, E_f, w_f, ids_f, torch.empty_like(sc_b), torch.empty_like(cnt_b))
+    torch.cuda.synchronize()
+    Lb.close()
+    ok = w_f >= 1e-3
+    Eb, Ef = E_b[ok].double(), E_f[ok].double()
+    cos = (Eb * Ef).sum(1) / (Eb.norm(dim=1) * Ef.norm(dim=1))
+    En = E_f.double() / E_f.double().norm(dim=1, keepdim=True).clamp_min(1e-300)
+    Qd = d_Q.double()
+    sb = torch.einsum("qkd,qd->qk", En[ids_b.clamp_min(0)], Qd)
+    sf = torch.einsum("qkd,qd->qk", En[ids_f.clamp_min(0)], Qd)
+    tie = (sb >= sf.min(dim=1, keepdim=True).values - 1e-3).double().mean().item()
+    strict = float(np.mean([len(set(x) & set(y)) / a.k for x, y in zip(ids_b.tolist(), ids_f.tolist())]))
+    return {"value": job_rate(contrib * a.steps, ws, ms / 1e3), "unit": UNIT, "ms_per_step": ms / a.steps,
+            "views_per_s": job_rate(len(cams) * a.steps, ws, ms / 1e3), "dtype": "bf16 operands, f32 accumulate",
+            "cos_err_vs_fp32": {"max": float((1 - cos).max().item()), "mean": float((1 - cos).mean().item()),
+                                "gaussians": int(ok.sum().item())},
+            "top10_agree_vs_fp32": {"tie_tolerant": tie, "strict": strict}}
 
 
 def main():
