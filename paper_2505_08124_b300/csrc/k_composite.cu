@@ -57,8 +57,8 @@ constexpr int kWStride = 33;
 constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2(1/255)
 
 struct Smem {
-    float4 rec_a[kBatch];                 // (mu'x, mu'y, a', b')
-    float4 rec_b[kBatch];                 // (c', log2 opacity, ex, ey)
+    float4 rec_a[kBatch];                 // staged (mu'x, mu'y, a', b'); then (K0, K1, K2, K3)
+    float4 rec_b[kBatch];                 // staged (c', log2 opacity, ex, ey); then (K4, K5, warp mask, log2 o)
     uint32_t gid[kBatch];                 // internal Gaussian index
     int32_t fill[4];                      // per-warp hit counts of a fill round
     float wb[kSmemSlots][kBatch];         // per (slot, Gaussian of the batch)
@@ -67,6 +67,7 @@ struct Smem {
     int32_t slot_lane[kThreads];          // slot of the sums each lane stores (its first pixel's)
     int32_t seg_of_slot[kPix];
     int32_t group_slot[kThreads / 32];    // slot shared by all of a warp's pixels, -2 = mixed
+    float4 wbox[kThreads / 32];           // each warp's box of pixel centres (x0, x1, y0, y1), tile-local
     int32_t warp_tot[kThreads / 32];
     int32_t scalar[4];
     uint32_t rec_g[kRecBuf];              // queued sums: Gaussian, weight, shared slot
@@ -221,19 +222,25 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
     const int px0 = tx * kTile + (pix0 & 15), py0 = ty * kTile + row0 + (pix0 >> 4);
     const int px1 = tx * kTile + (pix1 & 15), py1 = ty * kTile + row0 + (pix1 >> 4);
     const bool inside0 = px0 < W && py0 < H, inside1 = px1 < W && py1 < H;
-    const float pxc0 = (float)px0 + 0.5f, pyc0 = (float)py0 + 0.5f;
-    const float pxc1 = (float)px1 + 0.5f, pyc1 = (float)py1 + 0.5f;
-    // bounding box of this warp's pixel centres (culling of Gaussians per warp)
-    float wx0 = fminf(inside0 ? pxc0 : INFINITY, inside1 ? pxc1 : INFINITY);
-    float wx1 = fmaxf(inside0 ? pxc0 : -INFINITY, inside1 ? pxc1 : -INFINITY);
-    float wy0 = fminf(inside0 ? pyc0 : INFINITY, inside1 ? pyc1 : INFINITY);
-    float wy1 = fmaxf(inside0 ? pyc0 : -INFINITY, inside1 ? pyc1 : -INFINITY);
+    // pixel centres relative to the CTA's origin (ox, oy), and their monomials: the exponent of a
+    // Gaussian is a quadratic polynomial in them (see the record conversion below)
+    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile + row0);
+    const float X0 = (float)(pix0 & 15) + 0.5f, Y0 = (float)(pix0 >> 4) + 0.5f;
+    const float X1 = (float)(pix1 & 15) + 0.5f, Y1 = (float)(pix1 >> 4) + 0.5f;
+    const float XX0 = X0 * X0, XY0 = X0 * Y0, YY0 = Y0 * Y0;
+    const float XX1 = X1 * X1, XY1 = X1 * Y1, YY1 = Y1 * Y1;
+    // bounding box of this warp's pixel centres (culling of Gaussians per warp), tile-local
+    float wx0 = fminf(inside0 ? X0 : INFINITY, inside1 ? X1 : INFINITY);
+    float wx1 = fmaxf(inside0 ? X0 : -INFINITY, inside1 ? X1 : -INFINITY);
+    float wy0 = fminf(inside0 ? Y0 : INFINITY, inside1 ? Y1 : INFINITY);
+    float wy1 = fmaxf(inside0 ? Y0 : -INFINITY, inside1 ? Y1 : -INFINITY);
     for (int o = 16; o; o >>= 1) {
         wx0 = fminf(wx0, __shfl_xor_sync(0xffffffffu, wx0, o));
         wx1 = fmaxf(wx1, __shfl_xor_sync(0xffffffffu, wx1, o));
         wy0 = fminf(wy0, __shfl_xor_sync(0xffffffffu, wy0, o));
         wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
     }
+    if (lane == 0) sm.wbox[w] = make_float4(wx0, wx1, wy0, wy1);
     float T0 = 1.f, T1 = 1.f, wsum0 = 0.f, wsum1 = 0.f;
     int count0 = 0, count1 = 0, evals = 0;
     bool done0 = !inside0, done1 = !inside1;
@@ -307,6 +314,25 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
         cp_async_wait_all();
         __syncthreads();
         if (nb == 0) continue;
+        // records -> tile-local exponent polynomials. With X = px + 0.5 - ox, mx = mu'x - ox (and
+        // Y, my likewise), the exponent q2 + log2 o = a' dx^2 + b' dx dy + c' dy^2 + log2 o with
+        // dx = mx - X, dy = my - Y is K0 + K1 X + K2 Y + K3 X^2 + K4 X Y + K5 Y^2. The culling
+        // test against the two warps' boxes is taken here once per Gaussian (bit w of the mask).
+        {
+            const float4 b0 = sm.wbox[0], b1 = sm.wbox[1];
+            for (int i = tid; i < nb; i += kThreads) {
+                const float4 ra = sm.rec_a[i], rb = sm.rec_b[i];
+                const float mx = ra.x - ox, my = ra.y - oy;
+                const float A = ra.z, Bc = ra.w, C = rb.x, lo = rb.y;
+                const float K1 = -fmaf(2.f * A, mx, Bc * my);
+                const float K2 = -fmaf(Bc, mx, 2.f * C * my);
+                const float K0 = fmaf(fmaf(A, mx, Bc * my), mx, fmaf(C * my, my, lo));
+                const uint32_t m0 = (mx - rb.z <= b0.y && mx + rb.z >= b0.x && my - rb.w <= b0.w && my + rb.w >= b0.z) ? 1u : 0u;
+                const uint32_t m1 = (mx - rb.z <= b1.y && mx + rb.z >= b1.x && my - rb.w <= b1.w && my + rb.w >= b1.z) ? 2u : 0u;
+                sm.rec_a[i] = make_float4(K0, K1, K2, A);
+                sm.rec_b[i] = make_float4(Bc, C, __uint_as_float(m0 | m1), lo);
+            }
+        }
         if (tid < kBatch)
             for (int s2 = 0; s2 < ns_smem; ++s2) sm.wb[s2][tid] = 0.f;
         for (int i = tid + kThreads; i < nb; i += kThreads)
@@ -319,12 +345,7 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
             if (!__any_sync(0xffffffffu, !(done0 && done1))) break;
             const int nvalid = min(32, nb - c * 32);
             // which of the chunk's Gaussians can reach alpha >= 1/255 inside this warp's pixels
-            bool hitw = false;
-            if (lane < nvalid) {
-                const float4 ra = rec_a[c * 32 + lane];
-                const float4 rb = rec_b[c * 32 + lane];
-                hitw = (ra.x - rb.z <= wx1) && (ra.x + rb.z >= wx0) && (ra.y - rb.w <= wy1) && (ra.y + rb.w >= wy0);
-            }
+            const bool hitw = lane < nvalid && ((__float_as_uint(rec_b[c * 32 + lane].z) >> w) & 1u);
             const uint32_t mask = __ballot_sync(0xffffffffu, hitw);
             evals += nvalid * ((done0 ? 0 : 1) + (done1 ? 0 : 1));
             if (mask == 0) continue;
@@ -347,25 +368,16 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                     if (jj[k] >= 0) {
                         const float4 ra = rec_a[c * 32 + jj[k]];
                         const float4 rb = rec_b[c * 32 + jj[k]];
-                        {
-                            const float dx = ra.x - pxc0, dy = ra.y - pyc0;
-                            const float u = fmaf(ra.z, dx, ra.w * dy);
-                            const float q2 = fmaf(u, dx, rb.x * dy * dy);
-                            const float e = q2 + rb.y;
-                            if (q2 <= 0.f && e >= kLog2AlphaMin) {
-                                al0[k] = fminf(0.99f, fast_exp2(e));
-                                kq0[k] = q2;
-                            }
+                        // e = q2 + log2 opacity; q2 <= 0 holds exactly (positive definite conic)
+                        const float e0 = fmaf(rb.y, YY0, fmaf(rb.x, XY0, fmaf(ra.w, XX0, fmaf(ra.z, Y0, fmaf(ra.y, X0, ra.x)))));
+                        const float e1 = fmaf(rb.y, YY1, fmaf(rb.x, XY1, fmaf(ra.w, XX1, fmaf(ra.z, Y1, fmaf(ra.y, X1, ra.x)))));
+                        if (e0 >= kLog2AlphaMin) {
+                            al0[k] = fminf(0.99f, fast_exp2(e0));
+                            kq0[k] = e0 - rb.w;
                         }
-                        {
-                            const float dx = ra.x - pxc1, dy = ra.y - pyc1;
-                            const float u = fmaf(ra.z, dx, ra.w * dy);
-                            const float q2 = fmaf(u, dx, rb.x * dy * dy);
-                            const float e = q2 + rb.y;
-                            if (q2 <= 0.f && e >= kLog2AlphaMin) {
-                                al1[k] = fminf(0.99f, fast_exp2(e));
-                                kq1[k] = q2;
-                            }
+                        if (e1 >= kLog2AlphaMin) {
+                            al1[k] = fminf(0.99f, fast_exp2(e1));
+                            kq1[k] = e1 - rb.w;
                         }
                     }
                 }
