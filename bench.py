@@ -40,6 +40,8 @@ sys.path.insert(0, ROOT)
 METRIC = "Gaussian-pixel contribs/s & views/s, D=512: BF16/latent vs FP32 plain at stated cos err"
 UNIT = "contribs/s"
 WORKLOAD = "plain FP32 mid scale: 300k Gaussians on 20 ellipsoids, 64 views 960x540, 64 segments, D=512, +1000 top-10 queries"
+WORKLOAD_PRECISION = ("precision form at scale (a view subset): 2M Gaussians on 60 ellipsoids, 1920x1080 views, "
+                      "128 segments, D=512, +1000 top-10 queries")
 
 # Dense FP32 issue rate used as the compositing kernel's ALU roofline: 148 SMs x 128 FP32 lanes
 # x the maximum SM clock, one operation per lane per cycle (most of the work is not FMA).
@@ -66,6 +68,8 @@ def _args():
     p.add_argument("--views", type=int, default=0, help="use only the first V views (0 = all)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the BF16 form's line")
+    p.add_argument("--workload", default="mid", choices=["mid", "precision"],
+                   help="mid: the headline workload; precision: 2M Gaussians at 1920x1080 on a view subset")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
@@ -93,12 +97,26 @@ def job_rate(units_per_rank, world_size, seconds):
     return units_per_rank * world_size / seconds
 
 
-def _scene(views_limit=0):
+def _scene(views_limit=0, workload="mid"):
+    """The bench's scene: the mid-scale workload (default, every view), or the precision
+    configuration on its first `views_limit` views (32 by default)."""
     import synth
-    s = synth.config_mid()
+    if workload == "precision":
+        s = synth.config_precision()
+        views_limit = views_limit or 32
+    else:
+        s = synth.config_mid()
     nv = s.n_views if not views_limit else min(views_limit, s.n_views)
     views = [s.view(i) for i in range(nv)]
     return s, views
+
+
+def _config(a, scene, views, parallelism, l2):
+    v0 = views[0]
+    return {"workload": WORKLOAD_PRECISION if a.workload == "precision" else WORKLOAD,
+            "gaussians": scene.gaussians.n, "views": len(views),
+            "resolution": "%dx%d" % (v0.camera.width, v0.camera.height), "segments": int(v0.table.shape[0]),
+            "dim": scene.dim, "queries": a.queries, "k": a.k, "parallelism": parallelism, "l2": l2}
 
 
 def _queries(views, B, seed=4):
@@ -205,7 +223,7 @@ def run_reference(a):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    scene, views = _scene(a.views)
+    scene, views = _scene(a.views, a.workload)
     per_step = []
     s = None
     for it in range(a.warmup + a.steps):
@@ -218,9 +236,7 @@ def run_reference(a):
            "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "views_per_s": vps,
-           "config": {"workload": WORKLOAD, "gaussians": scene.gaussians.n, "views": len(views),
-                      "resolution": "960x540", "segments": 64, "dim": scene.dim, "queries": a.queries, "k": a.k,
-                      "parallelism": "rank 0 on host cores", "l2": "n/a (host)"},
+           "config": _config(a, scene, views, "rank 0 on host cores", "n/a (host)"),
            "cpu_baseline": dict(s, value=value),
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -241,7 +257,7 @@ def run_slag(a):
     from paper_2505_08124_b300 import slag as S
     S.load_library()
 
-    scene, views = _scene(a.views)
+    scene, views = _scene(a.views, a.workload)
     g = scene.gaussians
     D = scene.dim
     Q = _queries(views, a.queries)
@@ -373,11 +389,11 @@ def run_slag(a):
                "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "views_per_s": views_per_s,
-               "config": {"workload": WORKLOAD, "gaussians": g.n, "views": len(views), "resolution": "960x540",
-                          "segments": 64, "dim": D, "queries": a.queries, "k": a.k,
-                          "parallelism": "replicas x%d" % ws,
-                          "l2": "inputs larger than L2 (133 MB of segment maps + 8 MB tables per step; "
-                                "614 MB embeddings written per step)"},
+               "config": _config(a, scene, views, "replicas x%d" % ws,
+                                 "inputs larger than L2 (%d MB of segment maps + %d MB tables per step; %d MB embeddings "
+                                 "written per step)" % (sum(v.seg.nbytes for v in views) >> 20,
+                                                        sum(v.table.nbytes for v in views) >> 20,
+                                                        (g.n * D * 4) >> 20)),
                "clocks": clk.summary(),
                "e2e": e2e,
                "roofline": roofline,
