@@ -68,6 +68,15 @@ enum { SLAG_WEIGHT_ALPHA_T = 0, SLAG_WEIGHT_KERNEL = 1 };
  * float64 is used on the GPU in either form. */
 enum { SLAG_PREC_FP32 = 0, SLAG_PREC_BF16 = 1 };
 
+/* SLAG_FLAG_EMBEDDINGS_ON_HOST: the context holds no n x D copy of the
+ * embeddings on the device (out-of-core aggregation, after the paper's
+ * multi-GPU section, where the aggregation tensor outgrows device memory and
+ * is processed in Gaussian-range chunks). slag_finalize then writes host
+ * memory only, computing the rows in chunks of spatially adjacent Gaussians,
+ * and queries return SLAG_ERR_STATE; slag_export_partitions works in both
+ * modes. */
+enum { SLAG_FLAG_EMBEDDINGS_ON_HOST = 1 };
+
 /* The Gaussian set G = {G_1..G_N} (Method, Rasterizer_SLAG statement). */
 typedef struct {
     int64_t n;               /* number of Gaussians, 1 <= n < 2^31 */
@@ -93,7 +102,7 @@ typedef struct {
     int32_t dim;             /* D: embedding width, a multiple of 128, 128 .. 4096 */
     int32_t precision;       /* SLAG_PREC_FP32 or SLAG_PREC_BF16 */
     int32_t weight_mode;     /* SLAG_WEIGHT_ALPHA_T (default) or SLAG_WEIGHT_KERNEL */
-    int32_t reserved;        /* must be 0 */
+    int32_t flags;           /* SLAG_FLAG_* bits, or 0 */
     void *cuda_stream;       /* cudaStream_t, NULL = legacy default stream */
 } slag_options;
 
@@ -217,6 +226,25 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
  * over every contributing Gaussian and the number of contributors. */
 slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_T, float *out_wsum,
                               int32_t *out_count);
+
+/* ---- out-of-core output: per-area embedding files ------------------------- */
+
+/* Spatial partition export (the paper stores a large scene's embeddings per
+ * area of a grid over the Gaussian means instead of in a vector database).
+ * Aggregates the views added so far in chunks of at most chunk_gaussians
+ * Gaussians on the device (rounded to blocks of 128 spatially adjacent
+ * Gaussians; <= 0 picks 2^20) and appends every touched Gaussian (sum w > 0)
+ * to the file of its cell of a cells_x x cells_y grid over the x-y bounding
+ * box of all means. The directory is created if missing. Files:
+ *   dir/cell_<cx>_<cy>.slag: "SLAGPART" (8 bytes), uint32 version = 1,
+ *     uint32 D, int64 count, float x0, x1, y0, y1 (the cell's bounds), then
+ *     count records of int64 caller index, float sum w, float E[D];
+ *   dir/index.txt: one line per non-empty cell: cx cy count x0 x1 y0 y1 file.
+ * *out_written (nullable) receives the number of records. Errors: STATE
+ * before any view, INVALID_ARG for a bad grid or path, the CUDA and OOM codes,
+ * and SLAG_ERR_CUDA for a file that cannot be written. */
+slag_status slag_export_partitions(slag_ctx *ctx, const char *dir, int32_t cells_x, int32_t cells_y,
+                                   int64_t chunk_gaussians, int64_t *out_written);
 
 /* ---- diagnostics: per-stage device time ---------------------------------- */
 

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) aggregate_tc_k(const AggArgs a, 
     AggCtl *ctl = reinterpret_cast<AggCtl *>(smem_raw + kStages * kStageBytes + Sh::kWfBytes + kListBytes);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t b = blockIdx.x;
+    const int64_t b = a.block0 + blockIdx.x;
     const uint32_t ts = a.bstart[b], te = a.bend[b];
     const bool any = ts < te;
     // unique (block, column) index of triple t = exclusive count + own flag - 1
@@ -284,7 +284,8 @@ __global__ void __launch_bounds__(kThreadsA, 1) aggregate_tc_k(const AggArgs a, 
         if (__syncthreads_or(!ok)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (warp < 4) {
-            float *out = (g < a.n) ? a.E + (int64_t)a.orig_of_int[g] * a.D + d0 : nullptr;
+            float *out = a.E_chunk ? a.E_chunk + ((int64_t)blockIdx.x * kG + tid) * a.D + d0
+                                   : ((g < a.n) ? a.E + (int64_t)a.orig_of_int[g] * a.D + d0 : nullptr);
             const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16);
             for (int cb = 0; cb < kNP; cb += 32) {
                 float v[32];
@@ -317,11 +318,17 @@ __global__ void __launch_bounds__(kThreadsA, 1) aggregate_tc_k(const AggArgs a, 
             const int64_t last = gc - 1;
             mbar_wait(&ctl->bar[last % kStages], (uint32_t)(last / kStages) & 1u);
         }
-    } else if (tid < kG && g < a.n) {
-        const uint32_t o = a.orig_of_int[g];
-        const bool nz = S > 0.f && norm2 > 0.f;
-        a.inv_norm[o] = nz ? 1.f / sqrtf(norm2) : 0.f;
-        a.wsum[o] = S;
+    } else if (tid < kG) {
+        const uint32_t o = g < a.n ? a.orig_of_int[g] : 0xffffffffu;
+        if (g < a.n) {
+            const bool nz = S > 0.f && norm2 > 0.f;
+            a.inv_norm[o] = nz ? 1.f / sqrtf(norm2) : 0.f;
+            a.wsum[o] = S;
+        }
+        if (a.E_chunk) {
+            a.ids_chunk[(int64_t)blockIdx.x * kG + tid] = o;
+            a.wsum_chunk[(int64_t)blockIdx.x * kG + tid] = S;
+        }
     }
     if (ok && warp < 4) {
         const unsigned touched = __ballot_sync(0xffffffffu, tid < kG && g < a.n && S > 0.f);

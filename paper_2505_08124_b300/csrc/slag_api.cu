@@ -20,8 +20,10 @@
 //   (block, column, Gaussian) -> distinct columns per block -> blocked
 //   contraction with the stored segment embeddings -> divide by sum w.
 // slag_query ("Query processing for inference"): cosine scores + top-k.
+#include <errno.h>
 #include <stdio.h>
 #include <string.h>
+#include <sys/stat.h>
 
 #include <algorithm>
 #include <atomic>
@@ -89,6 +91,8 @@ struct slag_ctx {
     int32_t D = 0;
     int32_t weight_mode = 0;
     int32_t precision = 0;
+    int32_t opt_flags = 0;                   // SLAG_FLAG_*
+    int64_t chunk_gaussians = 1 << 20;       // rows per chunk of the out-of-core contraction
     std::string err;
 
     // Gaussians, internal (Morton) order
@@ -451,7 +455,7 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     if (opt->dim < 128 || opt->dim > 4096 || opt->dim % 128 != 0) return SLAG_ERR_INVALID_ARG;
     if (opt->precision != SLAG_PREC_FP32 && opt->precision != SLAG_PREC_BF16) return SLAG_ERR_INVALID_ARG;
     if (opt->weight_mode != SLAG_WEIGHT_ALPHA_T && opt->weight_mode != SLAG_WEIGHT_KERNEL) return SLAG_ERR_INVALID_ARG;
-    if (opt->reserved != 0) return SLAG_ERR_INVALID_ARG;
+    if ((opt->flags & ~SLAG_FLAG_EMBEDDINGS_ON_HOST) != 0) return SLAG_ERR_INVALID_ARG;
 
     slag_ctx *ctx = new (std::nothrow) slag_ctx();
     if (!ctx) return SLAG_ERR_OOM;
@@ -468,6 +472,7 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     ctx->D = opt->dim;
     ctx->weight_mode = opt->weight_mode;
     ctx->precision = opt->precision;
+    ctx->opt_flags = opt->flags;
     ctx->stream = (cudaStream_t)opt->cuda_stream;
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(SLAG_ERR_CUDA);
     cudaStream_t st = ctx->stream;
@@ -534,7 +539,8 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
 
     // accumulators and outputs
     CA(dalloc(&ctx->s_hi, n)); CA(dalloc(&ctx->s_lo, n)); CA(dalloc(&ctx->s_ovf, n));
-    CA(dalloc(&ctx->E, n * (int64_t)ctx->D)); CA(dalloc(&ctx->inv_norm, n)); CA(dalloc(&ctx->wsum, n));
+    if (!(ctx->opt_flags & SLAG_FLAG_EMBEDDINGS_ON_HOST)) CA(dalloc(&ctx->E, n * (int64_t)ctx->D));
+    CA(dalloc(&ctx->inv_norm, n)); CA(dalloc(&ctx->wsum, n));
     CA(dalloc(&ctx->qrows, n)); CA(dalloc(&ctx->qflags, n)); CA(dalloc(&ctx->qpos, n)); CA(dalloc(&ctx->d_nq, 1));
     CA(dalloc(&ctx->bstart, (n + kBlockG - 1) / kBlockG)); CA(dalloc(&ctx->bend, (n + kBlockG - 1) / kBlockG));
     for (int i = 0; i < kSlots; ++i) launch_hash_init(ctx->slot[i].hash, n, st);
@@ -682,8 +688,14 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     return SLAG_OK;
 }
 
-slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device) {
-    if (!ctx) return SLAG_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Everything finalize does before the contraction: join the views in flight,
+// read the totals, sort the triple log by (block, column, Gaussian) and list
+// the distinct columns of every block.
+slag_status finalize_prepare(slag_ctx *ctx) {
     if (ctx->stats.views == 0) return fail(ctx, SLAG_ERR_STATE, "finalize before any view");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
@@ -739,7 +751,12 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
         launch_uniques(ctx->log_key, ctx->flags, ctx->uidx, Z, ctx->ucol, ctx->ustart, ctx->bstart, ctx->bend, st);
         span_end(ctx, st);
     }
+    return SLAG_OK;
+}
+
+AggArgs agg_args(slag_ctx *ctx) {
     AggArgs g;
+    memset(&g, 0, sizeof(g));
     g.keys = ctx->log_key;
     g.w = ctx->log_w;
     g.flags = ctx->flags;
@@ -753,13 +770,128 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     g.s_lo = ctx->s_lo;
     g.s_ovf = ctx->s_ovf;
     g.orig_of_int = ctx->orig_of_int;
-    g.n = n;
+    g.n = ctx->n;
     g.D = ctx->D;
     g.E = ctx->E;
     g.inv_norm = ctx->inv_norm;
     g.wsum = ctx->wsum;
     g.touched = ctx->touched;
     g.bf16 = ctx->precision == SLAG_PREC_BF16 ? 1 : 0;
+    return g;
+}
+
+// The contraction in chunks of blocks, for outputs that need not be resident on
+// the device: each chunk's rows (Morton order), their caller ids, weight sums and
+// means are copied to pinned host memory and handed to `sink` (rows with id
+// 0xffffffff lie past the last Gaussian). At most chunk_gaussians rows are
+// resident on the device at a time.
+struct ChunkView {
+    const float *E;          // rows x D
+    const uint32_t *ids;     // rows
+    const float *wsum;       // rows
+    const float4 *means;     // rows: (x, y, z, opacity)
+    int64_t rows;
+};
+
+template <typename Sink>
+slag_status aggregate_chunks(slag_ctx *ctx, int64_t chunk_gaussians, Sink &&sink) {
+    cudaStream_t st = ctx->stream;
+    const int64_t n = ctx->n, D = ctx->D;
+    const int64_t nblocks = (n + kBlockG - 1) / kBlockG;
+    int64_t cb = chunk_gaussians / kBlockG;
+    if (cb < 1) cb = 1;
+    if (cb > nblocks) cb = nblocks;
+    const int64_t rows = cb * kBlockG;
+    float *dE = nullptr, *dW = nullptr, *hE = nullptr, *hW = nullptr;
+    uint32_t *dI = nullptr, *hI = nullptr;
+    float4 *hM = nullptr;
+    slag_status rc = SLAG_OK;
+    auto release = [&]() {
+        dfree(dE); dfree(dW); dfree(dI);
+        if (hE) cudaFreeHost(hE);
+        if (hW) cudaFreeHost(hW);
+        if (hI) cudaFreeHost(hI);
+        if (hM) cudaFreeHost(hM);
+    };
+#define CC(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            release();                                                                              \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? SLAG_ERR_OOM : SLAG_ERR_CUDA,        \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+        }                                                                                           \
+    } while (0)
+    CC(dalloc(&dE, rows * D));
+    CC(dalloc(&dW, rows));
+    CC(dalloc(&dI, rows));
+    CC(cudaMallocHost((void **)&hE, sizeof(float) * (size_t)(rows * D)));
+    CC(cudaMallocHost((void **)&hW, sizeof(float) * (size_t)rows));
+    CC(cudaMallocHost((void **)&hI, sizeof(uint32_t) * (size_t)rows));
+    CC(cudaMallocHost((void **)&hM, sizeof(float4) * (size_t)rows));
+    AggArgs g = agg_args(ctx);
+    g.E_chunk = dE;
+    g.ids_chunk = dI;
+    g.wsum_chunk = dW;
+    for (int64_t b0 = 0; b0 < nblocks && rc == SLAG_OK; b0 += cb) {
+        const int64_t nb = (b0 + cb <= nblocks) ? cb : nblocks - b0;
+        g.block0 = b0;
+        launch_aggregate(g, nb, ctx->tc_err, st);
+        const int64_t r = nb * kBlockG;
+        const int64_t first = b0 * kBlockG;
+        const int64_t valid = (first + r <= n) ? r : n - first;
+        CC(cudaMemcpyAsync(hE, dE, sizeof(float) * (size_t)(r * D), cudaMemcpyDeviceToHost, st));
+        CC(cudaMemcpyAsync(hW, dW, sizeof(float) * (size_t)r, cudaMemcpyDeviceToHost, st));
+        CC(cudaMemcpyAsync(hI, dI, sizeof(uint32_t) * (size_t)r, cudaMemcpyDeviceToHost, st));
+        CC(cudaMemcpyAsync(hM, ctx->mean_op + first, sizeof(float4) * (size_t)valid, cudaMemcpyDeviceToHost, st));
+        CC(cudaMemcpyAsync(&ctx->hc->tc_err, ctx->tc_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CC(cudaStreamSynchronize(st));
+        if (ctx->hc->tc_err) {
+            release();
+            return fail(ctx, SLAG_ERR_TIMEOUT, "the tensor-core aggregation gave up waiting");
+        }
+        rc = sink(ChunkView{hE, hI, hW, hM, valid});
+    }
+#undef CC
+    release();
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    slag_status s = finalize_prepare(ctx);
+    if (s != SLAG_OK) return s;
+    cudaStream_t st = ctx->stream;
+    const int64_t n = ctx->n;
+    const int64_t nblocks = (n + kBlockG - 1) / kBlockG;
+    if (ctx->opt_flags & SLAG_FLAG_EMBEDDINGS_ON_HOST) {
+        // no resident n x D copy: the rows arrive in chunks and are placed in caller order here
+        if (out_emb && on_device) return fail(ctx, SLAG_ERR_INVALID_ARG, "embeddings are kept on the host: out_emb must be host memory");
+        const int64_t D = ctx->D;
+        s = aggregate_chunks(ctx, ctx->chunk_gaussians, [&](const ChunkView &c) {
+            for (int64_t r = 0; r < c.rows; ++r) {
+                const uint32_t id = c.ids[r];
+                if (id == 0xffffffffu) continue;
+                if (out_emb) memcpy(out_emb + (int64_t)id * D, c.E + r * D, sizeof(float) * (size_t)D);
+                if (out_wsum && !on_device) out_wsum[id] = c.wsum[r];
+            }
+            return SLAG_OK;
+        });
+        if (s != SLAG_OK) return s;
+        if (out_wsum && on_device) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(&ctx->hc->touched, ctx->touched, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        spans_resolve(ctx);
+        ctx->stats.touched = (int64_t)ctx->hc->touched;
+        ctx->n_q = 0;
+        ctx->finalized = false;   // queries need the embeddings on the device
+        return SLAG_OK;
+    }
+    AggArgs g = agg_args(ctx);
     span_begin(ctx, SLAG_STAGE_AGGREGATE, st);
     launch_aggregate(g, nblocks, ctx->tc_err, st);
     // query candidates: the rows of E with a non-zero embedding, in caller order
@@ -871,6 +1003,105 @@ slag_status slag_reset(slag_ctx *ctx) {
     ctx->finalized = false;
     ctx->hc->v = ViewCounters{};
     ctx->stats = slag_stats{};
+    return SLAG_OK;
+}
+
+slag_status slag_export_partitions(slag_ctx *ctx, const char *dir, int32_t cells_x, int32_t cells_y,
+                                   int64_t chunk_gaussians, int64_t *out_written) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    if (!dir || !dir[0]) return fail(ctx, SLAG_ERR_INVALID_ARG, "no directory");
+    if (cells_x < 1 || cells_y < 1 || (int64_t)cells_x * cells_y > (1 << 20))
+        return fail(ctx, SLAG_ERR_INVALID_ARG, "grid must have 1 .. 2^20 cells");
+    if (out_written) *out_written = 0;
+    slag_status s = finalize_prepare(ctx);
+    if (s != SLAG_OK) return s;
+    if (mkdir(dir, 0755) != 0 && errno != EEXIST)
+        return fail(ctx, SLAG_ERR_INVALID_ARG, std::string("cannot create ") + dir);
+    const int64_t n = ctx->n;
+    const int32_t D = ctx->D;
+    // x-y bounds of all means
+    std::vector<float4> means((size_t)n);
+    CK(cudaMemcpyAsync(means.data(), ctx->mean_op, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    float x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (const float4 &m : means) {
+        x0 = fminf(x0, m.x); x1 = fmaxf(x1, m.x);
+        y0 = fminf(y0, m.y); y1 = fmaxf(y1, m.y);
+    }
+    const float sx = x1 > x0 ? (float)cells_x / (x1 - x0) : 0.f, sy = y1 > y0 ? (float)cells_y / (y1 - y0) : 0.f;
+    const float cwx = x1 > x0 ? (x1 - x0) / (float)cells_x : 0.f, cwy = y1 > y0 ? (y1 - y0) / (float)cells_y : 0.f;
+    const size_t ncell = (size_t)cells_x * (size_t)cells_y;
+    const size_t rec_bytes = 8 + 4 + 4 * (size_t)D;
+    const size_t hdr_bytes = 8 + 4 + 4 + 8 + 16;
+    std::vector<int64_t> count(ncell, 0);
+    std::vector<std::vector<char>> pend(ncell);
+    auto path_of = [&](size_t c) {
+        return std::string(dir) + "/cell_" + std::to_string(c % cells_x) + "_" + std::to_string(c / cells_x) + ".slag";
+    };
+    auto flush = [&](size_t c) -> bool {
+        if (pend[c].empty()) return true;
+        const std::string p = path_of(c);
+        FILE *f = fopen(p.c_str(), count[c] == (int64_t)(pend[c].size() / rec_bytes) ? "wb" : "ab");
+        if (!f) return false;
+        bool ok = true;
+        if (count[c] == (int64_t)(pend[c].size() / rec_bytes)) {   // new file: header with count 0 for now
+            const uint32_t ver = 1, d = (uint32_t)D;
+            const int64_t zero = 0;
+            const float b[4] = {x0 + cwx * (float)(c % cells_x), x0 + cwx * (float)(c % cells_x + 1),
+                                y0 + cwy * (float)(c / cells_x), y0 + cwy * (float)(c / cells_x + 1)};
+            ok = fwrite("SLAGPART", 1, 8, f) == 8 && fwrite(&ver, 4, 1, f) == 1 && fwrite(&d, 4, 1, f) == 1 &&
+                 fwrite(&zero, 8, 1, f) == 1 && fwrite(b, 4, 4, f) == 4;
+        }
+        ok = ok && fwrite(pend[c].data(), 1, pend[c].size(), f) == pend[c].size();
+        ok = (fclose(f) == 0) && ok;
+        pend[c].clear();
+        return ok;
+    };
+    int64_t written = 0;
+    s = aggregate_chunks(ctx, chunk_gaussians > 0 ? chunk_gaussians : (int64_t)1 << 20, [&](const ChunkView &v) {
+        std::vector<size_t> touched_cells;
+        for (int64_t r = 0; r < v.rows; ++r) {
+            const uint32_t id = v.ids[r];
+            if (id == 0xffffffffu || !(v.wsum[r] > 0.f)) continue;
+            int cx = (int)floorf((v.means[r].x - x0) * sx), cy = (int)floorf((v.means[r].y - y0) * sy);
+            cx = cx < 0 ? 0 : (cx >= cells_x ? cells_x - 1 : cx);
+            cy = cy < 0 ? 0 : (cy >= cells_y ? cells_y - 1 : cy);
+            const size_t c = (size_t)cy * cells_x + cx;
+            std::vector<char> &buf = pend[c];
+            if (buf.empty()) touched_cells.push_back(c);
+            const size_t at = buf.size();
+            buf.resize(at + rec_bytes);
+            const int64_t id64 = id;
+            memcpy(buf.data() + at, &id64, 8);
+            memcpy(buf.data() + at + 8, &v.wsum[r], 4);
+            memcpy(buf.data() + at + 12, v.E + r * D, 4 * (size_t)D);
+            ++count[c];
+            ++written;
+        }
+        for (size_t c : touched_cells)
+            if (!flush(c)) return fail(ctx, SLAG_ERR_CUDA, "cannot write " + path_of(c));
+        return SLAG_OK;
+    });
+    if (s != SLAG_OK) return s;
+    // final counts in the headers, and the index
+    FILE *idx = fopen((std::string(dir) + "/index.txt").c_str(), "w");
+    if (!idx) return fail(ctx, SLAG_ERR_CUDA, std::string("cannot write ") + dir + "/index.txt");
+    for (size_t c = 0; c < ncell; ++c) {
+        if (!count[c]) continue;
+        FILE *f = fopen(path_of(c).c_str(), "r+b");
+        bool ok = f && fseek(f, 16, SEEK_SET) == 0 && fwrite(&count[c], 8, 1, f) == 1;
+        if (f) ok = (fclose(f) == 0) && ok;
+        if (!ok) {
+            fclose(idx);
+            return fail(ctx, SLAG_ERR_CUDA, "cannot write " + path_of(c));
+        }
+        fprintf(idx, "%zu %zu %lld %.9g %.9g %.9g %.9g cell_%zu_%zu.slag\n", c % cells_x, c / cells_x,
+                (long long)count[c], x0 + cwx * (float)(c % cells_x), x0 + cwx * (float)(c % cells_x + 1),
+                y0 + cwy * (float)(c / cells_x), y0 + cwy * (float)(c / cells_x + 1), c % cells_x, c / cells_x);
+    }
+    if (fclose(idx) != 0) return fail(ctx, SLAG_ERR_CUDA, std::string("cannot write ") + dir + "/index.txt");
+    (void)hdr_bytes;
+    if (out_written) *out_written = written;
     return SLAG_OK;
 }
 

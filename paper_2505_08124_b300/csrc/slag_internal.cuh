@@ -240,6 +240,13 @@ struct AggArgs {
     float *wsum;                   // n, caller order
     unsigned long long *touched;
     int bf16;                      // BF16 operands (FP32 accumulation) instead of the 3xTF32 split
+    // Chunked output (out-of-core finalize): the launch covers blocks block0 .. block0 + grid;
+    // with E_chunk set, row r = (b - block0) * 128 + i of E_chunk / ids_chunk / wsum_chunk
+    // receives Gaussian i of block b (id 0xffffffff past n) instead of E's caller-order row.
+    int64_t block0;
+    float *E_chunk;
+    uint32_t *ids_chunk;
+    float *wsum_chunk;
 };
 // k_aggregate_tc.cu: one CTA per block of 128 Gaussians on the tensor cores; *err is set
 // when a bounded wait gives up

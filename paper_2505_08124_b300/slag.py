@@ -22,6 +22,7 @@ _NAMES = {1: "INVALID_ARG", 2: "STATE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "C
 WEIGHT_ALPHA_T, WEIGHT_KERNEL = 0, 1
 PREC_FP32 = 0
 PREC_BF16 = 1
+FLAG_EMBEDDINGS_ON_HOST = 1
 
 
 class SlagError(RuntimeError):
@@ -44,7 +45,7 @@ class CGaussians(ctypes.Structure):
 
 class COptions(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("precision", ctypes.c_int32), ("weight_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("flags", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
 
 
 class CStats(ctypes.Structure):
@@ -57,7 +58,8 @@ _lib = None
 
 EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_query_batch", "slag_reset",
            "slag_get_stats", "slag_last_error", "slag_destroy", "slag_bin_view", "slag_render_debug",
-           "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk", "slag_kernel_launches")
+           "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk", "slag_kernel_launches",
+           "slag_export_partitions")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -91,6 +93,7 @@ def load_library(path: str = LIB_PATH):
     lib.slag_render_debug.argtypes = [P, ctypes.POINTER(CCamera), P, P, P]
     lib.slag_set_profiling.argtypes = [P, i32]
     lib.slag_get_profile.argtypes = [P, ctypes.POINTER(CProfile), i32]
+    lib.slag_export_partitions.argtypes = [P, ctypes.c_char_p, i32, i32, i64, ctypes.POINTER(i64)]
     lib.slag_kernel_launches.argtypes = []
     lib.slag_kernel_launches.restype = ctypes.c_uint64
     lib.slag_noalloc_query_topk.argtypes = [P, i64, i32, P, P, i32, i32, P, P, P, P]
@@ -153,7 +156,7 @@ class Lifter:
     """One lifting context: a fixed Gaussian set, views added one at a time."""
 
     def __init__(self, gaussians, dim: int = 512, weight_mode: int = WEIGHT_ALPHA_T,
-                 stream: Optional[int] = None, precision: int = PREC_FP32):
+                 stream: Optional[int] = None, precision: int = PREC_FP32, embeddings_on_host: bool = False):
         self._lib = load_library()
         self.n = int(gaussians.means.shape[0])
         self.dim = int(dim)
@@ -162,7 +165,8 @@ class Lifter:
         if len(dev) != 1:
             raise ValueError("Gaussian arrays must all be on the host or all on the device")
         g = CGaussians(self.n, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], dev.pop())
-        o = COptions(self.dim, int(precision), int(weight_mode), 0, ctypes.c_void_p(stream) if stream else None)
+        flags = FLAG_EMBEDDINGS_ON_HOST if embeddings_on_host else 0
+        o = COptions(self.dim, int(precision), int(weight_mode), flags, ctypes.c_void_p(stream) if stream else None)
         h = ctypes.c_void_p()
         rc = self._lib.slag_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h))
         if rc != OK:
@@ -253,6 +257,15 @@ class Lifter:
     def reset(self):
         self._check(self._lib.slag_reset(self._h), "slag_reset")
 
+    def export_partitions(self, directory: str, cells_x: int, cells_y: int, chunk_gaussians: int = 0) -> int:
+        """Per-area embedding files of the touched Gaussians (see slag_export_partitions); returns
+        the number of records written."""
+        written = ctypes.c_int64()
+        self._check(self._lib.slag_export_partitions(self._h, os.fsencode(directory), int(cells_x), int(cells_y),
+                                                     int(chunk_gaussians), ctypes.byref(written)),
+                    "slag_export_partitions")
+        return int(written.value)
+
     def stats(self) -> dict:
         s = CStats()
         self._check(self._lib.slag_get_stats(self._h, ctypes.byref(s)), "slag_get_stats")
@@ -304,3 +317,26 @@ class Lifter:
 def kernel_launches() -> int:
     """Kernel launches issued by libslag so far (process-wide running count)."""
     return int(load_library().slag_kernel_launches())
+
+
+def read_partitions(directory: str) -> dict:
+    """Reads the files of slag_export_partitions: {(cx, cy): {"bounds": (x0, x1, y0, y1),
+    "ids": int64[count], "wsum": float32[count], "E": float32[count, D]}}."""
+    out = {}
+    with open(os.path.join(directory, "index.txt")) as f:
+        lines = [ln.split() for ln in f if ln.strip()]
+    for cx, cy, count, x0, x1, y0, y1, name in lines:
+        with open(os.path.join(directory, name), "rb") as f:
+            raw = f.read()
+        if raw[:8] != b"SLAGPART":
+            raise ValueError("%s: not a partition file" % name)
+        ver, D = np.frombuffer(raw, np.uint32, 2, 8)
+        cnt = int(np.frombuffer(raw, np.int64, 1, 16)[0])
+        bounds = tuple(float(x) for x in np.frombuffer(raw, np.float32, 4, 24))
+        if ver != 1 or cnt != int(count):
+            raise ValueError("%s: version %d, count %d (index says %s)" % (name, ver, cnt, count))
+        rec = np.dtype([("id", "<i8"), ("wsum", "<f4"), ("E", "<f4", (int(D),))])
+        r = np.frombuffer(raw, rec, cnt, 40)
+        out[(int(cx), int(cy))] = {"bounds": bounds, "ids": r["id"].copy(), "wsum": r["wsum"].copy(),
+                                   "E": r["E"].copy()}
+    return out
