@@ -66,7 +66,13 @@ enum { SLAG_WEIGHT_ALPHA_T = 0, SLAG_WEIGHT_KERNEL = 1 };
  * float32 accumulation; the error against float64 is stated per result by the
  * tests (cosine >= 1 - 1e-3 per touched Gaussian at the tested scales). No
  * float64 is used on the GPU in either form. */
-enum { SLAG_PREC_FP32 = 0, SLAG_PREC_BF16 = 1 };
+enum { SLAG_PREC_FP32 = 0, SLAG_PREC_BF16 = 1, SLAG_PREC_LATENT32 = 2 };
+/* LATENT32: the learned latent form. Each view's segment embeddings are
+ * encoded to 32-d codes by a small autoencoder (slag_latent_train; set with
+ * slag_set_latent before the first view), the aggregation runs on the codes,
+ * and finalize decodes each touched Gaussian's mean code to D dimensions
+ * (the decoder is not linear: dec(mean code) is not the mean of decoded
+ * codes; the float32 path is the reference for its error). */
 
 /* SLAG_FLAG_EMBEDDINGS_ON_HOST: the context holds no n x D copy of the
  * embeddings on the device (out-of-core aggregation, after the paper's
@@ -226,6 +232,36 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
  * over every contributing Gaussian and the number of contributors. */
 slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_T, float *out_wsum,
                               int32_t *out_count);
+
+/* ---- the latent form: autoencoder D -> 256 -> 32 -> 256 -> D ---------------- */
+
+/* Parameters of the autoencoder for input width dim (float32, layout: W1 dim x 256,
+ * b1 256, W2 256 x 32, b2 32, W3 32 x 256, b3 256, W4 256 x dim, b4 dim; W row-major
+ * input x output). 0 for an unsupported width. */
+int64_t slag_latent_param_count(int32_t dim);
+
+/* Trains the autoencoder on n samples (n x dim float32, rows of unit length in
+ * the method's use) with Adam at learning rate lr, batches of `batch`, for
+ * `epochs` passes over a seeded shuffle. Products take the weights rounded to
+ * bfloat16 with float32 accumulation (float32 master weights). The loss per
+ * sample is mean((dec(enc(x)) - x)^2) + (1 - cos(dec(enc(x)), x)).
+ * samples: host (on_device = 0) or device memory. out_params (host,
+ * slag_latent_param_count(dim) floats) receives the trained parameters,
+ * out_loss (host, `epochs` floats, nullable) the mean loss of each epoch.
+ * dim must be a multiple of 32 in 32 .. 4096. */
+slag_status slag_latent_train(const float *samples, int64_t n, int32_t dim, int32_t epochs, int32_t batch,
+                              float lr, uint64_t seed, int32_t on_device, float *out_params, float *out_loss,
+                              void *cuda_stream);
+
+/* Applies the autoencoder (host parameters) to `rows` host vectors: mode 0
+ * encodes (in rows x dim -> out rows x 32), 1 decodes (rows x 32 -> rows x
+ * dim), 2 does both (rows x dim -> rows x dim). */
+slag_status slag_latent_apply(const float *params, int32_t dim, const float *in, int64_t rows, int32_t mode,
+                              float *out, void *cuda_stream);
+
+/* Sets the autoencoder (host parameters, slag_latent_param_count(D) floats) of
+ * a context created with SLAG_PREC_LATENT32; before the first view. */
+slag_status slag_set_latent(slag_ctx *ctx, const float *params);
 
 /* ---- out-of-core output: per-area embedding files ------------------------- */
 

@@ -147,6 +147,13 @@ struct slag_ctx {
     int64_t n_q = 0;
     bool finalized = false;
 
+    // latent form: autoencoder parameters, codes of the stored segment embeddings, scratch
+    float *lat_params = nullptr;
+    float *ztable = nullptr;                 // columns x kLatent
+    int64_t ztable_cap = 0;
+    float *lat_hidden = nullptr;             // rows x kLatentHidden
+    int64_t lat_hidden_cap = 0;
+
     // queries
     float *qbuf = nullptr;
     int64_t qbuf_cap = 0;
@@ -453,7 +460,8 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     if (g->n < 1 || g->n >= (1LL << 31)) return SLAG_ERR_INVALID_ARG;
     if (!g->means || !g->scales || !g->quats || !g->opacities) return SLAG_ERR_INVALID_ARG;
     if (opt->dim < 128 || opt->dim > 4096 || opt->dim % 128 != 0) return SLAG_ERR_INVALID_ARG;
-    if (opt->precision != SLAG_PREC_FP32 && opt->precision != SLAG_PREC_BF16) return SLAG_ERR_INVALID_ARG;
+    if (opt->precision != SLAG_PREC_FP32 && opt->precision != SLAG_PREC_BF16 && opt->precision != SLAG_PREC_LATENT32)
+        return SLAG_ERR_INVALID_ARG;
     if (opt->weight_mode != SLAG_WEIGHT_ALPHA_T && opt->weight_mode != SLAG_WEIGHT_KERNEL) return SLAG_ERR_INVALID_ARG;
     if ((opt->flags & ~SLAG_FLAG_EMBEDDINGS_ON_HOST) != 0) return SLAG_ERR_INVALID_ARG;
 
@@ -586,6 +594,17 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D), kind, fr));
+    if (ctx->precision == SLAG_PREC_LATENT32) {
+        // the view's segment embeddings -> 32-d codes (rows table_rows .. + M of the code store)
+        if (!ctx->lat_params) return fail(ctx, SLAG_ERR_STATE, "latent form: slag_set_latent before the first view");
+        if ((ctx->table_rows + M) * kLatent > ctx->ztable_cap) {
+            CK(drain_views(ctx));
+            CK(grow(ctx->ztable, ctx->ztable_cap, (ctx->table_rows + M) * kLatent, fr, ctx->table_rows * kLatent));
+        }
+        CK(grow(ctx->lat_hidden, ctx->lat_hidden_cap, (int64_t)M * kLatentHidden, fr));
+        latent_encode(ctx->lat_params, ctx->D, ctx->table + ctx->table_rows * D, M, ctx->lat_hidden,
+                      ctx->ztable + ctx->table_rows * kLatent, fr);
+    }
     if (npx > vs.seg_cap) CK(grow(vs.seg_buf, vs.seg_cap, npx, fr));
     CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, fr));
     const int32_t *seg = vs.seg_buf;
@@ -893,7 +912,29 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     }
     AggArgs g = agg_args(ctx);
     span_begin(ctx, SLAG_STAGE_AGGREGATE, st);
-    launch_aggregate(g, nblocks, ctx->tc_err, st);
+    if (ctx->precision == SLAG_PREC_LATENT32) {
+        // mean codes per Gaussian, then the decoder in chunks of rows (internal order) -> E in caller order
+        const int64_t chunk = std::min<int64_t>(n, 1 << 18);
+        float *Z = nullptr, *Y = nullptr;
+        CK(dalloc(&Z, n * kLatent));
+        cudaError_t e = dalloc(&Y, chunk * ctx->D);
+        if (e == cudaSuccess) e = grow(ctx->lat_hidden, ctx->lat_hidden_cap, chunk * kLatentHidden, st);
+        if (e != cudaSuccess) {
+            dfree(Z); dfree(Y);
+            return fail(ctx, SLAG_ERR_OOM, "latent decode buffers");
+        }
+        CK(cudaMemsetAsync(ctx->touched, 0, sizeof(unsigned long long), st));
+        launch_latent_aggregate(g, ctx->ztable, Z, nblocks, st);
+        for (int64_t g0 = 0; g0 < n; g0 += chunk) {
+            const int64_t rows = std::min<int64_t>(chunk, n - g0);
+            latent_decode(ctx->lat_params, ctx->D, Z + g0 * kLatent, (int)rows, ctx->lat_hidden, Y, st);
+            launch_latent_finish(g, Y, g0, rows, st);
+        }
+        CK(cudaStreamSynchronize(st));
+        dfree(Z); dfree(Y);
+    } else {
+        launch_aggregate(g, nblocks, ctx->tc_err, st);
+    }
     // query candidates: the rows of E with a non-zero embedding, in caller order
     launch_touched_rows(ctx->inv_norm, n, ctx->qflags, ctx->qpos, ctx->qrows, ctx->d_nq, ctx->scratch, st);
     span_end(ctx, st);
@@ -1105,6 +1146,19 @@ slag_status slag_export_partitions(slag_ctx *ctx, const char *dir, int32_t cells
     return SLAG_OK;
 }
 
+slag_status slag_set_latent(slag_ctx *ctx, const float *params) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    if (!params) return fail(ctx, SLAG_ERR_INVALID_ARG, "params is NULL");
+    if (ctx->precision != SLAG_PREC_LATENT32) return fail(ctx, SLAG_ERR_STATE, "context not created with SLAG_PREC_LATENT32");
+    if (ctx->stats.views > 0) return fail(ctx, SLAG_ERR_STATE, "slag_set_latent after the first view");
+    CK(cudaSetDevice(ctx->device));
+    const int64_t P = latent_layout(ctx->D).total;
+    if (!ctx->lat_params) CK(dalloc(&ctx->lat_params, P));
+    CK(cudaMemcpyAsync(ctx->lat_params, params, sizeof(float) * (size_t)P, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SLAG_OK;
+}
+
 uint64_t slag_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 slag_status slag_get_stats(const slag_ctx *ctx, slag_stats *out) {
@@ -1135,6 +1189,7 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
     dfree(ctx->table); dfree(ctx->E); dfree(ctx->inv_norm); dfree(ctx->wsum);
     dfree(ctx->qrows); dfree(ctx->qflags); dfree(ctx->qpos); dfree(ctx->d_nq);
+    dfree(ctx->lat_params); dfree(ctx->ztable); dfree(ctx->lat_hidden);
     dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);
     scratch_free(ctx->scratch);
     for (auto &sp : ctx->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }

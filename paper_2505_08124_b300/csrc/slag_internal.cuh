@@ -252,6 +252,31 @@ struct AggArgs {
 // when a bounded wait gives up
 void launch_aggregate(const AggArgs &a, int64_t nblocks, uint32_t *err, cudaStream_t st);
 
+// k_latent.cu: the latent form's autoencoder (D -> kLatentHidden -> kLatent -> kLatentHidden -> D)
+constexpr int kLatent = 32;
+constexpr int kLatentHidden = 256;
+void latent_gemm(bool ta, bool tb, int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C,
+                 int ldc, const float *bias, bool gelu_act, float *pre, bool round_a, bool round_b, bool accumulate,
+                 cudaStream_t st);
+void latent_loss(const float *Y, const float *X, int B, int D, float *dY, float *loss_sum, cudaStream_t st);
+void latent_gelu_bwd(float *dH, const float *pre, int64_t n, cudaStream_t st);
+void latent_colsum(const float *dC, int M, int N, float *db, cudaStream_t st);
+void latent_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, int step, cudaStream_t st);
+void latent_gather_rows(const float *src, const uint32_t *idx, int rows, int D, float *dst, cudaStream_t st);
+// Z (n x kLatent, internal order) = sum w z_col / sum w per Gaussian from the sorted triple log
+void launch_latent_aggregate(const AggArgs &a, const float *ztable, float *Z, int64_t nblocks, cudaStream_t st);
+// E[orig] = Y[g] (untouched Gaussians: 0), inv_norm, wsum, touched count
+void launch_latent_finish(const AggArgs &a, const float *Y, int64_t g0, int64_t rows, cudaStream_t st);
+
+// slag_latent.cu: parameter layout and inference for input width D
+struct LatentLayout {
+    int64_t W1, b1, W2, b2, W3, b3, W4, b4, total;
+};
+LatentLayout latent_layout(int32_t D);
+// enc: X (rows x D) -> Z (rows x kLatent); dec: Z -> Y (rows x D); hidden: rows x kLatentHidden scratch
+void latent_encode(const float *params, int32_t D, const float *X, int rows, float *hidden, float *Z, cudaStream_t st);
+void latent_decode(const float *params, int32_t D, const float *Z, int rows, float *hidden, float *Y, cudaStream_t st);
+
 // k_query.cu
 size_t query_cand_entries(int32_t B, int64_t n, int32_t k);
 // per query: the best k of `per_query` candidates (score, index; index 0xffffffff = none);

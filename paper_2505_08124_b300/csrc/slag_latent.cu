@@ -1,0 +1,223 @@
+// The latent form's autoencoder: parameter layout, inference and training
+// (C ABI: slag_latent_param_count, slag_latent_train, slag_latent_apply).
+//
+// Architecture for input width D: enc(x) = W2^T gelu(W1^T x + b1) + b2 and
+// dec(z) = W4^T gelu(W3^T z + b3) + b4 with W1: D x 256, W2: 256 x 32,
+// W3: 32 x 256, W4: 256 x D (row-major, input x output), erf-GELU. The
+// products take the weights rounded to bfloat16 with float32 accumulation;
+// training keeps float32 masters and updates them with Adam (beta 0.9 / 0.999,
+// eps 1e-8) on the per-sample loss mean((dec(enc(x)) - x)^2) + (1 - cos).
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <random>
+#include <vector>
+
+#include "slag_internal.cuh"
+
+namespace slag {
+
+LatentLayout latent_layout(int32_t D) {
+    const int64_t H = kLatentHidden, L = kLatent;
+    LatentLayout o;
+    int64_t at = 0;
+    o.W1 = at; at += (int64_t)D * H;
+    o.b1 = at; at += H;
+    o.W2 = at; at += H * L;
+    o.b2 = at; at += L;
+    o.W3 = at; at += L * H;
+    o.b3 = at; at += H;
+    o.W4 = at; at += H * D;
+    o.b4 = at; at += D;
+    o.total = at;
+    return o;
+}
+
+void latent_encode(const float *p, int32_t D, const float *X, int rows, float *hidden, float *Z, cudaStream_t st) {
+    const LatentLayout o = latent_layout(D);
+    latent_gemm(false, false, rows, kLatentHidden, D, X, D, p + o.W1, kLatentHidden, hidden, kLatentHidden, p + o.b1,
+                true, nullptr, false, true, false, st);
+    latent_gemm(false, false, rows, kLatent, kLatentHidden, hidden, kLatentHidden, p + o.W2, kLatent, Z, kLatent,
+                p + o.b2, false, nullptr, false, true, false, st);
+}
+
+void latent_decode(const float *p, int32_t D, const float *Z, int rows, float *hidden, float *Y, cudaStream_t st) {
+    const LatentLayout o = latent_layout(D);
+    latent_gemm(false, false, rows, kLatentHidden, kLatent, Z, kLatent, p + o.W3, kLatentHidden, hidden,
+                kLatentHidden, p + o.b3, true, nullptr, false, true, false, st);
+    latent_gemm(false, false, rows, D, kLatentHidden, hidden, kLatentHidden, p + o.W4, D, Y, D, p + o.b4, false,
+                nullptr, false, true, false, st);
+}
+
+}  // namespace slag
+
+using namespace slag;
+
+namespace {
+
+template <typename T>
+cudaError_t dmalloc(T **p, int64_t count) {
+    *p = nullptr;
+    return cudaMalloc((void **)p, sizeof(T) * (size_t)(count > 0 ? count : 1));
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t slag_latent_param_count(int32_t dim) { return dim >= 32 ? latent_layout(dim).total : 0; }
+
+slag_status slag_latent_train(const float *samples, int64_t n, int32_t dim, int32_t epochs, int32_t batch, float lr,
+                              uint64_t seed, int32_t on_device, float *out_params, float *out_loss,
+                              void *cuda_stream) {
+    if (!samples || !out_params || n < 1 || dim < 32 || dim > 4096 || dim % 32 != 0 || epochs < 1 || batch < 1 ||
+        !(lr > 0.f) || n >= (1LL << 31))
+        return SLAG_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const LatentLayout o = latent_layout(dim);
+    const int64_t P = o.total;
+    const int Bt = (int)std::min<int64_t>(batch, n);
+    const int H = kLatentHidden, L = kLatent, D = dim;
+
+    // initial parameters: uniform(-a, a) with a = sqrt(6 / (fan_in + fan_out)), zero biases
+    std::vector<float> h(P, 0.f);
+    std::mt19937_64 rng(seed);
+    auto init = [&](int64_t at, int fin, int fout) {
+        std::uniform_real_distribution<float> u(-sqrtf(6.f / (float)(fin + fout)), sqrtf(6.f / (float)(fin + fout)));
+        for (int64_t i = 0; i < (int64_t)fin * fout; ++i) h[at + i] = u(rng);
+    };
+    init(o.W1, D, H);
+    init(o.W2, H, L);
+    init(o.W3, L, H);
+    init(o.W4, H, D);
+
+    float *dX = nullptr, *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *Xb = nullptr;
+    float *H1 = nullptr, *A1 = nullptr, *Z = nullptr, *H3 = nullptr, *A3 = nullptr, *Y = nullptr;
+    float *dY = nullptr, *dH3 = nullptr, *dZ = nullptr, *dH1 = nullptr, *loss = nullptr;
+    uint32_t *idx = nullptr;
+    slag_status rc = SLAG_OK;
+    auto cleanup = [&]() {
+        float *bufs[] = {p, g, m, v, Xb, H1, A1, Z, H3, A3, Y, dY, dH3, dZ, dH1, loss};
+        for (float *b : bufs) if (b) cudaFree(b);
+        if (dX && !on_device) cudaFree(dX);
+        if (idx) cudaFree(idx);
+    };
+#define CT(call)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            cleanup();                                                                                   \
+            return e_ == cudaErrorMemoryAllocation ? SLAG_ERR_OOM : SLAG_ERR_CUDA;                       \
+        }                                                                                                \
+    } while (0)
+    if (on_device) {
+        dX = const_cast<float *>(samples);
+    } else {
+        CT(dmalloc(&dX, n * D));
+        CT(cudaMemcpyAsync(dX, samples, sizeof(float) * (size_t)(n * D), cudaMemcpyHostToDevice, st));
+    }
+    CT(dmalloc(&p, P)); CT(dmalloc(&g, P)); CT(dmalloc(&m, P)); CT(dmalloc(&v, P));
+    CT(dmalloc(&Xb, (int64_t)Bt * D)); CT(dmalloc(&Y, (int64_t)Bt * D)); CT(dmalloc(&dY, (int64_t)Bt * D));
+    CT(dmalloc(&H1, (int64_t)Bt * H)); CT(dmalloc(&A1, (int64_t)Bt * H)); CT(dmalloc(&dH1, (int64_t)Bt * H));
+    CT(dmalloc(&H3, (int64_t)Bt * H)); CT(dmalloc(&A3, (int64_t)Bt * H)); CT(dmalloc(&dH3, (int64_t)Bt * H));
+    CT(dmalloc(&Z, (int64_t)Bt * L)); CT(dmalloc(&dZ, (int64_t)Bt * L));
+    CT(dmalloc(&loss, 1));
+    CT(dmalloc(&idx, n));
+    CT(cudaMemcpyAsync(p, h.data(), sizeof(float) * (size_t)P, cudaMemcpyHostToDevice, st));
+    CT(cudaMemsetAsync(m, 0, sizeof(float) * (size_t)P, st));
+    CT(cudaMemsetAsync(v, 0, sizeof(float) * (size_t)P, st));
+
+    std::vector<uint32_t> perm((size_t)n);
+    for (int64_t i = 0; i < n; ++i) perm[i] = (uint32_t)i;
+    int step = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::shuffle(perm.begin(), perm.end(), rng);
+        CT(cudaMemcpyAsync(idx, perm.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice, st));
+        CT(cudaMemsetAsync(loss, 0, sizeof(float), st));
+        int64_t seen = 0;
+        for (int64_t b0 = 0; b0 + Bt <= n; b0 += Bt) {   // full batches; the tail waits for the next shuffle
+            const int B = Bt;
+            latent_gather_rows(dX, idx + b0, B, D, Xb, st);
+            // forward
+            latent_gemm(false, false, B, H, D, Xb, D, p + o.W1, H, H1, H, p + o.b1, true, A1, false, true, false, st);
+            latent_gemm(false, false, B, L, H, H1, H, p + o.W2, L, Z, L, p + o.b2, false, nullptr, false, true, false, st);
+            latent_gemm(false, false, B, H, L, Z, L, p + o.W3, H, H3, H, p + o.b3, true, A3, false, true, false, st);
+            latent_gemm(false, false, B, D, H, H3, H, p + o.W4, D, Y, D, p + o.b4, false, nullptr, false, true, false, st);
+            latent_loss(Y, Xb, B, D, dY, loss, st);
+            // backward (weights rounded as in the forward pass)
+            latent_gemm(true, false, H, D, B, H3, H, dY, D, g + o.W4, D, nullptr, false, nullptr, false, false, false, st);
+            latent_colsum(dY, B, D, g + o.b4, st);
+            latent_gemm(false, true, B, H, D, dY, D, p + o.W4, D, dH3, H, nullptr, false, nullptr, false, true, false, st);
+            latent_gelu_bwd(dH3, A3, (int64_t)B * H, st);
+            latent_gemm(true, false, L, H, B, Z, L, dH3, H, g + o.W3, H, nullptr, false, nullptr, false, false, false, st);
+            latent_colsum(dH3, B, H, g + o.b3, st);
+            latent_gemm(false, true, B, L, H, dH3, H, p + o.W3, H, dZ, L, nullptr, false, nullptr, false, true, false, st);
+            latent_gemm(true, false, H, L, B, H1, H, dZ, L, g + o.W2, L, nullptr, false, nullptr, false, false, false, st);
+            latent_colsum(dZ, B, L, g + o.b2, st);
+            latent_gemm(false, true, B, H, L, dZ, L, p + o.W2, L, dH1, H, nullptr, false, nullptr, false, true, false, st);
+            latent_gelu_bwd(dH1, A1, (int64_t)B * H, st);
+            latent_gemm(true, false, D, H, B, Xb, D, dH1, H, g + o.W1, H, nullptr, false, nullptr, false, false, false, st);
+            latent_colsum(dH1, B, H, g + o.b1, st);
+            latent_adam(p, g, m, v, P, lr, ++step, st);
+            seen += B;
+        }
+        if (out_loss) {
+            float ls = 0.f;
+            CT(cudaMemcpyAsync(&ls, loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+            CT(cudaStreamSynchronize(st));
+            out_loss[ep] = seen > 0 ? ls / (float)seen : 0.f;
+        }
+    }
+    CT(cudaMemcpyAsync(out_params, p, sizeof(float) * (size_t)P, cudaMemcpyDeviceToHost, st));
+    CT(cudaStreamSynchronize(st));
+    CT(cudaGetLastError());
+#undef CT
+    cleanup();
+    return rc;
+}
+
+slag_status slag_latent_apply(const float *params, int32_t dim, const float *in, int64_t rows, int32_t mode,
+                              float *out, void *cuda_stream) {
+    if (!params || !in || !out || rows < 0 || rows >= (1LL << 31) || dim < 32 || dim > 4096 || dim % 32 != 0 ||
+        mode < 0 || mode > 2)
+        return SLAG_ERR_INVALID_ARG;
+    if (rows == 0) return SLAG_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t P = latent_layout(dim).total;
+    const int64_t din = mode == 1 ? kLatent : dim, dout = mode == 0 ? kLatent : dim;
+    float *p = nullptr, *X = nullptr, *Hd = nullptr, *Z = nullptr, *Y = nullptr;
+    auto cleanup = [&]() {
+        float *bufs[] = {p, X, Hd, Z, Y};
+        for (float *b : bufs) if (b) cudaFree(b);
+    };
+#define CA2(call)                                                                                        \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            cleanup();                                                                                   \
+            return e_ == cudaErrorMemoryAllocation ? SLAG_ERR_OOM : SLAG_ERR_CUDA;                       \
+        }                                                                                                \
+    } while (0)
+    CA2(dmalloc(&p, P)); CA2(dmalloc(&X, rows * din)); CA2(dmalloc(&Hd, rows * kLatentHidden));
+    CA2(dmalloc(&Z, rows * kLatent)); CA2(dmalloc(&Y, rows * dim));
+    CA2(cudaMemcpyAsync(p, params, sizeof(float) * (size_t)P, cudaMemcpyHostToDevice, st));
+    CA2(cudaMemcpyAsync(X, in, sizeof(float) * (size_t)(rows * din), cudaMemcpyHostToDevice, st));
+    if (mode == 0) {
+        latent_encode(p, dim, X, (int)rows, Hd, Z, st);
+    } else if (mode == 1) {
+        latent_decode(p, dim, X, (int)rows, Hd, Y, st);
+    } else {
+        latent_encode(p, dim, X, (int)rows, Hd, Z, st);
+        latent_decode(p, dim, Z, (int)rows, Hd, Y, st);
+    }
+    CA2(cudaMemcpyAsync(out, mode == 0 ? Z : Y, sizeof(float) * (size_t)(rows * dout), cudaMemcpyDeviceToHost, st));
+    CA2(cudaStreamSynchronize(st));
+    CA2(cudaGetLastError());
+#undef CA2
+    cleanup();
+    return SLAG_OK;
+}
+
+}  // extern "C"

@@ -22,6 +22,7 @@ _NAMES = {1: "INVALID_ARG", 2: "STATE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "C
 WEIGHT_ALPHA_T, WEIGHT_KERNEL = 0, 1
 PREC_FP32 = 0
 PREC_BF16 = 1
+PREC_LATENT32 = 2
 FLAG_EMBEDDINGS_ON_HOST = 1
 
 
@@ -59,7 +60,8 @@ _lib = None
 EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_query_batch", "slag_reset",
            "slag_get_stats", "slag_last_error", "slag_destroy", "slag_bin_view", "slag_render_debug",
            "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk", "slag_kernel_launches",
-           "slag_export_partitions")
+           "slag_export_partitions", "slag_latent_param_count", "slag_latent_train", "slag_latent_apply",
+           "slag_set_latent")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -94,6 +96,11 @@ def load_library(path: str = LIB_PATH):
     lib.slag_set_profiling.argtypes = [P, i32]
     lib.slag_get_profile.argtypes = [P, ctypes.POINTER(CProfile), i32]
     lib.slag_export_partitions.argtypes = [P, ctypes.c_char_p, i32, i32, i64, ctypes.POINTER(i64)]
+    lib.slag_latent_param_count.argtypes = [i32]
+    lib.slag_latent_param_count.restype = i64
+    lib.slag_latent_train.argtypes = [P, i64, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, i32, P, P, P]
+    lib.slag_latent_apply.argtypes = [P, i32, P, i64, i32, P, P]
+    lib.slag_set_latent.argtypes = [P, P]
     lib.slag_kernel_launches.argtypes = []
     lib.slag_kernel_launches.restype = ctypes.c_uint64
     lib.slag_noalloc_query_topk.argtypes = [P, i64, i32, P, P, i32, i32, P, P, P, P]
@@ -156,7 +163,8 @@ class Lifter:
     """One lifting context: a fixed Gaussian set, views added one at a time."""
 
     def __init__(self, gaussians, dim: int = 512, weight_mode: int = WEIGHT_ALPHA_T,
-                 stream: Optional[int] = None, precision: int = PREC_FP32, embeddings_on_host: bool = False):
+                 stream: Optional[int] = None, precision: int = PREC_FP32, embeddings_on_host: bool = False,
+                 latent_params=None):
         self._lib = load_library()
         self.n = int(gaussians.means.shape[0])
         self.dim = int(dim)
@@ -172,6 +180,9 @@ class Lifter:
         if rc != OK:
             raise SlagError(rc, "slag_create")
         self._h = h
+        if latent_params is not None:
+            lp = np.ascontiguousarray(latent_params, np.float32)
+            self._check(self._lib.slag_set_latent(self._h, lp.ctypes.data_as(ctypes.c_void_p)), "slag_set_latent")
 
     # -- helpers --------------------------------------------------------------
     def _check(self, rc: int, what: str):
@@ -263,7 +274,8 @@ class Lifter:
         written = ctypes.c_int64()
         self._check(self._lib.slag_export_partitions(self._h, os.fsencode(directory), int(cells_x), int(cells_y),
                                                      int(chunk_gaussians), ctypes.byref(written)),
-                    "slag_export_partitions")
+                    "slag_export_partitions", "slag_latent_param_count", "slag_latent_train", "slag_latent_apply",
+           "slag_set_latent")
         return int(written.value)
 
     def stats(self) -> dict:
@@ -339,4 +351,39 @@ def read_partitions(directory: str) -> dict:
         r = np.frombuffer(raw, rec, cnt, 40)
         out[(int(cx), int(cy))] = {"bounds": bounds, "ids": r["id"].copy(), "wsum": r["wsum"].copy(),
                                    "E": r["E"].copy()}
+    return out
+
+
+def latent_param_count(dim: int) -> int:
+    return int(load_library().slag_latent_param_count(int(dim)))
+
+
+def latent_train(samples, epochs: int = 4, batch: int = 1024, lr: float = 1e-3, seed: int = 0):
+    """Trains the latent form's autoencoder on host samples (n x dim float32); returns
+    (parameters, mean loss per epoch)."""
+    lib = load_library()
+    X = np.ascontiguousarray(samples, np.float32)
+    n, dim = X.shape
+    params = np.empty(latent_param_count(dim), np.float32)
+    losses = np.empty(int(epochs), np.float32)
+    rc = lib.slag_latent_train(X.ctypes.data_as(ctypes.c_void_p), n, dim, int(epochs), int(batch), float(lr),
+                               int(seed), 0, params.ctypes.data_as(ctypes.c_void_p),
+                               losses.ctypes.data_as(ctypes.c_void_p), None)
+    if rc != OK:
+        raise SlagError(rc, "slag_latent_train")
+    return params, losses
+
+
+def latent_apply(params, X, mode: int):
+    """mode 0: encode (rows x dim -> rows x 32); 1: decode (rows x 32 -> rows x dim); 2: both."""
+    lib = load_library()
+    p = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    rows = X.shape[0]
+    dim = X.shape[1] if mode != 1 else (p.size - 2 * 32 * 256 - 256 - 32 - 256) // (2 * 256 + 1)
+    out = np.empty((rows, 32 if mode == 0 else dim), np.float32)
+    rc = lib.slag_latent_apply(p.ctypes.data_as(ctypes.c_void_p), int(dim), X.ctypes.data_as(ctypes.c_void_p), rows,
+                               int(mode), out.ctypes.data_as(ctypes.c_void_p), None)
+    if rc != OK:
+        raise SlagError(rc, "slag_latent_apply")
     return out

@@ -283,9 +283,17 @@ def config_precision(seed: int = 2) -> Scene:
 
 def small_scene(seed: int, n: int, n_views: int, width: int, height: int, n_segments: int,
                 dim: int = 64, surfaces: int = 0, empty_fraction: float = 0.0,
-                n_protos: int = 8) -> Scene:
+                n_protos: int = 8, noise_sigma: float = 0.1) -> Scene:
     """Parity-test scene: sizes chosen so the oracle finishes in seconds."""
     g = ellipsoid_gaussians(seed, n, surfaces) if surfaces else random_gaussians(seed, n)
     return make_scene(f"small{seed}", seed, g, n_views=n_views, width=width, height=height,
                       n_segments=n_segments, n_protos=n_protos, dim=dim, jitter=True,
-                      empty_fraction=empty_fraction)
+                      empty_fraction=empty_fraction, noise_sigma=noise_sigma)
+
+
+def segment_samples(scene_seed: int, n: int, dim: int, n_protos: int, noise_sigma: float = 0.1,
+                    sample_seed: int = 0) -> np.ndarray:
+    """n segment embeddings drawn like the tables of the scene made with `scene_seed` (the
+    same prototypes and noise law): training data for the latent form's autoencoder."""
+    protos = _prototypes(scene_seed, n_protos, dim)
+    return prototype_table(_rng(scene_seed, 50_000 + sample_seed), protos, n, noise_sigma)
