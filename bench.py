@@ -378,7 +378,9 @@ def run_slag(a):
 
     forms = None
     if not a.no_forms:
-        forms = {"bf16": _bf16_form(S, torch, L, g, D, cams, d_seg, d_tab, d_Q, a, stream, dev, rank_max, ws)}
+        fargs = (L, g, D, cams, d_seg, d_tab, d_Q, a, stream, dev, rank_max, ws)
+        forms = {"bf16": dict(_form(S, torch, *fargs, precision=S.PREC_BF16), dtype="bf16 operands, f32 accumulate"),
+                 "latent32": _latent_form(S, torch, scene, *fargs)}
 
     cpu = None
     if rank == 0 and not a.no_cpu:
@@ -409,14 +411,15 @@ def run_slag(a):
         dist.destroy_process_group()
 
 
-def _bf16_form(S, torch, L, g, D, cams, d_seg, d_tab, d_Q, a, stream, dev, rank_max, ws):
-    """The BF16 form on the same workload: the same step with the contraction of the weights
-    and the segment embeddings in bfloat16 (float32 accumulation); its error is stated against
-    the float32 path's embeddings of the same job (1 - cosine per Gaussian with sum w >= 1e-3)
-    and its top-10 answers against the float32 path's (strict overlap, and tie-tolerant: an id
-    counts when its float32 cosine is within 1e-3 of the float32 10th best)."""
+def _form(S, torch, L, g, D, cams, d_seg, d_tab, d_Q, a, stream, dev, rank_max, ws, precision, latent=None,
+          tie_eps=1e-3):
+    """A form of the aggregation on the same workload: the same step with another precision;
+    its error is stated against the float32 path's embeddings of the same job (1 - cosine per
+    Gaussian with sum w >= 1e-3) and its top-10 answers against the float32 path's (strict
+    overlap, and tie-tolerant: an id counts when its float32 cosine is within tie_eps of the
+    float32 10th best)."""
     n = g.n
-    Lb = S.Lifter(g, dim=D, stream=stream.cuda_stream, precision=S.PREC_BF16)
+    Lb = S.Lifter(g, dim=D, stream=stream.cuda_stream, precision=precision, latent_params=latent)
     ids_b = torch.empty((a.queries, a.k), dtype=torch.int64, device=dev)
     sc_b = torch.empty((a.queries, a.k), dtype=torch.float32, device=dev)
     cnt_b = torch.empty(a.queries, dtype=torch.int32, device=dev)
@@ -458,13 +461,30 @@ def _bf16_form(S, torch, L, g, D, cams, d_seg, d_tab, d_Q, a, stream, dev, rank_
     Qd = d_Q.double()
     sb = torch.einsum("qkd,qd->qk", En[ids_b.clamp_min(0)], Qd)
     sf = torch.einsum("qkd,qd->qk", En[ids_f.clamp_min(0)], Qd)
-    tie = (sb >= sf.min(dim=1, keepdim=True).values - 1e-3).double().mean().item()
+    tie = (sb >= sf.min(dim=1, keepdim=True).values - tie_eps).double().mean().item()
     strict = float(np.mean([len(set(x) & set(y)) / a.k for x, y in zip(ids_b.tolist(), ids_f.tolist())]))
     return {"value": job_rate(contrib * a.steps, ws, ms / 1e3), "unit": UNIT, "ms_per_step": ms / a.steps,
-            "views_per_s": job_rate(len(cams) * a.steps, ws, ms / 1e3), "dtype": "bf16 operands, f32 accumulate",
+            "views_per_s": job_rate(len(cams) * a.steps, ws, ms / 1e3),
             "cos_err_vs_fp32": {"max": float((1 - cos).max().item()), "mean": float((1 - cos).mean().item()),
                                 "gaussians": int(ok.sum().item())},
-            "top10_agree_vs_fp32": {"tie_tolerant": tie, "strict": strict}}
+            "top10_agree_vs_fp32": {"tie_tolerant": tie, "tie_eps": tie_eps, "strict": strict}}
+
+
+def _latent_form(S, torch, scene, *args):
+    """The latent form: the autoencoder trained on segment embeddings drawn like the
+    workload's tables (same prototypes and noise law), then the same step aggregating codes."""
+    import synth
+    D = scene.dim
+    n_train, epochs = 1 << 18, 4
+    X = synth.segment_samples(1, n_train, D, 32, noise_sigma=0.1)     # the mid-scale scene's law (seed 1)
+    t0 = time.perf_counter()
+    params, losses = S.latent_train(X, epochs=epochs, batch=512, lr=2e-3, seed=5)
+    train_s = time.perf_counter() - t0
+    out = _form(S, torch, *args, precision=S.PREC_LATENT32, latent=params, tie_eps=1e-2)
+    out["dtype"] = "32-d codes, bf16 weights, f32 accumulate"
+    out["training"] = {"samples": n_train, "epochs": epochs, "seconds": train_s,
+                       "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1])}
+    return out
 
 
 def main():
