@@ -233,6 +233,33 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
 slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_T, float *out_wsum,
                               int32_t *out_count);
 
+/* ---- batched scenes ------------------------------------------------------- */
+
+/* One view of a batched call (the arguments of slag_add_view). */
+typedef struct {
+    const slag_camera *camera;
+    const int32_t *seg_ids;
+    const float *seg_table;
+    int32_t M;
+    int32_t on_device;
+} slag_view;
+
+/* Adds views to several independent scenes (one context each) in one call:
+ * views[c][0 .. n_views[c]) go to ctxs[c], taken round-robin by view index
+ * (view 0 of every scene, then view 1, ...), so that each scene's pipeline
+ * has views in flight while the host waits on another's. The result of each
+ * context is that of adding its views in order with slag_add_view. Stops at
+ * the first error; *failed_ctx (nullable) receives its context index, or -1. */
+slag_status slag_add_views_batched(int32_t n_ctx, slag_ctx *const *ctxs, const slag_view *const *views,
+                                   const int32_t *n_views, int32_t *failed_ctx);
+
+/* Query autotuning (on by default): for a batch shape with enough work, the
+ * first device-side query times the tensor-core kernel at the default split of
+ * the Gaussian tiles, half and double of it, and keeps the fastest for that
+ * (batch, candidates) shape. Device-side queries run as a CUDA graph that is
+ * captured once and replayed while the buffers, shape and embeddings repeat. */
+slag_status slag_set_autotune(slag_ctx *ctx, int32_t enable);
+
 /* ---- the latent form: autoencoder D -> 256 -> 32 -> 256 -> D ---------------- */
 
 /* Parameters of the autoencoder for input width dim (float32, layout: W1 dim x 256,

@@ -298,6 +298,8 @@ size_t tc_smem() { return (size_t)kStages * kStageBytes + 64 + kN * 4; }
 
 bool query_tc_supported(int32_t D, int32_t k) { return k >= 1 && k <= kTopTC && D % kKC == 0; }
 
+int64_t query_tc_tiles(int64_t n) { return (n + kN - 1) / kN; }
+
 int32_t query_tc_splits(int32_t B, int64_t n) {
     const int64_t qt = (B + kM - 1) / kM;
     const int64_t nt = (n + kN - 1) / kN;
@@ -309,7 +311,7 @@ int32_t query_tc_splits(int32_t B, int64_t n) {
 
 void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, const uint32_t *rows,
                           int64_t n, int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
-                          float *out_scores, int32_t *out_count, uint32_t *err, cudaStream_t st) {
+                          float *out_scores, int32_t *out_count, uint32_t *err, cudaStream_t st, int32_t splits) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(query_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem());
@@ -320,7 +322,9 @@ void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float
         launch_query_merge(cand_s, cand_i, 0, B, k, rows, out_ids, out_scores, out_count, st);
         return;
     }
-    const int32_t nsplit = query_tc_splits(B, n);
+    int32_t nsplit = splits > 0 ? splits : query_tc_splits(B, n);
+    const int64_t ntiles = (n + kN - 1) / kN;
+    if (nsplit > ntiles) nsplit = (int32_t)ntiles;
     dim3 grid((unsigned)((B + kM - 1) / kM), (unsigned)nsplit);
     query_tc_k<<<grid, kThreadsTC, tc_smem(), st>>>(Q, B, E, inv_norm, rows, n, D, k, nsplit, cand_s, cand_i, err); note_launch();
     launch_query_merge(cand_s, cand_i, (int64_t)nsplit * kk, B, k, rows, out_ids, out_scores, out_count, st);

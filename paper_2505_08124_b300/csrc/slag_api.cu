@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <cmath>
 #include <string>
 #include <utility>
@@ -154,7 +155,28 @@ struct slag_ctx {
     float *lat_hidden = nullptr;             // rows x kLatentHidden
     int64_t lat_hidden_cap = 0;
 
-    // queries
+    // queries: split counts chosen by the autotuner per (batch, candidates) shape, and the
+    // CUDA graph of the last device-side query (replayed while its buffers and shape repeat)
+    std::map<std::pair<int32_t, int64_t>, int32_t> qsplits;
+    bool autotune = true;
+    cudaStream_t qstream = nullptr;
+    cudaEvent_t qev_in = nullptr, qev_out = nullptr;
+    cudaGraphExec_t qgraph = nullptr;
+    unsigned long long qgraph_launches = 0;  // kernels in the graph (counted at each replay)
+    struct QKey {
+        const float *Q;
+        int64_t *ids;
+        float *scores;
+        int32_t *cnt;
+        int32_t B, k, splits;
+        int64_t nq;
+        uint64_t gen;
+        bool operator==(const QKey &o) const {
+            return Q == o.Q && ids == o.ids && scores == o.scores && cnt == o.cnt && B == o.B && k == o.k &&
+                   splits == o.splits && nq == o.nq && gen == o.gen;
+        }
+    } qkey{};
+    uint64_t qgen = 0;                       // bumped by every finalize (candidate list changes)
     float *qbuf = nullptr;
     int64_t qbuf_cap = 0;
     float *cand_s = nullptr;
@@ -512,6 +534,9 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     CA(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
     CA(cudaEventCreateWithFlags(&ctx->ev_front, cudaEventDisableTiming));
     CA(cudaEventCreateWithFlags(&ctx->ev_consumed, cudaEventDisableTiming));
+    CA(cudaStreamCreateWithFlags(&ctx->qstream, cudaStreamNonBlocking));
+    CA(cudaEventCreateWithFlags(&ctx->qev_in, cudaEventDisableTiming));
+    CA(cudaEventCreateWithFlags(&ctx->qev_out, cudaEventDisableTiming));
     CA(dalloc(&ctx->totals, 4));
     ctx->log_count = ctx->totals;
     ctx->contrib = ctx->totals + 1;
@@ -951,6 +976,7 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     ctx->stats.touched = (int64_t)ctx->hc->touched;
     ctx->n_q = (int64_t)ctx->hc->n_q;
     ctx->finalized = true;
+    ++ctx->qgen;
     return SLAG_OK;
 }
 
@@ -996,14 +1022,93 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
         scores = ctx->qscores;
         cnt = ctx->qcount;
     }
-    span_begin(ctx, SLAG_STAGE_QUERY, st);
-    if (tc)
-        launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s, ctx->cand_i,
-                             ids, scores, cnt, ctx->tc_err, st);
-    else
-        launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s, ctx->cand_i, ids,
-                          scores, cnt, st);
-    span_end(ctx, st);
+    int32_t splits = 0;
+    if (tc && nq > 0) {
+        const int64_t ntiles = query_tc_tiles(nq);
+        const int32_t d = std::min<int64_t>(query_tc_splits(B, nq), ntiles);
+        auto it = ctx->qsplits.find({B, nq});
+        if (it != ctx->qsplits.end()) {
+            splits = it->second;
+        } else if (ctx->autotune && (double)B * (double)nq >= 2e7) {
+            // autotuner: time the default split, half and double (once per shape, after a warm run)
+            const int32_t cands[3] = {d, std::max(1, d / 2), (int32_t)std::min<int64_t>(ntiles, 2 * (int64_t)d)};
+            const int kk = k < 16 ? k : 16;
+            const int64_t need = (int64_t)B * cands[2] * kk;
+            if (need > ctx->cand_cap) {
+                int64_t c1 = ctx->cand_cap, c2 = ctx->cand_cap;
+                CK(grow(ctx->cand_s, c1, need, st));
+                CK(grow(ctx->cand_i, c2, need, st));
+                ctx->cand_cap = c1;
+            }
+            cudaEvent_t t0 = take_event(ctx), t1 = take_event(ctx);
+            float best = INFINITY;
+            int32_t pick = d;
+            for (int32_t c : cands) {
+                launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s,
+                                     ctx->cand_i, ids, scores, cnt, ctx->tc_err, st, c);
+                CK(cudaEventRecord(t0, st));
+                launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s,
+                                     ctx->cand_i, ids, scores, cnt, ctx->tc_err, st, c);
+                CK(cudaEventRecord(t1, st));
+                CK(cudaEventSynchronize(t1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, t0, t1));
+                if (ms < best) { best = ms; pick = c; }
+            }
+            ctx->event_pool.push_back(t0);
+            ctx->event_pool.push_back(t1);
+            ctx->qsplits[{B, nq}] = pick;
+            splits = pick;
+        } else {
+            splits = d;
+        }
+        const int64_t need = (int64_t)B * splits * (k < 16 ? k : 16);
+        if (need > ctx->cand_cap) {
+            int64_t c1 = ctx->cand_cap, c2 = ctx->cand_cap;
+            CK(grow(ctx->cand_s, c1, need, st));
+            CK(grow(ctx->cand_i, c2, need, st));
+            ctx->cand_cap = c1;
+        }
+    }
+    auto launch = [&](cudaStream_t s2) {
+        if (tc)
+            launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s, ctx->cand_i,
+                                 ids, scores, cnt, ctx->tc_err, s2, splits);
+        else
+            launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s, ctx->cand_i, ids,
+                              scores, cnt, s2);
+    };
+    if (on_device && !ctx->prof_on) {
+        // device buffers: the launches run as a CUDA graph on the query stream, captured for this
+        // (buffers, shape, split, finalize) and replayed while they repeat
+        const slag_ctx::QKey key{dQ, ids, scores, cnt, B, k, splits, nq, ctx->qgen};
+        if (!ctx->qgraph || !(ctx->qkey == key)) {
+            if (ctx->qgraph) { cudaGraphExecDestroy(ctx->qgraph); ctx->qgraph = nullptr; }
+            cudaGraph_t graph = nullptr;
+            const unsigned long long l0 = g_launches.load(std::memory_order_relaxed);
+            CK(cudaStreamBeginCapture(ctx->qstream, cudaStreamCaptureModeRelaxed));
+            launch(ctx->qstream);
+            CK(cudaStreamEndCapture(ctx->qstream, &graph));
+            // the capture counted its kernels once; replays count them below
+            const unsigned long long l1 = g_launches.load(std::memory_order_relaxed);
+            ctx->qgraph_launches = l1 - l0;
+            g_launches.fetch_sub(l1 - l0, std::memory_order_relaxed);
+            cudaError_t e = cudaGraphInstantiate(&ctx->qgraph, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(e);
+            ctx->qkey = key;
+        }
+        CK(cudaEventRecord(ctx->qev_in, st));
+        CK(cudaStreamWaitEvent(ctx->qstream, ctx->qev_in, 0));
+        CK(cudaGraphLaunch(ctx->qgraph, ctx->qstream));
+        g_launches.fetch_add(ctx->qgraph_launches, std::memory_order_relaxed);
+        CK(cudaEventRecord(ctx->qev_out, ctx->qstream));
+        CK(cudaStreamWaitEvent(st, ctx->qev_out, 0));
+    } else {
+        span_begin(ctx, SLAG_STAGE_QUERY, st);
+        launch(st);
+        span_end(ctx, st);
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&ctx->hc->tc_err, ctx->tc_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     if (!on_device) {
@@ -1159,6 +1264,38 @@ slag_status slag_set_latent(slag_ctx *ctx, const float *params) {
     return SLAG_OK;
 }
 
+slag_status slag_add_views_batched(int32_t n_ctx, slag_ctx *const *ctxs, const slag_view *const *views,
+                                   const int32_t *n_views, int32_t *failed_ctx) {
+    if (failed_ctx) *failed_ctx = -1;
+    if (n_ctx < 0 || (n_ctx > 0 && (!ctxs || !views || !n_views))) return SLAG_ERR_INVALID_ARG;
+    int32_t most = 0;
+    for (int32_t c = 0; c < n_ctx; ++c) {
+        if (!ctxs[c] || n_views[c] < 0 || (n_views[c] > 0 && !views[c])) {
+            if (failed_ctx) *failed_ctx = c;
+            return SLAG_ERR_INVALID_ARG;
+        }
+        most = std::max(most, n_views[c]);
+    }
+    for (int32_t v = 0; v < most; ++v)
+        for (int32_t c = 0; c < n_ctx; ++c) {
+            if (v >= n_views[c]) continue;
+            const slag_view &w = views[c][v];
+            const slag_status s = slag_add_view(ctxs[c], w.camera, w.seg_ids, w.seg_table, w.M, w.on_device);
+            if (s != SLAG_OK) {
+                if (failed_ctx) *failed_ctx = c;
+                return s;
+            }
+        }
+    return SLAG_OK;
+}
+
+slag_status slag_set_autotune(slag_ctx *ctx, int32_t enable) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    ctx->autotune = enable != 0;
+    if (!ctx->autotune) ctx->qsplits.clear();
+    return SLAG_OK;
+}
+
 uint64_t slag_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 slag_status slag_get_stats(const slag_ctx *ctx, slag_stats *out) {
@@ -1181,6 +1318,10 @@ void slag_destroy(slag_ctx *ctx) {
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_front) cudaEventDestroy(ctx->ev_front);
     if (ctx->ev_consumed) cudaEventDestroy(ctx->ev_consumed);
+    if (ctx->qgraph) cudaGraphExecDestroy(ctx->qgraph);
+    if (ctx->qstream) { cudaStreamSynchronize(ctx->qstream); cudaStreamDestroy(ctx->qstream); }
+    if (ctx->qev_in) cudaEventDestroy(ctx->qev_in);
+    if (ctx->qev_out) cudaEventDestroy(ctx->qev_out);
     dfree(ctx->mean_op); dfree(ctx->cov_a); dfree(ctx->cov_b); dfree(ctx->orig_of_int); dfree(ctx->int_of_orig);
     dfree(ctx->s_hi); dfree(ctx->s_lo); dfree(ctx->s_ovf);
     dfree(ctx->dbg_T); dfree(ctx->dbg_wsum); dfree(ctx->dbg_count);

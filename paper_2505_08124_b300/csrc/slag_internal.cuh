@@ -294,9 +294,12 @@ void launch_touched_rows(const float *inv_norm, int64_t n, uint32_t *flags, uint
 
 // k_query_tc.cu: tensor-core scores (3xTF32 on tcgen05) for k <= 16 and D % 32 == 0
 bool query_tc_supported(int32_t D, int32_t k);
+// Default split of the Gaussian tiles over CTAs (one wave of 148 CTAs); tiles of n candidates.
 int32_t query_tc_splits(int32_t B, int64_t n);
+int64_t query_tc_tiles(int64_t n);
+// splits <= 0: the default split
 void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, const uint32_t *rows,
                           int64_t n, int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
-                          float *out_scores, int32_t *out_count, uint32_t *err, cudaStream_t st);
+                          float *out_scores, int32_t *out_count, uint32_t *err, cudaStream_t st, int32_t splits);
 
 }  // namespace slag

@@ -49,6 +49,11 @@ class COptions(ctypes.Structure):
                 ("flags", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
 
 
+class CView(ctypes.Structure):
+    _fields_ = [("camera", ctypes.c_void_p), ("seg_ids", ctypes.c_void_p), ("seg_table", ctypes.c_void_p),
+                ("M", ctypes.c_int32), ("on_device", ctypes.c_int32)]
+
+
 class CStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("views", "pairs", "contributions", "triples", "columns",
                                                "last_pairs", "last_contributions", "touched",
@@ -61,7 +66,7 @@ EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_
            "slag_get_stats", "slag_last_error", "slag_destroy", "slag_bin_view", "slag_render_debug",
            "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk", "slag_kernel_launches",
            "slag_export_partitions", "slag_latent_param_count", "slag_latent_train", "slag_latent_apply",
-           "slag_set_latent")
+           "slag_set_latent", "slag_add_views_batched", "slag_set_autotune")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -101,6 +106,8 @@ def load_library(path: str = LIB_PATH):
     lib.slag_latent_train.argtypes = [P, i64, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, i32, P, P, P]
     lib.slag_latent_apply.argtypes = [P, i32, P, i64, i32, P, P]
     lib.slag_set_latent.argtypes = [P, P]
+    lib.slag_add_views_batched.argtypes = [i32, P, P, P, ctypes.POINTER(i32)]
+    lib.slag_set_autotune.argtypes = [P, i32]
     lib.slag_kernel_launches.argtypes = []
     lib.slag_kernel_launches.restype = ctypes.c_uint64
     lib.slag_noalloc_query_topk.argtypes = [P, i64, i32, P, P, i32, i32, P, P, P, P]
@@ -268,14 +275,16 @@ class Lifter:
     def reset(self):
         self._check(self._lib.slag_reset(self._h), "slag_reset")
 
+    def set_autotune(self, on: bool = True):
+        self._check(self._lib.slag_set_autotune(self._h, 1 if on else 0), "slag_set_autotune")
+
     def export_partitions(self, directory: str, cells_x: int, cells_y: int, chunk_gaussians: int = 0) -> int:
         """Per-area embedding files of the touched Gaussians (see slag_export_partitions); returns
         the number of records written."""
         written = ctypes.c_int64()
         self._check(self._lib.slag_export_partitions(self._h, os.fsencode(directory), int(cells_x), int(cells_y),
                                                      int(chunk_gaussians), ctypes.byref(written)),
-                    "slag_export_partitions", "slag_latent_param_count", "slag_latent_train", "slag_latent_apply",
-           "slag_set_latent")
+                    "slag_export_partitions")
         return int(written.value)
 
     def stats(self) -> dict:
@@ -387,3 +396,28 @@ def latent_apply(params, X, mode: int):
     if rc != OK:
         raise SlagError(rc, "slag_latent_apply")
     return out
+
+
+def add_views_batched(lifters, view_lists):
+    """Adds view_lists[i] (lists of (camera, seg_ids, table) with host numpy or CUDA torch arrays)
+    to lifters[i], interleaved round-robin across the scenes (slag_add_views_batched)."""
+    lib = load_library()
+    keep = []
+    arrays = []
+    counts = (ctypes.c_int32 * len(lifters))()
+    for i, (L, views) in enumerate(zip(lifters, view_lists)):
+        arr = (CView * max(1, len(views)))()
+        for j, (cam, seg, tab) in enumerate(views):
+            c = camera_struct(cam)
+            sp, sdev, s_keep = _ptr(seg, np.int32)
+            tp, tdev, t_keep = _ptr(tab, np.float32)
+            keep += [c, s_keep, t_keep]
+            arr[j] = CView(ctypes.addressof(c), sp.value, tp.value, int(tab.shape[0]), 1 if sdev else 0)
+        counts[i] = len(views)
+        arrays.append(arr)
+    ctxs = (ctypes.c_void_p * len(lifters))(*[L._h for L in lifters])
+    vptrs = (ctypes.c_void_p * len(lifters))(*[ctypes.addressof(a) for a in arrays])
+    failed = ctypes.c_int32(-1)
+    rc = lib.slag_add_views_batched(len(lifters), ctxs, vptrs, counts, ctypes.byref(failed))
+    if rc != OK:
+        raise SlagError(rc, "slag_add_views_batched (scene %d)" % failed.value)
