@@ -68,8 +68,9 @@ def _args():
     p.add_argument("--views", type=int, default=0, help="use only the first V views (0 = all)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the BF16 form's line")
-    p.add_argument("--workload", default="mid", choices=["mid", "precision"],
-                   help="mid: the headline workload; precision: 2M Gaussians at 1920x1080 on a view subset")
+    p.add_argument("--workload", default="mid", choices=["mid", "precision", "batched"],
+                   help="mid: the headline workload; precision: 2M Gaussians at 1920x1080 on a view subset; "
+                        "batched: 16 uneven scenes, their first --views views each (16 by default)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
@@ -487,10 +488,94 @@ def _latent_form(S, torch, scene, *args):
     return out
 
 
+def _batched_view(job):
+    """(scene index, view index) -> (camera, segment map, table) of the batched workload."""
+    import synth
+    i, j = job
+    v = synth.config_batched()[i].view(j)
+    return i, j, v.camera, v.seg, v.table
+
+
+def run_batched(a):
+    """16 independent uneven scenes (config_batched, seed 3), their first `views` views each:
+    every scene lifted on its own in turn, against all scenes in one slag_add_views_batched call
+    (round-robin); both with device-resident inputs, finalize included, no queries."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import synth
+    scenes = synth.config_batched()
+    cap = a.views or 16
+    jobs = [(i, j) for i, s in enumerate(scenes) for j in range(min(cap, s.n_views))]
+    # views generated on the host cores before any CUDA call
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        got = list(ex.map(_batched_view, jobs, chunksize=4))
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2505_08124_b300 import slag as S
+    S.load_library()
+    stream = torch.cuda.current_stream()
+    views = [[] for _ in scenes]
+    for i, j, cam, seg, tab in sorted(got, key=lambda t: (t[0], t[1])):
+        views[i].append((cam, torch.from_numpy(seg).to(dev), torch.from_numpy(tab).to(dev)))
+    lifters = [S.Lifter(s.gaussians, dim=s.dim, stream=stream.cuda_stream) for s in scenes]
+    wbuf = [torch.empty(s.gaussians.n, dtype=torch.float32, device=dev) for s in scenes]
+
+    def sequential():
+        for L, vs, w in zip(lifters, views, wbuf):
+            L.reset()
+            for cam, seg, tab in vs:
+                L.add_view(cam, seg, tab)
+            L.finalize(None, w)
+
+    def batched():
+        for L in lifters:
+            L.reset()
+        S.add_views_batched(lifters, views)
+        for L, w in zip(lifters, wbuf):
+            L.finalize(None, w)
+
+    def timed(fn):
+        for _ in range(max(1, a.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / a.steps
+
+    ms_seq = timed(sequential)
+    ms_bat = timed(batched)
+    contrib = sum(L.stats()["contributions"] for L in lifters)
+    nviews = sum(len(v) for v in views)
+    for L in lifters:
+        L.close()
+    if rank == 0:
+        out = {"metric": METRIC, "value": contrib / (ms_bat / 1e3), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": ms_bat, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "views_per_s": nviews / (ms_bat / 1e3),
+               "sequential": {"ms_per_step": ms_seq, "views_per_s": nviews / (ms_seq / 1e3),
+                              "value": contrib / (ms_seq / 1e3)},
+               "config": {"workload": "batched form: 16 independent scenes (log-uniform 50k-1.5M Gaussians, "
+                                      "640x480 / 960x540 / 1920x1080, 32-128 segments, D=512), the first %d views "
+                                      "of each (of 20-200)" % cap,
+                          "scenes": len(scenes), "views": nviews,
+                          "gaussians": [s.gaussians.n for s in scenes],
+                          "parallelism": "replicas x%d" % ws}}
+        print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batched":
+        run_batched(a)
     else:
         run_slag(a)
 

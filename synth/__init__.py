@@ -9,5 +9,5 @@ from .scenes import (  # noqa: F401
     Gaussians, Camera, View, Scene,
     random_gaussians, ellipsoid_gaussians, orbit_camera, look_at, voronoi_segments,
     prototype_table, make_scene, config_tiny, config_mid, config_precision,
-    small_scene, segment_samples,
+    small_scene, segment_samples, config_batched,
 )

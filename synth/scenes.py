@@ -281,6 +281,24 @@ def config_precision(seed: int = 2) -> Scene:
                       n_protos=64, jitter=True)
 
 
+def config_batched(seed: int = 3, n_scenes: int = 16) -> List[Scene]:
+    """16 independent scenes: Gaussian counts log-uniform in [50k, 1.5M] on ellipsoid surfaces
+    (one per 25k Gaussians), view counts uniform in [20, 200], resolutions drawn from
+    {640x480, 960x540, 1920x1080}, 32..128 segments per view, D = 512, 32 prototypes."""
+    rng = _rng(seed, 77)
+    res = [(640, 480), (960, 540), (1920, 1080)]
+    out = []
+    for i in range(n_scenes):
+        n = int(round(math.exp(rng.uniform(math.log(50_000), math.log(1_500_000)))))
+        n_views = int(rng.integers(20, 201))
+        w, h = res[int(rng.integers(0, 3))]
+        m = int(rng.integers(32, 129))
+        g = ellipsoid_gaussians(seed * 1000 + i, n, max(1, n // 25_000))
+        out.append(make_scene(f"batched{i}", seed * 1000 + i, g, n_views=n_views, width=w, height=h,
+                              n_segments=m, n_protos=32, jitter=True))
+    return out
+
+
 def small_scene(seed: int, n: int, n_views: int, width: int, height: int, n_segments: int,
                 dim: int = 64, surfaces: int = 0, empty_fraction: float = 0.0,
                 n_protos: int = 8, noise_sigma: float = 0.1) -> Scene:
