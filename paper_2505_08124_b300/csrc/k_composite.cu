@@ -241,9 +241,15 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
         wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
     }
     if (lane == 0) sm.wbox[w] = make_float4(wx0, wx1, wy0, wy1);
-    float T0 = 1.f, T1 = 1.f, wsum0 = 0.f, wsum1 = 0.f;
-    int count0 = 0, count1 = 0, evals = 0;
-    bool done0 = !inside0, done1 = !inside1;
+    // T = 0 marks a pixel that has stopped (or lies outside the image): its weights are then 0
+    // and every later Gaussian takes it below 1e-4 again, so no flag is needed
+    float T0 = inside0 ? 1.f : 0.f, T1 = inside1 ? 1.f : 0.f;
+    float wsum0 = 0.f, wsum1 = 0.f, Tf0 = 0.f, Tf1 = 0.f;   // diagnostics: weight sum, T at the stop
+    int count0 = 0, count1 = 0;
+    // examined pairs: a stopped pixel examined the list up to its stopping Gaussian (position
+    // evp in the tile's candidate order); the others examined every candidate the warp went
+    // through (seen)
+    int evp0 = 0, evp1 = 0, seen = 0;
 
     // this tile's candidates: the depth-ordered list of its bin (a 2^shift x
     // 2^shift square of tiles); the Gaussians whose tile rectangle holds this tile
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
     }
 
     while (true) {
-        int live = __syncthreads_count(!(done0 && done1));   // also: the previous batch is consumed
+        int live = __syncthreads_count(T0 > 0.f || T1 > 0.f);   // also: the previous batch is consumed
         if (live == 0 || cursor >= end) break;
         // fill: rounds of kRound candidates until at least kBatch - kRound records are
         // staged; the records of the hits are copied asynchronously, the next round's
@@ -342,12 +348,13 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
         const float4 *rec_b = sm.rec_b;
         const int gs = sm.group_slot[w];
         for (int c = 0; c * 32 < nb; ++c) {
-            if (!__any_sync(0xffffffffu, !(done0 && done1))) break;
+            if (!__any_sync(0xffffffffu, T0 > 0.f || T1 > 0.f)) break;
             const int nvalid = min(32, nb - c * 32);
             // which of the chunk's Gaussians can reach alpha >= 1/255 inside this warp's pixels
             const bool hitw = lane < nvalid && ((__float_as_uint(rec_b[c * 32 + lane].z) >> w) & 1u);
             const uint32_t mask = __ballot_sync(0xffffffffu, hitw);
-            evals += nvalid * ((done0 ? 0 : 1) + (done1 ? 0 : 1));
+            const int base = seen;
+            seen += nvalid;
             if (mask == 0) continue;
             // A: composite the surviving Gaussians for this thread's two pixels, two
             // Gaussians at a time: the four exponents and exp2 of a group are independent;
@@ -384,24 +391,29 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (jj[k] < 0) break;
-                    // predicated, branch-free: a Gaussian contributes unless the pixel has
-                    // stopped or alpha is below the floor; the one whose (1 - alpha) would
-                    // take T below 1e-4 stops the pixel and contributes nothing
+                    // branch-free: the Gaussian whose (1 - alpha) would take T below 1e-4 stops the
+                    // pixel (T = 0) and contributes nothing; alpha = 0 leaves T as it is
+                    const int pos = base + jj[k] + 1;
                     const float Tn0 = T0 - al0[k] * T0, Tn1 = T1 - al1[k] * T1;
-                    const bool act0 = !done0 && al0[k] > 0.f, act1 = !done1 && al1[k] > 0.f;
-                    const bool stop0 = act0 && Tn0 < 1e-4f, stop1 = act1 && Tn1 < 1e-4f;
-                    const bool take0 = act0 && !stop0, take1 = act1 && !stop1;
-                    float w0 = kKernel ? fast_exp2(kq0[k]) : al0[k] * T0;
-                    float w1 = kKernel ? fast_exp2(kq1[k]) : al1[k] * T1;
-                    w0 = take0 ? w0 : 0.f;
-                    w1 = take1 ? w1 : 0.f;
-                    T0 = take0 ? Tn0 : T0;
-                    T1 = take1 ? Tn1 : T1;
-                    done0 = done0 || stop0;
-                    done1 = done1 || stop1;
-                    count0 += take0 ? 1 : 0;
-                    count1 += take1 ? 1 : 0;
-                    evals -= ((stop0 ? 1 : 0) + (stop1 ? 1 : 0)) * (nvalid - 1 - jj[k]);
+                    const bool stop0 = Tn0 < 1e-4f, stop1 = Tn1 < 1e-4f;
+                    evp0 = T0 > 0.f ? pos : evp0;
+                    evp1 = T1 > 0.f ? pos : evp1;
+                    if (kDebug) {
+                        Tf0 = (stop0 && T0 > 0.f) ? T0 : Tf0;
+                        Tf1 = (stop1 && T1 > 0.f) ? T1 : Tf1;
+                    }
+                    float w0, w1;
+                    if (kKernel) {
+                        w0 = (stop0 || !(al0[k] > 0.f)) ? 0.f : fast_exp2(kq0[k]);
+                        w1 = (stop1 || !(al1[k] > 0.f)) ? 0.f : fast_exp2(kq1[k]);
+                    } else {
+                        w0 = stop0 ? 0.f : al0[k] * T0;
+                        w1 = stop1 ? 0.f : al1[k] * T1;
+                    }
+                    T0 = stop0 ? 0.f : Tn0;
+                    T1 = stop1 ? 0.f : Tn1;
+                    count0 += w0 > 0.f ? 1 : 0;
+                    count1 += w1 > 0.f ? 1 : 0;
                     if (kDebug) {
                         wsum0 += w0;
                         wsum1 += w1;
@@ -484,17 +496,18 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
 
     if (inside0) {
         const int64_t pi = (int64_t)py0 * W + px0;
-        if (a.dbg_T) a.dbg_T[pi] = T0;
+        if (a.dbg_T) a.dbg_T[pi] = T0 > 0.f ? T0 : Tf0;
         if (a.dbg_wsum) a.dbg_wsum[pi] = wsum0;
         if (a.dbg_count) a.dbg_count[pi] = count0;
     }
     if (inside1) {
         const int64_t pi = (int64_t)py1 * W + px1;
-        if (a.dbg_T) a.dbg_T[pi] = T1;
+        if (a.dbg_T) a.dbg_T[pi] = T1 > 0.f ? T1 : Tf1;
         if (a.dbg_wsum) a.dbg_wsum[pi] = wsum1;
         if (a.dbg_count) a.dbg_count[pi] = count1;
     }
-    unsigned long long cnt = (unsigned long long)(count0 + count1), ev = (unsigned long long)evals;
+    const int ev0 = inside0 ? (T0 > 0.f ? seen : evp0) : 0, ev1 = inside1 ? (T1 > 0.f ? seen : evp1) : 0;
+    unsigned long long cnt = (unsigned long long)(count0 + count1), ev = (unsigned long long)(ev0 + ev1);
     for (int o = 16; o; o >>= 1) {
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         ev += __shfl_xor_sync(0xffffffffu, ev, o);
