@@ -2,25 +2,39 @@
 // inference": score_k = q . E_k / |E_k|, top-k by descending score, ties to
 // the lower Gaussian index).
 //
-// A CTA scores 256 queries x 128 Gaussians per tile as two tcgen05.mma
-// accumulators of M = 128 TMEM lanes (queries) x N = 128 TMEM columns
-// (Gaussians), fp32, over K = D in chunks of 32. Float32 accuracy comes from
-// the three-term TF32 split x = hi + lo (hi = x rounded to TF32, lo = the
-// rest rounded to TF32): q.e ~ q_hi.e_hi + q_hi.e_lo + q_lo.e_hi, so each
-// chunk issues 2 accumulators x 4 K-steps x 3 MMAs of K = 8. The CTA's 512
-// threads stage operands into shared memory in the 128-byte-swizzled K-major
-// layout (atoms of 8 rows x 128 bytes = 32 TF32 values per row, the 16-byte
-// chunk c of row r stored at chunk c ^ (r mod 8), atoms 1024 bytes apart; a
-// K-step of 8 advances the descriptor start by 32 bytes), two stages deep
-// against the MMAs (mbarriers), with the next chunk's global loads in flight
-// while the current one is converted. After a tile's last chunk, the first 8
-// warps read one query's 128 scores each from TMEM (tcgen05.ld 32x32b),
-// scale them by 1/|E_k| and keep a running top-16 in registers. A grid of
+// Float32 accuracy comes from the three-term TF32 split x = hi + lo (hi = x
+// rounded to TF32, lo = the rest rounded to TF32): q.e ~ q_hi.e_hi + q_hi.e_lo
+// + q_lo.e_hi. Both operands are split once, outside the scoring kernel, into
+// two planes (hi, then lo) of rows of D floats: the candidate rows of E once per
+// finalize (with their inverse norms, NaN where the row is zero), the queries
+// once per batch.
+//
+// A CTA owns 128 queries (the M = 128 TMEM lanes of a kind::tf32 MMA) and a
+// range of Gaussian tiles of N = 256 candidates (256 TMEM columns). Its warps
+// have fixed roles:
+//   warp 0      one thread issues TMA loads: per K-chunk of 32 values, a 3-D
+//               box {32, 128, 2} of the query planes and {32, 256, 2} of the
+//               candidate planes, 128-byte swizzled (the canonical K-major
+//               layout of the MMA operands), into one of two 96 KB stages;
+//   warp 1      owns the TMEM allocation (512 columns: two accumulators) and
+//               one thread issues the MMAs: 4 K-steps x 3 products per chunk,
+//               freeing the stage by tcgen05.commit and, after a tile's last
+//               chunk, signalling the accumulator full;
+//   warps 2..5  the epilogue: warp w reads TMEM lanes 32 (w mod 4) .. (one
+//               query per thread), 32 columns per tcgen05.ld, scales them by
+//               1/|E_k| and keeps a running top-16 in registers; then frees
+//               the accumulator for the tile after next.
+// So loads, MMAs and the epilogue of the previous tile all overlap. A grid of
 // (query tiles x Gaussian splits) writes per-split candidates that the merge
 // kernel of k_query.cu reduces to the final top-k.
 //
-// Every wait on an mbarrier is bounded (about one second of globaltimer);
-// on timeout the kernel sets *err, stops issuing work and releases its TMEM.
+// Every wait on an mbarrier is bounded (about one second of globaltimer) and
+// also gives up once another role has given up (a shared abort flag). Before
+// the CTA exits, the producer waits for its loads in flight and the MMA
+// thread for its MMAs in flight (bounded), then warp 1 releases the TMEM;
+// *err is set.
+#include <cuda.h>
+
 #include "slag_internal.cuh"
 #include "tc_util.cuh"
 
@@ -28,44 +42,71 @@ namespace slag {
 
 namespace {
 
-constexpr int kM = 256;          // queries per CTA tile: two accumulators of 128 TMEM lanes
-constexpr int kMmaM = 128;       // M of one MMA (TMEM lanes of one accumulator)
-constexpr int kN = 128;          // Gaussians per tile (TMEM columns of one accumulator)
-constexpr int kKC = 32;          // K per staged chunk: one 128-byte swizzle atom row of TF32
+constexpr int kQM = 128;          // queries per CTA: TMEM lanes of one accumulator
+constexpr int kQN = 256;          // candidates per tile: TMEM columns of one accumulator
+constexpr int kKC = 32;           // K per stage: one 128-byte swizzle row of TF32
 constexpr int kStages = 2;
-constexpr int kThreadsTC = 512;
-constexpr int kTopTC = 16;       // running top-k kept per query
-constexpr uint32_t kTmemCols = 256;
+constexpr int kThreads = 192;     // 6 warps: TMA, MMA, 4 x epilogue
+constexpr int kTop = 16;          // running top-k kept per query
+constexpr uint32_t kTmemCols = 2 * kQN;
 
-// byte sizes of one stage
-constexpr int kABytes = kM * kKC * 4;   // 32 KB
-constexpr int kBBytes = kN * kKC * 4;   // 16 KB
-constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr int kSBO = tc::kSBO;          // bytes between 8-row swizzle atoms
-constexpr int kLoadsPerThread = (kM + kN) * (kKC / 4) / kThreadsTC;   // float4 per thread per chunk
+constexpr int kAPlane = kQM * kKC * 4;             // 16 KB: one TF32 plane of the query chunk
+constexpr int kBPlane = kQN * kKC * 4;             // 32 KB
+constexpr int kStageBytes = 2 * kAPlane + 2 * kBPlane;   // 96 KB
+static_assert(kAPlane % 1024 == 0 && kBPlane % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
+static_assert(kKC * 4 == 128, "a chunk row is one 128-byte swizzle row");
 
-struct __align__(8) TcCtl {
-    uint64_t bar[kStages];
+struct __align__(8) Ctl {
+    uint64_t full[kStages];    // TMA -> MMA (transaction bytes)
+    uint64_t empty[kStages];   // MMA -> TMA (tcgen05.commit)
+    uint64_t tfull[2];         // MMA -> epilogue (tcgen05.commit)
+    uint64_t tempty[2];        // epilogue -> MMA (one arrival per epilogue warp)
     uint32_t tmem_addr;
     uint32_t abort;
 };
 
-using tc::core_off;
+constexpr size_t kSmemBytes = 1024 /* alignment slack */ + (size_t)kStages * kStageBytes + sizeof(Ctl);
+static_assert(kSmemBytes <= 232448, "fits the opt-in shared memory of a CTA");
+
 using tc::gtimer;
 using tc::mbar_init;
-using tc::mbar_wait;
+using tc::mbar_try_wait;
 using tc::mma_commit;
 using tc::smem_desc;
 using tc::smem_u32;
-using tc::split_store;
 using tc::tmem_ld32;
 
-constexpr uint32_t kIdesc = tc::idesc_tf32<kN>();
-static_assert(kMmaM == 128, "cta_group::1 tf32 MMA shape");
-static_assert(kKC * 4 == 128, "a chunk row is one 128-byte swizzle row");
+constexpr uint32_t kIdesc = tc::idesc_tf32<kQN>();
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
-    tc::mma_tf32(tmem, adesc, bdesc, kIdesc, accum);
+// Bounded wait that also gives up once *abort is set; a timeout sets *abort.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile uint32_t *abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (gtimer() - t0 > 1000000000ull) {
+            *abort = 1u;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 3-D tiled TMA load of box {x.., y.., z..} into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
 }
 
 __device__ __forceinline__ bool better(float s, uint32_t i, float s2, uint32_t i2) {
@@ -86,34 +127,40 @@ __device__ __forceinline__ float select32(const float (&v)[32], int j) {
     return (j & 16) ? d[1] : d[0];
 }
 
-__global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restrict__ Q, int32_t B,
-                                                            const float *__restrict__ E,
-                                                            const float *__restrict__ inv_norm,
-                                                            const uint32_t *__restrict__ rows, int64_t n,
-                                                            int32_t D, int32_t k, int32_t nsplit,
-                                                            float *__restrict__ cand_s,
-                                                            uint32_t *__restrict__ cand_i, uint32_t *err) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *stage0 = smem_raw;
-    TcCtl *ctl = reinterpret_cast<TcCtl *>(smem_raw + kStages * kStageBytes);
-    float *sinv = reinterpret_cast<float *>(smem_raw + kStages * kStageBytes + 64);
+__global__ void __launch_bounds__(kThreads, 1)
+    query_tc_k(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmE, int32_t B,
+               const float *__restrict__ qinv, int64_t n, int32_t D, int32_t k, int32_t nsplit,
+               float *__restrict__ cand_s, uint32_t *__restrict__ cand_i, uint32_t *err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    Ctl *ctl = reinterpret_cast<Ctl *>(base + kStages * kStageBytes);
+    volatile uint32_t *abort = &ctl->abort;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q0 = blockIdx.x * kM;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q0 = blockIdx.x * kQM;
     const int split = blockIdx.y;
-    const int64_t ntile_g = (n + kN - 1) / kN;
-    const int64_t per = (ntile_g + nsplit - 1) / nsplit;
-    const int64_t t_begin = split * per;
-    const int64_t t_end = min(ntile_g, t_begin + per);
+    const int64_t ntile = (n + kQN - 1) / kQN;
+    const int64_t per = (ntile + nsplit - 1) / nsplit;
+    const int64_t t_begin = (int64_t)split * per;
+    const int64_t t_end = min(ntile, t_begin + per);
+    const int ntl = t_end > t_begin ? (int)(t_end - t_begin) : 0;
     const int nchunk = D / kKC;
-    const int64_t total_chunks = t_end > t_begin ? (t_end - t_begin) * nchunk : 0;
 
-    if (tid == 0) {
-        for (int i = 0; i < kStages; ++i) mbar_init(&ctl->bar[i], 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&ctl->full[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&ctl->tfull[a], 1);
+            mbar_init(&ctl->tempty[a], 4);
+        }
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmQ)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmE)) : "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_addr)),
                      "r"(kTmemCols)
                      : "memory");
@@ -124,125 +171,126 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = ctl->tmem_addr;
 
-    float bs[kTopTC];
-    uint32_t bi[kTopTC];
-#pragma unroll
-    for (int i = 0; i < kTopTC; ++i) {
-        bs[i] = -INFINITY;
-        bi[i] = 0xffffffffu;
-    }
-    // Running threshold: the split's k-th best score so far. Columns arrive in
-    // increasing Gaussian index, so a score equal to the k-th best never ranks
-    // above it and the test is strict. Rows past the last query take none.
-    const int kk = k < kTopTC ? k : kTopTC;
-    float thr_run = -INFINITY;
-    if (warp < 8 && q0 + (warp >> 2) * 128 + (warp & 3) * 32 + lane >= B) thr_run = INFINITY;
-
-    // this thread's share of a chunk: kLoadsPerThread float4, A rows first then B rows
-    auto fetch = [&](int64_t gc, float4 (&v)[kLoadsPerThread]) {
-        const int64_t t = t_begin + gc / nchunk;
-        const int d0 = (int)(gc % nchunk) * kKC;
-        const int64_t g0 = t * kN;
-#pragma unroll
-        for (int j = 0; j < kLoadsPerThread; ++j) {
-            const int i = tid + j * kThreadsTC;          // 0 .. (kM + kN) * 8
-            const int row = i >> 3, kq = i & 7;
-            v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (row < kM) {
-                if (q0 + row < B) v[j] = __ldg(reinterpret_cast<const float4 *>(Q + (int64_t)(q0 + row) * D + d0 + kq * 4));
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: load i goes to stage i % kStages once the MMAs of load i - kStages are done
+            int64_t i = 0;
+            bool ok = true;
+            for (int j = 0; j < ntl && ok; ++j) {
+                const int row = (int)((t_begin + j) * kQN);
+                for (int c = 0; c < nchunk; ++c, ++i) {
+                    const int s = (int)(i % kStages);
+                    if (i >= kStages && !wait_or_abort(&ctl->empty[s], (uint32_t)((i / kStages - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *stg = base + s * kStageBytes;
+                    expect_tx(&ctl->full[s], (uint32_t)kStageBytes);
+                    tma_load_3d(smem_u32(stg), &tmQ, &ctl->full[s], c * kKC, q0, 0);
+                    tma_load_3d(smem_u32(stg + 2 * kAPlane), &tmE, &ctl->full[s], c * kKC, row, 0);
+                }
+            }
+            if (ok) {
+                // tail: the commits that free the last stages arrive before the CTA exits
+                for (int64_t l = i > kStages ? i - kStages : 0; l < i; ++l)
+                    if (!wait_or_abort(&ctl->empty[l % kStages], (uint32_t)((l / kStages) & 1), abort)) break;
             } else {
-                const int64_t g = g0 + (row - kM);
-                if (g < n) {
-                    const int64_t er = rows ? (int64_t)__ldg(rows + g) : g;
-                    v[j] = __ldg(reinterpret_cast<const float4 *>(E + er * D + d0 + kq * 4));
+                // loads in flight write this CTA's shared memory: let them land (bounded)
+                for (int64_t l = i > kStages ? i - kStages : 0; l < i; ++l) {
+                    volatile uint32_t never = 0;
+                    wait_or_abort(&ctl->full[l % kStages], (uint32_t)((l / kStages) & 1), &never);
                 }
             }
         }
-    };
-
-    float4 pf[kLoadsPerThread];
-    if (total_chunks > 0) fetch(0, pf);
-    bool ok = true;
-    int64_t gc = 0;
-    for (; gc < total_chunks; ++gc) {
-        const int st = (int)(gc % kStages);
-        unsigned char *A_hi = stage0 + st * kStageBytes;
-        unsigned char *A_lo = A_hi + kABytes;
-        unsigned char *B_hi = A_lo + kABytes;
-        unsigned char *B_lo = B_hi + kBBytes;
-        const int c = (int)(gc % nchunk);
-        // the MMAs that last read this stage (chunk gc - kStages) must be done
-        if (gc >= kStages) {
-            if (!mbar_wait(&ctl->bar[st], (uint32_t)((gc - kStages) / kStages) & 1u)) ok = false;
-        }
-        if (__syncthreads_or(!ok)) { ok = false; break; }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: tile j accumulates into accumulator j & 1
+            int64_t i = 0, last = -1;
+            bool ok = true;
+            for (int j = 0; j < ntl && ok; ++j) {
+                const int acc = j & 1;
+                if (j >= 2 && !wait_or_abort(&ctl->tempty[acc], (uint32_t)((j / 2 - 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dt = tmem + (uint32_t)(acc * kQN);
+                for (int c = 0; c < nchunk; ++c, ++i) {
+                    const int s = (int)(i % kStages);
+                    if (!wait_or_abort(&ctl->full[s], (uint32_t)((i / kStages) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a_hi = smem_u32(base + s * kStageBytes), a_lo = a_hi + kAPlane;
+                    const uint32_t b_hi = a_hi + 2 * kAPlane, b_lo = b_hi + kBPlane;
 #pragma unroll
-        for (int j = 0; j < kLoadsPerThread; ++j) {
-            const int i = tid + j * kThreadsTC;
-            const int row = i >> 3, kq = i & 7;
-            if (row < kM) split_store(A_hi, A_lo, core_off(row, kq), pf[j]);
-            else split_store(B_hi, B_lo, core_off(row - kM, kq), pf[j]);
+                    for (int ks = 0; ks < kKC / 8; ++ks) {
+                        const uint32_t ko = ks * 32;   // K = 8 TF32 = 32 bytes along the swizzled row
+                        const uint64_t dah = smem_desc(a_hi + ko), dal = smem_desc(a_lo + ko);
+                        const uint64_t dbh = smem_desc(b_hi + ko), dbl = smem_desc(b_lo + ko);
+                        tc::mma_tf32(dt, dah, dbh, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
+                        tc::mma_tf32(dt, dah, dbl, kIdesc, 1u);
+                        tc::mma_tf32(dt, dal, dbh, kIdesc, 1u);
+                    }
+                    mma_commit(&ctl->empty[s]);
+                    last = i;
+                }
+                if (ok) mma_commit(&ctl->tfull[acc]);
+            }
+            if (!ok && last >= 0) {
+                // MMAs in flight read shared memory and write TMEM: let them finish (bounded)
+                volatile uint32_t never = 0;
+                wait_or_abort(&ctl->empty[last % kStages], (uint32_t)((last / kStages) & 1), &never);
+            }
         }
-        if (gc + 1 < total_chunks) fetch(gc + 1, pf);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    } else {
+        // epilogue: one query per thread
+        const int quarter = warp & 3;
+        const int q = q0 + quarter * 32 + lane;
+        const int kk = k < kTop ? k : kTop;
+        float bs[kTop];
+        uint32_t bi[kTop];
+#pragma unroll
+        for (int p = 0; p < kTop; ++p) {
+            bs[p] = -INFINITY;
+            bi[p] = 0xffffffffu;
+        }
+        // Running threshold: the split's k-th best score so far. Columns arrive in increasing
+        // candidate index, so a score equal to the k-th best never ranks above it and the test is
+        // strict. Rows past the last query take none.
+        float thr_run = q < B ? -INFINITY : INFINITY;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        for (int j = 0; j < ntl; ++j) {
+            const int acc = j & 1;
+            const bool got = wait_or_abort(&ctl->tfull[acc], (uint32_t)((j / 2) & 1), abort);
+            if (!__all_sync(0xffffffffu, got)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_hi = smem_u32(A_hi), a_lo = smem_u32(A_lo);
-            const uint32_t b_hi = smem_u32(B_hi), b_lo = smem_u32(B_lo);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t ah = a_hi + h * 16 * kSBO, al = a_lo + h * 16 * kSBO;   // rows 128h..
-                const uint32_t dt = tmem + (uint32_t)(h * kN);                         // columns 128h..
-#pragma unroll
-                for (int s2 = 0; s2 < kKC / 8; ++s2) {
-                    const uint32_t ko = s2 * 32;    // K = 8 TF32 = 32 bytes along the swizzled row
-                    const uint64_t dah = smem_desc(ah + ko), dal = smem_desc(al + ko);
-                    const uint64_t dbh = smem_desc(b_hi + ko), dbl = smem_desc(b_lo + ko);
-                    mma_tf32(dt, dah, dbh, (c > 0 || s2 > 0) ? 1u : 0u);
-                    mma_tf32(dt, dah, dbl, 1u);
-                    mma_tf32(dt, dal, dbh, 1u);
-                }
-            }
-            mma_commit(&ctl->bar[st]);
-        }
-        if (c != nchunk - 1) continue;
-        // epilogue of the tile: its last commit follows every earlier MMA
-        if (!mbar_wait(&ctl->bar[st], (uint32_t)(gc / kStages) & 1u)) ok = false;
-        if (__syncthreads_or(!ok)) { ok = false; ++gc; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int64_t g0 = (t_begin + gc / nchunk) * kN;
-        for (int i = tid; i < kN; i += kThreadsTC) {
-            const int64_t g = g0 + i;
-            const float inv = g < n ? inv_norm[rows ? (int64_t)rows[g] : g] : 0.f;
-            sinv[i] = inv > 0.f ? inv : __int_as_float(0x7fc00000);   // NaN: never passes a threshold
-        }
-        __syncthreads();
-        if (warp < 8) {
-            // warp w: accumulator w / 4, TMEM lanes 32 (w % 4) ..
-            const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * kN);
-            for (int cb = 0; cb < kN; cb += 32) {
+            const int64_t g0 = (t_begin + j) * kQN;
+            for (int cb = 0; cb < kQN; cb += 32) {
                 float v[32];
-                tmem_ld32(base + (uint32_t)cb, v);
+                tmem_ld32(lane_base + (uint32_t)(acc * kQN + cb), v);
+                const int64_t gl = g0 + cb + lane;
+                const float inv = __ldg(qinv + gl);   // padded to whole tiles
                 uint32_t mask = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    v[j] *= sinv[cb + j];
-                    mask |= (v[j] > thr_run ? 1u : 0u) << j;
+                for (int jj = 0; jj < 32; ++jj) {
+                    v[jj] *= __shfl_sync(0xffffffffu, inv, jj);   // NaN never passes a threshold
+                    mask |= (v[jj] > thr_run ? 1u : 0u) << jj;
                 }
-                // candidates at or above the running threshold, one per lane per round, so that
-                // the lanes of the warp insert together
+                // candidates above the running threshold, one per lane per round, so that the
+                // lanes of the warp insert together
                 while (__any_sync(0xffffffffu, mask != 0u)) {
                     float sc = -INFINITY;
                     uint32_t gi = 0xffffffffu;
                     if (mask) {
-                        const int j = __ffs(mask) - 1;
+                        const int jj = __ffs(mask) - 1;
                         mask &= mask - 1u;
-                        sc = select32(v, j);
-                        gi = (uint32_t)(g0 + cb + j);
+                        sc = select32(v, jj);
+                        gi = (uint32_t)(g0 + cb + jj);
                     }
 #pragma unroll
-                    for (int p = 0; p < kTopTC; ++p) {
+                    for (int p = 0; p < kTop; ++p) {
                         const bool b = better(sc, gi, bs[p], bi[p]);
                         const float ts = b ? bs[p] : sc;
                         const uint32_t ti = b ? bi[p] : gi;
@@ -253,81 +301,156 @@ __global__ void __launch_bounds__(kThreadsTC, 1) query_tc_k(const float *__restr
                     }
                     float kth = bs[0];
 #pragma unroll
-                    for (int p = 1; p < kTopTC; ++p) kth = p == kk - 1 ? bs[p] : kth;
+                    for (int p = 1; p < kTop; ++p) kth = p == kk - 1 ? bs[p] : kth;
                     thr_run = kth;
                 }
             }
+            // this warp has read the accumulator: it may take the tile after next
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) arrive(&ctl->tempty[acc]);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();   // every thread has read the accumulators before the next tile overwrites them
-    }
-
-    if (!ok) {
-        if (tid == 0) atomicOr(err, 1u);
-        // let MMAs in flight finish (bounded) before TMEM is released
-        if (gc > 0) {
-            const int64_t last = gc - 1;
-            mbar_wait(&ctl->bar[last % kStages], (uint32_t)(last / kStages) & 1u);
-        }
-    }
-    // this query's candidates of this split
-    if (warp < 8) {
-        const int q = q0 + (warp >> 2) * 128 + (warp & 3) * 32 + lane;
         if (q < B) {
             float *cs = cand_s + ((int64_t)q * nsplit + split) * kk;
             uint32_t *ci = cand_i + ((int64_t)q * nsplit + split) * kk;
 #pragma unroll
-            for (int p = 0; p < kTopTC; ++p)
+            for (int p = 0; p < kTop; ++p)
                 if (p < kk) {
                     cs[p] = bs[p];
                     ci[p] = bs[p] == -INFINITY ? 0xffffffffu : bi[p];
                 }
         }
     }
+
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x == 0 && *abort) atomicOr(err, 1u);
+    if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
 }
 
-size_t tc_smem() { return (size_t)kStages * kStageBytes + 64 + kN * 4; }
+// The TF32 split of rows (rows[r] of src, or row r without a row list) into two planes of n_pad x D
+// floats (hi, then lo); rows n .. n_pad are zero. With qinv, also the rows' inverse norms (NaN
+// where not positive, and for the zero rows).
+__global__ void __launch_bounds__(256) tf32_split_k(const float *__restrict__ src, const uint32_t *__restrict__ rows,
+                                                    int64_t n, int64_t n_pad, int32_t D, float *__restrict__ dst,
+                                                    const float *__restrict__ inv_norm, float *__restrict__ qinv) {
+    const int64_t d4 = D / 4;
+    const int64_t total = n_pad * d4;
+    const int64_t plane = n_pad * (int64_t)D;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / d4, c = i - r * d4;
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+        int64_t sr = -1;
+        if (r < n) {
+            sr = rows ? (int64_t)__ldg(rows + r) : r;
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(src + sr * D) + c);
+            h.x = tc::to_tf32(x.x); l.x = tc::to_tf32(x.x - h.x);
+            h.y = tc::to_tf32(x.y); l.y = tc::to_tf32(x.y - h.y);
+            h.z = tc::to_tf32(x.z); l.z = tc::to_tf32(x.z - h.z);
+            h.w = tc::to_tf32(x.w); l.w = tc::to_tf32(x.w - h.w);
+        }
+        reinterpret_cast<float4 *>(dst + r * D)[c] = h;
+        reinterpret_cast<float4 *>(dst + plane + r * D)[c] = l;
+        if (qinv && c == 0) {
+            const float v = sr >= 0 ? inv_norm[sr] : 0.f;
+            qinv[r] = v > 0.f ? v : __int_as_float(0x7fc00000);
+        }
+    }
+}
+
+void launch_split(const float *src, const uint32_t *rows, int64_t n, int64_t n_pad, int32_t D, float *dst,
+                  const float *inv_norm, float *qinv, cudaStream_t st) {
+    const int64_t total = n_pad * (D / 4);
+    if (total <= 0) return;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 16);
+    tf32_split_k<<<(unsigned)blocks, 256, 0, st>>>(src, rows, n, n_pad, D, dst, inv_norm, qinv); note_launch();
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// Map of two planes of `rows` x D floats (plane stride rows x D; rows a multiple of box_rows, so
+// that every box lies inside): box {32, box_rows, 2}, 128-byte swizzle.
+bool encode_planes(CUtensorMap *m, const float *base, int64_t rows, int32_t D, int box_rows) {
+    EncodeTiled fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)D, (cuuint64_t)rows, 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)D * 4, (cuuint64_t)rows * D * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kKC, (cuuint32_t)box_rows, 2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
-bool query_tc_supported(int32_t D, int32_t k) { return k >= 1 && k <= kTopTC && D % kKC == 0; }
+bool query_tc_supported(int32_t D, int32_t k) { return k >= 1 && k <= kTop && D % kKC == 0; }
 
-int64_t query_tc_tiles(int64_t n) { return (n + kN - 1) / kN; }
+int64_t query_tc_tiles(int64_t n) { return (n + kQN - 1) / kQN; }
 
 int32_t query_tc_splits(int32_t B, int64_t n) {
-    const int64_t qt = (B + kM - 1) / kM;
-    const int64_t nt = (n + kN - 1) / kN;
+    const int64_t qt = (B + kQM - 1) / kQM;
+    const int64_t nt = (n + kQN - 1) / kQN;
     int64_t s = 148 / qt;
     if (s < 1) s = 1;
     if (s > nt) s = nt;
     return (int32_t)s;
 }
 
-void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, const uint32_t *rows,
-                          int64_t n, int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
-                          float *out_scores, int32_t *out_count, uint32_t *err, cudaStream_t st, int32_t splits) {
+int64_t query_tc_pad_rows(int64_t n) { return (n + kQN - 1) / kQN * kQN; }
+int64_t query_tc_pad_queries(int32_t B) { return ((int64_t)B + kQM - 1) / kQM * kQM; }
+
+void launch_query_split_e(const float *E, const float *inv_norm, const uint32_t *rows, int64_t n, int32_t D,
+                          float *Ehl, float *qinv, cudaStream_t st) {
+    launch_split(E, rows, n, query_tc_pad_rows(n), D, Ehl, inv_norm, qinv, st);
+}
+
+cudaError_t launch_query_topk_tc(const float *Q, int32_t B, float *Qhl, const float *Ehl, const float *qinv,
+                                 const uint32_t *rows, int64_t n, int32_t D, int32_t k, float *cand_s,
+                                 uint32_t *cand_i, int64_t *out_ids, float *out_scores, int32_t *out_count,
+                                 uint32_t *err, cudaStream_t st, int32_t splits) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(query_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem());
+        cudaError_t e = cudaFuncSetAttribute(query_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int32_t kk = k < kTopTC ? k : kTopTC;
+    const int32_t kk = k < kTop ? k : kTop;
     if (n <= 0) {   // no candidates: every query gets an empty result
         launch_query_merge(cand_s, cand_i, 0, B, k, rows, out_ids, out_scores, out_count, st);
-        return;
+        return cudaGetLastError();
     }
+    const int64_t bp = query_tc_pad_queries(B), np = query_tc_pad_rows(n);
+    CUtensorMap tq, te;
+    if (!encode_planes(&tq, Qhl, bp, D, kQM) || !encode_planes(&te, Ehl, np, D, kQN)) return cudaErrorInvalidValue;
+    launch_split(Q, nullptr, B, bp, D, Qhl, nullptr, nullptr, st);
     int32_t nsplit = splits > 0 ? splits : query_tc_splits(B, n);
-    const int64_t ntiles = (n + kN - 1) / kN;
+    const int64_t ntiles = np / kQN;
     if (nsplit > ntiles) nsplit = (int32_t)ntiles;
-    dim3 grid((unsigned)((B + kM - 1) / kM), (unsigned)nsplit);
-    query_tc_k<<<grid, kThreadsTC, tc_smem(), st>>>(Q, B, E, inv_norm, rows, n, D, k, nsplit, cand_s, cand_i, err); note_launch();
+    dim3 grid((unsigned)(bp / kQM), (unsigned)nsplit);
+    query_tc_k<<<grid, kThreads, kSmemBytes, st>>>(tq, te, B, qinv, n, D, k, nsplit, cand_s, cand_i, err); note_launch();
     launch_query_merge(cand_s, cand_i, (int64_t)nsplit * kk, B, k, rows, out_ids, out_scores, out_count, st);
+    return cudaGetLastError();
 }
 
 }  // namespace slag

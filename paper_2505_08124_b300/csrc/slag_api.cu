@@ -179,6 +179,11 @@ struct slag_ctx {
     uint64_t qgen = 0;                       // bumped by every finalize (candidate list changes)
     float *qbuf = nullptr;
     int64_t qbuf_cap = 0;
+    // tensor-core query operands: TF32 hi/lo planes of the candidate rows (rebuilt when qgen moves)
+    // and of the current query batch, with the candidates' inverse norms
+    float *ehl = nullptr, *qinv = nullptr, *qhl = nullptr;
+    int64_t ehl_cap = 0, qinv_cap = 0, qhl_cap = 0;
+    uint64_t ehl_gen = ~0ull;
     float *cand_s = nullptr;
     uint32_t *cand_i = nullptr;
     int64_t cand_cap = 0;
@@ -1024,6 +1029,14 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
     }
     int32_t splits = 0;
     if (tc && nq > 0) {
+        if (ctx->ehl_gen != ctx->qgen) {
+            const int64_t np = query_tc_pad_rows(nq);
+            CK(grow(ctx->ehl, ctx->ehl_cap, 2 * np * D, st));
+            CK(grow(ctx->qinv, ctx->qinv_cap, np, st));
+            launch_query_split_e(ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, ctx->ehl, ctx->qinv, st);
+            ctx->ehl_gen = ctx->qgen;
+        }
+        CK(grow(ctx->qhl, ctx->qhl_cap, 2 * query_tc_pad_queries(B) * D, st));
         const int64_t ntiles = query_tc_tiles(nq);
         const int32_t d = std::min<int64_t>(query_tc_splits(B, nq), ntiles);
         auto it = ctx->qsplits.find({B, nq});
@@ -1044,11 +1057,11 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
             float best = INFINITY;
             int32_t pick = d;
             for (int32_t c : cands) {
-                launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s,
-                                     ctx->cand_i, ids, scores, cnt, ctx->tc_err, st, c);
+                CK(launch_query_topk_tc(dQ, B, ctx->qhl, ctx->ehl, ctx->qinv, ctx->qrows, nq, ctx->D, k,
+                                        ctx->cand_s, ctx->cand_i, ids, scores, cnt, ctx->tc_err, st, c));
                 CK(cudaEventRecord(t0, st));
-                launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s,
-                                     ctx->cand_i, ids, scores, cnt, ctx->tc_err, st, c);
+                CK(launch_query_topk_tc(dQ, B, ctx->qhl, ctx->ehl, ctx->qinv, ctx->qrows, nq, ctx->D, k,
+                                        ctx->cand_s, ctx->cand_i, ids, scores, cnt, ctx->tc_err, st, c));
                 CK(cudaEventRecord(t1, st));
                 CK(cudaEventSynchronize(t1));
                 float ms = 0.f;
@@ -1070,13 +1083,13 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
             ctx->cand_cap = c1;
         }
     }
-    auto launch = [&](cudaStream_t s2) {
+    auto launch = [&](cudaStream_t s2) -> cudaError_t {
         if (tc)
-            launch_query_topk_tc(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s, ctx->cand_i,
-                                 ids, scores, cnt, ctx->tc_err, s2, splits);
-        else
-            launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s, ctx->cand_i, ids,
-                              scores, cnt, s2);
+            return launch_query_topk_tc(dQ, B, ctx->qhl, ctx->ehl, ctx->qinv, ctx->qrows, nq, ctx->D, k,
+                                        ctx->cand_s, ctx->cand_i, ids, scores, cnt, ctx->tc_err, s2, splits);
+        launch_query_topk(dQ, B, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, k, ctx->cand_s, ctx->cand_i, ids,
+                          scores, cnt, s2);
+        return cudaGetLastError();
     };
     if (on_device && !ctx->prof_on) {
         // device buffers: the launches run as a CUDA graph on the query stream, captured for this
@@ -1087,8 +1100,12 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
             cudaGraph_t graph = nullptr;
             const unsigned long long l0 = g_launches.load(std::memory_order_relaxed);
             CK(cudaStreamBeginCapture(ctx->qstream, cudaStreamCaptureModeRelaxed));
-            launch(ctx->qstream);
+            const cudaError_t le = launch(ctx->qstream);
             CK(cudaStreamEndCapture(ctx->qstream, &graph));
+            if (le != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                CK(le);
+            }
             // the capture counted its kernels once; replays count them below
             const unsigned long long l1 = g_launches.load(std::memory_order_relaxed);
             ctx->qgraph_launches = l1 - l0;
@@ -1106,8 +1123,9 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
         CK(cudaStreamWaitEvent(st, ctx->qev_out, 0));
     } else {
         span_begin(ctx, SLAG_STAGE_QUERY, st);
-        launch(st);
+        const cudaError_t le = launch(st);
         span_end(ctx, st);
+        CK(le);
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&ctx->hc->tc_err, ctx->tc_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -1331,6 +1349,7 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->table); dfree(ctx->E); dfree(ctx->inv_norm); dfree(ctx->wsum);
     dfree(ctx->qrows); dfree(ctx->qflags); dfree(ctx->qpos); dfree(ctx->d_nq);
     dfree(ctx->lat_params); dfree(ctx->ztable); dfree(ctx->lat_hidden);
+    dfree(ctx->ehl); dfree(ctx->qinv); dfree(ctx->qhl);
     dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);
     scratch_free(ctx->scratch);
     for (auto &sp : ctx->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }

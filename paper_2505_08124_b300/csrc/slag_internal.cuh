@@ -297,9 +297,18 @@ bool query_tc_supported(int32_t D, int32_t k);
 // Default split of the Gaussian tiles over CTAs (one wave of 148 CTAs); tiles of n candidates.
 int32_t query_tc_splits(int32_t B, int64_t n);
 int64_t query_tc_tiles(int64_t n);
-// splits <= 0: the default split
-void launch_query_topk_tc(const float *Q, int32_t B, const float *E, const float *inv_norm, const uint32_t *rows,
-                          int64_t n, int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
-                          float *out_scores, int32_t *out_count, uint32_t *err, cudaStream_t st, int32_t splits);
+// Rows of the split operand planes: n candidates padded to whole tiles, B queries padded likewise.
+int64_t query_tc_pad_rows(int64_t n);
+int64_t query_tc_pad_queries(int32_t B);
+// The TF32 hi/lo planes of the candidates rows[0..n) of E (Ehl: 2 x query_tc_pad_rows(n) x D
+// floats) and their inverse norms (qinv: query_tc_pad_rows(n) floats, NaN for zero and padding rows).
+void launch_query_split_e(const float *E, const float *inv_norm, const uint32_t *rows, int64_t n, int32_t D,
+                          float *Ehl, float *qinv, cudaStream_t st);
+// Splits Q into Qhl (2 x query_tc_pad_queries(B) x D floats), scores it against Ehl / qinv and
+// merges; result ids are rows[candidate]. splits <= 0: the default split.
+cudaError_t launch_query_topk_tc(const float *Q, int32_t B, float *Qhl, const float *Ehl, const float *qinv,
+                                 const uint32_t *rows, int64_t n, int32_t D, int32_t k, float *cand_s,
+                                 uint32_t *cand_i, int64_t *out_ids, float *out_scores, int32_t *out_count,
+                                 uint32_t *err, cudaStream_t st, int32_t splits);
 
 }  // namespace slag

@@ -237,6 +237,40 @@ def test_query_topk(slag):
         np.testing.assert_array_equal(i1, ids[3, :10] if k == 10 else L.query_batch(Q[3:4], 10)[0][0])
 
 
+@pytest.mark.parametrize("dim,B", [(128, 1000), (512, 300)])
+def test_query_tensor_core_tiles(slag, dim, B):
+    # several tiles of 128 queries (the last one ragged), several tiles of 256 candidates per split
+    # (both TMEM accumulators reused), four and sixteen K-chunks of 32; host and device query
+    # buffers (the latter replayed as a graph) return the same ids
+    import torch
+    s = synth.small_scene(24, 30000, 4, 320, 240, 12, dim=dim, surfaces=6)
+    views = list(s.views())
+    rng = np.random.default_rng(11)
+    with slag.Lifter(s.gaussians, dim=dim) as L:
+        for v in views:
+            L.add_view(v.camera, v.seg, v.table)
+        E, w = L.finalize()
+        assert (w > 0).sum() > 256 * 20
+        Q = rng.standard_normal((B, dim)).astype(np.float32)
+        Q[:8] = views[0].table[:8]
+        Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+        k = 16
+        ids, sc, cnt = L.query_batch(Q, k)
+        E64, w64 = E.astype(np.float64), w.astype(np.float64)
+        for b in sorted(set(range(0, B, 17)) | {B - 1, 127, 128}):
+            _check_topk(ids[b, :cnt[b]], sc[b, :cnt[b]], E64, w64, Q[b].astype(np.float64), k)
+        dQ = torch.from_numpy(Q).cuda()
+        d_ids = torch.empty((B, k), dtype=torch.int64, device="cuda")
+        d_sc = torch.empty((B, k), dtype=torch.float32, device="cuda")
+        d_cnt = torch.empty(B, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            d_ids.fill_(-7)
+            L.query_batch(dQ, k, d_ids, d_sc, d_cnt)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(d_ids.cpu().numpy(), ids)
+            np.testing.assert_array_equal(d_sc.cpu().numpy(), sc)
+
+
 def test_query_more_than_candidates(slag):
     s = synth.small_scene(19, 500, 1, 64, 64, 3, dim=128)
     with slag.Lifter(s.gaussians, dim=128) as L:
