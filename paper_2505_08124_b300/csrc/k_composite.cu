@@ -134,6 +134,33 @@ __device__ void flush_queue(const CompositeArgs &a, Smem &sm, int tid) {
     if (tid == 0) sm.nrec = 0;
 }
 
+// Whether the exponent e(X, Y) = lo + A dx^2 + Bc dx dy + C dy^2 (dx = mx - X, dy = my - Y; A, C < 0
+// and 4AC > Bc^2: a concave quadratic) reaches `thr` anywhere on the box (x0, x1, y0, y1) of a warp's
+// pixel centres. The maximum over the box is lo at the mean when the mean lies inside; otherwise it
+// lies on the box's boundary, where each edge is a concave parabola maximised at its clamped vertex.
+// An empty box (x0 = +inf) reaches nothing.
+__device__ __forceinline__ bool reaches(float mx, float my, float A, float Bc, float C, float lo, float4 box,
+                                        float thr) {
+    if (!(box.x <= box.y)) return false;
+    if (mx >= box.x && mx <= box.y && my >= box.z && my <= box.w) return lo >= thr;
+    const float ia = __frcp_rn(2.f * A), ic = __frcp_rn(2.f * C);
+    const float dx0 = mx - box.y, dx1 = mx - box.x;   // dx range over the box
+    const float dy0 = my - box.w, dy1 = my - box.z;
+    float best = -INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        // vertical edges: dx fixed, dy free in [dy0, dy1]
+        const float dx = e ? dx1 : dx0;
+        const float dy = fminf(fmaxf(-Bc * dx * ic, dy0), dy1);
+        best = fmaxf(best, fmaf(fmaf(A, dx, Bc * dy), dx, fmaf(C * dy, dy, lo)));
+        // horizontal edges: dy fixed, dx free in [dx0, dx1]
+        const float dy2 = e ? dy1 : dy0;
+        const float dx2 = fminf(fmaxf(-Bc * dy2 * ia, dx0), dx1);
+        best = fmaxf(best, fmaf(fmaf(A, dx2, Bc * dy2), dx2, fmaf(C * dy2, dy2, lo)));
+    }
+    return best >= thr;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -333,8 +360,16 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                 const float K1 = -fmaf(2.f * A, mx, Bc * my);
                 const float K2 = -fmaf(Bc, mx, 2.f * C * my);
                 const float K0 = fmaf(fmaf(A, mx, Bc * my), mx, fmaf(C * my, my, lo));
-                const uint32_t m0 = (mx - rb.z <= b0.y && mx + rb.z >= b0.x && my - rb.w <= b0.w && my + rb.w >= b0.z) ? 1u : 0u;
-                const uint32_t m1 = (mx - rb.z <= b1.y && mx + rb.z >= b1.x && my - rb.w <= b1.w && my + rb.w >= b1.z) ? 2u : 0u;
+                // a Gaussian is kept for a warp when its alpha-floor box meets the warp's box and
+                // its exponent reaches the floor on that box, less a margin that bounds the
+                // rounding of the per-pixel polynomial (terms at most S in size; X < 16, Y < 8)
+                const float S = fabsf(K0) + 16.f * fabsf(K1) + 8.f * fabsf(K2) + 256.f * fabsf(A) +
+                                128.f * fabsf(Bc) + 64.f * fabsf(C);
+                const float thr = kLog2AlphaMin - fmaf(4e-6f, S, 0.01f);
+                const uint32_t m0 = (mx - rb.z <= b0.y && mx + rb.z >= b0.x && my - rb.w <= b0.w && my + rb.w >= b0.z &&
+                                     reaches(mx, my, A, Bc, C, lo, b0, thr)) ? 1u : 0u;
+                const uint32_t m1 = (mx - rb.z <= b1.y && mx + rb.z >= b1.x && my - rb.w <= b1.w && my + rb.w >= b1.z &&
+                                     reaches(mx, my, A, Bc, C, lo, b1, thr)) ? 2u : 0u;
                 sm.rec_a[i] = make_float4(K0, K1, K2, A);
                 sm.rec_b[i] = make_float4(Bc, C, __uint_as_float(m0 | m1), lo);
             }
