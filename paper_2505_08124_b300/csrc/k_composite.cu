@@ -85,6 +85,32 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
+// Two floats as one 64-bit operand of the packed FP32 instructions (lane-pair arithmetic of
+// fma/mul .f32x2: each half rounds like the scalar instruction).
+__device__ __forceinline__ uint64_t pk(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 unpk(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -254,8 +280,9 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
     const float ox = (float)(tx * kTile), oy = (float)(ty * kTile + row0);
     const float X0 = (float)(pix0 & 15) + 0.5f, Y0 = (float)(pix0 >> 4) + 0.5f;
     const float X1 = (float)(pix1 & 15) + 0.5f, Y1 = (float)(pix1 >> 4) + 0.5f;
-    const float XX0 = X0 * X0, XY0 = X0 * Y0, YY0 = Y0 * Y0;
-    const float XX1 = X1 * X1, XY1 = X1 * Y1, YY1 = Y1 * Y1;
+    // the two pixels' monomials as packed pairs (pixel 0, pixel 1)
+    const uint64_t PX = pk(X0, X1), PY = pk(Y0, Y1);
+    const uint64_t PXX = pk(X0 * X0, X1 * X1), PXY = pk(X0 * Y0, X1 * Y1), PYY = pk(Y0 * Y0, Y1 * Y1);
     // bounding box of this warp's pixel centres (culling of Gaussians per warp), tile-local
     float wx0 = fminf(inside0 ? X0 : INFINITY, inside1 ? X1 : INFINITY);
     float wx1 = fmaxf(inside0 ? X0 : -INFINITY, inside1 ? X1 : -INFINITY);
@@ -397,7 +424,8 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
             uint32_t m = mask;
             while (m) {
                 int jj[2];
-                float al0[2], al1[2], kq0[2], kq1[2];
+                // nal = -alpha of each pixel (0 below the alpha floor)
+                float nal0[2], nal1[2], kq0[2], kq1[2];
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     jj[k] = m ? __ffs(m) - 1 : -1;
@@ -405,21 +433,23 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                 }
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    al0[k] = al1[k] = 0.f;
+                    nal0[k] = nal1[k] = 0.f;
                     kq0[k] = kq1[k] = 0.f;
                     if (jj[k] >= 0) {
                         const float4 ra = rec_a[c * 32 + jj[k]];
                         const float4 rb = rec_b[c * 32 + jj[k]];
-                        // e = q2 + log2 opacity; q2 <= 0 holds exactly (positive definite conic)
-                        const float e0 = fmaf(rb.y, YY0, fmaf(rb.x, XY0, fmaf(ra.w, XX0, fmaf(ra.z, Y0, fmaf(ra.y, X0, ra.x)))));
-                        const float e1 = fmaf(rb.y, YY1, fmaf(rb.x, XY1, fmaf(ra.w, XX1, fmaf(ra.z, Y1, fmaf(ra.y, X1, ra.x)))));
-                        if (e0 >= kLog2AlphaMin) {
-                            al0[k] = fminf(0.99f, fast_exp2(e0));
-                            kq0[k] = e0 - rb.w;
+                        // e = q2 + log2 opacity of both pixels at once; q2 <= 0 holds exactly
+                        // (positive definite conic)
+                        const float2 e = unpk(fma2(pk(rb.y, rb.y), PYY, fma2(pk(rb.x, rb.x), PXY,
+                                              fma2(pk(ra.w, ra.w), PXX, fma2(pk(ra.z, ra.z), PY,
+                                              fma2(pk(ra.y, ra.y), PX, pk(ra.x, ra.x)))))));
+                        if (e.x >= kLog2AlphaMin) {
+                            nal0[k] = fmaxf(-0.99f, -fast_exp2(e.x));
+                            kq0[k] = e.x - rb.w;
                         }
-                        if (e1 >= kLog2AlphaMin) {
-                            al1[k] = fminf(0.99f, fast_exp2(e1));
-                            kq1[k] = e1 - rb.w;
+                        if (e.y >= kLog2AlphaMin) {
+                            nal1[k] = fmaxf(-0.99f, -fast_exp2(e.y));
+                            kq1[k] = e.y - rb.w;
                         }
                     }
                 }
@@ -427,37 +457,40 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                 for (int k = 0; k < 2; ++k) {
                     if (jj[k] < 0) break;
                     // branch-free: the Gaussian whose (1 - alpha) would take T below 1e-4 stops the
-                    // pixel (T = 0) and contributes nothing; alpha = 0 leaves T as it is
+                    // pixel (T = 0) and contributes nothing; alpha = 0 leaves T as it is. Weights
+                    // are kept negated (nw = -w), as the packed products give them.
                     const int pos = base + jj[k] + 1;
-                    const float Tn0 = T0 - al0[k] * T0, Tn1 = T1 - al1[k] * T1;
-                    const bool stop0 = Tn0 < 1e-4f, stop1 = Tn1 < 1e-4f;
+                    const uint64_t PT = pk(T0, T1), PA = pk(nal0[k], nal1[k]);
+                    const float2 Tn = unpk(fma2(PA, PT, PT));   // T - alpha T
+                    const float2 aw = unpk(mul2(PA, PT));       // -alpha T
+                    const bool stop0 = Tn.x < 1e-4f, stop1 = Tn.y < 1e-4f;
                     evp0 = T0 > 0.f ? pos : evp0;
                     evp1 = T1 > 0.f ? pos : evp1;
                     if (kDebug) {
                         Tf0 = (stop0 && T0 > 0.f) ? T0 : Tf0;
                         Tf1 = (stop1 && T1 > 0.f) ? T1 : Tf1;
                     }
-                    float w0, w1;
+                    float nw0, nw1;
                     if (kKernel) {
-                        w0 = (stop0 || !(al0[k] > 0.f)) ? 0.f : fast_exp2(kq0[k]);
-                        w1 = (stop1 || !(al1[k] > 0.f)) ? 0.f : fast_exp2(kq1[k]);
+                        nw0 = (stop0 || !(nal0[k] < 0.f)) ? 0.f : -fast_exp2(kq0[k]);
+                        nw1 = (stop1 || !(nal1[k] < 0.f)) ? 0.f : -fast_exp2(kq1[k]);
                     } else {
-                        w0 = stop0 ? 0.f : al0[k] * T0;
-                        w1 = stop1 ? 0.f : al1[k] * T1;
+                        nw0 = stop0 ? 0.f : aw.x;
+                        nw1 = stop1 ? 0.f : aw.y;
                     }
-                    T0 = stop0 ? 0.f : Tn0;
-                    T1 = stop1 ? 0.f : Tn1;
-                    count0 += w0 > 0.f ? 1 : 0;
-                    count1 += w1 > 0.f ? 1 : 0;
+                    T0 = stop0 ? 0.f : Tn.x;
+                    T1 = stop1 ? 0.f : Tn.y;
+                    count0 += nw0 < 0.f ? 1 : 0;
+                    count1 += nw1 < 0.f ? 1 : 0;
                     if (kDebug) {
-                        wsum0 += w0;
-                        wsum1 += w1;
+                        wsum0 -= nw0;
+                        wsum1 -= nw1;
                     }
-                    wb_warp[jj[k] * kWStride + lane] = pair_same ? w0 + w1 : w0;
+                    wb_warp[jj[k] * kWStride + lane] = pair_same ? nw0 + nw1 : nw0;
                     // the second pixel of a pair that straddles a segment boundary adds
                     // its weight to its own slot directly
-                    if (!pair_same && w1 != 0.f && slot1 >= 0 && a.accumulate)
-                        flush_slot(a, sm, slot1, c * 32 + jj[k], w1);
+                    if (!pair_same && nw1 != 0.f && slot1 >= 0 && a.accumulate)
+                        flush_slot(a, sm, slot1, c * 32 + jj[k], -nw1);
                 }
             }
             __syncwarp();
@@ -474,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                         p2 += row[q + 2];
                         p3 += row[q + 3];
                     }
-                    const float acc = (p0 + p1) + (p2 + p3);
+                    const float acc = -((p0 + p1) + (p2 + p3));   // the buffer holds -w
                     if (acc != 0.f) flush_slot(a, sm, gs, gi, acc);
                 } else {
                     int cur = sm.slot_lane[w * 32];
@@ -486,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                             acc = 0.f;
                             cur = sl;
                         }
-                        acc += row[q];
+                        acc -= row[q];   // the buffer holds -w
                     }
                     if (cur >= 0 && acc != 0.f) flush_slot(a, sm, cur, gi, acc);
                 }
