@@ -51,9 +51,9 @@ constexpr int kSubTiles = kTile / kRows;
 constexpr int kRound = 128;                           // candidates examined per fill round
 constexpr int kBatch = 64 + kRound;                   // record capacity of a batch
 constexpr int kSmemSlots = 4;
-constexpr int kRecBuf = 256;                          // queued (Gaussian, slot) sums of a CTA
-constexpr int kRecFlush = 128;                        // queue level that triggers a flush after a batch
-constexpr int kWStride = 33;
+constexpr int kWarpQ = 104;                           // queued (Gaussian, slot) sums of a warp
+constexpr int kWarpFlush = 64;                        // queue level that triggers a flush after a batch
+constexpr int kWStride = 36;                          // transposition rows: 16-byte aligned, conflict-free
 constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2(1/255)
 
 struct Smem {
@@ -62,19 +62,20 @@ struct Smem {
     uint32_t gid[kBatch];                 // internal Gaussian index
     int32_t fill[4];                      // per-warp hit counts of a fill round
     float wb[kSmemSlots][kBatch];         // per (slot, Gaussian of the batch)
-    float wbuf[kThreads / 32][32 * kWStride];
-    uint32_t keys[kPix];
+    union {
+        float wbuf[kThreads / 32][32 * kWStride];   // per warp: (Gaussian of the chunk) x lane
+        uint32_t keys[kPix];                        // the prologue's segment sort
+    };
+    int32_t clist[kThreads / 32][34];     // per warp: the chunk's surviving Gaussians, then -1
     int32_t slot_lane[kThreads];          // slot of the sums each lane stores (its first pixel's)
     int32_t seg_of_slot[kPix];
     int32_t group_slot[kThreads / 32];    // slot shared by all of a warp's pixels, -2 = mixed
     float4 wbox[kThreads / 32];           // each warp's box of pixel centres (x0, x1, y0, y1), tile-local
     int32_t warp_tot[kThreads / 32];
     int32_t scalar[4];
-    uint32_t rec_g[kRecBuf];              // queued sums: Gaussian, weight, shared slot
-    float rec_w[kRecBuf];
-    uint8_t rec_s[kRecBuf];
-    int32_t nrec;
-    unsigned long long rec_base;
+    uint32_t rec_g[kThreads / 32][kWarpQ];   // each warp's queued sums: Gaussian, weight, slot
+    float rec_w[kThreads / 32][kWarpQ];
+    uint8_t rec_s[kThreads / 32][kWarpQ];
 };
 // 10 CTAs per SM (228 KB of shared memory, 1 KB of it reserved per CTA)
 static_assert(sizeof(Smem) + 1024 <= 233472 / 10, "composite shared memory above the 10-CTA budget");
@@ -102,6 +103,12 @@ __device__ __forceinline__ float2 unpk(uint64_t v) {
 __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
     uint64_t d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 
@@ -134,30 +141,29 @@ __device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int
     else sink_add(sink_of(a), sm.gid[gi], sm.seg_of_slot[slot], acc);
 }
 
-// Moves the queued records to the view's record list: one reservation for
-// all of them. Every thread of the CTA calls it (after a barrier).
-__device__ void flush_queue(const CompositeArgs &a, Smem &sm, int tid) {
-    const int nr = min(sm.nrec, kRecBuf);
-    if (tid == 0) sm.rec_base = nr ? atomicAdd(a.rec_count, (unsigned long long)nr) : 0ull;
-    __syncthreads();
-    const unsigned long long base = sm.rec_base;
-    for (int k = tid; k < nr; k += kThreads) {
-        const uint32_t g = sm.rec_g[k];
-        const int32_t seg = sm.seg_of_slot[sm.rec_s[k]];
-        const float w = sm.rec_w[k];
+// Moves a warp's n queued records to the view's record list with one reservation; the
+// queue is the warp's own, so only the warp takes part.
+__device__ void flush_warp(const CompositeArgs &a, Smem &sm, int w, int lane, int n) {
+    __syncwarp();
+    unsigned long long base = 0ull;
+    if (lane == 0) base = atomicAdd(a.rec_count, (unsigned long long)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int k = lane; k < n; k += 32) {
+        const uint32_t g = sm.rec_g[w][k];
+        const int32_t seg = sm.seg_of_slot[sm.rec_s[w][k]];
+        const float wt = sm.rec_w[w][k];
         if (base + (unsigned long long)k < a.rec_cap) {
             WeightRecord r;
             r.g = g;
             r.seg = seg;
-            r.w = w;
+            r.w = wt;
             r.pad = 0u;
             a.recs[base + k] = r;
         } else {
-            sink_add(sink_of(a), g, seg, w);
+            sink_add(sink_of(a), g, seg, wt);
         }
     }
-    __syncthreads();
-    if (tid == 0) sm.nrec = 0;
+    __syncwarp();
 }
 
 // Whether the exponent e(X, Y) = lo + A dx^2 + Bc dx dy + C dy^2 (dx = mx - X, dy = my - Y; A, C < 0
@@ -218,10 +224,9 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
         s_nat[h] = sg;
         sm.keys[p] = ((uint32_t)(sg + 1) << 8) | (uint32_t)p;
     }
-    if (tid == 0) {
-        sm.scalar[0] = s_nat[0];
-        sm.nrec = 0;
-    }
+    if (tid == 0) sm.scalar[0] = s_nat[0];
+    // the (slot x Gaussian) sums start at zero; each batch's reader clears what it read
+    for (int i = tid; i < kSmemSlots * kBatch; i += kThreads) (&sm.wb[0][0])[i] = 0.f;
     __syncthreads();
     const bool uniform = __syncthreads_and(s_nat[0] == sm.scalar[0] && s_nat[1] == sm.scalar[0]);
     int pos0 = tid, pos1 = tid + kThreads;
@@ -265,6 +270,9 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
     if (new1) sm.seg_of_slot[slot1] = seg1;
     sm.slot_lane[tid] = slot0;   // the slot of the sums this lane stores
     const bool pair_same = slot0 == slot1;
+    // the second pixel of a pair that straddles a segment boundary adds its weights to its own
+    // slot directly
+    const bool split1 = !pair_same && slot1 >= 0 && a.accumulate;
     {
         const int first = __shfl_sync(0xffffffffu, slot0, 0);
         const bool same = __all_sync(0xffffffffu, slot0 == first && slot1 == first);
@@ -313,6 +321,7 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
     int cursor = (int)rg.x;
     float *wb_warp = sm.wbuf[w];
     const uint32_t lt = lanemask_lt();
+    int qn = 0;   // this warp's queued records
 
     // candidates of the next fill round, prefetched into registers
     constexpr int kPer = kRound / kThreads;
@@ -401,10 +410,6 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                 sm.rec_b[i] = make_float4(Bc, C, __uint_as_float(m0 | m1), lo);
             }
         }
-        if (tid < kBatch)
-            for (int s2 = 0; s2 < ns_smem; ++s2) sm.wb[s2][tid] = 0.f;
-        for (int i = tid + kThreads; i < nb; i += kThreads)
-            for (int s2 = 0; s2 < ns_smem; ++s2) sm.wb[s2][i] = 0.f;
         __syncthreads();
         const float4 *rec_a = sm.rec_a;
         const float4 *rec_b = sm.rec_b;
@@ -421,16 +426,17 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
             // A: composite the surviving Gaussians for this thread's two pixels, two
             // Gaussians at a time: the four exponents and exp2 of a group are independent;
             // only each pixel's transmittance updates run in order
-            uint32_t m = mask;
-            while (m) {
-                int jj[2];
+            // the survivors' chunk positions in order, then -1
+            const int n = __popc(mask);
+            int32_t *cl = sm.clist[w];
+            if (hitw) cl[__popc(mask & lt)] = lane;
+            if (lane == 0) cl[n] = -1;
+            __syncwarp();
+            for (int i = 0; i < n; i += 2) {
+                const int2 jp = *reinterpret_cast<const int2 *>(cl + i);
+                const int jj[2] = {jp.x, jp.y};
                 // nal = -alpha of each pixel (0 below the alpha floor)
                 float nal0[2], nal1[2], kq0[2], kq1[2];
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    jj[k] = m ? __ffs(m) - 1 : -1;
-                    m &= m ? m - 1 : 0u;
-                }
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     nal0[k] = nal1[k] = 0.f;
@@ -487,10 +493,7 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                         wsum1 -= nw1;
                     }
                     wb_warp[jj[k] * kWStride + lane] = pair_same ? nw0 + nw1 : nw0;
-                    // the second pixel of a pair that straddles a segment boundary adds
-                    // its weight to its own slot directly
-                    if (!pair_same && nw1 != 0.f && slot1 >= 0 && a.accumulate)
-                        flush_slot(a, sm, slot1, c * 32 + jj[k], -nw1);
+                    if (split1 && nw1 != 0.f) flush_slot(a, sm, slot1, c * 32 + jj[k], -nw1);
                 }
             }
             __syncwarp();
@@ -499,15 +502,17 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                 const float *row = wb_warp + lane * kWStride;
                 const int gi = c * 32 + lane;
                 if (gs >= 0) {
-                    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+                    // four running sums (lanes q mod 4), two per packed add
+                    const float4 *row4 = reinterpret_cast<const float4 *>(row);
+                    uint64_t s01 = pk(0.f, 0.f), s23 = pk(0.f, 0.f);
 #pragma unroll
-                    for (int q = 0; q < 32; q += 4) {
-                        p0 += row[q];
-                        p1 += row[q + 1];
-                        p2 += row[q + 2];
-                        p3 += row[q + 3];
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 v = row4[q];
+                        s01 = add2(s01, pk(v.x, v.y));
+                        s23 = add2(s23, pk(v.z, v.w));
                     }
-                    const float acc = -((p0 + p1) + (p2 + p3));   // the buffer holds -w
+                    const float2 a01 = unpk(s01), a23 = unpk(s23);
+                    const float acc = -((a01.x + a01.y) + (a23.x + a23.y));   // the buffer holds -w
                     if (acc != 0.f) flush_slot(a, sm, gs, gi, acc);
                 } else {
                     int cur = sm.slot_lane[w * 32];
@@ -527,40 +532,47 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
             __syncwarp();
         }
         __syncthreads();
-        // C: per Gaussian of the batch, the non-zero (segment, sum) entries are queued;
-        // the queue goes to the view's record list in blocks, and the combine pass
-        // adds the records to the per-Gaussian tables
+        // C: per Gaussian of the batch, the non-zero (segment, sum) entries go to the warp's
+        // queue (its fill level qn is warp-uniform), clearing the table for the next batch; the
+        // queue goes to the view's record list in blocks, and the combine pass adds the
+        // records to the per-Gaussian tables
         if (a.accumulate) {
             for (int i0 = 0; i0 < nb; i0 += kThreads) {
                 const int i = i0 + tid;
                 const bool valid = i < nb;
                 const uint32_t g = valid ? sm.gid[i] : 0u;
                 for (int s2 = 0; s2 < ns_smem; ++s2) {
-                    const float v = valid ? sm.wb[s2][i] : 0.f;
+                    float v = 0.f;
+                    if (valid) {
+                        v = sm.wb[s2][i];
+                        sm.wb[s2][i] = 0.f;
+                    }
                     const uint32_t bal = __ballot_sync(0xffffffffu, v != 0.f);
                     if (bal == 0u) continue;
-                    // one queue reservation per warp; without room (or without a record
-                    // list) the sum goes to the Gaussian's table directly
-                    int base = kRecBuf;
-                    if (lane == 0 && a.recs) base = atomicAdd(&sm.nrec, __popc(bal));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (v != 0.f) {
-                        const int k = base + __popc(bal & lt);
-                        if (k < kRecBuf) {
-                            sm.rec_g[k] = g;
-                            sm.rec_w[k] = v;
-                            sm.rec_s[k] = (uint8_t)s2;
-                        } else {
-                            sink_add(sink_of(a), g, sm.seg_of_slot[s2], v);
-                        }
+                    if (!a.recs) {   // no record list: the sums go to the tables directly
+                        if (v != 0.f) sink_add(sink_of(a), g, sm.seg_of_slot[s2], v);
+                        continue;
                     }
+                    if (qn + 32 > kWarpQ) {
+                        flush_warp(a, sm, w, lane, qn);
+                        qn = 0;
+                    }
+                    if (v != 0.f) {
+                        const int k = qn + __popc(bal & lt);
+                        sm.rec_g[w][k] = g;
+                        sm.rec_w[w][k] = v;
+                        sm.rec_s[w][k] = (uint8_t)s2;
+                    }
+                    qn += __popc(bal);
                 }
             }
-            __syncthreads();
-            if (sm.nrec >= kRecFlush) flush_queue(a, sm, tid);
+            if (qn >= kWarpFlush) {
+                flush_warp(a, sm, w, lane, qn);
+                qn = 0;
+            }
         }
     }
-    if (a.accumulate && a.recs) flush_queue(a, sm, tid);
+    if (a.accumulate && a.recs && qn > 0) flush_warp(a, sm, w, lane, qn);
 
     if (inside0) {
         const int64_t pi = (int64_t)py0 * W + px0;
