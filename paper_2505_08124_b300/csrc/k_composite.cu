@@ -11,15 +11,17 @@
 // a segment carries the same embedding E_j, the D-wide product B . E is
 // deferred to the aggregation (this view only emits B).
 //
-// One CTA (64 threads, two pixels each) per 16x8 half of a 16x16 tile; the
-// tile's Gaussians are those of its bin's list (a 4x4-tile super-tile) whose
-// tile rectangle holds the tile, taken in list order:
-//   * the half tile's pixels are reordered by segment ("slot"); a thread takes
+// One CTA (128 threads, two pixels each) per 16x16 tile; the tile's Gaussians
+// are those of its bin's list (a 4x4-tile super-tile) whose tile rectangle
+// holds the tile, taken in list order:
+//   * the tile's pixels are reordered by segment ("slot"); a thread takes
 //     two neighbours in that order (almost always one segment), so each warp's
 //     64 pixels usually share one segment, and the record loads, culling and
 //     bookkeeping of a Gaussian serve two pixels with independent
 //     transmittance chains;
-//   * records of up to 192 Gaussians at a time are staged in shared memory; a
+//   * records of up to 480 Gaussians at a time are staged in shared memory (a
+//     batch is filled until it holds at least 352: few batches, hence few
+//     barriers, per tile; four CTAs per SM); a
 //     record holds mu', the conic scaled by -log2(e)/2 (so that alpha =
 //     min(0.99, 2^(q2 + log2 opacity)) needs one SFU exp2 and the alpha
 //     floor is tested on the exponent before it), and the half extents of
@@ -44,12 +46,14 @@ namespace slag {
 
 namespace {
 
-constexpr int kRows = 8;                              // tile rows per CTA: a 16x16 tile = 2 CTAs
+constexpr int kRows = 16;                             // tile rows per CTA: one CTA per 16x16 tile
 constexpr int kPix = kTile * kRows;                   // 128 pixels per CTA
-constexpr int kThreads = kPix / 2;                    // 64: two pixels per thread
+constexpr int kThreads = kPix / 2;                    // two pixels per thread
+constexpr int kWarps = kThreads / 32;
+constexpr int kCtasPerSm = 4;                         // resident CTAs per SM (shared memory)
 constexpr int kSubTiles = kTile / kRows;
 constexpr int kRound = 128;                           // candidates examined per fill round
-constexpr int kBatch = 64 + kRound;                   // record capacity of a batch
+constexpr int kBatch = 352 + kRound;                  // record capacity of a batch
 constexpr int kSmemSlots = 4;
 constexpr int kWarpQ = 104;                           // queued (Gaussian, slot) sums of a warp
 constexpr int kWarpFlush = 64;                        // queue level that triggers a flush after a batch
@@ -60,7 +64,7 @@ struct Smem {
     float4 rec_a[kBatch];                 // staged (mu'x, mu'y, a', b'); then (K0, K1, K2, K3)
     float4 rec_b[kBatch];                 // staged (c', log2 opacity, ex, ey); then (K4, K5, warp mask, log2 o)
     uint32_t gid[kBatch];                 // internal Gaussian index
-    int32_t fill[4];                      // per-warp hit counts of a fill round
+    int32_t fill[(kRound / kThreads) * kWarps];   // per-warp hit counts of a fill round
     float wb[kSmemSlots][kBatch];         // per (slot, Gaussian of the batch)
     union {
         float wbuf[kThreads / 32][32 * kWStride];   // per warp: (Gaussian of the chunk) x lane
@@ -77,8 +81,8 @@ struct Smem {
     float rec_w[kThreads / 32][kWarpQ];
     uint8_t rec_s[kThreads / 32][kWarpQ];
 };
-// 10 CTAs per SM (228 KB of shared memory, 1 KB of it reserved per CTA)
-static_assert(sizeof(Smem) + 1024 <= 233472 / 10, "composite shared memory above the 10-CTA budget");
+// kCtasPerSm CTAs per SM (228 KB of shared memory, 1 KB of it reserved per CTA)
+static_assert(sizeof(Smem) + 1024 <= 233472 / kCtasPerSm, "composite shared memory above the CTA budget");
 
 __device__ __forceinline__ float fast_exp2(float x) {
     float y;
@@ -202,7 +206,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // kKernel: record Eq. 2's kernel exp(-q/2) instead of alpha * T; kDebug: keep the
 // per-pixel weight sums and counts of the diagnostic render.
 template <bool kKernel, bool kDebug>
-__global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs a) {
+// (registers capped as for six CTAs per SM: more registers per thread measured slower)
+__global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -262,8 +267,12 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
     }
     if (lane == 31) sm.warp_tot[w] = incl;
     __syncthreads();
-    const int before = (w == 1 ? sm.warp_tot[0] : 0) + incl - new0 - new1;
-    const int nslots = sm.warp_tot[0] + sm.warp_tot[1];
+    int before = incl - new0 - new1, nslots = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+        before += q < w ? sm.warp_tot[q] : 0;
+        nslots += sm.warp_tot[q];
+    }
     const int slot0 = seg0 >= 0 ? before + new0 - 1 : -1;
     const int slot1 = seg1 >= 0 ? before + new0 + new1 - 1 : -1;
     if (new0) sm.seg_of_slot[slot0] = seg0;
@@ -386,9 +395,8 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
         // records -> tile-local exponent polynomials. With X = px + 0.5 - ox, mx = mu'x - ox (and
         // Y, my likewise), the exponent q2 + log2 o = a' dx^2 + b' dx dy + c' dy^2 + log2 o with
         // dx = mx - X, dy = my - Y is K0 + K1 X + K2 Y + K3 X^2 + K4 X Y + K5 Y^2. The culling
-        // test against the two warps' boxes is taken here once per Gaussian (bit w of the mask).
+        // test against the warps' boxes is taken here once per Gaussian (bit w of the mask).
         {
-            const float4 b0 = sm.wbox[0], b1 = sm.wbox[1];
             for (int i = tid; i < nb; i += kThreads) {
                 const float4 ra = sm.rec_a[i], rb = sm.rec_b[i];
                 const float mx = ra.x - ox, my = ra.y - oy;
@@ -398,16 +406,19 @@ __global__ void __launch_bounds__(kThreads, 12) composite_k(const CompositeArgs 
                 const float K0 = fmaf(fmaf(A, mx, Bc * my), mx, fmaf(C * my, my, lo));
                 // a Gaussian is kept for a warp when its alpha-floor box meets the warp's box and
                 // its exponent reaches the floor on that box, less a margin that bounds the
-                // rounding of the per-pixel polynomial (terms at most S in size; X < 16, Y < 8)
-                const float S = fabsf(K0) + 16.f * fabsf(K1) + 8.f * fabsf(K2) + 256.f * fabsf(A) +
-                                128.f * fabsf(Bc) + 64.f * fabsf(C);
+                // rounding of the per-pixel polynomial (terms at most S in size; X, Y < 16)
+                const float S = fabsf(K0) + 16.f * (fabsf(K1) + fabsf(K2)) + 256.f * (fabsf(A) + fabsf(Bc) + fabsf(C));
                 const float thr = kLog2AlphaMin - fmaf(4e-6f, S, 0.01f);
-                const uint32_t m0 = (mx - rb.z <= b0.y && mx + rb.z >= b0.x && my - rb.w <= b0.w && my + rb.w >= b0.z &&
-                                     reaches(mx, my, A, Bc, C, lo, b0, thr)) ? 1u : 0u;
-                const uint32_t m1 = (mx - rb.z <= b1.y && mx + rb.z >= b1.x && my - rb.w <= b1.w && my + rb.w >= b1.z &&
-                                     reaches(mx, my, A, Bc, C, lo, b1, thr)) ? 2u : 0u;
+                uint32_t mw = 0u;
+#pragma unroll
+                for (int q = 0; q < kWarps; ++q) {
+                    const float4 bq = sm.wbox[q];
+                    if (mx - rb.z <= bq.y && mx + rb.z >= bq.x && my - rb.w <= bq.w && my + rb.w >= bq.z &&
+                        reaches(mx, my, A, Bc, C, lo, bq, thr))
+                        mw |= 1u << q;
+                }
                 sm.rec_a[i] = make_float4(K0, K1, K2, A);
-                sm.rec_b[i] = make_float4(Bc, C, __uint_as_float(m0 | m1), lo);
+                sm.rec_b[i] = make_float4(Bc, C, __uint_as_float(mw), lo);
             }
         }
         __syncthreads();
