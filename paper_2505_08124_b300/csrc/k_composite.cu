@@ -14,9 +14,11 @@
 // One CTA (128 threads, two pixels each) per 16x16 tile; the tile's Gaussians
 // are those of its bin's list (a 4x4-tile super-tile) whose tile rectangle
 // holds the tile, taken in list order:
-//   * the tile's pixels are reordered by segment ("slot"); a thread takes
-//     two neighbours in that order (almost always one segment), so each warp's
-//     64 pixels usually share one segment, and the record loads, culling and
+//   * the tile's pixels are reordered by segment ("slot"), and within a
+//     segment by 8x8 block; a thread takes two neighbours in that order (almost
+//     always one segment), so each warp's 64 pixels usually share one segment
+//     and form a square block (fewer Gaussians reach a square than a 16x4
+//     strip of the same area), and the record loads, culling and
 //     bookkeeping of a Gaussian serve two pixels with independent
 //     transmittance chains;
 //   * records of up to 480 Gaussians at a time are staged in shared memory (a
@@ -197,6 +199,11 @@ __device__ __forceinline__ bool reaches(float mx, float my, float A, float Bc, f
     return best >= thr;
 }
 
+// Pixel index p of the tile in block order: four 8x8 blocks (row-major), each row-major, so that
+// a warp's 64 pixels of one segment form an 8x8 block.
+__device__ __forceinline__ int pix_x(int p) { return ((p >> 3) & 8) | (p & 7); }
+__device__ __forceinline__ int pix_y(int p) { return ((p >> 4) & 8) | ((p >> 3) & 7); }
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -222,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int p = tid + h * kThreads;
-        const int px = tx * kTile + (p & 15), py = ty * kTile + row0 + (p >> 4);
+        const int px = tx * kTile + pix_x(p), py = ty * kTile + row0 + pix_y(p);
         const bool inside = px < W && py < H;
         int32_t sg = (inside && a.seg && a.accumulate) ? a.seg[(int64_t)py * W + px] : -1;
         if (sg < -1) sg = -1;
@@ -289,14 +296,14 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
     }
     const int ns_smem = nslots < kSmemSlots ? nslots : kSmemSlots;
 
-    const int px0 = tx * kTile + (pix0 & 15), py0 = ty * kTile + row0 + (pix0 >> 4);
-    const int px1 = tx * kTile + (pix1 & 15), py1 = ty * kTile + row0 + (pix1 >> 4);
+    const int px0 = tx * kTile + pix_x(pix0), py0 = ty * kTile + row0 + pix_y(pix0);
+    const int px1 = tx * kTile + pix_x(pix1), py1 = ty * kTile + row0 + pix_y(pix1);
     const bool inside0 = px0 < W && py0 < H, inside1 = px1 < W && py1 < H;
     // pixel centres relative to the CTA's origin (ox, oy), and their monomials: the exponent of a
     // Gaussian is a quadratic polynomial in them (see the record conversion below)
     const float ox = (float)(tx * kTile), oy = (float)(ty * kTile + row0);
-    const float X0 = (float)(pix0 & 15) + 0.5f, Y0 = (float)(pix0 >> 4) + 0.5f;
-    const float X1 = (float)(pix1 & 15) + 0.5f, Y1 = (float)(pix1 >> 4) + 0.5f;
+    const float X0 = (float)pix_x(pix0) + 0.5f, Y0 = (float)pix_y(pix0) + 0.5f;
+    const float X1 = (float)pix_x(pix1) + 0.5f, Y1 = (float)pix_y(pix1) + 0.5f;
     // the two pixels' monomials as packed pairs (pixel 0, pixel 1)
     const uint64_t PX = pk(X0, X1), PY = pk(Y0, Y1);
     const uint64_t PXX = pk(X0 * X0, X1 * X1), PXY = pk(X0 * Y0, X1 * Y1), PYY = pk(Y0 * Y0, Y1 * Y1);
