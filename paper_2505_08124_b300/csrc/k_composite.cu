@@ -66,13 +66,15 @@ struct Smem {
     float4 rec_a[kBatch];                 // staged (mu'x, mu'y, a', b'); then (K0, K1, K2, K3)
     float4 rec_b[kBatch];                 // staged (c', log2 opacity, ex, ey); then (K4, K5, warp mask, log2 o)
     uint32_t gid[kBatch];                 // internal Gaussian index
-    int32_t fill[(kRound / kThreads) * kWarps];   // per-warp hit counts of a fill round
+    int32_t fill[2][(kRound / kThreads) * kWarps];   // per-warp hit counts of a fill round (by parity)
     float wb[kSmemSlots][kBatch];         // per (slot, Gaussian of the batch)
     union {
         float wbuf[kThreads / 32][32 * kWStride];   // per warp: (Gaussian of the chunk) x lane
         uint32_t keys[kPix];                        // the prologue's segment sort
     };
     int32_t clist[kThreads / 32][34];     // per warp: the chunk's surviving Gaussians, then -1
+    uint32_t split_min[2][kThreads / 32];   // prologue multi-split: per-warp minimum segment
+    int32_t split_cnt[2][kThreads / 32];    // and per-warp counts (first | second pixel << 16)
     int32_t slot_lane[kThreads];          // slot of the sums each lane stores (its first pixel's)
     int32_t seg_of_slot[kPix];
     int32_t group_slot[kThreads / 32];    // slot shared by all of a warp's pixels, -2 = mixed
@@ -223,7 +225,8 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
     const int tx = tile % a.cam.tiles_x, ty = tile / a.cam.tiles_x;
     const int W = a.cam.width, H = a.cam.height;
 
-    // ---- segment of each of the CTA's 128 pixels; positions sorted by segment --------
+    const uint32_t lt = lanemask_lt();
+    // ---- segment of each of the CTA's pixels; positions sorted by segment --------
     // (thread t reads pixels t and t + 64; a pixel index fits in the low 8 bits of a key)
     int32_t s_nat[2];
 #pragma unroll
@@ -243,16 +246,44 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
     const bool uniform = __syncthreads_and(s_nat[0] == sm.scalar[0] && s_nat[1] == sm.scalar[0]);
     int pos0 = tid, pos1 = tid + kThreads;
     if (!uniform) {
-        const uint32_t m0 = sm.keys[tid], m1 = sm.keys[tid + kThreads];
-        int r0 = 0, r1 = 0;
-#pragma unroll 8
-        for (int q = 0; q < kPix; ++q) {
-            const uint32_t kq = sm.keys[q];
-            r0 += kq < m0 ? 1 : 0;
-            r1 += kq < m1 ? 1 : 0;
+        // stable multi-split into (segment, pixel) order: one round per distinct segment of the
+        // tile, smallest first; pixel tid precedes pixel tid + kThreads of the same segment
+        const uint32_t g0 = (uint32_t)(s_nat[0] + 1), g1 = (uint32_t)(s_nat[1] + 1);
+        bool left0 = true, left1 = true;
+        int placed = 0;
+        for (int rnd = 0;; rnd ^= 1) {
+            const uint32_t mine = min(left0 ? g0 : 0xffffffffu, left1 ? g1 : 0xffffffffu);
+            const uint32_t wmin = __reduce_min_sync(0xffffffffu, mine);
+            const bool t0 = left0 && g0 == wmin, t1 = left1 && g1 == wmin;
+            if (lane == 0) sm.split_min[rnd][w] = wmin;
+            __syncthreads();
+            uint32_t mn = 0xffffffffu;
+#pragma unroll
+            for (int q = 0; q < kWarps; ++q) mn = min(mn, sm.split_min[rnd][q]);
+            if (mn == 0xffffffffu) break;
+            const bool u0 = t0 && wmin == mn, u1 = t1 && wmin == mn;
+            const uint32_t b0 = __ballot_sync(0xffffffffu, u0), b1 = __ballot_sync(0xffffffffu, u1);
+            if (lane == 0) sm.split_cnt[rnd][w] = __popc(b0) | (__popc(b1) << 16);
+            __syncthreads();
+            int before0 = 0, before1 = 0, tot0 = 0, tot1 = 0;
+#pragma unroll
+            for (int q = 0; q < kWarps; ++q) {
+                const int c = sm.split_cnt[rnd][q], c0 = c & 0xffff, c1 = c >> 16;
+                before0 += q < w ? c0 : 0;
+                before1 += q < w ? c1 : 0;
+                tot0 += c0;
+                tot1 += c1;
+            }
+            if (u0) {
+                pos0 = placed + before0 + __popc(b0 & lt);
+                left0 = false;
+            }
+            if (u1) {
+                pos1 = placed + tot0 + before1 + __popc(b1 & lt);
+                left1 = false;
+            }
+            placed += tot0 + tot1;
         }
-        pos0 = r0;
-        pos1 = r1;
     }
     __syncthreads();
     sm.keys[pos0] = ((uint32_t)(s_nat[0] + 1) << 8) | (uint32_t)tid;
@@ -336,7 +367,6 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
     const int end = (int)rg.y;
     int cursor = (int)rg.x;
     float *wb_warp = sm.wbuf[w];
-    const uint32_t lt = lanemask_lt();
     int qn = 0;   // this warp's queued records
 
     // candidates of the next fill round, prefetched into registers
@@ -356,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
         // fill: rounds of kRound candidates until at least kBatch - kRound records are
         // staged; the records of the hits are copied asynchronously, the next round's
         // candidates are loaded while this round is compacted
-        int nb = 0;
+        int nb = 0, rp = 0;
         while (nb < kBatch - kRound && cursor < end) {
             uint32_t r[kPer];
             bool hit[kPer];
@@ -376,15 +406,15 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
 #pragma unroll
             for (int k = 0; k < kPer; ++k) {
                 bal[k] = __ballot_sync(0xffffffffu, hit[k]);
-                if (lane == 0) sm.fill[k * (kThreads / 32) + w] = __popc(bal[k]);
+                if (lane == 0) sm.fill[rp][k * (kThreads / 32) + w] = __popc(bal[k]);
             }
             __syncthreads();
             int nh = 0;
-            for (int q = 0; q < kPer * (kThreads / 32); ++q) nh += sm.fill[q];
+            for (int q = 0; q < kPer * (kThreads / 32); ++q) nh += sm.fill[rp][q];
 #pragma unroll
             for (int k = 0; k < kPer; ++k) {
                 int bk = 0;
-                for (int q = 0; q < k * (kThreads / 32) + w; ++q) bk += sm.fill[q];
+                for (int q = 0; q < k * (kThreads / 32) + w; ++q) bk += sm.fill[rp][q];
                 if (hit[k]) {
                     const int pos = nb + bk + __popc(bal[k] & lt);
                     cp_async16(&sm.rec_a[pos], a.srec_a + r[k]);
@@ -394,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
             }
             nb += nh;
             cursor += kRound;
-            __syncthreads();
+            rp ^= 1;   // the next round writes the other count array: no barrier needed here
         }
         cp_async_wait_all();
         __syncthreads();
