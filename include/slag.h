@@ -157,6 +157,22 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
  * overflowed its bound in some view; OOM; CUDA. */
 slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device);
 
+/* slag_finalize with asynchronous outputs: the aggregation runs as in
+ * slag_finalize (the call returns once the embeddings are queryable), but the
+ * copies into out_emb and out_wsum are queued on the context's copy stream and
+ * complete later; the output buffers must not be read (nor freed) before
+ * slag_wait_outputs returns. Host outputs overlap with later work only when
+ * they are pinned (page-locked) memory. The context keeps two device copies
+ * of the embeddings and sum w so that the next finalize does not wait for
+ * these copies; the second copy (n x dim + n float32) is allocated by the
+ * first finalize that needs it. Errors: as slag_finalize; INVALID_ARG with
+ * SLAG_FLAG_EMBEDDINGS_ON_HOST. */
+slag_status slag_finalize_async(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device);
+
+/* Waits until every output copy queued by slag_finalize_async is complete.
+ * Errors: CUDA. */
+slag_status slag_wait_outputs(slag_ctx *ctx);
+
 /* Cosine top-k of one query vector q (dim float32, host) over the finalized
  * embeddings ("Query processing for inference"). Candidates are Gaussians
  * with sum w > 0 and a non-zero embedding; scores are q . E_k / |E_k| (q is

@@ -131,6 +131,25 @@ void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st) {
     hash_init_k<<<blocks_for(n, 256), 256, 0, st>>>(hash, n); note_launch();
 }
 
+namespace {
+
+// dst[i] = src[i] for n 32-bit words; dst may be mapped (zero-copy) host memory.
+__global__ void __launch_bounds__(256) copy_words_k(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                                    int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+}  // namespace
+
+void launch_copy_words(const void *src, void *dst, int64_t bytes, cudaStream_t st) {
+    const int64_t n = bytes / 4;
+    if (n <= 0) return;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 64);
+    copy_words_k<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const uint32_t *>(src), static_cast<uint32_t *>(dst),
+                                                   n); note_launch();
+}
+
 void launch_combine(const WeightRecord *recs, const unsigned long long *rec_count, unsigned long long rec_cap,
                     const HashSink &sink, cudaStream_t st) {
     if (rec_cap == 0) return;

@@ -76,7 +76,8 @@ struct ViewSlot {
     struct Host {
         ViewCounters v;
         unsigned long long totals[4];
-    } *h = nullptr;                        // pinned host copy read at the front sync
+    } *h = nullptr;                        // mapped pinned host copy read at the front sync
+    Host *h_dev = nullptr;                 // its device alias (written by launch_copy_words)
     cudaStream_t back = nullptr;
     cudaEvent_t ev_bin = nullptr;          // front work of the slot's view done
     cudaEvent_t ev_done = nullptr;         // back work of the slot's view done
@@ -124,7 +125,10 @@ struct slag_ctx {
         unsigned long long n_q;              // query candidates (touched rows)
         uint32_t tc_err;
         uint32_t pad;
-    } *hc = nullptr;                         // pinned host
+    } *hc = nullptr;                         // mapped pinned host
+    HostCounters *hc_dev = nullptr;          // its device alias (written by launch_copy_words)
+    unsigned char *qstage = nullptr, *qstage_dev = nullptr;   // mapped staging of host query results
+    int64_t qstage_cap = 0;
     uint32_t *tc_err = nullptr;              // device: a tensor-core kernel gave up waiting
 
     // triple log + finalize scratch
@@ -161,6 +165,15 @@ struct slag_ctx {
     bool autotune = true;
     cudaStream_t qstream = nullptr;
     cudaEvent_t qev_in = nullptr, qev_out = nullptr;
+    // Asynchronous outputs: E and sum w are double-buffered; buf[cur] holds the latest result
+    // (ctx->E and ctx->wsum point into it). A finalize moves to the other buffer while
+    // copies of the current one are still queued on cstream; ev_copy[b] completes once the
+    // copies from buffer b are done.
+    float *E_buf[2] = {nullptr, nullptr}, *wsum_buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    bool copy_pending[2] = {false, false};
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_fin = nullptr, ev_copy[2] = {nullptr, nullptr};
     cudaGraphExec_t qgraph = nullptr;
     unsigned long long qgraph_launches = 0;  // kernels in the graph (counted at each replay)
     struct QKey {
@@ -387,8 +400,8 @@ slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamPara
                          vs.srect, vs.stouched, shift, st);
     exclusive_scan_u32(vs.stouched, vs.offsets, n, &vs.ctr->P, ctx->scratch, st);
     span_end(ctx, st);
-    CK(cudaMemcpyAsync(&vs.h->v, vs.ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(vs.h->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    launch_copy_words(vs.ctr, &vs.h_dev->v, sizeof(ViewCounters), st);
+    launch_copy_words(ctx->totals, vs.h_dev->totals, 4 * sizeof(unsigned long long), st);
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     spans_resolve(ctx);
@@ -451,7 +464,8 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
     SA(dalloc(&vs.hash, n));
     SA(dalloc(&vs.ctr, 1));
     SA(dalloc(&vs.rec_count, 1));
-    SA(cudaMallocHost((void **)&vs.h, sizeof(ViewSlot::Host)));
+    SA(cudaHostAlloc((void **)&vs.h, sizeof(ViewSlot::Host), cudaHostAllocMapped));
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&vs.h_dev, vs.h, 0);
     int lo = 0, hi = 0;
     SA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     SA(cudaStreamCreateWithPriority(&vs.back, cudaStreamNonBlocking, lo));
@@ -529,7 +543,8 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
         CA(cudaMemcpyAsync(dop, g->opacities, sizeof(float) * n, cudaMemcpyHostToDevice, st));
         im = dm; is = ds; iq = dq; io = dop;
     }
-    CA(cudaMallocHost((void **)&ctx->hc, sizeof(slag_ctx::HostCounters)));
+    CA(cudaHostAlloc((void **)&ctx->hc, sizeof(slag_ctx::HostCounters), cudaHostAllocMapped));
+    CA(cudaHostGetDevicePointer((void **)&ctx->hc_dev, ctx->hc, 0));
     for (int i = 0; i < kSlots; ++i) CA(slot_alloc(ctx->slot[i], n));
     {
         int lo = 0, hi = 0;
@@ -579,6 +594,8 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     CA(dalloc(&ctx->s_hi, n)); CA(dalloc(&ctx->s_lo, n)); CA(dalloc(&ctx->s_ovf, n));
     if (!(ctx->opt_flags & SLAG_FLAG_EMBEDDINGS_ON_HOST)) CA(dalloc(&ctx->E, n * (int64_t)ctx->D));
     CA(dalloc(&ctx->inv_norm, n)); CA(dalloc(&ctx->wsum, n));
+    ctx->E_buf[0] = ctx->E;
+    ctx->wsum_buf[0] = ctx->wsum;
     CA(dalloc(&ctx->qrows, n)); CA(dalloc(&ctx->qflags, n)); CA(dalloc(&ctx->qpos, n)); CA(dalloc(&ctx->d_nq, 1));
     CA(dalloc(&ctx->bstart, (n + kBlockG - 1) / kBlockG)); CA(dalloc(&ctx->bend, (n + kBlockG - 1) / kBlockG));
     for (int i = 0; i < kSlots; ++i) launch_hash_init(ctx->slot[i].hash, n, st);
@@ -659,7 +676,7 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
         // fill level; the new capacity keeps room for a full pipeline of views, so
         // that the next views pass this test without waiting
         CK(drain_views(ctx));
-        CK(cudaMemcpyAsync(vs.h->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, fr));
+        launch_copy_words(ctx->totals, vs.h_dev->totals, 4 * sizeof(unsigned long long), fr);
         CK(cudaStreamSynchronize(fr));
         const int64_t used = (int64_t)vs.h->totals[0];
         const int64_t need = used + others + vs.log_bound;
@@ -750,8 +767,8 @@ slag_status finalize_prepare(slag_ctx *ctx) {
     cudaStream_t st = ctx->stream;
     CK(join_views(ctx));
     const ViewSlot &last = ctx->slot[(ctx->views_enqueued + kSlots - 1) % kSlots];
-    CK(cudaMemcpyAsync(ctx->hc->totals, ctx->totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&ctx->hc->v, last.ctr, sizeof(ViewCounters), cudaMemcpyDeviceToHost, st));
+    launch_copy_words(ctx->totals, ctx->hc_dev->totals, 4 * sizeof(unsigned long long), st);
+    launch_copy_words(last.ctr, &ctx->hc_dev->v, sizeof(ViewCounters), st);
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     ctx->stats.contributions = (int64_t)ctx->hc->totals[1];
@@ -906,11 +923,52 @@ slag_status aggregate_chunks(slag_ctx *ctx, int64_t chunk_gaussians, Sink &&sink
     return rc;
 }
 
-}  // namespace
+// Makes ctx->E / ctx->wsum writable by this finalize: when copies of the current buffers are
+// still queued, the finalize moves to the other pair (allocated on first use) after the copies
+// that last read it.
+slag_status claim_output_buffers(slag_ctx *ctx, cudaStream_t st) {
+    if (!ctx->copy_pending[ctx->cur]) return SLAG_OK;
+    const int nx = 1 - ctx->cur;
+    if (!ctx->E_buf[nx]) {
+        CK(dalloc(&ctx->E_buf[nx], ctx->n * (int64_t)ctx->D));
+        CK(dalloc(&ctx->wsum_buf[nx], ctx->n));
+    }
+    if (ctx->copy_pending[nx]) CK(cudaStreamWaitEvent(st, ctx->ev_copy[nx], 0));
+    ctx->copy_pending[nx] = false;
+    ctx->cur = nx;
+    ctx->E = ctx->E_buf[nx];
+    ctx->wsum = ctx->wsum_buf[nx];
+    return SLAG_OK;
+}
 
-extern "C" {
+// Queues the copies of E and sum w of this finalize on the copy stream, after the work queued on
+// st so far.
+slag_status queue_output_copies(slag_ctx *ctx, cudaStream_t st, float *out_emb, float *out_wsum,
+                                cudaMemcpyKind kind) {
+    if (!ctx->cstream) {
+        CK(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fin, cudaEventDisableTiming));
+        for (int b = 0; b < 2; ++b) CK(cudaEventCreateWithFlags(&ctx->ev_copy[b], cudaEventDisableTiming));
+    }
+    const int64_t n = ctx->n;
+    CK(cudaEventRecord(ctx->ev_fin, st));
+    CK(cudaStreamWaitEvent(ctx->cstream, ctx->ev_fin, 0));
+    if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, kind, ctx->cstream));
+    if (out_emb) {
+        // in pieces of 8 MB, so that the small copies of other streams (query results, counters)
+        // wait for one piece at most rather than for the whole matrix
+        const size_t total = sizeof(float) * (size_t)(n * ctx->D), piece = (size_t)8 << 20;
+        const char *src = reinterpret_cast<const char *>(ctx->E);
+        char *dst = reinterpret_cast<char *>(out_emb);
+        for (size_t off = 0; off < total; off += piece)
+            CK(cudaMemcpyAsync(dst + off, src + off, std::min(piece, total - off), kind, ctx->cstream));
+    }
+    CK(cudaEventRecord(ctx->ev_copy[ctx->cur], ctx->cstream));
+    ctx->copy_pending[ctx->cur] = true;
+    return SLAG_OK;
+}
 
-slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device) {
+slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device, bool async_out) {
     if (!ctx) return SLAG_ERR_INVALID_ARG;
     slag_status s = finalize_prepare(ctx);
     if (s != SLAG_OK) return s;
@@ -939,6 +997,10 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
         ctx->n_q = 0;
         ctx->finalized = false;   // queries need the embeddings on the device
         return SLAG_OK;
+    }
+    if (async_out || ctx->copy_pending[ctx->cur]) {
+        s = claim_output_buffers(ctx, st);
+        if (s != SLAG_OK) return s;
     }
     AggArgs g = agg_args(ctx);
     span_begin(ctx, SLAG_STAGE_AGGREGATE, st);
@@ -970,11 +1032,17 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     span_end(ctx, st);
     CK(cudaGetLastError());
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (out_emb) CK(cudaMemcpyAsync(out_emb, ctx->E, sizeof(float) * (size_t)(n * ctx->D), kind, st));
-    if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, kind, st));
-    CK(cudaMemcpyAsync(&ctx->hc->touched, ctx->touched, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&ctx->hc->n_q, ctx->d_nq, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&ctx->hc->tc_err, ctx->tc_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (async_out) {
+        s = queue_output_copies(ctx, st, out_emb, out_wsum, kind);
+        if (s != SLAG_OK) return s;
+    } else {
+        if (out_emb) CK(cudaMemcpyAsync(out_emb, ctx->E, sizeof(float) * (size_t)(n * ctx->D), kind, st));
+        if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, kind, st));
+    }
+    // small results through the SMs: the copy engine may be busy with an earlier step's outputs
+    launch_copy_words(ctx->touched, &ctx->hc_dev->touched, sizeof(unsigned long long), st);
+    launch_copy_words(ctx->d_nq, &ctx->hc_dev->n_q, sizeof(unsigned long long), st);
+    launch_copy_words(ctx->tc_err, &ctx->hc_dev->tc_err, sizeof(uint32_t), st);
     CK(cudaStreamSynchronize(st));
     if (ctx->hc->tc_err) return fail(ctx, SLAG_ERR_TIMEOUT, "the tensor-core aggregation gave up waiting");
     spans_resolve(ctx);
@@ -982,6 +1050,29 @@ slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     ctx->n_q = (int64_t)ctx->hc->n_q;
     ctx->finalized = true;
     ++ctx->qgen;
+    return SLAG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device) {
+    return finalize_impl(ctx, out_emb, out_wsum, on_device, false);
+}
+
+slag_status slag_finalize_async(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device) {
+    if (ctx && (ctx->opt_flags & SLAG_FLAG_EMBEDDINGS_ON_HOST))
+        return fail(ctx, SLAG_ERR_INVALID_ARG, "asynchronous outputs need the embeddings on the device");
+    return finalize_impl(ctx, out_emb, out_wsum, on_device, true);
+}
+
+slag_status slag_wait_outputs(slag_ctx *ctx) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    if (!ctx->cstream) return SLAG_OK;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->cstream));
+    ctx->copy_pending[0] = ctx->copy_pending[1] = false;
     return SLAG_OK;
 }
 
@@ -1128,12 +1219,28 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
         CK(le);
     }
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(&ctx->hc->tc_err, ctx->tc_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    launch_copy_words(ctx->tc_err, &ctx->hc_dev->tc_err, sizeof(uint32_t), st);
     if (!on_device) {
-        CK(cudaMemcpyAsync(out_ids, ids, sizeof(int64_t) * (size_t)B * k, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(out_scores, scores, sizeof(float) * (size_t)B * k, cudaMemcpyDeviceToHost, st));
-        if (out_count) CK(cudaMemcpyAsync(out_count, cnt, sizeof(int32_t) * (size_t)B, cudaMemcpyDeviceToHost, st));
+        // the results go through mapped staging written by the SMs, so that they do not queue
+        // behind an earlier finalize's output copies on the copy engine
+        const size_t bi = sizeof(int64_t) * (size_t)B * k, bs = sizeof(float) * (size_t)B * k,
+                     bc = sizeof(int32_t) * (size_t)B;
+        if ((int64_t)(bi + bs + bc) > ctx->qstage_cap) {
+            if (ctx->qstage) cudaFreeHost(ctx->qstage);
+            ctx->qstage = nullptr;
+            ctx->qstage_cap = 0;
+            const size_t cap = (bi + bs + bc) * 3 / 2;
+            CK(cudaHostAlloc((void **)&ctx->qstage, cap, cudaHostAllocMapped));
+            CK(cudaHostGetDevicePointer((void **)&ctx->qstage_dev, ctx->qstage, 0));
+            ctx->qstage_cap = (int64_t)cap;
+        }
+        launch_copy_words(ids, ctx->qstage_dev, (int64_t)bi, st);
+        launch_copy_words(scores, ctx->qstage_dev + bi, (int64_t)bs, st);
+        launch_copy_words(cnt, ctx->qstage_dev + bi + bs, (int64_t)bc, st);
         CK(cudaStreamSynchronize(st));
+        memcpy(out_ids, ctx->qstage, bi);
+        memcpy(out_scores, ctx->qstage + bi, bs);
+        if (out_count) memcpy(out_count, ctx->qstage + bi + bs, bc);
         if (ctx->hc->tc_err) return fail(ctx, SLAG_ERR_TIMEOUT, "a tensor-core query kernel gave up waiting");
     }
     return SLAG_OK;
@@ -1340,13 +1447,19 @@ void slag_destroy(slag_ctx *ctx) {
     if (ctx->qstream) { cudaStreamSynchronize(ctx->qstream); cudaStreamDestroy(ctx->qstream); }
     if (ctx->qev_in) cudaEventDestroy(ctx->qev_in);
     if (ctx->qev_out) cudaEventDestroy(ctx->qev_out);
+    if (ctx->cstream) { cudaStreamSynchronize(ctx->cstream); cudaStreamDestroy(ctx->cstream); }
+    if (ctx->ev_fin) cudaEventDestroy(ctx->ev_fin);
+    for (int b = 0; b < 2; ++b)
+        if (ctx->ev_copy[b]) cudaEventDestroy(ctx->ev_copy[b]);
+    ctx->E = ctx->wsum = nullptr;
+    for (int b = 0; b < 2; ++b) { dfree(ctx->E_buf[b]); dfree(ctx->wsum_buf[b]); }
     dfree(ctx->mean_op); dfree(ctx->cov_a); dfree(ctx->cov_b); dfree(ctx->orig_of_int); dfree(ctx->int_of_orig);
     dfree(ctx->s_hi); dfree(ctx->s_lo); dfree(ctx->s_ovf);
     dfree(ctx->dbg_T); dfree(ctx->dbg_wsum); dfree(ctx->dbg_count);
     dfree(ctx->totals); dfree(ctx->touched); dfree(ctx->tc_err);
     dfree(ctx->log_key); dfree(ctx->log_key_alt); dfree(ctx->log_w); dfree(ctx->log_w_alt);
     dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
-    dfree(ctx->table); dfree(ctx->E); dfree(ctx->inv_norm); dfree(ctx->wsum);
+    dfree(ctx->table); dfree(ctx->inv_norm);
     dfree(ctx->qrows); dfree(ctx->qflags); dfree(ctx->qpos); dfree(ctx->d_nq);
     dfree(ctx->lat_params); dfree(ctx->ztable); dfree(ctx->lat_hidden);
     dfree(ctx->ehl); dfree(ctx->qinv); dfree(ctx->qhl);
@@ -1356,6 +1469,7 @@ void slag_destroy(slag_ctx *ctx) {
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->prof_base) cudaEventDestroy(ctx->prof_base);
     if (ctx->hc) cudaFreeHost(ctx->hc);
+    if (ctx->qstage) cudaFreeHost(ctx->qstage);
     delete ctx;
 }
 

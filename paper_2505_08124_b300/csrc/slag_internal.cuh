@@ -214,6 +214,10 @@ void launch_composite(const CompositeArgs &a, cudaStream_t st);
 // k_accum.cu
 void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st);
 // Adds the view's records (the first min(*rec_count, rec_cap)) to the per-Gaussian tables.
+// Copies `bytes` (a multiple of 4) from device memory to dst with the SMs. dst may be the device
+// alias of mapped pinned host memory: small results then reach the host without queueing behind
+// bulk copies on the copy engines.
+void launch_copy_words(const void *src, void *dst, int64_t bytes, cudaStream_t st);
 void launch_combine(const WeightRecord *recs, const unsigned long long *rec_count, unsigned long long rec_cap,
                     const HashSink &sink, cudaStream_t st);
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,

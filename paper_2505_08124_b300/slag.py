@@ -66,7 +66,8 @@ EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_
            "slag_get_stats", "slag_last_error", "slag_destroy", "slag_bin_view", "slag_render_debug",
            "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk", "slag_kernel_launches",
            "slag_export_partitions", "slag_latent_param_count", "slag_latent_train", "slag_latent_apply",
-           "slag_set_latent", "slag_add_views_batched", "slag_set_autotune")
+           "slag_set_latent", "slag_add_views_batched", "slag_set_autotune", "slag_finalize_async",
+           "slag_wait_outputs")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -88,6 +89,8 @@ def load_library(path: str = LIB_PATH):
     lib.slag_create.argtypes = [ctypes.POINTER(CGaussians), ctypes.POINTER(COptions), ctypes.POINTER(P)]
     lib.slag_add_view.argtypes = [P, ctypes.POINTER(CCamera), P, P, i32, i32]
     lib.slag_finalize.argtypes = [P, P, P, i32]
+    lib.slag_finalize_async.argtypes = [P, P, P, i32]
+    lib.slag_wait_outputs.argtypes = [P]
     lib.slag_query.argtypes = [P, P, i32, P, P, P]
     lib.slag_query_batch.argtypes = [P, P, i32, i32, P, P, P, i32]
     lib.slag_reset.argtypes = [P]
@@ -241,6 +244,21 @@ class Lifter:
         dev = edev if out_emb is not None else wdev
         self._check(self._lib.slag_finalize(self._h, ep, wp, dev), "slag_finalize")
         return out_emb, out_wsum
+
+    def finalize_async(self, out_emb=None, out_wsum=None):
+        """slag_finalize_async: fills out_emb / out_wsum (numpy arrays, pinned for overlap, or torch
+        tensors) once wait_outputs() returns; the embeddings are queryable on return."""
+        for x in (out_emb, out_wsum):
+            # the copies land later: a converted temporary would be written after it is gone
+            if isinstance(x, np.ndarray) and not (x.dtype == np.float32 and x.flags.c_contiguous):
+                raise ValueError("asynchronous outputs must be C-contiguous float32 arrays")
+        ep, edev, _ = _ptr(out_emb, np.float32)
+        wp, wdev, _ = _ptr(out_wsum, np.float32)
+        dev = edev if out_emb is not None else wdev
+        self._check(self._lib.slag_finalize_async(self._h, ep, wp, dev), "slag_finalize_async")
+
+    def wait_outputs(self):
+        self._check(self._lib.slag_wait_outputs(self._h), "slag_wait_outputs")
 
     def query(self, q, k: int):
         q = np.ascontiguousarray(q, np.float32)
