@@ -106,8 +106,9 @@ __global__ void unique_flags_k(const uint64_t *__restrict__ keys, int64_t Z, uin
     flags[i] = (i == 0 || (keys[i] >> 7) != (keys[i - 1] >> 7)) ? 1u : 0u;
 }
 
+// keys in the compact layout of repack_keys_k (block above cb column bits)
 __global__ void uniques_k(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ flags,
-                          const uint32_t *__restrict__ uidx, int64_t Z, uint32_t *__restrict__ ucol,
+                          const uint32_t *__restrict__ uidx, int64_t Z, int cb, uint32_t *__restrict__ ucol,
                           uint32_t *__restrict__ ustart, uint32_t *__restrict__ bstart,
                           uint32_t *__restrict__ bend) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -115,12 +116,31 @@ __global__ void uniques_k(const uint64_t *__restrict__ keys, const uint32_t *__r
     const uint64_t k = keys[i];
     if (flags[i]) {
         const uint32_t u = uidx[i];
-        ucol[u] = (uint32_t)(k >> 7);
+        ucol[u] = (uint32_t)((k >> 7) & ((1ull << cb) - 1ull));
         ustart[u] = (uint32_t)i;
     }
-    const uint32_t blk = (uint32_t)(k >> 39);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 39) != blk) bstart[blk] = (uint32_t)i;
-    if (i == Z - 1 || (uint32_t)(keys[i + 1] >> 39) != blk) bend[blk] = (uint32_t)(i + 1);
+    const int sb = 7 + cb;
+    const uint32_t blk = (uint32_t)(k >> sb);
+    if (i == 0 || (uint32_t)(keys[i - 1] >> sb) != blk) bstart[blk] = (uint32_t)i;
+    if (i == Z - 1 || (uint32_t)(keys[i + 1] >> sb) != blk) bend[blk] = (uint32_t)(i + 1);
+}
+
+// The log key of pack_key, (block << 39) | (column << 7) | (Gaussian & 127), to the compact
+// layout (block << (7 + cb)) | (column << 7) | (Gaussian & 127) for columns < 2^cb (forward), and
+// back. The compact layout puts the sorted fields (block, column) in 7 + cb + block bits
+// without a gap, so the radix sort needs fewer passes.
+// keys_out[i] = the repacked keys_in[i] (in place when they alias); with w_in, w_out[i] = w_in[i].
+__global__ void repack_keys_k(const uint64_t *keys_in, uint64_t *keys_out, const float *w_in, float *w_out,
+                              int64_t Z, int cb, int forward) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Z) return;
+    const uint64_t k = keys_in[i];
+    const uint64_t cmask = (1ull << cb) - 1ull;
+    if (forward)
+        keys_out[i] = ((k >> 39) << (7 + cb)) | (((k >> 7) & cmask) << 7) | (k & 127ull);
+    else
+        keys_out[i] = ((k >> (7 + cb)) << 39) | (((k >> 7) & cmask) << 7) | (k & 127ull);
+    if (w_in) w_out[i] = w_in[i];
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -175,10 +195,19 @@ void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaS
     unique_flags_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys, Z, flags); note_launch();
 }
 
-void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z, uint32_t *ucol,
-                    uint32_t *ustart, uint32_t *bstart, uint32_t *bend, cudaStream_t st) {
+void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z, int col_bits,
+                    uint32_t *ucol, uint32_t *ustart, uint32_t *bstart, uint32_t *bend, cudaStream_t st) {
     if (Z <= 0) return;
-    uniques_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys, flags, uidx, Z, ucol, ustart, bstart, bend); note_launch();
+    uniques_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys, flags, uidx, Z, col_bits, ucol, ustart, bstart, bend);
+    note_launch();
+}
+
+void launch_repack_keys(const uint64_t *keys_in, uint64_t *keys_out, const float *w_in, float *w_out, int64_t Z,
+                        int col_bits, bool to_compact, cudaStream_t st) {
+    if (Z <= 0) return;
+    repack_keys_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys_in, keys_out, w_in, w_out, Z, col_bits,
+                                                      to_compact ? 1 : 0);
+    note_launch();
 }
 
 }  // namespace slag

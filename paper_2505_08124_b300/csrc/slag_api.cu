@@ -797,24 +797,25 @@ slag_status finalize_prepare(slag_ctx *ctx) {
             CK(scratch_reserve(ctx->scratch, Z));
         }
         span_begin(ctx, SLAG_STAGE_LOG_SORT, st);
-        // sort by (block, column, Gaussian): bits [0, 7 + col_bits) then [39, 39 + block_bits)
+        // sort by (block, column) -- the order of a group's Gaussians is free, the aggregation
+        // adds them in any order -- on the compact key layout, whose sorted fields are one
+        // contiguous range of col_bits + block_bits bits
+        const int cb = ceil_log2((uint64_t)ctx->table_rows);
+        launch_repack_keys(ctx->log_key, ctx->log_key, nullptr, nullptr, Z, cb, true, st);
         int shifts[16], widths[16];
-        int np = digit_passes(0, 7 + ceil_log2((uint64_t)ctx->table_rows), shifts, widths, Z);
-        np += digit_passes(39, ceil_log2((uint64_t)nblocks), shifts + np, widths + np, Z);
-        bool alt = radix_sort_u64(ctx->log_key, ctx->log_key_alt, reinterpret_cast<uint32_t *>(ctx->log_w),
-                                  reinterpret_cast<uint32_t *>(ctx->log_w_alt), Z, shifts, widths, np,
-                                  ctx->scratch, st);
-        if (alt) {
-            // the sorted log becomes the log (its order is free); capacities follow the buffers
-            std::swap(ctx->log_key, ctx->log_key_alt);
-            std::swap(ctx->log_w, ctx->log_w_alt);
-            std::swap(ctx->log_cap, ctx->fin_cap);
-            // fin_cap must cover every finalize buffer: take the smaller of the two
-            if (ctx->fin_cap > ctx->log_cap) ctx->fin_cap = ctx->log_cap;
-        }
-        launch_unique_flags(ctx->log_key, Z, ctx->flags, st);
+        int np = digit_passes(7, cb + ceil_log2((uint64_t)nblocks), shifts, widths, Z);
+        const bool alt = radix_sort_u64(ctx->log_key, ctx->log_key_alt, reinterpret_cast<uint32_t *>(ctx->log_w),
+                                        reinterpret_cast<uint32_t *>(ctx->log_w_alt), Z, shifts, widths, np,
+                                        ctx->scratch, st);
+        const uint64_t *sk = alt ? ctx->log_key_alt : ctx->log_key;
+        const float *sw = alt ? ctx->log_w_alt : ctx->log_w;
+        launch_unique_flags(sk, Z, ctx->flags, st);
         exclusive_scan_u32(ctx->flags, ctx->uidx, Z, nullptr, ctx->scratch, st);
-        launch_uniques(ctx->log_key, ctx->flags, ctx->uidx, Z, ctx->ucol, ctx->ustart, ctx->bstart, ctx->bend, st);
+        launch_uniques(sk, ctx->flags, ctx->uidx, Z, cb, ctx->ucol, ctx->ustart, ctx->bstart, ctx->bend, st);
+        // the sorted log, back in pack_key's layout, becomes the log (its order is free; later
+        // views append to it and the aggregations read it); the log keeps its own buffers, so
+        // its capacity for the views in flight stays as it was
+        launch_repack_keys(sk, ctx->log_key, alt ? sw : nullptr, ctx->log_w, Z, cb, false, st);
         span_end(ctx, st);
     }
     return SLAG_OK;

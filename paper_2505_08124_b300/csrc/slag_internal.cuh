@@ -225,9 +225,15 @@ void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, 
                     float *log_w, uint32_t *overflow, const unsigned long long *view_contrib,
                     unsigned long long *total_contrib, cudaStream_t st);
 void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaStream_t st);
-void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z,
+// keys in the compact layout (launch_repack_keys with to_compact) of columns < 2^col_bits
+void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z, int col_bits,
                     uint32_t *ucol, uint32_t *ustart, uint32_t *bstart, uint32_t *bend,
                     cudaStream_t st);
+// Log keys between pack_key's layout, (block << 39) | (column << 7) | (Gaussian & 127), and the
+// compact (block << (7 + col_bits)) | (column << 7) | (Gaussian & 127): keys_out = repacked
+// keys_in (in place when they alias); w_in (nullable) is copied to w_out alongside.
+void launch_repack_keys(const uint64_t *keys_in, uint64_t *keys_out, const float *w_in, float *w_out, int64_t Z,
+                        int col_bits, bool to_compact, cudaStream_t st);
 struct AggArgs {
     const uint64_t *keys;
     const float *w;
