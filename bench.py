@@ -480,8 +480,11 @@ def _latent_form(S, torch, scene, *args):
     workload's tables (same prototypes and noise law), then the same step aggregating codes."""
     import synth
     D = scene.dim
-    n_train, epochs = 1 << 18, 4
-    X = synth.segment_samples(1, n_train, D, 32, noise_sigma=0.1)     # the mid-scale scene's law (seed 1)
+    m = scene.meta
+    # training data drawn by the lifted scene's own generator (its seed, prototypes and noise):
+    # 1M samples on the 2M-Gaussian configuration, 262k on the mid scale (a short default run)
+    n_train, epochs = (1 << 20) if scene.gaussians.n >= 1_000_000 else (1 << 18), 4
+    X = synth.segment_samples(m["seed"], n_train, D, m["n_protos"], noise_sigma=m["noise_sigma"])
     t0 = time.perf_counter()
     params, losses = S.latent_train(X, epochs=epochs, batch=512, lr=2e-3, seed=5)
     train_s = time.perf_counter() - t0

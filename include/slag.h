@@ -67,9 +67,10 @@ enum { SLAG_WEIGHT_ALPHA_T = 0, SLAG_WEIGHT_KERNEL = 1 };
  * tests (cosine >= 1 - 1e-3 per touched Gaussian at the tested scales). No
  * float64 is used on the GPU in either form. */
 enum { SLAG_PREC_FP32 = 0, SLAG_PREC_BF16 = 1, SLAG_PREC_LATENT32 = 2 };
-/* LATENT32: the learned latent form. Each view's segment embeddings are
+/* LATENT32: the learned latent form. The views' segment embeddings are
  * encoded to 32-d codes by a small autoencoder (slag_latent_train; set with
- * slag_set_latent before the first view), the aggregation runs on the codes,
+ * slag_set_latent before the first view; finalize encodes every stored
+ * segment embedding in one pass), the aggregation runs on the codes,
  * and finalize decodes each touched Gaussian's mean code to D dimensions
  * (the decoder is not linear: dec(mean code) is not the mean of decoded
  * codes; the float32 path is the reference for its error). */

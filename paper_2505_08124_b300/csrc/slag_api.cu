@@ -158,6 +158,8 @@ struct slag_ctx {
     int64_t ztable_cap = 0;
     float *lat_hidden = nullptr;             // rows x kLatentHidden
     int64_t lat_hidden_cap = 0;
+    float *lat_Z = nullptr, *lat_Y = nullptr;   // finalize: mean codes (n x kLatent), decoded rows
+    int64_t lat_Z_cap = 0, lat_Y_cap = 0;
 
     // queries: split counts chosen by the autotuner per (batch, candidates) shape, and the
     // CUDA graph of the last device-side query (replayed while its buffers and shape repeat)
@@ -641,17 +643,10 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D), kind, fr));
-    if (ctx->precision == SLAG_PREC_LATENT32) {
-        // the view's segment embeddings -> 32-d codes (rows table_rows .. + M of the code store)
-        if (!ctx->lat_params) return fail(ctx, SLAG_ERR_STATE, "latent form: slag_set_latent before the first view");
-        if ((ctx->table_rows + M) * kLatent > ctx->ztable_cap) {
-            CK(drain_views(ctx));
-            CK(grow(ctx->ztable, ctx->ztable_cap, (ctx->table_rows + M) * kLatent, fr, ctx->table_rows * kLatent));
-        }
-        CK(grow(ctx->lat_hidden, ctx->lat_hidden_cap, (int64_t)M * kLatentHidden, fr));
-        latent_encode(ctx->lat_params, ctx->D, ctx->table + ctx->table_rows * D, M, ctx->lat_hidden,
-                      ctx->ztable + ctx->table_rows * kLatent, fr);
-    }
+    // latent form: the segment embeddings are encoded to 32-d codes at finalize, all views' rows
+    // in one pass (the codes are only read there)
+    if (ctx->precision == SLAG_PREC_LATENT32 && !ctx->lat_params)
+        return fail(ctx, SLAG_ERR_STATE, "latent form: slag_set_latent before the first view");
     if (npx > vs.seg_cap) CK(grow(vs.seg_buf, vs.seg_cap, npx, fr));
     CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, fr));
     const int32_t *seg = vs.seg_buf;
@@ -1006,16 +1001,16 @@ slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     AggArgs g = agg_args(ctx);
     span_begin(ctx, SLAG_STAGE_AGGREGATE, st);
     if (ctx->precision == SLAG_PREC_LATENT32) {
-        // mean codes per Gaussian, then the decoder in chunks of rows (internal order) -> E in caller order
+        // the segment embeddings of every view -> codes; mean codes per Gaussian; the decoder in
+        // chunks of rows (internal order) -> E in caller order
         const int64_t chunk = std::min<int64_t>(n, 1 << 18);
-        float *Z = nullptr, *Y = nullptr;
-        CK(dalloc(&Z, n * kLatent));
-        cudaError_t e = dalloc(&Y, chunk * ctx->D);
-        if (e == cudaSuccess) e = grow(ctx->lat_hidden, ctx->lat_hidden_cap, chunk * kLatentHidden, st);
-        if (e != cudaSuccess) {
-            dfree(Z); dfree(Y);
-            return fail(ctx, SLAG_ERR_OOM, "latent decode buffers");
-        }
+        const int64_t rows_t = ctx->table_rows;
+        CK(grow(ctx->ztable, ctx->ztable_cap, rows_t * kLatent, st));
+        CK(grow(ctx->lat_hidden, ctx->lat_hidden_cap, std::max(chunk, rows_t) * kLatentHidden, st));
+        CK(grow(ctx->lat_Z, ctx->lat_Z_cap, n * kLatent, st));
+        CK(grow(ctx->lat_Y, ctx->lat_Y_cap, chunk * ctx->D, st));
+        float *Z = ctx->lat_Z, *Y = ctx->lat_Y;
+        latent_encode(ctx->lat_params, ctx->D, ctx->table, (int)rows_t, ctx->lat_hidden, ctx->ztable, st);
         CK(cudaMemsetAsync(ctx->touched, 0, sizeof(unsigned long long), st));
         launch_latent_aggregate(g, ctx->ztable, Z, nblocks, st);
         for (int64_t g0 = 0; g0 < n; g0 += chunk) {
@@ -1023,8 +1018,6 @@ slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
             latent_decode(ctx->lat_params, ctx->D, Z + g0 * kLatent, (int)rows, ctx->lat_hidden, Y, st);
             launch_latent_finish(g, Y, g0, rows, st);
         }
-        CK(cudaStreamSynchronize(st));
-        dfree(Z); dfree(Y);
     } else {
         launch_aggregate(g, nblocks, ctx->tc_err, st);
     }
@@ -1462,7 +1455,7 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
     dfree(ctx->table); dfree(ctx->inv_norm);
     dfree(ctx->qrows); dfree(ctx->qflags); dfree(ctx->qpos); dfree(ctx->d_nq);
-    dfree(ctx->lat_params); dfree(ctx->ztable); dfree(ctx->lat_hidden);
+    dfree(ctx->lat_params); dfree(ctx->ztable); dfree(ctx->lat_hidden); dfree(ctx->lat_Z); dfree(ctx->lat_Y);
     dfree(ctx->ehl); dfree(ctx->qinv); dfree(ctx->qhl);
     dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);
     scratch_free(ctx->scratch);
