@@ -299,7 +299,10 @@ slag_status slag_latent_train(const float *samples, int64_t n, int32_t dim, int3
 
 /* Applies the autoencoder (host parameters) to `rows` host vectors: mode 0
  * encodes (in rows x dim -> out rows x 32), 1 decodes (rows x 32 -> rows x
- * dim), 2 does both (rows x dim -> rows x dim). */
+ * dim), 2 does both (rows x dim -> rows x dim). The decoder runs on the tensor
+ * cores (TF32 hi/lo activations times the bfloat16-rounded weights), as at
+ * finalize. Errors: INVALID_ARG, OOM, CUDA; TIMEOUT when a tensor-core wait
+ * gave up. */
 slag_status slag_latent_apply(const float *params, int32_t dim, const float *in, int64_t rows, int32_t mode,
                               float *out, void *cuda_stream);
 

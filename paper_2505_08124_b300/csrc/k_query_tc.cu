@@ -68,8 +68,12 @@ struct __align__(8) Ctl {
 constexpr size_t kSmemBytes = 1024 /* alignment slack */ + (size_t)kStages * kStageBytes + sizeof(Ctl);
 static_assert(kSmemBytes <= 232448, "fits the opt-in shared memory of a CTA");
 
+using tc::arrive;
+using tc::expect_tx;
 using tc::gtimer;
 using tc::mbar_init;
+using tc::tma_load_3d;
+using tc::wait_or_abort;
 using tc::mbar_try_wait;
 using tc::mma_commit;
 using tc::smem_desc;
@@ -77,37 +81,6 @@ using tc::smem_u32;
 using tc::tmem_ld32;
 
 constexpr uint32_t kIdesc = tc::idesc_tf32<kQN>();
-
-// Bounded wait that also gives up once *abort is set; a timeout sets *abort.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile uint32_t *abort) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*abort) return false;
-        if (gtimer() - t0 > 1000000000ull) {
-            *abort = 1u;
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// 3-D tiled TMA load of box {x.., y.., z..} into shared memory, completing on `bar`.
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-        "[%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-        : "memory");
-}
 
 __device__ __forceinline__ bool better(float s, uint32_t i, float s2, uint32_t i2) {
     return s > s2 || (s == s2 && i < i2);
@@ -369,39 +342,6 @@ void launch_split(const float *src, const uint32_t *rows, int64_t n, int64_t n_p
     tf32_split_k<<<(unsigned)blocks, 256, 0, st>>>(src, rows, n, n_pad, D, dst, inv_norm, qinv); note_launch();
 }
 
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encoder() {
-    static EncodeTiled fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    }
-    return fn;
-}
-
-// Map of two planes of `rows` x D floats (plane stride rows x D; rows a multiple of box_rows, so
-// that every box lies inside): box {32, box_rows, 2}, 128-byte swizzle.
-bool encode_planes(CUtensorMap *m, const float *base, int64_t rows, int32_t D, int box_rows) {
-    EncodeTiled fn = encoder();
-    if (!fn) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)D, (cuuint64_t)rows, 2};
-    const cuuint64_t strides[2] = {(cuuint64_t)D * 4, (cuuint64_t)rows * D * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kKC, (cuuint32_t)box_rows, 2};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 }  // namespace
 
 bool query_tc_supported(int32_t D, int32_t k) { return k >= 1 && k <= kTop && D % kKC == 0; }
@@ -415,6 +355,10 @@ int32_t query_tc_splits(int32_t B, int64_t n) {
     if (s < 1) s = 1;
     if (s > nt) s = nt;
     return (int32_t)s;
+}
+
+void launch_tf32_planes(const float *src, int64_t rows, int64_t rows_pad, int32_t K, float *dst, cudaStream_t st) {
+    launch_split(src, nullptr, rows, rows_pad, K, dst, nullptr, nullptr, st);
 }
 
 int64_t query_tc_pad_rows(int64_t n) { return (n + kQN - 1) / kQN * kQN; }
@@ -442,7 +386,8 @@ cudaError_t launch_query_topk_tc(const float *Q, int32_t B, float *Qhl, const fl
     }
     const int64_t bp = query_tc_pad_queries(B), np = query_tc_pad_rows(n);
     CUtensorMap tq, te;
-    if (!encode_planes(&tq, Qhl, bp, D, kQM) || !encode_planes(&te, Ehl, np, D, kQN)) return cudaErrorInvalidValue;
+    if (!tc::encode_planes(&tq, Qhl, bp, D, kQM, 2) || !tc::encode_planes(&te, Ehl, np, D, kQN, 2))
+        return cudaErrorInvalidValue;
     launch_split(Q, nullptr, B, bp, D, Qhl, nullptr, nullptr, st);
     int32_t nsplit = splits > 0 ? splits : query_tc_splits(B, n);
     const int64_t ntiles = np / kQN;

@@ -1006,7 +1006,8 @@ slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
         const int64_t chunk = std::min<int64_t>(n, 1 << 18);
         const int64_t rows_t = ctx->table_rows;
         CK(grow(ctx->ztable, ctx->ztable_cap, rows_t * kLatent, st));
-        CK(grow(ctx->lat_hidden, ctx->lat_hidden_cap, std::max(chunk, rows_t) * kLatentHidden, st));
+        CK(grow(ctx->lat_hidden, ctx->lat_hidden_cap,
+                std::max(rows_t * kLatentHidden, latent_decode_scratch((int)chunk, ctx->D)), st));
         CK(grow(ctx->lat_Z, ctx->lat_Z_cap, n * kLatent, st));
         CK(grow(ctx->lat_Y, ctx->lat_Y_cap, chunk * ctx->D, st));
         float *Z = ctx->lat_Z, *Y = ctx->lat_Y;
@@ -1015,7 +1016,8 @@ slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
         launch_latent_aggregate(g, ctx->ztable, Z, nblocks, st);
         for (int64_t g0 = 0; g0 < n; g0 += chunk) {
             const int64_t rows = std::min<int64_t>(chunk, n - g0);
-            latent_decode(ctx->lat_params, ctx->D, Z + g0 * kLatent, (int)rows, ctx->lat_hidden, Y, st);
+            CK(latent_decode(ctx->lat_params, ctx->D, Z + g0 * kLatent, (int)rows, ctx->lat_hidden, Y, ctx->tc_err,
+                             st));
             launch_latent_finish(g, Y, g0, rows, st);
         }
     } else {

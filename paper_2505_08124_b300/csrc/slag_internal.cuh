@@ -285,7 +285,11 @@ struct LatentLayout {
 LatentLayout latent_layout(int32_t D);
 // enc: X (rows x D) -> Z (rows x kLatent); dec: Z -> Y (rows x D); hidden: rows x kLatentHidden scratch
 void latent_encode(const float *params, int32_t D, const float *X, int rows, float *hidden, float *Z, cudaStream_t st);
-void latent_decode(const float *params, int32_t D, const float *Z, int rows, float *hidden, float *Y, cudaStream_t st);
+// dec: Z (rows x kLatent) -> Y (rows x D) on the tensor cores; scratch: latent_decode_scratch floats;
+// *err is set when a tensor-core wait gave up
+int64_t latent_decode_scratch(int rows, int32_t D);
+cudaError_t latent_decode(const float *params, int32_t D, const float *Z, int rows, float *scratch, float *Y,
+                          uint32_t *err, cudaStream_t st);
 
 // k_query.cu
 size_t query_cand_entries(int32_t B, int64_t n, int32_t k);
@@ -301,6 +305,21 @@ void launch_query_topk(const float *Q, int32_t B, const float *E, const float *i
 // rows[0..*d_count) = the Gaussians with inv_norm > 0, in increasing order (flags, pos: n each)
 void launch_touched_rows(const float *inv_norm, int64_t n, uint32_t *flags, uint32_t *pos, uint32_t *rows,
                          unsigned long long *d_count, SortScratch &scratch, cudaStream_t st);
+
+// k_dense_tc.cu: dense layers on tcgen05. out = act(A W + b) for A given as TF32 hi/lo planes
+// (2 x rows_pad x K, rows_pad = dense_tc_pad_rows(rows)) and wt = the transposed, bfloat16-rounded
+// weights (N x K, launch_weights_t). gelu_planes: out receives gelu(A W + b) as TF32 hi/lo
+// planes (2 x rows_pad x N); otherwise float32 rows (rows x ldo). K % 32 == 0, N % 128 == 0.
+// *err is set when a wait gave up.
+int64_t dense_tc_pad_rows(int64_t rows);
+void launch_weights_t(const float *W, int32_t K, int32_t N, float *wt, cudaStream_t st);
+cudaError_t launch_dense_tc(const float *a_planes, int64_t rows, int64_t rows_pad, int32_t K, const float *wt,
+                            int32_t N, const float *bias, bool gelu_planes, float *out, int64_t ldo, uint32_t *err,
+                            cudaStream_t st);
+
+// TF32 hi/lo planes (2 x rows_pad x K floats; rows rows .. rows_pad zero) of a row-major
+// rows x K float32 matrix (K a multiple of 4).
+void launch_tf32_planes(const float *src, int64_t rows, int64_t rows_pad, int32_t K, float *dst, cudaStream_t st);
 
 // k_query_tc.cu: tensor-core scores (3xTF32 on tcgen05) for k <= 16 and D % 32 == 0
 bool query_tc_supported(int32_t D, int32_t k);

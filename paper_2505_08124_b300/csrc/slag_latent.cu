@@ -43,12 +43,27 @@ void latent_encode(const float *p, int32_t D, const float *X, int rows, float *h
                 p + o.b2, false, nullptr, false, true, false, st);
 }
 
-void latent_decode(const float *p, int32_t D, const float *Z, int rows, float *hidden, float *Y, cudaStream_t st) {
+int64_t latent_decode_scratch(int rows, int32_t D) {
+    const int64_t rp = dense_tc_pad_rows(rows);
+    return rp * 2 * (kLatent + kLatentHidden) + (int64_t)kLatentHidden * kLatent + (int64_t)D * kLatentHidden;
+}
+
+// The decoder on the tensor cores (k_dense_tc.cu): the codes' TF32 planes, then
+// gelu(Z W3 + b3) as the TF32 planes of the hidden layer, then H W4 + b4 as float32 rows.
+cudaError_t latent_decode(const float *p, int32_t D, const float *Z, int rows, float *scratch, float *Y,
+                          uint32_t *err, cudaStream_t st) {
     const LatentLayout o = latent_layout(D);
-    latent_gemm(false, false, rows, kLatentHidden, kLatent, Z, kLatent, p + o.W3, kLatentHidden, hidden,
-                kLatentHidden, p + o.b3, true, nullptr, false, true, false, st);
-    latent_gemm(false, false, rows, D, kLatentHidden, hidden, kLatentHidden, p + o.W4, D, Y, D, p + o.b4, false,
-                nullptr, false, true, false, st);
+    const int64_t rp = dense_tc_pad_rows(rows);
+    float *Zp = scratch;                                   // 2 x rp x kLatent
+    float *Hp = Zp + rp * 2 * kLatent;                     // 2 x rp x kLatentHidden
+    float *W3t = Hp + rp * 2 * kLatentHidden;              // kLatentHidden x kLatent
+    float *W4t = W3t + (int64_t)kLatentHidden * kLatent;   // D x kLatentHidden
+    launch_tf32_planes(Z, rows, rp, kLatent, Zp, st);
+    launch_weights_t(p + o.W3, kLatent, kLatentHidden, W3t, st);
+    launch_weights_t(p + o.W4, kLatentHidden, D, W4t, st);
+    cudaError_t e = launch_dense_tc(Zp, rows, rp, kLatent, W3t, kLatentHidden, p + o.b3, true, Hp, 0, err, st);
+    if (e != cudaSuccess) return e;
+    return launch_dense_tc(Hp, rows, rp, kLatentHidden, W4t, D, p + o.b4, false, Y, D, err, st);
 }
 
 }  // namespace slag
@@ -187,10 +202,12 @@ slag_status slag_latent_apply(const float *params, int32_t dim, const float *in,
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int64_t P = latent_layout(dim).total;
     const int64_t din = mode == 1 ? kLatent : dim, dout = mode == 0 ? kLatent : dim;
-    float *p = nullptr, *X = nullptr, *Hd = nullptr, *Z = nullptr, *Y = nullptr;
+    float *p = nullptr, *X = nullptr, *Hd = nullptr, *Z = nullptr, *Y = nullptr, *Sd = nullptr;
+    uint32_t *derr = nullptr;
     auto cleanup = [&]() {
-        float *bufs[] = {p, X, Hd, Z, Y};
+        float *bufs[] = {p, X, Hd, Z, Y, Sd};
         for (float *b : bufs) if (b) cudaFree(b);
+        if (derr) cudaFree(derr);
     };
 #define CA2(call)                                                                                        \
     do {                                                                                                 \
@@ -202,19 +219,28 @@ slag_status slag_latent_apply(const float *params, int32_t dim, const float *in,
     } while (0)
     CA2(dmalloc(&p, P)); CA2(dmalloc(&X, rows * din)); CA2(dmalloc(&Hd, rows * kLatentHidden));
     CA2(dmalloc(&Z, rows * kLatent)); CA2(dmalloc(&Y, rows * dim));
+    CA2(dmalloc(&Sd, latent_decode_scratch((int)rows, dim)));
+    CA2(cudaMalloc((void **)&derr, sizeof(uint32_t)));
+    CA2(cudaMemsetAsync(derr, 0, sizeof(uint32_t), st));
     CA2(cudaMemcpyAsync(p, params, sizeof(float) * (size_t)P, cudaMemcpyHostToDevice, st));
     CA2(cudaMemcpyAsync(X, in, sizeof(float) * (size_t)(rows * din), cudaMemcpyHostToDevice, st));
     if (mode == 0) {
         latent_encode(p, dim, X, (int)rows, Hd, Z, st);
     } else if (mode == 1) {
-        latent_decode(p, dim, X, (int)rows, Hd, Y, st);
+        CA2(latent_decode(p, dim, X, (int)rows, Sd, Y, derr, st));
     } else {
         latent_encode(p, dim, X, (int)rows, Hd, Z, st);
-        latent_decode(p, dim, Z, (int)rows, Hd, Y, st);
+        CA2(latent_decode(p, dim, Z, (int)rows, Sd, Y, derr, st));
     }
+    uint32_t herr = 0;
     CA2(cudaMemcpyAsync(out, mode == 0 ? Z : Y, sizeof(float) * (size_t)(rows * dout), cudaMemcpyDeviceToHost, st));
+    CA2(cudaMemcpyAsync(&herr, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CA2(cudaStreamSynchronize(st));
     CA2(cudaGetLastError());
+    if (herr) {
+        cleanup();
+        return SLAG_ERR_TIMEOUT;
+    }
 #undef CA2
     cleanup();
     return SLAG_OK;
