@@ -106,6 +106,8 @@ struct slag_ctx {
     ViewSlot slot[kSlots];
     cudaStream_t front = nullptr;            // projection through binning of every view
     cudaEvent_t ev_in = nullptr;             // caller's stream at the start of a call
+    cudaStream_t up = nullptr;               // uploads of a view's inputs, beside the front stream
+    cudaEvent_t ev_up = nullptr;             // a view's uploads are done
     cudaEvent_t ev_front = nullptr;          // front stream after a view's front work
     cudaEvent_t ev_consumed = nullptr;       // the last enqueued consume
     int64_t views_enqueued = 0;              // views since create / reset (slot = count % kSlots)
@@ -385,11 +387,10 @@ int ceil_log2(uint64_t v) {
 // copies the log's fill level of that moment into vs.h->totals.
 slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int64_t *P_out,
                      uint32_t **keys_out, uint32_t **list_out, const int32_t *seg_check, int32_t M,
-                     const uint32_t **sgid_out, int shift) {
+                     const uint32_t **sgid_out, int shift, cudaEvent_t seg_ready = nullptr) {
     const int64_t n = ctx->n;
     CK(cudaMemsetAsync(vs.ctr, 0, sizeof(ViewCounters), st));
     span_begin(ctx, SLAG_STAGE_PROJECT, st);
-    if (seg_check) launch_check_seg(seg_check, (int64_t)cp.width * cp.height, M, vs.ctr, st);
     launch_project(cp, ctx->mean_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, vs.dkey[0], vs.dval[0],
                    vs.rec_a, vs.rec_b, vs.rect, vs.ctr, st);
     int shifts[8], widths[8];
@@ -401,6 +402,9 @@ slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamPara
     launch_gather_sorted(sorted_vals, n, vs.ctr, vs.rec_a, vs.rec_b, vs.rect, vs.srec_a, vs.srec_b,
                          vs.srect, vs.stouched, shift, st);
     exclusive_scan_u32(vs.stouched, vs.offsets, n, &vs.ctr->P, ctx->scratch, st);
+    // the segment map arrives on the upload stream while the above runs
+    if (seg_ready) CK(cudaStreamWaitEvent(st, seg_ready, 0));
+    if (seg_check) launch_check_seg(seg_check, (int64_t)cp.width * cp.height, M, vs.ctr, st);
     span_end(ctx, st);
     launch_copy_words(vs.ctr, &vs.h_dev->v, sizeof(ViewCounters), st);
     launch_copy_words(ctx->totals, vs.h_dev->totals, 4 * sizeof(unsigned long long), st);
@@ -554,6 +558,8 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
         CA(cudaStreamCreateWithPriority(&ctx->front, cudaStreamNonBlocking, hi));
     }
     CA(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+    CA(cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking));
+    CA(cudaEventCreateWithFlags(&ctx->ev_up, cudaEventDisableTiming));
     CA(cudaEventCreateWithFlags(&ctx->ev_front, cudaEventDisableTiming));
     CA(cudaEventCreateWithFlags(&ctx->ev_consumed, cudaEventDisableTiming));
     CA(cudaStreamCreateWithFlags(&ctx->qstream, cudaStreamNonBlocking));
@@ -630,31 +636,40 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     // the front stream starts after the caller's work so far (inputs written
     // on the caller's stream) and after the slot's previous view has been
     // composited and consumed
-    CK(cudaEventRecord(ctx->ev_in, ctx->stream));
-    CK(cudaStreamWaitEvent(fr, ctx->ev_in, 0));
-    CK(cudaStreamWaitEvent(fr, vs.ev_done, 0));
-
-    // segment embeddings -> rows [table_rows, table_rows + M) of the column store;
-    // the segment map -> the slot (both read on the front stream before the host
-    // sync below, so the caller's buffers are free when this call returns)
-    if (ctx->table_rows + M > ctx->table_cap / D) {
-        CK(drain_views(ctx));   // growing frees the old store
-        CK(grow(ctx->table, ctx->table_cap, (ctx->table_rows + M) * D, fr, ctx->table_rows * D));
-    }
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D), kind, fr));
     // latent form: the segment embeddings are encoded to 32-d codes at finalize, all views' rows
     // in one pass (the codes are only read there)
     if (ctx->precision == SLAG_PREC_LATENT32 && !ctx->lat_params)
         return fail(ctx, SLAG_ERR_STATE, "latent form: slag_set_latent before the first view");
-    if (npx > vs.seg_cap) CK(grow(vs.seg_buf, vs.seg_cap, npx, fr));
-    CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, fr));
+    CK(cudaEventRecord(ctx->ev_in, ctx->stream));
+    CK(cudaStreamWaitEvent(fr, ctx->ev_in, 0));
+    CK(cudaStreamWaitEvent(fr, vs.ev_done, 0));
+    CK(cudaStreamWaitEvent(ctx->up, ctx->ev_in, 0));
+    CK(cudaStreamWaitEvent(ctx->up, vs.ev_done, 0));
+
+    // segment embeddings -> rows [table_rows, table_rows + M) of the column store;
+    // the segment map -> the slot. Both copies run on the upload stream while the front
+    // stream projects, sorts and bins (which do not read them); the front stream waits for
+    // them before the segment check, ahead of the host sync below, so the caller's buffers
+    // are free when this call returns.
+    if (ctx->table_rows + M > ctx->table_cap / D) {
+        CK(drain_views(ctx));   // growing frees the old store
+        CK(cudaStreamSynchronize(ctx->up));
+        CK(grow(ctx->table, ctx->table_cap, (ctx->table_rows + M) * D, fr, ctx->table_rows * D));
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D), kind, ctx->up));
+    if (npx > vs.seg_cap) {
+        CK(cudaStreamSynchronize(ctx->up));
+        CK(grow(vs.seg_buf, vs.seg_cap, npx, fr));
+    }
+    CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, ctx->up));
+    CK(cudaEventRecord(ctx->ev_up, ctx->up));
     const int32_t *seg = vs.seg_buf;
 
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, vs, fr, cp, &P, &keys, &list, seg, M, &sgid, kSuperShift);
+    s = bin_view(ctx, vs, fr, cp, &P, &keys, &list, seg, M, &sgid, kSuperShift, ctx->ev_up);
     if (s != SLAG_OK) return s;
     CK(cudaEventRecord(vs.ev_bin, fr));
 
@@ -1437,6 +1452,8 @@ void slag_destroy(slag_ctx *ctx) {
     for (int i = 0; i < kSlots; ++i) slot_free(ctx->slot[i]);
     if (ctx->front) cudaStreamDestroy(ctx->front);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->up) { cudaStreamSynchronize(ctx->up); cudaStreamDestroy(ctx->up); }
+    if (ctx->ev_up) cudaEventDestroy(ctx->ev_up);
     if (ctx->ev_front) cudaEventDestroy(ctx->ev_front);
     if (ctx->ev_consumed) cudaEventDestroy(ctx->ev_consumed);
     if (ctx->qgraph) cudaGraphExecDestroy(ctx->qgraph);
