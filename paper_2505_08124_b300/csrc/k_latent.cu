@@ -13,8 +13,8 @@
 //   * the loss per sample, mean((y - x)^2) + (1 - cos(y, x)), and its
 //     gradient, one warp per sample;
 //   * bias gradients (column sums), GELU backward, Adam, row gathers.
-// The aggregation in the latent space: one warp per triple (lane = latent
-// dimension), the block's 128 x 32 sums in shared memory.
+// The aggregation in the latent space: a warp per 32 triples at a time (lane =
+// latent dimension), the block's 128 x 32 sums in shared memory.
 #include <cuda_bf16.h>
 
 #include "slag_internal.cuh"
@@ -174,10 +174,34 @@ __global__ void __launch_bounds__(256) latent_aggregate_k(const AggArgs a, const
     for (int e = tid; e < kBlockG * (kLatent + 1); e += 256) (&acc[0][0])[e] = 0.f;
     __syncthreads();
     const uint32_t ts = a.bstart[b], te = a.bend[b];
-    for (uint32_t t = ts + warp; t < te; t += 8) {
-        const uint64_t key = a.keys[t];
-        const uint32_t col = (uint32_t)((key >> 7) & 0xffffffffu);
-        atomicAdd(&acc[key & 127u][lane], a.w[t] * ztable[(int64_t)col * kLatent + lane]);
+    // a warp takes 32 triples at a time: one coalesced load of their keys and weights, then the
+    // code rows of 8 triples in flight together before their adds (lane = latent dimension)
+    for (uint32_t t0 = ts + (uint32_t)warp * 32u; t0 < te; t0 += 8u * 32u) {
+        const uint32_t t = t0 + (uint32_t)lane;
+        uint32_t colv = 0u, gv = 0u;
+        float wv = 0.f;
+        if (t < te) {
+            const uint64_t key = a.keys[t];
+            colv = (uint32_t)((key >> 7) & 0xffffffffu);
+            gv = (uint32_t)(key & 127u);
+            wv = a.w[t];
+        }
+        const int nt = (int)min(32u, te - t0);
+        for (int j = 0; j < nt; j += 8) {
+            float z[8], wj[8];
+            uint32_t gj[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int src = min(j + u, 31);
+                const uint32_t c = __shfl_sync(0xffffffffu, colv, src);
+                gj[u] = __shfl_sync(0xffffffffu, gv, src);
+                wj[u] = j + u < nt ? __shfl_sync(0xffffffffu, wv, src) : 0.f;
+                z[u] = __ldg(ztable + (int64_t)c * kLatent + lane);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (j + u < nt) atomicAdd(&acc[gj[u]][lane], wj[u] * z[u]);
+        }
     }
     __syncthreads();
     for (int e = tid; e < kBlockG * kLatent; e += 256) {
