@@ -78,6 +78,21 @@ def test_autoencoder_forward_matches_float64(slag):
     np.testing.assert_allclose(slag.latent_apply(p, Z, 1), ref, rtol=0, atol=2e-5 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("D,rows", [(512, 50000), (384, 20000)])
+def test_decoder_many_tiles_matches_float64(slag, D, rows):
+    # the decoder's dense layers are persistent: with more 128-row tiles than SMs each CTA takes
+    # several, alternating its two TMEM accumulators (D = 384: 128-column tiles, else 256)
+    import torch
+    rng = np.random.default_rng(7)
+    p = (rng.standard_normal(slag.latent_param_count(D)) * 0.05).astype(np.float32)
+    Z = rng.standard_normal((rows, L)).astype(np.float32)
+    P = _unpack(p, D, torch)
+    ref = _ref_forward(P, torch.tensor(Z.astype(np.float64)), torch, 1).numpy()
+    got = slag.latent_apply(p, Z, 1)
+    assert got.shape == (rows, D)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-5 * np.abs(ref).max())
+
+
 def test_first_adam_step_follows_the_gradient(slag):
     import torch
     D, n = 128, 512
