@@ -696,9 +696,9 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
         ctx->log_cap = c1;
     }
 
-    // record list of the composite: one record per (Gaussian, 16x4 quarter tile,
-    // segment) with a non-zero sum; sums beyond the capacity go to the tables
-    // directly, so the capacity only bounds the fast path
+    // record list of the composite: one record per (Gaussian, tile, segment) with a
+    // non-zero sum (per batch of the tile's CTA); sums beyond the capacity go to the
+    // tables directly, so the capacity only bounds the fast path
     const int64_t rec_need = (int64_t)vs.h->v.P_tiles + ctx->n;
     if (rec_need > vs.rec_cap) CK(grow(vs.recs, vs.rec_cap, rec_need, fr));
 
