@@ -22,8 +22,9 @@
 //     bookkeeping of a Gaussian serve two pixels with independent
 //     transmittance chains;
 //   * records of up to 480 Gaussians at a time are staged in shared memory (a
-//     batch is filled until it holds at least 352: few batches, hence few
-//     barriers, per tile; four CTAs per SM); a
+//     batch is filled, in rounds of 256 candidates, until it holds at least
+//     224: few batches and rounds, hence few barriers, per tile; four CTAs per
+//     SM); a
 //     record holds mu', the conic scaled by -log2(e)/2 (so that alpha =
 //     min(0.99, 2^(q2 + log2 opacity)) needs one SFU exp2 and the alpha
 //     floor is tested on the exponent before it), and the half extents of
@@ -54,8 +55,8 @@ constexpr int kThreads = kPix / 2;                    // two pixels per thread
 constexpr int kWarps = kThreads / 32;
 constexpr int kCtasPerSm = 4;                         // resident CTAs per SM (shared memory)
 constexpr int kSubTiles = kTile / kRows;
-constexpr int kRound = 128;                           // candidates examined per fill round
-constexpr int kBatch = 352 + kRound;                  // record capacity of a batch
+constexpr int kRound = 256;                           // candidates examined per fill round
+constexpr int kBatch = 224 + kRound;                  // record capacity of a batch
 constexpr int kSmemSlots = 4;
 constexpr int kWarpQ = 104;                           // queued (Gaussian, slot) sums of a warp
 constexpr int kWarpFlush = 64;                        // queue level that triggers a flush after a batch
