@@ -178,6 +178,14 @@ struct slag_ctx {
     bool copy_pending[2] = {false, false};
     cudaStream_t cstream = nullptr;
     cudaEvent_t ev_fin = nullptr, ev_copy[2] = {nullptr, nullptr};
+    // The embeddings' download of an asynchronous finalize, still to be issued: a piece after
+    // each later view's host sync (a continuous download of the whole matrix would hold the
+    // PCIe link and delay every view's sync), the rest at the next finalize or wait.
+    const char *pend_src = nullptr;
+    char *pend_dst = nullptr;
+    size_t pend_left = 0, pend_off = 0, pend_piece = 0;
+    cudaMemcpyKind pend_kind = cudaMemcpyDeviceToHost;
+    int pend_buf = 0;
     cudaGraphExec_t qgraph = nullptr;
     unsigned long long qgraph_launches = 0;  // kernels in the graph (counted at each replay)
     struct QKey {
@@ -496,6 +504,9 @@ void slot_free(ViewSlot &vs) {
     vs.back = nullptr; vs.ev_bin = vs.ev_done = nullptr;
 }
 
+// issues pieces of a pending asynchronous download (defined with the finalize helpers)
+slag_status issue_pending(slag_ctx *ctx, int pieces);
+
 }  // namespace
 
 extern "C" {
@@ -670,6 +681,10 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
     s = bin_view(ctx, vs, fr, cp, &P, &keys, &list, seg, M, &sgid, kSuperShift, ctx->ev_up);
+    if (s != SLAG_OK) return s;
+    // one piece of an earlier asynchronous finalize's download: it runs while this view is
+    // composited, between two views' host syncs
+    s = issue_pending(ctx, 1);
     if (s != SLAG_OK) return s;
     CK(cudaEventRecord(vs.ev_bin, fr));
 
@@ -934,6 +949,21 @@ slag_status aggregate_chunks(slag_ctx *ctx, int64_t chunk_gaussians, Sink &&sink
     return rc;
 }
 
+// Issues up to `pieces` pieces of the pending download on the copy stream (all of them when
+// pieces < 0); with the last one, the download's buffer gets its copy event.
+slag_status issue_pending(slag_ctx *ctx, int pieces) {
+    if (!ctx->pend_left) return SLAG_OK;
+    for (int i = 0; (pieces < 0 || i < pieces) && ctx->pend_left > 0; ++i) {
+        const size_t b = std::min(ctx->pend_piece, ctx->pend_left);
+        CK(cudaMemcpyAsync(ctx->pend_dst + ctx->pend_off, ctx->pend_src + ctx->pend_off, b, ctx->pend_kind,
+                           ctx->cstream));
+        ctx->pend_off += b;
+        ctx->pend_left -= b;
+    }
+    if (!ctx->pend_left) CK(cudaEventRecord(ctx->ev_copy[ctx->pend_buf], ctx->cstream));
+    return SLAG_OK;
+}
+
 // Makes ctx->E / ctx->wsum writable by this finalize: when copies of the current buffers are
 // still queued, the finalize moves to the other pair (allocated on first use) after the copies
 // that last read it.
@@ -962,26 +992,33 @@ slag_status queue_output_copies(slag_ctx *ctx, cudaStream_t st, float *out_emb, 
         for (int b = 0; b < 2; ++b) CK(cudaEventCreateWithFlags(&ctx->ev_copy[b], cudaEventDisableTiming));
     }
     const int64_t n = ctx->n;
+    slag_status s = issue_pending(ctx, -1);
+    if (s != SLAG_OK) return s;
     CK(cudaEventRecord(ctx->ev_fin, st));
     CK(cudaStreamWaitEvent(ctx->cstream, ctx->ev_fin, 0));
     if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, kind, ctx->cstream));
-    if (out_emb) {
-        // in pieces of 8 MB, so that the small copies of other streams (query results, counters)
-        // wait for one piece at most rather than for the whole matrix
-        const size_t total = sizeof(float) * (size_t)(n * ctx->D), piece = (size_t)8 << 20;
-        const char *src = reinterpret_cast<const char *>(ctx->E);
-        char *dst = reinterpret_cast<char *>(out_emb);
-        for (size_t off = 0; off < total; off += piece)
-            CK(cudaMemcpyAsync(dst + off, src + off, std::min(piece, total - off), kind, ctx->cstream));
-    }
-    CK(cudaEventRecord(ctx->ev_copy[ctx->cur], ctx->cstream));
     ctx->copy_pending[ctx->cur] = true;
+    if (!out_emb) {
+        CK(cudaEventRecord(ctx->ev_copy[ctx->cur], ctx->cstream));
+        return SLAG_OK;
+    }
+    // the embeddings in pieces of about 1/64 (at least 4 MB), issued by later calls
+    const size_t total = sizeof(float) * (size_t)(n * ctx->D);
+    ctx->pend_src = reinterpret_cast<const char *>(ctx->E);
+    ctx->pend_dst = reinterpret_cast<char *>(out_emb);
+    ctx->pend_left = total;
+    ctx->pend_off = 0;
+    ctx->pend_piece = std::max<size_t>((size_t)4 << 20, (total + 63) / 64);
+    ctx->pend_kind = kind;
+    ctx->pend_buf = ctx->cur;
     return SLAG_OK;
 }
 
 slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device, bool async_out) {
     if (!ctx) return SLAG_ERR_INVALID_ARG;
-    slag_status s = finalize_prepare(ctx);
+    slag_status s = issue_pending(ctx, -1);   // an earlier download's remaining pieces
+    if (s != SLAG_OK) return s;
+    s = finalize_prepare(ctx);
     if (s != SLAG_OK) return s;
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->n;
@@ -1082,6 +1119,8 @@ slag_status slag_wait_outputs(slag_ctx *ctx) {
     if (!ctx) return SLAG_ERR_INVALID_ARG;
     if (!ctx->cstream) return SLAG_OK;
     CK(cudaSetDevice(ctx->device));
+    slag_status s = issue_pending(ctx, -1);
+    if (s != SLAG_OK) return s;
     CK(cudaStreamSynchronize(ctx->cstream));
     ctx->copy_pending[0] = ctx->copy_pending[1] = false;
     return SLAG_OK;
