@@ -355,6 +355,15 @@ typedef struct {
  * synchronisation: spans are resolved at the calls that synchronise). */
 slag_status slag_set_profiling(slag_ctx *ctx, int32_t enable);
 
+/* Per-stage timing of the stages in `stages` only (bit s = stage s; bits at
+ * or above SLAG_STAGE_COUNT are ignored; 0 turns timing off). Each timed
+ * span costs two event records and, when resolved, a few driver calls on
+ * the host, so timing only the stage of interest disturbs the rest least.
+ * Spans resolve at slag_get_profile, or once 4096 are pending. The first
+ * call that turns timing on creates the events for that backlog. With the
+ * query stage untimed, device-buffer queries keep their CUDA graph. */
+slag_status slag_set_profiling_stages(slag_ctx *ctx, uint32_t stages);
+
 /* Synchronises the context's streams, adds every finished span to *out and,
  * when reset is non-zero, clears the totals. busy_ms covers the spans
  * resolved since profiling was enabled or last reset. */

@@ -225,7 +225,8 @@ struct slag_ctx {
         int stage;
         cudaEvent_t a, b;
     };
-    bool prof_on = false;
+    uint32_t prof_mask = 0;                                // stages timed (bit s = stage s)
+    bool span_open = false;                                // spans.back() waits for its end event
     std::vector<Span> spans;
     std::vector<cudaEvent_t> event_pool;
     slag_profile prof{};
@@ -331,19 +332,28 @@ cudaEvent_t take_event(slag_ctx *ctx) {
 // Spans of views in flight overlap, so stage totals add device time per
 // stream, not wall time.
 void span_begin(slag_ctx *ctx, int stage, cudaStream_t st) {
-    if (!ctx->prof_on) return;
+    if (!((ctx->prof_mask >> stage) & 1u)) return;
     slag_ctx::Span sp{stage, take_event(ctx), take_event(ctx)};
     cudaEventRecord(sp.a, st);
     ctx->spans.push_back(sp);
+    ctx->span_open = true;
 }
 
 void span_end(slag_ctx *ctx, cudaStream_t st) {
-    if (!ctx->prof_on || ctx->spans.empty()) return;
+    if (!ctx->span_open) return;
     cudaEventRecord(ctx->spans.back().b, st);
+    ctx->span_open = false;
 }
 
+// Spans left open between resolutions. Reading a span's times costs several
+// driver calls on the host, and the views' host syncs are on the critical path,
+// so routine calls resolve only once this many spans are pending; the totals
+// resolve everything.
+constexpr size_t kSpanBacklog = 4096;
+
 // Adds every finished span to the totals; spans still in flight stay.
-void spans_resolve(slag_ctx *ctx) {
+void spans_resolve(slag_ctx *ctx, bool all = true) {
+    if (!all && ctx->spans.size() < kSpanBacklog) return;
     size_t keep = 0;
     for (size_t i = 0; i < ctx->spans.size(); ++i) {
         auto &sp = ctx->spans[i];
@@ -418,7 +428,7 @@ slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamPara
     launch_copy_words(ctx->totals, vs.h_dev->totals, 4 * sizeof(unsigned long long), st);
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
-    spans_resolve(ctx);
+    spans_resolve(ctx, false);
     if (vs.h->v.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
     const int64_t P = (int64_t)vs.h->v.P;   // pairs at the binning granularity
     if (P > 0x7fffffffLL || vs.h->v.P_tiles > 0x7fffffffULL)
@@ -676,15 +686,18 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, ctx->up));
     CK(cudaEventRecord(ctx->ev_up, ctx->up));
     const int32_t *seg = vs.seg_buf;
+    // one piece of an earlier asynchronous finalize's download, queued behind this view's
+    // upload: the two would share the PCIe link, and the front stream waits for the upload
+    if (ctx->pend_left) {
+        CK(cudaStreamWaitEvent(ctx->cstream, ctx->ev_up, 0));
+        s = issue_pending(ctx, 1);
+        if (s != SLAG_OK) return s;
+    }
 
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
     s = bin_view(ctx, vs, fr, cp, &P, &keys, &list, seg, M, &sgid, kSuperShift, ctx->ev_up);
-    if (s != SLAG_OK) return s;
-    // one piece of an earlier asynchronous finalize's download: it runs while this view is
-    // composited, between two views' host syncs
-    s = issue_pending(ctx, 1);
     if (s != SLAG_OK) return s;
     CK(cudaEventRecord(vs.ev_bin, fr));
 
@@ -1040,7 +1053,7 @@ slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
         if (out_wsum && on_device) CK(cudaMemcpyAsync(out_wsum, ctx->wsum, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(&ctx->hc->touched, ctx->touched, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        spans_resolve(ctx);
+        spans_resolve(ctx, false);
         ctx->stats.touched = (int64_t)ctx->hc->touched;
         ctx->n_q = 0;
         ctx->finalized = false;   // queries need the embeddings on the device
@@ -1093,7 +1106,7 @@ slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     launch_copy_words(ctx->tc_err, &ctx->hc_dev->tc_err, sizeof(uint32_t), st);
     CK(cudaStreamSynchronize(st));
     if (ctx->hc->tc_err) return fail(ctx, SLAG_ERR_TIMEOUT, "the tensor-core aggregation gave up waiting");
-    spans_resolve(ctx);
+    spans_resolve(ctx, false);
     ctx->stats.touched = (int64_t)ctx->hc->touched;
     ctx->n_q = (int64_t)ctx->hc->n_q;
     ctx->finalized = true;
@@ -1232,7 +1245,7 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
                           scores, cnt, s2);
         return cudaGetLastError();
     };
-    if (on_device && !ctx->prof_on) {
+    if (on_device && !((ctx->prof_mask >> SLAG_STAGE_QUERY) & 1u)) {
         // device buffers: the launches run as a CUDA graph on the query stream, captured for this
         // (buffers, shape, split, finalize) and replayed while they repeat
         const slag_ctx::QKey key{dQ, ids, scores, cnt, B, k, splits, nq, ctx->qgen};
@@ -1525,16 +1538,27 @@ void slag_destroy(slag_ctx *ctx) {
     delete ctx;
 }
 
-slag_status slag_set_profiling(slag_ctx *ctx, int32_t enable) {
+slag_status slag_set_profiling_stages(slag_ctx *ctx, uint32_t stages) {
     if (!ctx) return SLAG_ERR_INVALID_ARG;
     CK(cudaSetDevice(ctx->device));
-    if (enable && !ctx->prof_on) {
+    stages &= (1u << SLAG_STAGE_COUNT) - 1;
+    if (stages && !ctx->prof_mask) {
         if (!ctx->prof_base) CK(cudaEventCreate(&ctx->prof_base));
+        // events for a full backlog of spans, created here rather than inside the timed work
+        while (ctx->event_pool.size() < 2 * kSpanBacklog + 64) {
+            cudaEvent_t e = nullptr;
+            CK(cudaEventCreate(&e));
+            ctx->event_pool.push_back(e);
+        }
         CK(cudaEventRecord(ctx->prof_base, ctx->stream));
         for (auto &b : ctx->busy) b.clear();
     }
-    ctx->prof_on = enable != 0;
+    ctx->prof_mask = stages;
     return SLAG_OK;
+}
+
+slag_status slag_set_profiling(slag_ctx *ctx, int32_t enable) {
+    return slag_set_profiling_stages(ctx, enable ? (1u << SLAG_STAGE_COUNT) - 1 : 0u);
 }
 
 slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset) {

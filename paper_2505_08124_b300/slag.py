@@ -67,7 +67,7 @@ EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_
            "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk", "slag_kernel_launches",
            "slag_export_partitions", "slag_latent_param_count", "slag_latent_train", "slag_latent_apply",
            "slag_set_latent", "slag_add_views_batched", "slag_set_autotune", "slag_finalize_async",
-           "slag_wait_outputs")
+           "slag_wait_outputs", "slag_set_profiling_stages")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH):
     lib.slag_bin_view.argtypes = [P, ctypes.POINTER(CCamera), P, P, P, i64, P]
     lib.slag_render_debug.argtypes = [P, ctypes.POINTER(CCamera), P, P, P]
     lib.slag_set_profiling.argtypes = [P, i32]
+    lib.slag_set_profiling_stages.argtypes = [P, ctypes.c_uint32]
     lib.slag_get_profile.argtypes = [P, ctypes.POINTER(CProfile), i32]
     lib.slag_export_partitions.argtypes = [P, ctypes.c_char_p, i32, i32, i64, ctypes.POINTER(i64)]
     lib.slag_latent_param_count.argtypes = [i32]
@@ -311,8 +312,15 @@ class Lifter:
         return {k: int(getattr(s, k)) for k, _ in CStats._fields_}
 
     # -- diagnostics ----------------------------------------------------------
-    def set_profiling(self, on: bool = True):
-        self._check(self._lib.slag_set_profiling(self._h, 1 if on else 0), "slag_set_profiling")
+    def set_profiling(self, on: bool = True, stages=None):
+        """Per-stage timing on or off; `stages` (names from STAGES) limits it to those stages."""
+        if stages is None:
+            self._check(self._lib.slag_set_profiling(self._h, 1 if on else 0), "slag_set_profiling")
+            return
+        mask = 0
+        for name in stages:
+            mask |= 1 << STAGES.index(name)
+        self._check(self._lib.slag_set_profiling_stages(self._h, mask if on else 0), "slag_set_profiling_stages")
 
     def profile(self, reset: bool = False) -> dict:
         """{stage: (summed span ms, spans)} from events recorded in the streams that run each stage."""
