@@ -141,11 +141,19 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
  * row-major, the embedding E_j of segment j. A pixel may belong to several
  * overlapping masks by adding the same camera again with a second id map.
  * Runs projection, tile binning, the two sorts, compositing, masking and the
- * per-view reduction; synchronises the stream once, to size the view's
- * workspace. Errors: INVALID_ARG (NULL pointer, camera not finite or out of
- * range, M < 1 or M >= 2^24, a segment id outside [-1, M): the view is then
- * not added); CAPACITY (more than 2^31 - 1 Gaussian-tile pairs in the view);
- * OOM; CUDA. */
+ * per-view reduction, in two halves. This call uploads the inputs, checks the
+ * segment ids and queues the first half (projection, depth sort, tile-count
+ * scan). The second half (pair emission, bin sort, compositing, masking,
+ * reduction) needs the view's pair count on the host to size its workspace;
+ * it is queued by the next call on the context: the next slag_add_view, or
+ * slag_finalize / slag_finalize_async / slag_export_partitions /
+ * slag_get_profile / slag_bin_view / slag_render_debug. The caller's buffers
+ * are free when the call returns. Errors: INVALID_ARG (NULL pointer, camera
+ * not finite or out of range, M < 1 or M >= 2^24, a segment id outside
+ * [-1, M): the view is then not added); OOM; CUDA. The second half's errors,
+ * CAPACITY (more than 2^31 - 1 Gaussian-tile pairs in the view), OOM and CUDA,
+ * are returned by the call that queues it, and the context then needs
+ * slag_reset. slag_reset drops a view whose second half is not queued. */
 slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *seg_ids,
                           const float *seg_table, int32_t M, int32_t on_device);
 

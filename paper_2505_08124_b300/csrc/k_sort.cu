@@ -400,8 +400,12 @@ __global__ void __launch_bounds__(kThreads) scan_tiles(const uint32_t *__restric
 }  // namespace
 
 cudaError_t scratch_reserve(SortScratch &s, int64_t n) {
-    // 2048 bins x the tile count of the tiling used for n items (1024-item tiles below 2M)
-    const int64_t tiles = n < (1 << 21) ? (n + 1023) / 1024 + 1 : (n + kTileItems - 1) / kTileItems + 1;
+    // 2048 bins x the largest tile count of a sort of at most n items: 1024-item tiles below
+    // 2M items (up to 2049 tiles), kTileItems-item tiles above, so the count is not monotonic
+    // in the size and a reservation for n must cover every smaller sort too
+    const int64_t small_max = n < (1 << 21) ? (n + 1023) / 1024 + 1 : ((1 << 21) - 1 + 1023) / 1024 + 1;
+    const int64_t large = n < (1 << 21) ? 0 : (n + kTileItems - 1) / kTileItems + 1;
+    const int64_t tiles = small_max > large ? small_max : large;
     size_t need_hist = (size_t)2048 * tiles;
     if (!s.digit_tot) {
         cudaError_t e = cudaMalloc(&s.digit_tot, 2048 * sizeof(uint32_t));

@@ -48,9 +48,9 @@ namespace {
 
 constexpr int kSlots = 6;   // views in flight
 
-// Buffers of one view in flight. The front stream fills them; the slot's back
-// stream composites from them; the front stream reuses them for the view
-// kSlots later once ev_done has fired.
+// Buffers of one view in flight. Stage A (front stream) and stage B (second
+// front stream) fill them; the slot's back stream composites from them; stage A
+// reuses them for the view kSlots later once ev_done has fired.
 struct ViewSlot {
     // n-sized
     uint32_t *dkey[2] = {nullptr, nullptr}, *dval[2] = {nullptr, nullptr};
@@ -72,16 +72,23 @@ struct ViewSlot {
     WeightRecord *recs = nullptr;          // the composite's (Gaussian, segment, weight) sums
     int64_t rec_cap = 0;
     unsigned long long *rec_count = nullptr;
-    ViewCounters *ctr = nullptr;           // device
+    ViewCounters *ctr = nullptr;           // device: stage A's counters
+    ViewCounters *ctr_up = nullptr;        // device: the segment-id check of the view's upload
     struct Host {
-        ViewCounters v;
-        unsigned long long totals[4];
-    } *h = nullptr;                        // mapped pinned host copy read at the front sync
+        ViewCounters v;                    // stage A's counters
+        ViewCounters vu;                   // the segment-id check
+        unsigned long long totals[4];      // the context's totals when stage A ended
+    } *h = nullptr;                        // mapped pinned host copy
     Host *h_dev = nullptr;                 // its device alias (written by launch_copy_words)
+    const uint32_t *sgid = nullptr;        // internal ids in depth order (stage A's output)
+    CamParams cp{};                        // the view's camera
+    int64_t view_base = 0;                 // its first column in the segment-embedding store
     cudaStream_t back = nullptr;
-    cudaEvent_t ev_bin = nullptr;          // front work of the slot's view done
+    cudaEvent_t ev_a = nullptr;            // stage A of the slot's view done
+    cudaEvent_t ev_up = nullptr;           // the view's uploads and segment-id check done
+    cudaEvent_t ev_bin = nullptr;          // stage B of the slot's view done
     cudaEvent_t ev_done = nullptr;         // back work of the slot's view done
-    int64_t log_bound = 0;                 // triples the slot's view may append after its front sync
+    int64_t log_bound = 0;                 // triples the slot's view may append after stage A
 };
 
 }  // namespace
@@ -104,13 +111,16 @@ struct slag_ctx {
 
     // views in flight
     ViewSlot slot[kSlots];
-    cudaStream_t front = nullptr;            // projection through binning of every view
+    cudaStream_t front = nullptr;            // stage A of every view: projection to tile-count scan
+    cudaStream_t front_b = nullptr;          // stage B: pair emission, bin sort, tile order
     cudaEvent_t ev_in = nullptr;             // caller's stream at the start of a call
-    cudaStream_t up = nullptr;               // uploads of a view's inputs, beside the front stream
-    cudaEvent_t ev_up = nullptr;             // a view's uploads are done
-    cudaEvent_t ev_front = nullptr;          // front stream after a view's front work
+    cudaStream_t up = nullptr;               // uploads of a view's inputs and their check
+    cudaEvent_t ev_front = nullptr;          // front stream at a join
+    cudaEvent_t ev_front_b = nullptr;        // stage-B stream at a join
     cudaEvent_t ev_consumed = nullptr;       // the last enqueued consume
-    int64_t views_enqueued = 0;              // views since create / reset (slot = count % kSlots)
+    int64_t views_enqueued = 0;              // views accepted since create / reset (slot = count % kSlots)
+    bool deferred = false;                   // the last accepted view's stage B and back half wait
+                                             // for the next call
     float *s_hi = nullptr, *s_lo = nullptr, *s_ovf = nullptr;
     float *dbg_T = nullptr, *dbg_wsum = nullptr;
     int32_t *dbg_count = nullptr;
@@ -217,7 +227,8 @@ struct slag_ctx {
     int32_t *qcount = nullptr;
     int64_t qout_cap = 0;
 
-    SortScratch scratch;
+    SortScratch scratch;                     // stage A, finalize, queries (caller's or front stream)
+    SortScratch scratch_b;                   // stage B (its own stream)
     slag_stats stats{};
 
     // per-stage timing
@@ -377,17 +388,21 @@ void spans_resolve(slag_ctx *ctx, bool all = true) {
     (void)cudaGetLastError();   // clears cudaErrorNotReady left by the queries
 }
 
-// The caller's stream waits for every view in flight and for the front stream.
+// The caller's stream waits for every view in flight and for both front streams.
 cudaError_t join_views(slag_ctx *ctx) {
     cudaError_t e = cudaEventRecord(ctx->ev_front, ctx->front);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_front, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_front_b, ctx->front_b);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_front_b, 0);
     for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->stream, ctx->slot[i].ev_done, 0);
     return e;
 }
 
-// Host waits for every internal stream (the caller's stream is not waited for).
+// Host waits for every internal stream of the views (the caller's stream is not waited for).
 cudaError_t drain_views(slag_ctx *ctx) {
     cudaError_t e = cudaStreamSynchronize(ctx->front);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->front_b);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->up);
     for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaStreamSynchronize(ctx->slot[i].back);
     return e;
 }
@@ -403,33 +418,35 @@ int ceil_log2(uint64_t v) {
 // in the slot; returns the pair count in *P_out and the list buffer in
 // *list_out. The host waits for `st` once (pair count, error flags) and
 // copies the log's fill level of that moment into vs.h->totals.
-slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int64_t *P_out,
-                     uint32_t **keys_out, uint32_t **list_out, const int32_t *seg_check, int32_t M,
-                     const uint32_t **sgid_out, int shift, cudaEvent_t seg_ready = nullptr) {
+// Stage A of a view: projection, depth sort, depth-rank gather and the scan of the
+// per-Gaussian tile counts (Method: the rasterizer's per-view preprocessing). Reads neither
+// the segment map nor the table. The counters and the log's fill level are copied to the
+// slot's mapped host struct; the host reads them once the stage has ended.
+slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int shift) {
     const int64_t n = ctx->n;
     CK(cudaMemsetAsync(vs.ctr, 0, sizeof(ViewCounters), st));
     span_begin(ctx, SLAG_STAGE_PROJECT, st);
     launch_project(cp, ctx->mean_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, vs.dkey[0], vs.dval[0],
                    vs.rec_a, vs.rec_b, vs.rect, vs.ctr, st);
     int shifts[8], widths[8];
-    int np = digit_passes(0, 32, shifts, widths, n);
-    bool alt = radix_sort_u32(vs.dkey[0], vs.dkey[1], vs.dval[0], vs.dval[1], n, shifts, widths, np,
-                              ctx->scratch, st);
-    const uint32_t *sorted_vals = vs.dval[alt ? 1 : 0];
-    *sgid_out = sorted_vals;
-    launch_gather_sorted(sorted_vals, n, vs.ctr, vs.rec_a, vs.rec_b, vs.rect, vs.srec_a, vs.srec_b,
-                         vs.srect, vs.stouched, shift, st);
+    const int np = digit_passes(0, 32, shifts, widths, n);
+    const bool alt = radix_sort_u32(vs.dkey[0], vs.dkey[1], vs.dval[0], vs.dval[1], n, shifts, widths, np,
+                                    ctx->scratch, st);
+    vs.sgid = vs.dval[alt ? 1 : 0];
+    launch_gather_sorted(vs.sgid, n, vs.ctr, vs.rec_a, vs.rec_b, vs.rect, vs.srec_a, vs.srec_b, vs.srect,
+                         vs.stouched, shift, st);
     exclusive_scan_u32(vs.stouched, vs.offsets, n, &vs.ctr->P, ctx->scratch, st);
-    // the segment map arrives on the upload stream while the above runs
-    if (seg_ready) CK(cudaStreamWaitEvent(st, seg_ready, 0));
-    if (seg_check) launch_check_seg(seg_check, (int64_t)cp.width * cp.height, M, vs.ctr, st);
     span_end(ctx, st);
     launch_copy_words(vs.ctr, &vs.h_dev->v, sizeof(ViewCounters), st);
     launch_copy_words(ctx->totals, vs.h_dev->totals, 4 * sizeof(unsigned long long), st);
-    CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
-    spans_resolve(ctx, false);
-    if (vs.h->v.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
+    return SLAG_OK;
+}
+
+// Stage B, once stage A's counters are on the host: pair emission, the stable sort of the
+// pairs by bin (tile or super-tile), bin ranges and the tile order; sorts with `scr`.
+slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int shift,
+                    SortScratch &scr, int64_t *P_out, uint32_t **keys_out, uint32_t **list_out) {
     const int64_t P = (int64_t)vs.h->v.P;   // pairs at the binning granularity
     if (P > 0x7fffffffLL || vs.h->v.P_tiles > 0x7fffffffULL)
         return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^31-1 Gaussian-tile pairs in one view");
@@ -441,27 +458,27 @@ slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamPara
             CK(grow(vs.pval[b], c2, P, st));
             vs.p_cap = c1;
         }
-        CK(scratch_reserve(ctx->scratch, vs.p_cap));
     }
+    CK(scratch_reserve(scr, vs.p_cap));
     const int bins_x = ((cp.tiles_x - 1) >> shift) + 1, bins_y = ((cp.tiles_y - 1) >> shift) + 1;
     const int64_t bins = (int64_t)bins_x * bins_y;
     const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
     CK(grow(vs.ranges, vs.ranges_cap, bins, st));
-    uint32_t nv = vs.h->v.n_visible;
+    const uint32_t nv = vs.h->v.n_visible;
     span_begin(ctx, SLAG_STAGE_BIN, st);
     launch_emit(vs.srect, vs.offsets, nv, shift, bins_x, vs.pkey[0], vs.pval[0], st);
-    np = digit_passes(0, ceil_log2((uint64_t)bins), shifts, widths, P);
+    int shifts[8], widths[8];
+    const int np = digit_passes(0, ceil_log2((uint64_t)bins), shifts, widths, P);
     uint32_t *keys = vs.pkey[0];
-    alt = false;
+    bool alt = false;
     if (P > 0 && np == 1) {
         // one pass: its digit is the bin id, and the pass's offsets give the ranges
-        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np,
-                             ctx->scratch, st, vs.ranges, (int)bins);
+        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr, st,
+                             vs.ranges, (int)bins);
         keys = vs.pkey[alt ? 1 : 0];
     } else {
         CK(cudaMemsetAsync(vs.ranges, 0, sizeof(uint2) * (size_t)bins, st));
-        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np,
-                             ctx->scratch, st);
+        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr, st);
         keys = vs.pkey[alt ? 1 : 0];
         launch_ranges(keys, P, vs.ranges, st);
     }
@@ -472,10 +489,23 @@ slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamPara
         launch_pair_rects(vs.pval[alt ? 1 : 0], P, vs.srect, vs.prect, st);
     }
     span_end(ctx, st);
+    CK(cudaGetLastError());
     *P_out = P;
     *keys_out = keys;
     *list_out = vs.pval[alt ? 1 : 0];
     return SLAG_OK;
+}
+
+// Both stages in one stream with a host sync between them (the diagnostic entry points).
+slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int64_t *P_out,
+                     uint32_t **keys_out, uint32_t **list_out, const uint32_t **sgid_out, int shift) {
+    slag_status s = stage_a(ctx, vs, st, cp, shift);
+    if (s != SLAG_OK) return s;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    spans_resolve(ctx, false);
+    *sgid_out = vs.sgid;
+    return stage_b(ctx, vs, st, cp, shift, ctx->scratch, P_out, keys_out, list_out);
 }
 
 cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
@@ -487,12 +517,15 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
     SA(dalloc(&vs.stouched, n)); SA(dalloc(&vs.offsets, n));
     SA(dalloc(&vs.hash, n));
     SA(dalloc(&vs.ctr, 1));
+    SA(dalloc(&vs.ctr_up, 1));
     SA(dalloc(&vs.rec_count, 1));
     SA(cudaHostAlloc((void **)&vs.h, sizeof(ViewSlot::Host), cudaHostAllocMapped));
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&vs.h_dev, vs.h, 0);
     int lo = 0, hi = 0;
     SA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     SA(cudaStreamCreateWithPriority(&vs.back, cudaStreamNonBlocking, lo));
+    SA(cudaEventCreateWithFlags(&vs.ev_a, cudaEventDisableTiming));
+    SA(cudaEventCreateWithFlags(&vs.ev_up, cudaEventDisableTiming));
     SA(cudaEventCreateWithFlags(&vs.ev_bin, cudaEventDisableTiming));
     SA(cudaEventCreateWithFlags(&vs.ev_done, cudaEventDisableTiming));
 #undef SA
@@ -505,13 +538,15 @@ void slot_free(ViewSlot &vs) {
     dfree(vs.rec_a); dfree(vs.rec_b); dfree(vs.srec_a); dfree(vs.srec_b); dfree(vs.rect); dfree(vs.srect);
     dfree(vs.stouched); dfree(vs.offsets); dfree(vs.hash);
     dfree(vs.prect); dfree(vs.ranges); dfree(vs.tile_order); dfree(vs.seg_buf); dfree(vs.ctr);
-    dfree(vs.recs); dfree(vs.rec_count);
+    dfree(vs.ctr_up); dfree(vs.recs); dfree(vs.rec_count);
     if (vs.h) cudaFreeHost(vs.h);
     vs.h = nullptr;
     if (vs.back) cudaStreamDestroy(vs.back);
-    if (vs.ev_bin) cudaEventDestroy(vs.ev_bin);
-    if (vs.ev_done) cudaEventDestroy(vs.ev_done);
-    vs.back = nullptr; vs.ev_bin = vs.ev_done = nullptr;
+    for (cudaEvent_t *e : {&vs.ev_a, &vs.ev_up, &vs.ev_bin, &vs.ev_done}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+    }
+    vs.back = nullptr;
 }
 
 // issues pieces of a pending asynchronous download (defined with the finalize helpers)
@@ -577,11 +612,14 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
         int lo = 0, hi = 0;
         CA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         CA(cudaStreamCreateWithPriority(&ctx->front, cudaStreamNonBlocking, hi));
+        CA(cudaStreamCreateWithPriority(&ctx->front_b, cudaStreamNonBlocking, hi));
+        // the segment-id check runs here and slag_add_view waits for it: it must not queue
+        // behind the composites' CTAs
+        CA(cudaStreamCreateWithPriority(&ctx->up, cudaStreamNonBlocking, hi));
     }
     CA(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
-    CA(cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking));
-    CA(cudaEventCreateWithFlags(&ctx->ev_up, cudaEventDisableTiming));
     CA(cudaEventCreateWithFlags(&ctx->ev_front, cudaEventDisableTiming));
+    CA(cudaEventCreateWithFlags(&ctx->ev_front_b, cudaEventDisableTiming));
     CA(cudaEventCreateWithFlags(&ctx->ev_consumed, cudaEventDisableTiming));
     CA(cudaStreamCreateWithFlags(&ctx->qstream, cudaStreamNonBlocking));
     CA(cudaEventCreateWithFlags(&ctx->qev_in, cudaEventDisableTiming));
@@ -596,6 +634,7 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     CA(cudaMemsetAsync(vctr, 0, sizeof(ViewCounters), st));
     CA(cudaMemsetAsync(ctx->totals, 0, 4 * sizeof(unsigned long long), st));
     CA(scratch_reserve(ctx->scratch, n));
+    CA(scratch_reserve(ctx->scratch_b, n));
 
     // validation
     launch_check_gaussians(im, is, iq, io, n, &vctr->bad_seg, st);
@@ -639,72 +678,34 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     return SLAG_OK;
 }
 
-slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *seg_ids, const float *seg_table,
-                          int32_t M, int32_t on_device) {
-    if (!ctx) return SLAG_ERR_INVALID_ARG;
-    slag_status s = check_camera(ctx, cam);
-    if (s != SLAG_OK) return s;
-    if (!seg_ids || !seg_table) return fail(ctx, SLAG_ERR_INVALID_ARG, "seg_ids / seg_table is NULL");
-    if (M < 1 || M >= (1 << 24)) return fail(ctx, SLAG_ERR_INVALID_ARG, "M outside [1, 2^24)");
-    if (ctx->table_rows + M >= (1LL << 32)) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^32 segment columns");
-    CK(cudaSetDevice(ctx->device));
-    ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
-    cudaStream_t fr = ctx->front;
-    const CamParams cp = cam_params(cam);
-    const int64_t npx = (int64_t)cam->width * cam->height;
-    const int64_t D = ctx->D;
+}  // extern "C"
 
-    // the front stream starts after the caller's work so far (inputs written
-    // on the caller's stream) and after the slot's previous view has been
-    // composited and consumed
-    // latent form: the segment embeddings are encoded to 32-d codes at finalize, all views' rows
-    // in one pass (the codes are only read there)
-    if (ctx->precision == SLAG_PREC_LATENT32 && !ctx->lat_params)
-        return fail(ctx, SLAG_ERR_STATE, "latent form: slag_set_latent before the first view");
-    CK(cudaEventRecord(ctx->ev_in, ctx->stream));
-    CK(cudaStreamWaitEvent(fr, ctx->ev_in, 0));
-    CK(cudaStreamWaitEvent(fr, vs.ev_done, 0));
-    CK(cudaStreamWaitEvent(ctx->up, ctx->ev_in, 0));
-    CK(cudaStreamWaitEvent(ctx->up, vs.ev_done, 0));
+namespace {
 
-    // segment embeddings -> rows [table_rows, table_rows + M) of the column store;
-    // the segment map -> the slot. Both copies run on the upload stream while the front
-    // stream projects, sorts and bins (which do not read them); the front stream waits for
-    // them before the segment check, ahead of the host sync below, so the caller's buffers
-    // are free when this call returns.
-    if (ctx->table_rows + M > ctx->table_cap / D) {
-        CK(drain_views(ctx));   // growing frees the old store
-        CK(cudaStreamSynchronize(ctx->up));
-        CK(grow(ctx->table, ctx->table_cap, (ctx->table_rows + M) * D, fr, ctx->table_rows * D));
-    }
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D), kind, ctx->up));
-    if (npx > vs.seg_cap) {
-        CK(cudaStreamSynchronize(ctx->up));
-        CK(grow(vs.seg_buf, vs.seg_cap, npx, fr));
-    }
-    CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, ctx->up));
-    CK(cudaEventRecord(ctx->ev_up, ctx->up));
-    const int32_t *seg = vs.seg_buf;
-    // one piece of an earlier asynchronous finalize's download, queued behind this view's
-    // upload: the two would share the PCIe link, and the front stream waits for the upload
-    if (ctx->pend_left) {
-        CK(cudaStreamWaitEvent(ctx->cstream, ctx->ev_up, 0));
-        s = issue_pending(ctx, 1);
-        if (s != SLAG_OK) return s;
-    }
-
+// The second half of the last accepted view: stage B on its own stream once stage A's counters
+// are on the host, then the composite, the combine pass and the consume pass on the slot's back
+// stream. It runs in the next call (the next view's slag_add_view, or any call that joins the
+// views), so that stage A of the next view is already queued while the host waits for this
+// view's counters: the front streams never idle on a host round trip.
+slag_status launch_deferred_view(slag_ctx *ctx) {
+    if (!ctx->deferred) return SLAG_OK;
+    ctx->deferred = false;
+    ViewSlot &vs = ctx->slot[(ctx->views_enqueued - 1) % kSlots];
+    const CamParams &cp = vs.cp;
+    CK(cudaEventSynchronize(vs.ev_a));
+    CK(cudaGetLastError());
+    spans_resolve(ctx, false);
+    cudaStream_t fb = ctx->front_b;
+    CK(cudaStreamWaitEvent(fb, vs.ev_a, 0));
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
-    const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, vs, fr, cp, &P, &keys, &list, seg, M, &sgid, kSuperShift, ctx->ev_up);
+    slag_status s = stage_b(ctx, vs, fb, cp, kSuperShift, ctx->scratch_b, &P, &keys, &list);
     if (s != SLAG_OK) return s;
-    CK(cudaEventRecord(vs.ev_bin, fr));
+    CK(cudaEventRecord(vs.ev_bin, fb));
 
-    // room in the triple log: its fill level at the front sync, plus what the
-    // other views in flight may still append, plus this view's bound (at most
-    // kHashSlots per Gaussian from the consume pass and the composite's
-    // overflow appends)
+    // room in the triple log: its fill level when stage A ended, plus what the other views in
+    // flight may still append, plus this view's bound (at most kHashSlots per Gaussian from
+    // the consume pass and the composite's overflow appends)
     vs.log_bound = ctx->n * kHashSlots + 2 * (int64_t)vs.h->v.P_tiles + (1 << 20);
     int64_t others = 0;
     for (int i = 0; i < kSlots; ++i)
@@ -714,13 +715,13 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
         // fill level; the new capacity keeps room for a full pipeline of views, so
         // that the next views pass this test without waiting
         CK(drain_views(ctx));
-        launch_copy_words(ctx->totals, vs.h_dev->totals, 4 * sizeof(unsigned long long), fr);
-        CK(cudaStreamSynchronize(fr));
+        launch_copy_words(ctx->totals, vs.h_dev->totals, 4 * sizeof(unsigned long long), fb);
+        CK(cudaStreamSynchronize(fb));
         const int64_t used = (int64_t)vs.h->totals[0];
         const int64_t need = used + others + vs.log_bound;
         int64_t c1 = ctx->log_cap, c2 = ctx->log_cap;
-        CK(grow(ctx->log_key, c1, need, fr, used));
-        CK(grow(ctx->log_w, c2, need, fr, used));
+        CK(grow(ctx->log_key, c1, need, fb, used));
+        CK(grow(ctx->log_w, c2, need, fb, used));
         ctx->log_cap = c1;
     }
 
@@ -728,11 +729,12 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     // non-zero sum (per batch of the tile's CTA); sums beyond the capacity go to the
     // tables directly, so the capacity only bounds the fast path
     const int64_t rec_need = (int64_t)vs.h->v.P_tiles + ctx->n;
-    if (rec_need > vs.rec_cap) CK(grow(vs.recs, vs.rec_cap, rec_need, fr));
+    if (rec_need > vs.rec_cap) CK(grow(vs.recs, vs.rec_cap, rec_need, fb));
 
     // back half on the slot's stream
     cudaStream_t bk = vs.back;
     CK(cudaStreamWaitEvent(bk, vs.ev_bin, 0));
+    CK(cudaStreamWaitEvent(bk, vs.ev_up, 0));   // the segment map
     CK(cudaMemsetAsync(vs.rec_count, 0, sizeof(unsigned long long), bk));
     CompositeArgs a;
     a.cam = cp;
@@ -744,9 +746,9 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     a.prect = vs.prect;
     a.srec_a = vs.srec_a;
     a.srec_b = vs.srec_b;
-    a.sgid = sgid;
-    a.seg = seg;
-    a.view_base = (int32_t)ctx->table_rows;
+    a.sgid = vs.sgid;
+    a.seg = vs.seg_buf;
+    a.view_base = (int32_t)vs.view_base;
     a.weight_mode = ctx->weight_mode;
     a.hash = vs.hash;
     a.log_count = ctx->log_count;
@@ -768,25 +770,99 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     launch_composite(a, bk);
     span_end(ctx, bk);
     const HashSink sink{vs.hash, ctx->log_count, (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
-                        ctx->s_ovf, reinterpret_cast<uint32_t *>(ctx->totals + 2), (int32_t)ctx->table_rows};
+                        ctx->s_ovf, reinterpret_cast<uint32_t *>(ctx->totals + 2), (int32_t)vs.view_base};
     span_begin(ctx, SLAG_STAGE_CONSUME, bk);
     launch_combine(vs.recs, vs.rec_count, (unsigned long long)vs.rec_cap, sink, bk);
     span_end(ctx, bk);
     // consumes in view order: the compensated sums are updated without atomics
     CK(cudaStreamWaitEvent(bk, ctx->ev_consumed, 0));
     span_begin(ctx, SLAG_STAGE_CONSUME, bk);
-    launch_consume(vs.hash, ctx->n, (int32_t)ctx->table_rows, ctx->s_hi, ctx->s_lo, ctx->log_count,
+    launch_consume(vs.hash, ctx->n, (int32_t)vs.view_base, ctx->s_hi, ctx->s_lo, ctx->log_count,
                    (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
                    reinterpret_cast<uint32_t *>(ctx->totals + 2), &vs.ctr->contributions, ctx->contrib, bk);
     span_end(ctx, bk);
     CK(cudaEventRecord(ctx->ev_consumed, bk));
     CK(cudaEventRecord(vs.ev_done, bk));
     CK(cudaGetLastError());
-    ctx->views_enqueued += 1;
-    ctx->table_rows += M;
-    ctx->stats.views += 1;
     ctx->stats.pairs += (int64_t)vs.h->v.P_tiles;
     ctx->stats.last_pairs = (int64_t)vs.h->v.P_tiles;
+    return SLAG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *seg_ids, const float *seg_table,
+                          int32_t M, int32_t on_device) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    slag_status s = check_camera(ctx, cam);
+    if (s != SLAG_OK) return s;
+    if (!seg_ids || !seg_table) return fail(ctx, SLAG_ERR_INVALID_ARG, "seg_ids / seg_table is NULL");
+    if (M < 1 || M >= (1 << 24)) return fail(ctx, SLAG_ERR_INVALID_ARG, "M outside [1, 2^24)");
+    if (ctx->table_rows + M >= (1LL << 32)) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^32 segment columns");
+    CK(cudaSetDevice(ctx->device));
+    // latent form: the segment embeddings are encoded to 32-d codes at finalize, all views' rows
+    // in one pass (the codes are only read there)
+    if (ctx->precision == SLAG_PREC_LATENT32 && !ctx->lat_params)
+        return fail(ctx, SLAG_ERR_STATE, "latent form: slag_set_latent before the first view");
+    ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
+    cudaStream_t fr = ctx->front, up = ctx->up;
+    const CamParams cp = cam_params(cam);
+    const int64_t npx = (int64_t)cam->width * cam->height;
+    const int64_t D = ctx->D;
+
+    // stage A and the uploads start after the caller's work so far (inputs written on the
+    // caller's stream) and after the slot's previous view has been composited and consumed
+    CK(cudaEventRecord(ctx->ev_in, ctx->stream));
+    CK(cudaStreamWaitEvent(fr, ctx->ev_in, 0));
+    CK(cudaStreamWaitEvent(fr, vs.ev_done, 0));
+    CK(cudaStreamWaitEvent(up, ctx->ev_in, 0));
+    CK(cudaStreamWaitEvent(up, vs.ev_done, 0));
+
+    // segment embeddings -> rows [table_rows, table_rows + M) of the column store; the segment
+    // map -> the slot; then the check of its ids. All on the upload stream: stage A does not
+    // read them, and the composite waits for them.
+    if (ctx->table_rows + M > ctx->table_cap / D) {
+        CK(drain_views(ctx));   // growing frees the old store
+        CK(grow(ctx->table, ctx->table_cap, (ctx->table_rows + M) * D, fr, ctx->table_rows * D));
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D), kind, up));
+    if (npx > vs.seg_cap) {
+        CK(cudaStreamSynchronize(up));   // the slot's previous composite has read the old map
+        CK(grow(vs.seg_buf, vs.seg_cap, npx, fr));
+    }
+    CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, up));
+    CK(cudaMemsetAsync(vs.ctr_up, 0, sizeof(ViewCounters), up));
+    launch_check_seg(vs.seg_buf, npx, M, vs.ctr_up, up);
+    launch_copy_words(vs.ctr_up, &vs.h_dev->vu, sizeof(ViewCounters), up);
+    CK(cudaEventRecord(vs.ev_up, up));
+    // one piece of an earlier asynchronous finalize's download, queued behind this view's
+    // upload so that the two do not share the PCIe link
+    if (ctx->pend_left) {
+        CK(cudaStreamWaitEvent(ctx->cstream, vs.ev_up, 0));
+        s = issue_pending(ctx, 1);
+        if (s != SLAG_OK) return s;
+    }
+
+    // stage A of this view, then the previous view's second half
+    s = stage_a(ctx, vs, fr, cp, kSuperShift);
+    if (s != SLAG_OK) return s;
+    CK(cudaEventRecord(vs.ev_a, fr));
+    s = launch_deferred_view(ctx);
+    if (s != SLAG_OK) return s;
+
+    // the caller's buffers are free once the uploads are done; the check's result came with them
+    CK(cudaEventSynchronize(vs.ev_up));
+    CK(cudaGetLastError());
+    if (vs.h->vu.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
+    vs.cp = cp;
+    vs.view_base = ctx->table_rows;
+    ctx->views_enqueued += 1;
+    ctx->table_rows += M;
+    ctx->deferred = true;
+    ctx->stats.views += 1;
     ctx->stats.columns = ctx->table_rows;
     ctx->finalized = false;
     return SLAG_OK;
@@ -803,6 +879,8 @@ slag_status finalize_prepare(slag_ctx *ctx) {
     if (ctx->stats.views == 0) return fail(ctx, SLAG_ERR_STATE, "finalize before any view");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
+    slag_status s0 = launch_deferred_view(ctx);
+    if (s0 != SLAG_OK) return s0;
     CK(join_views(ctx));
     const ViewSlot &last = ctx->slot[(ctx->views_enqueued + kSlots - 1) % kSlots];
     launch_copy_words(ctx->totals, ctx->hc_dev->totals, 4 * sizeof(unsigned long long), st);
@@ -1319,6 +1397,7 @@ slag_status slag_reset(slag_ctx *ctx) {
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->n;
+    ctx->deferred = false;   // the last view's second half is dropped with the rest
     CK(join_views(ctx));
     // a view that failed after its front sync can leave entries in its slot's table
     for (int i = 0; i < kSlots; ++i) {
@@ -1499,14 +1578,17 @@ void slag_destroy(slag_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
     if (ctx->front) cudaStreamSynchronize(ctx->front);
+    if (ctx->front_b) cudaStreamSynchronize(ctx->front_b);
+    if (ctx->up) cudaStreamSynchronize(ctx->up);
     for (int i = 0; i < kSlots; ++i)
         if (ctx->slot[i].back) cudaStreamSynchronize(ctx->slot[i].back);
     for (int i = 0; i < kSlots; ++i) slot_free(ctx->slot[i]);
     if (ctx->front) cudaStreamDestroy(ctx->front);
+    if (ctx->front_b) cudaStreamDestroy(ctx->front_b);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
-    if (ctx->up) { cudaStreamSynchronize(ctx->up); cudaStreamDestroy(ctx->up); }
-    if (ctx->ev_up) cudaEventDestroy(ctx->ev_up);
+    if (ctx->up) cudaStreamDestroy(ctx->up);
     if (ctx->ev_front) cudaEventDestroy(ctx->ev_front);
+    if (ctx->ev_front_b) cudaEventDestroy(ctx->ev_front_b);
     if (ctx->ev_consumed) cudaEventDestroy(ctx->ev_consumed);
     if (ctx->qgraph) cudaGraphExecDestroy(ctx->qgraph);
     if (ctx->qstream) { cudaStreamSynchronize(ctx->qstream); cudaStreamDestroy(ctx->qstream); }
@@ -1530,6 +1612,7 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->ehl); dfree(ctx->qinv); dfree(ctx->qhl);
     dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);
     scratch_free(ctx->scratch);
+    scratch_free(ctx->scratch_b);
     for (auto &sp : ctx->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->prof_base) cudaEventDestroy(ctx->prof_base);
@@ -1564,6 +1647,8 @@ slag_status slag_set_profiling(slag_ctx *ctx, int32_t enable) {
 slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset) {
     if (!ctx || !out) return SLAG_ERR_INVALID_ARG;
     CK(cudaSetDevice(ctx->device));
+    slag_status s0 = launch_deferred_view(ctx);
+    if (s0 != SLAG_OK) return s0;
     CK(cudaStreamSynchronize(ctx->stream));
     CK(drain_views(ctx));
     spans_resolve(ctx);
@@ -1600,13 +1685,15 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
     if (s != SLAG_OK) return s;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
+    s = launch_deferred_view(ctx);
+    if (s != SLAG_OK) return s;
     CK(join_views(ctx));
     ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
     const CamParams cp = cam_params(cam);
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, nullptr, 0, &sgid, 0);
+    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, &sgid, 0);
     if (s != SLAG_OK) return s;
     if (out_P) *out_P = P;
     const int64_t n = ctx->n;
@@ -1670,6 +1757,8 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     if (s != SLAG_OK) return s;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
+    s = launch_deferred_view(ctx);
+    if (s != SLAG_OK) return s;
     CK(join_views(ctx));
     ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
     const CamParams cp = cam_params(cam);
@@ -1677,7 +1766,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, nullptr, 0, &sgid, kSuperShift);
+    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, &sgid, kSuperShift);
     if (s != SLAG_OK) return s;
     if (npx > ctx->dbg_cap) {
         int64_t c1 = ctx->dbg_cap, c2 = ctx->dbg_cap, c3 = ctx->dbg_cap;

@@ -1,0 +1,132 @@
+"""The two halves of slag_add_view.
+
+A view's first half (uploads, segment-id check, projection, depth sort, tile-count scan) is
+queued by its own slag_add_view; its second half (pair emission, bin sort, compositing,
+masking, reduction) by the next call on the context. These tests check that every way of
+ending a view's wait gives the result of the plain sequence, up to the float32 summation order
+of the weight atomics:
+- calls between views (diagnostics, profiles);
+- a rejected view after an accepted one;
+- slag_reset with a view still waiting;
+- the caller's input buffers reused as soon as slag_add_view returns (host and device)."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def slag():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2505_08124_b300 import build
+    build.build()
+    from paper_2505_08124_b300 import slag as S
+    S.load_library()
+    return S
+
+
+@pytest.fixture(scope="module")
+def scene():
+    s = synth.small_scene(43, 6000, 9, 176, 120, 8, dim=128, surfaces=4)
+    return s, list(s.views())
+
+
+def _plain(slag, s, views):
+    with slag.Lifter(s.gaussians, dim=128) as L:
+        for v in views:
+            L.add_view(v.camera, v.seg, v.table)
+        E, w = L.finalize()
+        return E, w, L.stats()
+
+
+def _close(a, b):
+    (E, w), (Er, wr) = a, b
+    np.testing.assert_allclose(E, Er, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(w, wr, rtol=1e-5, atol=1e-7)
+
+
+def test_calls_between_views(slag, scene):
+    s, views = scene
+    Er, wr, st_r = _plain(slag, s, views)
+    with slag.Lifter(s.gaussians, dim=128) as L:
+        L.set_profiling(True)
+        for i, v in enumerate(views):
+            L.add_view(v.camera, v.seg, v.table)
+            if i == 1:
+                L.render_debug(views[5].camera)
+            elif i == 3:
+                L.bin_view(views[0].camera)
+            elif i == 4:
+                prof = L.profile()
+                assert prof["composite"][1] == 5   # the second halves of views 0..4 are queued
+        E, w = L.finalize()
+        st = L.stats()
+    _close((E, w), (Er, wr))
+    for k in ("views", "pairs", "columns", "triples"):
+        assert st[k] == st_r[k], k
+
+
+def test_rejected_view_after_accepted(slag, scene):
+    s, views = scene
+    Er, wr, _ = _plain(slag, s, [views[0], views[2]])
+    bad = views[1].seg.copy()
+    bad[7, 11] = views[1].m
+    with slag.Lifter(s.gaussians, dim=128) as L:
+        L.add_view(views[0].camera, views[0].seg, views[0].table)
+        with pytest.raises(slag.SlagError) as e:
+            L.add_view(views[1].camera, bad, views[1].table)
+        assert e.value.status == slag.ERR_INVALID_ARG
+        L.add_view(views[2].camera, views[2].seg, views[2].table)
+        E, w = L.finalize()
+        assert L.stats()["views"] == 2
+    _close((E, w), (Er, wr))
+
+
+def test_reset_drops_waiting_view(slag, scene):
+    s, views = scene
+    Er, wr, _ = _plain(slag, s, [views[3], views[4]])
+    with slag.Lifter(s.gaussians, dim=128) as L:
+        for v in views[:3]:
+            L.add_view(v.camera, v.seg, v.table)
+        L.reset()
+        L.add_view(views[3].camera, views[3].seg, views[3].table)
+        L.add_view(views[4].camera, views[4].seg, views[4].table)
+        E, w = L.finalize()
+        assert L.stats()["views"] == 2
+    _close((E, w), (Er, wr))
+
+
+def test_input_buffers_free_on_return(slag, scene):
+    import torch
+    s, views = scene
+    Er, wr, _ = _plain(slag, s, views)
+    H, W = views[0].seg.shape
+    M = max(v.m for v in views)
+    # one pinned host buffer pair and one device buffer pair, rewritten for every view; the
+    # device buffers are rewritten on the caller's stream right after the call returns
+    h_seg = torch.empty((H, W), dtype=torch.int32).pin_memory().numpy()
+    h_tab = torch.empty((M, 128), dtype=torch.float32).pin_memory().numpy()
+    d_seg = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    d_tab = torch.empty((M, 128), dtype=torch.float32, device="cuda")
+    junk = np.full((H, W), -1, np.int32)
+    for device in (False, True):
+        with slag.Lifter(s.gaussians, dim=128, stream=torch.cuda.current_stream().cuda_stream) as L:
+            for v in views:
+                if device:
+                    d_seg.copy_(torch.from_numpy(v.seg))
+                    d_tab[:v.m].copy_(torch.from_numpy(v.table))
+                    L.add_view(v.camera, d_seg, d_tab[:v.m])
+                    d_seg.fill_(-1)
+                    d_tab.fill_(7.0)
+                else:
+                    h_seg[:] = v.seg
+                    h_tab[:v.m] = v.table
+                    L.add_view(v.camera, h_seg, h_tab[:v.m])
+                    h_seg[:] = junk
+                    h_tab[:] = 7.0
+            E, w = L.finalize()
+        _close((E, w), (Er, wr))
