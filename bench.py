@@ -516,8 +516,9 @@ def _batched_view(job):
 
 def run_batched(a):
     """16 independent uneven scenes (config_batched, seed 3), their first `views` views each:
-    every scene lifted on its own in turn, against all scenes in one slag_add_views_batched call
-    (round-robin); both with device-resident inputs, finalize included, no queries."""
+    every scene lifted on its own in turn (its views, then its finalize), against all scenes in
+    one slag_add_views_batched call and then every finalize; both with device-resident inputs, no
+    queries."""
     import concurrent.futures as cf
     import multiprocessing as mp
     import synth

@@ -270,11 +270,12 @@ typedef struct {
 } slag_view;
 
 /* Adds views to several independent scenes (one context each) in one call:
- * views[c][0 .. n_views[c]) go to ctxs[c], taken round-robin by view index
- * (view 0 of every scene, then view 1, ...), so that each scene's pipeline
- * has views in flight while the host waits on another's. The result of each
- * context is that of adding its views in order with slag_add_view. Stops at
- * the first error; *failed_ctx (nullable) receives its context index, or -1. */
+ * views[c][0 .. n_views[c]) go to ctxs[c], scene after scene. After a scene's
+ * last view the call also queues that view's second half (see slag_add_view),
+ * so the scene's work runs while the next scene's views are added, with no
+ * finalize in between to drain the GPU. The result of each context is that of
+ * adding its views in order with slag_add_view. Stops at the first error;
+ * *failed_ctx (nullable) receives its context index, or -1. */
 slag_status slag_add_views_batched(int32_t n_ctx, slag_ctx *const *ctxs, const slag_view *const *views,
                                    const int32_t *n_views, int32_t *failed_ctx);
 

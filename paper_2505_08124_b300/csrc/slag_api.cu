@@ -1535,24 +1535,30 @@ slag_status slag_add_views_batched(int32_t n_ctx, slag_ctx *const *ctxs, const s
                                    const int32_t *n_views, int32_t *failed_ctx) {
     if (failed_ctx) *failed_ctx = -1;
     if (n_ctx < 0 || (n_ctx > 0 && (!ctxs || !views || !n_views))) return SLAG_ERR_INVALID_ARG;
-    int32_t most = 0;
     for (int32_t c = 0; c < n_ctx; ++c) {
         if (!ctxs[c] || n_views[c] < 0 || (n_views[c] > 0 && !views[c])) {
             if (failed_ctx) *failed_ctx = c;
             return SLAG_ERR_INVALID_ARG;
         }
-        most = std::max(most, n_views[c]);
     }
-    for (int32_t v = 0; v < most; ++v)
-        for (int32_t c = 0; c < n_ctx; ++c) {
-            if (v >= n_views[c]) continue;
+    // scene after scene: each context's own pipeline keeps the GPU busy, and its last view's
+    // second half is queued before the next scene starts
+    for (int32_t c = 0; c < n_ctx; ++c) {
+        slag_status s = SLAG_OK;
+        for (int32_t v = 0; v < n_views[c] && s == SLAG_OK; ++v) {
             const slag_view &w = views[c][v];
-            const slag_status s = slag_add_view(ctxs[c], w.camera, w.seg_ids, w.seg_table, w.M, w.on_device);
-            if (s != SLAG_OK) {
-                if (failed_ctx) *failed_ctx = c;
-                return s;
-            }
+            s = slag_add_view(ctxs[c], w.camera, w.seg_ids, w.seg_table, w.M, w.on_device);
         }
+        if (s == SLAG_OK && n_views[c] > 0) {
+            slag_ctx *ctx = ctxs[c];
+            if (cudaSetDevice(ctx->device) != cudaSuccess) s = fail(ctx, SLAG_ERR_CUDA, "cudaSetDevice");
+            else s = launch_deferred_view(ctx);
+        }
+        if (s != SLAG_OK) {
+            if (failed_ctx) *failed_ctx = c;
+            return s;
+        }
+    }
     return SLAG_OK;
 }
 

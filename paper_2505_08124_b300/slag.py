@@ -426,7 +426,7 @@ def latent_apply(params, X, mode: int):
 
 def add_views_batched(lifters, view_lists):
     """Adds view_lists[i] (lists of (camera, seg_ids, table) with host numpy or CUDA torch arrays)
-    to lifters[i], interleaved round-robin across the scenes (slag_add_views_batched)."""
+    to lifters[i], scene after scene, in one call (slag_add_views_batched)."""
     lib = load_library()
     keep = []
     arrays = []

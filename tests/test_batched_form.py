@@ -1,8 +1,9 @@
 """The batched form: several independent scenes in one call, and the query
 path's autotuned split and CUDA-graph replay.
 
-slag_add_views_batched interleaves the scenes' views round-robin; each
-scene's result must be that of adding its views alone. Device-side queries
+slag_add_views_batched adds the scenes one after another and queues each
+scene's last second half before the next; each scene's result must be that of
+adding its views alone. Device-side queries
 replay a captured CUDA graph and must return what a fresh launch returns,
 also after the embeddings change (a new finalize), and with the autotuner on
 or off."""
