@@ -113,6 +113,10 @@ typedef struct {
     void *cuda_stream;       /* cudaStream_t, NULL = legacy default stream */
 } slag_options;
 
+/* Counters of the views added since create / reset. views and columns count
+ * every accepted view; pairs and last_pairs count the views whose second half
+ * is queued (all of them after a finalize); contributions, triples,
+ * last_contributions and evaluations are read at finalize. */
 typedef struct {
     int64_t views;           /* views added since create / reset */
     int64_t pairs;           /* sum over views of Gaussian-tile pairs P */
