@@ -1399,7 +1399,7 @@ slag_status slag_reset(slag_ctx *ctx) {
     const int64_t n = ctx->n;
     ctx->deferred = false;   // the last view's second half is dropped with the rest
     CK(join_views(ctx));
-    // a view that failed after its front sync can leave entries in its slot's table
+    // a view that failed after its first half can leave entries in its slot's table
     for (int i = 0; i < kSlots; ++i) {
         launch_hash_init(ctx->slot[i].hash, n, st);
         CK(cudaMemsetAsync(ctx->slot[i].ctr, 0, sizeof(ViewCounters), st));
