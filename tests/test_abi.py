@@ -73,3 +73,33 @@ def test_missing_library_fails_loudly(tmp_path):
             slag.load_library(str(tmp_path / "nope.so"))
     finally:
         slag._lib = saved
+
+
+def test_null_arguments_rejected_without_a_gpu(lib):
+    # every entry point checks its context and pointers before any CUDA call, so a NULL context
+    # or missing output is INVALID_ARG on any machine, GPU or not
+    from paper_2505_08124_b300 import slag as S
+    I = S.ERR_INVALID_ARG
+    assert lib.slag_add_view(None, None, None, None, 4, 0) == I
+    assert lib.slag_finalize(None, None, None, 0) == I
+    assert lib.slag_finalize_async(None, None, None, 0) == I
+    assert lib.slag_wait_outputs(None) == I
+    assert lib.slag_query(None, None, 10, None, None, None) == I
+    assert lib.slag_query_batch(None, None, 1, 10, None, None, None, 0) == I
+    assert lib.slag_reset(None) == I
+    assert lib.slag_get_stats(None, None) == I
+    assert lib.slag_bin_view(None, None, None, None, None, 0, None) == I
+    assert lib.slag_render_debug(None, None, None, None, None) == I
+    assert lib.slag_set_profiling(None, 1) == I
+    assert lib.slag_set_profiling_stages(None, 4) == I
+    assert lib.slag_get_profile(None, None, 0) == I
+    assert lib.slag_export_partitions(None, b"x", 1, 1, 0, None) == I
+    assert lib.slag_set_latent(None, None) == I
+    assert lib.slag_set_autotune(None, 1) == I
+    assert lib.slag_add_views_batched(-1, None, None, None, None) == I
+    assert lib.slag_noalloc_query_topk(None, 10, 128, None, None, 1, 10, None, None, None, None) == I
+    out = ctypes.c_void_p(1)
+    assert lib.slag_create(None, None, ctypes.byref(out)) == I and out.value is None
+    assert lib.slag_create(None, None, None) == I
+    assert lib.slag_last_error(None) == b"no context"
+    lib.slag_destroy(None)   # a no-op
