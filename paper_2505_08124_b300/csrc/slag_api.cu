@@ -828,30 +828,38 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
         CK(grow(ctx->table, ctx->table_cap, (ctx->table_rows + M) * D, fr, ctx->table_rows * D));
     }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D), kind, up));
-    if (npx > vs.seg_cap) {
-        CK(cudaStreamSynchronize(up));   // the slot's previous composite has read the old map
-        CK(grow(vs.seg_buf, vs.seg_cap, npx, fr));
+    // everything from the first copy on; on an error the call still waits for the upload stream
+    // before it returns, since the caller may free its buffers once the call returns
+    auto queue_view = [&]() -> slag_status {
+        CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, seg_table, sizeof(float) * (size_t)(M * D), kind,
+                           up));
+        if (npx > vs.seg_cap) {
+            CK(cudaStreamSynchronize(up));   // the slot's previous composite has read the old map
+            CK(grow(vs.seg_buf, vs.seg_cap, npx, fr));
+        }
+        CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, up));
+        CK(cudaMemsetAsync(vs.ctr_up, 0, sizeof(ViewCounters), up));
+        launch_check_seg(vs.seg_buf, npx, M, vs.ctr_up, up);
+        launch_copy_words(vs.ctr_up, &vs.h_dev->vu, sizeof(ViewCounters), up);
+        CK(cudaEventRecord(vs.ev_up, up));
+        // one piece of an earlier asynchronous finalize's download, queued behind this view's
+        // upload so that the two do not share the PCIe link
+        if (ctx->pend_left) {
+            CK(cudaStreamWaitEvent(ctx->cstream, vs.ev_up, 0));
+            const slag_status sp = issue_pending(ctx, 1);
+            if (sp != SLAG_OK) return sp;
+        }
+        // stage A of this view, then the previous view's second half
+        const slag_status sa = stage_a(ctx, vs, fr, cp, kSuperShift);
+        if (sa != SLAG_OK) return sa;
+        CK(cudaEventRecord(vs.ev_a, fr));
+        return launch_deferred_view(ctx);
+    };
+    s = queue_view();
+    if (s != SLAG_OK) {
+        cudaStreamSynchronize(up);
+        return s;
     }
-    CK(cudaMemcpyAsync(vs.seg_buf, seg_ids, sizeof(int32_t) * (size_t)npx, kind, up));
-    CK(cudaMemsetAsync(vs.ctr_up, 0, sizeof(ViewCounters), up));
-    launch_check_seg(vs.seg_buf, npx, M, vs.ctr_up, up);
-    launch_copy_words(vs.ctr_up, &vs.h_dev->vu, sizeof(ViewCounters), up);
-    CK(cudaEventRecord(vs.ev_up, up));
-    // one piece of an earlier asynchronous finalize's download, queued behind this view's
-    // upload so that the two do not share the PCIe link
-    if (ctx->pend_left) {
-        CK(cudaStreamWaitEvent(ctx->cstream, vs.ev_up, 0));
-        s = issue_pending(ctx, 1);
-        if (s != SLAG_OK) return s;
-    }
-
-    // stage A of this view, then the previous view's second half
-    s = stage_a(ctx, vs, fr, cp, kSuperShift);
-    if (s != SLAG_OK) return s;
-    CK(cudaEventRecord(vs.ev_a, fr));
-    s = launch_deferred_view(ctx);
-    if (s != SLAG_OK) return s;
 
     // the caller's buffers are free once the uploads are done; the check's result came with them
     CK(cudaEventSynchronize(vs.ev_up));
