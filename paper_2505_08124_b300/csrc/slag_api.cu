@@ -1236,9 +1236,18 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
     cudaStream_t st = ctx->stream;
     const int64_t D = ctx->D;
     const float *dQ = Q;
+    // host queries: an error return after the upload is queued still waits for the stream, since
+    // the caller may free or rewrite Q once the call returns
+    struct StreamGuard {
+        cudaStream_t st = nullptr;
+        ~StreamGuard() {
+            if (st) cudaStreamSynchronize(st);
+        }
+    } guard;
     if (!on_device) {
         CK(grow(ctx->qbuf, ctx->qbuf_cap, (int64_t)B * D, st));
         CK(cudaMemcpyAsync(ctx->qbuf, Q, sizeof(float) * (size_t)(B * D), cudaMemcpyHostToDevice, st));
+        guard.st = st;
         dQ = ctx->qbuf;
     }
     if (((uintptr_t)dQ & 15u) != 0) return fail(ctx, SLAG_ERR_INVALID_ARG, "Q must be 16-byte aligned");
@@ -1387,6 +1396,7 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
         launch_copy_words(scores, ctx->qstage_dev + bi, (int64_t)bs, st);
         launch_copy_words(cnt, ctx->qstage_dev + bi + bs, (int64_t)bc, st);
         CK(cudaStreamSynchronize(st));
+        guard.st = nullptr;
         memcpy(out_ids, ctx->qstage, bi);
         memcpy(out_scores, ctx->qstage + bi, bs);
         if (out_count) memcpy(out_count, ctx->qstage + bi + bs, bc);
