@@ -574,8 +574,8 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     uint32_t *bb = nullptr;
     auto free_inputs = [&]() { dfree(dm); dfree(ds); dfree(dq); dfree(dop); dfree(bb); };
     auto bail = [&](slag_status s) {
+        slag_destroy(ctx);   // first: it waits for the stream, where copies from g may be queued
         free_inputs();
-        slag_destroy(ctx);
         return s;
     };
     const int64_t n = g->n;
