@@ -46,3 +46,23 @@ def test_gpu_arm_fails_loudly_without_cuda():
     assert r.returncode != 0
     assert "cuda" in r.stderr.lower() or "nvidia" in r.stderr.lower(), r.stderr[-2000:]
     assert not any(l.strip().startswith("{") for l in r.stdout.splitlines())
+
+
+def test_clock_record_summary():
+    # nvidia-smi lines as the sampler reads them: sm, max sm, power, active mask, then the
+    # hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown and sw_power_cap states
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler("0")
+    c.lines = ["1965, 2032, 700.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "2032, 2032, 650.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "2010, 2032, 690.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+               "not a sample"]
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2010.0 and s["sm_max_mhz"] == 2032.0
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = ["1400, 2032, 900.0, 0x0000000000000008, Active, Not Active, Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
