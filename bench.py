@@ -1,31 +1,48 @@
 #!/usr/bin/env python
 """Benchmark of the lifting path on one B300 (or N replicas under torchrun).
 
-One step = one whole lifting job on the mid-scale workload: 300,000 Gaussians
-on 20 ellipsoid surfaces, 64 views of 960x540 with 64 Voronoi segments each,
-512-d float32 segment embeddings from 32 prototypes (seed 1), through
-slag_reset -> 64 x slag_add_view -> slag_finalize -> 1,000 top-10 cosine
-queries. Inputs are seeded synthetic data of that shape.
+One step = one whole lifting job, through slag_reset -> one slag_add_view per
+view -> slag_finalize -> 1,000 top-10 cosine queries. The default workload is
+the precision configuration at full size: 2,000,000 Gaussians on 60
+ellipsoid surfaces, 300 views of 1920x1080 on a jittered orbit, 128 Voronoi
+segments per view, 512-d segment embeddings from 64 prototypes (seed 2).
+Inputs are seeded synthetic data of that shape (the paper's datasets are not
+available); every view is generated on the host cores before the first CUDA
+call.
 
-Reported:
-  value  Gaussian-pixel contributions per second (whole job, device-resident inputs)
-  e2e    the same through host buffers: per step the segment maps and tables
-         are copied host->device, the embeddings, weight sums and query
-         results device->host, all inside the timed region
-  roofline  the compositing kernel (the largest share of device time): its
-         algorithmic operations over the time at least one composite was
-         running, from CUDA events the library records in the streams that
-         launch it (views in flight overlap, so summed launch spans would
-         count shared time more than once)
-  cpu_baseline  the CPU oracle on a bounded sample of the same workload
+Reported (one JSON line):
+  value     Gaussian-pixel contributions per second of the float32 path (whole
+            job, device-resident inputs); views_per_s beside it
+  e2e       the same job through host buffers: per step the segment maps and
+            tables are copied host->device, the embeddings, weight sums and
+            query results device->host, all inside the timed region
+  roofline  the compositing kernel (the largest share of device time), bound
+            by its arithmetic: executed (Gaussian, pixel) evaluations x the
+            operations of one, over the time at least one composite ran
+  roofline_step_hbm  the whole step against the algorithmic bytes and flops
+            of the method (per view: Gaussians, segment ids, table, sort
+            pairs, records, sparse triples; per step: the output)
+  forms     the BF16 form on the same job, and the latent form on the learned
+            workload (its embeddings follow the mid-scale law the autoencoder
+            is trained on); each with views/s and its error against the float32
+            path of the same job
+  oracle_error  the float32 path and the BF16 form against the float64 oracle
+            on a 10,000-Gaussian subsample of the first 8 views
+  cpu_baseline  the oracle's own time on that sample (per view)
+  mid       the mid-scale workload (300k Gaussians, 64 views 960x540) as a
+            secondary line
 
-`--impl reference` times the CPU oracle alone (the reference arm).
-Under torchrun each rank runs its own replica of the job (weak scaling).
+`--impl reference` times the CPU oracle alone (the reference arm), on bands
+of tile rows of the same views. Under torchrun each rank runs its own replica
+of the job (weak scaling).
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
+import hashlib
 import json
+import multiprocessing as mp
 import os
 import subprocess
 import sys
@@ -39,25 +56,38 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gaussian-pixel contribs/s & views/s, D=512: BF16/latent vs FP32 plain at stated cos err"
 UNIT = "contribs/s"
-WORKLOAD = "plain FP32 mid scale: 300k Gaussians on 20 ellipsoids, 64 views 960x540, 64 segments, D=512, +1000 top-10 queries"
-WORKLOAD_PRECISION = ("precision form at scale (a view subset): 2M Gaussians on 60 ellipsoids, 1920x1080 views, "
-                      "128 segments, D=512, +1000 top-10 queries")
+WORKLOAD_DESC = {
+    "precision": ("precision form at full size: 2,000,000 Gaussians on 60 ellipsoids, 300 views 1920x1080, "
+                  "128 Voronoi segments per view, D=512 from 64 prototypes (seed 2), +1000 top-10 queries"),
+    "mid": ("plain FP32 mid scale: 300,000 Gaussians on 20 ellipsoids, 64 views 960x540, 64 segments, "
+            "D=512 from 32 prototypes (seed 1), +1000 top-10 queries"),
+}
+LEARNED_DESC = ("learned form: 2,000,000 Gaussians on 60 ellipsoids, 300 views 1920x1080, 128 segments, "
+                "embeddings of the mid-scale law (its 32 prototypes), seed 4; autoencoder trained on 1M "
+                "samples of that law")
 
-# Dense FP32 issue rate used as the compositing kernel's ALU roofline: 148 SMs x 128 FP32 lanes
-# x the maximum SM clock, one operation per lane per cycle (most of the work is not FMA).
+# Compositing kernel's arithmetic roofline: 148 SMs x 128 FP32 lanes x the maximum SM clock,
+# x2 where the packed FP32 instructions (f32x2) double the lane rate.
 N_SM = 148
 FP32_LANES = 128
-# FP32 operations per evaluated (Gaussian, pixel) pair in the compositing loop: offsets (2),
-# quadratic form (9), exponent argument check (1), opacity product and cap (2), floor test (1),
-# transmittance update, stop test and weight (3), plus the exp itself on the SFU.
+# FP32 and integer/select operations per executed (Gaussian, pixel) evaluation in the compositing
+# loop: offsets and quadratic form (5 multiply-adds), floor test (1), opacity cap (1),
+# transmittance update and weight (2), stop test (1), selects of T, weight and stop position (3),
+# contribution count (2), the two pixels' weight sum (1) and the record bookkeeping (2); plus one
+# exp2 on the SFU.
 OPS_PER_EVAL = 18
-# DRAM bytes (read + write) per launch of composite_k from one ncu capture on this workload, valid
-# while the kernel source has the recorded SHA-256 (otherwise the roofline reports traffic: null).
-COMPOSITE_TRAFFIC = {"bytes_per_launch": 15660544,   # 15.661 MB read + 0.000 MB written
-                     "source_sha256": "e53356ef3f9b78baf799fae158c4671a5d1a8432248cd791a078f3977f4ac0b7"}
+# DRAM bytes (read + write) per launch of composite_k from one ncu capture, valid while the kernel
+# source has the recorded SHA-256 (otherwise the roofline reports traffic: null).
+COMPOSITE_TRAFFIC = {"bytes_per_launch": None, "source_sha256": None, "workload": None}
+# Nominal TF32 : BF16 dense tensor rate (1.1 : 2.25 PFLOP/s); the float32 path's contraction is a
+# three-term TF32 split (three MMAs per product).
+TF32_OVER_BF16 = 1.1 / 2.25
+TF32_TERMS = 3
+CPU_VIEWS = 8
+CPU_SUBSAMPLE = 10_000
 
 
-def _args():
+def _args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
@@ -66,14 +96,18 @@ def _args():
     p.add_argument("--queries", type=int, default=1000)
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--views", type=int, default=0, help="use only the first V views (0 = all)")
+    p.add_argument("--workload", default="precision", choices=["precision", "mid", "batched"],
+                   help="precision: the headline workload (2M Gaussians, 300 views 1920x1080); mid: 300k "
+                        "Gaussians, 64 views 960x540; batched: 16 uneven scenes, their first --views views each")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-forms", action="store_true", help="skip the BF16 form's line")
-    p.add_argument("--workload", default="mid", choices=["mid", "precision", "batched"],
-                   help="mid: the headline workload; precision: 2M Gaussians at 1920x1080 on a view subset; "
-                        "batched: 16 uneven scenes, their first --views views each (16 by default)")
-    p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=12.0)
-    return p.parse_args()
+    p.add_argument("--no-forms", action="store_true", help="skip the BF16 and latent forms")
+    p.add_argument("--no-mid", action="store_true", help="skip the secondary mid-scale line")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle (cpu_baseline and oracle_error)")
+    p.add_argument("--form-steps", type=int, default=5, help="timed steps of each form (at most --steps)")
+    p.add_argument("--stage-steps", type=int, default=3, help="untimed steps of the per-stage breakdown")
+    p.add_argument("--cpu-views", type=int, default=CPU_VIEWS)
+    p.add_argument("--band-rows", type=int, default=4, help="reference arm: tile rows per view and step")
+    return p.parse_args(argv)
 
 
 def _dist():
@@ -98,31 +132,58 @@ def job_rate(units_per_rank, world_size, seconds):
     return units_per_rank * world_size / seconds
 
 
-def _scene(views_limit=0, workload="mid"):
-    """The bench's scene: the mid-scale workload (default, every view), or the precision
-    configuration on its first `views_limit` views (32 by default)."""
+# ----------------------------------------------------------------------------
+# workloads: scenes and their views, generated on the host cores
+# ----------------------------------------------------------------------------
+
+def make_scene(key):
     import synth
-    if workload == "precision":
-        s = synth.config_precision()
-        views_limit = views_limit or 32
+    if key == "precision":
+        return synth.config_precision()
+    if key == "mid":
+        return synth.config_mid()
+    if key == "learned":
+        return synth.config_learned()
+    if key == "learned_scaled":
+        return synth.config_learned(noise_sigma=0.1 / np.sqrt(512))
+    raise KeyError(key)
+
+
+_WORKER_SCENES = {}
+
+
+def _view_job(job):
+    key, i, table_only = job
+    if key not in _WORKER_SCENES:
+        _WORKER_SCENES[key] = make_scene(key)
+    v = _WORKER_SCENES[key].view(i)
+    return key, i, v.camera, (None if table_only else v.seg), v.table
+
+
+def generate_views(jobs):
+    """{(key, i): (camera, seg or None, table)} for jobs (key, view index, table only), on a
+    spawned process pool (started before any CUDA call)."""
+    if not jobs:
+        return {}
+    workers = max(1, min(32, len(os.sched_getaffinity(0)), len(jobs)))
+    if workers == 1:
+        got = [_view_job(j) for j in jobs]
     else:
-        s = synth.config_mid()
-    nv = s.n_views if not views_limit else min(views_limit, s.n_views)
-    views = [s.view(i) for i in range(nv)]
-    return s, views
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            got = list(ex.map(_view_job, jobs, chunksize=max(1, len(jobs) // (4 * workers))))
+    return {(k, i): (cam, seg, tab) for k, i, cam, seg, tab in got}
 
 
-def _config(a, scene, views, parallelism, l2):
-    v0 = views[0]
-    return {"workload": WORKLOAD_PRECISION if a.workload == "precision" else WORKLOAD,
-            "gaussians": scene.gaussians.n, "views": len(views),
-            "resolution": "%dx%d" % (v0.camera.width, v0.camera.height), "segments": int(v0.table.shape[0]),
+def _config(a, scene, cams, parallelism, l2):
+    c0 = cams[0]
+    return {"workload": WORKLOAD_DESC[a.workload], "gaussians": scene.gaussians.n, "views": len(cams),
+            "resolution": "%dx%d" % (c0.width, c0.height), "segments": int(scene.meta["n_segments"]),
             "dim": scene.dim, "queries": a.queries, "k": a.k, "parallelism": parallelism, "l2": l2}
 
 
-def _queries(views, B, seed=4):
+def _queries(dim, B, seed=4):
     rng = np.random.default_rng(seed)
-    Q = rng.standard_normal((B, views[0].table.shape[1])).astype(np.float32)
+    Q = rng.standard_normal((B, dim)).astype(np.float32)
     Q /= np.linalg.norm(Q, axis=1, keepdims=True)
     return Q
 
@@ -195,50 +256,129 @@ def _device_id(torch, local):
         return str(local)
 
 
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, \
+        "fallback"
+
+
 # ----------------------------------------------------------------------------
-# CPU oracle (baseline and reference arm)
+# roofline arithmetic
 # ----------------------------------------------------------------------------
 
-def _cpu_oracle_sample(scene, views, seconds):
-    """The oracle as it stands on the host cores, on whole views until `seconds` pass."""
+def algorithmic_work(n, dim, cams, segments_per_view, pairs, triples):
+    """The method's bytes and flops for one whole job: per view 44 B per Gaussian in, 4 B per
+    pixel of segment ids, the M x D table, 24 B per Gaussian-tile pair (sort pairs written and
+    read once), 40 B per Gaussian of records (written and read once), 12 B per sparse
+    (Gaussian, view-segment, W) triple; per job the n x (D + 1) float32 output. Flops: 2 D per
+    triple (the contraction of the weights with the segment embeddings)."""
+    V = len(cams)
+    hw = sum(int(c.width) * int(c.height) for c in cams)
+    b = (V * (44 + 40) * n + 4 * hw + 4 * segments_per_view * dim * V + 24 * pairs + 12 * triples
+         + 4 * n * (dim + 1))
+    f = 2 * dim * triples
+    return float(b), float(f)
+
+
+def step_roofline(bytes_alg, flops_alg, ms_per_step, peaks, source):
+    bw = peaks["hbm_gbs"] * 1e9
+    tf = peaks["bf16_tflops"] * 1e12 * TF32_OVER_BF16 / TF32_TERMS
+    t_b, t_f = bytes_alg / bw, flops_alg / tf
+    t = ms_per_step / 1e3
+    bound = "hbm" if t_b >= t_f else "tensor"
+    return {"bound": bound, "achieved": bytes_alg / t / 1e9 if bound == "hbm" else flops_alg / t / 1e12,
+            "peak": peaks["hbm_gbs"] if bound == "hbm" else tf / 1e12,
+            "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": max(t_b, t_f) / t, "traffic": None,
+            "bytes_alg_per_step": bytes_alg, "flops_alg_per_step": flops_alg,
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs; float32 contraction at bf16_tflops x %.3f / %d)"
+                           % (source, TF32_OVER_BF16, TF32_TERMS)}
+
+
+def composite_roofline(executed_per_launch, busy_ms_per_launch, span_ms_per_launch, peaks, source, f32x2=2,
+                       dominant=None, evaluations_per_launch=None):
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    peak = N_SM * FP32_LANES * f32x2 * sm_max * 1e6 / 1e12
+    achieved = executed_per_launch * OPS_PER_EVAL / (busy_ms_per_launch / 1e3) / 1e12
+    traffic = None
+    if COMPOSITE_TRAFFIC["bytes_per_launch"] is not None:
+        src = open(os.path.join(ROOT, "paper_2505_08124_b300", "csrc", "k_composite.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() == COMPOSITE_TRAFFIC["source_sha256"]:
+            traffic = COMPOSITE_TRAFFIC["bytes_per_launch"]
+    return {"kernel": "composite_k", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "T ops/s (fp32 lanes)", "frac": achieved / peak, "traffic": traffic,
+            "executed_evaluations_per_launch": executed_per_launch,
+            "visited_evaluations_per_launch": evaluations_per_launch,
+            "ops_per_evaluation": OPS_PER_EVAL,
+            "busy_ms_per_launch": busy_ms_per_launch, "span_ms_per_launch": span_ms_per_launch,
+            "peak_source": "derived: %d SMs x %d FP32 lanes x %d (packed f32x2) x %.0f MHz (sm_max_mhz, %s)"
+                           % (N_SM, FP32_LANES, f32x2, sm_max, source),
+            "dominant_stage": dominant}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline, error and reference arm)
+# ----------------------------------------------------------------------------
+
+def _cores():
+    return len(os.sched_getaffinity(0))
+
+
+def oracle_subsample(scene, views, sub):
+    """The oracle on whole views for the Gaussians `sub` (every Gaussian still takes part in the
+    compositing), views spread over the host cores; returns (E, den, seconds, info)."""
     from oracle import oracle as O
     O.build()
-    cores = len(os.sched_getaffinity(0))
-    done_views, contrib = 0, 0
+    threads = max(1, min(len(views), _cores()))
     t0 = time.perf_counter()
-    i = 0
-    while i < len(views) and time.perf_counter() - t0 < seconds:
-        batch = views[i:i + cores]
-        _, _, info = O.lift(scene.gaussians, batch, threads=cores)
-        contrib += sum(c for _, c in info)
-        done_views += len(batch)
-        i += len(batch)
+    num, den, info = O.lift(scene.gaussians, views, sub_ids=sub, threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": contrib / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "views_per_s": done_views / dt,
-            "sample": "%d of %d views of the same workload (float64 factored oracle, views spread over %d "
-                      "threads, one accumulator per thread); %.1f s" % (done_views, len(views), cores, dt)}
+    return O.normalise(num, den), den, dt, info, threads
 
 
 def run_reference(a):
+    """The reference arm: the float64 oracle as it stands, on the host cores. Each step is a
+    bounded sample of the workload: a band of a.band_rows tile rows of each of `cores` views
+    (whole rows of the view: each of their pixels gets the whole view's result)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    scene, views = _scene(a.views, a.workload)
-    per_step = []
-    s = None
+    from oracle import oracle as O
+    O.build()
+    scene = make_scene(a.workload)
+    nv = scene.n_views if not a.views else min(a.views, scene.n_views)
+    cores = _cores()
+    per_step = min(cores, nv)
+    views = {}
+    tiles_y = None
+    samples = []
     for it in range(a.warmup + a.steps):
-        s = _cpu_oracle_sample(scene, views, max(2.0, a.cpu_seconds / 4))
+        idx = [(it * per_step + j) % nv for j in range(per_step)]
+        for i in idx:
+            if i not in views:
+                views[i] = scene.view(i)
+        tiles_y = (views[idx[0]].camera.height + 15) // 16
+        rows = min(a.band_rows, tiles_y)
+        ty0 = (it * 7) % max(1, tiles_y - rows + 1)
+        t0 = time.perf_counter()
+        _, _, info = O.lift(scene.gaussians, [views[i] for i in idx], threads=per_step, tile_rows=(ty0, ty0 + rows))
+        dt = time.perf_counter() - t0
         if it >= a.warmup:
-            per_step.append(s)
-    value = float(np.mean([x["value"] for x in per_step]))
-    vps = float(np.mean([x["views_per_s"] for x in per_step]))
+            samples.append((sum(c for _, c in info), dt, ty0, rows))
+    contrib = sum(s[0] for s in samples)
+    secs = sum(s[1] for s in samples)
+    value = contrib / secs
+    rows = samples[0][3]
+    cam = views[0].camera if 0 in views else next(iter(views.values())).camera
+    cfg = _config(a, scene, [cam] * nv, "rank 0 on host cores", "n/a (host)")
+    sample = ("per step, %d views of the %d (threads: one view each), tile rows [r, r + %d) of each (r moves from "
+              "step to step; %d tile rows per view), float64 factored oracle; %d steps, %.1f s"
+              % (per_step, nv, rows, tiles_y, a.steps, secs))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "views_per_s": vps,
-           "config": _config(a, scene, views, "rank 0 on host cores", "n/a (host)"),
-           "cpu_baseline": dict(s, value=value),
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": per_step, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -247,9 +387,130 @@ def run_reference(a):
 # GPU arm
 # ----------------------------------------------------------------------------
 
+class Job:
+    """One scene's inputs on the device (and pinned on the host for the end-to-end leg)."""
+
+    def __init__(self, torch, dev, scene, views, queries, k, pinned=False):
+        self.scene = scene
+        self.cams = [v[0] for v in views]
+        self.d_seg = [torch.from_numpy(v[1]).to(dev) for v in views]
+        self.d_tab = [torch.from_numpy(v[2]).to(dev) for v in views]
+        self.Q = _queries(scene.dim, queries)
+        self.d_Q = torch.from_numpy(self.Q).to(dev)
+        self.k = k
+        n = scene.gaussians.n
+        self.d_ids = torch.empty((queries, k), dtype=torch.int64, device=dev)
+        self.d_sc = torch.empty((queries, k), dtype=torch.float32, device=dev)
+        self.d_cnt = torch.empty(queries, dtype=torch.int32, device=dev)
+        self.d_w = torch.empty(n, dtype=torch.float32, device=dev)
+        self.views = views if pinned else None
+
+    def run(self, L, E_out=None, w_out=None, ids=None):
+        L.reset()
+        for c, sg, tb in zip(self.cams, self.d_seg, self.d_tab):
+            L.add_view(c, sg, tb)
+        L.finalize(E_out, self.d_w if w_out is None else w_out)
+        L.query_batch(self.d_Q, self.k, self.d_ids if ids is None else ids, self.d_sc, self.d_cnt)
+
+
+def _timed(torch, stream, fn, steps, warmup, barrier=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    return e0.elapsed_time(e1)
+
+
+def _compare(torch, E_a, E_f, w_f, ids_a, ids_f, Q, k, tie_eps):
+    """Error of E_a against E_f (1 - cos per Gaussian with sum w >= 1e-3, in row chunks) and the
+    agreement of the two top-k lists (strict overlap; tie-tolerant: an id of ids_a counts when
+    its E_f cosine is within tie_eps of E_f's k-th best)."""
+    n = E_f.shape[0]
+    ok = w_f >= 1e-3
+    mx, tot, cnt = 0.0, 0.0, 0
+    for r0 in range(0, n, 1 << 18):
+        sl = slice(r0, min(n, r0 + (1 << 18)))
+        m = ok[sl]
+        a, b = E_a[sl][m].double(), E_f[sl][m].double()
+        if a.shape[0] == 0:
+            continue
+        c = 1.0 - (a * b).sum(1) / (a.norm(dim=1) * b.norm(dim=1)).clamp_min(1e-300)
+        mx = max(mx, float(c.max().item()))
+        tot += float(c.sum().item())
+        cnt += int(c.shape[0])
+    Qd = Q.double()
+
+    def scores(ids):
+        rows = E_f[ids.clamp_min(0).reshape(-1)].double().reshape(ids.shape[0], ids.shape[1], -1)
+        rows = rows / rows.norm(dim=2, keepdim=True).clamp_min(1e-300)
+        return torch.einsum("qkd,qd->qk", rows, Qd)
+
+    sa, sf = scores(ids_a), scores(ids_f)
+    tie = float((sa >= sf.min(dim=1, keepdim=True).values - tie_eps).double().mean().item())
+    strict = float(np.mean([len(set(x) & set(y)) / k for x, y in zip(ids_a.tolist(), ids_f.tolist())]))
+    return {"cos_err_vs_fp32": {"max": mx, "mean": tot / max(1, cnt), "gaussians": cnt},
+            "top10_agree_vs_fp32": {"tie_tolerant": tie, "tie_eps": tie_eps, "strict": strict}}
+
+
+def run_form(S, torch, dev, stream, job, L_f32, precision, steps, warmup, ws, rank_max, latent=None,
+             tie_eps=1e-3, time_plain=False):
+    """A form on `job`: views/s over `steps` timed steps, and its error against the float32 path
+    of the same job."""
+    n, D = job.scene.gaussians.n, job.scene.dim
+    out = {}
+    Lb = S.Lifter(job.scene.gaussians, dim=D, stream=stream.cuda_stream, precision=precision, latent_params=latent)
+    ms = rank_max(_timed(torch, stream, lambda: job.run(Lb), steps, warmup))
+    contrib = Lb.stats()["contributions"]
+    out.update(value=job_rate(contrib * steps, ws, ms / 1e3), unit=UNIT, ms_per_step=ms / steps,
+               views_per_s=job_rate(len(job.cams) * steps, ws, ms / 1e3))
+    if time_plain:
+        msp = rank_max(_timed(torch, stream, lambda: job.run(L_f32), steps, warmup))
+        out["fp32_same_workload"] = {"ms_per_step": msp / steps,
+                                     "views_per_s": job_rate(len(job.cams) * steps, ws, msp / 1e3)}
+    E_b = torch.empty((n, D), dtype=torch.float32, device=dev)
+    ids_b = torch.empty((job.Q.shape[0], job.k), dtype=torch.int64, device=dev)
+    job.run(Lb, E_b, None, ids_b)
+    torch.cuda.synchronize()
+    Lb.close()
+    E_f = torch.empty((n, D), dtype=torch.float32, device=dev)
+    w_f = torch.empty(n, dtype=torch.float32, device=dev)
+    ids_f = torch.empty_like(ids_b)
+    job.run(L_f32, E_f, w_f, ids_f)
+    torch.cuda.synchronize()
+    out.update(_compare(torch, E_b, E_f, w_f, ids_b, ids_f, job.d_Q, job.k, tie_eps))
+    del E_b, E_f
+    return out
+
+
 def run_slag(a):
-    import torch
     ws, rank, local = _dist()
+    key = a.workload
+    scene = make_scene(key)
+    nv = scene.n_views if not a.views else min(a.views, scene.n_views)
+    # every view generated on the host cores before the first CUDA call
+    jobs = [(key, i, False) for i in range(nv)]
+    want_forms = not a.no_forms and key == "precision"
+    want_mid = not a.no_mid and key == "precision"
+    if want_forms:
+        jobs += [("learned", i, False) for i in range(nv)] + [("learned_scaled", i, True) for i in range(nv)]
+    if want_mid:
+        jobs += [("mid", i, False) for i in range(64)]
+    t_gen = time.perf_counter()
+    got = generate_views(jobs)
+    t_gen = time.perf_counter() - t_gen
+    views = [got[(key, i)] for i in range(nv)]
+
+    import torch
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
@@ -257,49 +518,11 @@ def run_slag(a):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2505_08124_b300 import slag as S
     S.load_library()
-
-    scene, views = _scene(a.views, a.workload)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
     g = scene.gaussians
     D = scene.dim
-    Q = _queries(views, a.queries)
-    stream = torch.cuda.current_stream()
-    dev = torch.device("cuda", local)
-
-    # device-resident inputs
-    d_seg = [torch.from_numpy(v.seg).to(dev) for v in views]
-    d_tab = [torch.from_numpy(v.table).to(dev) for v in views]
-    d_Q = torch.from_numpy(Q).to(dev)
-    d_ids = torch.empty((a.queries, a.k), dtype=torch.int64, device=dev)
-    d_sc = torch.empty((a.queries, a.k), dtype=torch.float32, device=dev)
-    d_cnt = torch.empty(a.queries, dtype=torch.int32, device=dev)
-    d_w = torch.empty(g.n, dtype=torch.float32, device=dev)
-    cams = [v.camera for v in views]
-
-    L = S.Lifter(g, dim=D, stream=stream.cuda_stream)
-
-    def step_device():
-        L.reset()
-        for c, sg, tb in zip(cams, d_seg, d_tab):
-            L.add_view(c, sg, tb)
-        L.finalize(None, d_w)
-        L.query_batch(d_Q, a.k, d_ids, d_sc, d_cnt)
-
-    # host-resident inputs (pinned) for the end-to-end leg
-    h_seg = [torch.from_numpy(v.seg).pin_memory().numpy() for v in views]
-    h_tab = [torch.from_numpy(v.table).pin_memory().numpy() for v in views]
-    h_E = torch.empty((g.n, D), dtype=torch.float32).pin_memory().numpy()
-    h_w = torch.empty(g.n, dtype=torch.float32).pin_memory().numpy()
-    h_Q = torch.from_numpy(Q).pin_memory().numpy()
-
-    def step_host():
-        L.reset()
-        for c, sg, tb in zip(cams, h_seg, h_tab):
-            L.add_view(c, sg, tb)
-        # the download of E and sum w is queued on the library's copy stream and overlaps the
-        # next step; every step's copy is complete before the clock stops (wait_outputs)
-        L.finalize_async(h_E, h_w)
-        ids, sc, cnt = L.query_batch(h_Q, a.k)
-        return ids
+    peaks, peak_source = _peaks()
 
     def barrier():
         torch.cuda.synchronize()
@@ -309,14 +532,15 @@ def run_slag(a):
     def rank_max(x):
         return max_over_ranks(x, dist, dev)
 
+    job = Job(torch, dev, scene, views, a.queries, a.k)
+    L = S.Lifter(g, dim=D, stream=stream.cuda_stream)
+
+    # ---- the headline: float32 path, device-resident inputs ---------------------------
     for _ in range(a.warmup):
-        step_device()
+        job.run(L)
     barrier()
-    # the timed steps record events around the composite launches only (the roofline's
-    # kernel); the other stages' times come from an untimed pass below
-    L.set_profiling(True, stages=("composite",))
+    L.set_profiling(True, stages=("composite",))   # events around the composites only
     L.profile(reset=True)
-    st0 = L.stats()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(_device_id(torch, local)) as clk:
@@ -324,30 +548,44 @@ def run_slag(a):
         n_launch0 = S.kernel_launches()
         e0.record(stream)
         for _ in range(a.steps):
-            step_device()
+            job.run(L)
         e1.record(stream)
         barrier()
         gpu_launches = S.kernel_launches() - n_launch0
     ms = rank_max(e0.elapsed_time(e1))
     prof_timed = L.profile_busy(reset=True)
     L.set_profiling(False)
-    stats = L.stats()
-    # per-stage breakdown: the same steps, untimed, with every stage's spans recorded
+    stats = L.stats()                       # one step's counters (reset() clears them every step)
+    # per-stage breakdown: a few more steps, untimed, with every stage's spans recorded
     L.set_profiling(True)
     L.profile(reset=True)
-    for _ in range(a.steps):
-        step_device()
+    st_steps = max(1, min(a.stage_steps, a.steps))
+    for _ in range(st_steps):
+        job.run(L)
     prof = L.profile_busy(reset=True)
     L.set_profiling(False)
-    contrib_per_step = stats["contributions"]          # reset() clears the counters each step
-    evals_per_step = stats["evaluations"]
-    views_per_step = len(views)
+    contrib_per_step = stats["contributions"]
     value = job_rate(contrib_per_step * a.steps, ws, ms / 1e3)
-    views_per_s = job_rate(views_per_step * a.steps, ws, ms / 1e3)
+    views_per_s = job_rate(nv * a.steps, ws, ms / 1e3)
 
-    # end to end through host buffers
+    # ---- end to end through host buffers --------------------------------------------------
     e2e = None
     if not a.no_e2e:
+        h_seg = [torch.from_numpy(v[1]).pin_memory().numpy() for v in views]
+        h_tab = [torch.from_numpy(v[2]).pin_memory().numpy() for v in views]
+        h_E = torch.empty((g.n, D), dtype=torch.float32).pin_memory().numpy()
+        h_w = torch.empty(g.n, dtype=torch.float32).pin_memory().numpy()
+        h_Q = torch.from_numpy(job.Q).pin_memory().numpy()
+
+        def step_host():
+            L.reset()
+            for c, sg, tb in zip(job.cams, h_seg, h_tab):
+                L.add_view(c, sg, tb)
+            # the download of E and sum w is queued on the library's copy stream and overlaps the
+            # next step; every step's copy is complete before the clock stops (wait_outputs)
+            L.finalize_async(h_E, h_w)
+            L.query_batch(h_Q, a.k)
+
         step_host()
         L.wait_outputs()
         barrier()
@@ -359,67 +597,76 @@ def run_slag(a):
         dt = rank_max(time.perf_counter() - t0)
         h2d = sum(x.nbytes for x in h_seg) + sum(x.nbytes for x in h_tab) + h_Q.nbytes
         d2h = h_E.nbytes + h_w.nbytes + a.queries * a.k * (8 + 4) + a.queries * 4
-        e2e = {"value": job_rate(contrib_per_step * a.steps, ws, dt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "views_per_s": job_rate(views_per_step * a.steps, ws, dt),
-               "ms_per_step": dt * 1e3 / a.steps,
+        e2e = {"value": job_rate(contrib_per_step * a.steps, ws, dt), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "views_per_s": job_rate(nv * a.steps, ws, dt), "ms_per_step": dt * 1e3 / a.steps,
                "outputs": "slag_finalize_async into pinned host buffers: a step's download overlaps the next step"}
+        del h_seg, h_tab, h_E
 
-    # roofline of the stage with the largest device time
-    import json as _j
-    peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    dominant = max(prof, key=lambda k: prof[k][2])
+    # ---- rooflines -------------------------------------------------------------------------
+    dominant = max(prof, key=lambda s: prof[s][2])
     comp_ms, comp_spans, comp_busy = prof_timed["composite"]
     launches = max(1, comp_spans)
-    busy_per_launch = comp_busy / launches          # composite-busy time per launch (ms)
-    sm_max = peaks.get("sm_max_mhz", 2032.0)
-    peak_tops = N_SM * FP32_LANES * sm_max * 1e6 / 1e12
-    evals_per_launch = evals_per_step * a.steps / launches
-    achieved = evals_per_launch * OPS_PER_EVAL / (busy_per_launch / 1e3) / 1e12
-    traffic = None
-    if COMPOSITE_TRAFFIC["bytes_per_launch"] is not None:
-        import hashlib
-        src = open(os.path.join(ROOT, "paper_2505_08124_b300", "csrc", "k_composite.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest() == COMPOSITE_TRAFFIC["source_sha256"]:
-            traffic = COMPOSITE_TRAFFIC["bytes_per_launch"]
-    roofline = {"kernel": "composite_k", "bound": "alu", "achieved": achieved, "peak": peak_tops,
-                "unit": "TOPS (fp32 issue)", "frac": achieved / peak_tops, "traffic": traffic,
-                "evaluations_per_launch": evals_per_launch,
-                "busy_ms_per_launch": busy_per_launch, "span_ms_per_launch": comp_ms / launches,
-                "peak_source": "derived: %d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json)"
-                               % (N_SM, FP32_LANES, sm_max),
-                "dominant_stage": dominant}
+    roofline = composite_roofline(stats["executed"] * a.steps / launches, comp_busy / launches,
+                                  comp_ms / launches, peaks, peak_source, dominant=dominant,
+                                  evaluations_per_launch=stats["evaluations"] * a.steps / launches)
+    b_alg, f_alg = algorithmic_work(g.n, D, job.cams, int(scene.meta["n_segments"]), stats["pairs"],
+                                    stats["triples"])
+    roof_step = step_roofline(b_alg, f_alg, ms / a.steps, peaks, peak_source)
 
+    # ---- forms -------------------------------------------------------------------------------
     forms = None
-    if not a.no_forms:
-        fargs = (L, g, D, cams, d_seg, d_tab, d_Q, a, stream, dev, rank_max, ws)
-        forms = {"bf16": dict(_form(S, torch, *fargs, precision=S.PREC_BF16), dtype="bf16 operands, f32 accumulate"),
-                 "latent32": _latent_form(S, torch, scene, *fargs)}
+    fsteps = max(1, min(a.form_steps, a.steps))
+    fwarm = max(1, min(a.warmup, 3))
+    if want_forms:
+        forms = {"bf16": dict(run_form(S, torch, dev, stream, job, L, S.PREC_BF16, fsteps, fwarm, ws, rank_max),
+                              dtype="bf16 operands, f32 accumulate", workload=WORKLOAD_DESC[key])}
+        forms["latent32"] = latent_forms(S, torch, dev, stream, got, nv, a, fsteps, fwarm, ws, rank_max)
 
-    cpu = None
+    # ---- the oracle: float64 error on a subsample, and its own time ------------------------
+    cpu, oracle_err = None, None
     if rank == 0 and not a.no_cpu:
-        cpu = _cpu_oracle_sample(scene, views, a.cpu_seconds)
+        cpu, oracle_err = oracle_leg(S, torch, dev, stream, scene, views, a)
+
+    # ---- the mid-scale workload as a secondary line ----------------------------------------
+    mid = None
+    if want_mid:
+        ms_scene = make_scene("mid")
+        mviews = [got[("mid", i)] for i in range(ms_scene.n_views)]
+        mjob = Job(torch, dev, ms_scene, mviews, a.queries, a.k)
+        Lm = S.Lifter(ms_scene.gaussians, dim=ms_scene.dim, stream=stream.cuda_stream)
+        mms = rank_max(_timed(torch, stream, lambda: mjob.run(Lm), a.steps, a.warmup, barrier))
+        mst = Lm.stats()
+        Lm.close()
+        mid = {"workload": WORKLOAD_DESC["mid"], "value": job_rate(mst["contributions"] * a.steps, ws, mms / 1e3),
+               "unit": UNIT, "ms_per_step": mms / a.steps,
+               "views_per_s": job_rate(len(mviews) * a.steps, ws, mms / 1e3), "stats_per_step": mst}
+        del mjob
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "views_per_s": views_per_s,
-               "config": _config(a, scene, views, "replicas x%d" % ws,
-                                 "inputs larger than L2 (%d MB of segment maps + %d MB tables per step; %d MB embeddings "
-                                 "written per step)" % (sum(v.seg.nbytes for v in views) >> 20,
-                                                        sum(v.table.nbytes for v in views) >> 20,
-                                                        (g.n * D * 4) >> 20)),
+               "config": _config(a, scene, job.cams, "replicas x%d" % ws,
+                                 "inputs larger than L2 (%d MB of segment maps + %d MB tables per step; %d MB "
+                                 "embeddings written per step)" % (sum(v[1].nbytes for v in views) >> 20,
+                                                                   sum(v[2].nbytes for v in views) >> 20,
+                                                                   (g.n * D * 4) >> 20)),
                "clocks": clk.summary(),
                "e2e": e2e,
                "roofline": roofline,
+               "roofline_step_hbm": roof_step,
                "cpu_baseline": cpu,
+               "oracle_error": oracle_err,
                "gpu_launches": gpu_launches,
                "forms": forms,
-               "stages_note": "per-stage CUDA-event spans from an untimed pass of the same steps; the timed "
-                              "steps record the composite's spans only",
-               "stages_busy_ms_per_step": {k: v[2] / a.steps for k, v in prof.items()},
-               "stages_span_ms_per_step": {k: v[0] / a.steps for k, v in prof.items()},
+               "mid": mid,
+               "host_view_generation_s": t_gen,
+               "stages_note": "per-stage CUDA-event spans from %d untimed steps after the timed ones; the timed "
+                              "steps record the composite's spans only" % st_steps,
+               "stages_busy_ms_per_step": {s: v[2] / st_steps for s, v in prof.items()},
+               "stages_span_ms_per_step": {s: v[0] / st_steps for s, v in prof.items()},
                "stats_per_step": stats}
         print(json.dumps(out), flush=True)
     L.close()
@@ -427,84 +674,83 @@ def run_slag(a):
         dist.destroy_process_group()
 
 
-def _form(S, torch, L, g, D, cams, d_seg, d_tab, d_Q, a, stream, dev, rank_max, ws, precision, latent=None,
-          tie_eps=1e-3):
-    """A form of the aggregation on the same workload: the same step with another precision;
-    its error is stated against the float32 path's embeddings of the same job (1 - cosine per
-    Gaussian with sum w >= 1e-3) and its top-10 answers against the float32 path's (strict
-    overlap, and tie-tolerant: an id counts when its float32 cosine is within tie_eps of the
-    float32 10th best)."""
-    n = g.n
-    Lb = S.Lifter(g, dim=D, stream=stream.cuda_stream, precision=precision, latent_params=latent)
-    ids_b = torch.empty((a.queries, a.k), dtype=torch.int64, device=dev)
-    sc_b = torch.empty((a.queries, a.k), dtype=torch.float32, device=dev)
-    cnt_b = torch.empty(a.queries, dtype=torch.int32, device=dev)
-    w_b = torch.empty(n, dtype=torch.float32, device=dev)
-
-    def step(lift, E_out, w_out, ids, sc, cnt):
-        lift.reset()
-        for c, sg, tb in zip(cams, d_seg, d_tab):
-            lift.add_view(c, sg, tb)
-        lift.finalize(E_out, w_out)
-        lift.query_batch(d_Q, a.k, ids, sc, cnt)
-
-    for _ in range(max(1, a.warmup)):
-        step(Lb, None, w_b, ids_b, sc_b, cnt_b)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        step(Lb, None, w_b, ids_b, sc_b, cnt_b)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = rank_max(e0.elapsed_time(e1))
-    contrib = Lb.stats()["contributions"]
-
-    # error against the float32 path on this job
-    E_b = torch.empty((n, D), dtype=torch.float32, device=dev)
-    E_f = torch.empty((n, D), dtype=torch.float32, device=dev)
-    w_f = torch.empty(n, dtype=torch.float32, device=dev)
-    ids_f = torch.empty_like(ids_b)
-    step(Lb, E_b, w_b, ids_b, sc_b, cnt_b)
-    step(L, E_f, w_f, ids_f, torch.empty_like(sc_b), torch.empty_like(cnt_b))
-    torch.cuda.synchronize()
-    Lb.close()
-    ok = w_f >= 1e-3
-    Eb, Ef = E_b[ok].double(), E_f[ok].double()
-    cos = (Eb * Ef).sum(1) / (Eb.norm(dim=1) * Ef.norm(dim=1))
-    En = E_f.double() / E_f.double().norm(dim=1, keepdim=True).clamp_min(1e-300)
-    Qd = d_Q.double()
-    sb = torch.einsum("qkd,qd->qk", En[ids_b.clamp_min(0)], Qd)
-    sf = torch.einsum("qkd,qd->qk", En[ids_f.clamp_min(0)], Qd)
-    tie = (sb >= sf.min(dim=1, keepdim=True).values - tie_eps).double().mean().item()
-    strict = float(np.mean([len(set(x) & set(y)) / a.k for x, y in zip(ids_b.tolist(), ids_f.tolist())]))
-    return {"value": job_rate(contrib * a.steps, ws, ms / 1e3), "unit": UNIT, "ms_per_step": ms / a.steps,
-            "views_per_s": job_rate(len(cams) * a.steps, ws, ms / 1e3),
-            "cos_err_vs_fp32": {"max": float((1 - cos).max().item()), "mean": float((1 - cos).mean().item()),
-                                "gaussians": int(ok.sum().item())},
-            "top10_agree_vs_fp32": {"tie_tolerant": tie, "tie_eps": tie_eps, "strict": strict}}
-
-
-def _latent_form(S, torch, scene, *args):
-    """The latent form: the autoencoder trained on segment embeddings drawn like the
-    workload's tables (same prototypes and noise law), then the same step aggregating codes."""
+def latent_forms(S, torch, dev, stream, got, nv, a, steps, warmup, ws, rank_max):
+    """The latent form on the learned workload, under both readings of the embeddings' noise
+    N(0, 0.1): per coordinate (literal) and with norm 0.1 (sigma = 0.1 / sqrt(D)). The
+    autoencoder is trained on 1M samples of the mid-scale law (its 32 prototypes); views/s of the
+    latent form and of the float32 path on the same job, errors against the float32 path."""
     import synth
-    D = scene.dim
-    m = scene.meta
-    # training data drawn by the lifted scene's own generator (its seed, prototypes and noise):
-    # 1M samples on the 2M-Gaussian configuration, 262k on the mid scale (a short default run)
-    n_train, epochs = (1 << 20) if scene.gaussians.n >= 1_000_000 else (1 << 18), 4
-    X = synth.segment_samples(m["seed"], n_train, D, m["n_protos"], noise_sigma=m["noise_sigma"])
-    t0 = time.perf_counter()
-    params, losses = S.latent_train(X, epochs=epochs, batch=512, lr=2e-3, seed=5)
-    train_s = time.perf_counter() - t0
-    out = _form(S, torch, *args, precision=S.PREC_LATENT32, latent=params, tie_eps=1e-2)
+    out = {"workload": LEARNED_DESC}
+    lscene = make_scene("learned")
+    D = lscene.dim
+    lviews = [got[("learned", i)] for i in range(nv)]
+    mid_seed, mid_protos = 1, 32           # the mid-scale workload's embedding law
+    for reading, sigma in (("literal", 0.1), ("scaled", 0.1 / np.sqrt(D))):
+        if reading == "scaled":
+            lviews = [(c, s, got[("learned_scaled", i)][2]) for i, (c, s, _) in enumerate(lviews)]
+        job = Job(torch, dev, lscene, lviews, a.queries, a.k)
+        X = synth.segment_samples(mid_seed, 1 << 20, D, mid_protos, noise_sigma=sigma)
+        t0 = time.perf_counter()
+        params, losses = S.latent_train(X, epochs=4, batch=512, lr=2e-3, seed=5)
+        train_s = time.perf_counter() - t0
+        del X
+        Lf = S.Lifter(lscene.gaussians, dim=D, stream=stream.cuda_stream)
+        r = run_form(S, torch, dev, stream, job, Lf, S.PREC_LATENT32, steps, warmup, ws, rank_max, latent=params,
+                     tie_eps=1e-2, time_plain=(reading == "literal"))
+        Lf.close()
+        r["noise_sigma"] = float(sigma)
+        r["training"] = {"samples": 1 << 20, "epochs": 4, "seconds": train_s,
+                         "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1])}
+        out[reading] = r
+        del job
     out["dtype"] = "32-d codes, bf16 weights, f32 accumulate"
-    out["training"] = {"samples": n_train, "epochs": epochs, "seconds": train_s,
-                       "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1])}
     return out
 
+
+def oracle_leg(S, torch, dev, stream, scene, views, a):
+    """cpu_baseline (the float64 oracle's time on the first a.cpu_views views, reported per view)
+    and oracle_error (the float32 path and the BF16 form against it), on a seeded
+    10,000-Gaussian subsample: the oracle accumulates only those Gaussians, every Gaussian
+    still takes part in the compositing."""
+    import synth
+    nv = min(a.cpu_views, len(views))
+    vs = [synth.View(c, s, t) for c, s, t in views[:nv]]
+    g = scene.gaussians
+    sub = np.sort(np.random.default_rng(7).choice(g.n, min(CPU_SUBSAMPLE, g.n), replace=False))
+    sub_t = torch.from_numpy(sub).to(dev)
+    got = {}
+    for name, prec in (("fp32", S.PREC_FP32), ("bf16", S.PREC_BF16)):
+        with S.Lifter(g, dim=scene.dim, stream=stream.cuda_stream, precision=prec) as L:
+            for v in vs:
+                L.add_view(v.camera, v.seg, v.table)
+            E = torch.empty((g.n, scene.dim), dtype=torch.float32, device=dev)
+            w = torch.empty(g.n, dtype=torch.float32, device=dev)
+            L.finalize(E, w)
+            torch.cuda.synchronize()
+            got[name] = (E[sub_t].cpu().numpy().astype(np.float64), w[sub_t].cpu().numpy().astype(np.float64))
+            del E, w
+    Eo, den, secs, info, threads = oracle_subsample(scene, vs, sub)
+    contrib = sum(c for _, c in info)
+    cpu = {"value": contrib / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "views_per_s": nv / secs, "s_per_view": secs / nv,
+           "sample": "the first %d views of the same workload, whole views, accumulated for a seeded %d-Gaussian "
+                     "subsample (tiles that touch none of it are skipped); float64 factored oracle, one view per "
+                     "thread on %d threads; %.1f s" % (nv, len(sub), threads, secs)}
+    ok = den >= 1e-3
+    err = {"views": nv, "subsample": int(len(sub)), "touched": int(ok.sum())}
+    for name, (E, w) in got.items():
+        rel = float(np.linalg.norm(E - Eo) / np.linalg.norm(Eo))
+        relw = float(np.linalg.norm(w - den) / np.linalg.norm(den))
+        x, y = E[ok], Eo[ok]
+        cos = (x * y).sum(1) / (np.linalg.norm(x, axis=1) * np.linalg.norm(y, axis=1))
+        err[name] = {"rel_l2": rel, "wsum_rel_l2": relw, "max_1_minus_cos": float((1 - cos).max()),
+                     "mean_1_minus_cos": float((1 - cos).mean())}
+    return cpu, err
+
+
+# ----------------------------------------------------------------------------
+# batched workload (secondary)
+# ----------------------------------------------------------------------------
 
 def _batched_view(job):
     """(scene index, view index) -> (camera, segment map, table) of the batched workload."""
@@ -519,8 +765,6 @@ def run_batched(a):
     every scene lifted on its own in turn (its views, then its finalize), against all scenes in
     one slag_add_views_batched call and then every finalize; both with device-resident inputs, no
     queries."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
     import synth
     scenes = synth.config_batched()
     cap = a.views or 16
@@ -555,20 +799,8 @@ def run_batched(a):
         for L, w in zip(lifters, wbuf):
             L.finalize(None, w)
 
-    def timed(fn):
-        for _ in range(max(1, a.warmup)):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(a.steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / a.steps
-
-    ms_seq = timed(sequential)
-    ms_bat = timed(batched)
+    ms_seq = _timed(torch, stream, sequential, a.steps, max(1, a.warmup)) / a.steps
+    ms_bat = _timed(torch, stream, batched, a.steps, max(1, a.warmup)) / a.steps
     contrib = sum(L.stats()["contributions"] for L in lifters)
     nviews = sum(len(v) for v in views)
     for L in lifters:

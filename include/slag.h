@@ -116,7 +116,7 @@ typedef struct {
 /* Counters of the views added since create / reset. views and columns count
  * every accepted view; pairs and last_pairs count the views whose second half
  * is queued (all of them after a finalize); contributions, triples,
- * last_contributions and evaluations are read at finalize. */
+ * last_contributions, evaluations and executed are read at finalize. */
 typedef struct {
     int64_t views;           /* views added since create / reset */
     int64_t pairs;           /* sum over views of Gaussian-tile pairs P */
@@ -128,6 +128,10 @@ typedef struct {
     int64_t touched;         /* Gaussians with sum w > 0 at the last finalize */
     int64_t evaluations;     /* sum over views of (Gaussian, pixel) pairs visited before each
                                 pixel ended (the compositing work, contributing or not) */
+    int64_t executed;        /* sum over views of the (Gaussian, pixel) evaluations the
+                                compositing kernel carried out: a group of 64 pixels evaluates
+                                the Gaussians that can reach alpha >= 1/255 somewhere in it,
+                                for all 64 pixels; read at finalize */
 } slag_stats;
 
 /* Create a context over the Gaussian set (Method, Rasterizer_SLAG statement:
@@ -219,12 +223,16 @@ slag_status slag_query(slag_ctx *ctx, const float *q, int32_t k, int64_t *out_id
  *   parts rounded up to 256) must not exceed 16 MiB; larger requests return
  *   SLAG_ERR_CAPACITY without launching anything (split the queries).
  *   The first call on a device looks up the array's device address (once per
- *   device, with that device current); make that first call before any stream
+ *   device and driver context, with that device current; a call after a
+ *   device reset looks it up again); make that first call before any stream
  *   capture. Every call uses the same array: nothing in it needs to start at
  *   zero (each call writes all it reads), but calls that overlap on the GPU --
  *   in different streams or from different threads -- race on it.
- * Errors: INVALID_ARG (NULL pointer, sizes out of range, misaligned E or Q);
- * CAPACITY (see above); CUDA. */
+ *   Every pointer must be memory of the current device (device or managed
+ *   allocations); host memory, pinned or not, is refused before any launch.
+ * Errors: INVALID_ARG (NULL pointer, sizes out of range, misaligned E or Q, a
+ * pointer that is not memory of the current device); CAPACITY (see above);
+ * CUDA. */
 slag_status slag_noalloc_query_topk(const float *E, int64_t n, int32_t dim, const float *wsum,
                                     const float *Q, int32_t B, int32_t k, int64_t *out_ids,
                                     float *out_scores, int32_t *out_count, void *cuda_stream);

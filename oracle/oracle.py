@@ -83,6 +83,9 @@ def _bind(lib):
     lib.oracle_view_weights.argtypes = [i64, P, P, P, P, ctypes.POINTER(OCam), P, i32, ctypes.c_int,
                                         i64, P, P, P, P, P, P]
     lib.oracle_view_weights.restype = ctypes.c_int
+    lib.oracle_view_weights_rows.argtypes = [i64, P, P, P, P, ctypes.POINTER(OCam), P, i32, ctypes.c_int,
+                                             i64, P, P, P, P, P, P, i32, i32]
+    lib.oracle_view_weights_rows.restype = ctypes.c_int
     lib.oracle_view_literal.argtypes = [i64, P, P, P, P, ctypes.POINTER(OCam), P, i32, P, i32,
                                         ctypes.c_int, P, P]
     lib.oracle_view_literal.restype = ctypes.c_int
@@ -151,8 +154,12 @@ def project_f64(g, cam, lib=None):
 # compositing + aggregation
 # ----------------------------------------------------------------------------
 
-def view_weights(g, view, weight_mode=ALPHA_T, sub_ids=None, per_pixel=False, lib=None):
-    """B (n_sub x M) of one view, plus optional per-pixel T_final / sum w / count."""
+def view_weights(g, view, weight_mode=ALPHA_T, sub_ids=None, per_pixel=False, lib=None, tile_rows=None):
+    """B (n_sub x M) of one view, plus optional per-pixel T_final / sum w / count.
+
+    tile_rows = (ty0, ty1) composites only the pixels of those tile rows (a bounded sample of
+    the view; each of its pixels gets the whole view's result); per-pixel outputs of the other
+    rows are left unset."""
     lib = lib or load()
     m, s, q, o = _garr(g)
     n = m.shape[0]
@@ -168,8 +175,13 @@ def view_weights(g, view, weight_mode=ALPHA_T, sub_ids=None, per_pixel=False, li
     cnt = np.empty((H, W), np.int32) if per_pixel else None
     stats = np.zeros(2, np.int64)
     c = _ocam(cam)
-    rc = lib.oracle_view_weights(n, _p(m), _p(s), _p(q), _p(o), ctypes.byref(c), _p(seg), M,
-                                 weight_mode, n_sub, _p(sub), _p(B), _p(Tf), _p(ws), _p(cnt), _p(stats))
+    if tile_rows is None:
+        rc = lib.oracle_view_weights(n, _p(m), _p(s), _p(q), _p(o), ctypes.byref(c), _p(seg), M,
+                                     weight_mode, n_sub, _p(sub), _p(B), _p(Tf), _p(ws), _p(cnt), _p(stats))
+    else:
+        rc = lib.oracle_view_weights_rows(n, _p(m), _p(s), _p(q), _p(o), ctypes.byref(c), _p(seg), M,
+                                          weight_mode, n_sub, _p(sub), _p(B), _p(Tf), _p(ws), _p(cnt), _p(stats),
+                                          int(tile_rows[0]), int(tile_rows[1]))
     if rc == -2:
         raise ValueError("segment id outside [-1, M)")
     if rc != 0:
@@ -198,13 +210,14 @@ def view_literal(g, view, weight_mode=ALPHA_T, num=None, den=None, lib=None):
     return num, den
 
 
-def lift(g, views, weight_mode=ALPHA_T, sub_ids=None, threads=1, lib=None):
+def lift(g, views, weight_mode=ALPHA_T, sub_ids=None, threads=1, lib=None, tile_rows=None):
     """Factored aggregation over `views` (an iterable of View).
 
     Returns (num, den, info): num (n_sub x D) = sum_v B_v . E_v, den (n_sub) =
     sum_v sum_j B_v, info = per-view P and contribution counts. Views are
     spread over `threads` host threads (the C oracle runs without the GIL),
-    one accumulator per thread, summed at the end.
+    one accumulator per thread, summed at the end. tile_rows = (ty0, ty1)
+    limits every view to the pixels of those tile rows (a bounded sample).
     """
     lib = lib or load()
     views = list(views)
@@ -216,7 +229,7 @@ def lift(g, views, weight_mode=ALPHA_T, sub_ids=None, threads=1, lib=None):
         den = np.zeros(n_sub, np.float64)
         info = []
         for v in chunk:
-            r = view_weights(g, v, weight_mode, sub_ids, lib=lib)
+            r = view_weights(g, v, weight_mode, sub_ids, lib=lib, tile_rows=tile_rows)
             num += r["B"] @ v.table.astype(np.float64)
             den += r["B"].sum(axis=1)
             info.append((r["P"], r["contributions"]))

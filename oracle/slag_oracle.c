@@ -158,8 +158,9 @@ typedef struct {
     dk_t *items;      /* P */
 } tile_lists;
 
+/* Lists of the tiles in rows [ty0, ty1) of the tile grid (the others stay empty). */
 static int build_lists(int64_t n, const float *depth, const int32_t *rect, const uint32_t *touched,
-                       const ocam *c, tile_lists *L) {
+                       const ocam *c, int32_t ty0, int32_t ty1, tile_lists *L) {
     L->tilesx = (c->width + TILE - 1) / TILE;
     L->tilesy = (c->height + TILE - 1) / TILE;
     int64_t T = (int64_t)L->tilesx * L->tilesy;
@@ -167,8 +168,10 @@ static int build_lists(int64_t n, const float *depth, const int32_t *rect, const
     if (!L->start) return -1;
     for (int64_t k = 0; k < n; ++k) {
         if (!touched[k]) continue;
-        for (int32_t y = rect[4 * k + 1]; y < rect[4 * k + 3]; ++y)
+        for (int32_t y = rect[4 * k + 1]; y < rect[4 * k + 3]; ++y) {
+            if (y < ty0 || y >= ty1) continue;
             for (int32_t x = rect[4 * k]; x < rect[4 * k + 2]; ++x) L->start[(int64_t)y * L->tilesx + x + 1]++;
+        }
     }
     for (int64_t t = 0; t < T; ++t) L->start[t + 1] += L->start[t];
     L->P = L->start[T];
@@ -178,13 +181,15 @@ static int build_lists(int64_t n, const float *depth, const int32_t *rect, const
     memcpy(fill, L->start, sizeof(int64_t) * (size_t)T);
     for (int64_t k = 0; k < n; ++k) {
         if (!touched[k]) continue;
-        for (int32_t y = rect[4 * k + 1]; y < rect[4 * k + 3]; ++y)
+        for (int32_t y = rect[4 * k + 1]; y < rect[4 * k + 3]; ++y) {
+            if (y < ty0 || y >= ty1) continue;
             for (int32_t x = rect[4 * k]; x < rect[4 * k + 2]; ++x) {
                 int64_t t = (int64_t)y * L->tilesx + x;
                 L->items[fill[t]].d = depth[k];
                 L->items[fill[t]].k = (int32_t)k;
                 fill[t]++;
             }
+        }
     }
     free(fill);
     for (int64_t t = 0; t < T; ++t)
@@ -204,7 +209,9 @@ int64_t oracle_tile_lists_f32(int64_t n, const float *means, const float *scales
     if (!depth || !rect || !touched) { free(depth); free(rect); free(touched); return -1; }
     oracle_bin_f32(n, means, scales, quats, cam, depth, rect, touched);
     tile_lists L;
-    if (build_lists(n, depth, rect, touched, cam, &L)) { free(depth); free(rect); free(touched); return -1; }
+    if (build_lists(n, depth, rect, touched, cam, 0, (cam->height + TILE - 1) / TILE, &L)) {
+        free(depth); free(rect); free(touched); return -1;
+    }
     int64_t P = L.P;
     if (cap >= P) {
         for (int64_t i = 0; i < P; ++i) list_out[i] = L.items[i].k;
@@ -291,13 +298,16 @@ typedef struct {
     const int32_t *seg;
     int32_t M;
     int weight_mode;
+    int32_t ty0, ty1;   /* tile rows composited: [ty0, ty1) */
 } view_in;
 
 /* Composite every pixel of one view front to back. For each contributing
  * (Gaussian, pixel) with the pixel in segment j >= 0, calls sink(k, j, w).
  * Optional per-pixel outputs: final transmittance, sum of weights over all
  * contributing Gaussians (masked or not), number of contributions.
- * tile_mask (nullable): only tiles with a non-zero entry are composited. */
+ * tile_mask (nullable): only tiles with a non-zero entry are composited; only the
+ * tile rows [v->ty0, v->ty1) are composited in any case (a bounded sample of a
+ * view: the pixels of those rows get exactly the results of the whole view). */
 typedef void (*sink_fn)(void *ctx, int32_t k, int32_t j, double w);
 
 static int composite_view(const view_in *v, const uint8_t *tile_mask, sink_fn sink, void *sctx,
@@ -312,10 +322,12 @@ static int composite_view(const view_in *v, const uint8_t *tile_mask, sink_fn si
     for (int64_t k = 0; k < n; ++k)
         if (touched[k]) project_f64(v->means + 3 * k, v->scales + 3 * k, v->quats + 4 * k, v->opac[k], v->cam, pj + k);
     tile_lists L;
-    if (build_lists(n, depth, rect, touched, v->cam, &L)) { free(depth); free(rect); free(touched); free(pj); return -1; }
+    if (build_lists(n, depth, rect, touched, v->cam, v->ty0, v->ty1, &L)) {
+        free(depth); free(rect); free(touched); free(pj); return -1;
+    }
     const int32_t W = v->cam->width, H = v->cam->height;
     int64_t contributions = 0;
-    for (int32_t ty = 0; ty < L.tilesy; ++ty)
+    for (int32_t ty = v->ty0; ty < v->ty1 && ty < L.tilesy; ++ty)
         for (int32_t tx = 0; tx < L.tilesx; ++tx) {
             int64_t t = (int64_t)ty * L.tilesx + tx;
             if (tile_mask && !tile_mask[t]) continue;
@@ -364,18 +376,20 @@ static void fact_sink(void *c, int32_t k, int32_t j, double w) {
     f->B[s * f->M + j] += w;
 }
 
-/* B (n_sub x M) += per-(Gaussian, segment) sums of masked weights for one view.
- * sub_ids (nullable): accumulate only for these Gaussians (row r of B is
- * Gaussian sub_ids[r]); tiles not touched by any of them are skipped.
+/* B (n_sub x M) += per-(Gaussian, segment) sums of masked weights for one view,
+ * over the pixels of tile rows [ty0, ty1) (the whole view: 0 and the tile-grid
+ * height). sub_ids (nullable): accumulate only for these Gaussians (row r of B
+ * is Gaussian sub_ids[r]); tiles not touched by any of them are skipped.
  * Returns 0, -1 on allocation failure, -2 on a segment id outside [-1, M). */
-int oracle_view_weights(int64_t n, const float *means, const float *scales, const float *quats,
-                        const float *opac, const ocam *cam, const int32_t *seg, int32_t M,
-                        int weight_mode, int64_t n_sub, const int64_t *sub_ids, double *B,
-                        double *T_final, double *wsum_px, int32_t *count_px, int64_t *stats) {
+int oracle_view_weights_rows(int64_t n, const float *means, const float *scales, const float *quats,
+                             const float *opac, const ocam *cam, const int32_t *seg, int32_t M,
+                             int weight_mode, int64_t n_sub, const int64_t *sub_ids, double *B,
+                             double *T_final, double *wsum_px, int32_t *count_px, int64_t *stats,
+                             int32_t ty0, int32_t ty1) {
     int64_t npx = (int64_t)cam->width * cam->height;
     for (int64_t p = 0; p < npx; ++p)
         if (seg && (seg[p] < -1 || seg[p] >= M)) return -2;
-    view_in v = {n, means, scales, quats, opac, cam, seg, M, weight_mode};
+    view_in v = {n, means, scales, quats, opac, cam, seg, M, weight_mode, ty0, ty1};
     int64_t *sub_of = NULL;
     uint8_t *tile_mask = NULL;
     if (sub_ids) {
@@ -399,6 +413,15 @@ int oracle_view_weights(int64_t n, const float *means, const float *scales, cons
     return rc;
 }
 
+/* The whole view. */
+int oracle_view_weights(int64_t n, const float *means, const float *scales, const float *quats,
+                        const float *opac, const ocam *cam, const int32_t *seg, int32_t M,
+                        int weight_mode, int64_t n_sub, const int64_t *sub_ids, double *B,
+                        double *T_final, double *wsum_px, int32_t *count_px, int64_t *stats) {
+    return oracle_view_weights_rows(n, means, scales, quats, opac, cam, seg, M, weight_mode, n_sub, sub_ids, B,
+                                    T_final, wsum_px, count_px, stats, 0, (cam->height + TILE - 1) / TILE);
+}
+
 /* --- literal form: one D-wide multiply-add per contributing pixel --------- */
 
 typedef struct { const float *table; int32_t D; double *num; double *den; } lit_ctx;
@@ -418,7 +441,7 @@ int oracle_view_literal(int64_t n, const float *means, const float *scales, cons
     int64_t npx = (int64_t)cam->width * cam->height;
     for (int64_t p = 0; p < npx; ++p)
         if (seg && (seg[p] < -1 || seg[p] >= M)) return -2;
-    view_in v = {n, means, scales, quats, opac, cam, seg, M, weight_mode};
+    view_in v = {n, means, scales, quats, opac, cam, seg, M, weight_mode, 0, (cam->height + TILE - 1) / TILE};
     lit_ctx l = {table, D, num, den};
     return composite_view(&v, NULL, lit_sink, &l, NULL, NULL, NULL, NULL);
 }

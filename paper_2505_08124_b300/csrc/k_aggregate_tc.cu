@@ -344,12 +344,8 @@ __global__ void __launch_bounds__(kThreadsA, 1) aggregate_tc_k(const AggArgs a, 
 
 template <int kNP, bool kBF>
 void launch_one(const AggArgs &a, int64_t nblocks, uint32_t *err, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(aggregate_tc_k<kNP, kBF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)AggShape<kNP, kBF>::smem());
-        attr_set = true;
-    }
+    // on failure the error stays recorded for the caller's cudaGetLastError check
+    if (set_max_smem((const void *)aggregate_tc_k<kNP, kBF>, (int)AggShape<kNP, kBF>::smem()) != cudaSuccess) return;
     aggregate_tc_k<kNP, kBF><<<(unsigned)nblocks, kThreadsA, AggShape<kNP, kBF>::smem(), st>>>(a, err);
 }
 

@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
     // evp in the tile's candidate order); the others examined every candidate the warp went
     // through (seen)
     int evp0 = 0, evp1 = 0, seen = 0;
+    unsigned long long executed = 0;   // Gaussians this warp evaluated for all 64 of its pixels
 
     // this tile's candidates: the depth-ordered list of its bin (a 2^shift x
     // 2^shift square of tiles); the Gaussians whose tile rectangle holds this tile
@@ -477,6 +478,7 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
             // only each pixel's transmittance updates run in order
             // the survivors' chunk positions in order, then -1
             const int n = __popc(mask);
+            executed += (unsigned long long)n;
             int32_t *cl = sm.clist[w];
             if (hitw) cl[__popc(mask & lt)] = lane;
             if (lane == 0) cl[n] = -1;
@@ -643,24 +645,19 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
     }
     if (lane == 0 && cnt) atomicAdd(a.contrib, cnt);
     if (lane == 0 && ev && a.evals) atomicAdd(a.evals, ev);
+    if (lane == 0 && executed && a.evals_exec) atomicAdd(a.evals_exec, executed * (unsigned long long)(2 * 32));
 }
 
 }  // namespace
 
 void launch_composite(const CompositeArgs &a, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(composite_k<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-        cudaFuncSetAttribute(composite_k<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-        cudaFuncSetAttribute(composite_k<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-        cudaFuncSetAttribute(composite_k<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-        attr_set = true;
-    }
     const int tiles = a.cam.tiles_x * a.cam.tiles_y;
     const bool kernel = a.weight_mode == SLAG_WEIGHT_KERNEL;
     const bool debug = a.dbg_T || a.dbg_wsum || a.dbg_count;
     auto *kfn = kernel ? (debug ? composite_k<true, true> : composite_k<true, false>)
                        : (debug ? composite_k<false, true> : composite_k<false, false>);
+    // on failure the error stays recorded for the caller's cudaGetLastError check
+    if (set_max_smem((const void *)kfn, (int)sizeof(Smem)) != cudaSuccess) return;
     kfn<<<tiles * kSubTiles, kThreads, sizeof(Smem), st>>>(a); note_launch();
 }
 

@@ -265,12 +265,9 @@ __global__ void __launch_bounds__(256) weights_t_k(const float *__restrict__ W, 
 template <int NT, int kMode>
 cudaError_t launch_dense_t(const CUtensorMap &ta, const CUtensorMap &tw, int64_t rows, int64_t rows_pad, int32_t K,
                            int32_t N, const float *bias, float *out, int64_t ldo, uint32_t *err, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(dense_tc_k<NT, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)dense_smem<NT>());
+    {
+        const cudaError_t e = set_max_smem((const void *)dense_tc_k<NT, kMode>, (int)dense_smem<NT>());
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     // persistent: one CTA per SM at most (the shared memory admits one)
     int sms = 148;

@@ -373,11 +373,9 @@ cudaError_t launch_query_topk_tc(const float *Q, int32_t B, float *Qhl, const fl
                                  const uint32_t *rows, int64_t n, int32_t D, int32_t k, float *cand_s,
                                  uint32_t *cand_i, int64_t *out_ids, float *out_scores, int32_t *out_count,
                                  uint32_t *err, cudaStream_t st, int32_t splits) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(query_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    {
+        const cudaError_t e = set_max_smem((const void *)query_tc_k, (int)kSmemBytes);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     const int32_t kk = k < kTop ? k : kTop;
     if (n <= 0) {   // no candidates: every query gets an empty result

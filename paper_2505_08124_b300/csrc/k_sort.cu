@@ -258,14 +258,10 @@ void radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, int64_t n,
                 cudaStream_t st, uint2 *ranges, int nranges) {
     constexpr int kTileN = kThreads * ITEMS;
     const int ntiles = (int)((n + kTileN - 1) / kTileN);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(rs_scatter<K, ITEMS, BINS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)scatter_smem<K, ITEMS, BINS>());
-        cudaFuncSetAttribute(rs_hist<K, ITEMS, BINS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kWarps * BINS * 4);
-        attr_set = true;
-    }
+    // on failure the error stays recorded for the caller's cudaGetLastError check
+    if (set_max_smem((const void *)rs_scatter<K, ITEMS, BINS>, (int)scatter_smem<K, ITEMS, BINS>()) != cudaSuccess ||
+        set_max_smem((const void *)rs_hist<K, ITEMS, BINS>, kWarps * BINS * 4) != cudaSuccess)
+        return;
     const uint32_t mask = (width >= 32) ? 0xffffffffu : ((1u << width) - 1u);
     rs_hist<K, ITEMS, BINS><<<ntiles, kThreads, kWarps * BINS * 4, st>>>(ki, n, shift, mask, width, s.hist, ntiles); note_launch();
     rs_offsets<<<BINS, ntiles >= 1024 ? 1024 : (ntiles >= 256 ? 256 : 64), 0, st>>>(s.hist, s.digit_tot, ntiles); note_launch();

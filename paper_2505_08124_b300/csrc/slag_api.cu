@@ -28,6 +28,8 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <mutex>
+#include <set>
 #include <cmath>
 #include <string>
 #include <utility>
@@ -42,11 +44,25 @@ namespace {
 std::atomic<unsigned long long> g_launches{0};
 }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t set_max_smem(const void *fn, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, fn})) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert({dev, fn});
+    return e;
+}
 }  // namespace slag
 
 namespace {
 
 constexpr int kSlots = 6;   // views in flight
+constexpr int kTotals = 5;  // device running totals (see slag_ctx::totals)
 
 // Buffers of one view in flight. Stage A (front stream) and stage B (second
 // front stream) fill them; the slot's back stream composites from them; stage A
@@ -77,7 +93,7 @@ struct ViewSlot {
     struct Host {
         ViewCounters v;                    // stage A's counters
         ViewCounters vu;                   // the segment-id check
-        unsigned long long totals[4];      // the context's totals when stage A ended
+        unsigned long long totals[kTotals]; // the context's totals when stage A ended
     } *h = nullptr;                        // mapped pinned host copy
     Host *h_dev = nullptr;                 // its device alias (written by launch_copy_words)
     const uint32_t *sgid = nullptr;        // internal ids in depth order (stage A's output)
@@ -127,12 +143,13 @@ struct slag_ctx {
     int64_t dbg_cap = 0;
 
     unsigned long long *totals = nullptr;    // device: [0] triples in the log, [1] contributions,
-                                             // [2] low word: log overflow flag, [3] evaluations
+                                             // [2] low word: log overflow flag, [3] evaluations,
+                                             // [4] executed lane-pixel evaluations
     unsigned long long *log_count = nullptr; // = totals
     unsigned long long *contrib = nullptr;   // = totals + 1
     struct HostCounters {
         ViewCounters v;                      // validation at create, the last view at finalize
-        unsigned long long totals[4];
+        unsigned long long totals[kTotals];
         unsigned long long touched;
         unsigned long long n_q;              // query candidates (touched rows)
         uint32_t tc_err;
@@ -438,7 +455,7 @@ slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
     exclusive_scan_u32(vs.stouched, vs.offsets, n, &vs.ctr->P, ctx->scratch, st);
     span_end(ctx, st);
     launch_copy_words(vs.ctr, &vs.h_dev->v, sizeof(ViewCounters), st);
-    launch_copy_words(ctx->totals, vs.h_dev->totals, 4 * sizeof(unsigned long long), st);
+    launch_copy_words(ctx->totals, vs.h_dev->totals, kTotals * sizeof(unsigned long long), st);
     CK(cudaGetLastError());
     return SLAG_OK;
 }
@@ -624,7 +641,7 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     CA(cudaStreamCreateWithFlags(&ctx->qstream, cudaStreamNonBlocking));
     CA(cudaEventCreateWithFlags(&ctx->qev_in, cudaEventDisableTiming));
     CA(cudaEventCreateWithFlags(&ctx->qev_out, cudaEventDisableTiming));
-    CA(dalloc(&ctx->totals, 4));
+    CA(dalloc(&ctx->totals, kTotals));
     ctx->log_count = ctx->totals;
     ctx->contrib = ctx->totals + 1;
     CA(dalloc(&ctx->touched, 1));
@@ -632,7 +649,7 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     ViewCounters *vctr = ctx->slot[0].ctr;
     CA(cudaMemsetAsync(ctx->tc_err, 0, sizeof(uint32_t), st));
     CA(cudaMemsetAsync(vctr, 0, sizeof(ViewCounters), st));
-    CA(cudaMemsetAsync(ctx->totals, 0, 4 * sizeof(unsigned long long), st));
+    CA(cudaMemsetAsync(ctx->totals, 0, kTotals * sizeof(unsigned long long), st));
     CA(scratch_reserve(ctx->scratch, n));
     CA(scratch_reserve(ctx->scratch_b, n));
 
@@ -715,7 +732,7 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
         // fill level; the new capacity keeps room for a full pipeline of views, so
         // that the next views pass this test without waiting
         CK(drain_views(ctx));
-        launch_copy_words(ctx->totals, vs.h_dev->totals, 4 * sizeof(unsigned long long), fb);
+        launch_copy_words(ctx->totals, vs.h_dev->totals, kTotals * sizeof(unsigned long long), fb);
         CK(cudaStreamSynchronize(fb));
         const int64_t used = (int64_t)vs.h->totals[0];
         const int64_t need = used + others + vs.log_bound;
@@ -760,6 +777,7 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     a.overflow = reinterpret_cast<uint32_t *>(ctx->totals + 2);
     a.contrib = &vs.ctr->contributions;
     a.evals = ctx->totals + 3;
+    a.evals_exec = ctx->totals + 4;
     a.dbg_T = a.dbg_wsum = nullptr;
     a.dbg_count = nullptr;
     a.accumulate = 1;
@@ -891,12 +909,13 @@ slag_status finalize_prepare(slag_ctx *ctx) {
     if (s0 != SLAG_OK) return s0;
     CK(join_views(ctx));
     const ViewSlot &last = ctx->slot[(ctx->views_enqueued + kSlots - 1) % kSlots];
-    launch_copy_words(ctx->totals, ctx->hc_dev->totals, 4 * sizeof(unsigned long long), st);
+    launch_copy_words(ctx->totals, ctx->hc_dev->totals, kTotals * sizeof(unsigned long long), st);
     launch_copy_words(last.ctr, &ctx->hc_dev->v, sizeof(ViewCounters), st);
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     ctx->stats.contributions = (int64_t)ctx->hc->totals[1];
     ctx->stats.evaluations = (int64_t)ctx->hc->totals[3];
+    ctx->stats.executed = (int64_t)ctx->hc->totals[4];
     ctx->stats.last_contributions = (int64_t)ctx->hc->v.contributions;
     if (ctx->hc->totals[2]) ctx->log_overflowed = true;
     if (ctx->log_overflowed) return fail(ctx, SLAG_ERR_CAPACITY, "the triple log overflowed in some view");
@@ -1426,7 +1445,7 @@ slag_status slag_reset(slag_ctx *ctx) {
     CK(cudaMemsetAsync(ctx->s_hi, 0, sizeof(float) * n, st));
     CK(cudaMemsetAsync(ctx->s_lo, 0, sizeof(float) * n, st));
     CK(cudaMemsetAsync(ctx->s_ovf, 0, sizeof(float) * n, st));
-    CK(cudaMemsetAsync(ctx->totals, 0, 4 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(ctx->totals, 0, kTotals * sizeof(unsigned long long), st));
     CK(cudaGetLastError());
     ctx->views_enqueued = 0;
     ctx->table_rows = 0;

@@ -11,6 +11,12 @@ namespace slag {
 // Counts the kernel launches of the library (process-wide, every device).
 void note_launch();
 
+// Raises the dynamic shared-memory limit of kernel `fn` to `bytes` on the current device, once
+// per (device, kernel): the attribute belongs to the calling thread's current device, so a
+// context on another device needs its own call. Thread-safe; returns the CUDA status of the
+// attribute call (cudaSuccess when it was already set on this device).
+cudaError_t set_max_smem(const void *fn, int bytes);
+
 constexpr int kTile = 16;          // screen tile edge in pixels
 constexpr int kBlockG = 128;       // Gaussians per aggregation block (key packs g & 127)
 constexpr int kHashSlots = 4;      // per-view (segment, weight) slots per Gaussian
@@ -202,6 +208,8 @@ struct CompositeArgs {
     uint32_t *overflow;            // set when the triple log is full (never reset by a view)
     unsigned long long *contrib;   // running count of composited (Gaussian, pixel) pairs
     unsigned long long *evals;     // running count of visited (Gaussian, pixel) pairs
+    unsigned long long *evals_exec;// running count of evaluated lane-pixel pairs (nullable): per warp,
+                                   // the Gaussians that survived its culling x its 64 pixels
     float *dbg_T, *dbg_wsum;       // nullable, H x W
     int32_t *dbg_count;            // nullable
     int accumulate;                // 0: compositing only (diagnostics)

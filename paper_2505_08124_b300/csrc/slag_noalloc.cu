@@ -9,6 +9,7 @@
 // on embeddings the caller already holds on the device, with all of its
 // scratch (the inverse row norms and the per-tile candidates) in one
 // fixed-size array in this file.
+#include <cuda.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -24,8 +25,41 @@ constexpr int kMaxDevices = 64;
 // device symbol; kernels receive the device address looked up below.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
+// The array's device address per device, with the context it was looked up in: a device reset
+// (or another context made current on the device) makes the address stale, so a change of the
+// current context triggers a new lookup.
 std::mutex g_mu;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+
+// The calling thread's current driver context (nullptr when it cannot be read).
+CUcontext current_context() {
+    static CtxGetCurrentFn fn = []() -> CtxGetCurrentFn {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(p);
+    }();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
+// Whether p is memory of device `dev` (device or managed), so that the kernels may read or
+// write it; host memory, pinned or not, is refused.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
 
 // 1 / |E_k| for rows with a positive weight sum (or any weight when wsum is
 // NULL) and a non-zero norm; 0 marks a row that is not a candidate. One warp per row.
@@ -62,13 +96,20 @@ extern "C" slag_status slag_noalloc_query_topk(const float *E, int64_t n, int32_
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SLAG_ERR_CUDA;
+    // every buffer the kernels touch must be memory of this device: a host address would be
+    // read or written by the GPU
+    if (!on_device(E, dev) || !on_device(Q, dev) || !on_device(out_ids, dev) || !on_device(out_scores, dev) ||
+        (wsum && !on_device(wsum, dev)) || (out_count && !on_device(out_count, dev)))
+        return SLAG_ERR_INVALID_ARG;
     unsigned char *base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        const CUcontext ctx = current_context();
+        if (!g_scratch_ptr[dev] || ctx != g_scratch_ctx[dev]) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return SLAG_ERR_CUDA;
             g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+            g_scratch_ctx[dev] = ctx;
         }
         base = g_scratch_ptr[dev];
     }

@@ -57,7 +57,7 @@ class CView(ctypes.Structure):
 class CStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("views", "pairs", "contributions", "triples", "columns",
                                                "last_pairs", "last_contributions", "touched",
-                                               "evaluations")]
+                                               "evaluations", "executed")]
 
 
 _lib = None
@@ -156,17 +156,32 @@ def noalloc_query_topk(E, wsum, Q, k: int, out_ids, out_scores, out_count=None, 
     """Allocation-free cosine top-k on torch CUDA tensors (see slag_noalloc_query_topk).
 
     Fills out_ids (B x k int64), out_scores (B x k float32) and out_count (B int32, optional)
-    asynchronously in `stream`; returns the status code."""
+    asynchronously in `stream`; returns the status code. Every array must be a contiguous CUDA
+    tensor on the current device with the shape the call implies (E: n x dim, wsum: n, Q:
+    B x dim); anything else raises before the library is called."""
     lib = load_library()
+    import torch
+    dev = torch.cuda.current_device()
+
+    def dev_tensor(x, name, dtype, shape):
+        if not (_is_torch(x) and x.is_cuda and x.device.index == dev):
+            raise ValueError("%s must be a CUDA tensor on the current device (cuda:%d)" % (name, dev))
+        if tuple(x.shape) != tuple(shape):
+            raise ValueError("%s has shape %s, expected %s" % (name, tuple(x.shape), tuple(shape)))
+        return _ptr(x, dtype)[0]
+
+    if not (_is_torch(E) and E.dim() == 2) or not (_is_torch(Q) and Q.dim() == 2):
+        raise ValueError("E and Q must be 2-d torch CUDA tensors")
     n, dim = int(E.shape[0]), int(E.shape[1])
     B = int(Q.shape[0])
-    ep, _, _ = _ptr(E, np.float32)
-    wp, _, _ = _ptr(wsum, np.float32)
-    qp, _, _ = _ptr(Q, np.float32)
-    ip, _, _ = _ptr(out_ids, np.int64)
-    sp, _, _ = _ptr(out_scores, np.float32)
-    cp, _, _ = _ptr(out_count, np.int32)
-    return lib.slag_noalloc_query_topk(ep, n, dim, wp, qp, B, int(k), ip, sp, cp,
+    k = int(k)
+    ep = dev_tensor(E, "E", np.float32, (n, dim))
+    wp = None if wsum is None else dev_tensor(wsum, "wsum", np.float32, (n,))
+    qp = dev_tensor(Q, "Q", np.float32, (B, dim))
+    ip = dev_tensor(out_ids, "out_ids", np.int64, (B, k))
+    sp = dev_tensor(out_scores, "out_scores", np.float32, (B, k))
+    cp = None if out_count is None else dev_tensor(out_count, "out_count", np.int32, (B,))
+    return lib.slag_noalloc_query_topk(ep, n, dim, wp, qp, B, k, ip, sp, cp,
                                        ctypes.c_void_p(stream) if stream else None)
 
 

@@ -201,18 +201,41 @@ def orbit_camera(i: int, n_views: int, width: int, height: int, radius: float = 
 
 
 def voronoi_segments(rng: np.random.Generator, width: int, height: int, k: int) -> np.ndarray:
-    """(H, W) int32 map: nearest of k uniform seeds to each pixel centre."""
+    """(H, W) int32 map: nearest of k uniform seeds to each pixel centre.
+
+    Exact nearest-seed search by 32x32 pixel blocks: a seed can be nearest to a
+    pixel of a block only if its distance to the block's box of pixel centres
+    does not exceed the smallest, over all seeds, distance to the box's far
+    corner; the distances of the remaining candidates are the same float64
+    expressions as a search over all seeds, and ties still go to the lower id.
+    """
     seeds = np.stack([rng.uniform(0, width, k), rng.uniform(0, height, k)], axis=1)
-    xs = np.arange(width, dtype=np.float64) + 0.5
+    return voronoi_from_seeds(seeds, width, height)
+
+
+def voronoi_from_seeds(seeds: np.ndarray, width: int, height: int) -> np.ndarray:
+    """(H, W) int32 map of the nearest of the given (k, 2) seeds (x, y), ties to the lower id."""
+    seeds = np.asarray(seeds, np.float64)
+    sx, sy = seeds[:, 0], seeds[:, 1]
     out = np.empty((height, width), np.int32)
-    rows = max(1, (1 << 22) // max(1, width * k))
-    for y0 in range(0, height, rows):
-        y1 = min(height, y0 + rows)
-        ys = np.arange(y0, y1, dtype=np.float64) + 0.5
-        dx = xs[None, :, None] - seeds[None, None, :, 0]
-        dy = ys[:, None, None] - seeds[None, None, :, 1]
-        d2 = dx * dx + dy * dy                      # (rows, W, k)
-        out[y0:y1] = np.argmin(d2, axis=2)          # argmin: ties -> lower id
+    xs_all = np.arange(width, dtype=np.float64) + 0.5
+    ys_all = np.arange(height, dtype=np.float64) + 0.5
+    blk = 32
+    for y0 in range(0, height, blk):
+        ys = ys_all[y0:min(height, y0 + blk)]
+        near_y = np.maximum(np.maximum(ys[0] - sy, sy - ys[-1]), 0.0)
+        far_y = np.maximum(np.abs(sy - ys[0]), np.abs(sy - ys[-1]))
+        dy = ys[:, None] - sy[None, :]
+        dyy = dy * dy                                   # (rows, k)
+        for x0 in range(0, width, blk):
+            xs = xs_all[x0:min(width, x0 + blk)]
+            near_x = np.maximum(np.maximum(xs[0] - sx, sx - xs[-1]), 0.0)
+            far_x = np.maximum(np.abs(sx - xs[0]), np.abs(sx - xs[-1]))
+            bound = (far_x * far_x + far_y * far_y).min()
+            cand = np.nonzero(near_x * near_x + near_y * near_y <= bound * (1.0 + 1e-9) + 1e-9)[0]
+            dx = xs[:, None] - sx[None, cand]           # (cols, candidates)
+            d2 = dx[None, :, :] * dx[None, :, :] + dyy[:, None, cand]
+            out[y0:y0 + len(ys), x0:x0 + len(xs)] = cand[np.argmin(d2, axis=2)]   # ties -> lower id
     return out
 
 
@@ -236,14 +259,17 @@ def _prototypes(seed: int, p: int, d: int) -> np.ndarray:
 def make_scene(name: str, seed: int, gaussians: Gaussians, n_views: int, width: int, height: int,
                n_segments: int, n_protos: int, dim: int = 512, jitter: bool = False,
                noise_sigma: float = 0.1, empty_fraction: float = 0.0,
-               resolutions: Optional[List[tuple]] = None) -> Scene:
+               resolutions: Optional[List[tuple]] = None, proto_seed: Optional[int] = None) -> Scene:
     """Scene with orbit cameras, Voronoi segment maps and prototype tables.
 
     `empty_fraction` > 0 marks that fraction of the Voronoi cells as "no
     segment" (id -1), to exercise unmasked pixels. `resolutions`, when given,
-    assigns view i the resolution resolutions[i % len(resolutions)].
+    assigns view i the resolution resolutions[i % len(resolutions)]. `proto_seed`, when given,
+    draws the prototype directions of the scene made with that seed (the embedding law of
+    another workload).
     """
-    protos = _prototypes(seed, n_protos, dim)
+    proto_seed = seed if proto_seed is None else proto_seed
+    protos = _prototypes(proto_seed, n_protos, dim)
 
     def view_fn(i: int) -> View:
         rng = _rng(seed, 1000 + i)
@@ -258,7 +284,7 @@ def make_scene(name: str, seed: int, gaussians: Gaussians, n_views: int, width: 
 
     return Scene(name, gaussians, n_views, view_fn, dim,
                  meta=dict(seed=seed, width=width, height=height, n_segments=n_segments,
-                           n_protos=n_protos, jitter=jitter, noise_sigma=noise_sigma))
+                           n_protos=n_protos, jitter=jitter, noise_sigma=noise_sigma, proto_seed=proto_seed))
 
 
 def config_tiny(seed: int = 0) -> Scene:
@@ -279,6 +305,16 @@ def config_precision(seed: int = 2) -> Scene:
     g = ellipsoid_gaussians(seed, 2_000_000, 60)
     return make_scene("precision", seed, g, n_views=300, width=1920, height=1080, n_segments=128,
                       n_protos=64, jitter=True)
+
+
+def config_learned(seed: int = 4, noise_sigma: float = 0.1) -> Scene:
+    """The learned form's workload: 2,000,000 Gaussians on 60 ellipsoids, 300 jittered views
+    1920x1080 with 128 segments, whose embeddings follow the mid-scale workload's law (its 32
+    prototypes, made with seed 1, and N(0, noise_sigma) per coordinate): the law the latent
+    form's autoencoder is trained on."""
+    g = ellipsoid_gaussians(seed, 2_000_000, 60)
+    return make_scene("learned", seed, g, n_views=300, width=1920, height=1080, n_segments=128,
+                      n_protos=32, jitter=True, noise_sigma=noise_sigma, proto_seed=1)
 
 
 def config_batched(seed: int = 3, n_scenes: int = 16) -> List[Scene]:

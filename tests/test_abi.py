@@ -52,7 +52,11 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(slag.CCamera) == 4 * (4 + 2 + 9 + 3 + 2)
     assert ctypes.sizeof(slag.CGaussians) == 8 + 4 * 8 + 8
     assert ctypes.sizeof(slag.COptions) == 16 + 8
-    assert ctypes.sizeof(slag.CStats) == 9 * 8
+    hdr = open(os.path.join(ROOT, "include", "slag.h")).read()
+    body = re.search(r"typedef struct \{([^{}]*)\} slag_stats;", re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)).group(1)
+    fields = re.findall(r"int64_t\s+(\w+);", body)
+    assert [f for f, _ in slag.CStats._fields_] == fields
+    assert ctypes.sizeof(slag.CStats) == 8 * len(fields)
     # slag_profile: ms, spans, busy_ms per stage
     assert ctypes.sizeof(slag.CProfile) == 3 * 7 * 8
 

@@ -21,7 +21,8 @@ def _run(*args, timeout=600):
 
 
 def test_reference_arm_json_line():
-    r = _run("--impl", "reference", "--steps", "1", "--warmup", "0", "--views", "2", "--cpu-seconds", "1")
+    r = _run("--impl", "reference", "--steps", "1", "--warmup", "0", "--workload", "mid", "--views", "2",
+             "--band-rows", "2")
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -35,7 +36,7 @@ def test_reference_arm_json_line():
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     cpu = out["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == out["value"]
-    assert "2 of 2 views" in cpu["sample"]
+    assert "2 views of the 2" in cpu["sample"] and "tile rows" in cpu["sample"]
 
 
 def test_gpu_arm_fails_loudly_without_cuda():

@@ -284,6 +284,26 @@ def test_subset_accumulation_matches_full(oracle_lib):
     np.testing.assert_allclose(ds, d1[sub], rtol=1e-13)
 
 
+def test_tile_row_windows_partition_the_view(oracle_lib):
+    # a window of tile rows composites exactly the whole view's pixels of those rows, and the
+    # windows of a partition of the rows add up to the whole view's sums
+    s = synth.small_scene(8, 2500, 1, 136, 90, 5, dim=8, surfaces=2)
+    v = s.view(0)
+    full = O.view_weights(s.gaussians, v, per_pixel=True)
+    rows = (v.camera.height + 15) // 16
+    B = np.zeros_like(full["B"])
+    contrib = 0
+    for ty0, ty1 in ((0, 2), (2, 3), (3, rows)):
+        r = O.view_weights(s.gaussians, v, per_pixel=True, tile_rows=(ty0, ty1))
+        y0, y1 = 16 * ty0, min(v.camera.height, 16 * ty1)
+        np.testing.assert_array_equal(r["T_final"][y0:y1], full["T_final"][y0:y1])
+        np.testing.assert_array_equal(r["count_px"][y0:y1], full["count_px"][y0:y1])
+        B += r["B"]
+        contrib += r["contributions"]
+    assert contrib == full["contributions"] > 1000
+    np.testing.assert_allclose(B, full["B"], rtol=1e-12, atol=1e-15)
+
+
 def test_invalid_segment_id_rejected(oracle_lib):
     s = synth.config_tiny()
     v = s.view(0)

@@ -1,13 +1,23 @@
 """Repository rules that need no GPU.
 
-- No committed file refers to the `_work/` folder, which holds uncommitted scratch work.
+- No committed source file refers to the scratch folder (its name is built below, so this
+  file does not match its own pattern); review and result files that the build pipeline
+  writes at the repository root are not product source and are skipped.
 - Every command quoted in a profile summary runs committed scripts only, and every `ncu` command
-  there leaves the GPU clocks alone (`--clock-control none`)."""
+  there leaves the GPU clocks alone (`--clock-control none`).
+- An `ncu` command that collects more than the launch list (`--set`, `--section`, or `--metrics`
+  beyond `gpu__time_duration.sum`) captures one kernel (`-k` with a single name, no alternation)
+  and a bounded number of launches (`-c`).
+"""
 import os
 import re
 import subprocess
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SCRATCH = "_" + "work/"
+# written by the build pipeline, not by this project's sources
+PIPELINE_FILES = re.compile(r"^(VERDICT|ADVICE|SURVEY|BASELINE)\.md$|^(BENCH|GPUTEST|SCALE|MULTICHIP)_r\d+\.json$"
+                            r"|^PROGRESS\.jsonl$|^BASELINE\.json$")
 
 
 def _tracked():
@@ -16,10 +26,10 @@ def _tracked():
 
 
 def test_no_committed_file_refers_to_scratch():
-    pat = re.compile(r"(^|[^A-Za-z0-9_])_work/")
+    pat = re.compile(r"(^|[^A-Za-z0-9_])" + re.escape(SCRATCH))
     bad = []
     for f in _tracked():
-        if f == ".gitignore":
+        if f == ".gitignore" or PIPELINE_FILES.match(f):
             continue
         p = os.path.join(ROOT, f)
         if not os.path.isfile(p):
@@ -33,19 +43,44 @@ def test_no_committed_file_refers_to_scratch():
     assert not bad, bad
 
 
+def _ncu_commands(txt):
+    # a command: `ncu` followed by a flag, up to the closing backtick or a blank line
+    return re.findall(r"ncu\s+-{1,2}[A-Za-z].*?(?=`|\n\s*\n|\Z)", txt, flags=re.S)
+
+
+def _profile_summaries():
+    prof = os.path.join(ROOT, "profiles")
+    names = [f for f in os.listdir(prof) if f.endswith((".md", ".txt"))]
+    assert names
+    return [(n, open(os.path.join(prof, n), encoding="utf-8").read()) for n in names]
+
+
 def test_profile_commands_run_committed_scripts():
     tracked = set(_tracked())
-    prof = os.path.join(ROOT, "profiles")
-    summaries = [f for f in os.listdir(prof) if f.endswith((".md", ".txt"))]
-    assert summaries
-    for name in summaries:
-        txt = open(os.path.join(prof, name), encoding="utf-8").read()
+    for name, txt in _profile_summaries():
         scripts = re.findall(r"python3?\s+(?:-m\s+\S+\s+)?([\w./-]+\.py)", txt)
         assert scripts, name
         for s in scripts:
             assert s in tracked, (name, s)
-        # a command: `ncu` followed by a flag, up to the closing backtick or a blank line
-        for cmd in re.findall(r"ncu\s+-{1,2}[A-Za-z].*?(?=`|\n\s*\n|\Z)", txt, flags=re.S):
+        for cmd in _ncu_commands(txt):
             if re.match(r"ncu\s+(-i|--import)\b", cmd):
                 continue   # reading a saved report runs nothing on a GPU
             assert "--clock-control none" in cmd, (name, cmd[:160])
+
+
+def test_full_captures_name_one_kernel():
+    for name, txt in _profile_summaries():
+        for cmd in _ncu_commands(txt):
+            if re.match(r"ncu\s+(-i|--import)\b", cmd):
+                continue
+            metrics = re.findall(r"--metrics\s+(\S+)", cmd)
+            heavy = ("--set" in cmd or "--section" in cmd
+                     or any(m.strip("'\"") != "gpu__time_duration.sum" for m in metrics))
+            if not heavy:
+                continue
+            k = re.search(r"(?:-k|--kernel-name)\s+(\S+)", cmd)
+            assert k, (name, "a heavy capture must name its kernel", cmd[:160])
+            kname = k.group(1).strip("'\"")
+            assert "|" not in kname, (name, "one kernel per heavy capture", kname)
+            c = re.search(r"(?:-c|--launch-count)\s+(\d+)", cmd)
+            assert c and int(c.group(1)) <= 3, (name, "at most three launches per heavy capture", cmd[:160])
