@@ -251,6 +251,56 @@ slag_status slag_get_stats(const slag_ctx *ctx, slag_stats *out);
 const char *slag_last_error(const slag_ctx *ctx);
 void slag_destroy(slag_ctx *ctx);
 
+/* ---- accumulated state: checkpoint, resume, merge -------------------------- */
+
+/* The aggregation sums are additive over views (Aggregation step: numerator
+ * and denominator of E_k are sums over views i), which is what lets the
+ * paper's multi-GPU section split the views across GPUs and sum the
+ * per-GPU tensors. A context's accumulated state -- every view's sparse
+ * (Gaussian, view-segment, W) weights, the stored segment embeddings, the
+ * compensated sums of w per Gaussian and the counters -- can therefore be
+ * saved, restored into another context over the same Gaussians, and merged
+ * with the state of a disjoint set of views. Format (little-endian):
+ *   header (96 bytes): "SLAGSTAT", uint32 version = 1, uint32 dim, int64 n,
+ *     int64 columns, int64 triples Z, uint64 fingerprint of the Gaussian set,
+ *     int64 views, pairs, contributions, evaluations, executed, int32
+ *     weight_mode, int32 reserved;
+ *   float32 segment embeddings, columns x dim;
+ *   float32 sum w as (hi, lo, overflow) planes, 3 x n, in caller order (the
+ *     sum is hi + lo + overflow; hi + lo is a compensated sum);
+ *   Z x uint32 caller index, Z x uint32 column, Z x float32 W.
+ * Size: 96 + 4 columns dim + 12 n + 12 Z bytes. */
+
+/* Writes the context's state (after joining the views in flight) into buf
+ * (host, cap bytes). *out_bytes (nullable) receives its size; with buf NULL
+ * only the size is returned. Errors: CAPACITY when cap is smaller than the
+ * state or the triple log overflowed in some view; OOM; CUDA. */
+slag_status slag_save_state(slag_ctx *ctx, void *buf, int64_t cap, int64_t *out_bytes);
+
+/* Replaces the context's accumulated state by the one in buf (host, `bytes`
+ * bytes): as slag_reset, then slag_merge_state. Later views add to it. */
+slag_status slag_load_state(slag_ctx *ctx, const void *buf, int64_t bytes);
+
+/* Adds the state in buf (host) to the context's: its segment embeddings are
+ * appended after the context's columns, its triples with their columns
+ * shifted past them, and its sums of w added with compensation. The result
+ * equals one context that was given both sets of views (the two sets should be
+ * disjoint, or views are counted twice). Errors: INVALID_ARG for a buffer that
+ * is not a state, or a state of another n, dim, weight mode or Gaussian set,
+ * or a triple whose index or column is out of range (its weight is dropped;
+ * reset the context); CAPACITY beyond 2^32 columns; OOM; CUDA. The caller's
+ * buffer is free when the call returns. */
+slag_status slag_merge_state(slag_ctx *ctx, const void *buf, int64_t bytes);
+
+/* Merges two states on the host, without a context or a GPU (for reducing the
+ * states of view-sharded jobs where they are stored): out (host, cap bytes)
+ * receives the state of both sets of views, a's columns first. *out_bytes
+ * (nullable) receives the size; with out NULL only the size is returned.
+ * Errors: INVALID_ARG (malformed, or states of other n, dim, weight mode or
+ * Gaussian set); CAPACITY (cap too small, or beyond 2^32 columns). */
+slag_status slag_state_merge_host(const void *a, int64_t a_bytes, const void *b, int64_t b_bytes, void *out,
+                                  int64_t cap, int64_t *out_bytes);
+
 /* ---- diagnostics: the integer stages and per-pixel compositing state ---- */
 
 /* Tile binning of one view without compositing. out_touched: n uint32 (host,
@@ -263,6 +313,34 @@ void slag_destroy(slag_ctx *ctx);
  * to out_list). */
 slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_touched,
                           int64_t *out_P, int32_t *out_list, int64_t list_cap, int64_t *out_ranges);
+
+/* The bins of one view at the granularity the compositing uses, without
+ * compositing (the integer stages as they run in slag_add_view). A bin is a
+ * 2^bin_shift x 2^bin_shift square of 16x16 tiles: bin_shift 0 gives the
+ * lists of slag_bin_view, bin_shift 2 the 4x4-tile super-tiles slag_add_view
+ * composites from (other values: INVALID_ARG). A Gaussian belongs to every
+ * bin its tile rectangle meets. *out_P: the number of (Gaussian, bin) pairs;
+ * out_list (host, nullable, list_cap entries): the caller index of each pair,
+ * grouped by bin in row-major bin order, each bin's Gaussians in ascending
+ * (float32 depth, Gaussian index); out_ranges (host, nullable): bins x 2 int64
+ * [start, end) into out_list, bins = ceil(tiles_x / 2^bin_shift) x
+ * ceil(tiles_y / 2^bin_shift); an empty bin is [e, e). Errors: as
+ * slag_bin_view. */
+slag_status slag_bin_view_bins(slag_ctx *ctx, const slag_camera *cam, int32_t bin_shift, int64_t *out_P,
+                               int32_t *out_list, int64_t list_cap, int64_t *out_ranges);
+
+/* The per-tile Gaussian sequences the compositing kernel of slag_add_view
+ * stages from the super-tile lists (its filter of each super-tile's list by
+ * tile rectangle), recorded by the kernel itself; no view is added. The trace
+ * keeps staging after every pixel of a tile has stopped, so that each tile's
+ * whole sequence is visible. *out_P: the number of Gaussian-tile pairs;
+ * out_list (host, nullable, list_cap >= P entries): caller indices, tile
+ * after tile in row-major order; out_ranges (host, nullable): tiles x 2 int64,
+ * [start, start + staged) of each tile, start being the tile's place in the
+ * flat per-tile lists of slag_bin_view. Errors: as slag_bin_view; CAPACITY
+ * when a tile staged more Gaussians than its flat list holds. */
+slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t *out_P, int32_t *out_list,
+                                 int64_t list_cap, int64_t *out_ranges);
 
 /* Composite one view without adding it: per pixel (height x width, host,
  * each nullable) the final transmittance, the sum of the recorded weights

@@ -143,9 +143,74 @@ __global__ void repack_keys_k(const uint64_t *keys_in, uint64_t *keys_out, const
     if (w_in) w_out[i] = w_in[i];
 }
 
+// Saved state: each log entry as (caller index, column).
+__global__ void state_unpack_k(const uint64_t *__restrict__ keys, int64_t Z, const uint32_t *__restrict__ orig_of_int,
+                               uint32_t *__restrict__ gauss, uint32_t *__restrict__ col) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Z) return;
+    const uint64_t k = keys[i];
+    const uint32_t g = (uint32_t)(((k >> 39) << 7) | (k & 127ull));
+    gauss[i] = orig_of_int[g];
+    col[i] = (uint32_t)((k >> 7) & 0xffffffffull);
+}
+
+// Merged state: entries (caller index, column, W) appended to the log, the columns shifted past
+// the context's own; an index or column out of range is not written and sets *bad.
+__global__ void state_pack_k(const uint32_t *__restrict__ gauss, const uint32_t *__restrict__ col,
+                             const float *__restrict__ w, int64_t Z, const uint32_t *__restrict__ int_of_orig,
+                             int64_t n, uint32_t col_shift, uint32_t cols_in, uint64_t *__restrict__ log_key,
+                             float *__restrict__ log_w, uint32_t *bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Z) return;
+    const uint32_t c = gauss[i], j = col[i];
+    if (c >= (uint64_t)n || j >= cols_in) {
+        atomicOr(bad, 1u);
+        log_key[i] = pack_key(0u, col_shift);   // a harmless entry: weight 0 on a valid column
+        log_w[i] = 0.f;
+        return;
+    }
+    log_key[i] = pack_key(int_of_orig[c], col_shift + j);
+    log_w[i] = w[i];
+}
+
+// Merged state: the compensated sums (hi, lo) and the overflow sums of another state added,
+// per Gaussian (internal order).
+__global__ void state_sums_k(float *__restrict__ hi, float *__restrict__ lo, float *__restrict__ ovf,
+                             const float *__restrict__ bhi, const float *__restrict__ blo,
+                             const float *__restrict__ bovf, int64_t n) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const float a = hi[g], b = bhi[g];
+    const float t = a + b;
+    const float err = fabsf(a) >= fabsf(b) ? (a - t) + b : (b - t) + a;
+    hi[g] = t;
+    lo[g] = (lo[g] + blo[g]) + err;
+    ovf[g] = ovf[g] + bovf[g];
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+void launch_state_unpack(const uint64_t *keys, int64_t Z, const uint32_t *orig_of_int, uint32_t *gauss, uint32_t *col,
+                         cudaStream_t st) {
+    if (Z <= 0) return;
+    state_unpack_k<<<blocks_for(Z, 256), 256, 0, st>>>(keys, Z, orig_of_int, gauss, col); note_launch();
+}
+
+void launch_state_pack(const uint32_t *gauss, const uint32_t *col, const float *w, int64_t Z,
+                       const uint32_t *int_of_orig, int64_t n, uint32_t col_shift, uint32_t cols_in,
+                       uint64_t *log_key, float *log_w, uint32_t *bad, cudaStream_t st) {
+    if (Z <= 0) return;
+    state_pack_k<<<blocks_for(Z, 256), 256, 0, st>>>(gauss, col, w, Z, int_of_orig, n, col_shift, cols_in, log_key,
+                                                     log_w, bad); note_launch();
+}
+
+void launch_state_sums(float *hi, float *lo, float *ovf, const float *bhi, const float *blo, const float *bovf,
+                       int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    state_sums_k<<<blocks_for(n, 256), 256, 0, st>>>(hi, lo, ovf, bhi, blo, bovf, n); note_launch();
+}
 
 void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st) {
     hash_init_k<<<blocks_for(n, 256), 256, 0, st>>>(hash, n); note_launch();

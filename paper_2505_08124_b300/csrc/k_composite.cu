@@ -370,6 +370,9 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
     int cursor = (int)rg.x;
     float *wb_warp = sm.wbuf[w];
     int qn = 0;   // this warp's queued records
+    // diagnostics: record every staged Gaussian, and stage the whole list
+    const bool trace = kDebug && a.dbg_list != nullptr;
+    int staged = 0;
 
     // candidates of the next fill round, prefetched into registers
     constexpr int kPer = kRound / kThreads;
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
 
     while (true) {
         int live = __syncthreads_count(T0 > 0.f || T1 > 0.f);   // also: the previous batch is consumed
-        if (live == 0 || cursor >= end) break;
+        if ((live == 0 && !trace) || cursor >= end) break;
         // fill: rounds of kRound candidates until at least kBatch - kRound records are
         // staged; the records of the hits are copied asynchronously, the next round's
         // candidates are loaded while this round is compacted
@@ -422,6 +425,11 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
                     cp_async16(&sm.rec_a[pos], a.srec_a + r[k]);
                     cp_async16(&sm.rec_b[pos], a.srec_b + r[k]);
                     cp_async4(&sm.gid[pos], a.sgid + r[k]);
+                    if (trace) {
+                        const int64_t at = a.dbg_off[tile] + staged + pos;
+                        if (at < a.dbg_off[tile + 1]) a.dbg_list[at] = r[k];
+                        else atomicOr(a.dbg_bad, 1u);
+                    }
                 }
             }
             nb += nh;
@@ -430,6 +438,7 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
         }
         cp_async_wait_all();
         __syncthreads();
+        staged += nb;
         if (nb == 0) continue;
         // records -> tile-local exponent polynomials. With X = px + 0.5 - ox, mx = mu'x - ox (and
         // Y, my likewise), the exponent q2 + log2 o = a' dx^2 + b' dx dy + c' dy^2 + log2 o with
@@ -624,6 +633,7 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
         }
     }
     if (a.accumulate && a.recs && qn > 0) flush_warp(a, sm, w, lane, qn);
+    if (trace && tid == 0) a.dbg_staged[tile] = (uint32_t)staged;
 
     if (inside0) {
         const int64_t pi = (int64_t)py0 * W + px0;

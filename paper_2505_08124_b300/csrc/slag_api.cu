@@ -1555,6 +1555,315 @@ slag_status slag_export_partitions(slag_ctx *ctx, const char *dir, int32_t cells
     return SLAG_OK;
 }
 
+// ---- accumulated state: save, load, merge --------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+// Serialised state (little-endian), see slag_save_state in slag.h.
+struct StateHeader {
+    char magic[8];                 // "SLAGSTAT"
+    uint32_t version;              // 1
+    uint32_t dim;
+    int64_t n;
+    int64_t columns;
+    int64_t triples;
+    uint64_t fingerprint;          // of the Gaussian set the state belongs to
+    int64_t views, pairs, contributions, evaluations, executed;
+    int32_t weight_mode;
+    int32_t reserved;
+};
+static_assert(sizeof(StateHeader) == 96, "state header layout");
+constexpr char kStateMagic[8] = {'S', 'L', 'A', 'G', 'S', 'T', 'A', 'T'};
+
+int64_t state_bytes(int64_t n, int64_t D, int64_t columns, int64_t triples) {
+    return (int64_t)sizeof(StateHeader) + 4 * columns * D + 12 * n + 12 * triples;
+}
+
+// Whether buf holds a well-formed state of `bytes` bytes; fills *h.
+bool parse_state(const void *buf, int64_t bytes, StateHeader *h) {
+    if (!buf || bytes < (int64_t)sizeof(StateHeader)) return false;
+    memcpy(h, buf, sizeof(StateHeader));
+    if (memcmp(h->magic, kStateMagic, 8) != 0 || h->version != 1) return false;
+    if (h->n < 1 || h->dim < 1 || h->columns < 0 || h->triples < 0 || h->columns >= (1LL << 32)) return false;
+    return state_bytes(h->n, h->dim, h->columns, h->triples) == bytes;
+}
+
+// FNV-1a over the Gaussian set in the context's internal layout (deterministic for a given input).
+slag_status gaussian_fingerprint(slag_ctx *ctx, uint64_t *out) {
+    const int64_t n = ctx->n;
+    std::vector<float4> a((size_t)n), b((size_t)n);
+    std::vector<float2> c((size_t)n);
+    CK(cudaMemcpyAsync(a.data(), ctx->mean_op, sizeof(float4) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b.data(), ctx->cov_a, sizeof(float4) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(c.data(), ctx->cov_b, sizeof(float2) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    uint64_t hsh = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t len) {
+        const unsigned char *q = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < len; ++i) hsh = (hsh ^ q[i]) * 1099511628211ull;
+    };
+    mix(&n, sizeof(n));
+    mix(a.data(), sizeof(float4) * (size_t)n);
+    mix(b.data(), sizeof(float4) * (size_t)n);
+    mix(c.data(), sizeof(float2) * (size_t)n);
+    *out = hsh;
+    return SLAG_OK;
+}
+
+// Joins every view in flight and reads the device totals into ctx->hc->totals.
+slag_status join_and_read_totals(slag_ctx *ctx) {
+    cudaStream_t st = ctx->stream;
+    slag_status s = launch_deferred_view(ctx);
+    if (s != SLAG_OK) return s;
+    CK(join_views(ctx));
+    launch_copy_words(ctx->totals, ctx->hc_dev->totals, kTotals * sizeof(unsigned long long), st);
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (ctx->hc->totals[2]) ctx->log_overflowed = true;
+    if (ctx->log_overflowed) return fail(ctx, SLAG_ERR_CAPACITY, "the triple log overflowed in some view");
+    return SLAG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slag_status slag_save_state(slag_ctx *ctx, void *buf, int64_t cap, int64_t *out_bytes) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    slag_status s = join_and_read_totals(ctx);
+    if (s != SLAG_OK) return s;
+    cudaStream_t st = ctx->stream;
+    const int64_t n = ctx->n, D = ctx->D, cols = ctx->table_rows;
+    const int64_t Z = (int64_t)ctx->hc->totals[0];
+    const int64_t need = state_bytes(n, D, cols, Z);
+    if (out_bytes) *out_bytes = need;
+    if (!buf) return SLAG_OK;
+    if (cap < need) return fail(ctx, SLAG_ERR_CAPACITY, "state buffer smaller than the state");
+    StateHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kStateMagic, 8);
+    h.version = 1;
+    h.dim = (uint32_t)D;
+    h.n = n;
+    h.columns = cols;
+    h.triples = Z;
+    s = gaussian_fingerprint(ctx, &h.fingerprint);
+    if (s != SLAG_OK) return s;
+    h.views = ctx->stats.views;
+    h.pairs = ctx->stats.pairs;
+    h.contributions = (int64_t)ctx->hc->totals[1];
+    h.evaluations = (int64_t)ctx->hc->totals[3];
+    h.executed = (int64_t)ctx->hc->totals[4];
+    h.weight_mode = ctx->weight_mode;
+    char *out = static_cast<char *>(buf);
+    memcpy(out, &h, sizeof(h));
+    char *p = out + sizeof(h);
+    // the stored segment embeddings
+    if (cols > 0) CK(cudaMemcpyAsync(p, ctx->table, sizeof(float) * (size_t)(cols * D), cudaMemcpyDeviceToHost, st));
+    p += 4 * cols * D;
+    // the compensated sums in caller order
+    std::vector<float> hi((size_t)n), lo((size_t)n), ovf((size_t)n);
+    std::vector<uint32_t> orig((size_t)n);
+    CK(cudaMemcpyAsync(hi.data(), ctx->s_hi, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(lo.data(), ctx->s_lo, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ovf.data(), ctx->s_ovf, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(orig.data(), ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+    // the triples: (caller index, column) unpacked on the device, then W
+    uint32_t *dg = nullptr, *dc = nullptr;
+    if (Z > 0) {
+        cudaError_t e = dalloc(&dg, Z);
+        if (e == cudaSuccess) e = dalloc(&dc, Z);
+        if (e != cudaSuccess) {
+            dfree(dg); dfree(dc);
+            return fail(ctx, SLAG_ERR_OOM, "state: triple staging");
+        }
+        launch_state_unpack(ctx->log_key, Z, ctx->orig_of_int, dg, dc, st);
+    }
+    CK(cudaStreamSynchronize(st));
+    float *fs = reinterpret_cast<float *>(p);
+    for (int64_t g = 0; g < n; ++g) {
+        const uint32_t c = orig[(size_t)g];
+        fs[c] = hi[(size_t)g];
+        fs[n + c] = lo[(size_t)g];
+        fs[2 * n + c] = ovf[(size_t)g];
+    }
+    p += 12 * n;
+    cudaError_t e = cudaSuccess;
+    if (Z > 0) {
+        e = cudaMemcpyAsync(p, dg, sizeof(uint32_t) * (size_t)Z, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p + 4 * Z, dc, sizeof(uint32_t) * (size_t)Z, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p + 8 * Z, ctx->log_w, sizeof(float) * (size_t)Z, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    dfree(dg);
+    dfree(dc);
+    if (e != cudaSuccess) return fail(ctx, SLAG_ERR_CUDA, cudaGetErrorString(e));
+    return SLAG_OK;
+}
+
+slag_status slag_merge_state(slag_ctx *ctx, const void *buf, int64_t bytes) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    StateHeader h;
+    if (!parse_state(buf, bytes, &h)) return fail(ctx, SLAG_ERR_INVALID_ARG, "not a state of this library");
+    if (h.n != ctx->n || (int64_t)h.dim != ctx->D) return fail(ctx, SLAG_ERR_INVALID_ARG, "state of another n or dim");
+    if (h.weight_mode != ctx->weight_mode) return fail(ctx, SLAG_ERR_INVALID_ARG, "state of another weight mode");
+    CK(cudaSetDevice(ctx->device));
+    uint64_t fp = 0;
+    slag_status s = gaussian_fingerprint(ctx, &fp);
+    if (s != SLAG_OK) return s;
+    if (fp != h.fingerprint) return fail(ctx, SLAG_ERR_INVALID_ARG, "state of another Gaussian set");
+    if (ctx->table_rows + h.columns >= (1LL << 32)) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^32 segment columns");
+    s = join_and_read_totals(ctx);
+    if (s != SLAG_OK) return s;
+    cudaStream_t st = ctx->stream;
+    const int64_t n = ctx->n, D = ctx->D;
+    const int64_t used = (int64_t)ctx->hc->totals[0];
+    const int64_t Zb = h.triples;
+    const char *p = static_cast<const char *>(buf) + sizeof(StateHeader);
+    // segment embeddings after the context's own
+    if (h.columns > 0) {
+        if (ctx->table_rows + h.columns > ctx->table_cap / D)
+            CK(grow(ctx->table, ctx->table_cap, (ctx->table_rows + h.columns) * D, st, ctx->table_rows * D));
+        CK(cudaMemcpyAsync(ctx->table + ctx->table_rows * D, p, sizeof(float) * (size_t)(h.columns * D),
+                           cudaMemcpyHostToDevice, st));
+    }
+    p += 4 * h.columns * D;
+    // sums: caller order -> internal order, added with compensation
+    std::vector<uint32_t> orig((size_t)n);
+    CK(cudaMemcpyAsync(orig.data(), ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<float> sums((size_t)(3 * n));
+    const float *fs = reinterpret_cast<const float *>(p);
+    for (int64_t g = 0; g < n; ++g) {
+        const uint32_t c = orig[(size_t)g];
+        sums[(size_t)g] = fs[c];
+        sums[(size_t)(n + g)] = fs[n + c];
+        sums[(size_t)(2 * n + g)] = fs[2 * n + c];
+    }
+    p += 12 * n;
+    float *dsum = nullptr;
+    uint32_t *dg = nullptr, *dc = nullptr, *dbad = nullptr;
+    float *dw = nullptr;
+    auto release = [&]() { dfree(dsum); dfree(dg); dfree(dc); dfree(dw); dfree(dbad); };
+    cudaError_t e = dalloc(&dsum, 3 * n);
+    if (e == cudaSuccess) e = dalloc(&dbad, 1);
+    if (e == cudaSuccess && Zb > 0) e = dalloc(&dg, Zb);
+    if (e == cudaSuccess && Zb > 0) e = dalloc(&dc, Zb);
+    if (e == cudaSuccess && Zb > 0) e = dalloc(&dw, Zb);
+    // room in the log for the other state's triples
+    if (e == cudaSuccess && used + Zb > ctx->log_cap) {
+        int64_t c1 = ctx->log_cap, c2 = ctx->log_cap;
+        e = grow(ctx->log_key, c1, used + Zb, st, used);
+        if (e == cudaSuccess) e = grow(ctx->log_w, c2, used + Zb, st, used);
+        if (e == cudaSuccess) ctx->log_cap = c1;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dsum, sums.data(), sizeof(float) * (size_t)(3 * n), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess && Zb > 0) {
+        e = cudaMemcpyAsync(dg, p, sizeof(uint32_t) * (size_t)Zb, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dc, p + 4 * Zb, sizeof(uint32_t) * (size_t)Zb, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dw, p + 8 * Zb, sizeof(float) * (size_t)Zb, cudaMemcpyHostToDevice, st);
+    }
+    uint32_t bad = 0;
+    if (e == cudaSuccess) {
+        launch_state_pack(dg, dc, dw, Zb, ctx->int_of_orig, n, (uint32_t)ctx->table_rows, (uint32_t)h.columns,
+                          ctx->log_key + used, ctx->log_w + used, dbad, st);
+        launch_state_sums(ctx->s_hi, ctx->s_lo, ctx->s_ovf, dsum, dsum + n, dsum + 2 * n, n, st);
+        // the device totals: triples in the log and the counters the state carries
+        unsigned long long *tot = ctx->hc->totals;
+        tot[0] = (unsigned long long)(used + Zb);
+        tot[1] += (unsigned long long)h.contributions;
+        tot[3] += (unsigned long long)h.evaluations;
+        tot[4] += (unsigned long long)h.executed;
+        e = cudaMemcpyAsync(ctx->totals, tot, kTotals * sizeof(unsigned long long), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    release();
+    if (e != cudaSuccess)
+        return fail(ctx, e == cudaErrorMemoryAllocation ? SLAG_ERR_OOM : SLAG_ERR_CUDA, cudaGetErrorString(e));
+    ctx->table_rows += h.columns;
+    ctx->stats.views += h.views;
+    ctx->stats.columns = ctx->table_rows;
+    ctx->stats.pairs += h.pairs;
+    ctx->finalized = false;
+    if (bad) return fail(ctx, SLAG_ERR_INVALID_ARG, "state: a triple names a Gaussian or column out of range "
+                                                    "(its weight was dropped; reset the context)");
+    return SLAG_OK;
+}
+
+slag_status slag_load_state(slag_ctx *ctx, const void *buf, int64_t bytes) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    StateHeader h;
+    if (!parse_state(buf, bytes, &h)) return fail(ctx, SLAG_ERR_INVALID_ARG, "not a state of this library");
+    slag_status s = slag_reset(ctx);
+    if (s != SLAG_OK) return s;
+    return slag_merge_state(ctx, buf, bytes);
+}
+
+slag_status slag_state_merge_host(const void *a, int64_t a_bytes, const void *b, int64_t b_bytes, void *out,
+                                  int64_t cap, int64_t *out_bytes) {
+    StateHeader ha, hb;
+    if (!parse_state(a, a_bytes, &ha) || !parse_state(b, b_bytes, &hb)) return SLAG_ERR_INVALID_ARG;
+    if (ha.n != hb.n || ha.dim != hb.dim || ha.fingerprint != hb.fingerprint || ha.weight_mode != hb.weight_mode)
+        return SLAG_ERR_INVALID_ARG;
+    if (ha.columns + hb.columns >= (1LL << 32)) return SLAG_ERR_CAPACITY;
+    const int64_t n = ha.n, D = ha.dim, ca = ha.columns, cb = hb.columns, za = ha.triples, zb = hb.triples;
+    const int64_t need = state_bytes(n, D, ca + cb, za + zb);
+    if (out_bytes) *out_bytes = need;
+    if (!out) return SLAG_OK;
+    if (cap < need) return SLAG_ERR_CAPACITY;
+    StateHeader h = ha;
+    h.columns = ca + cb;
+    h.triples = za + zb;
+    h.views += hb.views;
+    h.pairs += hb.pairs;
+    h.contributions += hb.contributions;
+    h.evaluations += hb.evaluations;
+    h.executed += hb.executed;
+    const char *pa = static_cast<const char *>(a) + sizeof(StateHeader);
+    const char *pb = static_cast<const char *>(b) + sizeof(StateHeader);
+    char *po = static_cast<char *>(out);
+    memcpy(po, &h, sizeof(h));
+    po += sizeof(h);
+    memcpy(po, pa, (size_t)(4 * ca * D));
+    memcpy(po + 4 * ca * D, pb, (size_t)(4 * cb * D));
+    po += 4 * (ca + cb) * D;
+    pa += 4 * ca * D;
+    pb += 4 * cb * D;
+    const float *sa = reinterpret_cast<const float *>(pa), *sb = reinterpret_cast<const float *>(pb);
+    float *so = reinterpret_cast<float *>(po);
+    for (int64_t g = 0; g < n; ++g) {
+        const float x = sa[g], y = sb[g];
+        const float t = x + y;
+        const float err = std::fabs(x) >= std::fabs(y) ? (x - t) + y : (y - t) + x;
+        so[g] = t;
+        so[n + g] = (sa[n + g] + sb[n + g]) + err;
+        so[2 * n + g] = sa[2 * n + g] + sb[2 * n + g];
+    }
+    po += 12 * n;
+    pa += 12 * n;
+    pb += 12 * n;
+    // triples: a's, then b's with columns shifted past a's
+    uint32_t *og = reinterpret_cast<uint32_t *>(po), *oc = og + (za + zb);
+    float *ow = reinterpret_cast<float *>(oc + (za + zb));
+    const uint32_t *ag = reinterpret_cast<const uint32_t *>(pa), *ac = ag + za;
+    const float *aw = reinterpret_cast<const float *>(ac + za);
+    const uint32_t *bg = reinterpret_cast<const uint32_t *>(pb), *bc = bg + zb;
+    const float *bw = reinterpret_cast<const float *>(bc + zb);
+    memcpy(og, ag, (size_t)(4 * za));
+    memcpy(og + za, bg, (size_t)(4 * zb));
+    memcpy(oc, ac, (size_t)(4 * za));
+    for (int64_t i = 0; i < zb; ++i) oc[za + i] = bc[i] + (uint32_t)ca;
+    memcpy(ow, aw, (size_t)(4 * za));
+    memcpy(ow + za, bw, (size_t)(4 * zb));
+    return SLAG_OK;
+}
+
 slag_status slag_set_latent(slag_ctx *ctx, const float *params) {
     if (!ctx) return SLAG_ERR_INVALID_ARG;
     if (!params) return fail(ctx, SLAG_ERR_INVALID_ARG, "params is NULL");
@@ -1721,7 +2030,29 @@ slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset) {
     return SLAG_OK;
 }
 
-slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_touched, int64_t *out_P,
+}  // extern "C"
+
+namespace {
+
+// The pair list of one binning (depth ranks) -> caller indices, on the host.
+slag_status ranks_to_callers(slag_ctx *ctx, cudaStream_t st, const uint32_t *d_ranks, int64_t count,
+                             const uint32_t *sgid, int32_t *out) {
+    const int64_t n = ctx->n;
+    std::vector<uint32_t> h_list((size_t)(count > 0 ? count : 1)), h_orig((size_t)n), h_gid((size_t)n);
+    if (count > 0) CK(cudaMemcpyAsync(h_list.data(), d_ranks, sizeof(uint32_t) * count, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_gid.data(), sgid, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_orig.data(), ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < count; ++i) {
+        const uint32_t r = h_list[(size_t)i];
+        out[i] = r < (uint32_t)n ? (int32_t)h_orig[h_gid[r]] : -1;
+    }
+    return SLAG_OK;
+}
+
+// Binning of one view at 2^shift x 2^shift tiles per bin, without compositing (slag_bin_view,
+// slag_bin_view_bins).
+slag_status bin_view_diag(slag_ctx *ctx, const slag_camera *cam, int shift, uint32_t *out_touched, int64_t *out_P,
                           int32_t *out_list, int64_t list_cap, int64_t *out_ranges) {
     if (!ctx) return SLAG_ERR_INVALID_ARG;
     slag_status s = check_camera(ctx, cam);
@@ -1736,60 +2067,164 @@ slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_t
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, &sgid, 0);
+    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, &sgid, shift);
     if (s != SLAG_OK) return s;
     if (out_P) *out_P = P;
     const int64_t n = ctx->n;
-    const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
+    const int64_t bins = (int64_t)(((cp.tiles_x - 1) >> shift) + 1) * (((cp.tiles_y - 1) >> shift) + 1);
     if (out_touched) {
         // tiles touched per Gaussian, caller order: depth-sorted values hold internal indices
-        uint32_t *h_orig = (uint32_t *)malloc(sizeof(uint32_t) * n);
-        uint2 *h_rect = (uint2 *)malloc(sizeof(uint2) * n);
-        if (!h_orig || !h_rect) {
-            free(h_orig); free(h_rect);
-            return fail(ctx, SLAG_ERR_OOM, "host allocation");
-        }
-        CK(cudaMemcpyAsync(h_rect, vs.rect, sizeof(uint2) * n, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(h_orig, ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+        std::vector<uint32_t> h_orig((size_t)n);
+        std::vector<uint2> h_rect((size_t)n);
+        CK(cudaMemcpyAsync(h_rect.data(), vs.rect, sizeof(uint2) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_orig.data(), ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         for (int64_t gI = 0; gI < n; ++gI) {
-            const uint2 rc = h_rect[gI];
-            out_touched[h_orig[gI]] = ((rc.x >> 16) - (rc.x & 0xffffu)) * ((rc.y >> 16) - (rc.y & 0xffffu));
+            const uint2 rc = h_rect[(size_t)gI];
+            out_touched[h_orig[(size_t)gI]] = ((rc.x >> 16) - (rc.x & 0xffffu)) * ((rc.y >> 16) - (rc.y & 0xffffu));
         }
-        free(h_orig); free(h_rect);
     }
     if (out_list) {
         if (list_cap < P) return fail(ctx, SLAG_ERR_CAPACITY, "list_cap < P");
         // list holds depth ranks; map rank -> internal -> caller index on the host
-        uint32_t *h_list = (uint32_t *)malloc(sizeof(uint32_t) * (P > 0 ? P : 1));
-        uint32_t *h_orig = (uint32_t *)malloc(sizeof(uint32_t) * n);
-        uint32_t *h_gid = (uint32_t *)malloc(sizeof(uint32_t) * n);
-        if (!h_list || !h_orig || !h_gid) {
-            free(h_list); free(h_orig); free(h_gid);
-            return fail(ctx, SLAG_ERR_OOM, "host allocation");
-        }
-        if (P > 0) CK(cudaMemcpyAsync(h_list, list, sizeof(uint32_t) * P, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(h_gid, sgid, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(h_orig, ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        for (int64_t i = 0; i < P; ++i) out_list[i] = (int32_t)h_orig[h_gid[h_list[i]]];
-        free(h_list); free(h_orig); free(h_gid);
+        s = ranks_to_callers(ctx, st, list, P, sgid, out_list);
+        if (s != SLAG_OK) return s;
     }
     if (out_ranges) {
-        uint2 *h_r = (uint2 *)malloc(sizeof(uint2) * tiles);
-        if (!h_r) return fail(ctx, SLAG_ERR_OOM, "host allocation");
-        CK(cudaMemcpyAsync(h_r, vs.ranges, sizeof(uint2) * tiles, cudaMemcpyDeviceToHost, st));
+        std::vector<uint2> h_r((size_t)bins);
+        CK(cudaMemcpyAsync(h_r.data(), vs.ranges, sizeof(uint2) * bins, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        // an empty tile is reported as [e, e) with e the end of the tiles before it
+        // an empty bin is reported as [e, e) with e the end of the bins before it
         int64_t at = 0;
-        for (int64_t t = 0; t < tiles; ++t) {
-            if (h_r[t].y > h_r[t].x) at = h_r[t].y;
-            out_ranges[2 * t] = h_r[t].y > h_r[t].x ? (int64_t)h_r[t].x : at;
-            out_ranges[2 * t + 1] = h_r[t].y > h_r[t].x ? (int64_t)h_r[t].y : at;
+        for (int64_t t = 0; t < bins; ++t) {
+            const uint2 r = h_r[(size_t)t];
+            if (r.y > r.x) at = r.y;
+            out_ranges[2 * t] = r.y > r.x ? (int64_t)r.x : at;
+            out_ranges[2 * t + 1] = r.y > r.x ? (int64_t)r.y : at;
         }
-        free(h_r);
     }
     (void)keys;
+    return SLAG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slag_status slag_bin_view(slag_ctx *ctx, const slag_camera *cam, uint32_t *out_touched, int64_t *out_P,
+                          int32_t *out_list, int64_t list_cap, int64_t *out_ranges) {
+    return bin_view_diag(ctx, cam, 0, out_touched, out_P, out_list, list_cap, out_ranges);
+}
+
+slag_status slag_bin_view_bins(slag_ctx *ctx, const slag_camera *cam, int32_t bin_shift, int64_t *out_P,
+                               int32_t *out_list, int64_t list_cap, int64_t *out_ranges) {
+    if (ctx && bin_shift != 0 && bin_shift != kSuperShift)
+        return fail(ctx, SLAG_ERR_INVALID_ARG, "bin_shift must be 0 or the compositing's super-tile shift");
+    return bin_view_diag(ctx, cam, bin_shift, nullptr, out_P, out_list, list_cap, out_ranges);
+}
+
+slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t *out_P, int32_t *out_list,
+                                 int64_t list_cap, int64_t *out_ranges) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    slag_status s = check_camera(ctx, cam);
+    if (s != SLAG_OK) return s;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    s = launch_deferred_view(ctx);
+    if (s != SLAG_OK) return s;
+    CK(join_views(ctx));
+    ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
+    const CamParams cp = cam_params(cam);
+    const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
+    // room per tile: the Gaussians whose tile rectangle holds it (the flat per-tile binning)
+    int64_t P = 0;
+    uint32_t *keys = nullptr, *list = nullptr;
+    const uint32_t *sgid = nullptr;
+    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, &sgid, 0);
+    if (s != SLAG_OK) return s;
+    std::vector<uint2> h_r((size_t)tiles);
+    CK(cudaMemcpyAsync(h_r.data(), vs.ranges, sizeof(uint2) * tiles, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<int64_t> off((size_t)tiles + 1, 0);
+    for (int64_t t = 0; t < tiles; ++t) {
+        const uint2 r = h_r[(size_t)t];
+        off[(size_t)t + 1] = off[(size_t)t] + (r.y > r.x ? (int64_t)(r.y - r.x) : 0);
+    }
+    if (out_P) *out_P = off[(size_t)tiles];
+    if (!out_list && !out_ranges) return SLAG_OK;
+    if (out_list && list_cap < off[(size_t)tiles]) return fail(ctx, SLAG_ERR_CAPACITY, "list_cap < P");
+    // the super-tile binning slag_add_view composites from, then the composite with a trace
+    int64_t Ps = 0;
+    s = bin_view(ctx, vs, st, cp, &Ps, &keys, &list, &sgid, kSuperShift);
+    if (s != SLAG_OK) return s;
+    uint32_t *d_list = nullptr, *d_staged = nullptr, *d_bad = nullptr;
+    int64_t *d_off = nullptr;
+    auto release = [&]() { dfree(d_list); dfree(d_staged); dfree(d_bad); dfree(d_off); };
+    cudaError_t e = dalloc(&d_list, off[(size_t)tiles]);
+    if (e == cudaSuccess) e = dalloc(&d_staged, tiles);
+    if (e == cudaSuccess) e = dalloc(&d_bad, 1);
+    if (e == cudaSuccess) e = dalloc(&d_off, tiles + 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * (tiles + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_staged, 0, sizeof(uint32_t) * tiles, st);
+    const int64_t npx = (int64_t)cam->width * cam->height;
+    if (e == cudaSuccess && npx > ctx->dbg_cap) {
+        int64_t c1 = ctx->dbg_cap, c2 = ctx->dbg_cap, c3 = ctx->dbg_cap;
+        e = grow(ctx->dbg_T, c1, npx, st);
+        if (e == cudaSuccess) e = grow(ctx->dbg_wsum, c2, npx, st);
+        if (e == cudaSuccess) e = grow(ctx->dbg_count, c3, npx, st);
+        if (e == cudaSuccess) ctx->dbg_cap = c1;
+    }
+    if (e != cudaSuccess) {
+        release();
+        return fail(ctx, e == cudaErrorMemoryAllocation ? SLAG_ERR_OOM : SLAG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    CompositeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.cam = cp;
+    a.ranges = vs.ranges;
+    a.bin_shift = kSuperShift;
+    a.bins_x = ((cp.tiles_x - 1) >> kSuperShift) + 1;
+    a.tile_order = vs.tile_order;
+    a.list = list;
+    a.prect = vs.prect;
+    a.srec_a = vs.srec_a;
+    a.srec_b = vs.srec_b;
+    a.sgid = sgid;
+    a.weight_mode = ctx->weight_mode;
+    a.ctr = vs.ctr;
+    a.overflow = reinterpret_cast<uint32_t *>(&vs.ctr->pad[0]);
+    a.contrib = &vs.ctr->contributions;
+    a.dbg_T = ctx->dbg_T;
+    a.dbg_wsum = ctx->dbg_wsum;
+    a.dbg_count = ctx->dbg_count;
+    a.dbg_list = d_list;
+    a.dbg_off = d_off;
+    a.dbg_staged = d_staged;
+    a.dbg_bad = d_bad;
+    a.accumulate = 0;
+    launch_composite(a, st);
+    e = cudaGetLastError();
+    std::vector<uint32_t> staged((size_t)tiles);
+    uint32_t bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(staged.data(), d_staged, sizeof(uint32_t) * tiles, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        release();
+        return fail(ctx, SLAG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (out_list) {
+        s = ranks_to_callers(ctx, st, d_list, off[(size_t)tiles], sgid, out_list);
+        if (s != SLAG_OK) { release(); return s; }
+    }
+    if (out_ranges)
+        for (int64_t t = 0; t < tiles; ++t) {
+            out_ranges[2 * t] = off[(size_t)t];
+            out_ranges[2 * t + 1] = off[(size_t)t] + (int64_t)staged[(size_t)t];
+        }
+    release();
+    if (bad) return fail(ctx, SLAG_ERR_CAPACITY, "a tile staged more Gaussians than its tile list holds");
     return SLAG_OK;
 }
 

@@ -212,6 +212,14 @@ struct CompositeArgs {
                                    // the Gaussians that survived its culling x its 64 pixels
     float *dbg_T, *dbg_wsum;       // nullable, H x W
     int32_t *dbg_count;            // nullable
+    // trace of the Gaussians each tile stages (diagnostics; nullable): the depth rank of every
+    // staged Gaussian at dbg_list[dbg_off[tile] + i], i < dbg_off[tile + 1] - dbg_off[tile]
+    // (beyond that *dbg_bad is set and nothing is written); dbg_staged[tile] = how many were
+    // staged. With a trace the kernel keeps staging after all of a tile's pixels have stopped.
+    uint32_t *dbg_list;
+    const int64_t *dbg_off;
+    uint32_t *dbg_staged;
+    uint32_t *dbg_bad;
     int accumulate;                // 0: compositing only (diagnostics)
     WeightRecord *recs;            // record list of the view (nullable: sums go to the tables directly)
     unsigned long long *rec_count; // records written (zeroed before the launch)
@@ -242,6 +250,16 @@ void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t 
 // keys_in (in place when they alias); w_in (nullable) is copied to w_out alongside.
 void launch_repack_keys(const uint64_t *keys_in, uint64_t *keys_out, const float *w_in, float *w_out, int64_t Z,
                         int col_bits, bool to_compact, cudaStream_t st);
+// Accumulated state (slag_save_state / slag_merge_state): log entries to (caller index, column),
+// (caller index, column, W) back into the log with the columns shifted, and the per-Gaussian
+// compensated sums of another state added.
+void launch_state_unpack(const uint64_t *keys, int64_t Z, const uint32_t *orig_of_int, uint32_t *gauss, uint32_t *col,
+                         cudaStream_t st);
+void launch_state_pack(const uint32_t *gauss, const uint32_t *col, const float *w, int64_t Z,
+                       const uint32_t *int_of_orig, int64_t n, uint32_t col_shift, uint32_t cols_in,
+                       uint64_t *log_key, float *log_w, uint32_t *bad, cudaStream_t st);
+void launch_state_sums(float *hi, float *lo, float *ovf, const float *bhi, const float *blo, const float *bovf,
+                       int64_t n, cudaStream_t st);
 struct AggArgs {
     const uint64_t *keys;
     const float *w;

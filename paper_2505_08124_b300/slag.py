@@ -67,7 +67,8 @@ EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_
            "slag_set_profiling", "slag_get_profile", "slag_noalloc_query_topk", "slag_kernel_launches",
            "slag_export_partitions", "slag_latent_param_count", "slag_latent_train", "slag_latent_apply",
            "slag_set_latent", "slag_add_views_batched", "slag_set_autotune", "slag_finalize_async",
-           "slag_wait_outputs", "slag_set_profiling_stages")
+           "slag_wait_outputs", "slag_set_profiling_stages", "slag_bin_view_bins", "slag_composite_trace",
+           "slag_save_state", "slag_load_state", "slag_merge_state", "slag_state_merge_host")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -101,6 +102,12 @@ def load_library(path: str = LIB_PATH):
     lib.slag_destroy.restype = None
     lib.slag_bin_view.argtypes = [P, ctypes.POINTER(CCamera), P, P, P, i64, P]
     lib.slag_render_debug.argtypes = [P, ctypes.POINTER(CCamera), P, P, P]
+    lib.slag_save_state.argtypes = [P, P, i64, ctypes.POINTER(i64)]
+    lib.slag_load_state.argtypes = [P, P, i64]
+    lib.slag_merge_state.argtypes = [P, P, i64]
+    lib.slag_state_merge_host.argtypes = [P, i64, P, i64, P, i64, ctypes.POINTER(i64)]
+    lib.slag_bin_view_bins.argtypes = [P, ctypes.POINTER(CCamera), i32, P, P, i64, P]
+    lib.slag_composite_trace.argtypes = [P, ctypes.POINTER(CCamera), P, P, i64, P]
     lib.slag_set_profiling.argtypes = [P, i32]
     lib.slag_set_profiling_stages.argtypes = [P, ctypes.c_uint32]
     lib.slag_get_profile.argtypes = [P, ctypes.POINTER(CProfile), i32]
@@ -321,6 +328,27 @@ class Lifter:
                     "slag_export_partitions")
         return int(written.value)
 
+    def save_state(self) -> np.ndarray:
+        """The accumulated state (slag_save_state) as a uint8 array."""
+        size = ctypes.c_int64()
+        self._check(self._lib.slag_save_state(self._h, None, 0, ctypes.byref(size)), "slag_save_state")
+        buf = np.empty(size.value, np.uint8)
+        self._check(self._lib.slag_save_state(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size,
+                                              ctypes.byref(size)), "slag_save_state")
+        return buf
+
+    def load_state(self, state):
+        buf = np.ascontiguousarray(np.frombuffer(state, np.uint8) if isinstance(state, (bytes, bytearray)) else state,
+                                   np.uint8)
+        self._check(self._lib.slag_load_state(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size),
+                    "slag_load_state")
+
+    def merge_state(self, state):
+        buf = np.ascontiguousarray(np.frombuffer(state, np.uint8) if isinstance(state, (bytes, bytearray)) else state,
+                                   np.uint8)
+        self._check(self._lib.slag_merge_state(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size),
+                    "slag_merge_state")
+
     def stats(self) -> dict:
         s = CStats()
         self._check(self._lib.slag_get_stats(self._h, ctypes.byref(s)), "slag_get_stats")
@@ -363,6 +391,35 @@ class Lifter:
                                             rng.ctypes.data_as(ctypes.c_void_p)), "slag_bin_view")
         return touched, lst[:P.value], rng
 
+    def bin_view_bins(self, camera, bin_shift: int):
+        """(list[P] caller ids grouped by bin, ranges[bins, 2]) of 2^bin_shift x 2^bin_shift-tile bins."""
+        c = camera_struct(camera)
+        P = ctypes.c_int64()
+        self._check(self._lib.slag_bin_view_bins(self._h, ctypes.byref(c), int(bin_shift), ctypes.byref(P), None, 0,
+                                                 None), "slag_bin_view_bins")
+        tx, ty = (int(camera.width) + 15) // 16, (int(camera.height) + 15) // 16
+        bins = (((tx - 1) >> bin_shift) + 1) * (((ty - 1) >> bin_shift) + 1)
+        lst = np.empty(max(P.value, 1), np.int32)
+        rng = np.empty((bins, 2), np.int64)
+        self._check(self._lib.slag_bin_view_bins(self._h, ctypes.byref(c), int(bin_shift), ctypes.byref(P),
+                                                 lst.ctypes.data_as(ctypes.c_void_p), lst.shape[0],
+                                                 rng.ctypes.data_as(ctypes.c_void_p)), "slag_bin_view_bins")
+        return lst[:P.value], rng
+
+    def composite_trace(self, camera):
+        """(list[P] caller ids staged per tile by the compositing kernel, ranges[tiles, 2])."""
+        c = camera_struct(camera)
+        P = ctypes.c_int64()
+        self._check(self._lib.slag_composite_trace(self._h, ctypes.byref(c), ctypes.byref(P), None, 0, None),
+                    "slag_composite_trace")
+        tiles = ((int(camera.width) + 15) // 16) * ((int(camera.height) + 15) // 16)
+        lst = np.full(max(P.value, 1), -1, np.int32)
+        rng = np.empty((tiles, 2), np.int64)
+        self._check(self._lib.slag_composite_trace(self._h, ctypes.byref(c), ctypes.byref(P),
+                                                   lst.ctypes.data_as(ctypes.c_void_p), lst.shape[0],
+                                                   rng.ctypes.data_as(ctypes.c_void_p)), "slag_composite_trace")
+        return lst[:P.value], rng
+
     def render_debug(self, camera):
         """Per pixel (final transmittance, sum of weights, contributor count)."""
         c = camera_struct(camera)
@@ -402,6 +459,49 @@ def read_partitions(directory: str) -> dict:
         out[(int(cx), int(cy))] = {"bounds": bounds, "ids": r["id"].copy(), "wsum": r["wsum"].copy(),
                                    "E": r["E"].copy()}
     return out
+
+
+def state_merge_host(a, b) -> np.ndarray:
+    """Merges two saved states on the host (slag_state_merge_host); no GPU is needed."""
+    lib = load_library()
+    A = np.ascontiguousarray(np.frombuffer(a, np.uint8) if isinstance(a, (bytes, bytearray)) else a, np.uint8)
+    B = np.ascontiguousarray(np.frombuffer(b, np.uint8) if isinstance(b, (bytes, bytearray)) else b, np.uint8)
+    size = ctypes.c_int64()
+    pa, pb = A.ctypes.data_as(ctypes.c_void_p), B.ctypes.data_as(ctypes.c_void_p)
+    rc = lib.slag_state_merge_host(pa, A.size, pb, B.size, None, 0, ctypes.byref(size))
+    if rc != OK:
+        raise SlagError(rc, "slag_state_merge_host")
+    out = np.empty(size.value, np.uint8)
+    rc = lib.slag_state_merge_host(pa, A.size, pb, B.size, out.ctypes.data_as(ctypes.c_void_p), out.size,
+                                   ctypes.byref(size))
+    if rc != OK:
+        raise SlagError(rc, "slag_state_merge_host")
+    return out
+
+
+STATE_HEADER = np.dtype([("magic", "S8"), ("version", "<u4"), ("dim", "<u4"), ("n", "<i8"), ("columns", "<i8"),
+                         ("triples", "<i8"), ("fingerprint", "<u8"), ("views", "<i8"), ("pairs", "<i8"),
+                         ("contributions", "<i8"), ("evaluations", "<i8"), ("executed", "<i8"),
+                         ("weight_mode", "<i4"), ("reserved", "<i4")])
+
+
+def read_state(state) -> dict:
+    """The parts of a saved state as numpy arrays (the format of slag_save_state)."""
+    buf = np.frombuffer(state, np.uint8) if isinstance(state, (bytes, bytearray)) else np.asarray(state, np.uint8)
+    h = np.frombuffer(buf, STATE_HEADER, 1, 0)[0]
+    if h["magic"] != b"SLAGSTAT" or h["version"] != 1:
+        raise ValueError("not a state of this library")
+    n, D, C, Z = int(h["n"]), int(h["dim"]), int(h["columns"]), int(h["triples"])
+    o = STATE_HEADER.itemsize
+    table = np.frombuffer(buf, np.float32, C * D, o).reshape(C, D)
+    o += 4 * C * D
+    sums = np.frombuffer(buf, np.float32, 3 * n, o).reshape(3, n)
+    o += 12 * n
+    g = np.frombuffer(buf, np.uint32, Z, o)
+    c = np.frombuffer(buf, np.uint32, Z, o + 4 * Z)
+    w = np.frombuffer(buf, np.float32, Z, o + 8 * Z)
+    return {"header": {k: h[k] for k in STATE_HEADER.names}, "table": table, "w_hi": sums[0], "w_lo": sums[1],
+            "w_ovf": sums[2], "gauss": g, "column": c, "w": w}
 
 
 def latent_param_count(dim: int) -> int:

@@ -95,6 +95,47 @@ def test_binning_bit_exact(slag, case):
             np.testing.assert_array_equal(rng, rng_ref)
 
 
+def _super_lists(g, cam, shift):
+    """Expected bins of 2^shift x 2^shift tiles from the oracle's float32 mirror: a Gaussian is in
+    every bin its tile rectangle meets; each bin's members in (float32 depth, index) order."""
+    depth, rect, touched = O.bin_f32(g, cam)
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    bx, by = ((tx - 1) >> shift) + 1, ((ty - 1) >> shift) + 1
+    members = [[] for _ in range(bx * by)]
+    for k in np.nonzero(touched)[0]:
+        x0, y0, x1, y1 = rect[k]
+        for yb in range(y0 >> shift, ((y1 - 1) >> shift) + 1):
+            for xb in range(x0 >> shift, ((x1 - 1) >> shift) + 1):
+                members[yb * bx + xb].append(k)
+    lst, rng, at = [], np.zeros((bx * by, 2), np.int64), 0
+    for b, m in enumerate(members):
+        m = np.array(m, np.int64)
+        order = np.lexsort((m, depth[m])) if len(m) else m
+        lst.extend(m[order].tolist())
+        rng[b] = (at, at + len(m))
+        at += len(m)
+    return np.array(lst, np.int32), rng
+
+
+@pytest.mark.parametrize("case", [c[0] for c in _binning_cases()])
+def test_super_tile_binning_bit_exact(slag, case):
+    # the binning slag_add_view composites from: 4x4-tile super-tile lists and ranges, and the
+    # per-tile sequences the compositing kernel itself stages from them
+    name, g, cams = next(c for c in _binning_cases() if c[0] == case)
+    with slag.Lifter(g, dim=128) as L:
+        for cam in cams:
+            for shift in (0, 2):
+                lst, rng = L.bin_view_bins(cam, shift)
+                lst_ref, rng_ref = _super_lists(g, cam, shift)
+                assert lst.shape == lst_ref.shape, (name, shift)
+                np.testing.assert_array_equal(lst, lst_ref)
+                np.testing.assert_array_equal(rng, rng_ref)
+            staged, trng = L.composite_trace(cam)
+            lst_ref, rng_ref = O.tile_lists(g, cam)
+            np.testing.assert_array_equal(trng, rng_ref)
+            np.testing.assert_array_equal(staged, lst_ref)
+
+
 # ----------------------------------------------------------------------------
 # compositing state per pixel
 # ----------------------------------------------------------------------------
