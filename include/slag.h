@@ -66,7 +66,7 @@ enum { SLAG_WEIGHT_ALPHA_T = 0, SLAG_WEIGHT_KERNEL = 1 };
  * float32 accumulation; the error against float64 is stated per result by the
  * tests (cosine >= 1 - 1e-3 per touched Gaussian at the tested scales). No
  * float64 is used on the GPU in either form. */
-enum { SLAG_PREC_FP32 = 0, SLAG_PREC_BF16 = 1, SLAG_PREC_LATENT32 = 2 };
+enum { SLAG_PREC_FP32 = 0, SLAG_PREC_BF16 = 1, SLAG_PREC_LATENT32 = 2, SLAG_PREC_LINEAR32 = 3 };
 /* LATENT32: the learned latent form. The views' segment embeddings are
  * encoded to 32-d codes by a small autoencoder (slag_latent_train; set with
  * slag_set_latent before the first view; finalize encodes every stored
@@ -74,6 +74,16 @@ enum { SLAG_PREC_FP32 = 0, SLAG_PREC_BF16 = 1, SLAG_PREC_LATENT32 = 2 };
  * and finalize decodes each touched Gaussian's mean code to D dimensions
  * (the decoder is not linear: dec(mean code) is not the mean of decoded
  * codes; the float32 path is the reference for its error). */
+
+/* LINEAR32: the latent form with a linear 32-d code. With U the top 32
+ * principal directions of training embeddings and mu their mean
+ * (slag_linear_code_fit; set with slag_set_linear_code before the first
+ * view), a segment embedding e is encoded as z = U^T (e - mu) and a code is
+ * decoded as mu + U z. The code is linear, so the aggregation of codes is
+ * exact: the decoded mean code is mu + U U^T (E_k - mu), the projection of the
+ * Aggregation step's E_k onto the code's affine subspace, and its error is the
+ * part of E_k outside it (the floor of any 32-d linear code fitted to those
+ * embeddings). */
 
 /* SLAG_FLAG_EMBEDDINGS_ON_HOST: the context holds no n x D copy of the
  * embeddings on the device (out-of-core aggregation, after the paper's
@@ -107,7 +117,7 @@ typedef struct {
 
 typedef struct {
     int32_t dim;             /* D: embedding width, a multiple of 128, 128 .. 4096 */
-    int32_t precision;       /* SLAG_PREC_FP32 or SLAG_PREC_BF16 */
+    int32_t precision;       /* SLAG_PREC_FP32, _BF16, _LATENT32 or _LINEAR32 */
     int32_t weight_mode;     /* SLAG_WEIGHT_ALPHA_T (default) or SLAG_WEIGHT_KERNEL */
     int32_t flags;           /* SLAG_FLAG_* bits, or 0 */
     void *cuda_stream;       /* cudaStream_t, NULL = legacy default stream */
@@ -409,6 +419,27 @@ slag_status slag_latent_apply(const float *params, int32_t dim, const float *in,
  * a context created with SLAG_PREC_LATENT32; before the first view. */
 slag_status slag_set_latent(slag_ctx *ctx, const float *params);
 
+/* ---- the linear 32-d code (SLAG_PREC_LINEAR32) --------------------------- */
+
+/* Parameters of the linear code for input width dim: U (dim x 32, row-major,
+ * input x output; orthonormal columns) then mu (dim): dim x 33 floats; 0 for
+ * an unsupported width. */
+int64_t slag_linear_param_count(int32_t dim);
+
+/* Fits the linear code to n samples (n x dim float32, host or device): mu is
+ * their mean and U the top 32 eigenvectors of their covariance (principal
+ * component analysis: the second moment is accumulated on the device, the
+ * eigenvectors found in float64 by subspace iteration with a Rayleigh-Ritz
+ * step). out_params (host, slag_linear_param_count(dim) floats); *out_kept
+ * (nullable) the fraction of the samples' variance the 32 directions keep.
+ * dim a multiple of 32 in 32 .. 4096, 2 <= n < 2^31. */
+slag_status slag_linear_code_fit(const float *samples, int64_t n, int32_t dim, int32_t on_device,
+                                 float *out_params, float *out_kept, void *cuda_stream);
+
+/* Sets the linear code (host parameters as above) of a context created with
+ * SLAG_PREC_LINEAR32; before the first view. */
+slag_status slag_set_linear_code(slag_ctx *ctx, const float *params);
+
 /* ---- out-of-core output: per-area embedding files ------------------------- */
 
 /* Spatial partition export (the paper stores a large scene's embeddings per
@@ -467,6 +498,38 @@ slag_status slag_set_profiling_stages(slag_ctx *ctx, uint32_t stages);
  * when reset is non-zero, clears the totals. busy_ms covers the spans
  * resolved since profiling was enabled or last reset. */
 slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset);
+
+/* ---- the checked build ------------------------------------------------------
+ * libslag_checks.so is this library compiled with -DSLAG_CHECKS: index checks
+ * in pair emission, the sort's scatter, compositing and aggregation, in place
+ * of the sanitizer that this library's tests cannot use. An index outside its
+ * buffer is then not used; the check sets an error word, and the next call
+ * that synchronises (slag_finalize, the diagnostics) returns
+ * SLAG_ERR_CAPACITY naming the stages. In the regular build the checks are
+ * compiled out. */
+
+/* 1 in the checked build, 0 otherwise. */
+int32_t slag_is_checked_build(void);
+
+/* Checked build only: the pair buffers of the following views behave as if
+ * they held cap pairs (0 = off), so that the emission's checks refuse the
+ * pairs beyond cap (a forced capacity overflow; the views' results are then
+ * wrong and the next synchronising call returns CAPACITY). In the regular
+ * build it returns SLAG_ERR_STATE and changes nothing. Errors: INVALID_ARG
+ * for cap < 0. */
+slag_status slag_debug_force_pair_capacity(slag_ctx *ctx, int64_t cap);
+
+/* Check of the bounded device waits. Every device-side wait of the library
+ * (the mbarrier waits of its tensor-core kernels) gives up after a bound of
+ * ~1 s; the kernel then sets the context's error word, the call returns
+ * SLAG_ERR_TIMEOUT and the context stays usable. This call runs that path on
+ * demand with nothing else in flight: one role waits limit_us microseconds
+ * (1 .. 1,000,000) on an mbarrier that nothing completes, and a second role,
+ * waiting on another barrier, gives up when the first one aborts. Returns
+ * SLAG_ERR_TIMEOUT, or SLAG_OK when `complete` is non-zero (the barrier is
+ * completed first and both roles finish normally). Joins the views in flight
+ * first. Errors: INVALID_ARG; CUDA. */
+slag_status slag_check_wait_timeout(slag_ctx *ctx, int32_t limit_us, int32_t complete);
 
 /* Kernel launches issued by the library so far, over every context and
  * device of the process (a running count; differences give the launches of

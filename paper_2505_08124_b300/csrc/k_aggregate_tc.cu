@@ -34,6 +34,9 @@
 
 namespace slag {
 
+SLAG_CHECKS_WORD
+
+
 namespace {
 
 using tc::core_off;
@@ -156,7 +159,9 @@ __global__ void __launch_bounds__(kThreadsA, 1) aggregate_tc_k(const AggArgs a, 
 #pragma unroll
         for (int i = 0; i < kCols; ++i) {
             const uint32_t lc = (uint32_t)(lane * kCols + i);
-            const float *row = lc < nk ? a.table + (int64_t)col_of(uc + lc) * a.D + d0 : nullptr;
+            const float *row = lc < nk && SLAG_IN_BOUNDS((int64_t)col_of(uc + lc) < a.columns, kCheckAggregate)
+                                   ? a.table + (int64_t)col_of(uc + lc) * a.D + d0
+                                   : nullptr;
 #pragma unroll
             for (int j = 0; j < kF4; ++j)
                 ev[i][j] = row ? __ldg(reinterpret_cast<const float4 *>(row) + warp * kF4 + j)
@@ -170,8 +175,10 @@ __global__ void __launch_bounds__(kThreadsA, 1) aggregate_tc_k(const AggArgs a, 
             tw_w[j] = 0.f;
             if (t < t1) {
                 const uint32_t lc = a.uidx[t] + a.flags[t] - 1u - uc;
-                tw_idx[j] = (int)(a.keys[t] & 127u) * kPitch + (int)lc;
-                tw_w[j] = a.w[t];
+                if (SLAG_IN_BOUNDS(lc < (uint32_t)kKA, kCheckAggregate)) {
+                    tw_idx[j] = (int)(a.keys[t] & 127u) * kPitch + (int)lc;
+                    tw_w[j] = a.w[t];
+                }
             }
         }
     };
@@ -199,6 +206,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) aggregate_tc_k(const AggArgs a, 
                 const uint32_t t0 = chunk_start(c), t1 = chunk_start(c + 1);
                 for (uint32_t t = t0 + tid + kTP * kThreadsA; t < t1; t += kThreadsA) {
                     const uint32_t lc = a.uidx[t] + a.flags[t] - 1u - uc;
+                    if (!SLAG_IN_BOUNDS(lc < (uint32_t)kKA, kCheckAggregate)) continue;
                     atomicAdd(&Wf[(int)(a.keys[t] & 127u) * kPitch + (int)lc], a.w[t]);
                 }
             }
@@ -361,5 +369,7 @@ void launch_aggregate(const AggArgs &a, int64_t nblocks, uint32_t *err, cudaStre
         launch_one<128, false>(a, nblocks, err, st);
     note_launch();
 }
+
+SLAG_CHECKS_TAKE(checks_take_aggregate)
 
 }  // namespace slag

@@ -13,13 +13,15 @@
 
 namespace slag {
 
+SLAG_CHECKS_WORD
+
 namespace {
 
 // One thread per Gaussian (in depth-rank order): the pairs of the bins its tile
 // rectangle meets, row-major; a bin is a 2^shift x 2^shift square of tiles.
 __global__ void __launch_bounds__(256) emit_k(const uint2 *__restrict__ srect, const uint32_t *__restrict__ offsets,
-                                              uint32_t n_visible, int shift, int bins_x, uint32_t *__restrict__ keys,
-                                              uint32_t *__restrict__ vals) {
+                                              uint32_t n_visible, int shift, int bins_x, int64_t cap,
+                                              uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_visible) return;
     const uint2 rc = srect[r];
@@ -28,6 +30,7 @@ __global__ void __launch_bounds__(256) emit_k(const uint2 *__restrict__ srect, c
     uint32_t off = offsets[r];
     for (uint32_t y = y0; y < y1; ++y)
         for (uint32_t x = x0; x < x1; ++x, ++off) {
+            if (!SLAG_IN_BOUNDS((int64_t)off < cap, kCheckEmit)) continue;
             keys[off] = y * (uint32_t)bins_x + x;
             vals[off] = r;
         }
@@ -91,11 +94,14 @@ void launch_tile_order(const uint2 *ranges, int tiles_x, int tiles_y, int shift,
     tile_order_k<<<1, 1024, 0, st>>>(ranges, tiles_x, tiles, shift, order); note_launch();
 }
 
-void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int shift, int bins_x,
+void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int shift, int bins_x, int64_t cap,
                  uint32_t *keys, uint32_t *vals, cudaStream_t st) {
     if (n_visible == 0) return;
-    emit_k<<<(n_visible + 255) / 256, 256, 0, st>>>(srect, offsets, n_visible, shift, bins_x, keys, vals); note_launch();
+    emit_k<<<(n_visible + 255) / 256, 256, 0, st>>>(srect, offsets, n_visible, shift, bins_x, cap, keys, vals);
+    note_launch();
 }
+
+SLAG_CHECKS_TAKE(checks_take_bin)
 
 void launch_pair_rects(const uint32_t *list, int64_t P, const uint2 *srect, uint2 *prect, cudaStream_t st) {
     if (P <= 0) return;

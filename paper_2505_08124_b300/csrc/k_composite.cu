@@ -47,6 +47,8 @@
 
 namespace slag {
 
+SLAG_CHECKS_WORD
+
 namespace {
 
 constexpr int kRows = 16;                             // tile rows per CTA: one CTA per 16x16 tile
@@ -420,7 +422,8 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
             for (int k = 0; k < kPer; ++k) {
                 int bk = 0;
                 for (int q = 0; q < k * (kThreads / 32) + w; ++q) bk += sm.fill[rp][q];
-                if (hit[k]) {
+                if (hit[k] && SLAG_IN_BOUNDS(nb + bk + __popc(bal[k] & lt) < kBatch && r[k] < a.n_ranks,
+                                             kCheckComposite)) {
                     const int pos = nb + bk + __popc(bal[k] & lt);
                     cp_async16(&sm.rec_a[pos], a.srec_a + r[k]);
                     cp_async16(&sm.rec_b[pos], a.srec_b + r[k]);
@@ -670,5 +673,7 @@ void launch_composite(const CompositeArgs &a, cudaStream_t st) {
     if (set_max_smem((const void *)kfn, (int)sizeof(Smem)) != cudaSuccess) return;
     kfn<<<tiles * kSubTiles, kThreads, sizeof(Smem), st>>>(a); note_launch();
 }
+
+SLAG_CHECKS_TAKE(checks_take_composite)
 
 }  // namespace slag

@@ -255,11 +255,12 @@ __global__ void __launch_bounds__(kThreadsD, 1)
 
 // wt[n][k] = bfloat16-rounded W[k][n] (W: K x N row-major)
 __global__ void __launch_bounds__(256) weights_t_k(const float *__restrict__ W, int32_t K, int32_t N,
-                                                   float *__restrict__ wt) {
+                                                   float *__restrict__ wt, int tf32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)K * N) return;
     const int64_t n = i / K, k = i - n * K;
-    wt[i] = __bfloat162float(__float2bfloat16_rn(W[k * N + n]));
+    const float w = W[k * N + n];
+    wt[i] = tf32 ? tc::to_tf32(w) : __bfloat162float(__float2bfloat16_rn(w));
 }
 
 template <int NT, int kMode>
@@ -284,9 +285,9 @@ cudaError_t launch_dense_t(const CUtensorMap &ta, const CUtensorMap &tw, int64_t
 
 int64_t dense_tc_pad_rows(int64_t rows) { return (rows + kRowsT - 1) / kRowsT * kRowsT; }
 
-void launch_weights_t(const float *W, int32_t K, int32_t N, float *wt, cudaStream_t st) {
+void launch_weights_t(const float *W, int32_t K, int32_t N, float *wt, cudaStream_t st, bool tf32) {
     const int64_t n = (int64_t)K * N;
-    weights_t_k<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, K, N, wt); note_launch();
+    weights_t_k<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, K, N, wt, tf32 ? 1 : 0); note_launch();
 }
 
 cudaError_t launch_dense_tc(const float *a_planes, int64_t rows, int64_t rows_pad, int32_t K, const float *wt,

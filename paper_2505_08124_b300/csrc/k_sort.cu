@@ -20,6 +20,9 @@
 
 namespace slag {
 
+SLAG_CHECKS_WORD
+
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -243,6 +246,7 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
         const K k = skeys[j];
         const uint32_t d = (uint32_t)(k >> shift) & mask;
         const uint32_t gp = gbase[d] + (uint32_t)j - lstart[d];
+        if (!SLAG_IN_BOUNDS((int64_t)gp < n, kCheckSort)) continue;
         kout[gp] = k;
         vout[gp] = svals[j];
     }
@@ -472,5 +476,7 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, unsigned l
     scan_spine<<<1, 1024, 0, st>>>(s.partials, tiles, d_total); note_launch();
     scan_tiles<<<(unsigned)tiles, kThreads, 0, st>>>(in, out, n, s.partials); note_launch();
 }
+
+SLAG_CHECKS_TAKE(checks_take_sort)
 
 }  // namespace slag

@@ -118,6 +118,7 @@ struct slag_ctx {
     int32_t precision = 0;
     int32_t opt_flags = 0;                   // SLAG_FLAG_*
     int64_t chunk_gaussians = 1 << 20;       // rows per chunk of the out-of-core contraction
+    int64_t force_pair_cap = 0;              // checked builds: pair capacity forced on the next views
     std::string err;
 
     // Gaussians, internal (Morton) order
@@ -183,6 +184,8 @@ struct slag_ctx {
 
     // latent form: autoencoder parameters, codes of the stored segment embeddings, scratch
     float *lat_params = nullptr;
+    float *lin_params = nullptr;             // linear code: U (D x 32) then mu (D), and -mu U
+    float *lin_enc_bias = nullptr;
     float *ztable = nullptr;                 // columns x kLatent
     int64_t ztable_cap = 0;
     float *lat_hidden = nullptr;             // rows x kLatentHidden
@@ -405,6 +408,31 @@ void spans_resolve(slag_ctx *ctx, bool all = true) {
     (void)cudaGetLastError();   // clears cudaErrorNotReady left by the queries
 }
 
+// A tensor-core kernel gave up a bounded wait (the error word is set): clears the word, so that
+// the context stays usable, and returns TIMEOUT with msg.
+slag_status timeout_reported(slag_ctx *ctx, const char *msg) {
+    ctx->hc->tc_err = 0;
+    cudaMemsetAsync(ctx->tc_err, 0, sizeof(uint32_t), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return fail(ctx, SLAG_ERR_TIMEOUT, msg);
+}
+
+// Checked builds: reads and clears the bounds-check words after the stream has synchronised;
+// a failed check is reported as CAPACITY, naming the stages.
+slag_status checks_reported(slag_ctx *ctx) {
+    if (!kChecked) return SLAG_OK;
+    cudaStream_t st = ctx->stream;
+    const uint32_t v = checks_take_bin(st) | checks_take_sort(st) | checks_take_composite(st) |
+                       checks_take_aggregate(st);
+    if (!v) return SLAG_OK;
+    std::string m = "bounds check failed in:";
+    if (v & kCheckEmit) m += " pair emission";
+    if (v & kCheckSort) m += " sort scatter";
+    if (v & kCheckComposite) m += " compositing";
+    if (v & kCheckAggregate) m += " aggregation";
+    return fail(ctx, SLAG_ERR_CAPACITY, m);
+}
+
 // The caller's stream waits for every view in flight and for both front streams.
 cudaError_t join_views(slag_ctx *ctx) {
     cudaError_t e = cudaEventRecord(ctx->ev_front, ctx->front);
@@ -464,7 +492,10 @@ slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
 // pairs by bin (tile or super-tile), bin ranges and the tile order; sorts with `scr`.
 slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int shift,
                     SortScratch &scr, int64_t *P_out, uint32_t **keys_out, uint32_t **list_out) {
-    const int64_t P = (int64_t)vs.h->v.P;   // pairs at the binning granularity
+    int64_t P = (int64_t)vs.h->v.P;         // pairs at the binning granularity
+    // checked builds only: a capacity forced below P; the emission's checks refuse the pairs
+    // beyond it and the later stages see only the first pairs
+    if (kChecked && ctx->force_pair_cap > 0 && ctx->force_pair_cap < P) P = ctx->force_pair_cap;
     if (P > 0x7fffffffLL || vs.h->v.P_tiles > 0x7fffffffULL)
         return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^31-1 Gaussian-tile pairs in one view");
     if (P > vs.p_cap) {
@@ -483,7 +514,7 @@ slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
     CK(grow(vs.ranges, vs.ranges_cap, bins, st));
     const uint32_t nv = vs.h->v.n_visible;
     span_begin(ctx, SLAG_STAGE_BIN, st);
-    launch_emit(vs.srect, vs.offsets, nv, shift, bins_x, vs.pkey[0], vs.pval[0], st);
+    launch_emit(vs.srect, vs.offsets, nv, shift, bins_x, P, vs.pkey[0], vs.pval[0], st);
     int shifts[8], widths[8];
     const int np = digit_passes(0, ceil_log2((uint64_t)bins), shifts, widths, P);
     uint32_t *keys = vs.pkey[0];
@@ -580,7 +611,8 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     if (g->n < 1 || g->n >= (1LL << 31)) return SLAG_ERR_INVALID_ARG;
     if (!g->means || !g->scales || !g->quats || !g->opacities) return SLAG_ERR_INVALID_ARG;
     if (opt->dim < 128 || opt->dim > 4096 || opt->dim % 128 != 0) return SLAG_ERR_INVALID_ARG;
-    if (opt->precision != SLAG_PREC_FP32 && opt->precision != SLAG_PREC_BF16 && opt->precision != SLAG_PREC_LATENT32)
+    if (opt->precision != SLAG_PREC_FP32 && opt->precision != SLAG_PREC_BF16 && opt->precision != SLAG_PREC_LATENT32 &&
+        opt->precision != SLAG_PREC_LINEAR32)
         return SLAG_ERR_INVALID_ARG;
     if (opt->weight_mode != SLAG_WEIGHT_ALPHA_T && opt->weight_mode != SLAG_WEIGHT_KERNEL) return SLAG_ERR_INVALID_ARG;
     if ((opt->flags & ~SLAG_FLAG_EMBEDDINGS_ON_HOST) != 0) return SLAG_ERR_INVALID_ARG;
@@ -764,6 +796,7 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     a.srec_a = vs.srec_a;
     a.srec_b = vs.srec_b;
     a.sgid = vs.sgid;
+    a.n_ranks = vs.h->v.n_visible;
     a.seg = vs.seg_buf;
     a.view_base = (int32_t)vs.view_base;
     a.weight_mode = ctx->weight_mode;
@@ -824,6 +857,8 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     // in one pass (the codes are only read there)
     if (ctx->precision == SLAG_PREC_LATENT32 && !ctx->lat_params)
         return fail(ctx, SLAG_ERR_STATE, "latent form: slag_set_latent before the first view");
+    if (ctx->precision == SLAG_PREC_LINEAR32 && !ctx->lin_params)
+        return fail(ctx, SLAG_ERR_STATE, "linear code: slag_set_linear_code before the first view");
     ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
     cudaStream_t fr = ctx->front, up = ctx->up;
     const CamParams cp = cam_params(cam);
@@ -913,6 +948,10 @@ slag_status finalize_prepare(slag_ctx *ctx) {
     launch_copy_words(last.ctr, &ctx->hc_dev->v, sizeof(ViewCounters), st);
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    {
+        const slag_status sc = checks_reported(ctx);
+        if (sc != SLAG_OK) return sc;
+    }
     ctx->stats.contributions = (int64_t)ctx->hc->totals[1];
     ctx->stats.evaluations = (int64_t)ctx->hc->totals[3];
     ctx->stats.executed = (int64_t)ctx->hc->totals[4];
@@ -976,6 +1015,7 @@ AggArgs agg_args(slag_ctx *ctx) {
     g.bstart = ctx->bstart;
     g.bend = ctx->bend;
     g.table = ctx->table;
+    g.columns = ctx->table_rows;
     g.s_hi = ctx->s_hi;
     g.s_lo = ctx->s_lo;
     g.s_ovf = ctx->s_ovf;
@@ -1058,7 +1098,7 @@ slag_status aggregate_chunks(slag_ctx *ctx, int64_t chunk_gaussians, Sink &&sink
         CC(cudaStreamSynchronize(st));
         if (ctx->hc->tc_err) {
             release();
-            return fail(ctx, SLAG_ERR_TIMEOUT, "the tensor-core aggregation gave up waiting");
+            return timeout_reported(ctx, "the tensor-core aggregation gave up waiting");
         }
         rc = sink(ChunkView{hE, hI, hW, hM, valid});
     }
@@ -1170,23 +1210,32 @@ slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     }
     AggArgs g = agg_args(ctx);
     span_begin(ctx, SLAG_STAGE_AGGREGATE, st);
-    if (ctx->precision == SLAG_PREC_LATENT32) {
+    if (ctx->precision == SLAG_PREC_LATENT32 || ctx->precision == SLAG_PREC_LINEAR32) {
+        const bool linear = ctx->precision == SLAG_PREC_LINEAR32;
         // the segment embeddings of every view -> codes; mean codes per Gaussian; the decoder in
         // chunks of rows (internal order) -> E in caller order
         const int64_t chunk = std::min<int64_t>(n, 1 << 18);
         const int64_t rows_t = ctx->table_rows;
         CK(grow(ctx->ztable, ctx->ztable_cap, rows_t * kLatent, st));
         CK(grow(ctx->lat_hidden, ctx->lat_hidden_cap,
-                std::max(rows_t * kLatentHidden, latent_decode_scratch((int)chunk, ctx->D)), st));
+                linear ? linear_decode_scratch((int)chunk, ctx->D)
+                       : std::max(rows_t * kLatentHidden, latent_decode_scratch((int)chunk, ctx->D)), st));
         CK(grow(ctx->lat_Z, ctx->lat_Z_cap, n * kLatent, st));
         CK(grow(ctx->lat_Y, ctx->lat_Y_cap, chunk * ctx->D, st));
         float *Z = ctx->lat_Z, *Y = ctx->lat_Y;
-        latent_encode(ctx->lat_params, ctx->D, ctx->table, (int)rows_t, ctx->lat_hidden, ctx->ztable, st);
+        if (linear)
+            linear_encode(ctx->lin_params, ctx->lin_enc_bias, ctx->D, ctx->table, (int)rows_t, ctx->ztable, st);
+        else
+            latent_encode(ctx->lat_params, ctx->D, ctx->table, (int)rows_t, ctx->lat_hidden, ctx->ztable, st);
         CK(cudaMemsetAsync(ctx->touched, 0, sizeof(unsigned long long), st));
         launch_latent_aggregate(g, ctx->ztable, Z, nblocks, st);
         for (int64_t g0 = 0; g0 < n; g0 += chunk) {
             const int64_t rows = std::min<int64_t>(chunk, n - g0);
-            CK(latent_decode(ctx->lat_params, ctx->D, Z + g0 * kLatent, (int)rows, ctx->lat_hidden, Y, ctx->tc_err,
+            if (linear)
+                CK(linear_decode(ctx->lin_params, ctx->D, Z + g0 * kLatent, (int)rows, ctx->lat_hidden, Y, ctx->tc_err,
+                                 st));
+            else
+                CK(latent_decode(ctx->lat_params, ctx->D, Z + g0 * kLatent, (int)rows, ctx->lat_hidden, Y, ctx->tc_err,
                              st));
             launch_latent_finish(g, Y, g0, rows, st);
         }
@@ -1210,7 +1259,11 @@ slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     launch_copy_words(ctx->d_nq, &ctx->hc_dev->n_q, sizeof(unsigned long long), st);
     launch_copy_words(ctx->tc_err, &ctx->hc_dev->tc_err, sizeof(uint32_t), st);
     CK(cudaStreamSynchronize(st));
-    if (ctx->hc->tc_err) return fail(ctx, SLAG_ERR_TIMEOUT, "the tensor-core aggregation gave up waiting");
+    if (ctx->hc->tc_err) return timeout_reported(ctx, "the tensor-core aggregation gave up waiting");
+    {
+        const slag_status sc = checks_reported(ctx);
+        if (sc != SLAG_OK) return sc;
+    }
     spans_resolve(ctx, false);
     ctx->stats.touched = (int64_t)ctx->hc->touched;
     ctx->n_q = (int64_t)ctx->hc->n_q;
@@ -1419,7 +1472,7 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
         memcpy(out_ids, ctx->qstage, bi);
         memcpy(out_scores, ctx->qstage + bi, bs);
         if (out_count) memcpy(out_count, ctx->qstage + bi + bs, bc);
-        if (ctx->hc->tc_err) return fail(ctx, SLAG_ERR_TIMEOUT, "a tensor-core query kernel gave up waiting");
+        if (ctx->hc->tc_err) return timeout_reported(ctx, "a tensor-core query kernel gave up waiting");
     }
     return SLAG_OK;
 }
@@ -1864,6 +1917,29 @@ slag_status slag_state_merge_host(const void *a, int64_t a_bytes, const void *b,
     return SLAG_OK;
 }
 
+slag_status slag_set_linear_code(slag_ctx *ctx, const float *params) {
+    if (!ctx || !params) return SLAG_ERR_INVALID_ARG;
+    if (ctx->precision != SLAG_PREC_LINEAR32) return fail(ctx, SLAG_ERR_STATE, "context is not SLAG_PREC_LINEAR32");
+    if (ctx->stats.views > 0) return fail(ctx, SLAG_ERR_STATE, "slag_set_linear_code before the first view");
+    CK(cudaSetDevice(ctx->device));
+    const int64_t D = ctx->D, P = linear_param_count(ctx->D);
+    for (int64_t i = 0; i < P; ++i)
+        if (!std::isfinite(params[i])) return fail(ctx, SLAG_ERR_INVALID_ARG, "linear code: non-finite parameter");
+    // the encoder's constant: -mu U
+    std::vector<float> bias((size_t)kLatent);
+    for (int j = 0; j < kLatent; ++j) {
+        double acc = 0.0;
+        for (int64_t d = 0; d < D; ++d) acc += (double)params[D * kLatent + d] * (double)params[d * kLatent + j];
+        bias[(size_t)j] = (float)-acc;
+    }
+    if (!ctx->lin_params) CK(dalloc(&ctx->lin_params, P));
+    if (!ctx->lin_enc_bias) CK(dalloc(&ctx->lin_enc_bias, kLatent));
+    CK(cudaMemcpyAsync(ctx->lin_params, params, sizeof(float) * (size_t)P, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->lin_enc_bias, bias.data(), sizeof(float) * kLatent, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SLAG_OK;
+}
+
 slag_status slag_set_latent(slag_ctx *ctx, const float *params) {
     if (!ctx) return SLAG_ERR_INVALID_ARG;
     if (!params) return fail(ctx, SLAG_ERR_INVALID_ARG, "params is NULL");
@@ -1917,6 +1993,32 @@ slag_status slag_set_autotune(slag_ctx *ctx, int32_t enable) {
 
 uint64_t slag_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
+slag_status slag_debug_force_pair_capacity(slag_ctx *ctx, int64_t cap) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    if (!kChecked) return fail(ctx, SLAG_ERR_STATE, "not a checked build (-DSLAG_CHECKS)");
+    if (cap < 0) return fail(ctx, SLAG_ERR_INVALID_ARG, "cap < 0");
+    ctx->force_pair_cap = cap;
+    return SLAG_OK;
+}
+
+int32_t slag_is_checked_build(void) { return kChecked ? 1 : 0; }
+
+slag_status slag_check_wait_timeout(slag_ctx *ctx, int32_t limit_us, int32_t complete) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    if (limit_us < 1 || limit_us > 1000000) return fail(ctx, SLAG_ERR_INVALID_ARG, "limit_us outside 1 .. 1,000,000");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    slag_status s = launch_deferred_view(ctx);
+    if (s != SLAG_OK) return s;
+    CK(join_views(ctx));
+    launch_wait_check((uint64_t)limit_us * 1000ull, complete ? 1 : 0, ctx->tc_err, st);
+    launch_copy_words(ctx->tc_err, &ctx->hc_dev->tc_err, sizeof(uint32_t), st);
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (ctx->hc->tc_err) return timeout_reported(ctx, "a bounded mbarrier wait gave up (wait check)");
+    return SLAG_OK;
+}
+
 slag_status slag_get_stats(const slag_ctx *ctx, slag_stats *out) {
     if (!ctx || !out) return SLAG_ERR_INVALID_ARG;
     *out = ctx->stats;
@@ -1960,7 +2062,7 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
     dfree(ctx->table); dfree(ctx->inv_norm);
     dfree(ctx->qrows); dfree(ctx->qflags); dfree(ctx->qpos); dfree(ctx->d_nq);
-    dfree(ctx->lat_params); dfree(ctx->ztable); dfree(ctx->lat_hidden); dfree(ctx->lat_Z); dfree(ctx->lat_Y);
+    dfree(ctx->lat_params); dfree(ctx->lin_params); dfree(ctx->lin_enc_bias); dfree(ctx->ztable); dfree(ctx->lat_hidden); dfree(ctx->lat_Z); dfree(ctx->lat_Y);
     dfree(ctx->ehl); dfree(ctx->qinv); dfree(ctx->qhl);
     dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);
     scratch_free(ctx->scratch);
@@ -2068,6 +2170,9 @@ slag_status bin_view_diag(slag_ctx *ctx, const slag_camera *cam, int shift, uint
     uint32_t *keys = nullptr, *list = nullptr;
     const uint32_t *sgid = nullptr;
     s = bin_view(ctx, vs, st, cp, &P, &keys, &list, &sgid, shift);
+    if (s != SLAG_OK) return s;
+    CK(cudaStreamSynchronize(st));
+    s = checks_reported(ctx);
     if (s != SLAG_OK) return s;
     if (out_P) *out_P = P;
     const int64_t n = ctx->n;
@@ -2191,6 +2296,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     a.srec_a = vs.srec_a;
     a.srec_b = vs.srec_b;
     a.sgid = sgid;
+    a.n_ranks = vs.h->v.n_visible;
     a.weight_mode = ctx->weight_mode;
     a.ctr = vs.ctr;
     a.overflow = reinterpret_cast<uint32_t *>(&vs.ctr->pad[0]);
@@ -2225,7 +2331,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
         }
     release();
     if (bad) return fail(ctx, SLAG_ERR_CAPACITY, "a tile staged more Gaussians than its tile list holds");
-    return SLAG_OK;
+    return checks_reported(ctx);
 }
 
 slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_T, float *out_wsum,
@@ -2265,6 +2371,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.srec_a = vs.srec_a;
     a.srec_b = vs.srec_b;
     a.sgid = sgid;
+    a.n_ranks = vs.h->v.n_visible;
     a.seg = nullptr;
     a.weight_mode = ctx->weight_mode;
     a.ctr = vs.ctr;
@@ -2284,7 +2391,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     if (out_count) CK(cudaMemcpyAsync(out_count, ctx->dbg_count, sizeof(int32_t) * npx, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     (void)keys;
-    return SLAG_OK;
+    return checks_reported(ctx);
 }
 
 }  // extern "C"

@@ -17,6 +17,46 @@ void note_launch();
 // attribute call (cudaSuccess when it was already set on this device).
 cudaError_t set_max_smem(const void *fn, int bytes);
 
+// ---- the checked build (-DSLAG_CHECKS, libslag_checks.so) ------------------------------------
+// Index checks compiled into pair emission, the sort's scatter, compositing and aggregation: an
+// index outside its buffer is not used, and the stage's bit is set in a device word of the
+// translation unit; the host reads and clears the words at its synchronisation points and
+// returns SLAG_ERR_CAPACITY. In other builds SLAG_IN_BOUNDS is `true` and costs nothing.
+enum : uint32_t { kCheckEmit = 1u, kCheckSort = 2u, kCheckComposite = 4u, kCheckAggregate = 8u };
+#ifdef SLAG_CHECKS
+__device__ __forceinline__ bool check_index(bool ok, uint32_t *word, uint32_t bit) {
+    if (!ok) atomicOr(word, bit);
+    return ok;
+}
+#define SLAG_CHECKS_WORD static __device__ uint32_t g_check_word;
+#define SLAG_IN_BOUNDS(cond, bit) ::slag::check_index((cond), &g_check_word, (bit))
+#define SLAG_CHECKS_TAKE(fn)                                                                         \
+    uint32_t fn(cudaStream_t st) {                                                                   \
+        uint32_t v = 0, z = 0;                                                                       \
+        if (cudaMemcpyFromSymbolAsync(&v, g_check_word, sizeof(v), 0, cudaMemcpyDeviceToHost, st) != \
+            cudaSuccess)                                                                             \
+            return 0;                                                                                \
+        cudaStreamSynchronize(st);                                                                   \
+        if (v) {                                                                                     \
+            cudaMemcpyToSymbolAsync(g_check_word, &z, sizeof(z), 0, cudaMemcpyHostToDevice, st);     \
+            cudaStreamSynchronize(st);                                                               \
+        }                                                                                            \
+        return v;                                                                                    \
+    }
+constexpr bool kChecked = true;
+#else
+#define SLAG_CHECKS_WORD
+#define SLAG_IN_BOUNDS(cond, bit) true
+#define SLAG_CHECKS_TAKE(fn) \
+    uint32_t fn(cudaStream_t) { return 0; }
+constexpr bool kChecked = false;
+#endif
+// Reads and clears the check word of each translation unit (0 in unchecked builds).
+uint32_t checks_take_bin(cudaStream_t st);
+uint32_t checks_take_sort(cudaStream_t st);
+uint32_t checks_take_composite(cudaStream_t st);
+uint32_t checks_take_aggregate(cudaStream_t st);
+
 constexpr int kTile = 16;          // screen tile edge in pixels
 constexpr int kBlockG = 128;       // Gaussians per aggregation block (key packs g & 127)
 constexpr int kHashSlots = 4;      // per-view (segment, weight) slots per Gaussian
@@ -118,7 +158,7 @@ void launch_check_seg(const int32_t *seg, int64_t npx, int32_t M, ViewCounters *
 // k_bin.cu
 // One (bin, depth rank) pair per Gaussian-bin overlap; bins are 2^shift-tile squares,
 // bins_x of them per row.
-void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int shift, int bins_x,
+void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int shift, int bins_x, int64_t cap,
                  uint32_t *keys, uint32_t *vals, cudaStream_t st);
 void launch_ranges(const uint32_t *keys, int64_t P, uint2 *ranges, cudaStream_t st);
 // prect[i] = srect[list[i]]: the tile rectangle of each sorted pair's Gaussian.
@@ -195,6 +235,7 @@ struct CompositeArgs {
     const uint2 *prect;            // tile rectangle of the Gaussian of each sorted pair
     const float4 *srec_a, *srec_b; // records in depth-rank order
     const uint32_t *sgid;          // internal Gaussian index of each depth rank
+    uint32_t n_ranks;              // records (depth ranks) in srec_a / srec_b / sgid
     const int32_t *seg;            // H x W
     int32_t view_base;             // column of segment 0 of this view
     int32_t weight_mode;
@@ -250,6 +291,11 @@ void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t 
 // keys_in (in place when they alias); w_in (nullable) is copied to w_out alongside.
 void launch_repack_keys(const uint64_t *keys_in, uint64_t *keys_out, const float *w_in, float *w_out, int64_t Z,
                         int col_bits, bool to_compact, cudaStream_t st);
+// k_waits.cu: one role waits limit_ns on an mbarrier that completes only when `complete` is set,
+// a second role waits until the first releases it or aborts; err |= 1 (the first gave up), 2 (the
+// second was aborted).
+void launch_wait_check(uint64_t limit_ns, int complete, uint32_t *err, cudaStream_t st);
+
 // Accumulated state (slag_save_state / slag_merge_state): log entries to (caller index, column),
 // (caller index, column, W) back into the log with the columns shifted, and the per-Gaussian
 // compensated sums of another state added.
@@ -267,6 +313,7 @@ struct AggArgs {
     const uint32_t *uidx;          // exclusive prefix count of flags
     const uint32_t *ucol, *ustart, *bstart, *bend;
     const float *table;            // columns x D
+    int64_t columns;
     const float *s_hi, *s_lo, *s_ovf;
     const uint32_t *orig_of_int;
     int64_t n;
@@ -317,6 +364,16 @@ int64_t latent_decode_scratch(int rows, int32_t D);
 cudaError_t latent_decode(const float *params, int32_t D, const float *Z, int rows, float *scratch, float *Y,
                           uint32_t *err, cudaStream_t st);
 
+// The linear code (SLAG_PREC_LINEAR32): params = U (D x kLatent, row-major, input x output) then
+// mu (D). enc: Z = (X - mu) U, with enc_bias = -mu U; dec: Y = Z U^T + mu on the tensor cores
+// (the codes as TF32 hi/lo planes times U rounded to TF32); scratch: linear_decode_scratch floats.
+int64_t linear_param_count(int32_t D);
+void linear_encode(const float *params, const float *enc_bias, int32_t D, const float *X, int rows, float *Z,
+                   cudaStream_t st);
+int64_t linear_decode_scratch(int rows, int32_t D);
+cudaError_t linear_decode(const float *params, int32_t D, const float *Z, int rows, float *scratch, float *Y,
+                          uint32_t *err, cudaStream_t st);
+
 // k_query.cu
 size_t query_cand_entries(int32_t B, int64_t n, int32_t k);
 // per query: the best k of `per_query` candidates (score, index; index 0xffffffff = none);
@@ -334,11 +391,11 @@ void launch_touched_rows(const float *inv_norm, int64_t n, uint32_t *flags, uint
 
 // k_dense_tc.cu: dense layers on tcgen05. out = act(A W + b) for A given as TF32 hi/lo planes
 // (2 x rows_pad x K, rows_pad = dense_tc_pad_rows(rows)) and wt = the transposed, bfloat16-rounded
-// weights (N x K, launch_weights_t). gelu_planes: out receives gelu(A W + b) as TF32 hi/lo
+// weights (N x K, launch_weights_t; rounded to TF32 instead with tf32). gelu_planes: out receives gelu(A W + b) as TF32 hi/lo
 // planes (2 x rows_pad x N); otherwise float32 rows (rows x ldo). K % 32 == 0, N % 128 == 0.
 // *err is set when a wait gave up.
 int64_t dense_tc_pad_rows(int64_t rows);
-void launch_weights_t(const float *W, int32_t K, int32_t N, float *wt, cudaStream_t st);
+void launch_weights_t(const float *W, int32_t K, int32_t N, float *wt, cudaStream_t st, bool tf32 = false);
 cudaError_t launch_dense_tc(const float *a_planes, int64_t rows, int64_t rows_pad, int32_t K, const float *wt,
                             int32_t N, const float *bias, bool gelu_planes, float *out, int64_t ldo, uint32_t *err,
                             cudaStream_t st);

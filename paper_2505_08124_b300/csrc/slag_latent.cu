@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <random>
 #include <vector>
 
@@ -66,9 +67,89 @@ cudaError_t latent_decode(const float *p, int32_t D, const float *Z, int rows, f
     return launch_dense_tc(Hp, rows, rp, kLatentHidden, W4t, D, p + o.b4, false, Y, D, err, st);
 }
 
+int64_t linear_param_count(int32_t D) { return (int64_t)D * (kLatent + 1); }
+
+void linear_encode(const float *params, const float *enc_bias, int32_t D, const float *X, int rows, float *Z,
+                   cudaStream_t st) {
+    latent_gemm(false, false, rows, kLatent, D, X, D, params, kLatent, Z, kLatent, enc_bias, false, nullptr, false, false,
+                false, st);
+}
+
+int64_t linear_decode_scratch(int rows, int32_t D) {
+    return dense_tc_pad_rows(rows) * 2 * kLatent + (int64_t)D * kLatent;
+}
+
+cudaError_t linear_decode(const float *params, int32_t D, const float *Z, int rows, float *scratch, float *Y,
+                          uint32_t *err, cudaStream_t st) {
+    const int64_t rp = dense_tc_pad_rows(rows);
+    float *Zp = scratch;                         // 2 x rp x kLatent
+    float *Ut = Zp + rp * 2 * kLatent;           // D x kLatent
+    launch_tf32_planes(Z, rows, rp, kLatent, Zp, st);
+    launch_weights_t(params, kLatent, D, Ut, st, true);
+    return launch_dense_tc(Zp, rows, rp, kLatent, Ut, D, params + (int64_t)D * kLatent, false, Y, D, err, st);
+}
+
 }  // namespace slag
 
 using namespace slag;
+
+namespace {
+
+// Symmetric eigenpairs of a small matrix by cyclic Jacobi rotations (float64): A (k x k, row-major,
+// overwritten) -> eigenvalues in w, eigenvectors in the columns of V.
+void jacobi_eigen(std::vector<double> &A, int k, std::vector<double> &w, std::vector<double> &V) {
+    V.assign((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i) V[(size_t)i * k + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) off += A[(size_t)p * k + q] * A[(size_t)p * k + q];
+        if (off < 1e-30) break;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                const double apq = A[(size_t)p * k + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                const double app = A[(size_t)p * k + p], aqq = A[(size_t)q * k + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < k; ++r) {   // A <- A J (columns p, q)
+                    const double arp = A[(size_t)r * k + p], arq = A[(size_t)r * k + q];
+                    A[(size_t)r * k + p] = c * arp - s * arq;
+                    A[(size_t)r * k + q] = s * arp + c * arq;
+                }
+                for (int r = 0; r < k; ++r) {   // A <- J^T A (rows p, q)
+                    const double apr = A[(size_t)p * k + r], aqr = A[(size_t)q * k + r];
+                    A[(size_t)p * k + r] = c * apr - s * aqr;
+                    A[(size_t)q * k + r] = s * apr + c * aqr;
+                }
+                for (int r = 0; r < k; ++r) {   // V <- V J
+                    const double vrp = V[(size_t)r * k + p], vrq = V[(size_t)r * k + q];
+                    V[(size_t)r * k + p] = c * vrp - s * vrq;
+                    V[(size_t)r * k + q] = s * vrp + c * vrq;
+                }
+            }
+    }
+    w.resize((size_t)k);
+    for (int i = 0; i < k; ++i) w[(size_t)i] = A[(size_t)i * k + i];
+}
+
+// Orthonormal columns of V (D x k, row-major) by modified Gram-Schmidt.
+void orthonormalise(std::vector<double> &V, int D, int k) {
+    for (int j = 0; j < k; ++j) {
+        for (int i = 0; i < j; ++i) {
+            double d = 0.0;
+            for (int r = 0; r < D; ++r) d += V[(size_t)r * k + i] * V[(size_t)r * k + j];
+            for (int r = 0; r < D; ++r) V[(size_t)r * k + j] -= d * V[(size_t)r * k + i];
+        }
+        double nrm = 0.0;
+        for (int r = 0; r < D; ++r) nrm += V[(size_t)r * k + j] * V[(size_t)r * k + j];
+        nrm = std::sqrt(nrm);
+        for (int r = 0; r < D; ++r) V[(size_t)r * k + j] = nrm > 0 ? V[(size_t)r * k + j] / nrm : 0.0;
+    }
+}
+
+}  // namespace
 
 namespace {
 
@@ -83,6 +164,115 @@ cudaError_t dmalloc(T **p, int64_t count) {
 extern "C" {
 
 int64_t slag_latent_param_count(int32_t dim) { return dim >= 32 ? latent_layout(dim).total : 0; }
+
+int64_t slag_linear_param_count(int32_t dim) { return dim >= 32 ? linear_param_count(dim) : 0; }
+
+slag_status slag_linear_code_fit(const float *samples, int64_t n, int32_t dim, int32_t on_device, float *out_params,
+                                 float *out_kept, void *cuda_stream) {
+    if (!samples || !out_params || n < 2 || n >= (1LL << 31) || dim < 32 || dim > 4096 || dim % 32 != 0)
+        return SLAG_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int D = dim, k = kLatent;
+    float *dX = nullptr, *dsum = nullptr, *dC = nullptr;
+    auto cleanup = [&]() {
+        if (dX && !on_device) cudaFree(dX);
+        if (dsum) cudaFree(dsum);
+        if (dC) cudaFree(dC);
+    };
+#define CF(call)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            cleanup();                                                                                   \
+            return e_ == cudaErrorMemoryAllocation ? SLAG_ERR_OOM : SLAG_ERR_CUDA;                       \
+        }                                                                                                \
+    } while (0)
+    if (on_device) {
+        dX = const_cast<float *>(samples);
+    } else {
+        CF(dmalloc(&dX, n * D));
+        CF(cudaMemcpyAsync(dX, samples, sizeof(float) * (size_t)(n * D), cudaMemcpyHostToDevice, st));
+    }
+    CF(dmalloc(&dsum, D));
+    CF(dmalloc(&dC, (int64_t)D * D));
+    // column sums and the second moment X^T X on the device (float32 accumulation)
+    latent_colsum(dX, (int)n, D, dsum, st);
+    latent_gemm(true, false, D, D, (int)n, dX, D, dX, D, dC, D, nullptr, false, nullptr, false, false, false, st);
+    std::vector<float> hs((size_t)D), hC((size_t)D * D);
+    CF(cudaMemcpyAsync(hs.data(), dsum, sizeof(float) * D, cudaMemcpyDeviceToHost, st));
+    CF(cudaMemcpyAsync(hC.data(), dC, sizeof(float) * (size_t)D * D, cudaMemcpyDeviceToHost, st));
+    CF(cudaStreamSynchronize(st));
+    CF(cudaGetLastError());
+#undef CF
+    cleanup();
+    // covariance in float64, then its top-k eigenvectors by subspace iteration with a Rayleigh-Ritz
+    // step (the principal directions of the samples)
+    std::vector<double> mu((size_t)D), C((size_t)D * D);
+    for (int i = 0; i < D; ++i) mu[(size_t)i] = (double)hs[(size_t)i] / (double)n;
+    double trace = 0.0;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            const double c = 0.5 * ((double)hC[(size_t)i * D + j] + (double)hC[(size_t)j * D + i]) / (double)n -
+                             mu[(size_t)i] * mu[(size_t)j];
+            C[(size_t)i * D + j] = c;
+            if (i == j) trace += c;
+        }
+    std::vector<double> V((size_t)D * k), W((size_t)D * k), H((size_t)k * k), ev, R;
+    std::mt19937_64 rng(12345);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    for (auto &x : V) x = nd(rng);
+    orthonormalise(V, D, k);
+    std::vector<double> prev((size_t)k, 0.0);
+    for (int it = 0; it < 1000; ++it) {
+        for (int r = 0; r < D; ++r)
+            for (int j = 0; j < k; ++j) {
+                double acc = 0.0;
+                for (int c = 0; c < D; ++c) acc += C[(size_t)r * D + c] * V[(size_t)c * k + j];
+                W[(size_t)r * k + j] = acc;
+            }
+        // Rayleigh quotients of the current basis, for the convergence test
+        double change = 0.0;
+        for (int j = 0; j < k; ++j) {
+            double q = 0.0;
+            for (int r = 0; r < D; ++r) q += V[(size_t)r * k + j] * W[(size_t)r * k + j];
+            change = std::max(change, std::fabs(q - prev[(size_t)j]) / std::max(std::fabs(q), 1e-300));
+            prev[(size_t)j] = q;
+        }
+        V.swap(W);
+        orthonormalise(V, D, k);
+        if (it > 8 && change < 1e-12) break;
+    }
+    // Rayleigh-Ritz: H = V^T C V, rotate V onto its eigenvectors, largest first
+    for (int r = 0; r < D; ++r)
+        for (int j = 0; j < k; ++j) {
+            double acc = 0.0;
+            for (int c = 0; c < D; ++c) acc += C[(size_t)r * D + c] * V[(size_t)c * k + j];
+            W[(size_t)r * k + j] = acc;
+        }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            double acc = 0.0;
+            for (int r = 0; r < D; ++r) acc += V[(size_t)r * k + i] * W[(size_t)r * k + j];
+            H[(size_t)i * k + j] = acc;
+        }
+    jacobi_eigen(H, k, ev, R);
+    std::vector<int> order((size_t)k);
+    for (int i = 0; i < k; ++i) order[(size_t)i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return ev[(size_t)a] > ev[(size_t)b]; });
+    double kept = 0.0;
+    for (int j = 0; j < k; ++j) {
+        const int src = order[(size_t)j];
+        kept += ev[(size_t)src];
+        for (int r = 0; r < D; ++r) {
+            double acc = 0.0;
+            for (int i = 0; i < k; ++i) acc += V[(size_t)r * k + i] * R[(size_t)i * k + src];
+            out_params[(int64_t)r * k + j] = (float)acc;
+        }
+    }
+    for (int r = 0; r < D; ++r) out_params[(int64_t)D * k + r] = (float)mu[(size_t)r];
+    if (out_kept) *out_kept = trace > 0 ? (float)(kept / trace) : 0.f;
+    return SLAG_OK;
+}
 
 slag_status slag_latent_train(const float *samples, int64_t n, int32_t dim, int32_t epochs, int32_t batch, float lr,
                               uint64_t seed, int32_t on_device, float *out_params, float *out_loss,

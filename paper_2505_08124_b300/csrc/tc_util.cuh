@@ -43,15 +43,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase of `parity` to complete; false after ~1 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // bound of every wait of the library's kernels: ~1 s
+
+// Bounded wait for the phase of `parity` to complete; false after limit_ns of globaltimer.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (gtimer() - t0 > 1000000000ull) return false;
+        if (gtimer() - t0 > limit_ns) return false;
     }
     return true;
 }
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) { return mbar_wait_for(bar, parity, kWaitLimitNs); }
 
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
@@ -152,19 +156,24 @@ __device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo
 
 // ---- TMA-fed, warp-specialised kernels ----------------------------------------------------
 
-// Bounded wait that also gives up once *abort is set (another role gave up); a timeout (~1 s of
+// Bounded wait that also gives up once *abort is set (another role gave up); a timeout (limit_ns of
 // globaltimer) sets *abort.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile uint32_t *abort) {
+__device__ __forceinline__ bool wait_or_abort_for(uint64_t *bar, uint32_t parity, volatile uint32_t *abort,
+                                                  uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort) return false;
-        if (gtimer() - t0 > 1000000000ull) {
+        if (gtimer() - t0 > limit_ns) {
             *abort = 1u;
             return false;
         }
     }
     return true;
+}
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile uint32_t *abort) {
+    return wait_or_abort_for(bar, parity, abort, kWaitLimitNs);
 }
 
 __device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {

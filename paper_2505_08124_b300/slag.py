@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libslag.so")
+CHECKED_LIB_PATH = os.path.join(_HERE, "libslag_checks.so")   # compiled with -DSLAG_CHECKS
 
 OK = 0
 ERR_INVALID_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY = 1, 2, 3, 4, 5, 6
@@ -23,6 +24,7 @@ WEIGHT_ALPHA_T, WEIGHT_KERNEL = 0, 1
 PREC_FP32 = 0
 PREC_BF16 = 1
 PREC_LATENT32 = 2
+PREC_LINEAR32 = 3
 FLAG_EMBEDDINGS_ON_HOST = 1
 
 
@@ -68,7 +70,9 @@ EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_
            "slag_export_partitions", "slag_latent_param_count", "slag_latent_train", "slag_latent_apply",
            "slag_set_latent", "slag_add_views_batched", "slag_set_autotune", "slag_finalize_async",
            "slag_wait_outputs", "slag_set_profiling_stages", "slag_bin_view_bins", "slag_composite_trace",
-           "slag_save_state", "slag_load_state", "slag_merge_state", "slag_state_merge_host")
+           "slag_save_state", "slag_load_state", "slag_merge_state", "slag_state_merge_host",
+           "slag_check_wait_timeout", "slag_is_checked_build", "slag_debug_force_pair_capacity",
+           "slag_linear_param_count", "slag_linear_code_fit", "slag_set_linear_code")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -102,6 +106,9 @@ def load_library(path: str = LIB_PATH):
     lib.slag_destroy.restype = None
     lib.slag_bin_view.argtypes = [P, ctypes.POINTER(CCamera), P, P, P, i64, P]
     lib.slag_render_debug.argtypes = [P, ctypes.POINTER(CCamera), P, P, P]
+    lib.slag_check_wait_timeout.argtypes = [P, i32, i32]
+    lib.slag_is_checked_build.argtypes = []
+    lib.slag_debug_force_pair_capacity.argtypes = [P, i64]
     lib.slag_save_state.argtypes = [P, P, i64, ctypes.POINTER(i64)]
     lib.slag_load_state.argtypes = [P, P, i64]
     lib.slag_merge_state.argtypes = [P, P, i64]
@@ -117,6 +124,10 @@ def load_library(path: str = LIB_PATH):
     lib.slag_latent_train.argtypes = [P, i64, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, i32, P, P, P]
     lib.slag_latent_apply.argtypes = [P, i32, P, i64, i32, P, P]
     lib.slag_set_latent.argtypes = [P, P]
+    lib.slag_linear_param_count.argtypes = [i32]
+    lib.slag_linear_param_count.restype = i64
+    lib.slag_linear_code_fit.argtypes = [P, i64, i32, i32, P, P, P]
+    lib.slag_set_linear_code.argtypes = [P, P]
     lib.slag_add_views_batched.argtypes = [i32, P, P, P, ctypes.POINTER(i32)]
     lib.slag_set_autotune.argtypes = [P, i32]
     lib.slag_kernel_launches.argtypes = []
@@ -197,7 +208,7 @@ class Lifter:
 
     def __init__(self, gaussians, dim: int = 512, weight_mode: int = WEIGHT_ALPHA_T,
                  stream: Optional[int] = None, precision: int = PREC_FP32, embeddings_on_host: bool = False,
-                 latent_params=None):
+                 latent_params=None, linear_code=None):
         self._lib = load_library()
         self.n = int(gaussians.means.shape[0])
         self.dim = int(dim)
@@ -216,6 +227,12 @@ class Lifter:
         if latent_params is not None:
             lp = np.ascontiguousarray(latent_params, np.float32)
             self._check(self._lib.slag_set_latent(self._h, lp.ctypes.data_as(ctypes.c_void_p)), "slag_set_latent")
+        if linear_code is not None:
+            lc = np.ascontiguousarray(linear_code, np.float32)
+            if lc.size != linear_param_count(self.dim):
+                raise ValueError("linear code has %d parameters, expected %d" % (lc.size, linear_param_count(self.dim)))
+            self._check(self._lib.slag_set_linear_code(self._h, lc.ctypes.data_as(ctypes.c_void_p)),
+                        "slag_set_linear_code")
 
     # -- helpers --------------------------------------------------------------
     def _check(self, rc: int, what: str):
@@ -327,6 +344,14 @@ class Lifter:
                                                      int(chunk_gaussians), ctypes.byref(written)),
                     "slag_export_partitions")
         return int(written.value)
+
+    def check_wait_timeout(self, limit_us: int, complete: bool = False) -> int:
+        """Runs the bounded-wait check (slag_check_wait_timeout); returns the status code."""
+        return int(self._lib.slag_check_wait_timeout(self._h, int(limit_us), 1 if complete else 0))
+
+    def debug_force_pair_capacity(self, cap: int) -> int:
+        """Checked build only (slag_debug_force_pair_capacity); returns the status code."""
+        return int(self._lib.slag_debug_force_pair_capacity(self._h, int(cap)))
 
     def save_state(self) -> np.ndarray:
         """The accumulated state (slag_save_state) as a uint8 array."""
@@ -502,6 +527,25 @@ def read_state(state) -> dict:
     w = np.frombuffer(buf, np.float32, Z, o + 8 * Z)
     return {"header": {k: h[k] for k in STATE_HEADER.names}, "table": table, "w_hi": sums[0], "w_lo": sums[1],
             "w_ovf": sums[2], "gauss": g, "column": c, "w": w}
+
+
+def linear_param_count(dim: int) -> int:
+    return int(load_library().slag_linear_param_count(int(dim)))
+
+
+def linear_code_fit(samples):
+    """The linear 32-d code of host samples (n x dim float32): (parameters U then mu, fraction of
+    the variance kept)."""
+    lib = load_library()
+    X = np.ascontiguousarray(samples, np.float32)
+    n, dim = X.shape
+    params = np.empty(linear_param_count(dim), np.float32)
+    kept = ctypes.c_float()
+    rc = lib.slag_linear_code_fit(X.ctypes.data_as(ctypes.c_void_p), n, dim, 0, params.ctypes.data_as(ctypes.c_void_p),
+                                  ctypes.byref(kept), None)
+    if rc != OK:
+        raise SlagError(rc, "slag_linear_code_fit")
+    return params, float(kept.value)
 
 
 def latent_param_count(dim: int) -> int:
