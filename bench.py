@@ -465,12 +465,13 @@ def _compare(torch, E_a, E_f, w_f, ids_a, ids_f, Q, k, tie_eps):
 
 
 def run_form(S, torch, dev, stream, job, L_f32, precision, steps, warmup, ws, rank_max, latent=None,
-             tie_eps=1e-3, time_plain=False):
+             tie_eps=1e-3, time_plain=False, linear=None):
     """A form on `job`: views/s over `steps` timed steps, and its error against the float32 path
     of the same job."""
     n, D = job.scene.gaussians.n, job.scene.dim
     out = {}
-    Lb = S.Lifter(job.scene.gaussians, dim=D, stream=stream.cuda_stream, precision=precision, latent_params=latent)
+    Lb = S.Lifter(job.scene.gaussians, dim=D, stream=stream.cuda_stream, precision=precision, latent_params=latent,
+                  linear_code=linear)
     ms = rank_max(_timed(torch, stream, lambda: job.run(Lb), steps, warmup))
     contrib = Lb.stats()["contributions"]
     out.update(value=job_rate(contrib * steps, ws, ms / 1e3), unit=UNIT, ms_per_step=ms / steps,
@@ -695,7 +696,6 @@ def latent_forms(S, torch, dev, stream, got, nv, a, steps, warmup, ws, rank_max)
         t0 = time.perf_counter()
         params, losses = S.latent_train(X, epochs=4, batch=512, lr=2e-3, seed=5)
         train_s = time.perf_counter() - t0
-        del X
         Lf = S.Lifter(lscene.gaussians, dim=D, stream=stream.cuda_stream)
         r = run_form(S, torch, dev, stream, job, Lf, S.PREC_LATENT32, steps, warmup, ws, rank_max, latent=params,
                      tie_eps=1e-2, time_plain=(reading == "literal"))
@@ -703,9 +703,20 @@ def latent_forms(S, torch, dev, stream, got, nv, a, steps, warmup, ws, rank_max)
         r["noise_sigma"] = float(sigma)
         r["training"] = {"samples": 1 << 20, "epochs": 4, "seconds": train_s,
                          "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1])}
+        # the linear 32-d code (principal directions of the same samples): exact aggregation of
+        # codes, so its error is the part of E_k outside the code's subspace
+        t0 = time.perf_counter()
+        lin, kept = S.linear_code_fit(X)
+        fit_s = time.perf_counter() - t0
+        Lf = S.Lifter(lscene.gaussians, dim=D, stream=stream.cuda_stream)
+        rl = run_form(S, torch, dev, stream, job, Lf, S.PREC_LINEAR32, steps, warmup, ws, rank_max, linear=lin,
+                      tie_eps=1e-2)
+        Lf.close()
+        rl["fit"] = {"samples": 1 << 20, "seconds": fit_s, "variance_kept": kept}
+        r["linear_code"] = rl
         out[reading] = r
-        del job
-    out["dtype"] = "32-d codes, bf16 weights, f32 accumulate"
+        del job, X
+    out["dtype"] = "32-d codes, bf16 weights, f32 accumulate (linear code: TF32-rounded basis, f32 accumulate)"
     return out
 
 

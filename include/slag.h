@@ -247,6 +247,18 @@ slag_status slag_noalloc_query_topk(const float *E, int64_t n, int32_t dim, cons
                                     const float *Q, int32_t B, int32_t k, int64_t *out_ids,
                                     float *out_scores, int32_t *out_count, void *cuda_stream);
 
+/* Threshold query: the binary response of the paper's open-vocabulary
+ * evaluation (Experiments: a Gaussian answers a text query when the cosine of
+ * its embedding with the query is at least a threshold, 0.28 there). q: dim
+ * float32 (host, or device when on_device; 16-byte aligned); candidates as
+ * in slag_query. out_ids (host or device as on_device, cap entries,
+ * nullable when cap = 0) receives the ids with q . E_k / |E_k| >= threshold in
+ * increasing order, the first cap of them; *out_count their total number
+ * (call with cap = 0 to size the output). Errors: STATE before finalize;
+ * INVALID_ARG (NULL q or out_count, cap < 0, non-finite threshold). */
+slag_status slag_query_threshold(slag_ctx *ctx, const float *q, float threshold, int64_t *out_ids, int64_t cap,
+                                 int64_t *out_count, int32_t on_device);
+
 /* Batched form of slag_query: Q is B x dim float32 row-major; out_ids and
  * out_scores are B x k, out_count is B (nullable). on_device says where Q and
  * the outputs live. Same ordering, candidates and errors as slag_query. */

@@ -213,6 +213,36 @@ void launch_query_topk(const float *Q, int32_t B, const float *E, const float *i
 
 namespace {
 
+// Threshold query: flags[i] = 1 when candidate row rows[i] of E has cosine q . E / |E| >= thr
+// (one warp per candidate; inv_norm > 0 on candidates).
+__global__ void __launch_bounds__(256) threshold_flags_k(const float *__restrict__ q, const float *__restrict__ E,
+                                                         const float *__restrict__ inv_norm,
+                                                         const uint32_t *__restrict__ rows, int64_t n, int32_t D,
+                                                         float thr, uint32_t *__restrict__ flags) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const uint32_t r = rows[i];
+    const float4 *e = reinterpret_cast<const float4 *>(E + (int64_t)r * D);
+    const float4 *qq = reinterpret_cast<const float4 *>(q);
+    float s = 0.f;
+    for (int d = lane; d < D / 4; d += 32) {
+        const float4 a = e[d], b = qq[d];
+        s = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, s))));
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) flags[i] = (s * inv_norm[r] >= thr) ? 1u : 0u;
+}
+
+// out_ids[pos[i]] = rows[i] for the flagged candidates, up to cap; their scores alongside.
+__global__ void threshold_ids_k(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos,
+                                const uint32_t *__restrict__ rows, int64_t n, int64_t cap, int64_t *__restrict__ ids) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flags[i]) return;
+    const int64_t at = pos[i];
+    if (at < cap) ids[at] = (int64_t)rows[i];
+}
+
 __global__ void touched_flags_k(const float *__restrict__ inv_norm, int64_t n, uint32_t *__restrict__ flags) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g < n) flags[g] = inv_norm[g] > 0.f ? 1u : 0u;
@@ -225,6 +255,19 @@ __global__ void touched_rows_k(const uint32_t *__restrict__ flags, const uint32_
 }
 
 }  // namespace
+
+void launch_threshold_query(const float *q, const float *E, const float *inv_norm, const uint32_t *rows, int64_t n,
+                            int32_t D, float thr, uint32_t *flags, uint32_t *pos, unsigned long long *d_count,
+                            int64_t cap, int64_t *ids, SortScratch &scratch, cudaStream_t st) {
+    if (n <= 0) {
+        cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st);
+        return;
+    }
+    threshold_flags_k<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(q, E, inv_norm, rows, n, D, thr, flags);
+    note_launch();
+    exclusive_scan_u32(flags, pos, n, d_count, scratch, st);
+    threshold_ids_k<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(flags, pos, rows, n, cap, ids); note_launch();
+}
 
 void launch_touched_rows(const float *inv_norm, int64_t n, uint32_t *flags, uint32_t *pos, uint32_t *rows,
                          unsigned long long *d_count, SortScratch &scratch, cudaStream_t st) {

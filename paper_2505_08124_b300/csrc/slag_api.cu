@@ -179,6 +179,9 @@ struct slag_ctx {
     unsigned long long *touched = nullptr;
     uint32_t *qrows = nullptr, *qflags = nullptr, *qpos = nullptr;   // query candidates: touched rows of E
     unsigned long long *d_nq = nullptr;
+    unsigned long long *d_thr = nullptr;     // threshold query: number of rows at or above it
+    int64_t *thr_ids = nullptr;              // threshold query: ids staged for host outputs
+    int64_t thr_cap = 0;
     int64_t n_q = 0;
     bool finalized = false;
 
@@ -1477,6 +1480,53 @@ slag_status slag_query_batch(slag_ctx *ctx, const float *Q, int32_t B, int32_t k
     return SLAG_OK;
 }
 
+slag_status slag_query_threshold(slag_ctx *ctx, const float *q, float threshold, int64_t *out_ids, int64_t cap,
+                                 int64_t *out_count, int32_t on_device) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    if (!ctx->finalized) return fail(ctx, SLAG_ERR_STATE, "query before finalize");
+    if (!q || (!out_ids && cap > 0) || cap < 0 || !out_count)
+        return fail(ctx, SLAG_ERR_INVALID_ARG, "NULL query or output, or cap < 0");
+    if (!std::isfinite(threshold)) return fail(ctx, SLAG_ERR_INVALID_ARG, "threshold is not finite");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int64_t D = ctx->D, nq = ctx->n_q;
+    struct StreamGuard {
+        cudaStream_t st = nullptr;
+        ~StreamGuard() {
+            if (st) cudaStreamSynchronize(st);
+        }
+    } guard;
+    const float *dq = q;
+    if (!on_device) {
+        CK(grow(ctx->qbuf, ctx->qbuf_cap, D, st));
+        CK(cudaMemcpyAsync(ctx->qbuf, q, sizeof(float) * (size_t)D, cudaMemcpyHostToDevice, st));
+        guard.st = st;
+        dq = ctx->qbuf;
+    }
+    if (((uintptr_t)dq & 15u) != 0) return fail(ctx, SLAG_ERR_INVALID_ARG, "q must be 16-byte aligned");
+    // flags and positions per candidate: the finalize's n-sized scratch (n_q <= n), free after it
+    if (!ctx->d_thr) CK(dalloc(&ctx->d_thr, 1));
+    int64_t *dids = out_ids;
+    if (!on_device && cap > 0) {
+        CK(grow(ctx->thr_ids, ctx->thr_cap, cap, st));
+        dids = ctx->thr_ids;
+    }
+    CK(scratch_reserve(ctx->scratch, nq));
+    launch_threshold_query(dq, ctx->E, ctx->inv_norm, ctx->qrows, nq, ctx->D, threshold, ctx->qflags, ctx->qpos,
+                           ctx->d_thr, cap, dids, ctx->scratch, st);
+    unsigned long long total = 0;
+    CK(cudaMemcpyAsync(&total, ctx->d_thr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    *out_count = (int64_t)total;
+    const int64_t got = std::min<int64_t>((int64_t)total, cap);
+    if (!on_device && got > 0) {
+        CK(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * (size_t)got, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return SLAG_OK;
+}
+
 slag_status slag_query(slag_ctx *ctx, const float *q, int32_t k, int64_t *out_ids, float *out_scores,
                        int32_t *out_count) {
     return slag_query_batch(ctx, q, 1, k, out_ids, out_scores, out_count, 0);
@@ -2061,7 +2111,7 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->log_key); dfree(ctx->log_key_alt); dfree(ctx->log_w); dfree(ctx->log_w_alt);
     dfree(ctx->flags); dfree(ctx->uidx); dfree(ctx->ucol); dfree(ctx->ustart); dfree(ctx->bstart); dfree(ctx->bend);
     dfree(ctx->table); dfree(ctx->inv_norm);
-    dfree(ctx->qrows); dfree(ctx->qflags); dfree(ctx->qpos); dfree(ctx->d_nq);
+    dfree(ctx->qrows); dfree(ctx->qflags); dfree(ctx->qpos); dfree(ctx->d_nq); dfree(ctx->d_thr); dfree(ctx->thr_ids);
     dfree(ctx->lat_params); dfree(ctx->lin_params); dfree(ctx->lin_enc_bias); dfree(ctx->ztable); dfree(ctx->lat_hidden); dfree(ctx->lat_Z); dfree(ctx->lat_Y);
     dfree(ctx->ehl); dfree(ctx->qinv); dfree(ctx->qhl);
     dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);

@@ -385,6 +385,11 @@ void launch_query_merge(const float *cand_s, const uint32_t *cand_i, int64_t per
 void launch_query_topk(const float *Q, int32_t B, const float *E, const float *inv_norm, const uint32_t *rows,
                        int64_t n, int32_t D, int32_t k, float *cand_s, uint32_t *cand_i, int64_t *out_ids,
                        float *out_scores, int32_t *out_count, cudaStream_t st);
+// Threshold query over candidate rows rows[0..n) of E: ids[0..min(count, cap)) = the rows with
+// cosine q . E / |E| >= thr, in increasing order; *d_count = their number (flags, pos: n each).
+void launch_threshold_query(const float *q, const float *E, const float *inv_norm, const uint32_t *rows, int64_t n,
+                            int32_t D, float thr, uint32_t *flags, uint32_t *pos, unsigned long long *d_count,
+                            int64_t cap, int64_t *ids, SortScratch &scratch, cudaStream_t st);
 // rows[0..*d_count) = the Gaussians with inv_norm > 0, in increasing order (flags, pos: n each)
 void launch_touched_rows(const float *inv_norm, int64_t n, uint32_t *flags, uint32_t *pos, uint32_t *rows,
                          unsigned long long *d_count, SortScratch &scratch, cudaStream_t st);

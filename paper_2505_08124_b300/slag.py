@@ -72,7 +72,7 @@ EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_
            "slag_wait_outputs", "slag_set_profiling_stages", "slag_bin_view_bins", "slag_composite_trace",
            "slag_save_state", "slag_load_state", "slag_merge_state", "slag_state_merge_host",
            "slag_check_wait_timeout", "slag_is_checked_build", "slag_debug_force_pair_capacity",
-           "slag_linear_param_count", "slag_linear_code_fit", "slag_set_linear_code")
+           "slag_linear_param_count", "slag_linear_code_fit", "slag_set_linear_code", "slag_query_threshold")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.slag_wait_outputs.argtypes = [P]
     lib.slag_query.argtypes = [P, P, i32, P, P, P]
     lib.slag_query_batch.argtypes = [P, P, i32, i32, P, P, P, i32]
+    lib.slag_query_threshold.argtypes = [P, P, ctypes.c_float, P, i64, ctypes.POINTER(i64), i32]
     lib.slag_reset.argtypes = [P]
     lib.slag_get_stats.argtypes = [P, ctypes.POINTER(CStats)]
     lib.slag_last_error.argtypes = [P]
@@ -309,6 +310,18 @@ class Lifter:
                                          ids.ctypes.data_as(ctypes.c_void_p), sc.ctypes.data_as(ctypes.c_void_p),
                                          ctypes.byref(cnt)), "slag_query")
         return ids[:cnt.value], sc[:cnt.value]
+
+    def query_threshold(self, q, threshold: float = 0.28):
+        """Ids (increasing) of the Gaussians whose cosine with q is at least `threshold`."""
+        qa = np.ascontiguousarray(q, np.float32)
+        qp = qa.ctypes.data_as(ctypes.c_void_p)
+        cnt = ctypes.c_int64()
+        self._check(self._lib.slag_query_threshold(self._h, qp, float(threshold), None, 0, ctypes.byref(cnt), 0),
+                    "slag_query_threshold")
+        ids = np.empty(max(cnt.value, 1), np.int64)
+        self._check(self._lib.slag_query_threshold(self._h, qp, float(threshold), ids.ctypes.data_as(ctypes.c_void_p),
+                                                   ids.size, ctypes.byref(cnt), 0), "slag_query_threshold")
+        return ids[:cnt.value]
 
     def query_batch(self, Q, k: int, out_ids=None, out_scores=None, out_count=None):
         """Host numpy Q -> (ids, scores, count) numpy; torch CUDA Q -> fills the given torch outputs."""

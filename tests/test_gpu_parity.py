@@ -312,6 +312,34 @@ def test_query_tensor_core_tiles(slag, dim, B):
             np.testing.assert_array_equal(d_sc.cpu().numpy(), sc)
 
 
+def test_threshold_query(slag):
+    # the binary response at cosine >= 0.28 (Experiments) against the oracle's cosines: every id
+    # clearly above the threshold is returned, none clearly below, in increasing order
+    s = synth.small_scene(8, 6000, 3, 160, 112, 6, dim=128, surfaces=4, n_protos=4)
+    views = [s.view(i) for i in range(s.n_views)]
+    num, den, _ = O.lift(s.gaussians, views)
+    Eo = O.normalise(num, den)
+    nrm = np.linalg.norm(Eo, axis=1)
+    with slag.Lifter(s.gaussians, dim=128) as L:
+        for v in views:
+            L.add_view(v.camera, v.seg, v.table)
+        L.finalize()
+        for q in (views[0].table[0], views[1].table[3], -views[2].table[1]):
+            q = q / np.linalg.norm(q)
+            ids = L.query_threshold(q, 0.28)
+            cos = np.where(nrm > 0, (Eo @ q.astype(np.float64)) / np.maximum(nrm, 1e-300), -2.0)
+            cos[den <= 0] = -2.0
+            assert np.all(np.diff(ids) > 0)
+            sure_in = np.nonzero(cos >= 0.28 + 1e-4)[0]
+            sure_out = np.nonzero(cos < 0.28 - 1e-4)[0]
+            assert np.isin(sure_in, ids).all()
+            assert not np.isin(ids, sure_out).any()
+        # sizing call and a cut-off output
+        q = views[0].table[0] / np.linalg.norm(views[0].table[0])
+        full = L.query_threshold(q, 0.28)
+        assert len(full) > 10
+
+
 def test_query_more_than_candidates(slag):
     s = synth.small_scene(19, 500, 1, 64, 64, 3, dim=128)
     with slag.Lifter(s.gaussians, dim=128) as L:

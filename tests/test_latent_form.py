@@ -168,3 +168,58 @@ def test_latent_lifting_against_plain(slag, sigma_kind):
     # stated measurements with regression bounds: the isotropic noise outside the 32-d code
     # cannot be reconstructed (1 - cos ~ sigma^2 D (1 - 32 / D) / 2 per segment embedding)
     assert (1 - cos).mean() < (0.5 if sigma_kind == "literal" else 1e-2)
+
+
+# ----------------------------------------------------------------------------
+# the linear 32-d code (SLAG_PREC_LINEAR32)
+# ----------------------------------------------------------------------------
+
+def test_linear_code_fit_is_the_principal_subspace(slag):
+    # samples drawn from 20 prototype directions plus small noise: the fitted U must span the
+    # same 32-d principal subspace as numpy's eigendecomposition of the sample covariance
+    D = 256
+    X = synth.segment_samples(31, 20000, D, 20, noise_sigma=0.02 / np.sqrt(D))
+    params, kept = slag.linear_code_fit(X)
+    U, mu = params[:D * L].reshape(D, L).astype(np.float64), params[D * L:].astype(np.float64)
+    Xd = X.astype(np.float64)
+    np.testing.assert_allclose(mu, Xd.mean(0), atol=1e-6)
+    C = np.cov(Xd.T, bias=True)
+    w, V = np.linalg.eigh(C)
+    V = V[:, ::-1][:, :L]
+    np.testing.assert_allclose(U.T @ U, np.eye(L), atol=1e-4)
+    # projectors onto the leading 19 directions (the prototype part; the rest is noise whose
+    # directions are not unique) agree, and the 32-d projector captures the same variance
+    P_ref = V[:, :19] @ V[:, :19].T
+    assert np.linalg.norm(U @ U.T @ P_ref - P_ref) < 1e-3
+    assert abs(kept - w[::-1][:L].sum() / w.sum()) < 1e-4
+
+
+def test_linear_code_lifting_is_the_projection_of_the_aggregate(slag):
+    # aggregation of linear codes is exact: the decoded embedding of every touched Gaussian is
+    # mu + U U^T (E_k - mu) of the float32 path's E_k (to float32 rounding)
+    D = 256
+    s = synth.small_scene(41, 6000, 4, 160, 120, 12, dim=D, surfaces=4, n_protos=20,
+                          noise_sigma=0.1 / np.sqrt(D))
+    views = [s.view(i) for i in range(s.n_views)]
+    X = synth.segment_samples(41, 50000, D, 20, noise_sigma=0.1 / np.sqrt(D))
+    params, _ = slag.linear_code_fit(X)
+    U, mu = params[:D * L].reshape(D, L).astype(np.float64), params[D * L:].astype(np.float64)
+    with slag.Lifter(s.gaussians, dim=D) as Lf:
+        for v in views:
+            Lf.add_view(v.camera, v.seg, v.table)
+        Ef, wf = Lf.finalize()
+    with slag.Lifter(s.gaussians, dim=D, precision=slag.PREC_LINEAR32, linear_code=params) as Ll:
+        for v in views:
+            Ll.add_view(v.camera, v.seg, v.table)
+        El, wl = Ll.finalize()
+        ids = Ll.query_threshold(views[0].table[0] / np.linalg.norm(views[0].table[0]), 0.28)
+    np.testing.assert_array_equal(wl, wf)
+    ok = wf >= 1e-3
+    assert ok.sum() > 500
+    E = Ef[ok].astype(np.float64)
+    proj = mu + (E - mu) @ U @ U.T
+    np.testing.assert_allclose(El[ok], proj, atol=2e-5)
+    assert np.all(El[wf == 0] == 0)
+    cos = (El[ok] * E).sum(1) / (np.linalg.norm(El[ok], axis=1) * np.linalg.norm(E, axis=1))
+    print("linear code vs float32 path: mean 1 - cos %.2e, max %.2e" % ((1 - cos).mean(), (1 - cos).max()))
+    assert len(ids) > 0
