@@ -454,6 +454,13 @@ slag_status slag_set_linear_code(slag_ctx *ctx, const float *params);
 
 /* ---- out-of-core output: per-area embedding files ------------------------- */
 
+/* Device memory the out-of-core finalize of SLAG_FLAG_EMBEDDINGS_ON_HOST may
+ * hold for output rows at a time: it then computes the rows in chunks of at
+ * most bytes / (4 dim + 8) Gaussians (whole blocks of 128, at least one
+ * block). 0 restores the default of 2^20 Gaussians per chunk. Errors:
+ * INVALID_ARG for bytes < 0. */
+slag_status slag_set_device_budget(slag_ctx *ctx, int64_t bytes);
+
 /* Spatial partition export (the paper stores a large scene's embeddings per
  * area of a grid over the Gaussian means instead of in a vector database).
  * Aggregates the views added so far in chunks of at most chunk_gaussians

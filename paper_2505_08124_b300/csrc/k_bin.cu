@@ -17,29 +17,63 @@ SLAG_CHECKS_WORD
 
 namespace {
 
-// One thread per Gaussian (in depth-rank order): the pairs of the bins its tile
-// rectangle meets, row-major; a bin is a 2^shift x 2^shift square of tiles.
-__global__ void __launch_bounds__(256) emit_k(const uint2 *__restrict__ srect, const uint32_t *__restrict__ offsets,
-                                              uint32_t n_visible, int shift, int bins_x, int64_t cap,
-                                              uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_visible) return;
-    const uint2 rc = srect[r];
-    const uint32_t x0 = (rc.x & 0xffffu) >> shift, x1 = (((rc.x >> 16) - 1) >> shift) + 1;
-    const uint32_t y0 = (rc.y & 0xffffu) >> shift, y1 = (((rc.y >> 16) - 1) >> shift) + 1;
-    uint32_t off = offsets[r];
-    for (uint32_t y = y0; y < y1; ++y)
-        for (uint32_t x = x0; x < x1; ++x, ++off) {
-            if (!SLAG_IN_BOUNDS((int64_t)off < cap, kCheckEmit)) continue;
-            keys[off] = y * (uint32_t)bins_x + x;
-            vals[off] = r;
-        }
-}
+// One thread per Gaussian (in depth-rank order): the pairs of the bins its tile rectangle meets,
+// row-major; a bin is a 2^shift x 2^shift square of tiles. A warp's 32 Gaussians own one
+// contiguous run of the output (their offsets are an exclusive scan of their pair counts): the
+// warp writes its pairs into shared memory in windows of kEmitStage and copies each window out
+// with coalesced stores.
+constexpr int kEmitThreads = 256;
+constexpr int kEmitStage = 256;
 
-__global__ void pair_rect_k(const uint32_t *__restrict__ list, int64_t P, const uint2 *__restrict__ srect,
-                            uint2 *__restrict__ prect) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < P) prect[i] = srect[list[i]];
+__global__ void __launch_bounds__(kEmitThreads) emit_k(const uint2 *__restrict__ srect,
+                                                       const uint32_t *__restrict__ offsets, uint32_t n_visible,
+                                                       int shift, int bins_x, int64_t cap,
+                                                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    __shared__ uint32_t sk[kEmitThreads / 32][kEmitStage], sv[kEmitThreads / 32][kEmitStage];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t r0 = blockIdx.x * kEmitThreads + w * 32;   // the warp's first Gaussian
+    if (r0 >= n_visible) return;                               // (warp-uniform)
+    const uint32_t r = r0 + lane;
+    const bool valid = r < n_visible;
+    uint32_t x0 = 0, wx = 1, y0 = 0, cnt = 0, off = 0;
+    if (valid) {
+        const uint2 rc = srect[r];
+        x0 = (rc.x & 0xffffu) >> shift;
+        const uint32_t x1 = (((rc.x >> 16) - 1) >> shift) + 1;
+        y0 = (rc.y & 0xffffu) >> shift;
+        const uint32_t y1 = (((rc.y >> 16) - 1) >> shift) + 1;
+        wx = x1 - x0;
+        cnt = wx * (y1 - y0);
+        off = offsets[r];
+    }
+    const uint32_t base = __shfl_sync(0xffffffffu, off, 0);
+    const uint32_t p = off - base;                             // this lane's first place in the run
+    uint32_t total = valid ? p + cnt : 0u;
+    for (int o = 16; o; o >>= 1) total = max(total, __shfl_xor_sync(0xffffffffu, total, o));
+    // this lane's next pair: index e of its rectangle, at bin (bx, by)
+    uint32_t e = 0, bx = x0, by = y0;
+    for (uint32_t s = 0; s < total; s += kEmitStage) {
+        const uint32_t lim = s + kEmitStage;
+        while (e < cnt && p + e < lim) {
+            const uint32_t at = p + e - s;
+            sk[w][at] = by * (uint32_t)bins_x + bx;
+            sv[w][at] = r;
+            ++e;
+            if (++bx == x0 + wx) {
+                bx = x0;
+                ++by;
+            }
+        }
+        __syncwarp();
+        const uint32_t m = min((uint32_t)kEmitStage, total - s);
+        for (uint32_t j = lane; j < m; j += 32) {
+            const int64_t g = (int64_t)base + s + j;
+            if (!SLAG_IN_BOUNDS(g < cap, kCheckEmit)) continue;
+            keys[g] = sk[w][j];
+            vals[g] = sv[w][j];
+        }
+        __syncwarp();
+    }
 }
 
 __global__ void ranges_k(const uint32_t *__restrict__ keys, int64_t P, uint2 *__restrict__ ranges) {
@@ -97,16 +131,12 @@ void launch_tile_order(const uint2 *ranges, int tiles_x, int tiles_y, int shift,
 void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int shift, int bins_x, int64_t cap,
                  uint32_t *keys, uint32_t *vals, cudaStream_t st) {
     if (n_visible == 0) return;
-    emit_k<<<(n_visible + 255) / 256, 256, 0, st>>>(srect, offsets, n_visible, shift, bins_x, cap, keys, vals);
+    emit_k<<<(n_visible + kEmitThreads - 1) / kEmitThreads, kEmitThreads, 0, st>>>(srect, offsets, n_visible, shift,
+                                                                               bins_x, cap, keys, vals);
     note_launch();
 }
 
 SLAG_CHECKS_TAKE(checks_take_bin)
-
-void launch_pair_rects(const uint32_t *list, int64_t P, const uint2 *srect, uint2 *prect, cudaStream_t st) {
-    if (P <= 0) return;
-    pair_rect_k<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(list, P, srect, prect); note_launch();
-}
 
 void launch_ranges(const uint32_t *keys, int64_t P, uint2 *ranges, cudaStream_t st) {
     if (P <= 0) return;

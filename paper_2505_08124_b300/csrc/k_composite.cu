@@ -11,39 +11,37 @@
 // a segment carries the same embedding E_j, the D-wide product B . E is
 // deferred to the aggregation (this view only emits B).
 //
-// One CTA (128 threads, two pixels each) per 16x16 tile; the tile's Gaussians
-// are those of its bin's list (a 4x4-tile super-tile) whose tile rectangle
-// holds the tile, taken in list order:
-//   * the tile's pixels are reordered by segment ("slot"), and within a
-//     segment by 8x8 block; a thread takes two neighbours in that order (almost
-//     always one segment), so each warp's 64 pixels usually share one segment
-//     and form a square block (fewer Gaussians reach a square than a 16x4
-//     strip of the same area), and the record loads, culling and
-//     bookkeeping of a Gaussian serve two pixels with independent
-//     transmittance chains;
-//   * records of up to 480 Gaussians at a time are staged in shared memory (a
-//     batch is filled, in rounds of 256 candidates, until it holds at least
-//     224: few batches and rounds, hence few barriers, per tile; four CTAs per
-//     SM); a
-//     record holds mu', the conic scaled by -log2(e)/2 (so that alpha =
-//     min(0.99, 2^(q2 + log2 opacity)) needs one SFU exp2 and the alpha
-//     floor is tested on the exponent before it), and the half extents of
-//     the alpha >= 1/255 ellipse;
-//   * per chunk of 32 Gaussians, each warp keeps (ballot) only those whose
-//     alpha >= 1/255 ellipse box meets the box of its 64 pixel centres --
-//     the others cannot contribute to any of its pixels -- composites its
-//     pixels against them, storing each lane's weight (its two pixels' sum)
-//     in a padded shared 32 x 32
-//     buffer, then reads the buffer transposed: lane j sums Gaussian j over
-//     the warp's pixels per slot and adds the partial into a shared
-//     (slot x Gaussian) table;
-//   * after each batch the non-zero table entries are queued in shared memory
-//     and moved, a block at a time, to the view's record list; a separate
-//     combine pass (many records in flight per SM) adds them to the per-view
-//     (segment, weight) table of each Gaussian (4 slots per Gaussian; further
-//     segments are appended directly as triples). Probing the tables here
-//     would leave each CTA waiting on a dependent chain of L2 round trips.
+// One CTA per 16x16 tile: four consumer warps own the tile's 256 pixels (two
+// per thread) and one producer warp feeds them. The tile's Gaussians are those
+// of its bin's list (a 4x4-tile super-tile) whose tile rectangle holds the
+// tile, taken in list order.
+//   * Producer: fills one of two record buffers at a time with the hits among
+//     the next 160 candidates of the bin's list (the following 160 are loaded
+//     meanwhile; records are copied asynchronously), turns each record into a tile-local exponent
+//     polynomial (keeping what the consumers' culling tests need), and publishes the
+//     buffer on an mbarrier; it refills a buffer once all consumers have
+//     released it, first moving that buffer's per-(segment, Gaussian) sums to
+//     the view's record list. It stops when the list ends or no consumer
+//     warp has a live pixel.
+//   * Consumers: the tile's pixels are reordered by segment ("slot"), and
+//     within a segment by 8x8 block; a thread takes two neighbours in that
+//     order (almost always one segment), so each warp's 64 pixels usually
+//     share one segment and form a square block. A warp composites each
+//     published buffer in chunks of 32 Gaussians, keeping only those whose
+//     alpha >= 1/255 reaches its pixel box, then sums each Gaussian's weights
+//     over its lanes per slot (a transposition through shared memory) into
+//     the buffer's (slot x Gaussian) table, and releases the buffer. Warps run
+//     independently: a warp whose pixels have all stopped only releases the
+//     buffers, and no warp waits for another at a CTA barrier.
+//   * Every wait is an mbarrier wait bounded by ~1 s of globaltimer; a wait
+//     that gives up sets the context's error word and an abort flag that
+//     releases every other wait of the CTA (nothing asynchronous is in flight
+//     at a wait).
+// A combine pass (many records in flight per SM) adds the records to the
+// per-view (segment, weight) table of each Gaussian (4 slots per Gaussian;
+// further segments are appended directly as triples).
 #include "slag_internal.cuh"
+#include "tc_util.cuh"
 
 namespace slag {
 
@@ -51,42 +49,48 @@ SLAG_CHECKS_WORD
 
 namespace {
 
-constexpr int kRows = 16;                             // tile rows per CTA: one CTA per 16x16 tile
-constexpr int kPix = kTile * kRows;                   // 128 pixels per CTA
-constexpr int kThreads = kPix / 2;                    // two pixels per thread
-constexpr int kWarps = kThreads / 32;
-constexpr int kCtasPerSm = 4;                         // resident CTAs per SM (shared memory)
-constexpr int kSubTiles = kTile / kRows;
-constexpr int kRound = 256;                           // candidates examined per fill round
-constexpr int kBatch = 224 + kRound;                  // record capacity of a batch
+constexpr int kPix = kTile * kTile;                   // 256 pixels per CTA (one tile)
+constexpr int kConsumers = 4;                         // compositing warps, 64 pixels each
+constexpr int kPixThreads = 32 * kConsumers;          // two pixels per consumer thread
+constexpr int kThreads = kPixThreads + 32;            // + the producer warp
+constexpr int kProducer = kConsumers;                 // warp index of the producer
+constexpr int kCtasPerSm = 5;                         // resident CTAs per SM (shared memory)
+constexpr int kPerLane = 5;                           // candidates per producer lane and batch
+constexpr int kBuf = 32 * kPerLane;                   // candidates per batch = record capacity of a buffer
 constexpr int kSmemSlots = 4;
-constexpr int kWarpQ = 104;                           // queued (Gaussian, slot) sums of a warp
-constexpr int kWarpFlush = 64;                        // queue level that triggers a flush after a batch
+constexpr int kQ = 104;                               // the producer's queued (Gaussian, slot) sums
+constexpr int kQFlush = 64;                           // queue level that triggers a flush after a buffer
 constexpr int kWStride = 36;                          // transposition rows: 16-byte aligned, conflict-free
 constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2(1/255)
+constexpr uint32_t kBarConsumers = 1;                 // named barrier of the consumer warps
 
 struct Smem {
-    float4 rec_a[kBatch];                 // staged (mu'x, mu'y, a', b'); then (K0, K1, K2, K3)
-    float4 rec_b[kBatch];                 // staged (c', log2 opacity, ex, ey); then (K4, K5, warp mask, log2 o)
-    uint32_t gid[kBatch];                 // internal Gaussian index
-    int32_t fill[2][(kRound / kThreads) * kWarps];   // per-warp hit counts of a fill round (by parity)
-    float wb[kSmemSlots][kBatch];         // per (slot, Gaussian of the batch)
+    float4 rec_a[2][kBuf];                // staged (mu'x, mu'y, a', b'); then (K0, K1, K2, K3)
+    float4 rec_b[2][kBuf];                // staged (c', log2 opacity, ex, ey); then (K4, K5, floor margin, log2 o)
+    float4 rec_c[2][kBuf];                // (mu'x, mu'y) tile-local and the alpha-floor half extents
+    uint32_t gid[2][kBuf];                // internal Gaussian index
+    float wb[2][kSmemSlots][kBuf];        // per (buffer, slot, Gaussian of the buffer)
     union {
-        float wbuf[kThreads / 32][32 * kWStride];   // per warp: (Gaussian of the chunk) x lane
-        uint32_t keys[kPix];                        // the prologue's segment sort
+        float wbuf[kConsumers][32 * kWStride];   // per warp: (Gaussian of the chunk) x lane
+        uint32_t keys[kPix];                     // the prologue's segment sort
     };
-    int32_t clist[kThreads / 32][34];     // per warp: the chunk's surviving Gaussians, then -1
-    uint32_t split_min[2][kThreads / 32];   // prologue multi-split: per-warp minimum segment
-    int32_t split_cnt[2][kThreads / 32];    // and per-warp counts (first | second pixel << 16)
-    int32_t slot_lane[kThreads];          // slot of the sums each lane stores (its first pixel's)
+    int32_t clist[kConsumers][34];        // per warp: the chunk's surviving Gaussians, then -1
+    uint32_t split_min[2][kConsumers];    // prologue multi-split: per-warp minimum segment
+    int32_t split_cnt[2][kConsumers];     // and per-warp counts (first | second pixel << 16)
+    int32_t slot_lane[kPixThreads];       // slot of the sums each lane stores (its first pixel's)
     int32_t seg_of_slot[kPix];
-    int32_t group_slot[kThreads / 32];    // slot shared by all of a warp's pixels, -2 = mixed
-    float4 wbox[kThreads / 32];           // each warp's box of pixel centres (x0, x1, y0, y1), tile-local
-    int32_t warp_tot[kThreads / 32];
-    int32_t scalar[4];
-    uint32_t rec_g[kThreads / 32][kWarpQ];   // each warp's queued sums: Gaussian, weight, slot
-    float rec_w[kThreads / 32][kWarpQ];
-    uint8_t rec_s[kThreads / 32][kWarpQ];
+    int32_t group_slot[kConsumers];       // slot shared by all of a warp's pixels, -2 = mixed
+    int32_t warp_tot[kConsumers];
+    int32_t scalar[4];                    // [0] first pixel's segment, [1] slots in shared memory
+    int32_t count[2];                     // records in each buffer (-1: no more)
+    int32_t warp_live[kConsumers];        // a consumer warp still has a live pixel
+    uint32_t abort_flag;                  // a wait gave up: every other wait gives up too
+    uint32_t qg[kQ];                      // the producer's queued sums: Gaussian, weight, slot
+    float qw[kQ];
+    uint8_t qs[kQ];
+    __align__(8) uint64_t full[2];        // a buffer is published (32 producer arrivals)
+    __align__(8) uint64_t empty[2];       // a buffer is released (128 consumer arrivals)
+    __align__(8) uint64_t ready;          // the consumers' prologue is done (128 arrivals)
 };
 // kCtasPerSm CTAs per SM (228 KB of shared memory, 1 KB of it reserved per CTA)
 static_assert(sizeof(Smem) + 1024 <= 233472 / kCtasPerSm, "composite shared memory above the CTA budget");
@@ -143,26 +147,43 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Barriers of the consumer warps only (the producer never takes part).
+__device__ __forceinline__ void cbar() { asm volatile("bar.sync %0, %1;" ::"n"(kBarConsumers), "n"(kPixThreads) : "memory"); }
+
+__device__ __forceinline__ bool cbar_and(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n"
+        " .reg .pred a, b;\n"
+        " setp.ne.u32 a, %1, 0;\n"
+        " bar.red.and.pred b, %2, %3, a;\n"
+        " selp.u32 %0, 1, 0, b;\n"
+        "}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "n"(kBarConsumers), "n"(kPixThreads)
+        : "memory");
+    return r != 0;
+}
+
 __device__ __forceinline__ HashSink sink_of(const CompositeArgs &a) {
     return HashSink{a.hash, a.log_count, a.log_cap, a.log_key, a.log_w, a.s_ovf, a.overflow, a.view_base};
 }
 
-__device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int slot, int gi, float acc) {
-    if (slot < kSmemSlots) atomicAdd(&sm.wb[slot][gi], acc);
-    else sink_add(sink_of(a), sm.gid[gi], sm.seg_of_slot[slot], acc);
+__device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int b, int slot, int gi, float acc) {
+    if (slot < kSmemSlots) atomicAdd(&sm.wb[b][slot][gi], acc);
+    else sink_add(sink_of(a), sm.gid[b][gi], sm.seg_of_slot[slot], acc);
 }
 
-// Moves a warp's n queued records to the view's record list with one reservation; the
-// queue is the warp's own, so only the warp takes part.
-__device__ void flush_warp(const CompositeArgs &a, Smem &sm, int w, int lane, int n) {
+// Moves the producer's n queued records to the view's record list with one reservation.
+__device__ void flush_queue(const CompositeArgs &a, Smem &sm, int lane, int n) {
     __syncwarp();
     unsigned long long base = 0ull;
     if (lane == 0) base = atomicAdd(a.rec_count, (unsigned long long)n);
     base = __shfl_sync(0xffffffffu, base, 0);
     for (int k = lane; k < n; k += 32) {
-        const uint32_t g = sm.rec_g[w][k];
-        const int32_t seg = sm.seg_of_slot[sm.rec_s[w][k]];
-        const float wt = sm.rec_w[w][k];
+        const uint32_t g = sm.qg[k];
+        const int32_t seg = sm.seg_of_slot[sm.qs[k]];
+        const float wt = sm.qw[k];
         if (base + (unsigned long long)k < a.rec_cap) {
             WeightRecord r;
             r.g = g;
@@ -215,27 +236,213 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// A bounded wait on the phase `parity` of bar; on giving up, the error word is set and every other
+// wait of the CTA gives up through the abort flag.
+__device__ __forceinline__ bool wait_phase(const CompositeArgs &a, Smem &sm, uint64_t *bar, uint32_t parity) {
+    if (tc::wait_or_abort(bar, parity, &sm.abort_flag)) return true;
+    if (a.err) atomicOr(a.err, 1u);
+    return false;
+}
+
+// ---- the producer warp ---------------------------------------------------------------------
+
+// Moves buffer b's non-zero (slot, Gaussian) sums of its n records to the queue (and, when the
+// queue fills, to the view's record list), clearing the table for the buffer's next use.
+__device__ void drain_sums(const CompositeArgs &a, Smem &sm, int b, int n, int ns_smem, int lane, uint32_t lt,
+                           int &qn) {
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const bool valid = i < n;
+        const uint32_t g = valid ? sm.gid[b][i] : 0u;
+        for (int s2 = 0; s2 < ns_smem; ++s2) {
+            float v = 0.f;
+            if (valid) {
+                v = sm.wb[b][s2][i];
+                sm.wb[b][s2][i] = 0.f;
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, v != 0.f);
+            if (bal == 0u) continue;
+            if (!a.recs) {   // no record list: the sums go to the tables directly
+                if (v != 0.f) sink_add(sink_of(a), g, sm.seg_of_slot[s2], v);
+                continue;
+            }
+            if (qn + 32 > kQ) {
+                flush_queue(a, sm, lane, qn);
+                qn = 0;
+            }
+            if (v != 0.f) {
+                const int k = qn + __popc(bal & lt);
+                sm.qg[k] = g;
+                sm.qw[k] = v;
+                sm.qs[k] = (uint8_t)s2;
+            }
+            qn += __popc(bal);
+        }
+    }
+    if (qn >= kQFlush) {
+        flush_queue(a, sm, lane, qn);
+        qn = 0;
+    }
+}
+
+template <bool kDebug>
+__device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int ty, float ox, float oy, int lane) {
+    const uint32_t lt = lanemask_lt();
+    const bool trace = kDebug && a.dbg_list != nullptr;
+    const uint2 rg = a.ranges[(ty >> a.bin_shift) * a.bins_x + (tx >> a.bin_shift)];
+    const int end = (int)rg.y;
+    int cursor = (int)rg.x;
+    int staged = 0;   // Gaussians staged so far (their positions in the tile's own list)
+    int qn = 0;       // queued sums
+    int ns_smem = 0;  // slots with a shared-memory table (known after the consumers' prologue)
+    int prev0 = 0, prev1 = 0;   // records of the batch each buffer holds
+    // a batch is the next kBuf candidates of the bin's list; the candidates of the batch after the
+    // current one are loaded into registers while the current one is staged
+    uint32_t r_nx[kPerLane];
+    uint2 rc_nx[kPerLane];
+#pragma unroll
+    for (int k = 0; k < kPerLane; ++k) {
+        const int c = cursor + k * 32 + lane;
+        r_nx[k] = c < end ? a.list[c] : 0u;
+        rc_nx[k] = c < end ? a.prect[c] : make_uint2(0u, 0u);
+    }
+    bool ok = true, have_slots = false;
+    int it = 0;
+    for (;; ++it) {
+        const int b = it & 1;
+        if (it >= 2) {
+            // the consumers have released this buffer (its previous batch, it - 2): move its sums out
+            if (!wait_phase(a, sm, &sm.empty[b], (uint32_t)((it >> 1) - 1) & 1u)) { ok = false; break; }
+            if (a.accumulate) drain_sums(a, sm, b, b ? prev1 : prev0, ns_smem, lane, lt, qn);
+        }
+        bool live = trace;
+        if (!trace) {
+            // the consumers' liveness after the batches they have released
+            for (int q = 0; q < kConsumers; ++q) live = live || (*((volatile int32_t *)&sm.warp_live[q]) != 0);
+        }
+        if (cursor >= end || !live) {
+            if (lane == 0) sm.count[b] = -1;
+            __syncwarp();
+            tc::arrive(&sm.full[b]);
+            break;
+        }
+        // this batch's candidates; the next batch's loads are issued now
+        uint32_t r[kPerLane];
+        bool hit[kPerLane];
+#pragma unroll
+        for (int k = 0; k < kPerLane; ++k) {
+            const int c = cursor + k * 32 + lane;
+            r[k] = r_nx[k];
+            const uint2 rc = rc_nx[k];
+            hit[k] = c < end && (uint32_t)tx >= (rc.x & 0xffffu) && (uint32_t)tx < (rc.x >> 16) &&
+                     (uint32_t)ty >= (rc.y & 0xffffu) && (uint32_t)ty < (rc.y >> 16);
+            const int cn = c + kBuf;
+            r_nx[k] = cn < end ? a.list[cn] : 0u;
+            rc_nx[k] = cn < end ? a.prect[cn] : make_uint2(0u, 0u);
+        }
+        // stable compaction of the hits (candidate order is (k, lane)); their records are copied
+        // asynchronously
+        int nb = 0;
+#pragma unroll
+        for (int k = 0; k < kPerLane; ++k) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit[k]);
+            const int pos = nb + __popc(bal & lt);
+            if (hit[k] && SLAG_IN_BOUNDS(pos < kBuf && r[k] < a.n_ranks, kCheckComposite)) {
+                cp_async16(&sm.rec_a[b][pos], a.srec_a + r[k]);
+                cp_async16(&sm.rec_b[b][pos], a.srec_b + r[k]);
+                cp_async4(&sm.gid[b][pos], a.sgid + r[k]);
+                if (trace) {
+                    const int64_t at = a.dbg_off[tile] + staged + pos;
+                    if (at < a.dbg_off[tile + 1]) a.dbg_list[at] = r[k];
+                    else atomicOr(a.dbg_bad, 1u);
+                }
+            }
+            nb += __popc(bal);
+        }
+        cursor += kBuf;
+        cp_async_wait_all();
+        __syncwarp();
+        staged += nb;
+        if (!have_slots) {
+            // the number of slots comes from the consumers' prologue (needed by the drains)
+            if (!wait_phase(a, sm, &sm.ready, 0u)) { ok = false; break; }
+            ns_smem = sm.scalar[1];
+            have_slots = true;
+        }
+        // records -> tile-local exponent polynomials. With X = px + 0.5 - ox, mx = mu'x - ox (and
+        // Y, my likewise), the exponent q2 + log2 o = a' dx^2 + b' dx dy + c' dy^2 + log2 o with
+        // dx = mx - X, dy = my - Y is K0 + K1 X + K2 Y + K3 X^2 + K4 X Y + K5 Y^2. Each consumer
+        // warp culls against its own pixel box; the record keeps what that test needs.
+        for (int i = lane; i < nb; i += 32) {
+            const float4 ra = sm.rec_a[b][i], rb = sm.rec_b[b][i];
+            const float mx = ra.x - ox, my = ra.y - oy;
+            const float A = ra.z, Bc = ra.w, C = rb.x, lo = rb.y;
+            const float K1 = -fmaf(2.f * A, mx, Bc * my);
+            const float K2 = -fmaf(Bc, mx, 2.f * C * my);
+            const float K0 = fmaf(fmaf(A, mx, Bc * my), mx, fmaf(C * my, my, lo));
+            // a Gaussian is kept for a warp when its alpha-floor box meets the warp's box and its
+            // exponent reaches the floor on that box, less a margin that bounds the rounding of the
+            // per-pixel polynomial (terms at most S in size; X, Y < 16)
+            const float S = fabsf(K0) + 16.f * (fabsf(K1) + fabsf(K2)) + 256.f * (fabsf(A) + fabsf(Bc) + fabsf(C));
+            const float thr = kLog2AlphaMin - fmaf(4e-6f, S, 0.01f);
+            sm.rec_c[b][i] = make_float4(mx, my, rb.z, rb.w);
+            sm.rec_a[b][i] = make_float4(K0, K1, K2, A);
+            sm.rec_b[b][i] = make_float4(Bc, C, thr, lo);
+        }
+        if (lane == 0) sm.count[b] = nb;
+        if (b) prev1 = nb;
+        else prev0 = nb;
+        __syncwarp();
+        tc::arrive(&sm.full[b]);   // every lane: each publishes its own writes
+    }
+    if (ok && it >= 1) {
+        // the last batch (it - 1, in the other buffer): its sums once the consumers release it
+        const int b = (it - 1) & 1;
+        if (wait_phase(a, sm, &sm.empty[b], (uint32_t)((it - 1) >> 1) & 1u) && a.accumulate)
+            drain_sums(a, sm, b, b ? prev1 : prev0, ns_smem, lane, lt, qn);
+    }
+    if (a.accumulate && a.recs && qn > 0) flush_queue(a, sm, lane, qn);
+    if (trace && lane == 0) a.dbg_staged[tile] = (uint32_t)staged;
+}
+
 // kKernel: record Eq. 2's kernel exp(-q/2) instead of alpha * T; kDebug: keep the
-// per-pixel weight sums and counts of the diagnostic render.
+// per-pixel weight sums and counts of the diagnostic render (and its staging trace).
 template <bool kKernel, bool kDebug>
-// (registers capped as for six CTAs per SM: more registers per thread measured slower)
-__global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const CompositeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int tile = (int)a.tile_order[blockIdx.x / kSubTiles];
-    const int row0 = (int)(blockIdx.x % kSubTiles) * kRows;    // first tile row of this CTA
+    const int tile = (int)a.tile_order[blockIdx.x];
     const int tx = tile % a.cam.tiles_x, ty = tile / a.cam.tiles_x;
     const int W = a.cam.width, H = a.cam.height;
+    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+
+    if (tid == 0) {
+        tc::mbar_init(&sm.full[0], 32);
+        tc::mbar_init(&sm.full[1], 32);
+        tc::mbar_init(&sm.empty[0], kPixThreads);
+        tc::mbar_init(&sm.empty[1], kPixThreads);
+        tc::mbar_init(&sm.ready, kPixThreads);
+        sm.abort_flag = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the (slot x Gaussian) sums start at zero; each buffer's drain clears what it read
+    for (int i = tid; i < 2 * kSmemSlots * kBuf; i += kThreads) (&sm.wb[0][0][0])[i] = 0.f;
+    if (tid < kConsumers) sm.warp_live[tid] = 1;
+    __syncthreads();
+    if (w == kProducer) {
+        producer<kDebug>(a, sm, tile, tx, ty, ox, oy, lane);
+        return;
+    }
 
     const uint32_t lt = lanemask_lt();
     // ---- segment of each of the CTA's pixels; positions sorted by segment --------
-    // (thread t reads pixels t and t + 64; a pixel index fits in the low 8 bits of a key)
+    // (thread t reads pixels t and t + 128; a pixel index fits in the low 8 bits of a key)
     int32_t s_nat[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int p = tid + h * kThreads;
-        const int px = tx * kTile + pix_x(p), py = ty * kTile + row0 + pix_y(p);
+        const int p = tid + h * kPixThreads;
+        const int px = tx * kTile + pix_x(p), py = ty * kTile + pix_y(p);
         const bool inside = px < W && py < H;
         int32_t sg = (inside && a.seg && a.accumulate) ? a.seg[(int64_t)py * W + px] : -1;
         if (sg < -1) sg = -1;
@@ -243,14 +450,12 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
         sm.keys[p] = ((uint32_t)(sg + 1) << 8) | (uint32_t)p;
     }
     if (tid == 0) sm.scalar[0] = s_nat[0];
-    // the (slot x Gaussian) sums start at zero; each batch's reader clears what it read
-    for (int i = tid; i < kSmemSlots * kBatch; i += kThreads) (&sm.wb[0][0])[i] = 0.f;
-    __syncthreads();
-    const bool uniform = __syncthreads_and(s_nat[0] == sm.scalar[0] && s_nat[1] == sm.scalar[0]);
-    int pos0 = tid, pos1 = tid + kThreads;
+    cbar();
+    const bool uniform = cbar_and(s_nat[0] == sm.scalar[0] && s_nat[1] == sm.scalar[0]);
+    int pos0 = tid, pos1 = tid + kPixThreads;
     if (!uniform) {
         // stable multi-split into (segment, pixel) order: one round per distinct segment of the
-        // tile, smallest first; pixel tid precedes pixel tid + kThreads of the same segment
+        // tile, smallest first; pixel tid precedes pixel tid + 128 of the same segment
         const uint32_t g0 = (uint32_t)(s_nat[0] + 1), g1 = (uint32_t)(s_nat[1] + 1);
         bool left0 = true, left1 = true;
         int placed = 0;
@@ -259,18 +464,18 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
             const uint32_t wmin = __reduce_min_sync(0xffffffffu, mine);
             const bool t0 = left0 && g0 == wmin, t1 = left1 && g1 == wmin;
             if (lane == 0) sm.split_min[rnd][w] = wmin;
-            __syncthreads();
+            cbar();
             uint32_t mn = 0xffffffffu;
 #pragma unroll
-            for (int q = 0; q < kWarps; ++q) mn = min(mn, sm.split_min[rnd][q]);
+            for (int q = 0; q < kConsumers; ++q) mn = min(mn, sm.split_min[rnd][q]);
             if (mn == 0xffffffffu) break;
             const bool u0 = t0 && wmin == mn, u1 = t1 && wmin == mn;
             const uint32_t b0 = __ballot_sync(0xffffffffu, u0), b1 = __ballot_sync(0xffffffffu, u1);
             if (lane == 0) sm.split_cnt[rnd][w] = __popc(b0) | (__popc(b1) << 16);
-            __syncthreads();
+            cbar();
             int before0 = 0, before1 = 0, tot0 = 0, tot1 = 0;
 #pragma unroll
-            for (int q = 0; q < kWarps; ++q) {
+            for (int q = 0; q < kConsumers; ++q) {
                 const int c = sm.split_cnt[rnd][q], c0 = c & 0xffff, c1 = c >> 16;
                 before0 += q < w ? c0 : 0;
                 before1 += q < w ? c1 : 0;
@@ -288,10 +493,10 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
             placed += tot0 + tot1;
         }
     }
-    __syncthreads();
+    cbar();
     sm.keys[pos0] = ((uint32_t)(s_nat[0] + 1) << 8) | (uint32_t)tid;
-    sm.keys[pos1] = ((uint32_t)(s_nat[1] + 1) << 8) | (uint32_t)(tid + kThreads);
-    __syncthreads();
+    sm.keys[pos1] = ((uint32_t)(s_nat[1] + 1) << 8) | (uint32_t)(tid + kPixThreads);
+    cbar();
     // this thread's pixels: positions 2 tid and 2 tid + 1 (adjacent in segment order, so
     // they almost always share a segment)
     const uint32_t k0 = sm.keys[2 * tid], k1 = sm.keys[2 * tid + 1];
@@ -307,10 +512,10 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
         if (lane >= o) incl += y;
     }
     if (lane == 31) sm.warp_tot[w] = incl;
-    __syncthreads();
+    cbar();   // the keys are read: the transposition buffers may reuse them from here on
     int before = incl - new0 - new1, nslots = 0;
 #pragma unroll
-    for (int q = 0; q < kWarps; ++q) {
+    for (int q = 0; q < kConsumers; ++q) {
         before += q < w ? sm.warp_tot[q] : 0;
         nslots += sm.warp_tot[q];
     }
@@ -328,14 +533,13 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
         const bool same = __all_sync(0xffffffffu, slot0 == first && slot1 == first);
         if (lane == 0) sm.group_slot[w] = same ? first : -2;
     }
-    const int ns_smem = nslots < kSmemSlots ? nslots : kSmemSlots;
+    if (tid == 0) sm.scalar[1] = nslots < kSmemSlots ? nslots : kSmemSlots;
 
-    const int px0 = tx * kTile + pix_x(pix0), py0 = ty * kTile + row0 + pix_y(pix0);
-    const int px1 = tx * kTile + pix_x(pix1), py1 = ty * kTile + row0 + pix_y(pix1);
+    const int px0 = tx * kTile + pix_x(pix0), py0 = ty * kTile + pix_y(pix0);
+    const int px1 = tx * kTile + pix_x(pix1), py1 = ty * kTile + pix_y(pix1);
     const bool inside0 = px0 < W && py0 < H, inside1 = px1 < W && py1 < H;
-    // pixel centres relative to the CTA's origin (ox, oy), and their monomials: the exponent of a
-    // Gaussian is a quadratic polynomial in them (see the record conversion below)
-    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile + row0);
+    // pixel centres relative to the tile's origin, and their monomials: the exponent of a
+    // Gaussian is a quadratic polynomial in them (see the producer's record conversion)
     const float X0 = (float)pix_x(pix0) + 0.5f, Y0 = (float)pix_y(pix0) + 0.5f;
     const float X1 = (float)pix_x(pix1) + 0.5f, Y1 = (float)pix_y(pix1) + 0.5f;
     // the two pixels' monomials as packed pairs (pixel 0, pixel 1)
@@ -352,10 +556,18 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
         wy0 = fminf(wy0, __shfl_xor_sync(0xffffffffu, wy0, o));
         wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
     }
-    if (lane == 0) sm.wbox[w] = make_float4(wx0, wx1, wy0, wy1);
+    const float4 wbox = make_float4(wx0, wx1, wy0, wy1);   // every lane holds the warp's box
     // T = 0 marks a pixel that has stopped (or lies outside the image): its weights are then 0
     // and every later Gaussian takes it below 1e-4 again, so no flag is needed
     float T0 = inside0 ? 1.f : 0.f, T1 = inside1 ? 1.f : 0.f;
+    {
+        const bool any = __any_sync(0xffffffffu, T0 > 0.f || T1 > 0.f);
+        if (lane == 0) sm.warp_live[w] = any ? 1 : 0;
+    }
+    cbar();   // slots and group slots are complete
+    tc::arrive(&sm.ready);
+    const int gs = sm.group_slot[w];
+
     float wsum0 = 0.f, wsum1 = 0.f, Tf0 = 0.f, Tf1 = 0.f;   // diagnostics: weight sum, T at the stop
     int count0 = 0, count1 = 0;
     // examined pairs: a stopped pixel examined the list up to its stopping Gaussian (position
@@ -363,135 +575,38 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
     // through (seen)
     int evp0 = 0, evp1 = 0, seen = 0;
     unsigned long long executed = 0;   // Gaussians this warp evaluated for all 64 of its pixels
-
-    // this tile's candidates: the depth-ordered list of its bin (a 2^shift x
-    // 2^shift square of tiles); the Gaussians whose tile rectangle holds this tile
-    // form, in the same order, the tile's own list
-    const uint2 rg = a.ranges[(ty >> a.bin_shift) * a.bins_x + (tx >> a.bin_shift)];
-    const int end = (int)rg.y;
-    int cursor = (int)rg.x;
     float *wb_warp = sm.wbuf[w];
-    int qn = 0;   // this warp's queued records
-    // diagnostics: record every staged Gaussian, and stage the whole list
-    const bool trace = kDebug && a.dbg_list != nullptr;
-    int staged = 0;
+    int32_t *cl = sm.clist[w];
 
-    // candidates of the next fill round, prefetched into registers
-    constexpr int kPer = kRound / kThreads;
-    uint32_t r_nx[kPer];
-    uint2 rc_nx[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int c = cursor + k * kThreads + tid;
-        r_nx[k] = c < end ? a.list[c] : 0u;
-        rc_nx[k] = c < end ? a.prect[c] : make_uint2(0u, 0u);
-    }
-
-    while (true) {
-        int live = __syncthreads_count(T0 > 0.f || T1 > 0.f);   // also: the previous batch is consumed
-        if ((live == 0 && !trace) || cursor >= end) break;
-        // fill: rounds of kRound candidates until at least kBatch - kRound records are
-        // staged; the records of the hits are copied asynchronously, the next round's
-        // candidates are loaded while this round is compacted
-        int nb = 0, rp = 0;
-        while (nb < kBatch - kRound && cursor < end) {
-            uint32_t r[kPer];
-            bool hit[kPer];
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                const int c = cursor + k * kThreads + tid;
-                r[k] = r_nx[k];
-                const uint2 rc = rc_nx[k];
-                hit[k] = c < end && (uint32_t)tx >= (rc.x & 0xffffu) && (uint32_t)tx < (rc.x >> 16) &&
-                         (uint32_t)ty >= (rc.y & 0xffffu) && (uint32_t)ty < (rc.y >> 16);
-                const int cn = c + kRound;
-                r_nx[k] = cn < end ? a.list[cn] : 0u;
-                rc_nx[k] = cn < end ? a.prect[cn] : make_uint2(0u, 0u);
-            }
-            // stable compaction: candidate order is (k, warp, lane)
-            uint32_t bal[kPer];
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                bal[k] = __ballot_sync(0xffffffffu, hit[k]);
-                if (lane == 0) sm.fill[rp][k * (kThreads / 32) + w] = __popc(bal[k]);
-            }
-            __syncthreads();
-            int nh = 0;
-            for (int q = 0; q < kPer * (kThreads / 32); ++q) nh += sm.fill[rp][q];
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                int bk = 0;
-                for (int q = 0; q < k * (kThreads / 32) + w; ++q) bk += sm.fill[rp][q];
-                if (hit[k] && SLAG_IN_BOUNDS(nb + bk + __popc(bal[k] & lt) < kBatch && r[k] < a.n_ranks,
-                                             kCheckComposite)) {
-                    const int pos = nb + bk + __popc(bal[k] & lt);
-                    cp_async16(&sm.rec_a[pos], a.srec_a + r[k]);
-                    cp_async16(&sm.rec_b[pos], a.srec_b + r[k]);
-                    cp_async4(&sm.gid[pos], a.sgid + r[k]);
-                    if (trace) {
-                        const int64_t at = a.dbg_off[tile] + staged + pos;
-                        if (at < a.dbg_off[tile + 1]) a.dbg_list[at] = r[k];
-                        else atomicOr(a.dbg_bad, 1u);
-                    }
-                }
-            }
-            nb += nh;
-            cursor += kRound;
-            rp ^= 1;   // the next round writes the other count array: no barrier needed here
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        staged += nb;
-        if (nb == 0) continue;
-        // records -> tile-local exponent polynomials. With X = px + 0.5 - ox, mx = mu'x - ox (and
-        // Y, my likewise), the exponent q2 + log2 o = a' dx^2 + b' dx dy + c' dy^2 + log2 o with
-        // dx = mx - X, dy = my - Y is K0 + K1 X + K2 Y + K3 X^2 + K4 X Y + K5 Y^2. The culling
-        // test against the warps' boxes is taken here once per Gaussian (bit w of the mask).
-        {
-            for (int i = tid; i < nb; i += kThreads) {
-                const float4 ra = sm.rec_a[i], rb = sm.rec_b[i];
-                const float mx = ra.x - ox, my = ra.y - oy;
-                const float A = ra.z, Bc = ra.w, C = rb.x, lo = rb.y;
-                const float K1 = -fmaf(2.f * A, mx, Bc * my);
-                const float K2 = -fmaf(Bc, mx, 2.f * C * my);
-                const float K0 = fmaf(fmaf(A, mx, Bc * my), mx, fmaf(C * my, my, lo));
-                // a Gaussian is kept for a warp when its alpha-floor box meets the warp's box and
-                // its exponent reaches the floor on that box, less a margin that bounds the
-                // rounding of the per-pixel polynomial (terms at most S in size; X, Y < 16)
-                const float S = fabsf(K0) + 16.f * (fabsf(K1) + fabsf(K2)) + 256.f * (fabsf(A) + fabsf(Bc) + fabsf(C));
-                const float thr = kLog2AlphaMin - fmaf(4e-6f, S, 0.01f);
-                uint32_t mw = 0u;
-#pragma unroll
-                for (int q = 0; q < kWarps; ++q) {
-                    const float4 bq = sm.wbox[q];
-                    if (mx - rb.z <= bq.y && mx + rb.z >= bq.x && my - rb.w <= bq.w && my + rb.w >= bq.z &&
-                        reaches(mx, my, A, Bc, C, lo, bq, thr))
-                        mw |= 1u << q;
-                }
-                sm.rec_a[i] = make_float4(K0, K1, K2, A);
-                sm.rec_b[i] = make_float4(Bc, C, __uint_as_float(mw), lo);
-            }
-        }
-        __syncthreads();
-        const float4 *rec_a = sm.rec_a;
-        const float4 *rec_b = sm.rec_b;
-        const int gs = sm.group_slot[w];
+    for (int it = 0;; ++it) {
+        const int b = it & 1;
+        if (!wait_phase(a, sm, &sm.full[b], (uint32_t)(it >> 1) & 1u)) break;
+        const int nb = sm.count[b];
+        if (nb < 0) break;
+        const float4 *rec_a = sm.rec_a[b];
+        const float4 *rec_b = sm.rec_b[b];
+        const float4 *rec_c = sm.rec_c[b];
         for (int c = 0; c * 32 < nb; ++c) {
             if (!__any_sync(0xffffffffu, T0 > 0.f || T1 > 0.f)) break;
             const int nvalid = min(32, nb - c * 32);
-            // which of the chunk's Gaussians can reach alpha >= 1/255 inside this warp's pixels
-            const bool hitw = lane < nvalid && ((__float_as_uint(rec_b[c * 32 + lane].z) >> w) & 1u);
+            // which of the chunk's Gaussians can reach alpha >= 1/255 inside this warp's pixels: lane
+            // j tests Gaussian c*32 + j against the warp's box
+            bool hitw = false;
+            if (lane < nvalid) {
+                const float4 rq = rec_c[c * 32 + lane];
+                if (rq.x - rq.z <= wbox.y && rq.x + rq.z >= wbox.x && rq.y - rq.w <= wbox.w && rq.y + rq.w >= wbox.z) {
+                    const float4 rb = rec_b[c * 32 + lane];
+                    hitw = reaches(rq.x, rq.y, rec_a[c * 32 + lane].w, rb.x, rb.y, rb.w, wbox, rb.z);
+                }
+            }
             const uint32_t mask = __ballot_sync(0xffffffffu, hitw);
-            const int base = seen;
-            seen += nvalid;
+            const int base = seen + c * 32;
             if (mask == 0) continue;
-            // A: composite the surviving Gaussians for this thread's two pixels, two
-            // Gaussians at a time: the four exponents and exp2 of a group are independent;
-            // only each pixel's transmittance updates run in order
-            // the survivors' chunk positions in order, then -1
+            // A: composite the surviving Gaussians for this thread's two pixels, two Gaussians at a
+            // time: the four exponents and exp2 of a group are independent; only each pixel's
+            // transmittance updates run in order. The survivors' chunk positions in order, then -1.
             const int n = __popc(mask);
             executed += (unsigned long long)n;
-            int32_t *cl = sm.clist[w];
             if (hitw) cl[__popc(mask & lt)] = lane;
             if (lane == 0) cl[n] = -1;
             __syncwarp();
@@ -556,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
                         wsum1 -= nw1;
                     }
                     wb_warp[jj[k] * kWStride + lane] = pair_same ? nw0 + nw1 : nw0;
-                    if (split1 && nw1 != 0.f) flush_slot(a, sm, slot1, c * 32 + jj[k], -nw1);
+                    if (split1 && nw1 != 0.f) flush_slot(a, sm, b, slot1, c * 32 + jj[k], -nw1);
                 }
             }
             __syncwarp();
@@ -576,67 +691,32 @@ __global__ void __launch_bounds__(kThreads, 6) composite_k(const CompositeArgs a
                     }
                     const float2 a01 = unpk(s01), a23 = unpk(s23);
                     const float acc = -((a01.x + a01.y) + (a23.x + a23.y));   // the buffer holds -w
-                    if (acc != 0.f) flush_slot(a, sm, gs, gi, acc);
+                    if (acc != 0.f) flush_slot(a, sm, b, gs, gi, acc);
                 } else {
                     int cur = sm.slot_lane[w * 32];
                     float acc = 0.f;
                     for (int q = 0; q < 32; ++q) {
                         const int sl = sm.slot_lane[w * 32 + q];
                         if (sl != cur) {
-                            if (cur >= 0 && acc != 0.f) flush_slot(a, sm, cur, gi, acc);
+                            if (cur >= 0 && acc != 0.f) flush_slot(a, sm, b, cur, gi, acc);
                             acc = 0.f;
                             cur = sl;
                         }
                         acc -= row[q];   // the buffer holds -w
                     }
-                    if (cur >= 0 && acc != 0.f) flush_slot(a, sm, cur, gi, acc);
+                    if (cur >= 0 && acc != 0.f) flush_slot(a, sm, b, cur, gi, acc);
                 }
             }
             __syncwarp();
         }
-        __syncthreads();
-        // C: per Gaussian of the batch, the non-zero (segment, sum) entries go to the warp's
-        // queue (its fill level qn is warp-uniform), clearing the table for the next batch; the
-        // queue goes to the view's record list in blocks, and the combine pass adds the
-        // records to the per-Gaussian tables
-        if (a.accumulate) {
-            for (int i0 = 0; i0 < nb; i0 += kThreads) {
-                const int i = i0 + tid;
-                const bool valid = i < nb;
-                const uint32_t g = valid ? sm.gid[i] : 0u;
-                for (int s2 = 0; s2 < ns_smem; ++s2) {
-                    float v = 0.f;
-                    if (valid) {
-                        v = sm.wb[s2][i];
-                        sm.wb[s2][i] = 0.f;
-                    }
-                    const uint32_t bal = __ballot_sync(0xffffffffu, v != 0.f);
-                    if (bal == 0u) continue;
-                    if (!a.recs) {   // no record list: the sums go to the tables directly
-                        if (v != 0.f) sink_add(sink_of(a), g, sm.seg_of_slot[s2], v);
-                        continue;
-                    }
-                    if (qn + 32 > kWarpQ) {
-                        flush_warp(a, sm, w, lane, qn);
-                        qn = 0;
-                    }
-                    if (v != 0.f) {
-                        const int k = qn + __popc(bal & lt);
-                        sm.rec_g[w][k] = g;
-                        sm.rec_w[w][k] = v;
-                        sm.rec_s[w][k] = (uint8_t)s2;
-                    }
-                    qn += __popc(bal);
-                }
-            }
-            if (qn >= kWarpFlush) {
-                flush_warp(a, sm, w, lane, qn);
-                qn = 0;
-            }
+        seen += nb;
+        {
+            const bool any = __any_sync(0xffffffffu, T0 > 0.f || T1 > 0.f);
+            if (lane == 0) sm.warp_live[w] = any ? 1 : 0;
         }
+        __syncwarp();
+        tc::arrive(&sm.empty[b]);   // every lane: each releases its own reads and sums
     }
-    if (a.accumulate && a.recs && qn > 0) flush_warp(a, sm, w, lane, qn);
-    if (trace && tid == 0) a.dbg_staged[tile] = (uint32_t)staged;
 
     if (inside0) {
         const int64_t pi = (int64_t)py0 * W + px0;
@@ -671,7 +751,7 @@ void launch_composite(const CompositeArgs &a, cudaStream_t st) {
                        : (debug ? composite_k<false, true> : composite_k<false, false>);
     // on failure the error stays recorded for the caller's cudaGetLastError check
     if (set_max_smem((const void *)kfn, (int)sizeof(Smem)) != cudaSuccess) return;
-    kfn<<<tiles * kSubTiles, kThreads, sizeof(Smem), st>>>(a); note_launch();
+    kfn<<<tiles, kThreads, sizeof(Smem), st>>>(a); note_launch();
 }
 
 SLAG_CHECKS_TAKE(checks_take_composite)

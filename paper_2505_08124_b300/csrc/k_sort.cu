@@ -1,6 +1,6 @@
 // Stable LSD radix sort and exclusive scan (no CUB).
 //
-// Radix sort, one pass per digit of <= 11 bits (256 or 2048 bins), three
+// Radix sort, one pass per digit of <= 11 bits (256, 512, 1024 or 2048 bins), three
 // kernels per pass, over tiles of 256 x ITEMS items (ITEMS = 16, or 4 below
 // ~2M items so that the grid still covers the GPU):
 //   1. rs_hist:    each CTA counts the digits of its tile into per-warp
@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
                                                        int64_t n, int shift, uint32_t mask, int width,
                                                        const uint32_t *__restrict__ offs,
                                                        const uint32_t *__restrict__ digit_tot, int ntiles,
-                                                       uint2 *__restrict__ ranges, int nranges) {
+                                                       uint2 *__restrict__ ranges, int nranges,
+                                                       const uint2 *__restrict__ gsrc, uint2 *__restrict__ gout) {
     constexpr int kTileN = kThreads * ITEMS;
     constexpr int kPer = BINS / kThreads;              // digits per thread in the per-tile scans
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -248,7 +249,9 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
         const uint32_t gp = gbase[d] + (uint32_t)j - lstart[d];
         if (!SLAG_IN_BOUNDS((int64_t)gp < n, kCheckSort)) continue;
         kout[gp] = k;
-        vout[gp] = svals[j];
+        const uint32_t v = svals[j];
+        vout[gp] = v;
+        if (gout) gout[gp] = gsrc[v];   // a payload that follows the values (gathered by value)
     }
 }
 
@@ -259,7 +262,7 @@ size_t scatter_smem() {
 
 template <typename K, int ITEMS, int BINS>
 void radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, int64_t n, int shift, int width, SortScratch &s,
-                cudaStream_t st, uint2 *ranges, int nranges) {
+                cudaStream_t st, uint2 *ranges, int nranges, const uint2 *gsrc, uint2 *gout) {
     constexpr int kTileN = kThreads * ITEMS;
     const int ntiles = (int)((n + kTileN - 1) / kTileN);
     // on failure the error stays recorded for the caller's cudaGetLastError check
@@ -270,26 +273,37 @@ void radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, int64_t n,
     rs_hist<K, ITEMS, BINS><<<ntiles, kThreads, kWarps * BINS * 4, st>>>(ki, n, shift, mask, width, s.hist, ntiles); note_launch();
     rs_offsets<<<BINS, ntiles >= 1024 ? 1024 : (ntiles >= 256 ? 256 : 64), 0, st>>>(s.hist, s.digit_tot, ntiles); note_launch();
     rs_scatter<K, ITEMS, BINS><<<ntiles, kThreads, scatter_smem<K, ITEMS, BINS>(), st>>>(
-        ki, vi, ko, vo, n, shift, mask, width, s.hist, s.digit_tot, ntiles, ranges, nranges); note_launch();
+        ki, vi, ko, vo, n, shift, mask, width, s.hist, s.digit_tot, ntiles, ranges, nranges, gsrc, gout);
+    note_launch();
 }
 
 // Inputs below ~2M items use 1024-item tiles so that the grid still covers the GPU;
-// passes wider than 8 bits use 2048 bins.
+// a pass of w bits uses the smallest of 256, 512, 1024 and 2048 bins that holds its digits
+// (fewer bins: smaller per-tile histograms to clear, write and scan).
 template <typename K>
 bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, const int *shifts,
-                     const int *widths, int npass, SortScratch &s, cudaStream_t st, uint2 *ranges, int nranges) {
+                     const int *widths, int npass, SortScratch &s, cudaStream_t st, uint2 *ranges, int nranges,
+                     const uint2 *gsrc = nullptr, uint2 *gout = nullptr) {
     if (n <= 0 || npass <= 0) return false;
     const bool small = n < (1 << 21);
     K *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < npass; ++p) {
         uint2 *rg = (npass == 1) ? ranges : nullptr;
-        if (widths[p] > 8) {
-            if (small) radix_pass<K, 4, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges);
-            else radix_pass<K, kItems, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges);
+        const uint2 *gs = (p == npass - 1) ? gsrc : nullptr;   // the payload follows the last pass
+        uint2 *go = (p == npass - 1) ? gout : nullptr;
+        if (widths[p] > 10) {
+            if (small) radix_pass<K, 4, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+            else radix_pass<K, kItems, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+        } else if (widths[p] > 9) {
+            if (small) radix_pass<K, 4, 1024>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+            else radix_pass<K, kItems, 1024>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+        } else if (widths[p] > 8) {
+            if (small) radix_pass<K, 4, 512>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+            else radix_pass<K, kItems, 512>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
         } else {
-            if (small) radix_pass<K, 4, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges);
-            else radix_pass<K, kItems, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges);
+            if (small) radix_pass<K, 4, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+            else radix_pass<K, kItems, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
         }
         K *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
@@ -455,9 +469,9 @@ int digit_passes(int lo, int bits, int *shifts, int *widths, int64_t n) {
 
 bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                     const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st,
-                    uint2 *ranges, int nranges) {
+                    uint2 *ranges, int nranges, const uint2 *gather_src, uint2 *gather_out) {
     return radix_sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st, ranges,
-                                     nranges);
+                                     nranges, gather_src, gather_out);
 }
 
 bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,

@@ -519,26 +519,32 @@ slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
     span_begin(ctx, SLAG_STAGE_BIN, st);
     launch_emit(vs.srect, vs.offsets, nv, shift, bins_x, P, vs.pkey[0], vs.pval[0], st);
     int shifts[8], widths[8];
-    const int np = digit_passes(0, ceil_log2((uint64_t)bins), shifts, widths, P);
+    int np = digit_passes(0, ceil_log2((uint64_t)bins), shifts, widths, P);
+    if (np == 0) {
+        // a single bin: one 1-bit pass still runs, for the ranges and the pairs' rectangles
+        shifts[0] = 0;
+        widths[0] = 1;
+        np = 1;
+    }
     uint32_t *keys = vs.pkey[0];
     bool alt = false;
+    // the tile rectangle of each sorted pair (the composite's per-tile filter), for super-tile bins
+    if (shift > 0) CK(grow(vs.prect, vs.prect_cap, P, st));
     if (P > 0 && np == 1) {
-        // one pass: its digit is the bin id, and the pass's offsets give the ranges
+        // one pass: its digit is the bin id, and the pass's offsets give the ranges; the pass also
+        // gathers each sorted pair's tile rectangle
         alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr, st,
-                             vs.ranges, (int)bins);
+                             vs.ranges, (int)bins, shift > 0 ? vs.srect : nullptr, shift > 0 ? vs.prect : nullptr);
         keys = vs.pkey[alt ? 1 : 0];
     } else {
         CK(cudaMemsetAsync(vs.ranges, 0, sizeof(uint2) * (size_t)bins, st));
-        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr, st);
+        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr, st, nullptr,
+                             0, shift > 0 ? vs.srect : nullptr, shift > 0 ? vs.prect : nullptr);
         keys = vs.pkey[alt ? 1 : 0];
         launch_ranges(keys, P, vs.ranges, st);
     }
     CK(grow(vs.tile_order, vs.order_cap, tiles, st));
     launch_tile_order(vs.ranges, cp.tiles_x, cp.tiles_y, shift, vs.tile_order, st);
-    if (shift > 0) {
-        CK(grow(vs.prect, vs.prect_cap, P, st));
-        launch_pair_rects(vs.pval[alt ? 1 : 0], P, vs.srect, vs.prect, st);
-    }
     span_end(ctx, st);
     CK(cudaGetLastError());
     *P_out = P;
@@ -820,6 +826,11 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     a.recs = vs.recs;
     a.rec_count = vs.rec_count;
     a.rec_cap = (unsigned long long)vs.rec_cap;
+    a.dbg_list = nullptr;
+    a.dbg_off = nullptr;
+    a.dbg_staged = nullptr;
+    a.dbg_bad = nullptr;
+    a.err = ctx->tc_err;
     span_begin(ctx, SLAG_STAGE_COMPOSITE, bk);
     launch_composite(a, bk);
     span_end(ctx, bk);
@@ -1262,7 +1273,7 @@ slag_status finalize_impl(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_
     launch_copy_words(ctx->d_nq, &ctx->hc_dev->n_q, sizeof(unsigned long long), st);
     launch_copy_words(ctx->tc_err, &ctx->hc_dev->tc_err, sizeof(uint32_t), st);
     CK(cudaStreamSynchronize(st));
-    if (ctx->hc->tc_err) return timeout_reported(ctx, "the tensor-core aggregation gave up waiting");
+    if (ctx->hc->tc_err) return timeout_reported(ctx, "a bounded device wait gave up (compositing or aggregation)");
     {
         const slag_status sc = checks_reported(ctx);
         if (sc != SLAG_OK) return sc;
@@ -1967,6 +1978,18 @@ slag_status slag_state_merge_host(const void *a, int64_t a_bytes, const void *b,
     return SLAG_OK;
 }
 
+slag_status slag_set_device_budget(slag_ctx *ctx, int64_t bytes) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    if (bytes < 0) return fail(ctx, SLAG_ERR_INVALID_ARG, "budget < 0");
+    // a chunk's device rows: E (4 D bytes), sum w and the caller index (4 bytes each)
+    const int64_t per_row = 4 * (int64_t)ctx->D + 8;
+    int64_t rows = bytes > 0 ? bytes / per_row : ((int64_t)1 << 20);
+    rows = rows / kBlockG * kBlockG;
+    if (rows < kBlockG) rows = kBlockG;
+    ctx->chunk_gaussians = rows;
+    return SLAG_OK;
+}
+
 slag_status slag_set_linear_code(slag_ctx *ctx, const float *params) {
     if (!ctx || !params) return SLAG_ERR_INVALID_ARG;
     if (ctx->precision != SLAG_PREC_LINEAR32) return fail(ctx, SLAG_ERR_STATE, "context is not SLAG_PREC_LINEAR32");
@@ -2358,6 +2381,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     a.dbg_off = d_off;
     a.dbg_staged = d_staged;
     a.dbg_bad = d_bad;
+    a.err = ctx->tc_err;
     a.accumulate = 0;
     launch_composite(a, st);
     e = cudaGetLastError();
@@ -2430,6 +2454,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.dbg_T = ctx->dbg_T;
     a.dbg_wsum = ctx->dbg_wsum;
     a.dbg_count = ctx->dbg_count;
+    a.err = ctx->tc_err;
     a.accumulate = 0;
     a.recs = nullptr;
     a.rec_count = nullptr;

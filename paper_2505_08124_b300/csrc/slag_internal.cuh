@@ -113,10 +113,12 @@ void scratch_free(SortScratch &s);
 // shifts/widths (each width <= 11, applied in order). Ping-pongs between the
 // two buffers; returns true when the result is in the *_alt buffers. For a
 // single pass whose digit is the whole key, `ranges` (nullable) receives each
-// key value's [start, end) in the output for key values < nranges.
+// key value's [start, end) in the output for key values < nranges. With
+// gather_out (n entries), gather_out[i] = gather_src[sorted value i] as well.
 bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                     int64_t n, const int *shifts, const int *widths, int npass, SortScratch &s,
-                    cudaStream_t st, uint2 *ranges = nullptr, int nranges = 0);
+                    cudaStream_t st, uint2 *ranges = nullptr, int nranges = 0, const uint2 *gather_src = nullptr,
+                    uint2 *gather_out = nullptr);
 bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                     int64_t n, const int *shifts, const int *widths, int npass, SortScratch &s,
                     cudaStream_t st);
@@ -161,8 +163,6 @@ void launch_check_seg(const int32_t *seg, int64_t npx, int32_t M, ViewCounters *
 void launch_emit(const uint2 *srect, const uint32_t *offsets, uint32_t n_visible, int shift, int bins_x, int64_t cap,
                  uint32_t *keys, uint32_t *vals, cudaStream_t st);
 void launch_ranges(const uint32_t *keys, int64_t P, uint2 *ranges, cudaStream_t st);
-// prect[i] = srect[list[i]]: the tile rectangle of each sorted pair's Gaussian.
-void launch_pair_rects(const uint32_t *list, int64_t P, const uint2 *srect, uint2 *prect, cudaStream_t st);
 // Tiles grouped by descending floor(log2(list length + 1)) of their bin.
 void launch_tile_order(const uint2 *ranges, int tiles_x, int tiles_y, int shift, uint32_t *order,
                        cudaStream_t st);
@@ -261,6 +261,7 @@ struct CompositeArgs {
     const int64_t *dbg_off;
     uint32_t *dbg_staged;
     uint32_t *dbg_bad;
+    uint32_t *err;                 // set when a bounded wait gave up (nullable)
     int accumulate;                // 0: compositing only (diagnostics)
     WeightRecord *recs;            // record list of the view (nullable: sums go to the tables directly)
     unsigned long long *rec_count; // records written (zeroed before the launch)

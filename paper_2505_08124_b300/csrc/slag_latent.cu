@@ -76,17 +76,19 @@ void linear_encode(const float *params, const float *enc_bias, int32_t D, const 
 }
 
 int64_t linear_decode_scratch(int rows, int32_t D) {
-    return dense_tc_pad_rows(rows) * 2 * kLatent + (int64_t)D * kLatent;
+    return dense_tc_pad_rows(rows) * 2 * kLatent + 2 * (int64_t)D * kLatent;
 }
 
+// The dense layer takes its weights transposed, output x input: for the decoder (input 32, output
+// D) that is U itself (D x 32), rounded to TF32 (the first of its two TF32 planes).
 cudaError_t linear_decode(const float *params, int32_t D, const float *Z, int rows, float *scratch, float *Y,
                           uint32_t *err, cudaStream_t st) {
     const int64_t rp = dense_tc_pad_rows(rows);
     float *Zp = scratch;                         // 2 x rp x kLatent
-    float *Ut = Zp + rp * 2 * kLatent;           // D x kLatent
+    float *Up = Zp + rp * 2 * kLatent;           // 2 x D x kLatent: U rounded to TF32, then the rest
     launch_tf32_planes(Z, rows, rp, kLatent, Zp, st);
-    launch_weights_t(params, kLatent, D, Ut, st, true);
-    return launch_dense_tc(Zp, rows, rp, kLatent, Ut, D, params + (int64_t)D * kLatent, false, Y, D, err, st);
+    launch_tf32_planes(params, D, D, kLatent, Up, st);
+    return launch_dense_tc(Zp, rows, rp, kLatent, Up, D, params + (int64_t)D * kLatent, false, Y, D, err, st);
 }
 
 }  // namespace slag

@@ -72,7 +72,8 @@ EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_
            "slag_wait_outputs", "slag_set_profiling_stages", "slag_bin_view_bins", "slag_composite_trace",
            "slag_save_state", "slag_load_state", "slag_merge_state", "slag_state_merge_host",
            "slag_check_wait_timeout", "slag_is_checked_build", "slag_debug_force_pair_capacity",
-           "slag_linear_param_count", "slag_linear_code_fit", "slag_set_linear_code", "slag_query_threshold")
+           "slag_linear_param_count", "slag_linear_code_fit", "slag_set_linear_code", "slag_query_threshold",
+           "slag_set_device_budget")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -129,6 +130,7 @@ def load_library(path: str = LIB_PATH):
     lib.slag_linear_param_count.restype = i64
     lib.slag_linear_code_fit.argtypes = [P, i64, i32, i32, P, P, P]
     lib.slag_set_linear_code.argtypes = [P, P]
+    lib.slag_set_device_budget.argtypes = [P, i64]
     lib.slag_add_views_batched.argtypes = [i32, P, P, P, ctypes.POINTER(i32)]
     lib.slag_set_autotune.argtypes = [P, i32]
     lib.slag_kernel_launches.argtypes = []
@@ -345,6 +347,10 @@ class Lifter:
 
     def reset(self):
         self._check(self._lib.slag_reset(self._h), "slag_reset")
+
+    def set_device_budget(self, nbytes: int):
+        """Device bytes the out-of-core finalize may hold for output rows at a time (0 = default)."""
+        self._check(self._lib.slag_set_device_budget(self._h, int(nbytes)), "slag_set_device_budget")
 
     def set_autotune(self, on: bool = True):
         self._check(self._lib.slag_set_autotune(self._h, 1 if on else 0), "slag_set_autotune")

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +51,14 @@ def test_batched_scenes_match_single(slag):
             assert L.stats()["views"] == s.n_views
             np.testing.assert_allclose(wb, w, rtol=1e-6, atol=0)
             np.testing.assert_allclose(Eb, E, rtol=1e-5, atol=1e-7)
+            # and the float64 oracle over the scene's views: the float32 parity bar
+            num, den, _ = O.lift(s.gaussians, list(s.views()))
+            Eo = O.normalise(num, den)
+            assert np.linalg.norm(Eb - Eo) / np.linalg.norm(Eo) <= 1e-4
+            assert np.linalg.norm(wb - den) / np.linalg.norm(den) <= 1e-4
+            ok = den >= 1e-3
+            cos = (Eb[ok] * Eo[ok]).sum(1) / (np.linalg.norm(Eb[ok], axis=1) * np.linalg.norm(Eo[ok], axis=1))
+            assert cos.min() >= 0.99999
     finally:
         for L in lifters:
             L.close()

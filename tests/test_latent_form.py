@@ -213,13 +213,17 @@ def test_linear_code_lifting_is_the_projection_of_the_aggregate(slag):
             Ll.add_view(v.camera, v.seg, v.table)
         El, wl = Ll.finalize()
         ids = Ll.query_threshold(views[0].table[0] / np.linalg.norm(views[0].table[0]), 0.28)
-    np.testing.assert_array_equal(wl, wf)
+    # the weight sums are the float32 path's (float32 atomics add in a run-dependent order)
+    np.testing.assert_allclose(wl, wf, rtol=1e-5, atol=1e-7)
     ok = wf >= 1e-3
     assert ok.sum() > 500
     E = Ef[ok].astype(np.float64)
     proj = mu + (E - mu) @ U @ U.T
-    np.testing.assert_allclose(El[ok], proj, atol=2e-5)
-    assert np.all(El[wf == 0] == 0)
+    # the decoder multiplies the codes (exact hi/lo TF32 planes) by U rounded to TF32 (relative
+    # error <= 2^-11 per element): rows agree to that rounding
+    rel = np.linalg.norm(El[ok] - proj, axis=1) / np.linalg.norm(proj, axis=1)
+    assert rel.max() <= 5e-4, rel.max()
+    assert np.all(El[wl == 0] == 0)
     cos = (El[ok] * E).sum(1) / (np.linalg.norm(El[ok], axis=1) * np.linalg.norm(E, axis=1))
     print("linear code vs float32 path: mean 1 - cos %.2e, max %.2e" % ((1 - cos).mean(), (1 - cos).max()))
     assert len(ids) > 0
