@@ -17,7 +17,8 @@
 // tile, taken in list order.
 //   * Producer: fills one of two record buffers at a time with the hits among
 //     the next 160 candidates of the bin's list (the following 160 are loaded
-//     meanwhile; records are copied asynchronously), turns each record into a tile-local exponent
+//     meanwhile; each hit's record is copied asynchronously from the view's
+//     records through the rank -> Gaussian map), turns each record into a tile-local exponent
 //     polynomial (keeping what the consumers' culling tests need), and publishes the
 //     buffer on an mbarrier; it refills a buffer once all consumers have
 //     released it, first moving that buffer's per-(segment, Gaussian) sums to
@@ -310,6 +311,23 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
     int it = 0;
     for (;; ++it) {
         const int b = it & 1;
+        // this batch's candidates and their hits; the next batch's loads are issued now, and the
+        // Gaussian of each hit (the rank -> Gaussian map) is read while the buffer is drained
+        uint32_t r[kPerLane], g[kPerLane];
+        bool hit[kPerLane];
+#pragma unroll
+        for (int k = 0; k < kPerLane; ++k) {
+            const int c = cursor + k * 32 + lane;
+            r[k] = r_nx[k];
+            const uint2 rc = rc_nx[k];
+            hit[k] = c < end && (uint32_t)tx >= (rc.x & 0xffffu) && (uint32_t)tx < (rc.x >> 16) &&
+                     (uint32_t)ty >= (rc.y & 0xffffu) && (uint32_t)ty < (rc.y >> 16) &&
+                     SLAG_IN_BOUNDS(r[k] < a.n_ranks, kCheckComposite);
+            g[k] = hit[k] ? a.sgid[r[k]] : 0u;
+            const int cn = c + kBuf;
+            r_nx[k] = cn < end ? a.list[cn] : 0u;
+            rc_nx[k] = cn < end ? a.prect[cn] : make_uint2(0u, 0u);
+        }
         if (it >= 2) {
             // the consumers have released this buffer (its previous batch, it - 2): move its sums out
             if (!wait_phase(a, sm, &sm.empty[b], (uint32_t)((it >> 1) - 1) & 1u)) { ok = false; break; }
@@ -326,20 +344,6 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
             tc::arrive(&sm.full[b]);
             break;
         }
-        // this batch's candidates; the next batch's loads are issued now
-        uint32_t r[kPerLane];
-        bool hit[kPerLane];
-#pragma unroll
-        for (int k = 0; k < kPerLane; ++k) {
-            const int c = cursor + k * 32 + lane;
-            r[k] = r_nx[k];
-            const uint2 rc = rc_nx[k];
-            hit[k] = c < end && (uint32_t)tx >= (rc.x & 0xffffu) && (uint32_t)tx < (rc.x >> 16) &&
-                     (uint32_t)ty >= (rc.y & 0xffffu) && (uint32_t)ty < (rc.y >> 16);
-            const int cn = c + kBuf;
-            r_nx[k] = cn < end ? a.list[cn] : 0u;
-            rc_nx[k] = cn < end ? a.prect[cn] : make_uint2(0u, 0u);
-        }
         // stable compaction of the hits (candidate order is (k, lane)); their records are copied
         // asynchronously
         int nb = 0;
@@ -347,10 +351,10 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
         for (int k = 0; k < kPerLane; ++k) {
             const uint32_t bal = __ballot_sync(0xffffffffu, hit[k]);
             const int pos = nb + __popc(bal & lt);
-            if (hit[k] && SLAG_IN_BOUNDS(pos < kBuf && r[k] < a.n_ranks, kCheckComposite)) {
-                cp_async16(&sm.rec_a[b][pos], a.srec_a + r[k]);
-                cp_async16(&sm.rec_b[b][pos], a.srec_b + r[k]);
-                cp_async4(&sm.gid[b][pos], a.sgid + r[k]);
+            if (hit[k]) {
+                cp_async16(&sm.rec_a[b][pos], a.rec_a + g[k]);
+                cp_async16(&sm.rec_b[b][pos], a.rec_b + g[k]);
+                sm.gid[b][pos] = g[k];
                 if (trace) {
                     const int64_t at = a.dbg_off[tile] + staged + pos;
                     if (at < a.dbg_off[tile + 1]) a.dbg_list[at] = r[k];

@@ -246,11 +246,10 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(&ctr->n_visible, (uint32_t)__popc(b));
 }
 
-// r < n_visible: records, rectangle and tile count of the Gaussian of depth rank r.
+// r < n_visible: rectangle and bin count of the Gaussian of depth rank r (the records stay in the
+// internal order; the compositing kernel reads them through the rank -> Gaussian map).
 __global__ void gather_sorted_k(const uint32_t *__restrict__ sorted_vals, int64_t n, ViewCounters *ctr,
-                                const float4 *__restrict__ rec_a, const float4 *__restrict__ rec_b,
-                                const uint2 *__restrict__ rect, float4 *__restrict__ srec_a,
-                                float4 *__restrict__ srec_b, uint2 *__restrict__ srect,
+                                const uint2 *__restrict__ rect, uint2 *__restrict__ srect,
                                 uint32_t *__restrict__ stouched, int shift) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t tiles = 0;
@@ -258,8 +257,6 @@ __global__ void gather_sorted_k(const uint32_t *__restrict__ sorted_vals, int64_
         const uint32_t nv = ctr->n_visible;
         if (r < nv) {
             const uint32_t g = sorted_vals[r];
-            srec_a[r] = rec_a[g];
-            srec_b[r] = rec_b[g];
             const uint2 rc = rect[g];
             srect[r] = rc;
             const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
@@ -320,11 +317,10 @@ void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *c
                                                   dval_orig, rec_a, rec_b, rect, ctr); note_launch();
 }
 
-void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, ViewCounters *ctr, const float4 *rec_a,
-                          const float4 *rec_b, const uint2 *rect, float4 *srec_a, float4 *srec_b, uint2 *srect,
+void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, ViewCounters *ctr, const uint2 *rect, uint2 *srect,
                           uint32_t *stouched, int shift, cudaStream_t st) {
-    gather_sorted_k<<<blocks_for(n, 256), 256, 0, st>>>(sorted_vals, n, ctr, rec_a, rec_b, rect, srec_a, srec_b,
-                                                        srect, stouched, shift); note_launch();
+    gather_sorted_k<<<blocks_for(n, 256), 256, 0, st>>>(sorted_vals, n, ctr, rect, srect, stouched, shift);
+    note_launch();
 }
 
 void launch_check_seg(const int32_t *seg, int64_t npx, int32_t M, ViewCounters *ctr, cudaStream_t st) {

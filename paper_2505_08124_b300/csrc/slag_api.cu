@@ -70,7 +70,7 @@ constexpr int kTotals = 5;  // device running totals (see slag_ctx::totals)
 struct ViewSlot {
     // n-sized
     uint32_t *dkey[2] = {nullptr, nullptr}, *dval[2] = {nullptr, nullptr};
-    float4 *rec_a = nullptr, *rec_b = nullptr, *srec_a = nullptr, *srec_b = nullptr;
+    float4 *rec_a = nullptr, *rec_b = nullptr;
     uint2 *rect = nullptr, *srect = nullptr;
     uint32_t *stouched = nullptr, *offsets = nullptr;
     HashEntry *hash = nullptr;             // per-view (segment, weight) slots; consume clears them
@@ -481,8 +481,7 @@ slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
     const bool alt = radix_sort_u32(vs.dkey[0], vs.dkey[1], vs.dval[0], vs.dval[1], n, shifts, widths, np,
                                     ctx->scratch, st);
     vs.sgid = vs.dval[alt ? 1 : 0];
-    launch_gather_sorted(vs.sgid, n, vs.ctr, vs.rec_a, vs.rec_b, vs.rect, vs.srec_a, vs.srec_b, vs.srect,
-                         vs.stouched, shift, st);
+    launch_gather_sorted(vs.sgid, n, vs.ctr, vs.rect, vs.srect, vs.stouched, shift, st);
     exclusive_scan_u32(vs.stouched, vs.offsets, n, &vs.ctr->P, ctx->scratch, st);
     span_end(ctx, st);
     launch_copy_words(vs.ctr, &vs.h_dev->v, sizeof(ViewCounters), st);
@@ -569,7 +568,7 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
     cudaError_t e = cudaSuccess;
 #define SA(call) do { if (e == cudaSuccess) e = (call); } while (0)
     for (int b = 0; b < 2; ++b) { SA(dalloc(&vs.dkey[b], n)); SA(dalloc(&vs.dval[b], n)); }
-    SA(dalloc(&vs.rec_a, n)); SA(dalloc(&vs.rec_b, n)); SA(dalloc(&vs.srec_a, n)); SA(dalloc(&vs.srec_b, n));
+    SA(dalloc(&vs.rec_a, n)); SA(dalloc(&vs.rec_b, n));
     SA(dalloc(&vs.rect, n)); SA(dalloc(&vs.srect, n));
     SA(dalloc(&vs.stouched, n)); SA(dalloc(&vs.offsets, n));
     SA(dalloc(&vs.hash, n));
@@ -592,7 +591,7 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
 
 void slot_free(ViewSlot &vs) {
     for (int b = 0; b < 2; ++b) { dfree(vs.dkey[b]); dfree(vs.dval[b]); dfree(vs.pkey[b]); dfree(vs.pval[b]); }
-    dfree(vs.rec_a); dfree(vs.rec_b); dfree(vs.srec_a); dfree(vs.srec_b); dfree(vs.rect); dfree(vs.srect);
+    dfree(vs.rec_a); dfree(vs.rec_b); dfree(vs.rect); dfree(vs.srect);
     dfree(vs.stouched); dfree(vs.offsets); dfree(vs.hash);
     dfree(vs.prect); dfree(vs.ranges); dfree(vs.tile_order); dfree(vs.seg_buf); dfree(vs.ctr);
     dfree(vs.ctr_up); dfree(vs.recs); dfree(vs.rec_count);
@@ -802,8 +801,8 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     a.tile_order = vs.tile_order;
     a.list = list;
     a.prect = vs.prect;
-    a.srec_a = vs.srec_a;
-    a.srec_b = vs.srec_b;
+    a.rec_a = vs.rec_a;
+    a.rec_b = vs.rec_b;
     a.sgid = vs.sgid;
     a.n_ranks = vs.h->v.n_visible;
     a.seg = vs.seg_buf;
@@ -2366,8 +2365,8 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     a.tile_order = vs.tile_order;
     a.list = list;
     a.prect = vs.prect;
-    a.srec_a = vs.srec_a;
-    a.srec_b = vs.srec_b;
+    a.rec_a = vs.rec_a;
+    a.rec_b = vs.rec_b;
     a.sgid = sgid;
     a.n_ranks = vs.h->v.n_visible;
     a.weight_mode = ctx->weight_mode;
@@ -2442,8 +2441,8 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.tile_order = vs.tile_order;
     a.list = list;
     a.prect = vs.prect;
-    a.srec_a = vs.srec_a;
-    a.srec_b = vs.srec_b;
+    a.rec_a = vs.rec_a;
+    a.rec_b = vs.rec_b;
     a.sgid = sgid;
     a.n_ranks = vs.h->v.n_visible;
     a.seg = nullptr;

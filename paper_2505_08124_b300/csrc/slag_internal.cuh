@@ -149,12 +149,10 @@ void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *c
                     const float2 *cov_b, int64_t n, const uint32_t *orig_of_int, uint32_t *dkey_orig,
                     uint32_t *dval_orig, float4 *rec_a, float4 *rec_b, uint2 *rect,
                     ViewCounters *ctr, cudaStream_t st);
-// Records, rectangles and bin counts in depth-rank order. With shift s > 0 the
-// count is of 2^s x 2^s-tile super-tiles; the tile-pair total goes to ctr->P_tiles.
-void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, ViewCounters *ctr,
-                          const float4 *rec_a, const float4 *rec_b, const uint2 *rect,
-                          float4 *srec_a, float4 *srec_b, uint2 *srect, uint32_t *stouched,
-                          int shift, cudaStream_t st);
+// Rectangles and bin counts in depth-rank order. With shift s > 0 the count is of
+// 2^s x 2^s-tile super-tiles; the tile-pair total goes to ctr->P_tiles.
+void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, ViewCounters *ctr, const uint2 *rect,
+                          uint2 *srect, uint32_t *stouched, int shift, cudaStream_t st);
 void launch_check_seg(const int32_t *seg, int64_t npx, int32_t M, ViewCounters *ctr, cudaStream_t st);
 
 // k_bin.cu
@@ -233,7 +231,7 @@ struct CompositeArgs {
     const uint32_t *tile_order;    // CTAs of tile_order[i] come i-th
     const uint32_t *list;          // sorted values: depth rank of each pair
     const uint2 *prect;            // tile rectangle of the Gaussian of each sorted pair
-    const float4 *srec_a, *srec_b; // records in depth-rank order
+    const float4 *rec_a, *rec_b;   // records in internal order (the Gaussian of rank r is sgid[r])
     const uint32_t *sgid;          // internal Gaussian index of each depth rank
     uint32_t n_ranks;              // records (depth ranks) in srec_a / srec_b / sgid
     const int32_t *seg;            // H x W
