@@ -137,7 +137,9 @@ typedef struct {
     int64_t last_contributions;
     int64_t touched;         /* Gaussians with sum w > 0 at the last finalize */
     int64_t evaluations;     /* sum over views of (Gaussian, pixel) pairs visited before each
-                                pixel ended (the compositing work, contributing or not) */
+                                pixel ended (the compositing work, contributing or not): a pixel
+                                that stopped counts its tile's candidates up to the end of the
+                                chunk of 32 in which it stopped */
     int64_t executed;        /* sum over views of the (Gaussian, pixel) evaluations the
                                 compositing kernel carried out: a group of 64 pixels evaluates
                                 the Gaussians that can reach alpha >= 1/255 somewhere in it,

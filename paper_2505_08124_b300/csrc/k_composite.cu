@@ -66,16 +66,16 @@ constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2(1/255)
 constexpr uint32_t kBarConsumers = 1;                 // named barrier of the consumer warps
 
 struct Smem {
-    float4 rec_a[2][kBuf];                // staged (mu'x, mu'y, a', b'); then (K0, K1, K2, K3)
-    float4 rec_b[2][kBuf];                // staged (c', log2 opacity, ex, ey); then (K4, K5, floor margin, log2 o)
-    float4 rec_c[2][kBuf];                // (mu'x, mu'y) tile-local and the alpha-floor half extents
-    uint32_t gid[2][kBuf];                // internal Gaussian index
+    float4 q0[2][kBuf];                   // staged (mu'x, mu'y, a', b'); then (mx, my, r1, r2)
+    float4 q1[2][kBuf];                   // staged (c', log2 opacity, ex, ey); then (A, Bc, C, t)
+    uint2 q2[2][kBuf];                    // (log2 opacity bits, internal Gaussian index)
     float wb[2][kSmemSlots][kBuf];        // per (buffer, slot, Gaussian of the buffer)
     union {
-        float wbuf[kConsumers][32 * kWStride];   // per warp: (Gaussian of the chunk) x lane
+        float wbuf[kConsumers][32 * kWStride];   // per warp: (survivor of the chunk) x lane
         uint32_t keys[kPix];                     // the prologue's segment sort
     };
-    int32_t clist[kConsumers][34];        // per warp: the chunk's surviving Gaussians, then -1
+    float4 stage[kConsumers][16 * 3];     // per warp: survivors' polynomials, two Gaussians interleaved
+    int32_t clist[kConsumers][32];        // per warp: chunk position of each survivor
     uint32_t split_min[2][kConsumers];    // prologue multi-split: per-warp minimum segment
     int32_t split_cnt[2][kConsumers];     // and per-warp counts (first | second pixel << 16)
     int32_t slot_lane[kPixThreads];       // slot of the sums each lane stores (its first pixel's)
@@ -134,16 +134,29 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
     return d;
 }
 
+// 1.0f where a >= b, else 0.0f (false for NaN)
+__device__ __forceinline__ float set_ge(float a, float b) {
+    float d;
+    asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// The coefficients K0, K1, K2 of the exponent e = K0 + K1 X + K2 Y + A X^2 + Bc X Y + C Y^2 of a
+// Gaussian with tile-local mean (mx, my): e = lo + A dx^2 + Bc dx dy + C dy^2 with dx = mx - X,
+// dy = my - Y, expanded.
+__device__ __forceinline__ void poly_coeffs(float mx, float my, float A, float Bc, float C, float lo, float &K0,
+                                            float &K1, float &K2) {
+    K1 = -fmaf(2.f * A, mx, Bc * my);
+    K2 = -fmaf(Bc, mx, 2.f * C * my);
+    K0 = fmaf(fmaf(A, mx, Bc * my), mx, fmaf(C * my, my, lo));
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src));
-}
-
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src));
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -172,7 +185,7 @@ __device__ __forceinline__ HashSink sink_of(const CompositeArgs &a) {
 
 __device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int b, int slot, int gi, float acc) {
     if (slot < kSmemSlots) atomicAdd(&sm.wb[b][slot][gi], acc);
-    else sink_add(sink_of(a), sm.gid[b][gi], sm.seg_of_slot[slot], acc);
+    else sink_add(sink_of(a), sm.q2[b][gi].y, sm.seg_of_slot[slot], acc);
 }
 
 // Moves the producer's n queued records to the view's record list with one reservation.
@@ -200,15 +213,15 @@ __device__ void flush_queue(const CompositeArgs &a, Smem &sm, int lane, int n) {
 }
 
 // Whether the exponent e(X, Y) = lo + A dx^2 + Bc dx dy + C dy^2 (dx = mx - X, dy = my - Y; A, C < 0
-// and 4AC > Bc^2: a concave quadratic) reaches `thr` anywhere on the box (x0, x1, y0, y1) of a warp's
-// pixel centres. The maximum over the box is lo at the mean when the mean lies inside; otherwise it
-// lies on the box's boundary, where each edge is a concave parabola maximised at its clamped vertex.
-// An empty box (x0 = +inf) reaches nothing.
-__device__ __forceinline__ bool reaches(float mx, float my, float A, float Bc, float C, float lo, float4 box,
-                                        float thr) {
+// and 4AC > Bc^2: a concave quadratic) reaches lo + t anywhere on the box (x0, x1, y0, y1) of a warp's
+// pixel centres; q0 = (mx, my, r1, r2), q1 = (A, Bc, C, t). The maximum over the box is lo at the mean
+// when the mean lies inside; otherwise it lies on the box's boundary, where each edge is a concave
+// parabola maximised at its clamped vertex: dy = r1 dx on a vertical edge (r1 = -Bc / 2C), dx = r2 dy
+// on a horizontal one (r2 = -Bc / 2A). An empty box (x0 = +inf) reaches nothing.
+__device__ __forceinline__ bool reaches(float4 q0, float4 q1, float4 box) {
     if (!(box.x <= box.y)) return false;
-    if (mx >= box.x && mx <= box.y && my >= box.z && my <= box.w) return lo >= thr;
-    const float ia = __frcp_rn(2.f * A), ic = __frcp_rn(2.f * C);
+    const float mx = q0.x, my = q0.y, A = q1.x, Bc = q1.y, C = q1.z, t = q1.w;
+    if (mx >= box.x && mx <= box.y && my >= box.z && my <= box.w) return 0.f >= t;
     const float dx0 = mx - box.y, dx1 = mx - box.x;   // dx range over the box
     const float dy0 = my - box.w, dy1 = my - box.z;
     float best = -INFINITY;
@@ -216,14 +229,14 @@ __device__ __forceinline__ bool reaches(float mx, float my, float A, float Bc, f
     for (int e = 0; e < 2; ++e) {
         // vertical edges: dx fixed, dy free in [dy0, dy1]
         const float dx = e ? dx1 : dx0;
-        const float dy = fminf(fmaxf(-Bc * dx * ic, dy0), dy1);
-        best = fmaxf(best, fmaf(fmaf(A, dx, Bc * dy), dx, fmaf(C * dy, dy, lo)));
+        const float dy = fminf(fmaxf(q0.z * dx, dy0), dy1);
+        best = fmaxf(best, fmaf(fmaf(A, dx, Bc * dy), dx, C * dy * dy));
         // horizontal edges: dy fixed, dx free in [dx0, dx1]
         const float dy2 = e ? dy1 : dy0;
-        const float dx2 = fminf(fmaxf(-Bc * dy2 * ia, dx0), dx1);
-        best = fmaxf(best, fmaf(fmaf(A, dx2, Bc * dy2), dx2, fmaf(C * dy2, dy2, lo)));
+        const float dx2 = fminf(fmaxf(q0.w * dy2, dx0), dx1);
+        best = fmaxf(best, fmaf(fmaf(A, dx2, Bc * dy2), dx2, C * dy2 * dy2));
     }
-    return best >= thr;
+    return best >= t;
 }
 
 // Pixel index p of the tile in block order: four 8x8 blocks (row-major), each row-major, so that
@@ -254,7 +267,7 @@ __device__ void drain_sums(const CompositeArgs &a, Smem &sm, int b, int n, int n
     for (int i0 = 0; i0 < n; i0 += 32) {
         const int i = i0 + lane;
         const bool valid = i < n;
-        const uint32_t g = valid ? sm.gid[b][i] : 0u;
+        const uint32_t g = valid ? sm.q2[b][i].y : 0u;
         for (int s2 = 0; s2 < ns_smem; ++s2) {
             float v = 0.f;
             if (valid) {
@@ -352,9 +365,9 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
             const uint32_t bal = __ballot_sync(0xffffffffu, hit[k]);
             const int pos = nb + __popc(bal & lt);
             if (hit[k]) {
-                cp_async16(&sm.rec_a[b][pos], a.rec_a + g[k]);
-                cp_async16(&sm.rec_b[b][pos], a.rec_b + g[k]);
-                sm.gid[b][pos] = g[k];
+                cp_async16(&sm.q0[b][pos], a.rec_a + g[k]);
+                cp_async16(&sm.q1[b][pos], a.rec_b + g[k]);
+                sm.q2[b][pos].y = g[k];
                 if (trace) {
                     const int64_t at = a.dbg_off[tile] + staged + pos;
                     if (at < a.dbg_off[tile + 1]) a.dbg_list[at] = r[k];
@@ -375,23 +388,24 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
         }
         // records -> tile-local exponent polynomials. With X = px + 0.5 - ox, mx = mu'x - ox (and
         // Y, my likewise), the exponent q2 + log2 o = a' dx^2 + b' dx dy + c' dy^2 + log2 o with
-        // dx = mx - X, dy = my - Y is K0 + K1 X + K2 Y + K3 X^2 + K4 X Y + K5 Y^2. Each consumer
-        // warp culls against its own pixel box; the record keeps what that test needs.
+        // dx = mx - X, dy = my - Y is K0 + K1 X + K2 Y + A X^2 + Bc X Y + C Y^2 (poly_coeffs). Each
+        // consumer warp culls against its own pixel box and expands the survivors' coefficients; the
+        // record keeps what both need.
         for (int i = lane; i < nb; i += 32) {
-            const float4 ra = sm.rec_a[b][i], rb = sm.rec_b[b][i];
+            const float4 ra = sm.q0[b][i], rb = sm.q1[b][i];
             const float mx = ra.x - ox, my = ra.y - oy;
             const float A = ra.z, Bc = ra.w, C = rb.x, lo = rb.y;
-            const float K1 = -fmaf(2.f * A, mx, Bc * my);
-            const float K2 = -fmaf(Bc, mx, 2.f * C * my);
-            const float K0 = fmaf(fmaf(A, mx, Bc * my), mx, fmaf(C * my, my, lo));
-            // a Gaussian is kept for a warp when its alpha-floor box meets the warp's box and its
-            // exponent reaches the floor on that box, less a margin that bounds the rounding of the
-            // per-pixel polynomial (terms at most S in size; X, Y < 16)
+            float K0, K1, K2;
+            poly_coeffs(mx, my, A, Bc, C, lo, K0, K1, K2);
+            // a Gaussian is kept for a warp when its exponent reaches the floor on the warp's box,
+            // less a margin that bounds the rounding of the per-pixel polynomial (terms at most S in
+            // size; X, Y < 16)
             const float S = fabsf(K0) + 16.f * (fabsf(K1) + fabsf(K2)) + 256.f * (fabsf(A) + fabsf(Bc) + fabsf(C));
             const float thr = kLog2AlphaMin - fmaf(4e-6f, S, 0.01f);
-            sm.rec_c[b][i] = make_float4(mx, my, rb.z, rb.w);
-            sm.rec_a[b][i] = make_float4(K0, K1, K2, A);
-            sm.rec_b[b][i] = make_float4(Bc, C, thr, lo);
+            const float r1 = -Bc * __frcp_rn(2.f * C), r2 = -Bc * __frcp_rn(2.f * A);
+            sm.q0[b][i] = make_float4(mx, my, r1, r2);
+            sm.q1[b][i] = make_float4(A, Bc, C, lo > -INFINITY ? thr - lo : INFINITY);
+            sm.q2[b][i].x = __float_as_uint(lo);
         }
         if (lane == 0) sm.count[b] = nb;
         if (b) prev1 = nb;
@@ -546,9 +560,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
     // Gaussian is a quadratic polynomial in them (see the producer's record conversion)
     const float X0 = (float)pix_x(pix0) + 0.5f, Y0 = (float)pix_y(pix0) + 0.5f;
     const float X1 = (float)pix_x(pix1) + 0.5f, Y1 = (float)pix_y(pix1) + 0.5f;
-    // the two pixels' monomials as packed pairs (pixel 0, pixel 1)
-    const uint64_t PX = pk(X0, X1), PY = pk(Y0, Y1);
-    const uint64_t PXX = pk(X0 * X0, X1 * X1), PXY = pk(X0 * Y0, X1 * Y1), PYY = pk(Y0 * Y0, Y1 * Y1);
+    // each pixel's monomials in both halves of a packed pair: one packed product evaluates two
+    // Gaussians (whose coefficients are staged interleaved) at one pixel
+    const uint64_t X0d = pk(X0, X0), Y0d = pk(Y0, Y0), XX0d = pk(X0 * X0, X0 * X0), XY0d = pk(X0 * Y0, X0 * Y0),
+                   YY0d = pk(Y0 * Y0, Y0 * Y0);
+    const uint64_t X1d = pk(X1, X1), Y1d = pk(Y1, Y1), XX1d = pk(X1 * X1, X1 * X1), XY1d = pk(X1 * Y1, X1 * Y1),
+                   YY1d = pk(Y1 * Y1, Y1 * Y1);
     // bounding box of this warp's pixel centres (culling of Gaussians per warp), tile-local
     float wx0 = fminf(inside0 ? X0 : INFINITY, inside1 ? X1 : INFINITY);
     float wx1 = fmaxf(inside0 ? X0 : -INFINITY, inside1 ? X1 : -INFINITY);
@@ -561,128 +578,132 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
         wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
     }
     const float4 wbox = make_float4(wx0, wx1, wy0, wy1);   // every lane holds the warp's box
-    // T = 0 marks a pixel that has stopped (or lies outside the image): its weights are then 0
-    // and every later Gaussian takes it below 1e-4 again, so no flag is needed
-    float T0 = inside0 ? 1.f : 0.f, T1 = inside1 ? 1.f : 0.f;
+    // T (both pixels, packed) = 0 marks a pixel that has stopped (or lies outside the image): its
+    // weights are then 0 and every later Gaussian takes it below 1e-4 again, so no flag is needed
+    uint64_t PT = pk(inside0 ? 1.f : 0.f, inside1 ? 1.f : 0.f);
     {
-        const bool any = __any_sync(0xffffffffu, T0 > 0.f || T1 > 0.f);
+        const bool any = __any_sync(0xffffffffu, inside0 || inside1);
         if (lane == 0) sm.warp_live[w] = any ? 1 : 0;
     }
     cbar();   // slots and group slots are complete
     tc::arrive(&sm.ready);
     const int gs = sm.group_slot[w];
+    // the stored weight of a lane is its first pixel's, plus its second's when they share a slot
+    const float s1 = pair_same ? 1.f : 0.f;
 
     float wsum0 = 0.f, wsum1 = 0.f, Tf0 = 0.f, Tf1 = 0.f;   // diagnostics: weight sum, T at the stop
-    int count0 = 0, count1 = 0;
-    // examined pairs: a stopped pixel examined the list up to its stopping Gaussian (position
-    // evp in the tile's candidate order); the others examined every candidate the warp went
-    // through (seen)
+    uint64_t CNT = pk(0.f, 0.f);   // contributions of both pixels (exact: counts below 2^24)
+    // examined pairs: a stopped pixel examined the list up to the end of the chunk (32 candidates
+    // of the tile's list) in which it stopped (position evp in the tile's candidate order); the
+    // others examined every candidate the warp went through (seen)
     int evp0 = 0, evp1 = 0, seen = 0;
     unsigned long long executed = 0;   // Gaussians this warp evaluated for all 64 of its pixels
     float *wb_warp = sm.wbuf[w];
     int32_t *cl = sm.clist[w];
+    float4 *stg = sm.stage[w];
 
     for (int it = 0;; ++it) {
         const int b = it & 1;
         if (!wait_phase(a, sm, &sm.full[b], (uint32_t)(it >> 1) & 1u)) break;
         const int nb = sm.count[b];
         if (nb < 0) break;
-        const float4 *rec_a = sm.rec_a[b];
-        const float4 *rec_b = sm.rec_b[b];
-        const float4 *rec_c = sm.rec_c[b];
+        const float4 *q0 = sm.q0[b];
+        const float4 *q1 = sm.q1[b];
+        const uint2 *q2 = sm.q2[b];
         for (int c = 0; c * 32 < nb; ++c) {
-            if (!__any_sync(0xffffffffu, T0 > 0.f || T1 > 0.f)) break;
+            const float2 T = unpk(PT);
+            const bool alive0 = T.x > 0.f, alive1 = T.y > 0.f;
+            if (!__any_sync(0xffffffffu, alive0 || alive1)) break;
             const int nvalid = min(32, nb - c * 32);
             // which of the chunk's Gaussians can reach alpha >= 1/255 inside this warp's pixels: lane
             // j tests Gaussian c*32 + j against the warp's box
             bool hitw = false;
+            float4 qa, qb;
             if (lane < nvalid) {
-                const float4 rq = rec_c[c * 32 + lane];
-                if (rq.x - rq.z <= wbox.y && rq.x + rq.z >= wbox.x && rq.y - rq.w <= wbox.w && rq.y + rq.w >= wbox.z) {
-                    const float4 rb = rec_b[c * 32 + lane];
-                    hitw = reaches(rq.x, rq.y, rec_a[c * 32 + lane].w, rb.x, rb.y, rb.w, wbox, rb.z);
-                }
+                qa = q0[c * 32 + lane];
+                qb = q1[c * 32 + lane];
+                hitw = reaches(qa, qb, wbox);
             }
             const uint32_t mask = __ballot_sync(0xffffffffu, hitw);
-            const int base = seen + c * 32;
             if (mask == 0) continue;
-            // A: composite the surviving Gaussians for this thread's two pixels, two Gaussians at a
-            // time: the four exponents and exp2 of a group are independent; only each pixel's
-            // transmittance updates run in order. The survivors' chunk positions in order, then -1.
             const int n = __popc(mask);
             executed += (unsigned long long)n;
-            if (hitw) cl[__popc(mask & lt)] = lane;
-            if (lane == 0) cl[n] = -1;
-            __syncwarp();
-            for (int i = 0; i < n; i += 2) {
-                const int2 jp = *reinterpret_cast<const int2 *>(cl + i);
-                const int jj[2] = {jp.x, jp.y};
-                // nal = -alpha of each pixel (0 below the alpha floor)
-                float nal0[2], nal1[2], kq0[2], kq1[2];
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    nal0[k] = nal1[k] = 0.f;
-                    kq0[k] = kq1[k] = 0.f;
-                    if (jj[k] >= 0) {
-                        const float4 ra = rec_a[c * 32 + jj[k]];
-                        const float4 rb = rec_b[c * 32 + jj[k]];
-                        // e = q2 + log2 opacity of both pixels at once; q2 <= 0 holds exactly
-                        // (positive definite conic)
-                        const float2 e = unpk(fma2(pk(rb.y, rb.y), PYY, fma2(pk(rb.x, rb.x), PXY,
-                                              fma2(pk(ra.w, ra.w), PXX, fma2(pk(ra.z, ra.z), PY,
-                                              fma2(pk(ra.y, ra.y), PX, pk(ra.x, ra.x)))))));
-                        if (e.x >= kLog2AlphaMin) {
-                            nal0[k] = fmaxf(-0.99f, -fast_exp2(e.x));
-                            kq0[k] = e.x - rb.w;
-                        }
-                        if (e.y >= kLog2AlphaMin) {
-                            nal1[k] = fmaxf(-0.99f, -fast_exp2(e.y));
-                            kq1[k] = e.y - rb.w;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (jj[k] < 0) break;
-                    // branch-free: the Gaussian whose (1 - alpha) would take T below 1e-4 stops the
-                    // pixel (T = 0) and contributes nothing; alpha = 0 leaves T as it is. Weights
-                    // are kept negated (nw = -w), as the packed products give them.
-                    const int pos = base + jj[k] + 1;
-                    const uint64_t PT = pk(T0, T1), PA = pk(nal0[k], nal1[k]);
-                    const float2 Tn = unpk(fma2(PA, PT, PT));   // T - alpha T
-                    const float2 aw = unpk(mul2(PA, PT));       // -alpha T
-                    const bool stop0 = Tn.x < 1e-4f, stop1 = Tn.y < 1e-4f;
-                    evp0 = T0 > 0.f ? pos : evp0;
-                    evp1 = T1 > 0.f ? pos : evp1;
-                    if (kDebug) {
-                        Tf0 = (stop0 && T0 > 0.f) ? T0 : Tf0;
-                        Tf1 = (stop1 && T1 > 0.f) ? T1 : Tf1;
-                    }
-                    float nw0, nw1;
-                    if (kKernel) {
-                        nw0 = (stop0 || !(nal0[k] < 0.f)) ? 0.f : -fast_exp2(kq0[k]);
-                        nw1 = (stop1 || !(nal1[k] < 0.f)) ? 0.f : -fast_exp2(kq1[k]);
-                    } else {
-                        nw0 = stop0 ? 0.f : aw.x;
-                        nw1 = stop1 ? 0.f : aw.y;
-                    }
-                    T0 = stop0 ? 0.f : Tn.x;
-                    T1 = stop1 ? 0.f : Tn.y;
-                    count0 += nw0 < 0.f ? 1 : 0;
-                    count1 += nw1 < 0.f ? 1 : 0;
-                    if (kDebug) {
-                        wsum0 -= nw0;
-                        wsum1 -= nw1;
-                    }
-                    wb_warp[jj[k] * kWStride + lane] = pair_same ? nw0 + nw1 : nw0;
-                    if (split1 && nw1 != 0.f) flush_slot(a, sm, b, slot1, c * 32 + jj[k], -nw1);
-                }
+            // the survivors in chunk order: survivor r's coefficients go to half (r & 1) of staged
+            // pair r / 2; an odd count is padded with a Gaussian that reaches no pixel (e = -inf)
+            if (hitw) {
+                const int r = __popc(mask & lt);
+                float K0, K1, K2;
+                poly_coeffs(qa.x, qa.y, qb.x, qb.y, qb.z, __uint_as_float(q2[c * 32 + lane].x), K0, K1, K2);
+                float *sp = reinterpret_cast<float *>(stg + (r >> 1) * 3) + (r & 1);
+                sp[0] = K0;
+                sp[2] = K1;
+                sp[4] = K2;
+                sp[6] = qb.x;
+                sp[8] = qb.y;
+                sp[10] = qb.z;
+                cl[r] = lane;
+            }
+            if (lane == 0 && (n & 1)) {
+                float *sp = reinterpret_cast<float *>(stg + (n >> 1) * 3) + 1;
+                sp[0] = -INFINITY;
+                sp[2] = sp[4] = sp[6] = sp[8] = sp[10] = 0.f;
+                cl[n] = 0;   // a valid chunk position: the kernel weight reads the pad's record
             }
             __syncwarp();
-            // B: lane = Gaussian c*32+lane, sum over this warp's 32 lanes per slot
-            if (a.accumulate && gs != -1 && ((mask >> lane) & 1u)) {
+            // A: composite the survivors for this thread's two pixels, two Gaussians at a time: the
+            // packed exponents of a pair at each pixel and the four exp2 are independent; only each
+            // pixel's transmittance updates run in order. Floor and stop decisions are 0/1 factors.
+            for (int i = 0; i < n; i += 2) {
+                const ulonglong2 *cp = reinterpret_cast<const ulonglong2 *>(stg + (i >> 1) * 3);
+                const ulonglong2 c0 = cp[0], c1 = cp[1], c2 = cp[2];   // (K0, K1), (K2, A), (Bc, C) pairs
+                const float2 E0 = unpk(fma2(c2.y, YY0d, fma2(c2.x, XY0d, fma2(c1.y, XX0d, fma2(c1.x, Y0d,
+                                       fma2(c0.y, X0d, c0.x))))));
+                const float2 E1 = unpk(fma2(c2.y, YY1d, fma2(c2.x, XY1d, fma2(c1.y, XX1d, fma2(c1.x, Y1d,
+                                       fma2(c0.y, X1d, c0.x))))));
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    // e = q2 + log2 opacity of Gaussian i + k at both pixels; q2 <= 0 holds exactly
+                    // (positive definite conic)
+                    const float e0 = k ? E0.y : E0.x, e1 = k ? E1.y : E1.x;
+                    // FL: alpha >= 1/255; NAL = -alpha (0 below the floor)
+                    const uint64_t FL = pk(set_ge(e0, kLog2AlphaMin), set_ge(e1, kLog2AlphaMin));
+                    const uint64_t NAL = mul2(pk(fmaxf(-0.99f, -fast_exp2(e0)), fmaxf(-0.99f, -fast_exp2(e1))), FL);
+                    // the Gaussian whose (1 - alpha) would take T below 1e-4 stops the pixel (T = 0)
+                    // and contributes nothing: M = 0; alpha = 0 leaves T as it is. Weights are kept
+                    // negated (nw = -w), as the packed products give them.
+                    const uint64_t Tn = fma2(NAL, PT, PT);   // T - alpha T
+                    const float2 tn = unpk(Tn);
+                    const uint64_t M = pk(set_ge(tn.x, 1e-4f), set_ge(tn.y, 1e-4f));
+                    float2 nw;
+                    if (kKernel) {
+                        const float lo = __uint_as_float(q2[c * 32 + cl[i + k]].x);
+                        nw = unpk(mul2(mul2(pk(-fast_exp2(e0 - lo), -fast_exp2(e1 - lo)), FL), M));
+                    } else {
+                        nw = unpk(mul2(mul2(NAL, PT), M));   // -alpha T, or 0 at the stop
+                    }
+                    if (kDebug) {
+                        const float2 Tb = unpk(PT);
+                        Tf0 = (tn.x < 1e-4f && Tb.x > 0.f) ? Tb.x : Tf0;
+                        Tf1 = (tn.y < 1e-4f && Tb.y > 0.f) ? Tb.y : Tf1;
+                        wsum0 -= nw.x;
+                        wsum1 -= nw.y;
+                    }
+                    PT = mul2(Tn, M);
+                    CNT = fma2(FL, M, CNT);
+                    wb_warp[(i + k) * kWStride + lane] = fmaf(nw.y, s1, nw.x);
+                    if (split1 && nw.y != 0.f) flush_slot(a, sm, b, slot1, c * 32 + cl[i + k], -nw.y);
+                }
+            }
+            {
+                const float2 Ta = unpk(PT);
+                evp0 = (alive0 && !(Ta.x > 0.f)) ? seen + c * 32 + nvalid : evp0;
+                evp1 = (alive1 && !(Ta.y > 0.f)) ? seen + c * 32 + nvalid : evp1;
+            }
+            __syncwarp();
+            // B: lane r = survivor r, sum over this warp's 32 lanes per slot
+            if (a.accumulate && gs != -1 && lane < n) {
                 const float *row = wb_warp + lane * kWStride;
-                const int gi = c * 32 + lane;
+                const int gi = c * 32 + cl[lane];
                 if (gs >= 0) {
                     // four running sums (lanes q mod 4), two per packed add
                     const float4 *row4 = reinterpret_cast<const float4 *>(row);
@@ -715,13 +736,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
         }
         seen += nb;
         {
-            const bool any = __any_sync(0xffffffffu, T0 > 0.f || T1 > 0.f);
+            const float2 T = unpk(PT);
+            const bool any = __any_sync(0xffffffffu, T.x > 0.f || T.y > 0.f);
             if (lane == 0) sm.warp_live[w] = any ? 1 : 0;
         }
         __syncwarp();
         tc::arrive(&sm.empty[b]);   // every lane: each releases its own reads and sums
     }
 
+    const float2 Tfin = unpk(PT);
+    const float T0 = Tfin.x, T1 = Tfin.y;
+    const float2 cntf = unpk(CNT);
+    const int count0 = (int)cntf.x, count1 = (int)cntf.y;
     if (inside0) {
         const int64_t pi = (int64_t)py0 * W + px0;
         if (a.dbg_T) a.dbg_T[pi] = T0 > 0.f ? T0 : Tf0;
