@@ -33,12 +33,15 @@ __global__ void hash_init_k(HashEntry *h, int64_t n) {
 // Grid-stride over the view's records; many records per SM in flight hide the
 // latency of the table probes.
 __global__ void __launch_bounds__(256) combine_k(const WeightRecord *__restrict__ recs,
-                                                 const unsigned long long *__restrict__ rec_count,
-                                                 unsigned long long rec_cap, const HashSink sink) {
-    unsigned long long nr = *rec_count;
-    if (nr > rec_cap) nr = rec_cap;
+                                                 const unsigned long long *__restrict__ rec_chunks,
+                                                 const uint32_t *__restrict__ rec_fill,
+                                                 unsigned long long chunk_cap, const HashSink sink) {
+    unsigned long long nc = *rec_chunks;
+    if (nc > chunk_cap) nc = chunk_cap;
+    const unsigned long long nr = nc * kRecChunk;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < nr;
          i += (unsigned long long)gridDim.x * blockDim.x) {
+        if ((uint32_t)(i % kRecChunk) >= rec_fill[i / kRecChunk]) continue;
         const WeightRecord r = recs[i];
         sink_add(sink, r.g, r.seg, r.w);
     }
@@ -62,18 +65,27 @@ __global__ void __launch_bounds__(256) consume_k(HashEntry *__restrict__ hash, i
 #pragma unroll
         for (int s = 0; s < kHashSlots; ++s) cnt += e.seg[s] >= 0 ? 1 : 0;
     }
-    // warp-aggregated reservation in the log
+    // block-aggregated reservation in the log (one atomic per block on the shared counter)
+    __shared__ int wtot_s[8];
+    __shared__ unsigned long long base_s;
+    const int w = threadIdx.x >> 5;
     int incl = cnt;
     for (int o = 1; o < 32; o <<= 1) {
         int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
-    const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long base = 0;
-    if (lane == 31 && wtot) base = atomicAdd(log_count, (unsigned long long)wtot);
-    base = __shfl_sync(0xffffffffu, base, 31);
+    if (lane == 31) wtot_s[w] = incl;
+    __syncthreads();
+    int before = 0, btot = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        before += q < w ? wtot_s[q] : 0;
+        btot += wtot_s[q];
+    }
+    if (threadIdx.x == 0) base_s = btot ? atomicAdd(log_count, (unsigned long long)btot) : 0ull;
+    __syncthreads();
     if (g >= n || cnt == 0) return;
-    unsigned long long at = base + (unsigned long long)(incl - cnt);
+    unsigned long long at = base_s + (unsigned long long)(before + incl - cnt);
     float sh = s_hi[g], sl = s_lo[g];
     bool overflow = false;
     HashEntry clear;
@@ -235,16 +247,17 @@ void launch_copy_words(const void *src, void *dst, int64_t bytes, cudaStream_t s
                                                    n); note_launch();
 }
 
-void launch_combine(const WeightRecord *recs, const unsigned long long *rec_count, unsigned long long rec_cap,
-                    const HashSink &sink, cudaStream_t st) {
-    if (rec_cap == 0) return;
+void launch_combine(const WeightRecord *recs, const unsigned long long *rec_chunks, const uint32_t *rec_fill,
+                    unsigned long long chunk_cap, const HashSink &sink, cudaStream_t st) {
+    if (chunk_cap == 0) return;
+    const unsigned long long rec_cap = chunk_cap * kRecChunk;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     unsigned blocks = (unsigned)sms * 8u;
     const unsigned long long need = (rec_cap + 255) / 256;
     if (need < blocks) blocks = (unsigned)need;
-    combine_k<<<blocks, 256, 0, st>>>(recs, rec_count, rec_cap, sink); note_launch();
+    combine_k<<<blocks, 256, 0, st>>>(recs, rec_chunks, rec_fill, chunk_cap, sink); note_launch();
 }
 
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,

@@ -15,11 +15,11 @@
 // per thread) and one producer warp feeds them. The tile's Gaussians are those
 // of its bin's list (a 4x4-tile super-tile) whose tile rectangle holds the
 // tile, taken in list order.
-//   * Producer: fills one of two record buffers at a time with the hits among
-//     the next 160 candidates of the bin's list (the following 160 are loaded
-//     meanwhile; each hit's record is copied asynchronously from the view's
-//     records through the rank -> Gaussian map), turns each record into a tile-local exponent
-//     polynomial (keeping what the consumers' culling tests need), and publishes the
+//   * Producer: fills one of kNB record buffers at a time (a ring) with the hits among
+//     the next 128 candidates of the bin's list (the following 128 are loaded
+//     meanwhile; the list holds Gaussian indices, and each hit's record is
+//     copied asynchronously from the view's records), turns each record into a
+//     tile-local exponent polynomial (keeping what the consumers' culling tests need), and publishes the
 //     buffer on an mbarrier; it refills a buffer once all consumers have
 //     released it, first moving that buffer's per-(segment, Gaussian) sums to
 //     the view's record list. It stops when the list ends or no consumer
@@ -56,20 +56,20 @@ constexpr int kPixThreads = 32 * kConsumers;          // two pixels per consumer
 constexpr int kThreads = kPixThreads + 32;            // + the producer warp
 constexpr int kProducer = kConsumers;                 // warp index of the producer
 constexpr int kCtasPerSm = 5;                         // resident CTAs per SM (shared memory)
-constexpr int kPerLane = 5;                           // candidates per producer lane and batch
+constexpr int kPerLane = 4;                           // candidates per producer lane and batch
 constexpr int kBuf = 32 * kPerLane;                   // candidates per batch = record capacity of a buffer
+constexpr int kNB = 2;                                // record buffers (a ring)
 constexpr int kSmemSlots = 4;
-constexpr int kQ = 104;                               // the producer's queued (Gaussian, slot) sums
-constexpr int kQFlush = 64;                           // queue level that triggers a flush after a buffer
+static_assert(kBuf < kRecChunk, "one slot's sums of a buffer must fit in two record chunks");
 constexpr int kWStride = 36;                          // transposition rows: 16-byte aligned, conflict-free
 constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2(1/255)
 constexpr uint32_t kBarConsumers = 1;                 // named barrier of the consumer warps
 
 struct Smem {
-    float4 q0[2][kBuf];                   // staged (mu'x, mu'y, a', b'); then (mx, my, r1, r2)
-    float4 q1[2][kBuf];                   // staged (c', log2 opacity, ex, ey); then (A, Bc, C, t)
-    uint2 q2[2][kBuf];                    // (log2 opacity bits, internal Gaussian index)
-    float wb[2][kSmemSlots][kBuf];        // per (buffer, slot, Gaussian of the buffer)
+    float4 q0[kNB][kBuf];                 // staged (mu'x, mu'y, a', b'); then (mx, my, r1, r2)
+    float4 q1[kNB][kBuf];                 // staged (c', log2 opacity, ex, ey); then (A, Bc, C, t)
+    uint2 q2[kNB][kBuf];                  // (log2 opacity bits, internal Gaussian index)
+    float wb[kNB][kSmemSlots][kBuf];      // per (buffer, slot, Gaussian of the buffer)
     union {
         float wbuf[kConsumers][32 * kWStride];   // per warp: (survivor of the chunk) x lane
         uint32_t keys[kPix];                     // the prologue's segment sort
@@ -78,19 +78,17 @@ struct Smem {
     int32_t clist[kConsumers][32];        // per warp: chunk position of each survivor
     uint32_t split_min[2][kConsumers];    // prologue multi-split: per-warp minimum segment
     int32_t split_cnt[2][kConsumers];     // and per-warp counts (first | second pixel << 16)
-    int32_t slot_lane[kPixThreads];       // slot of the sums each lane stores (its first pixel's)
+    int16_t slot_lane[kPixThreads];       // slot of the sums each lane stores (its first pixel's)
     int32_t seg_of_slot[kPix];
     int32_t group_slot[kConsumers];       // slot shared by all of a warp's pixels, -2 = mixed
     int32_t warp_tot[kConsumers];
     int32_t scalar[4];                    // [0] first pixel's segment, [1] slots in shared memory
-    int32_t count[2];                     // records in each buffer (-1: no more)
+    int32_t count[kNB];                   // records in each buffer (-1: no more)
     int32_t warp_live[kConsumers];        // a consumer warp still has a live pixel
     uint32_t abort_flag;                  // a wait gave up: every other wait gives up too
-    uint32_t qg[kQ];                      // the producer's queued sums: Gaussian, weight, slot
-    float qw[kQ];
-    uint8_t qs[kQ];
-    __align__(8) uint64_t full[2];        // a buffer is published (32 producer arrivals)
-    __align__(8) uint64_t empty[2];       // a buffer is released (128 consumer arrivals)
+    unsigned long long totals[kConsumers][3];   // per consumer warp: contributions, visited, executed
+    __align__(8) uint64_t full[kNB];      // a buffer is published (32 producer arrivals)
+    __align__(8) uint64_t empty[kNB];     // a buffer is released (128 consumer arrivals)
     __align__(8) uint64_t ready;          // the consumers' prologue is done (128 arrivals)
 };
 // kCtasPerSm CTAs per SM (228 KB of shared memory, 1 KB of it reserved per CTA)
@@ -188,28 +186,35 @@ __device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int
     else sink_add(sink_of(a), sm.q2[b][gi].y, sm.seg_of_slot[slot], acc);
 }
 
-// Moves the producer's n queued records to the view's record list with one reservation.
-__device__ void flush_queue(const CompositeArgs &a, Smem &sm, int lane, int n) {
-    __syncwarp();
-    unsigned long long base = 0ull;
-    if (lane == 0) base = atomicAdd(a.rec_count, (unsigned long long)n);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (int k = lane; k < n; k += 32) {
-        const uint32_t g = sm.qg[k];
-        const int32_t seg = sm.seg_of_slot[sm.qs[k]];
-        const float wt = sm.qw[k];
-        if (base + (unsigned long long)k < a.rec_cap) {
-            WeightRecord r;
-            r.g = g;
-            r.seg = seg;
-            r.w = wt;
-            r.pad = 0u;
-            a.recs[base + k] = r;
-        } else {
-            sink_add(sink_of(a), g, seg, wt);
-        }
+// The producer's place in the view's record list: chunk `cur` is being filled (`used` records),
+// chunk `next` follows it. A chunk index comes from an atomicAdd issued one chunk ahead (lane 0
+// holds the result in `pend` until it is needed), so that no store waits for the reservation.
+struct RecRes {
+    unsigned long long cur, next, pend;   // pend: lane 0 only
+    int used;
+    bool requested, have_cur, have_next;
+};
+
+__device__ __forceinline__ void res_request(const CompositeArgs &a, RecRes &rr, int lane, unsigned long long k) {
+    if (lane == 0) rr.pend = atomicAdd(a.rec_chunks, k);
+}
+
+__device__ __forceinline__ void res_fill(const CompositeArgs &a, unsigned long long chunk, int lane, uint32_t fill) {
+    if (lane == 0 && chunk < a.chunk_cap) a.rec_fill[chunk] = fill;
+}
+
+// The producer's last act: the fills of its current and reserved chunks.
+__device__ void res_close(const CompositeArgs &a, RecRes &rr, int lane) {
+    if (!rr.requested) return;
+    if (!rr.have_cur) {   // reserved, never written
+        const unsigned long long c = __shfl_sync(0xffffffffu, rr.pend, 0);
+        res_fill(a, c, lane, 0u);
+        res_fill(a, c + 1ull, lane, 0u);
+        return;
     }
-    __syncwarp();
+    res_fill(a, rr.cur, lane, (uint32_t)rr.used);
+    const unsigned long long nx = rr.have_next ? rr.next : __shfl_sync(0xffffffffu, rr.pend, 0);
+    res_fill(a, nx, lane, 0u);
 }
 
 // Whether the exponent e(X, Y) = lo + A dx^2 + Bc dx dy + C dy^2 (dx = mx - X, dy = my - Y; A, C < 0
@@ -239,6 +244,22 @@ __device__ __forceinline__ bool reaches(float4 q0, float4 q1, float4 box) {
     return best >= t;
 }
 
+// The box (x0, x1, y0, y1) of the pixel centres (X0, Y0) and (X1, Y1) of the warp's lanes for
+// which l0 and l1 hold (x0 = +inf when there are none), in every lane.
+__device__ __forceinline__ float4 live_box(bool l0, bool l1, float X0, float Y0, float X1, float Y1) {
+    float x0 = fminf(l0 ? X0 : INFINITY, l1 ? X1 : INFINITY);
+    float x1 = fmaxf(l0 ? X0 : -INFINITY, l1 ? X1 : -INFINITY);
+    float y0 = fminf(l0 ? Y0 : INFINITY, l1 ? Y1 : INFINITY);
+    float y1 = fmaxf(l0 ? Y0 : -INFINITY, l1 ? Y1 : -INFINITY);
+    for (int o = 16; o; o >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    return make_float4(x0, x1, y0, y1);
+}
+
 // Pixel index p of the tile in block order: four 8x8 blocks (row-major), each row-major, so that
 // a warp's 64 pixels of one segment form an 8x8 block.
 __device__ __forceinline__ int pix_x(int p) { return ((p >> 3) & 8) | (p & 7); }
@@ -260,42 +281,76 @@ __device__ __forceinline__ bool wait_phase(const CompositeArgs &a, Smem &sm, uin
 
 // ---- the producer warp ---------------------------------------------------------------------
 
-// Moves buffer b's non-zero (slot, Gaussian) sums of its n records to the queue (and, when the
-// queue fills, to the view's record list), clearing the table for the buffer's next use.
-__device__ void drain_sums(const CompositeArgs &a, Smem &sm, int b, int n, int ns_smem, int lane, uint32_t lt,
-                           int &qn) {
-    for (int i0 = 0; i0 < n; i0 += 32) {
-        const int i = i0 + lane;
-        const bool valid = i < n;
-        const uint32_t g = valid ? sm.q2[b][i].y : 0u;
-        for (int s2 = 0; s2 < ns_smem; ++s2) {
-            float v = 0.f;
-            if (valid) {
-                v = sm.wb[b][s2][i];
+// Moves buffer b's non-zero (slot, Gaussian) sums of its n records (n <= kBuf) to the view's
+// record list, clearing the table for the buffer's next use. Per slot, lane l takes records
+// l, l + 32, ...; a warp scan of the lanes' counts places them, so the records of one slot
+// (at most kBuf < kRecChunk) always fit in chunks cur and next.
+__device__ void drain_sums(const CompositeArgs &a, Smem &sm, int b, int n, int ns_smem, int lane, RecRes &rr) {
+    for (int s2 = 0; s2 < ns_smem; ++s2) {
+        float v[kPerLane];
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+            const int i = lane + 32 * j;
+            v[j] = 0.f;
+            if (i < n) {
+                v[j] = sm.wb[b][s2][i];
                 sm.wb[b][s2][i] = 0.f;
             }
-            const uint32_t bal = __ballot_sync(0xffffffffu, v != 0.f);
-            if (bal == 0u) continue;
-            if (!a.recs) {   // no record list: the sums go to the tables directly
-                if (v != 0.f) sink_add(sink_of(a), g, sm.seg_of_slot[s2], v);
-                continue;
-            }
-            if (qn + 32 > kQ) {
-                flush_queue(a, sm, lane, qn);
-                qn = 0;
-            }
-            if (v != 0.f) {
-                const int k = qn + __popc(bal & lt);
-                sm.qg[k] = g;
-                sm.qw[k] = v;
-                sm.qs[k] = (uint8_t)s2;
-            }
-            qn += __popc(bal);
+            cnt += v[j] != 0.f ? 1 : 0;
         }
-    }
-    if (qn >= kQFlush) {
-        flush_queue(a, sm, lane, qn);
-        qn = 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot == 0) continue;
+        const int32_t seg = sm.seg_of_slot[s2];
+        if (!a.recs) {   // no record list: the sums go to the tables directly
+#pragma unroll
+            for (int j = 0; j < kPerLane; ++j)
+                if (v[j] != 0.f) sink_add(sink_of(a), sm.q2[b][lane + 32 * j].y, seg, v[j]);
+            continue;
+        }
+        if (!rr.have_cur) {   // the first records: the two chunks reserved at the start
+            rr.cur = __shfl_sync(0xffffffffu, rr.pend, 0);
+            rr.next = rr.cur + 1ull;
+            rr.used = 0;
+            rr.have_cur = rr.have_next = true;
+        }
+        if (rr.used + tot >= kRecChunk && !rr.have_next) {   // records go to, or continue in, chunk next
+            rr.next = __shfl_sync(0xffffffffu, rr.pend, 0);
+            rr.have_next = true;
+        }
+        int pos = rr.used + incl - cnt;
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+            if (v[j] == 0.f) continue;
+            const uint32_t g = sm.q2[b][lane + 32 * j].y;
+            const unsigned long long ch = pos < kRecChunk ? rr.cur : rr.next;
+            if (ch < a.chunk_cap) {
+                WeightRecord r;
+                r.g = g;
+                r.seg = seg;
+                r.w = v[j];
+                r.pad = 0u;
+                a.recs[ch * kRecChunk + (pos < kRecChunk ? pos : pos - kRecChunk)] = r;
+            } else {
+                sink_add(sink_of(a), g, seg, v[j]);
+            }
+            ++pos;
+        }
+        rr.used += tot;
+        if (rr.used >= kRecChunk) {
+            // chunk cur is full: continue in next, and reserve the one after it
+            res_fill(a, rr.cur, lane, (uint32_t)kRecChunk);
+            rr.cur = rr.next;
+            rr.used -= kRecChunk;
+            rr.have_next = false;
+            res_request(a, rr, lane, 1ull);
+        }
     }
 }
 
@@ -307,9 +362,15 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
     const int end = (int)rg.y;
     int cursor = (int)rg.x;
     int staged = 0;   // Gaussians staged so far (their positions in the tile's own list)
-    int qn = 0;       // queued sums
+    RecRes rr;        // place in the view's record list
+    rr.cur = rr.next = rr.pend = 0ull;
+    rr.used = 0;
+    rr.requested = rr.have_cur = rr.have_next = false;
+    if (a.accumulate && a.recs) {   // two chunks, reserved while the first batch is staged
+        res_request(a, rr, lane, 2ull);
+        rr.requested = true;
+    }
     int ns_smem = 0;  // slots with a shared-memory table (known after the consumers' prologue)
-    int prev0 = 0, prev1 = 0;   // records of the batch each buffer holds
     // a batch is the next kBuf candidates of the bin's list; the candidates of the batch after the
     // current one are loaded into registers while the current one is staged
     uint32_t r_nx[kPerLane];
@@ -323,28 +384,27 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
     bool ok = true, have_slots = false;
     int it = 0;
     for (;; ++it) {
-        const int b = it & 1;
-        // this batch's candidates and their hits; the next batch's loads are issued now, and the
-        // Gaussian of each hit (the rank -> Gaussian map) is read while the buffer is drained
-        uint32_t r[kPerLane], g[kPerLane];
+        const int b = it % kNB;
+        // this batch's candidates (Gaussian indices) and their hits; the next batch's loads are
+        // issued now
+        uint32_t g[kPerLane];
         bool hit[kPerLane];
 #pragma unroll
         for (int k = 0; k < kPerLane; ++k) {
             const int c = cursor + k * 32 + lane;
-            r[k] = r_nx[k];
+            g[k] = r_nx[k];
             const uint2 rc = rc_nx[k];
             hit[k] = c < end && (uint32_t)tx >= (rc.x & 0xffffu) && (uint32_t)tx < (rc.x >> 16) &&
                      (uint32_t)ty >= (rc.y & 0xffffu) && (uint32_t)ty < (rc.y >> 16) &&
-                     SLAG_IN_BOUNDS(r[k] < a.n_ranks, kCheckComposite);
-            g[k] = hit[k] ? a.sgid[r[k]] : 0u;
+                     SLAG_IN_BOUNDS(g[k] < a.n_ids, kCheckComposite);
             const int cn = c + kBuf;
             r_nx[k] = cn < end ? a.list[cn] : 0u;
             rc_nx[k] = cn < end ? a.prect[cn] : make_uint2(0u, 0u);
         }
-        if (it >= 2) {
-            // the consumers have released this buffer (its previous batch, it - 2): move its sums out
-            if (!wait_phase(a, sm, &sm.empty[b], (uint32_t)((it >> 1) - 1) & 1u)) { ok = false; break; }
-            if (a.accumulate) drain_sums(a, sm, b, b ? prev1 : prev0, ns_smem, lane, lt, qn);
+        if (it >= kNB) {
+            // the consumers have released this buffer (its previous batch, it - kNB): move its sums out
+            if (!wait_phase(a, sm, &sm.empty[b], (uint32_t)(it / kNB - 1) & 1u)) { ok = false; break; }
+            if (a.accumulate) drain_sums(a, sm, b, sm.count[b], ns_smem, lane, rr);
         }
         bool live = trace;
         if (!trace) {
@@ -370,7 +430,7 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
                 sm.q2[b][pos].y = g[k];
                 if (trace) {
                     const int64_t at = a.dbg_off[tile] + staged + pos;
-                    if (at < a.dbg_off[tile + 1]) a.dbg_list[at] = r[k];
+                    if (at < a.dbg_off[tile + 1]) a.dbg_list[at] = g[k];
                     else atomicOr(a.dbg_bad, 1u);
                 }
             }
@@ -408,18 +468,16 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
             sm.q2[b][i].x = __float_as_uint(lo);
         }
         if (lane == 0) sm.count[b] = nb;
-        if (b) prev1 = nb;
-        else prev0 = nb;
         __syncwarp();
         tc::arrive(&sm.full[b]);   // every lane: each publishes its own writes
     }
-    if (ok && it >= 1) {
-        // the last batch (it - 1, in the other buffer): its sums once the consumers release it
-        const int b = (it - 1) & 1;
-        if (wait_phase(a, sm, &sm.empty[b], (uint32_t)((it - 1) >> 1) & 1u) && a.accumulate)
-            drain_sums(a, sm, b, b ? prev1 : prev0, ns_smem, lane, lt, qn);
+    // the batches still held by the consumers (it - kNB + 1 .. it - 1): their sums once released
+    for (int bt = it - kNB + 1 > 0 ? it - kNB + 1 : 0; ok && bt < it; ++bt) {
+        const int b = bt % kNB;
+        ok = wait_phase(a, sm, &sm.empty[b], (uint32_t)(bt / kNB) & 1u);
+        if (ok && a.accumulate) drain_sums(a, sm, b, sm.count[b], ns_smem, lane, rr);
     }
-    if (a.accumulate && a.recs && qn > 0) flush_queue(a, sm, lane, qn);
+    if (a.accumulate && a.recs) res_close(a, rr, lane);
     if (trace && lane == 0) a.dbg_staged[tile] = (uint32_t)staged;
 }
 
@@ -436,16 +494,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
     const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
 
     if (tid == 0) {
-        tc::mbar_init(&sm.full[0], 32);
-        tc::mbar_init(&sm.full[1], 32);
-        tc::mbar_init(&sm.empty[0], kPixThreads);
-        tc::mbar_init(&sm.empty[1], kPixThreads);
+        for (int b = 0; b < kNB; ++b) {
+            tc::mbar_init(&sm.full[b], 32);
+            tc::mbar_init(&sm.empty[b], kPixThreads);
+        }
         tc::mbar_init(&sm.ready, kPixThreads);
         sm.abort_flag = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // the (slot x Gaussian) sums start at zero; each buffer's drain clears what it read
-    for (int i = tid; i < 2 * kSmemSlots * kBuf; i += kThreads) (&sm.wb[0][0][0])[i] = 0.f;
+    for (int i = tid; i < kNB * kSmemSlots * kBuf; i += kThreads) (&sm.wb[0][0][0])[i] = 0.f;
     if (tid < kConsumers) sm.warp_live[tid] = 1;
     __syncthreads();
     if (w == kProducer) {
@@ -541,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
     const int slot1 = seg1 >= 0 ? before + new0 + new1 - 1 : -1;
     if (new0) sm.seg_of_slot[slot0] = seg0;
     if (new1) sm.seg_of_slot[slot1] = seg1;
-    sm.slot_lane[tid] = slot0;   // the slot of the sums this lane stores
+    sm.slot_lane[tid] = (int16_t)slot0;   // the slot of the sums this lane stores (< 256, or -1)
     const bool pair_same = slot0 == slot1;
     // the second pixel of a pair that straddles a segment boundary adds its weights to its own
     // slot directly
@@ -567,17 +625,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
     const uint64_t X1d = pk(X1, X1), Y1d = pk(Y1, Y1), XX1d = pk(X1 * X1, X1 * X1), XY1d = pk(X1 * Y1, X1 * Y1),
                    YY1d = pk(Y1 * Y1, Y1 * Y1);
     // bounding box of this warp's pixel centres (culling of Gaussians per warp), tile-local
-    float wx0 = fminf(inside0 ? X0 : INFINITY, inside1 ? X1 : INFINITY);
-    float wx1 = fmaxf(inside0 ? X0 : -INFINITY, inside1 ? X1 : -INFINITY);
-    float wy0 = fminf(inside0 ? Y0 : INFINITY, inside1 ? Y1 : INFINITY);
-    float wy1 = fmaxf(inside0 ? Y0 : -INFINITY, inside1 ? Y1 : -INFINITY);
-    for (int o = 16; o; o >>= 1) {
-        wx0 = fminf(wx0, __shfl_xor_sync(0xffffffffu, wx0, o));
-        wx1 = fmaxf(wx1, __shfl_xor_sync(0xffffffffu, wx1, o));
-        wy0 = fminf(wy0, __shfl_xor_sync(0xffffffffu, wy0, o));
-        wy1 = fmaxf(wy1, __shfl_xor_sync(0xffffffffu, wy1, o));
-    }
-    const float4 wbox = make_float4(wx0, wx1, wy0, wy1);   // every lane holds the warp's box
+    const float4 wbox = live_box(inside0, inside1, X0, Y0, X1, Y1);   // every lane holds the warp's box
     // T (both pixels, packed) = 0 marks a pixel that has stopped (or lies outside the image): its
     // weights are then 0 and every later Gaussian takes it below 1e-4 again, so no flag is needed
     uint64_t PT = pk(inside0 ? 1.f : 0.f, inside1 ? 1.f : 0.f);
@@ -603,8 +651,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
     float4 *stg = sm.stage[w];
 
     for (int it = 0;; ++it) {
-        const int b = it & 1;
-        if (!wait_phase(a, sm, &sm.full[b], (uint32_t)(it >> 1) & 1u)) break;
+        const int b = it % kNB;
+        if (!wait_phase(a, sm, &sm.full[b], (uint32_t)(it / kNB) & 1u)) break;
         const int nb = sm.count[b];
         if (nb < 0) break;
         const float4 *q0 = sm.q0[b];
@@ -766,9 +814,20 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         ev += __shfl_xor_sync(0xffffffffu, ev, o);
     }
-    if (lane == 0 && cnt) atomicAdd(a.contrib, cnt);
-    if (lane == 0 && ev && a.evals) atomicAdd(a.evals, ev);
-    if (lane == 0 && executed && a.evals_exec) atomicAdd(a.evals_exec, executed * (unsigned long long)(2 * 32));
+    // one atomic per CTA and counter (counters shared by the whole grid)
+    if (lane == 0) {
+        sm.totals[w][0] = cnt;
+        sm.totals[w][1] = ev;
+        sm.totals[w][2] = executed * (unsigned long long)(2 * 32);
+    }
+    cbar();
+    if (tid < 3) {
+        unsigned long long t = 0;
+#pragma unroll
+        for (int q = 0; q < kConsumers; ++q) t += sm.totals[q][tid];
+        unsigned long long *dst = tid == 0 ? a.contrib : (tid == 1 ? a.evals : a.evals_exec);
+        if (t && dst) atomicAdd(dst, t);
+    }
 }
 
 }  // namespace

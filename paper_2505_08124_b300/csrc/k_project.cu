@@ -242,13 +242,21 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
         rec_b[g] = rb;
         rect[g] = rc;
     }
-    uint32_t b = __ballot_sync(0xffffffffu, visible);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&ctr->n_visible, (uint32_t)__popc(b));
+    // one atomic per block (a counter shared by the whole grid)
+    __shared__ uint32_t wcnt[8];
+    const uint32_t b = __ballot_sync(0xffffffffu, visible);
+    if ((threadIdx.x & 31) == 0) wcnt[threadIdx.x >> 5] = (uint32_t)__popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int q = 0; q < 8; ++q) t += wcnt[q];
+        if (t) atomicAdd(&ctr->n_visible, t);
+    }
 }
 
 // r < n_visible: rectangle and bin count of the Gaussian of depth rank r (the records stay in the
 // internal order; the compositing kernel reads them through the rank -> Gaussian map).
-__global__ void gather_sorted_k(const uint32_t *__restrict__ sorted_vals, int64_t n, ViewCounters *ctr,
+__global__ void __launch_bounds__(256) gather_sorted_k(const uint32_t *__restrict__ sorted_vals, int64_t n, ViewCounters *ctr,
                                 const uint2 *__restrict__ rect, uint2 *__restrict__ srect,
                                 uint32_t *__restrict__ stouched, int shift) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -266,9 +274,17 @@ __global__ void gather_sorted_k(const uint32_t *__restrict__ sorted_vals, int64_
             stouched[r] = 0;
         }
     }
+    // one atomic per block (a counter shared by the whole grid)
+    __shared__ unsigned long long wsum[8];
     unsigned long long t = tiles;
     for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if ((threadIdx.x & 31) == 0 && t) atomicAdd(&ctr->P_tiles, t);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long u = 0;
+        for (int q = 0; q < 8; ++q) u += wsum[q];
+        if (u) atomicAdd(&ctr->P_tiles, u);
+    }
 }
 
 __global__ void check_seg_k(const int32_t *__restrict__ seg, int64_t npx, int32_t M, ViewCounters *ctr) {

@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
                                                        const uint32_t *__restrict__ offs,
                                                        const uint32_t *__restrict__ digit_tot, int ntiles,
                                                        uint2 *__restrict__ ranges, int nranges,
-                                                       const uint2 *__restrict__ gsrc, uint2 *__restrict__ gout) {
+                                                       const uint2 *__restrict__ gsrc, uint2 *__restrict__ gout,
+                                                       const uint32_t *__restrict__ vmap) {
     constexpr int kTileN = kThreads * ITEMS;
     constexpr int kPer = BINS / kThreads;              // digits per thread in the per-tile scans
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
         if (!SLAG_IN_BOUNDS((int64_t)gp < n, kCheckSort)) continue;
         kout[gp] = k;
         const uint32_t v = svals[j];
-        vout[gp] = v;
+        vout[gp] = vmap ? vmap[v] : v;   // optionally written through a map of the values
         if (gout) gout[gp] = gsrc[v];   // a payload that follows the values (gathered by value)
     }
 }
@@ -262,7 +263,7 @@ size_t scatter_smem() {
 
 template <typename K, int ITEMS, int BINS>
 void radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, int64_t n, int shift, int width, SortScratch &s,
-                cudaStream_t st, uint2 *ranges, int nranges, const uint2 *gsrc, uint2 *gout) {
+                cudaStream_t st, uint2 *ranges, int nranges, const uint2 *gsrc, uint2 *gout, const uint32_t *vmap) {
     constexpr int kTileN = kThreads * ITEMS;
     const int ntiles = (int)((n + kTileN - 1) / kTileN);
     // on failure the error stays recorded for the caller's cudaGetLastError check
@@ -273,7 +274,7 @@ void radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, int64_t n,
     rs_hist<K, ITEMS, BINS><<<ntiles, kThreads, kWarps * BINS * 4, st>>>(ki, n, shift, mask, width, s.hist, ntiles); note_launch();
     rs_offsets<<<BINS, ntiles >= 1024 ? 1024 : (ntiles >= 256 ? 256 : 64), 0, st>>>(s.hist, s.digit_tot, ntiles); note_launch();
     rs_scatter<K, ITEMS, BINS><<<ntiles, kThreads, scatter_smem<K, ITEMS, BINS>(), st>>>(
-        ki, vi, ko, vo, n, shift, mask, width, s.hist, s.digit_tot, ntiles, ranges, nranges, gsrc, gout);
+        ki, vi, ko, vo, n, shift, mask, width, s.hist, s.digit_tot, ntiles, ranges, nranges, gsrc, gout, vmap);
     note_launch();
 }
 
@@ -283,7 +284,7 @@ void radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, int64_t n,
 template <typename K>
 bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, const int *shifts,
                      const int *widths, int npass, SortScratch &s, cudaStream_t st, uint2 *ranges, int nranges,
-                     const uint2 *gsrc = nullptr, uint2 *gout = nullptr) {
+                     const uint2 *gsrc = nullptr, uint2 *gout = nullptr, const uint32_t *vmap = nullptr) {
     if (n <= 0 || npass <= 0) return false;
     const bool small = n < (1 << 21);
     K *ki = keys, *ko = keys_alt;
@@ -292,18 +293,19 @@ bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, i
         uint2 *rg = (npass == 1) ? ranges : nullptr;
         const uint2 *gs = (p == npass - 1) ? gsrc : nullptr;   // the payload follows the last pass
         uint2 *go = (p == npass - 1) ? gout : nullptr;
+        const uint32_t *vm = (p == npass - 1) ? vmap : nullptr;   // the map applies to the last pass's output
         if (widths[p] > 10) {
-            if (small) radix_pass<K, 4, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
-            else radix_pass<K, kItems, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+            if (small) radix_pass<K, 4, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go, vm);
+            else radix_pass<K, kItems, 2048>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go, vm);
         } else if (widths[p] > 9) {
-            if (small) radix_pass<K, 4, 1024>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
-            else radix_pass<K, kItems, 1024>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+            if (small) radix_pass<K, 4, 1024>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go, vm);
+            else radix_pass<K, kItems, 1024>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go, vm);
         } else if (widths[p] > 8) {
-            if (small) radix_pass<K, 4, 512>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
-            else radix_pass<K, kItems, 512>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+            if (small) radix_pass<K, 4, 512>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go, vm);
+            else radix_pass<K, kItems, 512>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go, vm);
         } else {
-            if (small) radix_pass<K, 4, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
-            else radix_pass<K, kItems, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go);
+            if (small) radix_pass<K, 4, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go, vm);
+            else radix_pass<K, kItems, 256>(ki, vi, ko, vo, n, shifts[p], widths[p], s, st, rg, nranges, gs, go, vm);
         }
         K *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
@@ -469,9 +471,10 @@ int digit_passes(int lo, int bits, int *shifts, int *widths, int64_t n) {
 
 bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                     const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st,
-                    uint2 *ranges, int nranges, const uint2 *gather_src, uint2 *gather_out) {
+                    uint2 *ranges, int nranges, const uint2 *gather_src, uint2 *gather_out,
+                    const uint32_t *val_map) {
     return radix_sort_impl<uint32_t>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st, ranges,
-                                     nranges, gather_src, gather_out);
+                                     nranges, gather_src, gather_out, val_map);
 }
 
 bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,

@@ -86,8 +86,10 @@ struct ViewSlot {
     int32_t *seg_buf = nullptr;            // the view's segment map (always copied: the caller's buffer
     int64_t seg_cap = 0;                   // is free once slag_add_view returns)
     WeightRecord *recs = nullptr;          // the composite's (Gaussian, segment, weight) sums
-    int64_t rec_cap = 0;
-    unsigned long long *rec_count = nullptr;
+    int64_t rec_cap = 0;                   // records (a multiple of kRecChunk)
+    unsigned long long *rec_chunks = nullptr;   // chunks reserved by the composite
+    uint32_t *rec_fill = nullptr;          // per chunk: records written
+    int64_t fill_cap = 0;
     ViewCounters *ctr = nullptr;           // device: stage A's counters
     ViewCounters *ctr_up = nullptr;        // device: the segment-id check of the view's upload
     struct Host {
@@ -533,12 +535,13 @@ slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
         // one pass: its digit is the bin id, and the pass's offsets give the ranges; the pass also
         // gathers each sorted pair's tile rectangle
         alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr, st,
-                             vs.ranges, (int)bins, shift > 0 ? vs.srect : nullptr, shift > 0 ? vs.prect : nullptr);
+                             vs.ranges, (int)bins, shift > 0 ? vs.srect : nullptr, shift > 0 ? vs.prect : nullptr,
+                             vs.sgid);
         keys = vs.pkey[alt ? 1 : 0];
     } else {
         CK(cudaMemsetAsync(vs.ranges, 0, sizeof(uint2) * (size_t)bins, st));
         alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr, st, nullptr,
-                             0, shift > 0 ? vs.srect : nullptr, shift > 0 ? vs.prect : nullptr);
+                             0, shift > 0 ? vs.srect : nullptr, shift > 0 ? vs.prect : nullptr, vs.sgid);
         keys = vs.pkey[alt ? 1 : 0];
         launch_ranges(keys, P, vs.ranges, st);
     }
@@ -554,13 +557,12 @@ slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
 
 // Both stages in one stream with a host sync between them (the diagnostic entry points).
 slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int64_t *P_out,
-                     uint32_t **keys_out, uint32_t **list_out, const uint32_t **sgid_out, int shift) {
+                     uint32_t **keys_out, uint32_t **list_out, int shift) {
     slag_status s = stage_a(ctx, vs, st, cp, shift);
     if (s != SLAG_OK) return s;
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     spans_resolve(ctx, false);
-    *sgid_out = vs.sgid;
     return stage_b(ctx, vs, st, cp, shift, ctx->scratch, P_out, keys_out, list_out);
 }
 
@@ -574,7 +576,7 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
     SA(dalloc(&vs.hash, n));
     SA(dalloc(&vs.ctr, 1));
     SA(dalloc(&vs.ctr_up, 1));
-    SA(dalloc(&vs.rec_count, 1));
+    SA(dalloc(&vs.rec_chunks, 1));
     SA(cudaHostAlloc((void **)&vs.h, sizeof(ViewSlot::Host), cudaHostAllocMapped));
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&vs.h_dev, vs.h, 0);
     int lo = 0, hi = 0;
@@ -594,7 +596,7 @@ void slot_free(ViewSlot &vs) {
     dfree(vs.rec_a); dfree(vs.rec_b); dfree(vs.rect); dfree(vs.srect);
     dfree(vs.stouched); dfree(vs.offsets); dfree(vs.hash);
     dfree(vs.prect); dfree(vs.ranges); dfree(vs.tile_order); dfree(vs.seg_buf); dfree(vs.ctr);
-    dfree(vs.ctr_up); dfree(vs.recs); dfree(vs.rec_count);
+    dfree(vs.ctr_up); dfree(vs.recs); dfree(vs.rec_chunks); dfree(vs.rec_fill);
     if (vs.h) cudaFreeHost(vs.h);
     vs.h = nullptr;
     if (vs.back) cudaStreamDestroy(vs.back);
@@ -785,14 +787,21 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     // record list of the composite: one record per (Gaussian, tile, segment) with a
     // non-zero sum (per batch of the tile's CTA); sums beyond the capacity go to the
     // tables directly, so the capacity only bounds the fast path
-    const int64_t rec_need = (int64_t)vs.h->v.P_tiles + ctx->n;
-    if (rec_need > vs.rec_cap) CK(grow(vs.recs, vs.rec_cap, rec_need, fb));
+    // (plus two chunks per tile: a CTA's partly filled and reserved chunks)
+    const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
+    int64_t rec_need = (int64_t)vs.h->v.P_tiles + ctx->n + 2 * kRecChunk * tiles;
+    rec_need = (rec_need + kRecChunk - 1) / kRecChunk * kRecChunk;
+    if (rec_need > vs.rec_cap) {
+        CK(grow(vs.recs, vs.rec_cap, rec_need, fb));
+        vs.rec_cap = vs.rec_cap / kRecChunk * kRecChunk;
+        CK(grow(vs.rec_fill, vs.fill_cap, vs.rec_cap / kRecChunk, fb));
+    }
 
     // back half on the slot's stream
     cudaStream_t bk = vs.back;
     CK(cudaStreamWaitEvent(bk, vs.ev_bin, 0));
     CK(cudaStreamWaitEvent(bk, vs.ev_up, 0));   // the segment map
-    CK(cudaMemsetAsync(vs.rec_count, 0, sizeof(unsigned long long), bk));
+    CK(cudaMemsetAsync(vs.rec_chunks, 0, sizeof(unsigned long long), bk));
     CompositeArgs a;
     a.cam = cp;
     a.ranges = vs.ranges;
@@ -803,8 +812,7 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     a.prect = vs.prect;
     a.rec_a = vs.rec_a;
     a.rec_b = vs.rec_b;
-    a.sgid = vs.sgid;
-    a.n_ranks = vs.h->v.n_visible;
+    a.n_ids = (uint32_t)ctx->n;
     a.seg = vs.seg_buf;
     a.view_base = (int32_t)vs.view_base;
     a.weight_mode = ctx->weight_mode;
@@ -823,8 +831,9 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     a.dbg_count = nullptr;
     a.accumulate = 1;
     a.recs = vs.recs;
-    a.rec_count = vs.rec_count;
-    a.rec_cap = (unsigned long long)vs.rec_cap;
+    a.rec_chunks = vs.rec_chunks;
+    a.rec_fill = vs.rec_fill;
+    a.chunk_cap = (unsigned long long)(vs.rec_cap / kRecChunk);
     a.dbg_list = nullptr;
     a.dbg_off = nullptr;
     a.dbg_staged = nullptr;
@@ -836,7 +845,7 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     const HashSink sink{vs.hash, ctx->log_count, (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
                         ctx->s_ovf, reinterpret_cast<uint32_t *>(ctx->totals + 2), (int32_t)vs.view_base};
     span_begin(ctx, SLAG_STAGE_CONSUME, bk);
-    launch_combine(vs.recs, vs.rec_count, (unsigned long long)vs.rec_cap, sink, bk);
+    launch_combine(vs.recs, vs.rec_chunks, vs.rec_fill, (unsigned long long)(vs.rec_cap / kRecChunk), sink, bk);
     span_end(ctx, bk);
     // consumes in view order: the compensated sums are updated without atomics
     CK(cudaStreamWaitEvent(bk, ctx->ev_consumed, 0));
@@ -2209,17 +2218,15 @@ slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset) {
 namespace {
 
 // The pair list of one binning (depth ranks) -> caller indices, on the host.
-slag_status ranks_to_callers(slag_ctx *ctx, cudaStream_t st, const uint32_t *d_ranks, int64_t count,
-                             const uint32_t *sgid, int32_t *out) {
+slag_status ids_to_callers(slag_ctx *ctx, cudaStream_t st, const uint32_t *d_ids, int64_t count, int32_t *out) {
     const int64_t n = ctx->n;
-    std::vector<uint32_t> h_list((size_t)(count > 0 ? count : 1)), h_orig((size_t)n), h_gid((size_t)n);
-    if (count > 0) CK(cudaMemcpyAsync(h_list.data(), d_ranks, sizeof(uint32_t) * count, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_gid.data(), sgid, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+    std::vector<uint32_t> h_list((size_t)(count > 0 ? count : 1)), h_orig((size_t)n);
+    if (count > 0) CK(cudaMemcpyAsync(h_list.data(), d_ids, sizeof(uint32_t) * count, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h_orig.data(), ctx->orig_of_int, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     for (int64_t i = 0; i < count; ++i) {
-        const uint32_t r = h_list[(size_t)i];
-        out[i] = r < (uint32_t)n ? (int32_t)h_orig[h_gid[r]] : -1;
+        const uint32_t g = h_list[(size_t)i];
+        out[i] = g < (uint32_t)n ? (int32_t)h_orig[g] : -1;
     }
     return SLAG_OK;
 }
@@ -2240,8 +2247,7 @@ slag_status bin_view_diag(slag_ctx *ctx, const slag_camera *cam, int shift, uint
     const CamParams cp = cam_params(cam);
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
-    const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, &sgid, shift);
+    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, shift);
     if (s != SLAG_OK) return s;
     CK(cudaStreamSynchronize(st));
     s = checks_reported(ctx);
@@ -2263,8 +2269,8 @@ slag_status bin_view_diag(slag_ctx *ctx, const slag_camera *cam, int shift, uint
     }
     if (out_list) {
         if (list_cap < P) return fail(ctx, SLAG_ERR_CAPACITY, "list_cap < P");
-        // list holds depth ranks; map rank -> internal -> caller index on the host
-        s = ranks_to_callers(ctx, st, list, P, sgid, out_list);
+        // the list holds internal indices; map them to caller indices on the host
+        s = ids_to_callers(ctx, st, list, P, out_list);
         if (s != SLAG_OK) return s;
     }
     if (out_ranges) {
@@ -2316,8 +2322,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     // room per tile: the Gaussians whose tile rectangle holds it (the flat per-tile binning)
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
-    const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, &sgid, 0);
+    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, 0);
     if (s != SLAG_OK) return s;
     std::vector<uint2> h_r((size_t)tiles);
     CK(cudaMemcpyAsync(h_r.data(), vs.ranges, sizeof(uint2) * tiles, cudaMemcpyDeviceToHost, st));
@@ -2332,7 +2337,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     if (out_list && list_cap < off[(size_t)tiles]) return fail(ctx, SLAG_ERR_CAPACITY, "list_cap < P");
     // the super-tile binning slag_add_view composites from, then the composite with a trace
     int64_t Ps = 0;
-    s = bin_view(ctx, vs, st, cp, &Ps, &keys, &list, &sgid, kSuperShift);
+    s = bin_view(ctx, vs, st, cp, &Ps, &keys, &list, kSuperShift);
     if (s != SLAG_OK) return s;
     uint32_t *d_list = nullptr, *d_staged = nullptr, *d_bad = nullptr;
     int64_t *d_off = nullptr;
@@ -2367,8 +2372,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     a.prect = vs.prect;
     a.rec_a = vs.rec_a;
     a.rec_b = vs.rec_b;
-    a.sgid = sgid;
-    a.n_ranks = vs.h->v.n_visible;
+    a.n_ids = (uint32_t)ctx->n;
     a.weight_mode = ctx->weight_mode;
     a.ctr = vs.ctr;
     a.overflow = reinterpret_cast<uint32_t *>(&vs.ctr->pad[0]);
@@ -2394,7 +2398,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
         return fail(ctx, SLAG_ERR_CUDA, cudaGetErrorString(e));
     }
     if (out_list) {
-        s = ranks_to_callers(ctx, st, d_list, off[(size_t)tiles], sgid, out_list);
+        s = ids_to_callers(ctx, st, d_list, off[(size_t)tiles], out_list);
         if (s != SLAG_OK) { release(); return s; }
     }
     if (out_ranges)
@@ -2422,8 +2426,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     const int64_t npx = (int64_t)cam->width * cam->height;
     int64_t P = 0;
     uint32_t *keys = nullptr, *list = nullptr;
-    const uint32_t *sgid = nullptr;
-    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, &sgid, kSuperShift);
+    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, kSuperShift);
     if (s != SLAG_OK) return s;
     if (npx > ctx->dbg_cap) {
         int64_t c1 = ctx->dbg_cap, c2 = ctx->dbg_cap, c3 = ctx->dbg_cap;
@@ -2443,8 +2446,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.prect = vs.prect;
     a.rec_a = vs.rec_a;
     a.rec_b = vs.rec_b;
-    a.sgid = sgid;
-    a.n_ranks = vs.h->v.n_visible;
+    a.n_ids = (uint32_t)ctx->n;
     a.seg = nullptr;
     a.weight_mode = ctx->weight_mode;
     a.ctr = vs.ctr;
@@ -2456,8 +2458,9 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.err = ctx->tc_err;
     a.accumulate = 0;
     a.recs = nullptr;
-    a.rec_count = nullptr;
-    a.rec_cap = 0;
+    a.rec_chunks = nullptr;
+    a.rec_fill = nullptr;
+    a.chunk_cap = 0;
     launch_composite(a, st);
     CK(cudaGetLastError());
     if (out_T) CK(cudaMemcpyAsync(out_T, ctx->dbg_T, sizeof(float) * npx, cudaMemcpyDeviceToHost, st));

@@ -115,10 +115,12 @@ void scratch_free(SortScratch &s);
 // single pass whose digit is the whole key, `ranges` (nullable) receives each
 // key value's [start, end) in the output for key values < nranges. With
 // gather_out (n entries), gather_out[i] = gather_src[sorted value i] as well.
+// With val_map, the last pass writes val_map[v] in place of each value v (the
+// payload gather still reads gather_src[v]).
 bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                     int64_t n, const int *shifts, const int *widths, int npass, SortScratch &s,
                     cudaStream_t st, uint2 *ranges = nullptr, int nranges = 0, const uint2 *gather_src = nullptr,
-                    uint2 *gather_out = nullptr);
+                    uint2 *gather_out = nullptr, const uint32_t *val_map = nullptr);
 bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                     int64_t n, const int *shifts, const int *widths, int npass, SortScratch &s,
                     cudaStream_t st);
@@ -215,7 +217,12 @@ __device__ __forceinline__ void sink_add(const HashSink &k, uint32_t g, int32_t 
 }
 
 // One per-(Gaussian, sub-tile, segment) sum of a view, on its way from the
-// compositing kernel to the combine pass.
+// compositing kernel to the combine pass. The record list is reserved in chunks
+// of kRecChunk records: a CTA reserves its next chunk one chunk ahead (so that no
+// store waits for the reservation) and writes each chunk's fill (its first
+// fill records are valid) once it is done with it; every reserved chunk gets a
+// fill, zero when it was never used.
+constexpr int kRecChunk = 256;
 struct __align__(16) WeightRecord {
     uint32_t g;                    // internal Gaussian index
     int32_t seg;
@@ -229,11 +236,10 @@ struct CompositeArgs {
     const uint2 *ranges;           // per bin (tile, or super-tile when bin_shift > 0)
     int32_t bin_shift, bins_x;
     const uint32_t *tile_order;    // CTAs of tile_order[i] come i-th
-    const uint32_t *list;          // sorted values: depth rank of each pair
+    const uint32_t *list;          // sorted pairs' values: the internal index of each pair's Gaussian
     const uint2 *prect;            // tile rectangle of the Gaussian of each sorted pair
-    const float4 *rec_a, *rec_b;   // records in internal order (the Gaussian of rank r is sgid[r])
-    const uint32_t *sgid;          // internal Gaussian index of each depth rank
-    uint32_t n_ranks;              // records (depth ranks) in srec_a / srec_b / sgid
+    const float4 *rec_a, *rec_b;   // records in internal order
+    uint32_t n_ids;                // Gaussians (records in rec_a / rec_b)
     const int32_t *seg;            // H x W
     int32_t view_base;             // column of segment 0 of this view
     int32_t weight_mode;
@@ -251,7 +257,7 @@ struct CompositeArgs {
                                    // the Gaussians that survived its culling x its 64 pixels
     float *dbg_T, *dbg_wsum;       // nullable, H x W
     int32_t *dbg_count;            // nullable
-    // trace of the Gaussians each tile stages (diagnostics; nullable): the depth rank of every
+    // trace of the Gaussians each tile stages (diagnostics; nullable): the internal index of every
     // staged Gaussian at dbg_list[dbg_off[tile] + i], i < dbg_off[tile + 1] - dbg_off[tile]
     // (beyond that *dbg_bad is set and nothing is written); dbg_staged[tile] = how many were
     // staged. With a trace the kernel keeps staging after all of a tile's pixels have stopped.
@@ -262,20 +268,22 @@ struct CompositeArgs {
     uint32_t *err;                 // set when a bounded wait gave up (nullable)
     int accumulate;                // 0: compositing only (diagnostics)
     WeightRecord *recs;            // record list of the view (nullable: sums go to the tables directly)
-    unsigned long long *rec_count; // records written (zeroed before the launch)
-    unsigned long long rec_cap;
+    unsigned long long *rec_chunks;// chunks of kRecChunk records reserved (zeroed before the launch)
+    uint32_t *rec_fill;            // per chunk: records written (every reserved chunk below chunk_cap)
+    unsigned long long chunk_cap;  // chunks the record list holds (beyond: sums go to the tables)
 };
 void launch_composite(const CompositeArgs &a, cudaStream_t st);
 
 // k_accum.cu
 void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st);
-// Adds the view's records (the first min(*rec_count, rec_cap)) to the per-Gaussian tables.
 // Copies `bytes` (a multiple of 4) from device memory to dst with the SMs. dst may be the device
 // alias of mapped pinned host memory: small results then reach the host without queueing behind
 // bulk copies on the copy engines.
 void launch_copy_words(const void *src, void *dst, int64_t bytes, cudaStream_t st);
-void launch_combine(const WeightRecord *recs, const unsigned long long *rec_count, unsigned long long rec_cap,
-                    const HashSink &sink, cudaStream_t st);
+// Adds the view's records to the per-Gaussian tables: of the first min(*rec_chunks, chunk_cap)
+// chunks, the first rec_fill[c] records of chunk c.
+void launch_combine(const WeightRecord *recs, const unsigned long long *rec_chunks, const uint32_t *rec_fill,
+                    unsigned long long chunk_cap, const HashSink &sink, cudaStream_t st);
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
                     unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key,
                     float *log_w, uint32_t *overflow, const unsigned long long *view_contrib,
