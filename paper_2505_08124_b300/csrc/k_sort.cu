@@ -118,18 +118,24 @@ __global__ void __launch_bounds__(1024) rs_offsets(uint32_t *__restrict__ hist, 
     if (tid == 0) digit_tot[d] = carry;
 }
 
+// One tile of a stable scatter pass, its items already in registers: item r of this thread is
+// tile item w * 32 * ITEMS + r * 32 + lane (valid when its global index is below n), so (warp,
+// round, lane) order is input order. Ranks the tile's items by digit, stages them in digit order
+// in shared memory and writes each digit's run contiguously (keys to kout when it is non-null,
+// values through vmap when given, the payload gsrc[value] to gout when given). Shared memory:
+// scatter_smem<K, ITEMS, BINS>() bytes at smem_raw; the caller may have used the staging arrays
+// (skeys, svals) for its own input, since they are written only after a barrier.
 template <typename K, int ITEMS, int BINS>
-__global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
-                                                       K *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                       int64_t n, int shift, uint32_t mask, int width,
-                                                       const uint32_t *__restrict__ offs,
-                                                       const uint32_t *__restrict__ digit_tot, int ntiles,
-                                                       uint2 *__restrict__ ranges, int nranges,
-                                                       const uint2 *__restrict__ gsrc, uint2 *__restrict__ gout,
-                                                       const uint32_t *__restrict__ vmap) {
+__device__ __forceinline__ void scatter_tile(K (&key)[ITEMS], uint32_t (&val)[ITEMS], unsigned char *smem_raw,
+                                             K *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
+                                             int shift, uint32_t mask, int width,
+                                             const uint32_t *__restrict__ offs,
+                                             const uint32_t *__restrict__ digit_tot, int ntiles,
+                                             uint2 *__restrict__ ranges, int nranges,
+                                             const uint2 *__restrict__ gsrc, uint2 *__restrict__ gout,
+                                             const uint32_t *__restrict__ vmap) {
     constexpr int kTileN = kThreads * ITEMS;
     constexpr int kPer = BINS / kThreads;              // digits per thread in the per-tile scans
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem_raw);              // kWarps x BINS
     uint32_t *lstart = cnt + kWarps * BINS;                              // BINS
     uint32_t *gbase = lstart + BINS;                                     // BINS
@@ -138,23 +144,15 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
     uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + kTileN);
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    __syncthreads();   // the caller's reads of the staging arrays are done
     for (int i = tid; i < kWarps * BINS; i += kThreads) cnt[i] = 0;
     __syncthreads();
 
     const int64_t tile_base = (int64_t)blockIdx.x * kTileN;
     const int64_t base = tile_base + (int64_t)w * (32 * ITEMS);
-    K key[ITEMS];
-    uint32_t val[ITEMS];
     uint32_t pos[ITEMS];
     const uint32_t lt = lanemask_lt();
     uint32_t *cw = cnt + w * BINS;
-#pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const int64_t i = base + r * 32 + lane;
-        const bool valid = i < n;
-        key[r] = valid ? kin[i] : (K)0;
-        val[r] = valid ? vin[i] : 0u;
-    }
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         const int64_t i = base + r * 32 + lane;
@@ -249,11 +247,139 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
         const uint32_t d = (uint32_t)(k >> shift) & mask;
         const uint32_t gp = gbase[d] + (uint32_t)j - lstart[d];
         if (!SLAG_IN_BOUNDS((int64_t)gp < n, kCheckSort)) continue;
-        kout[gp] = k;
+        if (kout) kout[gp] = k;
         const uint32_t v = svals[j];
         vout[gp] = vmap ? vmap[v] : v;   // optionally written through a map of the values
         if (gout) gout[gp] = gsrc[v];   // a payload that follows the values (gathered by value)
     }
+}
+
+template <typename K, int ITEMS, int BINS>
+__global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                       K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                       int64_t n, int shift, uint32_t mask, int width,
+                                                       const uint32_t *__restrict__ offs,
+                                                       const uint32_t *__restrict__ digit_tot, int ntiles,
+                                                       uint2 *__restrict__ ranges, int nranges,
+                                                       const uint2 *__restrict__ gsrc, uint2 *__restrict__ gout,
+                                                       const uint32_t *__restrict__ vmap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * (kThreads * ITEMS) + (int64_t)w * (32 * ITEMS);
+    K key[ITEMS];
+    uint32_t val[ITEMS];
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : (K)0;
+        val[r] = valid ? vin[i] : 0u;
+    }
+    scatter_tile<K, ITEMS, BINS>(key, val, smem_raw, kout, vout, n, shift, mask, width, offs, digit_tot, ntiles,
+                                 ranges, nranges, gsrc, gout, vmap);
+}
+
+// ---- binning by bin without materialised pairs ---------------------------------------------
+// The pairs of a view, in emission order, are each visible Gaussian's bins (depth-rank order,
+// each Gaussian's bins row-major in its bin rectangle); pair p of Gaussian r is number
+// p - offsets[r] of r's rectangle. The fused binning sorts them by bin in one stable pass whose
+// tiles (kTileItems consecutive pairs) generate their own pairs from the rectangles, so the
+// emitted pair list is never written or read back.
+
+// The Gaussian whose pairs hold the first pair of each tile: tstart[t] for t < ntiles. In the
+// checked build, pairs beyond P (a capacity below the view's pair count) are refused here.
+__global__ void __launch_bounds__(256) tile_starts_k(const uint32_t *__restrict__ offsets,
+                                                     const uint32_t *__restrict__ counts, uint32_t nv, int64_t P,
+                                                     int ntiles, uint32_t *__restrict__ tstart) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nv) return;
+    const int64_t off = offsets[r], cnt = counts[r];
+    if (r == (int64_t)nv - 1) (void)SLAG_IN_BOUNDS(off + cnt <= P, kCheckEmit);
+    if (cnt == 0) return;
+    for (int64_t t = (off + kTileItems - 1) / kTileItems; t * kTileItems < off + cnt && t < ntiles; ++t)
+        tstart[t] = (uint32_t)r;
+}
+
+// Calls f(j, bin, r) for every pair of this CTA's tile: j = its place in the tile, r = its
+// Gaussian's depth rank. Threads take the tile's Gaussians in turn.
+template <typename F>
+__device__ __forceinline__ void for_tile_pairs(const uint2 *__restrict__ srect, const uint32_t *__restrict__ offsets,
+                                               const uint32_t *__restrict__ tstart, uint32_t nv, int64_t P,
+                                               int ntiles, int shift, int bins_x, F f) {
+    const int64_t P0 = (int64_t)blockIdx.x * kTileItems;
+    const int64_t P1 = P0 + kTileItems < P ? P0 + kTileItems : P;
+    const uint32_t r_lo = tstart[blockIdx.x];
+    const uint32_t r_hi = (int)blockIdx.x + 1 < ntiles ? tstart[blockIdx.x + 1] : nv - 1u;
+    for (uint32_t r = r_lo + threadIdx.x; r <= r_hi; r += kThreads) {
+        const uint2 rc = srect[r];
+        const uint32_t x0 = (rc.x & 0xffffu) >> shift, x1 = (((rc.x >> 16) - 1u) >> shift) + 1u;
+        const uint32_t y0 = (rc.y & 0xffffu) >> shift, y1 = (((rc.y >> 16) - 1u) >> shift) + 1u;
+        const uint32_t wx = x1 - x0;
+        const int64_t cnt = (int64_t)wx * (y1 - y0);
+        const int64_t off = offsets[r];
+        const int64_t e0 = P0 - off > 0 ? P0 - off : 0;
+        const int64_t e1 = P1 - off < cnt ? P1 - off : cnt;
+        if (e0 >= e1) continue;
+        uint32_t by = y0 + (uint32_t)(e0 / wx), bx = x0 + (uint32_t)(e0 % wx);
+        for (int64_t e = e0; e < e1; ++e) {
+            f((int)(off + e - P0), by * (uint32_t)bins_x + bx, r);
+            if (++bx == x1) {
+                bx = x0;
+                ++by;
+            }
+        }
+    }
+}
+
+// Per tile: the count of each bin among its pairs, to hist[bin][tile] (the layout of rs_hist).
+template <int BINS>
+__global__ void __launch_bounds__(kThreads) bin_hist_k(const uint2 *__restrict__ srect,
+                                                       const uint32_t *__restrict__ offsets,
+                                                       const uint32_t *__restrict__ tstart, uint32_t nv, int64_t P,
+                                                       int ntiles, int shift, int bins_x,
+                                                       uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[BINS];
+    for (int d = threadIdx.x; d < BINS; d += kThreads) h[d] = 0;
+    __syncthreads();
+    for_tile_pairs(srect, offsets, tstart, nv, P, ntiles, shift, bins_x,
+                   [&](int, uint32_t bin, uint32_t) { atomicAdd(&h[bin], 1u); });
+    __syncthreads();
+    for (int d = threadIdx.x; d < BINS; d += kThreads) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+// Per tile: its pairs, generated into the staging arrays in emission order, then scattered
+// stably by bin (scatter_tile); values leave as vmap[rank], with the Gaussian's tile rectangle.
+template <int BINS>
+__global__ void __launch_bounds__(kThreads) bin_place_k(const uint2 *__restrict__ srect,
+                                                        const uint32_t *__restrict__ offsets,
+                                                        const uint32_t *__restrict__ tstart, uint32_t nv, int64_t P,
+                                                        int ntiles, int shift, int bins_x, uint32_t mask, int width,
+                                                        const uint32_t *__restrict__ offs,
+                                                        const uint32_t *__restrict__ digit_tot,
+                                                        uint2 *__restrict__ ranges, int nranges,
+                                                        const uint2 *__restrict__ rect_src, uint2 *__restrict__ rect_out,
+                                                        const uint32_t *__restrict__ vmap,
+                                                        uint32_t *__restrict__ vout) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *skeys = reinterpret_cast<uint32_t *>(smem_raw) + (kWarps + 2) * BINS + 16;
+    uint32_t *svals = skeys + kTileItems;
+    for_tile_pairs(srect, offsets, tstart, nv, P, ntiles, shift, bins_x, [&](int j, uint32_t bin, uint32_t r) {
+        skeys[j] = bin;
+        svals[j] = r;
+    });
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tile_base = (int64_t)blockIdx.x * kTileItems;
+    uint32_t key[kItems], val[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const int j = w * (32 * kItems) + r * 32 + lane;
+        const bool valid = tile_base + j < P;
+        key[r] = valid ? skeys[j] : 0u;
+        val[r] = valid ? svals[j] : 0u;
+    }
+    scatter_tile<uint32_t, kItems, BINS>(key, val, smem_raw, nullptr, vout, P, 0, mask, width, offs, digit_tot, ntiles,
+                                         ranges, nranges, rect_src, rect_out, vmap);
 }
 
 template <typename K, int ITEMS, int BINS>
@@ -444,6 +570,14 @@ cudaError_t scratch_reserve(SortScratch &s, int64_t n) {
         if (e != cudaSuccess) return e;
         s.partials_cap = (size_t)scan_tiles_n;
     }
+    if ((size_t)scan_tiles_n > s.tstart_cap) {   // the fused binning's tiles (kTileItems pairs each)
+        cudaFree(s.tstart);
+        s.tstart = nullptr;
+        s.tstart_cap = 0;
+        cudaError_t e = cudaMalloc(&s.tstart, (size_t)scan_tiles_n * sizeof(uint32_t));
+        if (e != cudaSuccess) return e;
+        s.tstart_cap = (size_t)scan_tiles_n;
+    }
     return cudaSuccess;
 }
 
@@ -451,6 +585,7 @@ void scratch_free(SortScratch &s) {
     cudaFree(s.hist);
     cudaFree(s.digit_tot);
     cudaFree(s.partials);
+    cudaFree(s.tstart);
     s = SortScratch{};
 }
 
@@ -480,6 +615,54 @@ bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t
 bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n,
                     const int *shifts, const int *widths, int npass, SortScratch &s, cudaStream_t st) {
     return radix_sort_impl<uint64_t>(keys, keys_alt, vals, vals_alt, n, shifts, widths, npass, s, st, nullptr, 0);
+}
+
+namespace {
+
+template <int BINS>
+void bin_sort_fused_impl(const uint2 *srect, const uint32_t *offsets, const uint32_t *counts, uint32_t n_visible,
+                         int64_t P, int shift, int bins_x, int bins, const uint32_t *val_map, uint32_t *vals_out,
+                         uint2 *rect_out, uint2 *ranges, SortScratch &s, cudaStream_t st) {
+    const int ntiles = (int)((P + kTileItems - 1) / kTileItems);
+    const size_t smem = scatter_smem<uint32_t, kItems, BINS>();
+    // on failure the error stays recorded for the caller's cudaGetLastError check
+    if (set_max_smem((const void *)bin_place_k<BINS>, (int)smem) != cudaSuccess) return;
+    int width = 0;
+    while ((1 << width) < bins) ++width;
+    if (width == 0) width = 1;
+    const uint32_t mask = (1u << width) - 1u;
+    tile_starts_k<<<(n_visible + 255) / 256, 256, 0, st>>>(offsets, counts, n_visible, P, ntiles, s.tstart);
+    note_launch();
+    bin_hist_k<BINS><<<ntiles, kThreads, 0, st>>>(srect, offsets, s.tstart, n_visible, P, ntiles, shift, bins_x,
+                                                   s.hist);
+    note_launch();
+    rs_offsets<<<BINS, ntiles >= 1024 ? 1024 : (ntiles >= 256 ? 256 : 64), 0, st>>>(s.hist, s.digit_tot, ntiles);
+    note_launch();
+    bin_place_k<BINS><<<ntiles, kThreads, smem, st>>>(srect, offsets, s.tstart, n_visible, P, ntiles, shift, bins_x,
+                                                      mask, width, s.hist, s.digit_tot, ranges, bins, srect, rect_out,
+                                                      val_map, vals_out);
+    note_launch();
+}
+
+}  // namespace
+
+bool bin_sort_fused(const uint2 *srect, const uint32_t *offsets, const uint32_t *counts, uint32_t n_visible,
+                    int64_t P, int shift, int bins_x, int bins, const uint32_t *val_map, uint32_t *vals_out,
+                    uint2 *rect_out, uint2 *ranges, SortScratch &s, cudaStream_t st) {
+    if (P <= 0 || n_visible == 0 || bins < 1 || bins > 2048) return false;
+    if (bins <= 256)
+        bin_sort_fused_impl<256>(srect, offsets, counts, n_visible, P, shift, bins_x, bins, val_map, vals_out,
+                                 rect_out, ranges, s, st);
+    else if (bins <= 512)
+        bin_sort_fused_impl<512>(srect, offsets, counts, n_visible, P, shift, bins_x, bins, val_map, vals_out,
+                                 rect_out, ranges, s, st);
+    else if (bins <= 1024)
+        bin_sort_fused_impl<1024>(srect, offsets, counts, n_visible, P, shift, bins_x, bins, val_map, vals_out,
+                                  rect_out, ranges, s, st);
+    else
+        bin_sort_fused_impl<2048>(srect, offsets, counts, n_visible, P, shift, bins_x, bins, val_map, vals_out,
+                                  rect_out, ranges, s, st);
+    return true;
 }
 
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *d_total,

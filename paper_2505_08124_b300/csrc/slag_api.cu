@@ -495,7 +495,7 @@ slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
 // Stage B, once stage A's counters are on the host: pair emission, the stable sort of the
 // pairs by bin (tile or super-tile), bin ranges and the tile order; sorts with `scr`.
 slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int shift,
-                    SortScratch &scr, int64_t *P_out, uint32_t **keys_out, uint32_t **list_out) {
+                    SortScratch &scr, int64_t *P_out, uint32_t **list_out) {
     int64_t P = (int64_t)vs.h->v.P;         // pairs at the binning granularity
     // checked builds only: a capacity forced below P; the emission's checks refuse the pairs
     // beyond it and the later stages see only the first pairs
@@ -518,52 +518,42 @@ slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
     CK(grow(vs.ranges, vs.ranges_cap, bins, st));
     const uint32_t nv = vs.h->v.n_visible;
     span_begin(ctx, SLAG_STAGE_BIN, st);
-    launch_emit(vs.srect, vs.offsets, nv, shift, bins_x, P, vs.pkey[0], vs.pval[0], st);
-    int shifts[8], widths[8];
-    int np = digit_passes(0, ceil_log2((uint64_t)bins), shifts, widths, P);
-    if (np == 0) {
-        // a single bin: one 1-bit pass still runs, for the ranges and the pairs' rectangles
-        shifts[0] = 0;
-        widths[0] = 1;
-        np = 1;
-    }
-    uint32_t *keys = vs.pkey[0];
-    bool alt = false;
     // the tile rectangle of each sorted pair (the composite's per-tile filter), for super-tile bins
     if (shift > 0) CK(grow(vs.prect, vs.prect_cap, P, st));
-    if (P > 0 && np == 1) {
-        // one pass: its digit is the bin id, and the pass's offsets give the ranges; the pass also
-        // gathers each sorted pair's tile rectangle
-        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr, st,
-                             vs.ranges, (int)bins, shift > 0 ? vs.srect : nullptr, shift > 0 ? vs.prect : nullptr,
-                             vs.sgid);
-        keys = vs.pkey[alt ? 1 : 0];
-    } else {
+    uint32_t *list = vs.pval[0];
+    if (P == 0) {
         CK(cudaMemsetAsync(vs.ranges, 0, sizeof(uint2) * (size_t)bins, st));
-        alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr, st, nullptr,
-                             0, shift > 0 ? vs.srect : nullptr, shift > 0 ? vs.prect : nullptr, vs.sgid);
-        keys = vs.pkey[alt ? 1 : 0];
-        launch_ranges(keys, P, vs.ranges, st);
+    } else if (!bin_sort_fused(vs.srect, vs.offsets, vs.stouched, nv, P, shift, bins_x, (int)bins, vs.sgid, list,
+                               shift > 0 ? vs.prect : nullptr, vs.ranges, scr, st)) {
+        // more than 2048 bins: emit the pairs, then a radix sort of them by bin
+        launch_emit(vs.srect, vs.offsets, nv, shift, bins_x, P, vs.pkey[0], vs.pval[0], st);
+        int shifts[8], widths[8];
+        const int np = digit_passes(0, ceil_log2((uint64_t)bins), shifts, widths, P);
+        CK(cudaMemsetAsync(vs.ranges, 0, sizeof(uint2) * (size_t)bins, st));
+        const bool alt = radix_sort_u32(vs.pkey[0], vs.pkey[1], vs.pval[0], vs.pval[1], P, shifts, widths, np, scr,
+                                        st, nullptr, 0, shift > 0 ? vs.srect : nullptr,
+                                        shift > 0 ? vs.prect : nullptr, vs.sgid);
+        launch_ranges(vs.pkey[alt ? 1 : 0], P, vs.ranges, st);
+        list = vs.pval[alt ? 1 : 0];
     }
     CK(grow(vs.tile_order, vs.order_cap, tiles, st));
     launch_tile_order(vs.ranges, cp.tiles_x, cp.tiles_y, shift, vs.tile_order, st);
     span_end(ctx, st);
     CK(cudaGetLastError());
     *P_out = P;
-    *keys_out = keys;
-    *list_out = vs.pval[alt ? 1 : 0];
+    *list_out = list;
     return SLAG_OK;
 }
 
 // Both stages in one stream with a host sync between them (the diagnostic entry points).
 slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int64_t *P_out,
-                     uint32_t **keys_out, uint32_t **list_out, int shift) {
+                     uint32_t **list_out, int shift) {
     slag_status s = stage_a(ctx, vs, st, cp, shift);
     if (s != SLAG_OK) return s;
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     spans_resolve(ctx, false);
-    return stage_b(ctx, vs, st, cp, shift, ctx->scratch, P_out, keys_out, list_out);
+    return stage_b(ctx, vs, st, cp, shift, ctx->scratch, P_out, list_out);
 }
 
 cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
@@ -757,8 +747,8 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     cudaStream_t fb = ctx->front_b;
     CK(cudaStreamWaitEvent(fb, vs.ev_a, 0));
     int64_t P = 0;
-    uint32_t *keys = nullptr, *list = nullptr;
-    slag_status s = stage_b(ctx, vs, fb, cp, kSuperShift, ctx->scratch_b, &P, &keys, &list);
+    uint32_t *list = nullptr;
+    slag_status s = stage_b(ctx, vs, fb, cp, kSuperShift, ctx->scratch_b, &P, &list);
     if (s != SLAG_OK) return s;
     CK(cudaEventRecord(vs.ev_bin, fb));
 
@@ -2246,8 +2236,8 @@ slag_status bin_view_diag(slag_ctx *ctx, const slag_camera *cam, int shift, uint
     ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
     const CamParams cp = cam_params(cam);
     int64_t P = 0;
-    uint32_t *keys = nullptr, *list = nullptr;
-    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, shift);
+    uint32_t *list = nullptr;
+    s = bin_view(ctx, vs, st, cp, &P, &list, shift);
     if (s != SLAG_OK) return s;
     CK(cudaStreamSynchronize(st));
     s = checks_reported(ctx);
@@ -2286,7 +2276,6 @@ slag_status bin_view_diag(slag_ctx *ctx, const slag_camera *cam, int shift, uint
             out_ranges[2 * t + 1] = r.y > r.x ? (int64_t)r.y : at;
         }
     }
-    (void)keys;
     return SLAG_OK;
 }
 
@@ -2321,8 +2310,8 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
     // room per tile: the Gaussians whose tile rectangle holds it (the flat per-tile binning)
     int64_t P = 0;
-    uint32_t *keys = nullptr, *list = nullptr;
-    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, 0);
+    uint32_t *list = nullptr;
+    s = bin_view(ctx, vs, st, cp, &P, &list, 0);
     if (s != SLAG_OK) return s;
     std::vector<uint2> h_r((size_t)tiles);
     CK(cudaMemcpyAsync(h_r.data(), vs.ranges, sizeof(uint2) * tiles, cudaMemcpyDeviceToHost, st));
@@ -2337,7 +2326,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     if (out_list && list_cap < off[(size_t)tiles]) return fail(ctx, SLAG_ERR_CAPACITY, "list_cap < P");
     // the super-tile binning slag_add_view composites from, then the composite with a trace
     int64_t Ps = 0;
-    s = bin_view(ctx, vs, st, cp, &Ps, &keys, &list, kSuperShift);
+    s = bin_view(ctx, vs, st, cp, &Ps, &list, kSuperShift);
     if (s != SLAG_OK) return s;
     uint32_t *d_list = nullptr, *d_staged = nullptr, *d_bad = nullptr;
     int64_t *d_off = nullptr;
@@ -2425,8 +2414,8 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     const CamParams cp = cam_params(cam);
     const int64_t npx = (int64_t)cam->width * cam->height;
     int64_t P = 0;
-    uint32_t *keys = nullptr, *list = nullptr;
-    s = bin_view(ctx, vs, st, cp, &P, &keys, &list, kSuperShift);
+    uint32_t *list = nullptr;
+    s = bin_view(ctx, vs, st, cp, &P, &list, kSuperShift);
     if (s != SLAG_OK) return s;
     if (npx > ctx->dbg_cap) {
         int64_t c1 = ctx->dbg_cap, c2 = ctx->dbg_cap, c3 = ctx->dbg_cap;
@@ -2467,7 +2456,6 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     if (out_wsum) CK(cudaMemcpyAsync(out_wsum, ctx->dbg_wsum, sizeof(float) * npx, cudaMemcpyDeviceToHost, st));
     if (out_count) CK(cudaMemcpyAsync(out_count, ctx->dbg_count, sizeof(int32_t) * npx, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    (void)keys;
     return checks_reported(ctx);
 }
 

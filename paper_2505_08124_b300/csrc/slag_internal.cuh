@@ -104,6 +104,8 @@ struct SortScratch {
     uint32_t *digit_tot = nullptr; // 256
     uint32_t *partials = nullptr;  // scan partials
     size_t partials_cap = 0;
+    uint32_t *tstart = nullptr;    // fused binning: the first Gaussian of each tile
+    size_t tstart_cap = 0;
 };
 
 cudaError_t scratch_reserve(SortScratch &s, int64_t n);
@@ -124,6 +126,18 @@ bool radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t
 bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                     int64_t n, const int *shifts, const int *widths, int npass, SortScratch &s,
                     cudaStream_t st);
+
+// Binning of a view's Gaussian-bin pairs by bin in one stable pass, without writing the pairs in
+// emission order first: the Gaussians of depth rank r < n_visible, with bin rectangles from
+// srect at 2^shift tiles per bin (bins_x bins per row, `bins` in all), counts[r] pairs each and
+// offsets = the exclusive scan of counts; P (<= the pair total; smaller only in checked builds,
+// whose check then flags the pair emission) pairs in all. Writes, in bin order and within a bin
+// in emission order, vals_out[i] = val_map[r] and rect_out[i] = srect[r] of each pair's Gaussian
+// r, and ranges[b] = [start, end) of bin b. Returns false (and does nothing) when bins > 2048 or
+// there are no pairs; the caller then emits the pairs and radix-sorts them.
+bool bin_sort_fused(const uint2 *srect, const uint32_t *offsets, const uint32_t *counts, uint32_t n_visible,
+                    int64_t P, int shift, int bins_x, int bins, const uint32_t *val_map, uint32_t *vals_out,
+                    uint2 *rect_out, uint2 *ranges, SortScratch &s, cudaStream_t st);
 
 // Exclusive prefix sum of n uint32 values; writes the total to *d_total (may be null).
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *d_total,

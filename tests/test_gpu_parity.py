@@ -79,6 +79,14 @@ def _binning_cases():
     yield "edges", g, [synth.look_at([0.0, -1.5, 0.2], [0, 0, 0], 97, 61, 70.0)]
     # a single tile
     yield "onetile", s.gaussians.subset(np.arange(300)), [synth.look_at([0, -3, 0.5], [0, 0, 0], 16, 16)]
+    # large Gaussians (hundreds of tiles each): one Gaussian's pairs span several of the binning
+    # sort's 4096-pair tiles
+    g = synth.random_gaussians(11, 800, -1.0, 1.0)
+    g.scales *= 15.0
+    yield "wide", g, [synth.look_at([0.0, -3.0, 0.4], [0, 0, 0], 960, 540)]
+    # more tiles (2304) than the single-pass binning takes: pair emission and a two-pass sort
+    g = synth.random_gaussians(12, 30000, -1.0, 1.0)
+    yield "manytiles", g, [synth.look_at([0.3, -3.0, 0.4], [0, 0, 0], 1024, 576)]
 
 
 @pytest.mark.parametrize("case", [c[0] for c in _binning_cases()])
