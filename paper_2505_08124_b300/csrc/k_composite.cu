@@ -17,27 +17,29 @@
 // tile, taken in list order.
 //   * Producer: fills one of kNB record buffers at a time (a ring) with the hits among
 //     the next 128 candidates of the bin's list (the following 128 are loaded
-//     meanwhile; the list holds Gaussian indices, and each hit's record is
-//     copied asynchronously from the view's records), turns each record into a
-//     tile-local exponent polynomial (keeping what the consumers' culling tests need), and publishes the
-//     buffer on an mbarrier; it refills a buffer once all consumers have
-//     released it, first moving that buffer's per-(segment, Gaussian) sums to
-//     the view's record list. It stops when the list ends or no consumer
-//     warp has a live pixel.
+//     meanwhile; the list holds Gaussian indices), copying each hit's record
+//     (36 bytes, written by the projection) asynchronously and publishing the
+//     buffer on an mbarrier that completes once the copies have landed, so the
+//     producer never waits for them; it refills a buffer once all consumers
+//     have released it, first moving that buffer's per-(segment, Gaussian)
+//     sums to the view's record list. It stops when the list ends or no
+//     consumer warp has a live pixel.
 //   * Consumers: the tile's pixels are reordered by segment ("slot"), and
 //     within a segment by 8x8 block; a thread takes two neighbours in that
 //     order (almost always one segment), so each warp's 64 pixels usually
 //     share one segment and form a square block. A warp composites each
 //     published buffer in chunks of 32 Gaussians, keeping only those whose
-//     alpha >= 1/255 reaches its pixel box, then sums each Gaussian's weights
+//     alpha >= 1/255 reaches its pixel box (the record's mean made tile-local),
+//     expands the survivors' exponents into tile-local polynomials, composites
+//     them, then sums each Gaussian's weights
 //     over its lanes per slot (a transposition through shared memory) into
 //     the buffer's (slot x Gaussian) table, and releases the buffer. Warps run
 //     independently: a warp whose pixels have all stopped only releases the
 //     buffers, and no warp waits for another at a CTA barrier.
 //   * Every wait is an mbarrier wait bounded by ~1 s of globaltimer; a wait
 //     that gives up sets the context's error word and an abort flag that
-//     releases every other wait of the CTA (nothing asynchronous is in flight
-//     at a wait).
+//     releases every other wait of the CTA; the producer waits for its copies
+//     in flight before it exits.
 // A combine pass (many records in flight per SM) adds the records to the
 // per-view (segment, weight) table of each Gaussian (4 slots per Gaussian;
 // further segments are appended directly as triples).
@@ -62,13 +64,13 @@ constexpr int kNB = 2;                                // record buffers (a ring)
 constexpr int kSmemSlots = 4;
 static_assert(kBuf < kRecChunk, "one slot's sums of a buffer must fit in two record chunks");
 constexpr int kWStride = 36;                          // transposition rows: 16-byte aligned, conflict-free
-constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2(1/255)
 constexpr uint32_t kBarConsumers = 1;                 // named barrier of the consumer warps
 
 struct Smem {
-    float4 q0[kNB][kBuf];                 // staged (mu'x, mu'y, a', b'); then (mx, my, r1, r2)
-    float4 q1[kNB][kBuf];                 // staged (c', log2 opacity, ex, ey); then (A, Bc, C, t)
-    uint2 q2[kNB][kBuf];                  // (log2 opacity bits, internal Gaussian index)
+    float4 q0[kNB][kBuf];                 // records: (mu'x, mu'y, a', b')
+    float4 q1[kNB][kBuf];                 //          (c', log2 opacity, r1, r2)
+    float qt[kNB][kBuf];                  //          culling threshold t
+    uint32_t gid[kNB][kBuf];              // internal Gaussian index of each record
     float wb[kNB][kSmemSlots][kBuf];      // per (buffer, slot, Gaussian of the buffer)
     union {
         float wbuf[kConsumers][32 * kWStride];   // per warp: (survivor of the chunk) x lane
@@ -157,7 +159,17 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src));
 }
 
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src));
+}
+
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Arrival on bar once this thread's cp.async copies so far have landed (counted in the barrier's
+// arrival count: .noinc).
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 // Barriers of the consumer warps only (the producer never takes part).
 __device__ __forceinline__ void cbar() { asm volatile("bar.sync %0, %1;" ::"n"(kBarConsumers), "n"(kPixThreads) : "memory"); }
@@ -183,7 +195,7 @@ __device__ __forceinline__ HashSink sink_of(const CompositeArgs &a) {
 
 __device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int b, int slot, int gi, float acc) {
     if (slot < kSmemSlots) atomicAdd(&sm.wb[b][slot][gi], acc);
-    else sink_add(sink_of(a), sm.q2[b][gi].y, sm.seg_of_slot[slot], acc);
+    else sink_add(sink_of(a), sm.gid[b][gi], sm.seg_of_slot[slot], acc);
 }
 
 // The producer's place in the view's record list: chunk `cur` is being filled (`used` records),
@@ -219,13 +231,13 @@ __device__ void res_close(const CompositeArgs &a, RecRes &rr, int lane) {
 
 // Whether the exponent e(X, Y) = lo + A dx^2 + Bc dx dy + C dy^2 (dx = mx - X, dy = my - Y; A, C < 0
 // and 4AC > Bc^2: a concave quadratic) reaches lo + t anywhere on the box (x0, x1, y0, y1) of a warp's
-// pixel centres; q0 = (mx, my, r1, r2), q1 = (A, Bc, C, t). The maximum over the box is lo at the mean
-// when the mean lies inside; otherwise it lies on the box's boundary, where each edge is a concave
-// parabola maximised at its clamped vertex: dy = r1 dx on a vertical edge (r1 = -Bc / 2C), dx = r2 dy
-// on a horizontal one (r2 = -Bc / 2A). An empty box (x0 = +inf) reaches nothing.
-__device__ __forceinline__ bool reaches(float4 q0, float4 q1, float4 box) {
+// pixel centres. The maximum over the box is lo at the mean when the mean lies inside; otherwise it
+// lies on the box's boundary, where each edge is a concave parabola maximised at its clamped vertex:
+// dy = r1 dx on a vertical edge (r1 = -Bc / 2C), dx = r2 dy on a horizontal one (r2 = -Bc / 2A). An
+// empty box (x0 = +inf) reaches nothing.
+__device__ __forceinline__ bool reaches(float mx, float my, float r1, float r2, float A, float Bc, float C, float t,
+                                        float4 box) {
     if (!(box.x <= box.y)) return false;
-    const float mx = q0.x, my = q0.y, A = q1.x, Bc = q1.y, C = q1.z, t = q1.w;
     if (mx >= box.x && mx <= box.y && my >= box.z && my <= box.w) return 0.f >= t;
     const float dx0 = mx - box.y, dx1 = mx - box.x;   // dx range over the box
     const float dy0 = my - box.w, dy1 = my - box.z;
@@ -234,11 +246,11 @@ __device__ __forceinline__ bool reaches(float4 q0, float4 q1, float4 box) {
     for (int e = 0; e < 2; ++e) {
         // vertical edges: dx fixed, dy free in [dy0, dy1]
         const float dx = e ? dx1 : dx0;
-        const float dy = fminf(fmaxf(q0.z * dx, dy0), dy1);
+        const float dy = fminf(fmaxf(r1 * dx, dy0), dy1);
         best = fmaxf(best, fmaf(fmaf(A, dx, Bc * dy), dx, C * dy * dy));
         // horizontal edges: dy fixed, dx free in [dx0, dx1]
         const float dy2 = e ? dy1 : dy0;
-        const float dx2 = fminf(fmaxf(q0.w * dy2, dx0), dx1);
+        const float dx2 = fminf(fmaxf(r2 * dy2, dx0), dx1);
         best = fmaxf(best, fmaf(fmaf(A, dx2, Bc * dy2), dx2, C * dy2 * dy2));
     }
     return best >= t;
@@ -311,7 +323,7 @@ __device__ void drain_sums(const CompositeArgs &a, Smem &sm, int b, int n, int n
         if (!a.recs) {   // no record list: the sums go to the tables directly
 #pragma unroll
             for (int j = 0; j < kPerLane; ++j)
-                if (v[j] != 0.f) sink_add(sink_of(a), sm.q2[b][lane + 32 * j].y, seg, v[j]);
+                if (v[j] != 0.f) sink_add(sink_of(a), sm.gid[b][lane + 32 * j], seg, v[j]);
             continue;
         }
         if (!rr.have_cur) {   // the first records: the two chunks reserved at the start
@@ -328,7 +340,7 @@ __device__ void drain_sums(const CompositeArgs &a, Smem &sm, int b, int n, int n
 #pragma unroll
         for (int j = 0; j < kPerLane; ++j) {
             if (v[j] == 0.f) continue;
-            const uint32_t g = sm.q2[b][lane + 32 * j].y;
+            const uint32_t g = sm.gid[b][lane + 32 * j];
             const unsigned long long ch = pos < kRecChunk ? rr.cur : rr.next;
             if (ch < a.chunk_cap) {
                 WeightRecord r;
@@ -352,6 +364,13 @@ __device__ void drain_sums(const CompositeArgs &a, Smem &sm, int b, int n, int n
             res_request(a, rr, lane, 1ull);
         }
     }
+}
+
+// Publishes buffer b: every producer lane arrives twice on full[b] (count 64), once for its
+// shared-memory writes (release) and once, asynchronously, when its record copies have landed.
+__device__ __forceinline__ void publish(Smem &sm, int b) {
+    cp_async_arrive(&sm.full[b]);
+    tc::arrive(&sm.full[b]);
 }
 
 template <bool kDebug>
@@ -414,7 +433,7 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
         if (cursor >= end || !live) {
             if (lane == 0) sm.count[b] = -1;
             __syncwarp();
-            tc::arrive(&sm.full[b]);
+            publish(sm, b);
             break;
         }
         // stable compaction of the hits (candidate order is (k, lane)); their records are copied
@@ -427,7 +446,8 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
             if (hit[k]) {
                 cp_async16(&sm.q0[b][pos], a.rec_a + g[k]);
                 cp_async16(&sm.q1[b][pos], a.rec_b + g[k]);
-                sm.q2[b][pos].y = g[k];
+                cp_async4(&sm.qt[b][pos], a.rec_t + g[k]);
+                sm.gid[b][pos] = g[k];
                 if (trace) {
                     const int64_t at = a.dbg_off[tile] + staged + pos;
                     if (at < a.dbg_off[tile + 1]) a.dbg_list[at] = g[k];
@@ -437,8 +457,6 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
             nb += __popc(bal);
         }
         cursor += kBuf;
-        cp_async_wait_all();
-        __syncwarp();
         staged += nb;
         if (!have_slots) {
             // the number of slots comes from the consumers' prologue (needed by the drains)
@@ -446,30 +464,9 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
             ns_smem = sm.scalar[1];
             have_slots = true;
         }
-        // records -> tile-local exponent polynomials. With X = px + 0.5 - ox, mx = mu'x - ox (and
-        // Y, my likewise), the exponent q2 + log2 o = a' dx^2 + b' dx dy + c' dy^2 + log2 o with
-        // dx = mx - X, dy = my - Y is K0 + K1 X + K2 Y + A X^2 + Bc X Y + C Y^2 (poly_coeffs). Each
-        // consumer warp culls against its own pixel box and expands the survivors' coefficients; the
-        // record keeps what both need.
-        for (int i = lane; i < nb; i += 32) {
-            const float4 ra = sm.q0[b][i], rb = sm.q1[b][i];
-            const float mx = ra.x - ox, my = ra.y - oy;
-            const float A = ra.z, Bc = ra.w, C = rb.x, lo = rb.y;
-            float K0, K1, K2;
-            poly_coeffs(mx, my, A, Bc, C, lo, K0, K1, K2);
-            // a Gaussian is kept for a warp when its exponent reaches the floor on the warp's box,
-            // less a margin that bounds the rounding of the per-pixel polynomial (terms at most S in
-            // size; X, Y < 16)
-            const float S = fabsf(K0) + 16.f * (fabsf(K1) + fabsf(K2)) + 256.f * (fabsf(A) + fabsf(Bc) + fabsf(C));
-            const float thr = kLog2AlphaMin - fmaf(4e-6f, S, 0.01f);
-            const float r1 = -Bc * __frcp_rn(2.f * C), r2 = -Bc * __frcp_rn(2.f * A);
-            sm.q0[b][i] = make_float4(mx, my, r1, r2);
-            sm.q1[b][i] = make_float4(A, Bc, C, lo > -INFINITY ? thr - lo : INFINITY);
-            sm.q2[b][i].x = __float_as_uint(lo);
-        }
         if (lane == 0) sm.count[b] = nb;
         __syncwarp();
-        tc::arrive(&sm.full[b]);   // every lane: each publishes its own writes
+        publish(sm, b);   // complete once the records' copies have landed
     }
     // the batches still held by the consumers (it - kNB + 1 .. it - 1): their sums once released
     for (int bt = it - kNB + 1 > 0 ? it - kNB + 1 : 0; ok && bt < it; ++bt) {
@@ -479,6 +476,7 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
     }
     if (a.accumulate && a.recs) res_close(a, rr, lane);
     if (trace && lane == 0) a.dbg_staged[tile] = (uint32_t)staged;
+    cp_async_wait_all();   // no copy into the CTA's shared memory outlives it (after a wait gave up)
 }
 
 // kKernel: record Eq. 2's kernel exp(-q/2) instead of alpha * T; kDebug: keep the
@@ -495,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
 
     if (tid == 0) {
         for (int b = 0; b < kNB; ++b) {
-            tc::mbar_init(&sm.full[b], 32);
+            tc::mbar_init(&sm.full[b], 64);
             tc::mbar_init(&sm.empty[b], kPixThreads);
         }
         tc::mbar_init(&sm.ready, kPixThreads);
@@ -657,7 +655,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
         if (nb < 0) break;
         const float4 *q0 = sm.q0[b];
         const float4 *q1 = sm.q1[b];
-        const uint2 *q2 = sm.q2[b];
+        const float *qt = sm.qt[b];
         for (int c = 0; c * 32 < nb; ++c) {
             const float2 T = unpk(PT);
             const bool alive0 = T.x > 0.f, alive1 = T.y > 0.f;
@@ -667,28 +665,35 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
             // j tests Gaussian c*32 + j against the warp's box
             bool hitw = false;
             float4 qa, qb;
+            float mx = 0.f, my = 0.f;
             if (lane < nvalid) {
+                // the record (mu'x, mu'y, a', b'), (c', log2 o, r1, r2) and t; mean tile-local
                 qa = q0[c * 32 + lane];
                 qb = q1[c * 32 + lane];
-                hitw = reaches(qa, qb, wbox);
+                mx = qa.x - ox;
+                my = qa.y - oy;
+                hitw = reaches(mx, my, qb.z, qb.w, qa.z, qa.w, qb.x, qt[c * 32 + lane], wbox);
             }
             const uint32_t mask = __ballot_sync(0xffffffffu, hitw);
             if (mask == 0) continue;
             const int n = __popc(mask);
             executed += (unsigned long long)n;
             // the survivors in chunk order: survivor r's coefficients go to half (r & 1) of staged
-            // pair r / 2; an odd count is padded with a Gaussian that reaches no pixel (e = -inf)
+            // pair r / 2; an odd count is padded with a Gaussian that reaches no pixel (e = -inf).
+            // With pixel centres X = px + 0.5 - ox, Y likewise, and the tile-local mean (mx, my),
+            // the exponent q2 + log2 o = a' dx^2 + b' dx dy + c' dy^2 + log2 o (dx = mx - X,
+            // dy = my - Y) is K0 + K1 X + K2 Y + A X^2 + Bc X Y + C Y^2 (poly_coeffs).
             if (hitw) {
                 const int r = __popc(mask & lt);
                 float K0, K1, K2;
-                poly_coeffs(qa.x, qa.y, qb.x, qb.y, qb.z, __uint_as_float(q2[c * 32 + lane].x), K0, K1, K2);
+                poly_coeffs(mx, my, qa.z, qa.w, qb.x, qb.y, K0, K1, K2);
                 float *sp = reinterpret_cast<float *>(stg + (r >> 1) * 3) + (r & 1);
                 sp[0] = K0;
                 sp[2] = K1;
                 sp[4] = K2;
-                sp[6] = qb.x;
-                sp[8] = qb.y;
-                sp[10] = qb.z;
+                sp[6] = qa.z;
+                sp[8] = qa.w;
+                sp[10] = qb.x;
                 cl[r] = lane;
             }
             if (lane == 0 && (n & 1)) {
@@ -724,7 +729,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
                     const uint64_t M = pk(set_ge(tn.x, 1e-4f), set_ge(tn.y, 1e-4f));
                     float2 nw;
                     if (kKernel) {
-                        const float lo = __uint_as_float(q2[c * 32 + cl[i + k]].x);
+                        const float lo = q1[c * 32 + cl[i + k]].y;
                         nw = unpk(mul2(mul2(pk(-fast_exp2(e0 - lo), -fast_exp2(e1 - lo)), FL), M));
                     } else {
                         nw = unpk(mul2(mul2(NAL, PT), M));   // -alpha T, or 0 at the stop

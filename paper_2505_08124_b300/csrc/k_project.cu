@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
                                                  int64_t n, const uint32_t *__restrict__ orig_of_int,
                                                  uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
                                                  float4 *__restrict__ rec_a, float4 *__restrict__ rec_b,
+                                                 float *__restrict__ rec_t,
                                                  uint2 *__restrict__ rect, ViewCounters *ctr) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool visible = false;
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
         float tz = FA(FA(FA(FM(R[6], mo.x), FM(R[7], mo.y)), FM(R[8], mo.z)), c.t[2]);
         uint2 rc = make_uint2(0u, 0u);
         float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = make_float4(0.f, 0.f, 0.f, 0.f);
+        float rt = INFINITY;
         if (tz > c.near_z && tz < c.far_z) {
             float4 sa = cov_a[g];
             float2 sb = cov_b[g];
@@ -217,21 +219,27 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
                     rc = make_uint2(x0 | (x1 << 16), y0 | (y1 << 16));
                     // compositing record: the exponent of alpha in base 2 is
                     //   q2 + log2(o),  q2 = a' dx^2 + b' dx dy + c' dy^2  (d = mu' - pixel)
-                    // with (a', b', c') = log2(e) * (-A/2, -B, -C/2) for the conic (A, B, C);
-                    // (ex, ey): half extents of the alpha >= 1/255 ellipse q <= 2 ln(255 o)
-                    // (with a small safety margin), -inf when no pixel can reach the floor.
+                    // with (a', b', c') = log2(e) * (-A/2, -B, -C/2) for the conic (A, B, C).
+                    // For the compositing kernel's culling: the slopes r1 = -b'/2c', r2 = -b'/2a'
+                    // of the lines on which the concave q2 peaks along x and along y, and
+                    // t = the floor log2(1/255) less log2(o) and less a rounding margin of the
+                    // kernel's tile-local polynomial: 4e-6 S + 0.01 with S a bound on the size of
+                    // its terms. In any tile of the rectangle the tile-local mean is within r + 16
+                    // of the origin and pixel centres within 16 of it, which gives
+                    // S <= |log2 o| + (|a'| + |b'| + |c'|) (r + 32)^2.
                     const float kLog2e = 1.4426950408889634f;
                     const float inv = 1.f / det;
                     const float A = c11 * inv, B = -c01 * inv, C = c00 * inv;
                     const float op = mo.w;
-                    const float tau = 2.f * logf(255.f * op);
-                    float ex = -INFINITY, ey = -INFINITY;
-                    if (tau >= 0.f) {
-                        ex = sqrtf(tau * c00) * 1.001f + 0.01f;
-                        ey = sqrtf(tau * c11) * 1.001f + 0.01f;
-                    }
-                    ra = make_float4(px, py, -0.5f * kLog2e * A, -kLog2e * B);
-                    rb = make_float4(-0.5f * kLog2e * C, op > 0.f ? log2f(op) : -INFINITY, ex, ey);
+                    const float a2 = -0.5f * kLog2e * A, b2 = -kLog2e * B, c2 = -0.5f * kLog2e * C;
+                    const float lo = op > 0.f ? log2f(op) : -INFINITY;
+                    const float r1 = -b2 * __frcp_rn(2.f * c2), r2 = -b2 * __frcp_rn(2.f * a2);
+                    const float R = r + 32.f;
+                    const float S = fabsf(lo) + (fabsf(a2) + fabsf(b2) + fabsf(c2)) * R * R;
+                    const float thr = kLog2AlphaMin - fmaf(4e-6f, S, 0.01f);
+                    ra = make_float4(px, py, a2, b2);
+                    rb = make_float4(c2, lo, r1, r2);
+                    rt = lo > -INFINITY ? thr - lo : INFINITY;
                 }
             }
         }
@@ -240,6 +248,7 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
         dval[o] = (uint32_t)g;
         rec_a[g] = ra;
         rec_b[g] = rb;
+        rec_t[g] = rt;
         rect[g] = rc;
     }
     // one atomic per block (a counter shared by the whole grid)
@@ -328,9 +337,9 @@ void launch_pack_gaussians(const float *means, const float *scales, const float 
 
 void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *cov_a, const float2 *cov_b,
                     int64_t n, const uint32_t *orig_of_int, uint32_t *dkey_orig, uint32_t *dval_orig,
-                    float4 *rec_a, float4 *rec_b, uint2 *rect, ViewCounters *ctr, cudaStream_t st) {
+                    float4 *rec_a, float4 *rec_b, float *rec_t, uint2 *rect, ViewCounters *ctr, cudaStream_t st) {
     project_k<<<blocks_for(n, 256), 256, 0, st>>>(cam, mean_op, cov_a, cov_b, n, orig_of_int, dkey_orig,
-                                                  dval_orig, rec_a, rec_b, rect, ctr); note_launch();
+                                                  dval_orig, rec_a, rec_b, rec_t, rect, ctr); note_launch();
 }
 
 void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, ViewCounters *ctr, const uint2 *rect, uint2 *srect,

@@ -71,6 +71,7 @@ struct ViewSlot {
     // n-sized
     uint32_t *dkey[2] = {nullptr, nullptr}, *dval[2] = {nullptr, nullptr};
     float4 *rec_a = nullptr, *rec_b = nullptr;
+    float *rec_t = nullptr;
     uint2 *rect = nullptr, *srect = nullptr;
     uint32_t *stouched = nullptr, *offsets = nullptr;
     HashEntry *hash = nullptr;             // per-view (segment, weight) slots; consume clears them
@@ -477,7 +478,7 @@ slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
     CK(cudaMemsetAsync(vs.ctr, 0, sizeof(ViewCounters), st));
     span_begin(ctx, SLAG_STAGE_PROJECT, st);
     launch_project(cp, ctx->mean_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, vs.dkey[0], vs.dval[0],
-                   vs.rec_a, vs.rec_b, vs.rect, vs.ctr, st);
+                   vs.rec_a, vs.rec_b, vs.rec_t, vs.rect, vs.ctr, st);
     int shifts[8], widths[8];
     const int np = digit_passes(0, 32, shifts, widths, n);
     const bool alt = radix_sort_u32(vs.dkey[0], vs.dkey[1], vs.dval[0], vs.dval[1], n, shifts, widths, np,
@@ -560,7 +561,7 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
     cudaError_t e = cudaSuccess;
 #define SA(call) do { if (e == cudaSuccess) e = (call); } while (0)
     for (int b = 0; b < 2; ++b) { SA(dalloc(&vs.dkey[b], n)); SA(dalloc(&vs.dval[b], n)); }
-    SA(dalloc(&vs.rec_a, n)); SA(dalloc(&vs.rec_b, n));
+    SA(dalloc(&vs.rec_a, n)); SA(dalloc(&vs.rec_b, n)); SA(dalloc(&vs.rec_t, n));
     SA(dalloc(&vs.rect, n)); SA(dalloc(&vs.srect, n));
     SA(dalloc(&vs.stouched, n)); SA(dalloc(&vs.offsets, n));
     SA(dalloc(&vs.hash, n));
@@ -583,7 +584,7 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
 
 void slot_free(ViewSlot &vs) {
     for (int b = 0; b < 2; ++b) { dfree(vs.dkey[b]); dfree(vs.dval[b]); dfree(vs.pkey[b]); dfree(vs.pval[b]); }
-    dfree(vs.rec_a); dfree(vs.rec_b); dfree(vs.rect); dfree(vs.srect);
+    dfree(vs.rec_a); dfree(vs.rec_b); dfree(vs.rec_t); dfree(vs.rect); dfree(vs.srect);
     dfree(vs.stouched); dfree(vs.offsets); dfree(vs.hash);
     dfree(vs.prect); dfree(vs.ranges); dfree(vs.tile_order); dfree(vs.seg_buf); dfree(vs.ctr);
     dfree(vs.ctr_up); dfree(vs.recs); dfree(vs.rec_chunks); dfree(vs.rec_fill);
@@ -802,6 +803,7 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     a.prect = vs.prect;
     a.rec_a = vs.rec_a;
     a.rec_b = vs.rec_b;
+    a.rec_t = vs.rec_t;
     a.n_ids = (uint32_t)ctx->n;
     a.seg = vs.seg_buf;
     a.view_base = (int32_t)vs.view_base;
@@ -2361,6 +2363,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     a.prect = vs.prect;
     a.rec_a = vs.rec_a;
     a.rec_b = vs.rec_b;
+    a.rec_t = vs.rec_t;
     a.n_ids = (uint32_t)ctx->n;
     a.weight_mode = ctx->weight_mode;
     a.ctr = vs.ctr;
@@ -2435,6 +2438,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.prect = vs.prect;
     a.rec_a = vs.rec_a;
     a.rec_b = vs.rec_b;
+    a.rec_t = vs.rec_t;
     a.n_ids = (uint32_t)ctx->n;
     a.seg = nullptr;
     a.weight_mode = ctx->weight_mode;

@@ -58,6 +58,7 @@ uint32_t checks_take_composite(cudaStream_t st);
 uint32_t checks_take_aggregate(cudaStream_t st);
 
 constexpr int kTile = 16;          // screen tile edge in pixels
+constexpr float kLog2AlphaMin = -7.99435343685886f;   // log2 of the alpha floor 1/255
 constexpr int kBlockG = 128;       // Gaussians per aggregation block (key packs g & 127)
 constexpr int kHashSlots = 4;      // per-view (segment, weight) slots per Gaussian
 constexpr int kSuperShift = 2;     // compositing lists are binned per 4x4-tile super-tile
@@ -163,7 +164,7 @@ void launch_pack_gaussians(const float *means, const float *scales, const float 
                            cudaStream_t st);
 void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *cov_a,
                     const float2 *cov_b, int64_t n, const uint32_t *orig_of_int, uint32_t *dkey_orig,
-                    uint32_t *dval_orig, float4 *rec_a, float4 *rec_b, uint2 *rect,
+                    uint32_t *dval_orig, float4 *rec_a, float4 *rec_b, float *rec_t, uint2 *rect,
                     ViewCounters *ctr, cudaStream_t st);
 // Rectangles and bin counts in depth-rank order. With shift s > 0 the count is of
 // 2^s x 2^s-tile super-tiles; the tile-pair total goes to ctr->P_tiles.
@@ -252,7 +253,8 @@ struct CompositeArgs {
     const uint32_t *tile_order;    // CTAs of tile_order[i] come i-th
     const uint32_t *list;          // sorted pairs' values: the internal index of each pair's Gaussian
     const uint2 *prect;            // tile rectangle of the Gaussian of each sorted pair
-    const float4 *rec_a, *rec_b;   // records in internal order
+    const float4 *rec_a, *rec_b;   // records in internal order: (mu'x, mu'y, a', b'), (c', log2 o, r1, r2)
+    const float *rec_t;            // and the culling threshold t of each (k_project.cu)
     uint32_t n_ids;                // Gaussians (records in rec_a / rec_b)
     const int32_t *seg;            // H x W
     int32_t view_base;             // column of segment 0 of this view
