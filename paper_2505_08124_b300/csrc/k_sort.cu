@@ -2,7 +2,7 @@
 //
 // Radix sort, one pass per digit of <= 11 bits (256, 512, 1024 or 2048 bins), three
 // kernels per pass, over tiles of 256 x ITEMS items (ITEMS = 16, or 4 below
-// ~2M items so that the grid still covers the GPU):
+// ~1M items so that the grid still covers the GPU):
 //   1. rs_hist:    each CTA counts the digits of its tile into per-warp
 //                  shared histograms (one add per distinct digit of a warp
 //                  round); writes hist[digit][tile] and adds the digit totals.
@@ -29,6 +29,7 @@ constexpr int kThreads = 256;
 constexpr int kItems = 16;
 constexpr int kTileItems = kThreads * kItems;   // 4096
 constexpr int kWarps = kThreads / 32;
+constexpr int64_t kSmallSort = 1 << 20;         // sorts of fewer items use 1024-item tiles
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -242,15 +243,31 @@ __device__ __forceinline__ void scatter_tile(K (&key)[ITEMS], uint32_t (&val)[IT
     __syncthreads();
     const int64_t rem = n - tile_base;
     const int tile_n = rem < kTileN ? (int)rem : kTileN;
-    for (int j = tid; j < tile_n; j += kThreads) {
-        const K k = skeys[j];
-        const uint32_t d = (uint32_t)(k >> shift) & mask;
-        const uint32_t gp = gbase[d] + (uint32_t)j - lstart[d];
-        if (!SLAG_IN_BOUNDS((int64_t)gp < n, kCheckSort)) continue;
-        if (kout) kout[gp] = k;
-        const uint32_t v = svals[j];
-        vout[gp] = vmap ? vmap[v] : v;   // optionally written through a map of the values
-        if (gout) gout[gp] = gsrc[v];   // a payload that follows the values (gathered by value)
+    // each thread's ITEMS outputs: the gathers of all of them are issued before any store
+    uint32_t gpo[ITEMS], vo[ITEMS];
+    uint2 po[ITEMS];
+#pragma unroll
+    for (int q = 0; q < ITEMS; ++q) {
+        const int j = tid + q * kThreads;
+        gpo[q] = 0xffffffffu;
+        if (j < tile_n) {
+            const K k = skeys[j];
+            const uint32_t d = (uint32_t)(k >> shift) & mask;
+            const uint32_t gp = gbase[d] + (uint32_t)j - lstart[d];
+            if (SLAG_IN_BOUNDS((int64_t)gp < n, kCheckSort)) {
+                gpo[q] = gp;
+                if (kout) kout[gp] = k;
+                const uint32_t v = svals[j];
+                vo[q] = vmap ? vmap[v] : v;   // optionally written through a map of the values
+                if (gout) po[q] = gsrc[v];    // a payload that follows the values (gathered by value)
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < ITEMS; ++q) {
+        if (gpo[q] == 0xffffffffu) continue;
+        vout[gpo[q]] = vo[q];
+        if (gout) gout[gpo[q]] = po[q];
     }
 }
 
@@ -404,7 +421,7 @@ void radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, int64_t n,
     note_launch();
 }
 
-// Inputs below ~2M items use 1024-item tiles so that the grid still covers the GPU;
+// Inputs below ~1M items use 1024-item tiles so that the grid still covers the GPU;
 // a pass of w bits uses the smallest of 256, 512, 1024 and 2048 bins that holds its digits
 // (fewer bins: smaller per-tile histograms to clear, write and scan).
 template <typename K>
@@ -412,7 +429,7 @@ bool radix_sort_impl(K *keys, K *keys_alt, uint32_t *vals, uint32_t *vals_alt, i
                      const int *widths, int npass, SortScratch &s, cudaStream_t st, uint2 *ranges, int nranges,
                      const uint2 *gsrc = nullptr, uint2 *gout = nullptr, const uint32_t *vmap = nullptr) {
     if (n <= 0 || npass <= 0) return false;
-    const bool small = n < (1 << 21);
+    const bool small = n < kSmallSort;
     K *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < npass; ++p) {
@@ -543,10 +560,10 @@ __global__ void __launch_bounds__(kThreads) scan_tiles(const uint32_t *__restric
 
 cudaError_t scratch_reserve(SortScratch &s, int64_t n) {
     // 2048 bins x the largest tile count of a sort of at most n items: 1024-item tiles below
-    // 2M items (up to 2049 tiles), kTileItems-item tiles above, so the count is not monotonic
+    // ~1M items (up to 1025 tiles), kTileItems-item tiles above, so the count is not monotonic
     // in the size and a reservation for n must cover every smaller sort too
-    const int64_t small_max = n < (1 << 21) ? (n + 1023) / 1024 + 1 : ((1 << 21) - 1 + 1023) / 1024 + 1;
-    const int64_t large = n < (1 << 21) ? 0 : (n + kTileItems - 1) / kTileItems + 1;
+    const int64_t small_max = n < kSmallSort ? (n + 1023) / 1024 + 1 : (kSmallSort - 1 + 1023) / 1024 + 1;
+    const int64_t large = n < kSmallSort ? 0 : (n + kTileItems - 1) / kTileItems + 1;
     const int64_t tiles = small_max > large ? small_max : large;
     size_t need_hist = (size_t)2048 * tiles;
     if (!s.digit_tot) {
