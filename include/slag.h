@@ -124,9 +124,11 @@ typedef struct {
 } slag_options;
 
 /* Counters of the views added since create / reset. views and columns count
- * every accepted view; pairs and last_pairs count the views whose second half
- * is queued (all of them after a finalize); contributions, triples,
- * last_contributions, evaluations and executed are read at finalize. */
+ * every accepted view; pairs, last_pairs and resized_views count the views
+ * whose pair count the host has read (all of them after a finalize); a view
+ * sized on the device is read when its slot is reused or the views are
+ * joined; contributions, triples, last_contributions, evaluations and
+ * executed are read at finalize. */
 typedef struct {
     int64_t views;           /* views added since create / reset */
     int64_t pairs;           /* sum over views of Gaussian-tile pairs P */
@@ -144,6 +146,8 @@ typedef struct {
                                 compositing kernel carried out: a group of 64 pixels evaluates
                                 the Gaussians that can reach alpha >= 1/255 somewhere in it,
                                 for all 64 pixels; read at finalize */
+    int64_t resized_views;   /* views sized on the device whose pairs exceeded the capacity of
+                                their binning, binned again with their exact count */
 } slag_stats;
 
 /* Create a context over the Gaussian set (Method, Rasterizer_SLAG statement:

@@ -485,6 +485,7 @@ template <bool kKernel, bool kDebug>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const CompositeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    if (a.skip && *a.skip) return;   // the view is not composited (uniform, before any barrier)
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int tile = (int)a.tile_order[blockIdx.x];
     const int tx = tile % a.cam.tiles_x, ty = tile / a.cam.tiles_x;

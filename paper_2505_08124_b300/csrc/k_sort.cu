@@ -303,30 +303,52 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const K *__restrict__ kin
 // tiles (kTileItems consecutive pairs) generate their own pairs from the rectangles, so the
 // emitted pair list is never written or read back.
 
-// The Gaussian whose pairs hold the first pair of each tile: tstart[t] for t < ntiles. In the
-// checked build, pairs beyond P (a capacity below the view's pair count) are refused here.
+// The sizes of a fused binning, read on the device (so that the host need not wait for the
+// stage that counts them): nv visible Gaussians and P pairs. The pass holds at most cap pairs;
+// a larger P sets *overflow and leaves every bin empty, or, with truncate (checked builds'
+// forced capacities), keeps the first cap pairs.
+struct BinCounts {
+    const uint32_t *nv;
+    const unsigned long long *P;
+    int64_t cap;
+    int truncate;
+    uint32_t *overflow;
+};
+
+__device__ __forceinline__ int64_t pairs_held(const BinCounts &c) {
+    const unsigned long long p = *c.P;
+    if (p <= (unsigned long long)c.cap) return (int64_t)p;
+    return c.truncate ? c.cap : 0;
+}
+
+// The Gaussian whose pairs hold the first pair of each tile: tstart[t] for t < the tiles of the
+// pairs held. In the checked build, pairs beyond a forced capacity are refused here.
 __global__ void __launch_bounds__(256) tile_starts_k(const uint32_t *__restrict__ offsets,
-                                                     const uint32_t *__restrict__ counts, uint32_t nv, int64_t P,
-                                                     int ntiles, uint32_t *__restrict__ tstart) {
+                                                     const uint32_t *__restrict__ counts, const BinCounts c,
+                                                     uint32_t *__restrict__ tstart) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t P = pairs_held(c);
+    if (r == 0 && !c.truncate && c.overflow && *c.P > (unsigned long long)c.cap) *c.overflow = 1u;
+    const uint32_t nv = *c.nv;
     if (r >= nv) return;
+    const int64_t ntiles = (P + kTileItems - 1) / kTileItems;
     const int64_t off = offsets[r], cnt = counts[r];
-    if (r == (int64_t)nv - 1) (void)SLAG_IN_BOUNDS(off + cnt <= P, kCheckEmit);
+    if (r == (int64_t)nv - 1) (void)SLAG_IN_BOUNDS(off + cnt <= P || !c.truncate, kCheckEmit);
     if (cnt == 0) return;
     for (int64_t t = (off + kTileItems - 1) / kTileItems; t * kTileItems < off + cnt && t < ntiles; ++t)
         tstart[t] = (uint32_t)r;
 }
 
-// Calls f(j, bin, r) for every pair of this CTA's tile: j = its place in the tile, r = its
-// Gaussian's depth rank. Threads take the tile's Gaussians in turn.
+// Calls f(j, bin, r) for every pair of this CTA's tile (below P, of ntiles tiles): j = its place
+// in the tile, r = its Gaussian's depth rank. Threads take the tile's Gaussians in turn.
 template <typename F>
 __device__ __forceinline__ void for_tile_pairs(const uint2 *__restrict__ srect, const uint32_t *__restrict__ offsets,
                                                const uint32_t *__restrict__ tstart, uint32_t nv, int64_t P,
-                                               int ntiles, int shift, int bins_x, F f) {
+                                               int64_t ntiles, int shift, int bins_x, F f) {
     const int64_t P0 = (int64_t)blockIdx.x * kTileItems;
     const int64_t P1 = P0 + kTileItems < P ? P0 + kTileItems : P;
     const uint32_t r_lo = tstart[blockIdx.x];
-    const uint32_t r_hi = (int)blockIdx.x + 1 < ntiles ? tstart[blockIdx.x + 1] : nv - 1u;
+    const uint32_t r_hi = (int64_t)blockIdx.x + 1 < ntiles ? tstart[blockIdx.x + 1] : nv - 1u;
     for (uint32_t r = r_lo + threadIdx.x; r <= r_hi; r += kThreads) {
         const uint2 rc = srect[r];
         const uint32_t x0 = (rc.x & 0xffffu) >> shift, x1 = (((rc.x >> 16) - 1u) >> shift) + 1u;
@@ -348,29 +370,34 @@ __device__ __forceinline__ void for_tile_pairs(const uint2 *__restrict__ srect, 
     }
 }
 
-// Per tile: the count of each bin among its pairs, to hist[bin][tile] (the layout of rs_hist).
+// Per tile: the count of each bin among its pairs, to hist[bin][tile] (the layout of rs_hist,
+// ntiles_cap tiles; the tiles beyond the pairs held count nothing).
 template <int BINS>
 __global__ void __launch_bounds__(kThreads) bin_hist_k(const uint2 *__restrict__ srect,
                                                        const uint32_t *__restrict__ offsets,
-                                                       const uint32_t *__restrict__ tstart, uint32_t nv, int64_t P,
-                                                       int ntiles, int shift, int bins_x,
+                                                       const uint32_t *__restrict__ tstart, const BinCounts c,
+                                                       int ntiles_cap, int shift, int bins_x,
                                                        uint32_t *__restrict__ hist) {
     __shared__ uint32_t h[BINS];
     for (int d = threadIdx.x; d < BINS; d += kThreads) h[d] = 0;
+    const int64_t P = pairs_held(c);
+    const int64_t ntiles = (P + kTileItems - 1) / kTileItems;
     __syncthreads();
-    for_tile_pairs(srect, offsets, tstart, nv, P, ntiles, shift, bins_x,
-                   [&](int, uint32_t bin, uint32_t) { atomicAdd(&h[bin], 1u); });
+    if ((int64_t)blockIdx.x < ntiles)
+        for_tile_pairs(srect, offsets, tstart, *c.nv, P, ntiles, shift, bins_x,
+                       [&](int, uint32_t bin, uint32_t) { atomicAdd(&h[bin], 1u); });
     __syncthreads();
-    for (int d = threadIdx.x; d < BINS; d += kThreads) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+    for (int d = threadIdx.x; d < BINS; d += kThreads) hist[(int64_t)d * ntiles_cap + blockIdx.x] = h[d];
 }
 
 // Per tile: its pairs, generated into the staging arrays in emission order, then scattered
 // stably by bin (scatter_tile); values leave as vmap[rank], with the Gaussian's tile rectangle.
+// Block 0 always runs: it writes every bin's range.
 template <int BINS>
 __global__ void __launch_bounds__(kThreads) bin_place_k(const uint2 *__restrict__ srect,
                                                         const uint32_t *__restrict__ offsets,
-                                                        const uint32_t *__restrict__ tstart, uint32_t nv, int64_t P,
-                                                        int ntiles, int shift, int bins_x, uint32_t mask, int width,
+                                                        const uint32_t *__restrict__ tstart, const BinCounts c,
+                                                        int ntiles_cap, int shift, int bins_x, uint32_t mask, int width,
                                                         const uint32_t *__restrict__ offs,
                                                         const uint32_t *__restrict__ digit_tot,
                                                         uint2 *__restrict__ ranges, int nranges,
@@ -378,12 +405,16 @@ __global__ void __launch_bounds__(kThreads) bin_place_k(const uint2 *__restrict_
                                                         const uint32_t *__restrict__ vmap,
                                                         uint32_t *__restrict__ vout) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t P = pairs_held(c);
+    const int64_t ntiles = (P + kTileItems - 1) / kTileItems;
+    if (blockIdx.x > 0 && (int64_t)blockIdx.x >= ntiles) return;   // (uniform per CTA)
     uint32_t *skeys = reinterpret_cast<uint32_t *>(smem_raw) + (kWarps + 2) * BINS + 16;
     uint32_t *svals = skeys + kTileItems;
-    for_tile_pairs(srect, offsets, tstart, nv, P, ntiles, shift, bins_x, [&](int j, uint32_t bin, uint32_t r) {
-        skeys[j] = bin;
-        svals[j] = r;
-    });
+    if ((int64_t)blockIdx.x < ntiles)
+        for_tile_pairs(srect, offsets, tstart, *c.nv, P, ntiles, shift, bins_x, [&](int j, uint32_t bin, uint32_t r) {
+            skeys[j] = bin;
+            svals[j] = r;
+        });
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tile_base = (int64_t)blockIdx.x * kTileItems;
@@ -395,8 +426,8 @@ __global__ void __launch_bounds__(kThreads) bin_place_k(const uint2 *__restrict_
         key[r] = valid ? skeys[j] : 0u;
         val[r] = valid ? svals[j] : 0u;
     }
-    scatter_tile<uint32_t, kItems, BINS>(key, val, smem_raw, nullptr, vout, P, 0, mask, width, offs, digit_tot, ntiles,
-                                         ranges, nranges, rect_src, rect_out, vmap);
+    scatter_tile<uint32_t, kItems, BINS>(key, val, smem_raw, nullptr, vout, P, 0, mask, width, offs, digit_tot,
+                                         ntiles_cap, ranges, nranges, rect_src, rect_out, vmap);
 }
 
 template <typename K, int ITEMS, int BINS>
@@ -637,10 +668,10 @@ bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t
 namespace {
 
 template <int BINS>
-void bin_sort_fused_impl(const uint2 *srect, const uint32_t *offsets, const uint32_t *counts, uint32_t n_visible,
-                         int64_t P, int shift, int bins_x, int bins, const uint32_t *val_map, uint32_t *vals_out,
-                         uint2 *rect_out, uint2 *ranges, SortScratch &s, cudaStream_t st) {
-    const int ntiles = (int)((P + kTileItems - 1) / kTileItems);
+void bin_sort_fused_impl(const uint2 *srect, const uint32_t *offsets, const uint32_t *counts, int64_t n_cap,
+                         const BinCounts &c, int shift, int bins_x, int bins, const uint32_t *val_map,
+                         uint32_t *vals_out, uint2 *rect_out, uint2 *ranges, SortScratch &s, cudaStream_t st) {
+    const int ntiles_cap = (int)((c.cap + kTileItems - 1) / kTileItems);
     const size_t smem = scatter_smem<uint32_t, kItems, BINS>();
     // on failure the error stays recorded for the caller's cudaGetLastError check
     if (set_max_smem((const void *)bin_place_k<BINS>, (int)smem) != cudaSuccess) return;
@@ -648,37 +679,39 @@ void bin_sort_fused_impl(const uint2 *srect, const uint32_t *offsets, const uint
     while ((1 << width) < bins) ++width;
     if (width == 0) width = 1;
     const uint32_t mask = (1u << width) - 1u;
-    tile_starts_k<<<(n_visible + 255) / 256, 256, 0, st>>>(offsets, counts, n_visible, P, ntiles, s.tstart);
+    tile_starts_k<<<(unsigned)((n_cap + 255) / 256), 256, 0, st>>>(offsets, counts, c, s.tstart);
     note_launch();
-    bin_hist_k<BINS><<<ntiles, kThreads, 0, st>>>(srect, offsets, s.tstart, n_visible, P, ntiles, shift, bins_x,
-                                                   s.hist);
+    bin_hist_k<BINS><<<ntiles_cap, kThreads, 0, st>>>(srect, offsets, s.tstart, c, ntiles_cap, shift, bins_x, s.hist);
     note_launch();
-    rs_offsets<<<BINS, ntiles >= 1024 ? 1024 : (ntiles >= 256 ? 256 : 64), 0, st>>>(s.hist, s.digit_tot, ntiles);
+    rs_offsets<<<BINS, ntiles_cap >= 1024 ? 1024 : (ntiles_cap >= 256 ? 256 : 64), 0, st>>>(s.hist, s.digit_tot,
+                                                                                          ntiles_cap);
     note_launch();
-    bin_place_k<BINS><<<ntiles, kThreads, smem, st>>>(srect, offsets, s.tstart, n_visible, P, ntiles, shift, bins_x,
-                                                      mask, width, s.hist, s.digit_tot, ranges, bins, srect, rect_out,
-                                                      val_map, vals_out);
+    bin_place_k<BINS><<<ntiles_cap, kThreads, smem, st>>>(srect, offsets, s.tstart, c, ntiles_cap, shift, bins_x, mask,
+                                                          width, s.hist, s.digit_tot, ranges, bins, srect, rect_out,
+                                                          val_map, vals_out);
     note_launch();
 }
 
 }  // namespace
 
-bool bin_sort_fused(const uint2 *srect, const uint32_t *offsets, const uint32_t *counts, uint32_t n_visible,
-                    int64_t P, int shift, int bins_x, int bins, const uint32_t *val_map, uint32_t *vals_out,
-                    uint2 *rect_out, uint2 *ranges, SortScratch &s, cudaStream_t st) {
-    if (P <= 0 || n_visible == 0 || bins < 1 || bins > 2048) return false;
+bool bin_sort_fused(const uint2 *srect, const uint32_t *offsets, const uint32_t *counts, int64_t n_cap,
+                    const uint32_t *d_nv, const unsigned long long *d_P, int64_t cap, int truncate,
+                    uint32_t *d_overflow, int shift, int bins_x, int bins, const uint32_t *val_map,
+                    uint32_t *vals_out, uint2 *rect_out, uint2 *ranges, SortScratch &s, cudaStream_t st) {
+    if (cap <= 0 || n_cap <= 0 || bins < 1 || bins > 2048) return false;
+    const BinCounts c{d_nv, d_P, cap, truncate, d_overflow};
     if (bins <= 256)
-        bin_sort_fused_impl<256>(srect, offsets, counts, n_visible, P, shift, bins_x, bins, val_map, vals_out,
-                                 rect_out, ranges, s, st);
+        bin_sort_fused_impl<256>(srect, offsets, counts, n_cap, c, shift, bins_x, bins, val_map, vals_out, rect_out,
+                                 ranges, s, st);
     else if (bins <= 512)
-        bin_sort_fused_impl<512>(srect, offsets, counts, n_visible, P, shift, bins_x, bins, val_map, vals_out,
-                                 rect_out, ranges, s, st);
+        bin_sort_fused_impl<512>(srect, offsets, counts, n_cap, c, shift, bins_x, bins, val_map, vals_out, rect_out,
+                                 ranges, s, st);
     else if (bins <= 1024)
-        bin_sort_fused_impl<1024>(srect, offsets, counts, n_visible, P, shift, bins_x, bins, val_map, vals_out,
-                                  rect_out, ranges, s, st);
+        bin_sort_fused_impl<1024>(srect, offsets, counts, n_cap, c, shift, bins_x, bins, val_map, vals_out, rect_out,
+                                  ranges, s, st);
     else
-        bin_sort_fused_impl<2048>(srect, offsets, counts, n_visible, P, shift, bins_x, bins, val_map, vals_out,
-                                  rect_out, ranges, s, st);
+        bin_sort_fused_impl<2048>(srect, offsets, counts, n_cap, c, shift, bins_x, bins, val_map, vals_out, rect_out,
+                                  ranges, s, st);
     return true;
 }
 

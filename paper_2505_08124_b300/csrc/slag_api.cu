@@ -102,12 +102,16 @@ struct ViewSlot {
     const uint32_t *sgid = nullptr;        // internal ids in depth order (stage A's output)
     CamParams cp{};                        // the view's camera
     int64_t view_base = 0;                 // its first column in the segment-embedding store
+    cudaStream_t front = nullptr;          // the slot's stages A and B (high priority)
+    SortScratch scratch;                   // their sorts and scans
+    cudaEvent_t ev_front = nullptr;        // the front stream at a join
     cudaStream_t back = nullptr;
     cudaEvent_t ev_a = nullptr;            // stage A of the slot's view done
     cudaEvent_t ev_up = nullptr;           // the view's uploads and segment-id check done
     cudaEvent_t ev_bin = nullptr;          // stage B of the slot's view done
     cudaEvent_t ev_done = nullptr;         // back work of the slot's view done
     int64_t log_bound = 0;                 // triples the slot's view may append after stage A
+    bool pending = false;                  // its view was sized on the device and is not settled
 };
 
 }  // namespace
@@ -131,16 +135,14 @@ struct slag_ctx {
 
     // views in flight
     ViewSlot slot[kSlots];
-    cudaStream_t front = nullptr;            // stage A of every view: projection to tile-count scan
-    cudaStream_t front_b = nullptr;          // stage B: pair emission, bin sort, tile order
     cudaEvent_t ev_in = nullptr;             // caller's stream at the start of a call
     cudaStream_t up = nullptr;               // uploads of a view's inputs and their check
-    cudaEvent_t ev_front = nullptr;          // front stream at a join
-    cudaEvent_t ev_front_b = nullptr;        // stage-B stream at a join
     cudaEvent_t ev_consumed = nullptr;       // the last enqueued consume
     int64_t views_enqueued = 0;              // views accepted since create / reset (slot = count % kSlots)
     bool deferred = false;                   // the last accepted view's stage B and back half wait
                                              // for the next call
+    int64_t est_P = 0, est_P_tiles = 0;      // the largest pair counts seen (device-sized views)
+    int64_t log_fill_seen = 0;               // the triple log's fill level, as last read
     float *s_hi = nullptr, *s_lo = nullptr, *s_ovf = nullptr;
     float *dbg_T = nullptr, *dbg_wsum = nullptr;
     int32_t *dbg_count = nullptr;
@@ -253,8 +255,7 @@ struct slag_ctx {
     int32_t *qcount = nullptr;
     int64_t qout_cap = 0;
 
-    SortScratch scratch;                     // stage A, finalize, queries (caller's or front stream)
-    SortScratch scratch_b;                   // stage B (its own stream)
+    SortScratch scratch;                     // finalize, queries, diagnostics (the caller's stream)
     slag_stats stats{};
 
     // per-stage timing
@@ -441,19 +442,20 @@ slag_status checks_reported(slag_ctx *ctx) {
 
 // The caller's stream waits for every view in flight and for both front streams.
 cudaError_t join_views(slag_ctx *ctx) {
-    cudaError_t e = cudaEventRecord(ctx->ev_front, ctx->front);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_front, 0);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_front_b, ctx->front_b);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_front_b, 0);
-    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->stream, ctx->slot[i].ev_done, 0);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) {
+        ViewSlot &vs = ctx->slot[i];
+        e = cudaEventRecord(vs.ev_front, vs.front);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, vs.ev_front, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, vs.ev_done, 0);
+    }
     return e;
 }
 
 // Host waits for every internal stream of the views (the caller's stream is not waited for).
 cudaError_t drain_views(slag_ctx *ctx) {
-    cudaError_t e = cudaStreamSynchronize(ctx->front);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->front_b);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->up);
+    cudaError_t e = cudaStreamSynchronize(ctx->up);
+    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaStreamSynchronize(ctx->slot[i].front);
     for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaStreamSynchronize(ctx->slot[i].back);
     return e;
 }
@@ -473,7 +475,8 @@ int ceil_log2(uint64_t v) {
 // per-Gaussian tile counts (Method: the rasterizer's per-view preprocessing). Reads neither
 // the segment map nor the table. The counters and the log's fill level are copied to the
 // slot's mapped host struct; the host reads them once the stage has ended.
-slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int shift) {
+slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int shift,
+                    SortScratch &scr) {
     const int64_t n = ctx->n;
     CK(cudaMemsetAsync(vs.ctr, 0, sizeof(ViewCounters), st));
     span_begin(ctx, SLAG_STAGE_PROJECT, st);
@@ -482,10 +485,10 @@ slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
     int shifts[8], widths[8];
     const int np = digit_passes(0, 32, shifts, widths, n);
     const bool alt = radix_sort_u32(vs.dkey[0], vs.dkey[1], vs.dval[0], vs.dval[1], n, shifts, widths, np,
-                                    ctx->scratch, st);
+                                    scr, st);
     vs.sgid = vs.dval[alt ? 1 : 0];
     launch_gather_sorted(vs.sgid, n, vs.ctr, vs.rect, vs.srect, vs.stouched, shift, st);
-    exclusive_scan_u32(vs.stouched, vs.offsets, n, &vs.ctr->P, ctx->scratch, st);
+    exclusive_scan_u32(vs.stouched, vs.offsets, n, &vs.ctr->P, scr, st);
     span_end(ctx, st);
     launch_copy_words(vs.ctr, &vs.h_dev->v, sizeof(ViewCounters), st);
     launch_copy_words(ctx->totals, vs.h_dev->totals, kTotals * sizeof(unsigned long long), st);
@@ -524,8 +527,9 @@ slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
     uint32_t *list = vs.pval[0];
     if (P == 0) {
         CK(cudaMemsetAsync(vs.ranges, 0, sizeof(uint2) * (size_t)bins, st));
-    } else if (!bin_sort_fused(vs.srect, vs.offsets, vs.stouched, nv, P, shift, bins_x, (int)bins, vs.sgid, list,
-                               shift > 0 ? vs.prect : nullptr, vs.ranges, scr, st)) {
+    } else if (!bin_sort_fused(vs.srect, vs.offsets, vs.stouched, nv, &vs.ctr->n_visible, &vs.ctr->P, P,
+                               P < (int64_t)vs.h->v.P ? 1 : 0, &vs.ctr->overflow, shift, bins_x, (int)bins,
+                               vs.sgid, list, shift > 0 ? vs.prect : nullptr, vs.ranges, scr, st)) {
         // more than 2048 bins: emit the pairs, then a radix sort of them by bin
         launch_emit(vs.srect, vs.offsets, nv, shift, bins_x, P, vs.pkey[0], vs.pval[0], st);
         int shifts[8], widths[8];
@@ -549,7 +553,7 @@ slag_status stage_b(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParam
 // Both stages in one stream with a host sync between them (the diagnostic entry points).
 slag_status bin_view(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int64_t *P_out,
                      uint32_t **list_out, int shift) {
-    slag_status s = stage_a(ctx, vs, st, cp, shift);
+    slag_status s = stage_a(ctx, vs, st, cp, shift, ctx->scratch);
     if (s != SLAG_OK) return s;
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
@@ -573,6 +577,9 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
     int lo = 0, hi = 0;
     SA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     SA(cudaStreamCreateWithPriority(&vs.back, cudaStreamNonBlocking, lo));
+    SA(cudaStreamCreateWithPriority(&vs.front, cudaStreamNonBlocking, hi));
+    SA(cudaEventCreateWithFlags(&vs.ev_front, cudaEventDisableTiming));
+    SA(scratch_reserve(vs.scratch, n));
     SA(cudaEventCreateWithFlags(&vs.ev_a, cudaEventDisableTiming));
     SA(cudaEventCreateWithFlags(&vs.ev_up, cudaEventDisableTiming));
     SA(cudaEventCreateWithFlags(&vs.ev_bin, cudaEventDisableTiming));
@@ -591,7 +598,10 @@ void slot_free(ViewSlot &vs) {
     if (vs.h) cudaFreeHost(vs.h);
     vs.h = nullptr;
     if (vs.back) cudaStreamDestroy(vs.back);
-    for (cudaEvent_t *e : {&vs.ev_a, &vs.ev_up, &vs.ev_bin, &vs.ev_done}) {
+    if (vs.front) cudaStreamDestroy(vs.front);
+    vs.front = nullptr;
+    scratch_free(vs.scratch);
+    for (cudaEvent_t *e : {&vs.ev_a, &vs.ev_up, &vs.ev_bin, &vs.ev_done, &vs.ev_front}) {
         if (*e) cudaEventDestroy(*e);
         *e = nullptr;
     }
@@ -661,15 +671,11 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     {
         int lo = 0, hi = 0;
         CA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        CA(cudaStreamCreateWithPriority(&ctx->front, cudaStreamNonBlocking, hi));
-        CA(cudaStreamCreateWithPriority(&ctx->front_b, cudaStreamNonBlocking, hi));
         // the segment-id check runs here and slag_add_view waits for it: it must not queue
         // behind the composites' CTAs
         CA(cudaStreamCreateWithPriority(&ctx->up, cudaStreamNonBlocking, hi));
     }
     CA(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
-    CA(cudaEventCreateWithFlags(&ctx->ev_front, cudaEventDisableTiming));
-    CA(cudaEventCreateWithFlags(&ctx->ev_front_b, cudaEventDisableTiming));
     CA(cudaEventCreateWithFlags(&ctx->ev_consumed, cudaEventDisableTiming));
     CA(cudaStreamCreateWithFlags(&ctx->qstream, cudaStreamNonBlocking));
     CA(cudaEventCreateWithFlags(&ctx->qev_in, cudaEventDisableTiming));
@@ -684,7 +690,6 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
     CA(cudaMemsetAsync(vctr, 0, sizeof(ViewCounters), st));
     CA(cudaMemsetAsync(ctx->totals, 0, kTotals * sizeof(unsigned long long), st));
     CA(scratch_reserve(ctx->scratch, n));
-    CA(scratch_reserve(ctx->scratch_b, n));
 
     // validation
     launch_check_gaussians(im, is, iq, io, n, &vctr->bad_seg, st);
@@ -732,35 +737,23 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
 
 namespace {
 
-// The second half of the last accepted view: stage B on its own stream once stage A's counters
-// are on the host, then the composite, the combine pass and the consume pass on the slot's back
-// stream. It runs in the next call (the next view's slag_add_view, or any call that joins the
-// views), so that stage A of the next view is already queued while the host waits for this
-// view's counters: the front streams never idle on a host round trip.
-slag_status launch_deferred_view(slag_ctx *ctx) {
-    if (!ctx->deferred) return SLAG_OK;
-    ctx->deferred = false;
-    ViewSlot &vs = ctx->slot[(ctx->views_enqueued - 1) % kSlots];
+// The back half of a view whose binning is queued (ev_bin): room in the triple log and in the
+// record list, then the composite, the combine pass and the consume pass on the slot's back
+// stream, and a copy of the view's counters and the log's fill level to the slot's mapped host
+// struct at its end. P_tiles bounds the view's Gaussian-tile pairs (exact, or an estimate for a
+// view sized on the device); a non-null skip makes the three passes do nothing when *skip is set.
+slag_status queue_back_half(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list, int64_t P_tiles,
+                            const uint32_t *skip) {
     const CamParams &cp = vs.cp;
-    CK(cudaEventSynchronize(vs.ev_a));
-    CK(cudaGetLastError());
-    spans_resolve(ctx, false);
-    cudaStream_t fb = ctx->front_b;
-    CK(cudaStreamWaitEvent(fb, vs.ev_a, 0));
-    int64_t P = 0;
-    uint32_t *list = nullptr;
-    slag_status s = stage_b(ctx, vs, fb, cp, kSuperShift, ctx->scratch_b, &P, &list);
-    if (s != SLAG_OK) return s;
-    CK(cudaEventRecord(vs.ev_bin, fb));
-
-    // room in the triple log: its fill level when stage A ended, plus what the other views in
-    // flight may still append, plus this view's bound (at most kHashSlots per Gaussian from
-    // the consume pass and the composite's overflow appends)
-    vs.log_bound = ctx->n * kHashSlots + 2 * (int64_t)vs.h->v.P_tiles + (1 << 20);
+    cudaStream_t fb = vs.front;
+    // room in the triple log: its fill level as last seen, plus what the other views in flight
+    // may still append, plus this view's bound (at most kHashSlots per Gaussian from the consume
+    // pass and the composite's overflow appends)
+    vs.log_bound = ctx->n * kHashSlots + 2 * P_tiles + (1 << 20);
     int64_t others = 0;
     for (int i = 0; i < kSlots; ++i)
         if (&ctx->slot[i] != &vs) others += ctx->slot[i].log_bound;
-    if ((int64_t)vs.h->totals[0] + others + vs.log_bound > ctx->log_cap) {
+    if (ctx->log_fill_seen + others + vs.log_bound > ctx->log_cap) {
         // no view may append while the log moves: wait for all, then read the exact
         // fill level; the new capacity keeps room for a full pipeline of views, so
         // that the next views pass this test without waiting
@@ -768,6 +761,7 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
         launch_copy_words(ctx->totals, vs.h_dev->totals, kTotals * sizeof(unsigned long long), fb);
         CK(cudaStreamSynchronize(fb));
         const int64_t used = (int64_t)vs.h->totals[0];
+        ctx->log_fill_seen = used;
         const int64_t need = used + others + vs.log_bound;
         int64_t c1 = ctx->log_cap, c2 = ctx->log_cap;
         CK(grow(ctx->log_key, c1, need, fb, used));
@@ -780,7 +774,7 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     // tables directly, so the capacity only bounds the fast path
     // (plus two chunks per tile: a CTA's partly filled and reserved chunks)
     const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
-    int64_t rec_need = (int64_t)vs.h->v.P_tiles + ctx->n + 2 * kRecChunk * tiles;
+    int64_t rec_need = P_tiles + ctx->n + 2 * kRecChunk * tiles;
     rec_need = (rec_need + kRecChunk - 1) / kRecChunk * kRecChunk;
     if (rec_need > vs.rec_cap) {
         CK(grow(vs.recs, vs.rec_cap, rec_need, fb));
@@ -831,26 +825,134 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     a.dbg_staged = nullptr;
     a.dbg_bad = nullptr;
     a.err = ctx->tc_err;
+    a.skip = skip;
     span_begin(ctx, SLAG_STAGE_COMPOSITE, bk);
     launch_composite(a, bk);
     span_end(ctx, bk);
     const HashSink sink{vs.hash, ctx->log_count, (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
                         ctx->s_ovf, reinterpret_cast<uint32_t *>(ctx->totals + 2), (int32_t)vs.view_base};
     span_begin(ctx, SLAG_STAGE_CONSUME, bk);
-    launch_combine(vs.recs, vs.rec_chunks, vs.rec_fill, (unsigned long long)(vs.rec_cap / kRecChunk), sink, bk);
+    launch_combine(vs.recs, vs.rec_chunks, vs.rec_fill, (unsigned long long)(vs.rec_cap / kRecChunk), sink, skip,
+                   bk);
     span_end(ctx, bk);
     // consumes in view order: the compensated sums are updated without atomics
     CK(cudaStreamWaitEvent(bk, ctx->ev_consumed, 0));
     span_begin(ctx, SLAG_STAGE_CONSUME, bk);
     launch_consume(vs.hash, ctx->n, (int32_t)vs.view_base, ctx->s_hi, ctx->s_lo, ctx->log_count,
                    (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
-                   reinterpret_cast<uint32_t *>(ctx->totals + 2), &vs.ctr->contributions, ctx->contrib, bk);
+                   reinterpret_cast<uint32_t *>(ctx->totals + 2), &vs.ctr->contributions, ctx->contrib, skip, bk);
     span_end(ctx, bk);
     CK(cudaEventRecord(ctx->ev_consumed, bk));
+    launch_copy_words(vs.ctr, &vs.h_dev->v, sizeof(ViewCounters), bk);
+    launch_copy_words(ctx->totals, vs.h_dev->totals, kTotals * sizeof(unsigned long long), bk);
     CK(cudaEventRecord(vs.ev_done, bk));
     CK(cudaGetLastError());
-    ctx->stats.pairs += (int64_t)vs.h->v.P_tiles;
-    ctx->stats.last_pairs = (int64_t)vs.h->v.P_tiles;
+    return SLAG_OK;
+}
+
+// A view's exact counts join the statistics and the sizing estimates of later views.
+void count_view(slag_ctx *ctx, const ViewCounters &v) {
+    ctx->stats.pairs += (int64_t)v.P_tiles;
+    ctx->stats.last_pairs = (int64_t)v.P_tiles;
+    ctx->est_P = std::max(ctx->est_P, (int64_t)v.P);
+    ctx->est_P_tiles = std::max(ctx->est_P_tiles, (int64_t)v.P_tiles);
+}
+
+// The second half of the last accepted view sized on the host: stage B on its own stream once
+// stage A's counters are on the host, then the back half. It runs in the next call (the next
+// view's slag_add_view, or any call that joins the views), so that stage A of the next view is
+// already queued while the host waits for this view's counters.
+slag_status launch_deferred_view(slag_ctx *ctx) {
+    if (!ctx->deferred) return SLAG_OK;
+    ctx->deferred = false;
+    ViewSlot &vs = ctx->slot[(ctx->views_enqueued - 1) % kSlots];
+    CK(cudaEventSynchronize(vs.ev_a));
+    CK(cudaGetLastError());
+    spans_resolve(ctx, false);
+    cudaStream_t fb = vs.front;
+    CK(cudaStreamWaitEvent(fb, vs.ev_a, 0));
+    int64_t P = 0;
+    uint32_t *list = nullptr;
+    slag_status s = stage_b(ctx, vs, fb, vs.cp, kSuperShift, vs.scratch, &P, &list);
+    if (s != SLAG_OK) return s;
+    CK(cudaEventRecord(vs.ev_bin, fb));
+    ctx->log_fill_seen = std::max(ctx->log_fill_seen, (int64_t)vs.h->totals[0]);
+    s = queue_back_half(ctx, vs, list, (int64_t)vs.h->v.P_tiles, nullptr);
+    if (s != SLAG_OK) return s;
+    count_view(ctx, vs.h->v);
+    return SLAG_OK;
+}
+
+// Stage B of a view sized on the device: the binning reads the view's counts from device
+// memory and holds at most an estimate of its pairs (the largest count seen so far, with a
+// quarter more); a view with more sets its overflow flag, which makes its binning leave every
+// bin empty and its back half do nothing. The host finds the flag when it settles the view.
+slag_status stage_b_async(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, uint32_t **list_out) {
+    const CamParams &cp = vs.cp;
+    const int shift = kSuperShift;
+    const int64_t cap = ctx->est_P + ctx->est_P / 4 + 4096;
+    if (cap > 0x7fffffffLL) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^31-1 Gaussian-tile pairs in one view");
+    if (cap > vs.p_cap) {
+        int64_t c0 = vs.p_cap;
+        for (int b = 0; b < 2; ++b) {
+            int64_t c1 = c0, c2 = c0;
+            CK(grow(vs.pkey[b], c1, cap, st));
+            CK(grow(vs.pval[b], c2, cap, st));
+            vs.p_cap = c1;
+        }
+    }
+    CK(scratch_reserve(vs.scratch, vs.p_cap));
+    const int bins_x = ((cp.tiles_x - 1) >> shift) + 1, bins_y = ((cp.tiles_y - 1) >> shift) + 1;
+    const int64_t bins = (int64_t)bins_x * bins_y;
+    const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
+    CK(grow(vs.ranges, vs.ranges_cap, bins, st));
+    CK(grow(vs.prect, vs.prect_cap, cap, st));
+    CK(grow(vs.tile_order, vs.order_cap, tiles, st));
+    span_begin(ctx, SLAG_STAGE_BIN, st);
+    if (!bin_sort_fused(vs.srect, vs.offsets, vs.stouched, ctx->n, &vs.ctr->n_visible, &vs.ctr->P, cap, 0,
+                        &vs.ctr->overflow, shift, bins_x, (int)bins, vs.sgid, vs.pval[0], vs.prect, vs.ranges,
+                        vs.scratch, st))
+        return fail(ctx, SLAG_ERR_STATE, "device-sized binning needs at most 2048 bins");
+    launch_tile_order(vs.ranges, cp.tiles_x, cp.tiles_y, shift, vs.tile_order, st);
+    span_end(ctx, st);
+    CK(cudaGetLastError());
+    *list_out = vs.pval[0];
+    return SLAG_OK;
+}
+
+// Settles the slot's view if it was sized on the device: waits for it, counts it, and when its
+// pairs exceeded its binning's capacity re-runs its binning (its stage A results, segment map and
+// columns are still in place) and its back half with the exact count.
+slag_status settle_slot(slag_ctx *ctx, ViewSlot &vs) {
+    if (!vs.pending) return SLAG_OK;
+    vs.pending = false;
+    CK(cudaEventSynchronize(vs.ev_done));
+    CK(cudaGetLastError());
+    const ViewCounters v = vs.h->v;   // copied at the end of its back half
+    ctx->log_fill_seen = std::max(ctx->log_fill_seen, (int64_t)vs.h->totals[0]);
+    count_view(ctx, v);
+    if (!v.overflow) return SLAG_OK;
+    ctx->stats.pairs -= (int64_t)v.P_tiles;   // counted again below
+    cudaStream_t fb = vs.front;
+    CK(cudaMemsetAsync(&vs.ctr->overflow, 0, sizeof(uint32_t), fb));
+    int64_t P = 0;
+    uint32_t *list = nullptr;
+    slag_status s = stage_b(ctx, vs, fb, vs.cp, kSuperShift, vs.scratch, &P, &list);
+    if (s != SLAG_OK) return s;
+    CK(cudaEventRecord(vs.ev_bin, fb));
+    s = queue_back_half(ctx, vs, list, (int64_t)v.P_tiles, nullptr);
+    if (s != SLAG_OK) return s;
+    ctx->stats.pairs += (int64_t)v.P_tiles;
+    ctx->stats.resized_views += 1;
+    return SLAG_OK;
+}
+
+// Settles every view sized on the device (before a join reads the accumulated state).
+slag_status settle_views(slag_ctx *ctx) {
+    for (int i = 0; i < kSlots; ++i) {
+        slag_status s = settle_slot(ctx, ctx->slot[i]);
+        if (s != SLAG_OK) return s;
+    }
     return SLAG_OK;
 }
 
@@ -874,10 +976,13 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     if (ctx->precision == SLAG_PREC_LINEAR32 && !ctx->lin_params)
         return fail(ctx, SLAG_ERR_STATE, "linear code: slag_set_linear_code before the first view");
     ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
-    cudaStream_t fr = ctx->front, up = ctx->up;
+    cudaStream_t fr = vs.front, up = ctx->up;
     const CamParams cp = cam_params(cam);
     const int64_t npx = (int64_t)cam->width * cam->height;
     const int64_t D = ctx->D;
+    // the slot's previous view, if it was sized on the device, is settled before its buffers go
+    s = settle_slot(ctx, vs);
+    if (s != SLAG_OK) return s;
 
     // stage A and the uploads start after the caller's work so far (inputs written on the
     // caller's stream) and after the slot's previous view has been composited and consumed
@@ -917,7 +1022,7 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
             if (sp != SLAG_OK) return sp;
         }
         // stage A of this view, then the previous view's second half
-        const slag_status sa = stage_a(ctx, vs, fr, cp, kSuperShift);
+        const slag_status sa = stage_a(ctx, vs, fr, cp, kSuperShift, vs.scratch);
         if (sa != SLAG_OK) return sa;
         CK(cudaEventRecord(vs.ev_a, fr));
         return launch_deferred_view(ctx);
@@ -934,9 +1039,25 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     if (vs.h->vu.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
     vs.cp = cp;
     vs.view_base = ctx->table_rows;
+    // the view's second half: sized on the device and queued now when earlier views give an
+    // estimate of its pair count (and its bins fit the single-pass binning); otherwise sized on
+    // the host, in the next call
+    const int64_t bins = (int64_t)(((cp.tiles_x - 1) >> kSuperShift) + 1) * (((cp.tiles_y - 1) >> kSuperShift) + 1);
+    const bool device_sized = ctx->est_P > 0 && bins <= 2048 && !(kChecked && ctx->force_pair_cap > 0);
+    if (device_sized) {
+        cudaStream_t fb = vs.front;
+        CK(cudaStreamWaitEvent(fb, vs.ev_a, 0));
+        uint32_t *list = nullptr;
+        s = stage_b_async(ctx, vs, fb, &list);
+        if (s != SLAG_OK) return s;
+        CK(cudaEventRecord(vs.ev_bin, fb));
+        s = queue_back_half(ctx, vs, list, ctx->est_P_tiles + ctx->est_P_tiles / 4 + 4096, &vs.ctr->overflow);
+        if (s != SLAG_OK) return s;
+        vs.pending = true;
+    }
     ctx->views_enqueued += 1;
     ctx->table_rows += M;
-    ctx->deferred = true;
+    ctx->deferred = !device_sized;
     ctx->stats.views += 1;
     ctx->stats.columns = ctx->table_rows;
     ctx->finalized = false;
@@ -955,6 +1076,7 @@ slag_status finalize_prepare(slag_ctx *ctx) {
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     slag_status s0 = launch_deferred_view(ctx);
+    if (s0 == SLAG_OK) s0 = settle_views(ctx);
     if (s0 != SLAG_OK) return s0;
     CK(join_views(ctx));
     const ViewSlot &last = ctx->slot[(ctx->views_enqueued + kSlots - 1) % kSlots];
@@ -974,6 +1096,7 @@ slag_status finalize_prepare(slag_ctx *ctx) {
     if (ctx->log_overflowed) return fail(ctx, SLAG_ERR_CAPACITY, "the triple log overflowed in some view");
     const int64_t Z = (int64_t)ctx->hc->totals[0];
     ctx->stats.triples = Z;
+    ctx->log_fill_seen = Z;
     const int64_t n = ctx->n;
     const int64_t nblocks = (n + kBlockG - 1) / kBlockG;
     CK(cudaMemsetAsync(ctx->bstart, 0, sizeof(uint32_t) * nblocks, st));
@@ -1550,6 +1673,7 @@ slag_status slag_reset(slag_ctx *ctx) {
     const int64_t n = ctx->n;
     ctx->deferred = false;   // the last view's second half is dropped with the rest
     CK(join_views(ctx));
+    for (int i = 0; i < kSlots; ++i) ctx->slot[i].pending = false;   // dropped too
     // a view that failed after its first half can leave entries in its slot's table
     for (int i = 0; i < kSlots; ++i) {
         launch_hash_init(ctx->slot[i].hash, n, st);
@@ -1563,6 +1687,7 @@ slag_status slag_reset(slag_ctx *ctx) {
     CK(cudaGetLastError());
     ctx->views_enqueued = 0;
     ctx->table_rows = 0;
+    ctx->log_fill_seen = 0;
     ctx->log_overflowed = false;
     ctx->finalized = false;
     ctx->hc->v = ViewCounters{};
@@ -1730,11 +1855,13 @@ slag_status gaussian_fingerprint(slag_ctx *ctx, uint64_t *out) {
 slag_status join_and_read_totals(slag_ctx *ctx) {
     cudaStream_t st = ctx->stream;
     slag_status s = launch_deferred_view(ctx);
+    if (s == SLAG_OK) s = settle_views(ctx);
     if (s != SLAG_OK) return s;
     CK(join_views(ctx));
     launch_copy_words(ctx->totals, ctx->hc_dev->totals, kTotals * sizeof(unsigned long long), st);
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    ctx->log_fill_seen = (int64_t)ctx->hc->totals[0];
     if (ctx->hc->totals[2]) ctx->log_overflowed = true;
     if (ctx->log_overflowed) return fail(ctx, SLAG_ERR_CAPACITY, "the triple log overflowed in some view");
     return SLAG_OK;
@@ -1889,6 +2016,7 @@ slag_status slag_merge_state(slag_ctx *ctx, const void *buf, int64_t bytes) {
         // the device totals: triples in the log and the counters the state carries
         unsigned long long *tot = ctx->hc->totals;
         tot[0] = (unsigned long long)(used + Zb);
+        ctx->log_fill_seen = used + Zb;
         tot[1] += (unsigned long long)h.contributions;
         tot[3] += (unsigned long long)h.evaluations;
         tot[4] += (unsigned long long)h.executed;
@@ -2082,6 +2210,7 @@ slag_status slag_check_wait_timeout(slag_ctx *ctx, int32_t limit_us, int32_t com
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     slag_status s = launch_deferred_view(ctx);
+    if (s == SLAG_OK) s = settle_views(ctx);
     if (s != SLAG_OK) return s;
     CK(join_views(ctx));
     launch_wait_check((uint64_t)limit_us * 1000ull, complete ? 1 : 0, ctx->tc_err, st);
@@ -2104,18 +2233,14 @@ void slag_destroy(slag_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
-    if (ctx->front) cudaStreamSynchronize(ctx->front);
-    if (ctx->front_b) cudaStreamSynchronize(ctx->front_b);
     if (ctx->up) cudaStreamSynchronize(ctx->up);
-    for (int i = 0; i < kSlots; ++i)
+    for (int i = 0; i < kSlots; ++i) {
+        if (ctx->slot[i].front) cudaStreamSynchronize(ctx->slot[i].front);
         if (ctx->slot[i].back) cudaStreamSynchronize(ctx->slot[i].back);
+    }
     for (int i = 0; i < kSlots; ++i) slot_free(ctx->slot[i]);
-    if (ctx->front) cudaStreamDestroy(ctx->front);
-    if (ctx->front_b) cudaStreamDestroy(ctx->front_b);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->up) cudaStreamDestroy(ctx->up);
-    if (ctx->ev_front) cudaEventDestroy(ctx->ev_front);
-    if (ctx->ev_front_b) cudaEventDestroy(ctx->ev_front_b);
     if (ctx->ev_consumed) cudaEventDestroy(ctx->ev_consumed);
     if (ctx->qgraph) cudaGraphExecDestroy(ctx->qgraph);
     if (ctx->qstream) { cudaStreamSynchronize(ctx->qstream); cudaStreamDestroy(ctx->qstream); }
@@ -2139,7 +2264,6 @@ void slag_destroy(slag_ctx *ctx) {
     dfree(ctx->ehl); dfree(ctx->qinv); dfree(ctx->qhl);
     dfree(ctx->qbuf); dfree(ctx->cand_s); dfree(ctx->cand_i); dfree(ctx->qids); dfree(ctx->qscores); dfree(ctx->qcount);
     scratch_free(ctx->scratch);
-    scratch_free(ctx->scratch_b);
     for (auto &sp : ctx->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->prof_base) cudaEventDestroy(ctx->prof_base);
@@ -2175,6 +2299,7 @@ slag_status slag_get_profile(slag_ctx *ctx, slag_profile *out, int32_t reset) {
     if (!ctx || !out) return SLAG_ERR_INVALID_ARG;
     CK(cudaSetDevice(ctx->device));
     slag_status s0 = launch_deferred_view(ctx);
+    if (s0 == SLAG_OK) s0 = settle_views(ctx);
     if (s0 != SLAG_OK) return s0;
     CK(cudaStreamSynchronize(ctx->stream));
     CK(drain_views(ctx));
@@ -2233,6 +2358,7 @@ slag_status bin_view_diag(slag_ctx *ctx, const slag_camera *cam, int shift, uint
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     s = launch_deferred_view(ctx);
+    if (s == SLAG_OK) s = settle_views(ctx);
     if (s != SLAG_OK) return s;
     CK(join_views(ctx));
     ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
@@ -2305,6 +2431,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     s = launch_deferred_view(ctx);
+    if (s == SLAG_OK) s = settle_views(ctx);
     if (s != SLAG_OK) return s;
     CK(join_views(ctx));
     ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
@@ -2367,7 +2494,7 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     a.n_ids = (uint32_t)ctx->n;
     a.weight_mode = ctx->weight_mode;
     a.ctr = vs.ctr;
-    a.overflow = reinterpret_cast<uint32_t *>(&vs.ctr->pad[0]);
+    a.overflow = &vs.ctr->pad;
     a.contrib = &vs.ctr->contributions;
     a.dbg_T = ctx->dbg_T;
     a.dbg_wsum = ctx->dbg_wsum;
@@ -2411,6 +2538,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     s = launch_deferred_view(ctx);
+    if (s == SLAG_OK) s = settle_views(ctx);
     if (s != SLAG_OK) return s;
     CK(join_views(ctx));
     ViewSlot &vs = ctx->slot[ctx->views_enqueued % kSlots];
@@ -2443,7 +2571,7 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.seg = nullptr;
     a.weight_mode = ctx->weight_mode;
     a.ctr = vs.ctr;
-    a.overflow = reinterpret_cast<uint32_t *>(&vs.ctr->pad[0]);
+    a.overflow = &vs.ctr->pad;
     a.contrib = &vs.ctr->contributions;
     a.dbg_T = ctx->dbg_T;
     a.dbg_wsum = ctx->dbg_wsum;

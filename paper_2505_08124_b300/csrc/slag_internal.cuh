@@ -82,7 +82,8 @@ struct ViewCounters {
     unsigned long long P;             // pairs at the binning granularity (tiles or super-tiles)
     unsigned long long P_tiles;       // Gaussian-tile pairs
     unsigned long long contributions; // composited (Gaussian, pixel) pairs (diagnostic render)
-    uint32_t pad[2];
+    uint32_t overflow;                // the view's pairs exceeded the capacity its binning held
+    uint32_t pad;
 };
 
 struct CamParams {
@@ -129,16 +130,20 @@ bool radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t
                     cudaStream_t st);
 
 // Binning of a view's Gaussian-bin pairs by bin in one stable pass, without writing the pairs in
-// emission order first: the Gaussians of depth rank r < n_visible, with bin rectangles from
-// srect at 2^shift tiles per bin (bins_x bins per row, `bins` in all), counts[r] pairs each and
-// offsets = the exclusive scan of counts; P (<= the pair total; smaller only in checked builds,
-// whose check then flags the pair emission) pairs in all. Writes, in bin order and within a bin
-// in emission order, vals_out[i] = val_map[r] and rect_out[i] = srect[r] of each pair's Gaussian
-// r, and ranges[b] = [start, end) of bin b. Returns false (and does nothing) when bins > 2048 or
-// there are no pairs; the caller then emits the pairs and radix-sorts them.
-bool bin_sort_fused(const uint2 *srect, const uint32_t *offsets, const uint32_t *counts, uint32_t n_visible,
-                    int64_t P, int shift, int bins_x, int bins, const uint32_t *val_map, uint32_t *vals_out,
-                    uint2 *rect_out, uint2 *ranges, SortScratch &s, cudaStream_t st);
+// emission order first: the Gaussians of depth rank r < *d_nv (at most n_cap), with bin
+// rectangles from srect at 2^shift tiles per bin (bins_x bins per row, `bins` in all), counts[r]
+// pairs each and offsets = the exclusive scan of counts; *d_P pairs in all. The counts are read
+// on the device, so the host need not know them: the pass holds at most cap pairs, and a larger
+// *d_P sets *d_overflow and leaves every bin empty (with truncate, set only by checked builds'
+// forced capacities, the first cap pairs are kept and the pair emission's check flags the rest).
+// Writes, in bin order and within a bin in emission order, vals_out[i] = val_map[r] and
+// rect_out[i] = srect[r] (when rect_out is non-null) of each pair's Gaussian r, and ranges[b] =
+// [start, end) of bin b. Returns false (and does nothing) when bins > 2048 or cap is 0; the
+// caller then emits the pairs and radix-sorts them.
+bool bin_sort_fused(const uint2 *srect, const uint32_t *offsets, const uint32_t *counts, int64_t n_cap,
+                    const uint32_t *d_nv, const unsigned long long *d_P, int64_t cap, int truncate,
+                    uint32_t *d_overflow, int shift, int bins_x, int bins, const uint32_t *val_map,
+                    uint32_t *vals_out, uint2 *rect_out, uint2 *ranges, SortScratch &s, cudaStream_t st);
 
 // Exclusive prefix sum of n uint32 values; writes the total to *d_total (may be null).
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *d_total,
@@ -287,6 +292,7 @@ struct CompositeArgs {
     unsigned long long *rec_chunks;// chunks of kRecChunk records reserved (zeroed before the launch)
     uint32_t *rec_fill;            // per chunk: records written (every reserved chunk below chunk_cap)
     unsigned long long chunk_cap;  // chunks the record list holds (beyond: sums go to the tables)
+    const uint32_t *skip;          // nullable: the launch does nothing when *skip is non-zero
 };
 void launch_composite(const CompositeArgs &a, cudaStream_t st);
 
@@ -297,13 +303,15 @@ void launch_hash_init(HashEntry *hash, int64_t n, cudaStream_t st);
 // bulk copies on the copy engines.
 void launch_copy_words(const void *src, void *dst, int64_t bytes, cudaStream_t st);
 // Adds the view's records to the per-Gaussian tables: of the first min(*rec_chunks, chunk_cap)
-// chunks, the first rec_fill[c] records of chunk c.
+// chunks, the first rec_fill[c] records of chunk c. Nothing when *skip (nullable) is non-zero.
 void launch_combine(const WeightRecord *recs, const unsigned long long *rec_chunks, const uint32_t *rec_fill,
-                    unsigned long long chunk_cap, const HashSink &sink, cudaStream_t st);
+                    unsigned long long chunk_cap, const HashSink &sink, const uint32_t *skip, cudaStream_t st);
+// The view's per-Gaussian tables to triples and the compensated weight sums (k_accum.cu).
+// Nothing when *skip (nullable) is non-zero.
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
                     unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key,
                     float *log_w, uint32_t *overflow, const unsigned long long *view_contrib,
-                    unsigned long long *total_contrib, cudaStream_t st);
+                    unsigned long long *total_contrib, const uint32_t *skip, cudaStream_t st);
 void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaStream_t st);
 // keys in the compact layout (launch_repack_keys with to_compact) of columns < 2^col_bits
 void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z, int col_bits,

@@ -59,7 +59,7 @@ class CView(ctypes.Structure):
 class CStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("views", "pairs", "contributions", "triples", "columns",
                                                "last_pairs", "last_contributions", "touched",
-                                               "evaluations", "executed")]
+                                               "evaluations", "executed", "resized_views")]
 
 
 _lib = None

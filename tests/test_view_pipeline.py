@@ -1,18 +1,25 @@
 """The two halves of slag_add_view.
 
 A view's first half (uploads, segment-id check, projection, depth sort, tile-count scan) is
-queued by its own slag_add_view; its second half (pair emission, bin sort, compositing,
-masking, reduction) by the next call on the context. These tests check that every way of
-ending a view's wait gives the result of the plain sequence, up to the float32 summation order
-of the weight atomics:
+queued by its own slag_add_view. Its second half (binning, compositing, masking, reduction) is
+queued by the same call when earlier views give an estimate of its pair count (the binning then
+reads the counts on the device and flags a view whose pairs exceed the estimate; such a view is
+binned again with its exact count when its slot is reused or the views are joined), and
+otherwise by the next call on the context, once the host has read the count. These tests check
+that every way of ending a view's wait gives the result of the plain sequence, up to the
+float32 summation order of the weight atomics:
 - calls between views (diagnostics, profiles);
 - a rejected view after an accepted one;
 - slag_reset with a view still waiting;
-- the caller's input buffers reused as soon as slag_add_view returns (host and device)."""
+- the caller's input buffers reused as soon as slag_add_view returns (host and device);
+- views whose pair counts outgrow the estimate (against the oracle)."""
+import math
+
 import numpy as np
 import pytest
 
 import synth
+from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -130,3 +137,38 @@ def test_input_buffers_free_on_return(slag, scene):
                     h_tab[:] = 7.0
             E, w = L.finalize()
         _close((E, w), (Er, wr))
+
+
+def _zoomed(views, radii):
+    """The views' segment maps and tables, seen from an orbit of the given radius per view."""
+    out = []
+    for i, (v, r) in enumerate(zip(views, radii)):
+        az = 2.0 * math.pi * i / len(radii)
+        cam = synth.look_at([r * math.cos(az), r * math.sin(az), 0.3 * r], [0.0, 0.0, 0.0],
+                            v.camera.width, v.camera.height)
+        out.append(synth.View(cam, v.seg, v.table))
+    return out
+
+
+def test_views_outgrowing_the_estimate_are_binned_again(slag):
+    # two views from afar, then seven close up with about twice the super-tile pairs: the close
+    # views' binning, sized from the far ones, overflows; each is binned again with its exact
+    # count when its slot is reused (views 6..8) or at the finalize, and the result is the oracle's
+    s = synth.small_scene(43, 20000, 9, 480, 320, 8, dim=128, surfaces=4)
+    zv = _zoomed(list(s.views()), [9.0, 9.0] + [2.2] * 7)
+    with slag.Lifter(s.gaussians, dim=128) as L:
+        for v in zv:
+            L.add_view(v.camera, v.seg, v.table)
+        E, w = L.finalize()
+        st = L.stats()
+    pairs = [int(O.bin_f32(s.gaussians, v.camera)[2].sum()) for v in zv]
+    assert pairs[2] > 2 * pairs[0]
+    assert st["resized_views"] >= 5
+    assert st["pairs"] == sum(pairs)
+    assert st["views"] == len(zv)
+    num, den, _ = O.lift(s.gaussians, zv)
+    Eo = O.normalise(num, den)
+    rel = np.linalg.norm(E.astype(np.float64) - Eo) / np.linalg.norm(Eo)
+    relw = np.linalg.norm(w.astype(np.float64) - den) / np.linalg.norm(den)
+    assert rel <= 1e-4 and relw <= 1e-4, (rel, relw)
+
