@@ -24,11 +24,15 @@
  *
  * Precision. Continuous quantities (projected mean, 2D covariance, conic,
  * alpha, transmittance, weights, sums) are float64. The discrete decisions
- * whose outcome is an integer (visibility, tile rectangle, depth order) are
- * taken in float32 by a mirror of the projection written out below with a
- * fixed operation order and no fused multiply-add (build with
- * -ffp-contract=off); tile lists are sorted by (float32 depth, Gaussian
- * index). The paper gives no rasterizer constants; the ones used are: 2D
+ * whose outcome is an integer (visibility, tile rectangle, depth order, and
+ * whether a Gaussian's alpha reaches the floor 1/255 at a pixel) are taken in
+ * float32 by a mirror written out below with a fixed operation order (build
+ * with -ffp-contract=off; fused multiply-adds only where written as fmaf);
+ * tile lists are sorted by (float32 depth, Gaussian index). The floor test
+ * compares the base-2 exponent of alpha, log2(o) - (log2 e / 2) q, with
+ * log2(1/255), evaluating it as a quadratic polynomial in the pixel centre's
+ * offset from its tile's origin, with log2(o) rounded from float64. The stop
+ * test (transmittance below 1e-4) is taken in float64. The paper gives no rasterizer constants; the ones used are: 2D
  * dilation 0.3, radius ceil(3 sqrt(lambda_max)) with the eigenvalue
  * discriminant floored at 0.1, Jacobian clamp 1.3 * tan(half fov), alpha cap
  * 0.99, alpha floor 1/255 (skip), stop when the next transmittance would fall
@@ -79,9 +83,11 @@ static void cov3_f32(const float *s, const float *q, float out[6]) {
     out[5] = (m[6] * m[6] + m[7] * m[7]) + m[8] * m[8];
 }
 
-/* Returns tiles touched (0 = culled); writes depth and rect [x0,y0,x1,y1). */
+/* Returns tiles touched (0 = culled); writes depth and rect [x0,y0,x1,y1), and, when rec is
+ * non-null, the float32 floor-test record (projected mean, then the conic scaled to base-2
+ * exponent coefficients: -(log2 e / 2) A, -(log2 e) B, -(log2 e / 2) C for the conic (A, B, C)). */
 static uint32_t bin_one_f32(const float *mu, const float *s, const float *q, const ocam *c,
-                            float *depth, int32_t rect[4]) {
+                            float *depth, int32_t rect[4], float *rec) {
     const float *R = c->R;
     float tx = ((R[0] * mu[0] + R[1] * mu[1]) + R[2] * mu[2]) + c->t[0];
     float ty = ((R[3] * mu[0] + R[4] * mu[1]) + R[5] * mu[2]) + c->t[1];
@@ -128,14 +134,42 @@ static uint32_t bin_one_f32(const float *mu, const float *s, const float *q, con
     int32_t x0 = (int32_t)fx0, x1 = (int32_t)fx1, y0 = (int32_t)fy0, y1 = (int32_t)fy1;
     if (x0 >= x1 || y0 >= y1) return 0;
     rect[0] = x0; rect[1] = y0; rect[2] = x1; rect[3] = y1;
+    if (rec) {
+        const float kLog2e = 1.4426950408889634f;
+        float inv = 1.0f / det;
+        float A = c11 * inv, B = -c01 * inv, C = c00 * inv;
+        rec[0] = px;
+        rec[1] = py;
+        rec[2] = -0.5f * kLog2e * A;
+        rec[3] = -kLog2e * B;
+        rec[4] = -0.5f * kLog2e * C;
+    }
     return (uint32_t)((x1 - x0) * (y1 - y0));
+}
+
+/* log2 of an opacity, rounded to float32 from float64 (-inf for 0). */
+static float log2_opacity_f32(float o) { return o > 0.0f ? (float)log2((double)o) : -INFINITY; }
+
+/* Whether alpha reaches the floor 1/255 at the pixel centre (X, Y) = (pixel - tile origin) + 0.5
+ * of tile origin (ox, oy), in float32: the exponent e = q2 + log2 o, q2 = a' dx^2 + b' dx dy +
+ * c' dy^2 with d = (mean - origin) - (X, Y), expanded as K0 + K1 X + K2 Y + a' X^2 + b' X Y +
+ * c' Y^2 and evaluated in that order (Horner form by fused multiply-adds). */
+static int floor_reached_f32(const float *rec, float lo, float ox, float oy, float X, float Y) {
+    const float mx = rec[0] - ox, my = rec[1] - oy;
+    const float A = rec[2], Bc = rec[3], C = rec[4];
+    const float K1 = -fmaf(2.0f * A, mx, Bc * my);
+    const float K2 = -fmaf(Bc, mx, 2.0f * C * my);
+    const float K0 = fmaf(fmaf(A, mx, Bc * my), mx, fmaf(C * my, my, lo));
+    const float XX = X * X, XY = X * Y, YY = Y * Y;
+    const float e = fmaf(C, YY, fmaf(Bc, XY, fmaf(A, XX, fmaf(K2, Y, fmaf(K1, X, K0)))));
+    return e >= -7.99435343685886f;   /* log2(1/255) */
 }
 
 void oracle_bin_f32(int64_t n, const float *means, const float *scales, const float *quats,
                     const ocam *cam, float *depth, int32_t *rect, uint32_t *touched) {
     for (int64_t k = 0; k < n; ++k)
         touched[k] = bin_one_f32(means + 3 * k, scales + 3 * k, quats + 4 * k, cam, depth + k,
-                                 rect + 4 * k);
+                                 rect + 4 * k, NULL);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -317,13 +351,19 @@ static int composite_view(const view_in *v, const uint8_t *tile_mask, sink_fn si
     int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
     uint32_t *touched = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
     proj64 *pj = (proj64 *)malloc(sizeof(proj64) * (size_t)(n > 0 ? n : 1));
-    if (!depth || !rect || !touched || !pj) { free(depth); free(rect); free(touched); free(pj); return -1; }
-    oracle_bin_f32(n, v->means, v->scales, v->quats, v->cam, depth, rect, touched);
-    for (int64_t k = 0; k < n; ++k)
+    float *rec = (float *)malloc(sizeof(float) * 6 * (size_t)(n > 0 ? n : 1));   /* floor-test record, log2 o */
+    if (!depth || !rect || !touched || !pj || !rec) {
+        free(depth); free(rect); free(touched); free(pj); free(rec); return -1;
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        touched[k] = bin_one_f32(v->means + 3 * k, v->scales + 3 * k, v->quats + 4 * k, v->cam, depth + k,
+                                 rect + 4 * k, rec + 6 * k);
+        rec[6 * k + 5] = log2_opacity_f32(v->opac[k]);
         if (touched[k]) project_f64(v->means + 3 * k, v->scales + 3 * k, v->quats + 4 * k, v->opac[k], v->cam, pj + k);
+    }
     tile_lists L;
     if (build_lists(n, depth, rect, touched, v->cam, v->ty0, v->ty1, &L)) {
-        free(depth); free(rect); free(touched); free(pj); return -1;
+        free(depth); free(rect); free(touched); free(pj); free(rec); return -1;
     }
     const int32_t W = v->cam->width, H = v->cam->height;
     int64_t contributions = 0;
@@ -337,14 +377,17 @@ static int composite_view(const view_in *v, const uint8_t *tile_mask, sink_fn si
                     int32_t cnt = 0;
                     int32_t j = v->seg ? v->seg[(int64_t)py * W + px] : -1;
                     double cxp = px + 0.5, cyp = py + 0.5;
+                    const float ox = (float)(tx * TILE), oy = (float)(ty * TILE);
+                    const float X = (float)(px - tx * TILE) + 0.5f, Y = (float)(py - ty * TILE) + 0.5f;
                     for (int64_t i = L.start[t]; i < L.start[t + 1]; ++i) {
-                        const proj64 *g = pj + L.items[i].k;
+                        const int32_t k = L.items[i].k;
+                        const proj64 *g = pj + k;
                         double dx = g->mx - cxp, dy = g->my - cyp;
                         double power = -0.5 * (g->A * dx * dx + g->C * dy * dy) - g->B * dx * dy;
                         if (power > 0.0) continue;
+                        if (!floor_reached_f32(rec + 6 * k, rec[6 * k + 5], ox, oy, X, Y)) continue;
                         double kern = exp(power);
                         double alpha = fmin(0.99, g->op * kern);
-                        if (alpha < 1.0 / 255.0) continue;
                         double Tn = T * (1.0 - alpha);
                         if (Tn < 1e-4) break;
                         double w = v->weight_mode == 1 ? kern : alpha * T;
@@ -361,7 +404,7 @@ static int composite_view(const view_in *v, const uint8_t *tile_mask, sink_fn si
                 }
         }
     if (stats) { stats[0] = L.P; stats[1] = contributions; }
-    free_lists(&L); free(depth); free(rect); free(touched); free(pj);
+    free_lists(&L); free(depth); free(rect); free(touched); free(pj); free(rec);
     return 0;
 }
 
@@ -402,7 +445,7 @@ int oracle_view_weights_rows(int64_t n, const float *means, const float *scales,
             int64_t k = sub_ids[r];
             sub_of[k] = r;
             float d; int32_t rc[4];
-            if (bin_one_f32(means + 3 * k, scales + 3 * k, quats + 4 * k, cam, &d, rc))
+            if (bin_one_f32(means + 3 * k, scales + 3 * k, quats + 4 * k, cam, &d, rc, NULL))
                 for (int32_t y = rc[1]; y < rc[3]; ++y)
                     for (int32_t x = rc[0]; x < rc[2]; ++x) tile_mask[(int64_t)y * tilesx + x] = 1;
         }

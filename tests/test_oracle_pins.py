@@ -8,6 +8,7 @@
 * invariants: sum_k w_kp = 1 - T_final(p); constant features reproduce the
   constant; invariance to view order; literal form == factored form;
 * brute force: an independent numpy compositor over tiny scenes;
+* the alpha floor: the float32 decision equals the float64 one away from the floor;
 * queries: numpy's stable argsort of the cosine scores.
 """
 import math
@@ -374,6 +375,35 @@ def test_brute_force_tiny_scenes(oracle_lib, seed):
         assert Bb.sum() > 0
         np.testing.assert_allclose(r["B"], Bb, rtol=2e-6, atol=1e-9)
         np.testing.assert_allclose(r["T_final"], Tb, rtol=2e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_alpha_floor_decision(oracle_lib, seed):
+    # one Gaussian per view: a pixel counts a contribution exactly when alpha >= 1/255 there. The
+    # oracle takes that decision in float32 (a mirror of the compositing kernel's evaluation); it
+    # must equal the float64 decision (alpha from the numpy projection) at every pixel whose alpha
+    # is not within 1e-5 (relative) of the floor, with the floor's boundary crossing the image
+    rng = np.random.default_rng(300 + seed)
+    means = rng.uniform(-0.2, 0.2, (1, 3))
+    scales = np.exp(rng.normal(-2.2, 0.5, (1, 3)))
+    quats = synth.scenes._unit_quats(rng, 1)
+    op = np.array([0.2 + 0.7 * rng.uniform()])
+    g = _gauss(means, scales, quats, op)
+    W, H = 72, 56
+    cam = synth.look_at([0.2, -2.0, 0.3], [0, 0, 0], W, H, 60.0)
+    view = synth.View(cam, np.zeros((H, W), np.int32), np.eye(1, 4, dtype=np.float32))
+    r = O.view_weights(g, view, per_pixel=True)
+    ref = _np_project(g, cam)
+    px = np.arange(W) + 0.5
+    py = np.arange(H) + 0.5
+    dx = ref["mx"][0] - px[None, :]
+    dy = ref["my"][0] - py[:, None]
+    power = -0.5 * (ref["A"][0] * dx * dx + ref["C"][0] * dy * dy) - ref["B"][0] * dx * dy
+    alpha = np.minimum(0.99, op[0] * np.exp(power))
+    above = alpha >= 1 / 255
+    clear = np.abs(alpha * 255.0 - 1.0) > 1e-5
+    assert 20 < above.sum() < W * H - 20
+    np.testing.assert_array_equal(r["count_px"][clear], above[clear].astype(np.int32))
 
 
 # ----------------------------------------------------------------------------
