@@ -167,17 +167,28 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
  * Runs projection, tile binning, the two sorts, compositing, masking and the
  * per-view reduction, in two halves. This call uploads the inputs, checks the
  * segment ids and queues the first half (projection, depth sort, tile-count
- * scan). The second half (pair emission, bin sort, compositing, masking,
- * reduction) needs the view's pair count on the host to size its workspace;
- * it is queued by the next call on the context: the next slag_add_view, or
- * slag_finalize / slag_finalize_async / slag_export_partitions /
- * slag_get_profile / slag_bin_view / slag_render_debug. The caller's buffers
- * are free when the call returns. Errors: INVALID_ARG (NULL pointer, camera
- * not finite or out of range, M < 1 or M >= 2^24, a segment id outside
- * [-1, M): the view is then not added); OOM; CUDA. The second half's errors,
- * CAPACITY (more than 2^31 - 1 Gaussian-tile pairs in the view), OOM and CUDA,
- * are returned by the call that queues it, and the context then needs
- * slag_reset. slag_reset drops a view whose second half is not queued. */
+ * scan). The second half (binning, compositing, masking, reduction) is sized
+ * by the view's pair count:
+ *  - once earlier views give an estimate of it (from the second view of a
+ *    context on, when the view has at most 2048 bins of 4x4 tiles), this call
+ *    queues it too, sized on the device: a view whose pairs exceed the
+ *    estimate is flagged on the device, composites nothing, and is binned
+ *    again with its exact count when its slot is reused (kSlots = 6 views
+ *    later) or the views are joined (stats.resized_views counts these). Unless
+ *    stages are being timed (slag_set_profiling), these views replay CUDA
+ *    graphs of the view's work, captured once per slot and image size
+ *    (slag_set_graphs);
+ *  - otherwise the host reads the count, and the second half is queued by
+ *    the next call on the context: the next slag_add_view, or slag_finalize /
+ *    slag_finalize_async / slag_export_partitions / slag_get_profile /
+ *    slag_bin_view / slag_render_debug.
+ * The caller's buffers are free when the call returns. Errors: INVALID_ARG
+ * (NULL pointer, camera not finite or out of range, M < 1 or M >= 2^24, a
+ * segment id outside [-1, M): the view is then not added); OOM; CUDA. The
+ * second half's errors, CAPACITY (more than 2^31 - 1 Gaussian-tile pairs in
+ * the view), OOM and CUDA, are returned by the call that queues or settles
+ * it, and the context then needs slag_reset. slag_reset drops the views whose
+ * second half is not queued or not settled. */
 slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *seg_ids,
                           const float *seg_table, int32_t M, int32_t on_device);
 
@@ -396,6 +407,16 @@ typedef struct {
  * *failed_ctx (nullable) receives its context index, or -1. */
 slag_status slag_add_views_batched(int32_t n_ctx, slag_ctx *const *ctxs, const slag_view *const *views,
                                    const int32_t *n_views, int32_t *failed_ctx);
+
+/* Replays of captured CUDA graphs for views sized on the device (on by
+ * default): per slot of views in flight, the view's first half and binning,
+ * its compositing and combine pass, and its consume pass are captured as three
+ * graphs at the first such view of an image size (again whenever a buffer they
+ * use is reallocated) and replayed for the later ones, with the view's camera
+ * and first column read from device memory; the host then issues a handful of
+ * calls per view instead of some 60 launches and stream operations. Off: the
+ * same work is launched kernel by kernel. The results are the same. */
+slag_status slag_set_graphs(slag_ctx *ctx, int32_t enable);
 
 /* Query autotuning (on by default): for a batch shape with enough work, the
  * first device-side query times the tensor-core kernel at the default split of

@@ -35,9 +35,12 @@ __global__ void hash_init_k(HashEntry *h, int64_t n) {
 __global__ void __launch_bounds__(256) combine_k(const WeightRecord *__restrict__ recs,
                                                  const unsigned long long *__restrict__ rec_chunks,
                                                  const uint32_t *__restrict__ rec_fill,
-                                                 unsigned long long chunk_cap, const HashSink sink,
-                                                 const uint32_t *__restrict__ skip) {
+                                                 unsigned long long chunk_cap, const HashSink sink_in,
+                                                 const uint32_t *__restrict__ skip,
+                                                 const int32_t *__restrict__ view_base_dev) {
     if (skip && *skip) return;
+    HashSink sink = sink_in;
+    if (view_base_dev) sink.view_base = *view_base_dev;
     unsigned long long nc = *rec_chunks;
     if (nc > chunk_cap) nc = chunk_cap;
     const unsigned long long nr = nc * kRecChunk;
@@ -56,8 +59,10 @@ __global__ void __launch_bounds__(256) consume_k(HashEntry *__restrict__ hash, i
                                                  uint32_t *overflow_flag,
                                                  const unsigned long long *__restrict__ view_contrib,
                                                  unsigned long long *total_contrib,
-                                                 const uint32_t *__restrict__ skip) {
+                                                 const uint32_t *__restrict__ skip,
+                                                 const int32_t *__restrict__ view_base_dev) {
     if (skip && *skip) return;   // (uniform: before any barrier)
+    if (view_base_dev) view_base = *view_base_dev;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // the view's composited pairs join the running total (the view's composite has finished)
     if (g == 0 && view_contrib) atomicAdd(total_contrib, *view_contrib);
@@ -252,7 +257,8 @@ void launch_copy_words(const void *src, void *dst, int64_t bytes, cudaStream_t s
 }
 
 void launch_combine(const WeightRecord *recs, const unsigned long long *rec_chunks, const uint32_t *rec_fill,
-                    unsigned long long chunk_cap, const HashSink &sink, const uint32_t *skip, cudaStream_t st) {
+                    unsigned long long chunk_cap, const HashSink &sink, const uint32_t *skip, cudaStream_t st,
+                    const int32_t *view_base_dev) {
     if (chunk_cap == 0) return;
     const unsigned long long rec_cap = chunk_cap * kRecChunk;
     int dev = 0, sms = 148;
@@ -261,15 +267,17 @@ void launch_combine(const WeightRecord *recs, const unsigned long long *rec_chun
     unsigned blocks = (unsigned)sms * 8u;
     const unsigned long long need = (rec_cap + 255) / 256;
     if (need < blocks) blocks = (unsigned)need;
-    combine_k<<<blocks, 256, 0, st>>>(recs, rec_chunks, rec_fill, chunk_cap, sink, skip); note_launch();
+    combine_k<<<blocks, 256, 0, st>>>(recs, rec_chunks, rec_fill, chunk_cap, sink, skip, view_base_dev);
+    note_launch();
 }
 
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
                     unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key, float *log_w,
                     uint32_t *overflow, const unsigned long long *view_contrib, unsigned long long *total_contrib,
-                    const uint32_t *skip, cudaStream_t st) {
+                    const uint32_t *skip, cudaStream_t st, const int32_t *view_base_dev) {
     consume_k<<<blocks_for(n, 256), 256, 0, st>>>(hash, n, view_base, s_hi, s_lo, log_count, log_cap, log_key,
-                                                  log_w, overflow, view_contrib, total_contrib, skip); note_launch();
+                                                  log_w, overflow, view_contrib, total_contrib, skip, view_base_dev);
+    note_launch();
 }
 
 void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaStream_t st) {

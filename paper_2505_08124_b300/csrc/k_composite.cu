@@ -88,6 +88,7 @@ struct Smem {
     int32_t count[kNB];                   // records in each buffer (-1: no more)
     int32_t warp_live[kConsumers];        // a consumer warp still has a live pixel
     uint32_t abort_flag;                  // a wait gave up: every other wait gives up too
+    int32_t view_base;                    // column of the view's segment 0
     unsigned long long totals[kConsumers][3];   // per consumer warp: contributions, visited, executed
     __align__(8) uint64_t full[kNB];      // a buffer is published (32 producer arrivals)
     __align__(8) uint64_t empty[kNB];     // a buffer is released (128 consumer arrivals)
@@ -189,13 +190,13 @@ __device__ __forceinline__ bool cbar_and(bool p) {
     return r != 0;
 }
 
-__device__ __forceinline__ HashSink sink_of(const CompositeArgs &a) {
-    return HashSink{a.hash, a.log_count, a.log_cap, a.log_key, a.log_w, a.s_ovf, a.overflow, a.view_base};
+__device__ __forceinline__ HashSink sink_of(const CompositeArgs &a, const Smem &sm) {
+    return HashSink{a.hash, a.log_count, a.log_cap, a.log_key, a.log_w, a.s_ovf, a.overflow, sm.view_base};
 }
 
 __device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int b, int slot, int gi, float acc) {
     if (slot < kSmemSlots) atomicAdd(&sm.wb[b][slot][gi], acc);
-    else sink_add(sink_of(a), sm.gid[b][gi], sm.seg_of_slot[slot], acc);
+    else sink_add(sink_of(a, sm), sm.gid[b][gi], sm.seg_of_slot[slot], acc);
 }
 
 // The producer's place in the view's record list: chunk `cur` is being filled (`used` records),
@@ -323,7 +324,7 @@ __device__ void drain_sums(const CompositeArgs &a, Smem &sm, int b, int n, int n
         if (!a.recs) {   // no record list: the sums go to the tables directly
 #pragma unroll
             for (int j = 0; j < kPerLane; ++j)
-                if (v[j] != 0.f) sink_add(sink_of(a), sm.gid[b][lane + 32 * j], seg, v[j]);
+                if (v[j] != 0.f) sink_add(sink_of(a, sm), sm.gid[b][lane + 32 * j], seg, v[j]);
             continue;
         }
         if (!rr.have_cur) {   // the first records: the two chunks reserved at the start
@@ -350,7 +351,7 @@ __device__ void drain_sums(const CompositeArgs &a, Smem &sm, int b, int n, int n
                 r.pad = 0u;
                 a.recs[ch * kRecChunk + (pos < kRecChunk ? pos : pos - kRecChunk)] = r;
             } else {
-                sink_add(sink_of(a), g, seg, v[j]);
+                sink_add(sink_of(a, sm), g, seg, v[j]);
             }
             ++pos;
         }
@@ -499,6 +500,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
         }
         tc::mbar_init(&sm.ready, kPixThreads);
         sm.abort_flag = 0u;
+        sm.view_base = a.view_base_dev ? *a.view_base_dev : a.view_base;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // the (slot x Gaussian) sums start at zero; each buffer's drain clears what it read

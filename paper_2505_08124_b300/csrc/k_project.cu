@@ -135,7 +135,7 @@ __global__ void pack_k(const float *__restrict__ means, const float *__restrict_
                        const float *__restrict__ quats, const float *__restrict__ opac, int64_t n,
                        const uint32_t *__restrict__ orig_of_int, float4 *__restrict__ mean_op,
                        float4 *__restrict__ cov_a, float2 *__restrict__ cov_b,
-                       uint32_t *__restrict__ int_of_orig) {
+                       uint32_t *__restrict__ int_of_orig, float *__restrict__ log2_op) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     int64_t k = orig_of_int[g];
@@ -143,6 +143,8 @@ __global__ void pack_k(const float *__restrict__ means, const float *__restrict_
     cov3(scales[3 * k], scales[3 * k + 1], scales[3 * k + 2], quats[4 * k], quats[4 * k + 1],
          quats[4 * k + 2], quats[4 * k + 3], S);
     mean_op[g] = make_float4(means[3 * k], means[3 * k + 1], means[3 * k + 2], opac[k]);
+    // log2 of the opacity, rounded to float32 from float64 (the alpha floor is decided on it)
+    log2_op[g] = opac[k] > 0.f ? (float)log2((double)opac[k]) : -INFINITY;
     cov_a[g] = make_float4(S[0], S[1], S[2], S[3]);
     cov_b[g] = make_float2(S[4], S[5]);
     int_of_orig[k] = (uint32_t)g;
@@ -151,7 +153,9 @@ __global__ void pack_k(const float *__restrict__ means, const float *__restrict_
 // Per Gaussian (internal order): depth key for the depth sort, written at the
 // caller's index so that a stable sort breaks depth ties by that index;
 // record (mu', conic, opacity, internal index) and tile rectangle.
-__global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__restrict__ mean_op,
+__global__ void __launch_bounds__(256) project_k(CamParams cval, const CamParams *__restrict__ cam_dev,
+                                                 const float4 *__restrict__ mean_op,
+                                                 const float *__restrict__ log2_op,
                                                  const float4 *__restrict__ cov_a, const float2 *__restrict__ cov_b,
                                                  int64_t n, const uint32_t *__restrict__ orig_of_int,
                                                  uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
@@ -159,6 +163,7 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
                                                  float *__restrict__ rec_t,
                                                  uint2 *__restrict__ rect, ViewCounters *ctr) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const CamParams c = cam_dev ? *cam_dev : cval;   // read on the device in replayed graphs
     bool visible = false;
     if (g < n) {
         float4 mo = mean_op[g];
@@ -230,9 +235,8 @@ __global__ void __launch_bounds__(256) project_k(CamParams c, const float4 *__re
                     const float kLog2e = 1.4426950408889634f;
                     const float inv = 1.f / det;
                     const float A = c11 * inv, B = -c01 * inv, C = c00 * inv;
-                    const float op = mo.w;
                     const float a2 = -0.5f * kLog2e * A, b2 = -kLog2e * B, c2 = -0.5f * kLog2e * C;
-                    const float lo = op > 0.f ? log2f(op) : -INFINITY;
+                    const float lo = log2_op[g];
                     const float r1 = -b2 * __frcp_rn(2.f * c2), r2 = -b2 * __frcp_rn(2.f * a2);
                     const float R = r + 32.f;
                     const float S = fabsf(lo) + (fabsf(a2) + fabsf(b2) + fabsf(c2)) * R * R;
@@ -330,15 +334,16 @@ void launch_morton(const float *means, int64_t n, const uint32_t *d_bbox6, uint3
 
 void launch_pack_gaussians(const float *means, const float *scales, const float *quats, const float *opac,
                            int64_t n, const uint32_t *orig_of_int, float4 *mean_op, float4 *cov_a,
-                           float2 *cov_b, uint32_t *int_of_orig, cudaStream_t st) {
+                           float2 *cov_b, uint32_t *int_of_orig, float *log2_op, cudaStream_t st) {
     pack_k<<<blocks_for(n, 256), 256, 0, st>>>(means, scales, quats, opac, n, orig_of_int, mean_op, cov_a,
-                                               cov_b, int_of_orig); note_launch();
+                                               cov_b, int_of_orig, log2_op); note_launch();
 }
 
-void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *cov_a, const float2 *cov_b,
-                    int64_t n, const uint32_t *orig_of_int, uint32_t *dkey_orig, uint32_t *dval_orig,
-                    float4 *rec_a, float4 *rec_b, float *rec_t, uint2 *rect, ViewCounters *ctr, cudaStream_t st) {
-    project_k<<<blocks_for(n, 256), 256, 0, st>>>(cam, mean_op, cov_a, cov_b, n, orig_of_int, dkey_orig,
+void launch_project(const CamParams &cam, const float4 *mean_op, const float *log2_op, const float4 *cov_a,
+                    const float2 *cov_b, int64_t n, const uint32_t *orig_of_int, uint32_t *dkey_orig, uint32_t *dval_orig,
+                    float4 *rec_a, float4 *rec_b, float *rec_t, uint2 *rect, ViewCounters *ctr, cudaStream_t st,
+                    const CamParams *cam_dev) {
+    project_k<<<blocks_for(n, 256), 256, 0, st>>>(cam, cam_dev, mean_op, log2_op, cov_a, cov_b, n, orig_of_int, dkey_orig,
                                                   dval_orig, rec_a, rec_b, rec_t, rect, ctr); note_launch();
 }
 

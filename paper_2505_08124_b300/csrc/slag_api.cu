@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <initializer_list>
 #include <mutex>
 #include <set>
 #include <cmath>
@@ -44,6 +45,10 @@ namespace {
 std::atomic<unsigned long long> g_launches{0};
 }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// kernels of a replayed graph (k), and the undoing of the count of a capture (which launches nothing)
+void note_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void unnote_launches(unsigned long long k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
+unsigned long long launches_now() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t set_max_smem(const void *fn, int bytes) {
     static std::mutex mu;
@@ -63,6 +68,14 @@ namespace {
 
 constexpr int kSlots = 6;   // views in flight
 constexpr int kTotals = 5;  // device running totals (see slag_ctx::totals)
+
+// A view's camera and first column in device memory: the kernels of a replayed graph read them
+// there (everything else they use is fixed while the graph is valid).
+struct ViewParams {
+    CamParams cam;
+    int32_t view_base;
+    int32_t pad[3];
+};
 
 // Buffers of one view in flight. Stage A (front stream) and stage B (second
 // front stream) fill them; the slot's back stream composites from them; stage A
@@ -112,6 +125,13 @@ struct ViewSlot {
     cudaEvent_t ev_done = nullptr;         // back work of the slot's view done
     int64_t log_bound = 0;                 // triples the slot's view may append after stage A
     bool pending = false;                  // its view was sized on the device and is not settled
+    ViewParams *vp_dev = nullptr;          // the view's camera and first column (replayed graphs)
+    ViewParams *vp_host = nullptr;         // pinned staging of vp_dev (rewritten once the slot is settled)
+    // the slot's captured graphs: stages A and B (front stream), composite + combine and consume
+    // (back stream), with the kernels each holds; valid while gkey matches the slot's buffers
+    cudaGraphExec_t gx_front = nullptr, gx_comp = nullptr, gx_cons = nullptr;
+    unsigned long long gn_front = 0, gn_comp = 0, gn_cons = 0;
+    uint64_t gkey_front = 0, gkey_back = 0;
 };
 
 }  // namespace
@@ -131,6 +151,7 @@ struct slag_ctx {
     // Gaussians, internal (Morton) order
     float4 *mean_op = nullptr, *cov_a = nullptr;
     float2 *cov_b = nullptr;
+    float *log2_op = nullptr;                // log2 of each opacity (float64, rounded)
     uint32_t *orig_of_int = nullptr, *int_of_orig = nullptr;
 
     // views in flight
@@ -143,6 +164,7 @@ struct slag_ctx {
                                              // for the next call
     int64_t est_P = 0, est_P_tiles = 0;      // the largest pair counts seen (device-sized views)
     int64_t log_fill_seen = 0;               // the triple log's fill level, as last read
+    bool graphs = true;                      // device-sized views replay captured graphs (slag_set_graphs)
     float *s_hi = nullptr, *s_lo = nullptr, *s_ovf = nullptr;
     float *dbg_T = nullptr, *dbg_wsum = nullptr;
     int32_t *dbg_count = nullptr;
@@ -476,12 +498,12 @@ int ceil_log2(uint64_t v) {
 // the segment map nor the table. The counters and the log's fill level are copied to the
 // slot's mapped host struct; the host reads them once the stage has ended.
 slag_status stage_a(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, const CamParams &cp, int shift,
-                    SortScratch &scr) {
+                    SortScratch &scr, const CamParams *cam_dev = nullptr) {
     const int64_t n = ctx->n;
     CK(cudaMemsetAsync(vs.ctr, 0, sizeof(ViewCounters), st));
     span_begin(ctx, SLAG_STAGE_PROJECT, st);
-    launch_project(cp, ctx->mean_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, vs.dkey[0], vs.dval[0],
-                   vs.rec_a, vs.rec_b, vs.rec_t, vs.rect, vs.ctr, st);
+    launch_project(cp, ctx->mean_op, ctx->log2_op, ctx->cov_a, ctx->cov_b, n, ctx->orig_of_int, vs.dkey[0], vs.dval[0],
+                   vs.rec_a, vs.rec_b, vs.rec_t, vs.rect, vs.ctr, st, cam_dev);
     int shifts[8], widths[8];
     const int np = digit_passes(0, 32, shifts, widths, n);
     const bool alt = radix_sort_u32(vs.dkey[0], vs.dkey[1], vs.dval[0], vs.dval[1], n, shifts, widths, np,
@@ -580,6 +602,8 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
     SA(cudaStreamCreateWithPriority(&vs.front, cudaStreamNonBlocking, hi));
     SA(cudaEventCreateWithFlags(&vs.ev_front, cudaEventDisableTiming));
     SA(scratch_reserve(vs.scratch, n));
+    SA(dalloc(&vs.vp_dev, 1));
+    SA(cudaHostAlloc((void **)&vs.vp_host, sizeof(ViewParams), cudaHostAllocDefault));
     SA(cudaEventCreateWithFlags(&vs.ev_a, cudaEventDisableTiming));
     SA(cudaEventCreateWithFlags(&vs.ev_up, cudaEventDisableTiming));
     SA(cudaEventCreateWithFlags(&vs.ev_bin, cudaEventDisableTiming));
@@ -601,6 +625,13 @@ void slot_free(ViewSlot &vs) {
     if (vs.front) cudaStreamDestroy(vs.front);
     vs.front = nullptr;
     scratch_free(vs.scratch);
+    dfree(vs.vp_dev);
+    if (vs.vp_host) cudaFreeHost(vs.vp_host);
+    vs.vp_host = nullptr;
+    for (cudaGraphExec_t *g : {&vs.gx_front, &vs.gx_comp, &vs.gx_cons}) {
+        if (*g) cudaGraphExecDestroy(*g);
+        *g = nullptr;
+    }
     for (cudaEvent_t *e : {&vs.ev_a, &vs.ev_up, &vs.ev_bin, &vs.ev_done, &vs.ev_front}) {
         if (*e) cudaEventDestroy(*e);
         *e = nullptr;
@@ -710,8 +741,9 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
                               ctx->scratch, st);
     CA(cudaMemcpyAsync(ctx->orig_of_int, s0.dval[alt ? 1 : 0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
     CA(dalloc(&ctx->mean_op, n)); CA(dalloc(&ctx->cov_a, n)); CA(dalloc(&ctx->cov_b, n));
+    CA(dalloc(&ctx->log2_op, n));
     launch_pack_gaussians(im, is, iq, io, n, ctx->orig_of_int, ctx->mean_op, ctx->cov_a, ctx->cov_b,
-                          ctx->int_of_orig, st);
+                          ctx->int_of_orig, ctx->log2_op, st);
 
     // accumulators and outputs
     CA(dalloc(&ctx->s_hi, n)); CA(dalloc(&ctx->s_lo, n)); CA(dalloc(&ctx->s_ovf, n));
@@ -737,13 +769,9 @@ slag_status slag_create(const slag_gaussians *g, const slag_options *opt, slag_c
 
 namespace {
 
-// The back half of a view whose binning is queued (ev_bin): room in the triple log and in the
-// record list, then the composite, the combine pass and the consume pass on the slot's back
-// stream, and a copy of the view's counters and the log's fill level to the slot's mapped host
-// struct at its end. P_tiles bounds the view's Gaussian-tile pairs (exact, or an estimate for a
-// view sized on the device); a non-null skip makes the three passes do nothing when *skip is set.
-slag_status queue_back_half(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list, int64_t P_tiles,
-                            const uint32_t *skip) {
+// Room in the triple log and in the record list for the back half of the slot's view. P_tiles
+// bounds the view's Gaussian-tile pairs (exact, or an estimate for a view sized on the device).
+slag_status prepare_back_half(slag_ctx *ctx, ViewSlot &vs, int64_t P_tiles) {
     const CamParams &cp = vs.cp;
     cudaStream_t fb = vs.front;
     // room in the triple log: its fill level as last seen, plus what the other views in flight
@@ -781,11 +809,16 @@ slag_status queue_back_half(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list, i
         vs.rec_cap = vs.rec_cap / kRecChunk * kRecChunk;
         CK(grow(vs.rec_fill, vs.fill_cap, vs.rec_cap / kRecChunk, fb));
     }
+    return SLAG_OK;
+}
 
-    // back half on the slot's stream
+// The composite and the combine pass of the slot's view on its back stream (after its binning
+// and its upload). A non-null skip makes both do nothing when *skip is set; a non-null
+// view_base_dev gives the view's first column in device memory (replayed graphs).
+slag_status enqueue_composite(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list, const uint32_t *skip,
+                              const int32_t *view_base_dev) {
+    const CamParams &cp = vs.cp;
     cudaStream_t bk = vs.back;
-    CK(cudaStreamWaitEvent(bk, vs.ev_bin, 0));
-    CK(cudaStreamWaitEvent(bk, vs.ev_up, 0));   // the segment map
     CK(cudaMemsetAsync(vs.rec_chunks, 0, sizeof(unsigned long long), bk));
     CompositeArgs a;
     a.cam = cp;
@@ -801,6 +834,7 @@ slag_status queue_back_half(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list, i
     a.n_ids = (uint32_t)ctx->n;
     a.seg = vs.seg_buf;
     a.view_base = (int32_t)vs.view_base;
+    a.view_base_dev = view_base_dev;
     a.weight_mode = ctx->weight_mode;
     a.hash = vs.hash;
     a.log_count = ctx->log_count;
@@ -833,20 +867,47 @@ slag_status queue_back_half(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list, i
                         ctx->s_ovf, reinterpret_cast<uint32_t *>(ctx->totals + 2), (int32_t)vs.view_base};
     span_begin(ctx, SLAG_STAGE_CONSUME, bk);
     launch_combine(vs.recs, vs.rec_chunks, vs.rec_fill, (unsigned long long)(vs.rec_cap / kRecChunk), sink, skip,
-                   bk);
+                   bk, view_base_dev);
     span_end(ctx, bk);
-    // consumes in view order: the compensated sums are updated without atomics
-    CK(cudaStreamWaitEvent(bk, ctx->ev_consumed, 0));
+    CK(cudaGetLastError());
+    return SLAG_OK;
+}
+
+// The consume pass of the slot's view on its back stream (after the previous view's consume),
+// then the copy of the view's counters and the log's fill level to the slot's mapped host struct.
+slag_status enqueue_consume(slag_ctx *ctx, ViewSlot &vs, const uint32_t *skip, const int32_t *view_base_dev) {
+    cudaStream_t bk = vs.back;
     span_begin(ctx, SLAG_STAGE_CONSUME, bk);
     launch_consume(vs.hash, ctx->n, (int32_t)vs.view_base, ctx->s_hi, ctx->s_lo, ctx->log_count,
                    (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
-                   reinterpret_cast<uint32_t *>(ctx->totals + 2), &vs.ctr->contributions, ctx->contrib, skip, bk);
+                   reinterpret_cast<uint32_t *>(ctx->totals + 2), &vs.ctr->contributions, ctx->contrib, skip, bk,
+                   view_base_dev);
     span_end(ctx, bk);
-    CK(cudaEventRecord(ctx->ev_consumed, bk));
     launch_copy_words(vs.ctr, &vs.h_dev->v, sizeof(ViewCounters), bk);
     launch_copy_words(ctx->totals, vs.h_dev->totals, kTotals * sizeof(unsigned long long), bk);
-    CK(cudaEventRecord(vs.ev_done, bk));
     CK(cudaGetLastError());
+    return SLAG_OK;
+}
+
+// The back half of a view whose binning is queued (ev_bin): room in the triple log and in the
+// record list, then the composite, the combine pass and (in view order: the compensated sums are
+// updated without atomics) the consume pass on the slot's back stream, and a copy of the view's
+// counters to the slot's mapped host struct at its end. P_tiles bounds the view's Gaussian-tile
+// pairs; a non-null skip makes the passes do nothing when *skip is set.
+slag_status queue_back_half(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list, int64_t P_tiles,
+                            const uint32_t *skip) {
+    slag_status s = prepare_back_half(ctx, vs, P_tiles);
+    if (s != SLAG_OK) return s;
+    cudaStream_t bk = vs.back;
+    CK(cudaStreamWaitEvent(bk, vs.ev_bin, 0));
+    CK(cudaStreamWaitEvent(bk, vs.ev_up, 0));   // the segment map
+    s = enqueue_composite(ctx, vs, list, skip, nullptr);
+    if (s != SLAG_OK) return s;
+    CK(cudaStreamWaitEvent(bk, ctx->ev_consumed, 0));
+    s = enqueue_consume(ctx, vs, skip, nullptr);
+    if (s != SLAG_OK) return s;
+    CK(cudaEventRecord(ctx->ev_consumed, bk));
+    CK(cudaEventRecord(vs.ev_done, bk));
     return SLAG_OK;
 }
 
@@ -883,14 +944,20 @@ slag_status launch_deferred_view(slag_ctx *ctx) {
     return SLAG_OK;
 }
 
-// Stage B of a view sized on the device: the binning reads the view's counts from device
-// memory and holds at most an estimate of its pairs (the largest count seen so far, with a
-// quarter more); a view with more sets its overflow flag, which makes its binning leave every
-// bin empty and its back half do nothing. The host finds the flag when it settles the view.
-slag_status stage_b_async(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, uint32_t **list_out) {
+// The pair capacity of a view sized on the device: the largest pair count seen so far, with a
+// quarter more, rounded up to a sixteenth of its power of two (so that it changes rarely).
+int64_t device_pair_cap(const slag_ctx *ctx) {
+    int64_t c = ctx->est_P + ctx->est_P / 4 + 4096;
+    int b = 0;
+    while ((1ll << (b + 1)) <= c) ++b;
+    const int64_t step = b >= 4 ? (1ll << (b - 4)) : 1;
+    return (c + step - 1) / step * step;
+}
+
+// The buffers of stage B of a view sized on the device, for `cap` pairs.
+slag_status prepare_stage_b_async(slag_ctx *ctx, ViewSlot &vs, int64_t cap) {
     const CamParams &cp = vs.cp;
-    const int shift = kSuperShift;
-    const int64_t cap = ctx->est_P + ctx->est_P / 4 + 4096;
+    cudaStream_t st = vs.front;
     if (cap > 0x7fffffffLL) return fail(ctx, SLAG_ERR_CAPACITY, "more than 2^31-1 Gaussian-tile pairs in one view");
     if (cap > vs.p_cap) {
         int64_t c0 = vs.p_cap;
@@ -902,12 +969,23 @@ slag_status stage_b_async(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, uint32_t
         }
     }
     CK(scratch_reserve(vs.scratch, vs.p_cap));
+    const int bins_x = ((cp.tiles_x - 1) >> kSuperShift) + 1, bins_y = ((cp.tiles_y - 1) >> kSuperShift) + 1;
+    CK(grow(vs.ranges, vs.ranges_cap, (int64_t)bins_x * bins_y, st));
+    CK(grow(vs.prect, vs.prect_cap, cap, st));
+    CK(grow(vs.tile_order, vs.order_cap, (int64_t)cp.tiles_x * cp.tiles_y, st));
+    return SLAG_OK;
+}
+
+// Stage B of a view sized on the device: the binning reads the view's counts from device
+// memory and holds at most `cap` pairs; a view with more sets its overflow flag, which makes its
+// binning leave every bin empty and its back half do nothing. The host finds the flag when it
+// settles the view. Buffers from prepare_stage_b_async.
+slag_status enqueue_stage_b_async(slag_ctx *ctx, ViewSlot &vs, int64_t cap, uint32_t **list_out) {
+    const CamParams &cp = vs.cp;
+    cudaStream_t st = vs.front;
+    const int shift = kSuperShift;
     const int bins_x = ((cp.tiles_x - 1) >> shift) + 1, bins_y = ((cp.tiles_y - 1) >> shift) + 1;
     const int64_t bins = (int64_t)bins_x * bins_y;
-    const int64_t tiles = (int64_t)cp.tiles_x * cp.tiles_y;
-    CK(grow(vs.ranges, vs.ranges_cap, bins, st));
-    CK(grow(vs.prect, vs.prect_cap, cap, st));
-    CK(grow(vs.tile_order, vs.order_cap, tiles, st));
     span_begin(ctx, SLAG_STAGE_BIN, st);
     if (!bin_sort_fused(vs.srect, vs.offsets, vs.stouched, ctx->n, &vs.ctr->n_visible, &vs.ctr->P, cap, 0,
                         &vs.ctr->overflow, shift, bins_x, (int)bins, vs.sgid, vs.pval[0], vs.prect, vs.ranges,
@@ -918,6 +996,57 @@ slag_status stage_b_async(slag_ctx *ctx, ViewSlot &vs, cudaStream_t st, uint32_t
     CK(cudaGetLastError());
     *list_out = vs.pval[0];
     return SLAG_OK;
+}
+
+// Stream capture of enqueue() on st into *exec (replacing it) and the number of kernels it holds
+// in *nk; the capture launches nothing, so its count is taken back from the launch counter.
+template <typename F>
+slag_status capture_graph(slag_ctx *ctx, cudaStream_t st, cudaGraphExec_t *exec, unsigned long long *nk, F enqueue) {
+    if (*exec) cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+    const unsigned long long before = launches_now();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const slag_status s = enqueue();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    const unsigned long long k = launches_now() - before;
+    unnote_launches(k);
+    if (s == SLAG_OK && e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (s != SLAG_OK) return s;
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        (void)cudaGetLastError();
+        return fail(ctx, SLAG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    *nk = k;
+    return SLAG_OK;
+}
+
+// A hash of the values a slot's captured graphs depend on (FNV-1a over 64-bit words).
+uint64_t graph_key(std::initializer_list<uint64_t> vals) {
+    uint64_t h = 1469598103934665603ull;
+    for (uint64_t v : vals)
+        for (int b = 0; b < 8; ++b) {
+            h ^= (v >> (8 * b)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    return h;
+}
+
+uint64_t front_key(const slag_ctx *ctx, const ViewSlot &vs, int64_t cap) {
+    auto P = [](const void *p) { return (uint64_t)(uintptr_t)p; };
+    return graph_key({1, (uint64_t)vs.cp.width, (uint64_t)vs.cp.height, (uint64_t)ctx->n, (uint64_t)cap,
+                      (uint64_t)vs.p_cap, P(vs.pval[0]), P(vs.prect), P(vs.ranges), P(vs.tile_order),
+                      P(vs.scratch.hist), P(vs.scratch.tstart), P(vs.scratch.digit_tot), P(vs.scratch.partials)});
+}
+
+uint64_t back_key(const slag_ctx *ctx, const ViewSlot &vs) {
+    auto P = [](const void *p) { return (uint64_t)(uintptr_t)p; };
+    return graph_key({2, (uint64_t)vs.cp.width, (uint64_t)vs.cp.height, (uint64_t)ctx->n, P(vs.pval[0]),
+                      P(vs.prect), P(vs.ranges), P(vs.tile_order), P(vs.seg_buf), P(vs.recs), P(vs.rec_fill),
+                      (uint64_t)vs.rec_cap, P(ctx->log_key), P(ctx->log_w), (uint64_t)ctx->log_cap,
+                      (uint64_t)ctx->weight_mode});
 }
 
 // Settles the slot's view if it was sized on the device: waits for it, counts it, and when its
@@ -983,6 +1112,16 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     // the slot's previous view, if it was sized on the device, is settled before its buffers go
     s = settle_slot(ctx, vs);
     if (s != SLAG_OK) return s;
+    // the view's second half: sized on the device and queued by this call when earlier views give
+    // an estimate of its pair count (and its bins fit the single-pass binning), as replays of the
+    // slot's captured graphs unless stages are being timed; otherwise sized on the host, in the
+    // next call
+    const int64_t bins = (int64_t)(((cp.tiles_x - 1) >> kSuperShift) + 1) * (((cp.tiles_y - 1) >> kSuperShift) + 1);
+    const bool device_sized = ctx->est_P > 0 && bins <= 2048 && !(kChecked && ctx->force_pair_cap > 0);
+    const bool graphed = device_sized && ctx->graphs && ctx->prof_mask == 0;
+    const int64_t cap = device_sized ? device_pair_cap(ctx) : 0;
+    vs.cp = cp;
+    vs.view_base = ctx->table_rows;
 
     // stage A and the uploads start after the caller's work so far (inputs written on the
     // caller's stream) and after the slot's previous view has been composited and consumed
@@ -1021,10 +1160,45 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
             const slag_status sp = issue_pending(ctx, 1);
             if (sp != SLAG_OK) return sp;
         }
-        // stage A of this view, then the previous view's second half
-        const slag_status sa = stage_a(ctx, vs, fr, cp, kSuperShift, vs.scratch);
-        if (sa != SLAG_OK) return sa;
-        CK(cudaEventRecord(vs.ev_a, fr));
+        // stage A of this view (and stage B when it is sized on the device), then the previous
+        // view's second half
+        if (device_sized) {
+            const slag_status sp = prepare_stage_b_async(ctx, vs, cap);
+            if (sp != SLAG_OK) return sp;
+        }
+        bool front_graph = graphed;
+        if (graphed) {
+            vs.vp_host->cam = cp;
+            vs.vp_host->view_base = (int32_t)vs.view_base;
+            CK(cudaMemcpyAsync(vs.vp_dev, vs.vp_host, sizeof(ViewParams), cudaMemcpyHostToDevice, fr));
+            const uint64_t key = front_key(ctx, vs, cap);
+            if (!vs.gx_front || vs.gkey_front != key) {
+                vs.gkey_front = 0;
+                const slag_status sc = capture_graph(ctx, fr, &vs.gx_front, &vs.gn_front, [&]() -> slag_status {
+                    const slag_status sa = stage_a(ctx, vs, fr, cp, kSuperShift, vs.scratch, &vs.vp_dev->cam);
+                    if (sa != SLAG_OK) return sa;
+                    uint32_t *list = nullptr;
+                    return enqueue_stage_b_async(ctx, vs, cap, &list);
+                });
+                if (sc == SLAG_OK) vs.gkey_front = key;
+                else front_graph = false;   // launched kernel by kernel instead
+            }
+        }
+        if (front_graph) {
+            CK(cudaGraphLaunch(vs.gx_front, fr));
+            note_launches(vs.gn_front);
+            CK(cudaEventRecord(vs.ev_a, fr));
+        } else {
+            const slag_status sa = stage_a(ctx, vs, fr, cp, kSuperShift, vs.scratch);
+            if (sa != SLAG_OK) return sa;
+            CK(cudaEventRecord(vs.ev_a, fr));
+            if (device_sized) {
+                uint32_t *list = nullptr;
+                const slag_status sb = enqueue_stage_b_async(ctx, vs, cap, &list);
+                if (sb != SLAG_OK) return sb;
+            }
+        }
+        if (device_sized) CK(cudaEventRecord(vs.ev_bin, fr));
         return launch_deferred_view(ctx);
     };
     s = queue_view();
@@ -1037,22 +1211,43 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
     CK(cudaEventSynchronize(vs.ev_up));
     CK(cudaGetLastError());
     if (vs.h->vu.bad_seg) return fail(ctx, SLAG_ERR_INVALID_ARG, "segment id outside [-1, M)");
-    vs.cp = cp;
-    vs.view_base = ctx->table_rows;
-    // the view's second half: sized on the device and queued now when earlier views give an
-    // estimate of its pair count (and its bins fit the single-pass binning); otherwise sized on
-    // the host, in the next call
-    const int64_t bins = (int64_t)(((cp.tiles_x - 1) >> kSuperShift) + 1) * (((cp.tiles_y - 1) >> kSuperShift) + 1);
-    const bool device_sized = ctx->est_P > 0 && bins <= 2048 && !(kChecked && ctx->force_pair_cap > 0);
     if (device_sized) {
-        cudaStream_t fb = vs.front;
-        CK(cudaStreamWaitEvent(fb, vs.ev_a, 0));
-        uint32_t *list = nullptr;
-        s = stage_b_async(ctx, vs, fb, &list);
-        if (s != SLAG_OK) return s;
-        CK(cudaEventRecord(vs.ev_bin, fb));
-        s = queue_back_half(ctx, vs, list, ctx->est_P_tiles + ctx->est_P_tiles / 4 + 4096, &vs.ctr->overflow);
-        if (s != SLAG_OK) return s;
+        // the back half: queued now (the composite waits for the binning and the upload; its
+        // passes do nothing if the binning overflowed)
+        const int64_t tiles_bound = ctx->est_P_tiles + ctx->est_P_tiles / 4 + 4096;
+        bool back_graph = graphed;
+        if (graphed) {
+            s = prepare_back_half(ctx, vs, tiles_bound);
+            if (s != SLAG_OK) return s;
+            const uint64_t key = back_key(ctx, vs);
+            if (!vs.gx_comp || !vs.gx_cons || vs.gkey_back != key) {
+                vs.gkey_back = 0;
+                slag_status sc = capture_graph(ctx, vs.back, &vs.gx_comp, &vs.gn_comp, [&]() {
+                    return enqueue_composite(ctx, vs, vs.pval[0], &vs.ctr->overflow, &vs.vp_dev->view_base);
+                });
+                if (sc == SLAG_OK)
+                    sc = capture_graph(ctx, vs.back, &vs.gx_cons, &vs.gn_cons, [&]() {
+                        return enqueue_consume(ctx, vs, &vs.ctr->overflow, &vs.vp_dev->view_base);
+                    });
+                if (sc == SLAG_OK) vs.gkey_back = key;
+                else back_graph = false;   // launched kernel by kernel instead
+            }
+        }
+        if (back_graph) {
+            cudaStream_t bk = vs.back;
+            CK(cudaStreamWaitEvent(bk, vs.ev_bin, 0));
+            CK(cudaStreamWaitEvent(bk, vs.ev_up, 0));   // the segment map
+            CK(cudaGraphLaunch(vs.gx_comp, bk));
+            note_launches(vs.gn_comp);
+            CK(cudaStreamWaitEvent(bk, ctx->ev_consumed, 0));   // consumes in view order
+            CK(cudaGraphLaunch(vs.gx_cons, bk));
+            note_launches(vs.gn_cons);
+            CK(cudaEventRecord(ctx->ev_consumed, bk));
+            CK(cudaEventRecord(vs.ev_done, bk));
+        } else {
+            s = queue_back_half(ctx, vs, vs.pval[0], tiles_bound, &vs.ctr->overflow);
+            if (s != SLAG_OK) return s;
+        }
         vs.pending = true;
     }
     ctx->views_enqueued += 1;
@@ -2185,6 +2380,12 @@ slag_status slag_add_views_batched(int32_t n_ctx, slag_ctx *const *ctxs, const s
     return SLAG_OK;
 }
 
+slag_status slag_set_graphs(slag_ctx *ctx, int32_t enable) {
+    if (!ctx) return SLAG_ERR_INVALID_ARG;
+    ctx->graphs = enable != 0;
+    return SLAG_OK;
+}
+
 slag_status slag_set_autotune(slag_ctx *ctx, int32_t enable) {
     if (!ctx) return SLAG_ERR_INVALID_ARG;
     ctx->autotune = enable != 0;
@@ -2252,7 +2453,8 @@ void slag_destroy(slag_ctx *ctx) {
         if (ctx->ev_copy[b]) cudaEventDestroy(ctx->ev_copy[b]);
     ctx->E = ctx->wsum = nullptr;
     for (int b = 0; b < 2; ++b) { dfree(ctx->E_buf[b]); dfree(ctx->wsum_buf[b]); }
-    dfree(ctx->mean_op); dfree(ctx->cov_a); dfree(ctx->cov_b); dfree(ctx->orig_of_int); dfree(ctx->int_of_orig);
+    dfree(ctx->mean_op); dfree(ctx->cov_a); dfree(ctx->cov_b); dfree(ctx->log2_op);
+    dfree(ctx->orig_of_int); dfree(ctx->int_of_orig);
     dfree(ctx->s_hi); dfree(ctx->s_lo); dfree(ctx->s_ovf);
     dfree(ctx->dbg_T); dfree(ctx->dbg_wsum); dfree(ctx->dbg_count);
     dfree(ctx->totals); dfree(ctx->touched); dfree(ctx->tc_err);

@@ -166,11 +166,11 @@ void launch_morton(const float *means, int64_t n, const uint32_t *d_bbox6, uint3
 void launch_pack_gaussians(const float *means, const float *scales, const float *quats,
                            const float *opac, int64_t n, const uint32_t *orig_of_int,
                            float4 *mean_op, float4 *cov_a, float2 *cov_b, uint32_t *int_of_orig,
-                           cudaStream_t st);
-void launch_project(const CamParams &cam, const float4 *mean_op, const float4 *cov_a,
+                           float *log2_op, cudaStream_t st);
+void launch_project(const CamParams &cam, const float4 *mean_op, const float *log2_op, const float4 *cov_a,
                     const float2 *cov_b, int64_t n, const uint32_t *orig_of_int, uint32_t *dkey_orig,
                     uint32_t *dval_orig, float4 *rec_a, float4 *rec_b, float *rec_t, uint2 *rect,
-                    ViewCounters *ctr, cudaStream_t st);
+                    ViewCounters *ctr, cudaStream_t st, const CamParams *cam_dev = nullptr);
 // Rectangles and bin counts in depth-rank order. With shift s > 0 the count is of
 // 2^s x 2^s-tile super-tiles; the tile-pair total goes to ctr->P_tiles.
 void launch_gather_sorted(const uint32_t *sorted_vals, int64_t n, ViewCounters *ctr, const uint2 *rect,
@@ -263,6 +263,7 @@ struct CompositeArgs {
     uint32_t n_ids;                // Gaussians (records in rec_a / rec_b)
     const int32_t *seg;            // H x W
     int32_t view_base;             // column of segment 0 of this view
+    const int32_t *view_base_dev;  // nullable: the same, read on the device (replayed graphs)
     int32_t weight_mode;
     HashEntry *hash;               // n entries (internal order)
     unsigned long long *log_count;
@@ -305,13 +306,15 @@ void launch_copy_words(const void *src, void *dst, int64_t bytes, cudaStream_t s
 // Adds the view's records to the per-Gaussian tables: of the first min(*rec_chunks, chunk_cap)
 // chunks, the first rec_fill[c] records of chunk c. Nothing when *skip (nullable) is non-zero.
 void launch_combine(const WeightRecord *recs, const unsigned long long *rec_chunks, const uint32_t *rec_fill,
-                    unsigned long long chunk_cap, const HashSink &sink, const uint32_t *skip, cudaStream_t st);
+                    unsigned long long chunk_cap, const HashSink &sink, const uint32_t *skip, cudaStream_t st,
+                    const int32_t *view_base_dev = nullptr);
 // The view's per-Gaussian tables to triples and the compensated weight sums (k_accum.cu).
 // Nothing when *skip (nullable) is non-zero.
 void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
                     unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key,
                     float *log_w, uint32_t *overflow, const unsigned long long *view_contrib,
-                    unsigned long long *total_contrib, const uint32_t *skip, cudaStream_t st);
+                    unsigned long long *total_contrib, const uint32_t *skip, cudaStream_t st,
+                    const int32_t *view_base_dev = nullptr);
 void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaStream_t st);
 // keys in the compact layout (launch_repack_keys with to_compact) of columns < 2^col_bits
 void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z, int col_bits,

@@ -73,7 +73,7 @@ EXPORTS = ("slag_create", "slag_add_view", "slag_finalize", "slag_query", "slag_
            "slag_save_state", "slag_load_state", "slag_merge_state", "slag_state_merge_host",
            "slag_check_wait_timeout", "slag_is_checked_build", "slag_debug_force_pair_capacity",
            "slag_linear_param_count", "slag_linear_code_fit", "slag_set_linear_code", "slag_query_threshold",
-           "slag_set_device_budget")
+           "slag_set_device_budget", "slag_set_graphs")
 STAGES = ("project", "bin", "composite", "consume", "log_sort", "aggregate", "query")
 
 
@@ -133,6 +133,7 @@ def load_library(path: str = LIB_PATH):
     lib.slag_set_device_budget.argtypes = [P, i64]
     lib.slag_add_views_batched.argtypes = [i32, P, P, P, ctypes.POINTER(i32)]
     lib.slag_set_autotune.argtypes = [P, i32]
+    lib.slag_set_graphs.argtypes = [P, i32]
     lib.slag_kernel_launches.argtypes = []
     lib.slag_kernel_launches.restype = ctypes.c_uint64
     lib.slag_noalloc_query_topk.argtypes = [P, i64, i32, P, P, i32, i32, P, P, P, P]
@@ -354,6 +355,10 @@ class Lifter:
 
     def set_autotune(self, on: bool = True):
         self._check(self._lib.slag_set_autotune(self._h, 1 if on else 0), "slag_set_autotune")
+
+    def set_graphs(self, on: bool = True):
+        """Replay captured CUDA graphs for views sized on the device (on by default)."""
+        self._check(self._lib.slag_set_graphs(self._h, 1 if on else 0), "slag_set_graphs")
 
     def export_partitions(self, directory: str, cells_x: int, cells_y: int, chunk_gaussians: int = 0) -> int:
         """Per-area embedding files of the touched Gaussians (see slag_export_partitions); returns

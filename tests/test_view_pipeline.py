@@ -172,3 +172,30 @@ def test_views_outgrowing_the_estimate_are_binned_again(slag):
     relw = np.linalg.norm(w.astype(np.float64) - den) / np.linalg.norm(den)
     assert rel <= 1e-4 and relw <= 1e-4, (rel, relw)
 
+
+
+def test_graph_replays_match_kernel_launches(slag):
+    # views sized on the device replay the slot's captured graphs (on by default) or launch kernel
+    # by kernel, with two image sizes in one context; the two give the same sums, and the oracle's
+    g = synth.small_scene(44, 6000, 1, 16, 16, 4, dim=128, surfaces=4).gaussians
+    s = synth.make_scene("alt", 44, g, n_views=14, width=176, height=120, n_segments=8, n_protos=8, dim=128,
+                         jitter=True, resolutions=[(176, 120), (176, 120), (208, 96)])
+    views = list(s.views())
+    out = {}
+    for graphs in (True, False):
+        with slag.Lifter(g, dim=128) as L:
+            L.set_graphs(graphs)
+            n0 = slag.kernel_launches()
+            for v in views:
+                L.add_view(v.camera, v.seg, v.table)
+            E, w = L.finalize()
+            out[graphs] = (E, w, L.stats(), slag.kernel_launches() - n0)
+    _close(out[True][:2], out[False][:2])
+    for k in ("views", "pairs", "triples", "contributions", "columns"):
+        assert out[True][2][k] == out[False][2][k], k
+    # the launch counter counts the replayed graphs' kernels, not their captures
+    assert out[True][3] == out[False][3]
+    num, den, _ = O.lift(g, views)
+    Eo = O.normalise(num, den)
+    rel = np.linalg.norm(out[True][0].astype(np.float64) - Eo) / np.linalg.norm(Eo)
+    assert rel <= 1e-4, rel
