@@ -124,11 +124,12 @@ typedef struct {
 } slag_options;
 
 /* Counters of the views added since create / reset. views and columns count
- * every accepted view; pairs, last_pairs and resized_views count the views
- * whose pair count the host has read (all of them after a finalize); a view
- * sized on the device is read when its slot is reused or the views are
- * joined; contributions, triples, last_contributions, evaluations and
- * executed are read at finalize. */
+ * every accepted view; pairs, last_pairs, resized_views and recomposited_views
+ * count the views whose counters the host has read (all of them after a
+ * finalize); a view is read when its slot is reused or the views are joined;
+ * contributions, triples, last_contributions, evaluations and executed are
+ * read at finalize. evaluations and executed count the compositing work done,
+ * so a view composited twice counts twice there (and once everywhere else). */
 typedef struct {
     int64_t views;           /* views added since create / reset */
     int64_t pairs;           /* sum over views of Gaussian-tile pairs P */
@@ -148,6 +149,10 @@ typedef struct {
                                 for all 64 pixels; read at finalize */
     int64_t resized_views;   /* views sized on the device whose pairs exceeded the capacity of
                                 their binning, binned again with their exact count */
+    int64_t recomposited_views; /* views whose (Gaussian, segment) sums overflowed their slot's
+                                spill list (sums of Gaussians that reach more segments of the
+                                view than the per-Gaussian table holds), composited again with
+                                a list that holds them all */
 } slag_stats;
 
 /* Create a context over the Gaussian set (Method, Rasterizer_SLAG statement:

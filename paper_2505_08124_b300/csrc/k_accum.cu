@@ -5,7 +5,10 @@
 // into sparse triples (Gaussian k, column c = view base + segment, W) in an
 // append-only log -- only non-zero weights leave the view, as in the paper's
 // hand-off from the rasterization phase to the aggregation phase -- and adds
-// the weights to a compensated (Neumaier) float32 sum per Gaussian.
+// the weights to a compensated (Neumaier) float32 sum per Gaussian. Sums of
+// a Gaussian whose table slots are all taken by other segments of the view
+// wait in the view's spill list; the consume pass moves them to the log too
+// (their weights join a plain per-Gaussian float32 sum).
 //
 // At finalize, the log is sorted by (Gaussian block of 128, column,
 // Gaussian), so that each block of 128 spatially adjacent Gaussians (Morton
@@ -52,25 +55,59 @@ __global__ void __launch_bounds__(256) combine_k(const WeightRecord *__restrict_
     }
 }
 
-__global__ void __launch_bounds__(256) consume_k(HashEntry *__restrict__ hash, int64_t n, int32_t view_base,
-                                                 float *__restrict__ s_hi, float *__restrict__ s_lo,
-                                                 unsigned long long *log_count, unsigned long long log_cap,
-                                                 uint64_t *__restrict__ log_key, float *__restrict__ log_w,
-                                                 uint32_t *overflow_flag,
-                                                 const unsigned long long *__restrict__ view_contrib,
-                                                 unsigned long long *total_contrib,
-                                                 const uint32_t *__restrict__ skip,
-                                                 const int32_t *__restrict__ view_base_dev) {
-    if (skip && *skip) return;   // (uniform: before any barrier)
-    if (view_base_dev) view_base = *view_base_dev;
+// The view's spill list to the log: grid-stride over chunks of 256 entries, one reservation in
+// the log per chunk. Nothing when the list overflowed (the view is composited again).
+__global__ void __launch_bounds__(256) spill_commit_k(const ConsumeArgs a) {
+    if (a.skip && *a.skip) return;
+    const unsigned long long ns = *a.spill_count;
+    if (ns == 0 || ns > a.spill_cap) return;
+    __shared__ unsigned long long base_s;
+    for (unsigned long long c0 = (unsigned long long)blockIdx.x * 256; c0 < ns;
+         c0 += (unsigned long long)gridDim.x * 256) {
+        const unsigned long long cnt = ns - c0 < 256 ? ns - c0 : 256;
+        if (threadIdx.x == 0) base_s = atomicAdd(a.log_count, cnt);
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            const unsigned long long at = base_s + threadIdx.x;
+            const uint64_t key = a.spill_key[c0 + threadIdx.x];
+            const float w = a.spill_w[c0 + threadIdx.x];
+            if (at < a.log_cap) {
+                a.log_key[at] = key;
+                a.log_w[at] = w;
+                atomicAdd(&a.s_ovf[key_gaussian(key)], w);
+            } else {
+                atomicOr(a.overflow, 1u);
+            }
+        }
+        __syncthreads();   // base_s is rewritten by the next chunk
+    }
+}
+
+__global__ void __launch_bounds__(256) consume_k(const ConsumeArgs a) {
+    if (a.skip && *a.skip) return;   // (uniform: before any barrier)
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = a.n;
+    if (*a.spill_count > a.spill_cap) {
+        // the view is composited again: its tables are cleared, nothing is counted
+        if (g < n) {
+            HashEntry clear;
+#pragma unroll
+            for (int s = 0; s < kHashSlots; ++s) {
+                clear.seg[s] = -1;
+                clear.w[s] = 0.f;
+            }
+            a.hash[g] = clear;
+        }
+        return;
+    }
+    const int32_t view_base = a.view_base_dev ? *a.view_base_dev : a.view_base;
     // the view's composited pairs join the running total (the view's composite has finished)
-    if (g == 0 && view_contrib) atomicAdd(total_contrib, *view_contrib);
+    if (g == 0 && a.view_contrib) atomicAdd(a.total_contrib, *a.view_contrib);
     const int lane = threadIdx.x & 31;
     HashEntry e;
     int cnt = 0;
     if (g < n) {
-        e = hash[g];
+        e = a.hash[g];
 #pragma unroll
         for (int s = 0; s < kHashSlots; ++s) cnt += e.seg[s] >= 0 ? 1 : 0;
     }
@@ -91,11 +128,11 @@ __global__ void __launch_bounds__(256) consume_k(HashEntry *__restrict__ hash, i
         before += q < w ? wtot_s[q] : 0;
         btot += wtot_s[q];
     }
-    if (threadIdx.x == 0) base_s = btot ? atomicAdd(log_count, (unsigned long long)btot) : 0ull;
+    if (threadIdx.x == 0) base_s = btot ? atomicAdd(a.log_count, (unsigned long long)btot) : 0ull;
     __syncthreads();
     if (g >= n || cnt == 0) return;
     unsigned long long at = base_s + (unsigned long long)(before + incl - cnt);
-    float sh = s_hi[g], sl = s_lo[g];
+    float sh = a.s_hi[g], sl = a.s_lo[g];
     bool overflow = false;
     HashEntry clear;
 #pragma unroll
@@ -103,9 +140,9 @@ __global__ void __launch_bounds__(256) consume_k(HashEntry *__restrict__ hash, i
         clear.seg[s] = -1;
         clear.w[s] = 0.f;
         if (e.seg[s] < 0) continue;
-        if (at < log_cap) {
-            log_key[at] = pack_key((uint32_t)g, (uint32_t)(view_base + e.seg[s]));
-            log_w[at] = e.w[s];
+        if (at < a.log_cap) {
+            a.log_key[at] = pack_key((uint32_t)g, (uint32_t)(view_base + e.seg[s]));
+            a.log_w[at] = e.w[s];
             const float w = e.w[s];
             const float t = sh + w;
             sl += fabsf(sh) >= fabsf(w) ? (sh - t) + w : (w - t) + sh;
@@ -115,10 +152,10 @@ __global__ void __launch_bounds__(256) consume_k(HashEntry *__restrict__ hash, i
         }
         ++at;
     }
-    s_hi[g] = sh;
-    s_lo[g] = sl;
-    hash[g] = clear;
-    if (overflow) atomicOr(overflow_flag, 1u);
+    a.s_hi[g] = sh;
+    a.s_lo[g] = sl;
+    a.hash[g] = clear;
+    if (overflow) atomicOr(a.overflow, 1u);
 }
 
 __global__ void unique_flags_k(const uint64_t *__restrict__ keys, int64_t Z, uint32_t *__restrict__ flags) {
@@ -271,12 +308,13 @@ void launch_combine(const WeightRecord *recs, const unsigned long long *rec_chun
     note_launch();
 }
 
-void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
-                    unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key, float *log_w,
-                    uint32_t *overflow, const unsigned long long *view_contrib, unsigned long long *total_contrib,
-                    const uint32_t *skip, cudaStream_t st, const int32_t *view_base_dev) {
-    consume_k<<<blocks_for(n, 256), 256, 0, st>>>(hash, n, view_base, s_hi, s_lo, log_count, log_cap, log_key,
-                                                  log_w, overflow, view_contrib, total_contrib, skip, view_base_dev);
+void launch_consume(const ConsumeArgs &a, cudaStream_t st) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    spill_commit_k<<<(unsigned)sms * 2u, 256, 0, st>>>(a);
+    note_launch();
+    consume_k<<<blocks_for(a.n, 256), 256, 0, st>>>(a);
     note_launch();
 }
 

@@ -191,7 +191,7 @@ __device__ __forceinline__ bool cbar_and(bool p) {
 }
 
 __device__ __forceinline__ HashSink sink_of(const CompositeArgs &a, const Smem &sm) {
-    return HashSink{a.hash, a.log_count, a.log_cap, a.log_key, a.log_w, a.s_ovf, a.overflow, sm.view_base};
+    return HashSink{a.hash, a.spill_count, a.spill_cap, a.spill_key, a.spill_w, sm.view_base};
 }
 
 __device__ __forceinline__ void flush_slot(const CompositeArgs &a, Smem &sm, int b, int slot, int gi, float acc) {

@@ -67,6 +67,7 @@ cudaError_t set_max_smem(const void *fn, int bytes) {
 namespace {
 
 constexpr int kSlots = 6;   // views in flight
+constexpr int64_t kSpillMin = 1 << 18;   // initial capacity of a slot's spill list
 constexpr int kTotals = 5;  // device running totals (see slag_ctx::totals)
 
 // A view's camera and first column in device memory: the kernels of a replayed graph read them
@@ -104,6 +105,10 @@ struct ViewSlot {
     unsigned long long *rec_chunks = nullptr;   // chunks reserved by the composite
     uint32_t *rec_fill = nullptr;          // per chunk: records written
     int64_t fill_cap = 0;
+    uint64_t *spill_key = nullptr;         // the view's spill list: sums of Gaussians whose table
+    float *spill_w = nullptr;              // slots are all taken (log keys and weights)
+    int64_t spill_cap = 0;
+    const uint32_t *list = nullptr;        // the pair list the view's composite reads
     ViewCounters *ctr = nullptr;           // device: stage A's counters
     ViewCounters *ctr_up = nullptr;        // device: the segment-id check of the view's upload
     struct Host {
@@ -124,7 +129,8 @@ struct ViewSlot {
     cudaEvent_t ev_bin = nullptr;          // stage B of the slot's view done
     cudaEvent_t ev_done = nullptr;         // back work of the slot's view done
     int64_t log_bound = 0;                 // triples the slot's view may append after stage A
-    bool pending = false;                  // its view was sized on the device and is not settled
+    bool pending = false;                  // its back half is queued and its counters are not read
+    bool count_at_settle = false;          // its view was sized on the device and is not counted
     ViewParams *vp_dev = nullptr;          // the view's camera and first column (replayed graphs)
     ViewParams *vp_host = nullptr;         // pinned staging of vp_dev (rewritten once the slot is settled)
     // the slot's captured graphs: stages A and B (front stream), composite + combine and consume
@@ -618,7 +624,7 @@ void slot_free(ViewSlot &vs) {
     dfree(vs.rec_a); dfree(vs.rec_b); dfree(vs.rec_t); dfree(vs.rect); dfree(vs.srect);
     dfree(vs.stouched); dfree(vs.offsets); dfree(vs.hash);
     dfree(vs.prect); dfree(vs.ranges); dfree(vs.tile_order); dfree(vs.seg_buf); dfree(vs.ctr);
-    dfree(vs.ctr_up); dfree(vs.recs); dfree(vs.rec_chunks); dfree(vs.rec_fill);
+    dfree(vs.ctr_up); dfree(vs.recs); dfree(vs.rec_chunks); dfree(vs.rec_fill); dfree(vs.spill_key); dfree(vs.spill_w);
     if (vs.h) cudaFreeHost(vs.h);
     vs.h = nullptr;
     if (vs.back) cudaStreamDestroy(vs.back);
@@ -774,10 +780,16 @@ namespace {
 slag_status prepare_back_half(slag_ctx *ctx, ViewSlot &vs, int64_t P_tiles) {
     const CamParams &cp = vs.cp;
     cudaStream_t fb = vs.front;
+    if (vs.spill_cap < kSpillMin) {
+        int64_t c1 = vs.spill_cap, c2 = vs.spill_cap;
+        CK(grow(vs.spill_key, c1, kSpillMin, fb));
+        CK(grow(vs.spill_w, c2, kSpillMin, fb));
+        vs.spill_cap = c1;
+    }
     // room in the triple log: its fill level as last seen, plus what the other views in flight
-    // may still append, plus this view's bound (at most kHashSlots per Gaussian from the consume
-    // pass and the composite's overflow appends)
-    vs.log_bound = ctx->n * kHashSlots + 2 * P_tiles + (1 << 20);
+    // may still append, plus this view's bound: at most kHashSlots triples per Gaussian from its
+    // tables and its spill list's capacity (a view whose spills exceed it appends nothing)
+    vs.log_bound = ctx->n * kHashSlots + vs.spill_cap + (1 << 20);
     int64_t others = 0;
     for (int i = 0; i < kSlots; ++i)
         if (&ctx->slot[i] != &vs) others += ctx->slot[i].log_bound;
@@ -837,13 +849,11 @@ slag_status enqueue_composite(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list,
     a.view_base_dev = view_base_dev;
     a.weight_mode = ctx->weight_mode;
     a.hash = vs.hash;
-    a.log_count = ctx->log_count;
-    a.log_cap = (unsigned long long)ctx->log_cap;
-    a.log_key = ctx->log_key;
-    a.log_w = ctx->log_w;
-    a.s_ovf = ctx->s_ovf;
+    a.spill_count = &vs.ctr->spills;
+    a.spill_cap = (unsigned long long)vs.spill_cap;
+    a.spill_key = vs.spill_key;
+    a.spill_w = vs.spill_w;
     a.ctr = vs.ctr;
-    a.overflow = reinterpret_cast<uint32_t *>(ctx->totals + 2);
     a.contrib = &vs.ctr->contributions;
     a.evals = ctx->totals + 3;
     a.evals_exec = ctx->totals + 4;
@@ -863,8 +873,8 @@ slag_status enqueue_composite(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list,
     span_begin(ctx, SLAG_STAGE_COMPOSITE, bk);
     launch_composite(a, bk);
     span_end(ctx, bk);
-    const HashSink sink{vs.hash, ctx->log_count, (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
-                        ctx->s_ovf, reinterpret_cast<uint32_t *>(ctx->totals + 2), (int32_t)vs.view_base};
+    const HashSink sink{vs.hash, &vs.ctr->spills, (unsigned long long)vs.spill_cap, vs.spill_key, vs.spill_w,
+                        (int32_t)vs.view_base};
     span_begin(ctx, SLAG_STAGE_CONSUME, bk);
     launch_combine(vs.recs, vs.rec_chunks, vs.rec_fill, (unsigned long long)(vs.rec_cap / kRecChunk), sink, skip,
                    bk, view_base_dev);
@@ -877,11 +887,28 @@ slag_status enqueue_composite(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list,
 // then the copy of the view's counters and the log's fill level to the slot's mapped host struct.
 slag_status enqueue_consume(slag_ctx *ctx, ViewSlot &vs, const uint32_t *skip, const int32_t *view_base_dev) {
     cudaStream_t bk = vs.back;
+    ConsumeArgs c;
+    c.hash = vs.hash;
+    c.n = ctx->n;
+    c.view_base = (int32_t)vs.view_base;
+    c.view_base_dev = view_base_dev;
+    c.s_hi = ctx->s_hi;
+    c.s_lo = ctx->s_lo;
+    c.s_ovf = ctx->s_ovf;
+    c.log_count = ctx->log_count;
+    c.log_cap = (unsigned long long)ctx->log_cap;
+    c.log_key = ctx->log_key;
+    c.log_w = ctx->log_w;
+    c.overflow = reinterpret_cast<uint32_t *>(ctx->totals + 2);
+    c.spill_count = &vs.ctr->spills;
+    c.spill_cap = (unsigned long long)vs.spill_cap;
+    c.spill_key = vs.spill_key;
+    c.spill_w = vs.spill_w;
+    c.view_contrib = &vs.ctr->contributions;
+    c.total_contrib = ctx->contrib;
+    c.skip = skip;
     span_begin(ctx, SLAG_STAGE_CONSUME, bk);
-    launch_consume(vs.hash, ctx->n, (int32_t)vs.view_base, ctx->s_hi, ctx->s_lo, ctx->log_count,
-                   (unsigned long long)ctx->log_cap, ctx->log_key, ctx->log_w,
-                   reinterpret_cast<uint32_t *>(ctx->totals + 2), &vs.ctr->contributions, ctx->contrib, skip, bk,
-                   view_base_dev);
+    launch_consume(c, bk);
     span_end(ctx, bk);
     launch_copy_words(vs.ctr, &vs.h_dev->v, sizeof(ViewCounters), bk);
     launch_copy_words(ctx->totals, vs.h_dev->totals, kTotals * sizeof(unsigned long long), bk);
@@ -898,6 +925,8 @@ slag_status queue_back_half(slag_ctx *ctx, ViewSlot &vs, const uint32_t *list, i
                             const uint32_t *skip) {
     slag_status s = prepare_back_half(ctx, vs, P_tiles);
     if (s != SLAG_OK) return s;
+    vs.list = list;
+    vs.pending = true;
     cudaStream_t bk = vs.back;
     CK(cudaStreamWaitEvent(bk, vs.ev_bin, 0));
     CK(cudaStreamWaitEvent(bk, vs.ev_up, 0));   // the segment map
@@ -1046,37 +1075,54 @@ uint64_t back_key(const slag_ctx *ctx, const ViewSlot &vs) {
     return graph_key({2, (uint64_t)vs.cp.width, (uint64_t)vs.cp.height, (uint64_t)ctx->n, P(vs.pval[0]),
                       P(vs.prect), P(vs.ranges), P(vs.tile_order), P(vs.seg_buf), P(vs.recs), P(vs.rec_fill),
                       (uint64_t)vs.rec_cap, P(ctx->log_key), P(ctx->log_w), (uint64_t)ctx->log_cap,
-                      (uint64_t)ctx->weight_mode});
+                      (uint64_t)ctx->weight_mode, P(vs.spill_key), P(vs.spill_w), (uint64_t)vs.spill_cap});
 }
 
-// Settles the slot's view if it was sized on the device: waits for it, counts it, and when its
-// pairs exceeded its binning's capacity re-runs its binning (its stage A results, segment map and
-// columns are still in place) and its back half with the exact count.
+// Settles the slot's view: waits for its back half and reads its counters. A view sized on the
+// device is counted here; when its pairs exceeded its binning's capacity, its binning (its
+// stage A results, segment map and columns are still in place) and its back half run again with
+// the exact count. A view whose spills exceeded its slot's spill list gets a list that holds
+// them and is composited again (its consume pass changed nothing but its cleared tables).
 slag_status settle_slot(slag_ctx *ctx, ViewSlot &vs) {
-    if (!vs.pending) return SLAG_OK;
-    vs.pending = false;
-    CK(cudaEventSynchronize(vs.ev_done));
-    CK(cudaGetLastError());
-    const ViewCounters v = vs.h->v;   // copied at the end of its back half
-    ctx->log_fill_seen = std::max(ctx->log_fill_seen, (int64_t)vs.h->totals[0]);
-    count_view(ctx, v);
-    if (!v.overflow) return SLAG_OK;
-    ctx->stats.pairs -= (int64_t)v.P_tiles;   // counted again below
-    cudaStream_t fb = vs.front;
-    CK(cudaMemsetAsync(&vs.ctr->overflow, 0, sizeof(uint32_t), fb));
-    int64_t P = 0;
-    uint32_t *list = nullptr;
-    slag_status s = stage_b(ctx, vs, fb, vs.cp, kSuperShift, vs.scratch, &P, &list);
-    if (s != SLAG_OK) return s;
-    CK(cudaEventRecord(vs.ev_bin, fb));
-    s = queue_back_half(ctx, vs, list, (int64_t)v.P_tiles, nullptr);
-    if (s != SLAG_OK) return s;
-    ctx->stats.pairs += (int64_t)v.P_tiles;
-    ctx->stats.resized_views += 1;
+    while (vs.pending) {
+        vs.pending = false;
+        CK(cudaEventSynchronize(vs.ev_done));
+        CK(cudaGetLastError());
+        const ViewCounters v = vs.h->v;   // copied at the end of its back half
+        ctx->log_fill_seen = std::max(ctx->log_fill_seen, (int64_t)vs.h->totals[0]);
+        const bool sized_on_device = vs.count_at_settle;
+        vs.count_at_settle = false;
+        if (sized_on_device) count_view(ctx, v);
+        cudaStream_t fb = vs.front;
+        if (sized_on_device && v.overflow) {
+            ctx->stats.pairs -= (int64_t)v.P_tiles;   // counted again below
+            CK(cudaMemsetAsync(&vs.ctr->overflow, 0, sizeof(uint32_t), fb));
+            int64_t P = 0;
+            uint32_t *list = nullptr;
+            slag_status s = stage_b(ctx, vs, fb, vs.cp, kSuperShift, vs.scratch, &P, &list);
+            if (s != SLAG_OK) return s;
+            CK(cudaEventRecord(vs.ev_bin, fb));
+            s = queue_back_half(ctx, vs, list, (int64_t)v.P_tiles, nullptr);
+            if (s != SLAG_OK) return s;
+            ctx->stats.pairs += (int64_t)v.P_tiles;
+            ctx->stats.resized_views += 1;
+        } else if (v.spills > (unsigned long long)vs.spill_cap) {
+            int64_t c1 = vs.spill_cap, c2 = vs.spill_cap;
+            CK(grow(vs.spill_key, c1, (int64_t)v.spills, fb));
+            CK(grow(vs.spill_w, c2, (int64_t)v.spills, fb));
+            vs.spill_cap = c1;
+            CK(cudaMemsetAsync(&vs.ctr->spills, 0, sizeof(unsigned long long), fb));
+            CK(cudaMemsetAsync(&vs.ctr->contributions, 0, sizeof(unsigned long long), fb));
+            CK(cudaEventRecord(vs.ev_bin, fb));
+            const slag_status s = queue_back_half(ctx, vs, vs.list, (int64_t)v.P_tiles, nullptr);
+            if (s != SLAG_OK) return s;
+            ctx->stats.recomposited_views += 1;
+        }
+    }
     return SLAG_OK;
 }
 
-// Settles every view sized on the device (before a join reads the accumulated state).
+// Settles every view (before a join reads the accumulated state).
 slag_status settle_views(slag_ctx *ctx) {
     for (int i = 0; i < kSlots; ++i) {
         slag_status s = settle_slot(ctx, ctx->slot[i]);
@@ -1248,7 +1294,9 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
             s = queue_back_half(ctx, vs, vs.pval[0], tiles_bound, &vs.ctr->overflow);
             if (s != SLAG_OK) return s;
         }
+        vs.list = vs.pval[0];
         vs.pending = true;
+        vs.count_at_settle = true;
     }
     ctx->views_enqueued += 1;
     ctx->table_rows += M;
@@ -1868,7 +1916,7 @@ slag_status slag_reset(slag_ctx *ctx) {
     const int64_t n = ctx->n;
     ctx->deferred = false;   // the last view's second half is dropped with the rest
     CK(join_views(ctx));
-    for (int i = 0; i < kSlots; ++i) ctx->slot[i].pending = false;   // dropped too
+    for (int i = 0; i < kSlots; ++i) ctx->slot[i].pending = ctx->slot[i].count_at_settle = false;   // dropped too
     // a view that failed after its first half can leave entries in its slot's table
     for (int i = 0; i < kSlots; ++i) {
         launch_hash_init(ctx->slot[i].hash, n, st);
@@ -2696,7 +2744,6 @@ slag_status slag_composite_trace(slag_ctx *ctx, const slag_camera *cam, int64_t 
     a.n_ids = (uint32_t)ctx->n;
     a.weight_mode = ctx->weight_mode;
     a.ctr = vs.ctr;
-    a.overflow = &vs.ctr->pad;
     a.contrib = &vs.ctr->contributions;
     a.dbg_T = ctx->dbg_T;
     a.dbg_wsum = ctx->dbg_wsum;
@@ -2773,7 +2820,6 @@ slag_status slag_render_debug(slag_ctx *ctx, const slag_camera *cam, float *out_
     a.seg = nullptr;
     a.weight_mode = ctx->weight_mode;
     a.ctr = vs.ctr;
-    a.overflow = &vs.ctr->pad;
     a.contrib = &vs.ctr->contributions;
     a.dbg_T = ctx->dbg_T;
     a.dbg_wsum = ctx->dbg_wsum;

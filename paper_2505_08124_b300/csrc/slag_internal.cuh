@@ -82,6 +82,9 @@ struct ViewCounters {
     unsigned long long P;             // pairs at the binning granularity (tiles or super-tiles)
     unsigned long long P_tiles;       // Gaussian-tile pairs
     unsigned long long contributions; // composited (Gaussian, pixel) pairs (diagnostic render)
+    unsigned long long spills;        // (Gaussian, segment) sums that found no free slot in the
+                                      // view's table: the spill list's appends, also beyond its
+                                      // capacity
     uint32_t overflow;                // the view's pairs exceeded the capacity its binning held
     uint32_t pad;
 };
@@ -191,14 +194,16 @@ void launch_tile_order(const uint2 *ranges, int tiles_x, int tiles_y, int shift,
 // kHashSlots-entry table, or, once its slots hold other segments, a triple
 // (Gaussian, column, weight) appended to the log, whose weight also goes to
 // the Gaussian's overflow sum.
+// Where a view's (Gaussian, segment) sums go: the view's table of kHashSlots slots per Gaussian,
+// and, for a Gaussian whose slots are all taken by other segments, the view's spill list (log
+// keys and weights, moved to the triple log by the view's consume pass). The spill count keeps
+// counting beyond the list's capacity, so that the host learns how much room the view needed.
 struct HashSink {
     HashEntry *hash;               // n entries (internal order)
-    unsigned long long *log_count;
-    unsigned long long log_cap;
-    uint64_t *log_key;
-    float *log_w;
-    float *s_ovf;                  // per-Gaussian weight of overflow triples
-    uint32_t *overflow;            // set when the triple log is full (never reset by a view)
+    unsigned long long *spill_count;
+    unsigned long long spill_cap;
+    uint64_t *spill_key;
+    float *spill_w;
     int32_t view_base;             // column of segment 0 of this view
 };
 
@@ -207,14 +212,15 @@ __device__ __forceinline__ uint64_t pack_key(uint32_t g, uint32_t col) {
     return ((uint64_t)(g >> 7) << 39) | ((uint64_t)col << 7) | (uint64_t)(g & 127u);
 }
 
+__device__ __forceinline__ uint32_t key_gaussian(uint64_t key) {
+    return ((uint32_t)(key >> 39) << 7) | (uint32_t)(key & 127u);
+}
+
 __device__ __forceinline__ void sink_append(const HashSink &k, uint32_t g, int32_t seg, float w) {
-    const unsigned long long idx = atomicAdd(k.log_count, 1ull);
-    if (idx < k.log_cap) {
-        k.log_key[idx] = pack_key(g, (uint32_t)(k.view_base + seg));
-        k.log_w[idx] = w;
-        atomicAdd(&k.s_ovf[g], w);
-    } else {
-        atomicOr(k.overflow, 1u);
+    const unsigned long long idx = atomicAdd(k.spill_count, 1ull);
+    if (idx < k.spill_cap) {
+        k.spill_key[idx] = pack_key(g, (uint32_t)(k.view_base + seg));
+        k.spill_w[idx] = w;
     }
 }
 
@@ -266,13 +272,11 @@ struct CompositeArgs {
     const int32_t *view_base_dev;  // nullable: the same, read on the device (replayed graphs)
     int32_t weight_mode;
     HashEntry *hash;               // n entries (internal order)
-    unsigned long long *log_count;
-    unsigned long long log_cap;
-    uint64_t *log_key;
-    float *log_w;
-    float *s_ovf;                  // per-Gaussian weight of overflow triples
+    unsigned long long *spill_count;// the view's spill list (see HashSink)
+    unsigned long long spill_cap;
+    uint64_t *spill_key;
+    float *spill_w;
     ViewCounters *ctr;
-    uint32_t *overflow;            // set when the triple log is full (never reset by a view)
     unsigned long long *contrib;   // running count of composited (Gaussian, pixel) pairs
     unsigned long long *evals;     // running count of visited (Gaussian, pixel) pairs
     unsigned long long *evals_exec;// running count of evaluated lane-pixel pairs (nullable): per warp,
@@ -308,13 +312,31 @@ void launch_copy_words(const void *src, void *dst, int64_t bytes, cudaStream_t s
 void launch_combine(const WeightRecord *recs, const unsigned long long *rec_chunks, const uint32_t *rec_fill,
                     unsigned long long chunk_cap, const HashSink &sink, const uint32_t *skip, cudaStream_t st,
                     const int32_t *view_base_dev = nullptr);
-// The view's per-Gaussian tables to triples and the compensated weight sums (k_accum.cu).
-// Nothing when *skip (nullable) is non-zero.
-void launch_consume(HashEntry *hash, int64_t n, int32_t view_base, float *s_hi, float *s_lo,
-                    unsigned long long *log_count, unsigned long long log_cap, uint64_t *log_key,
-                    float *log_w, uint32_t *overflow, const unsigned long long *view_contrib,
-                    unsigned long long *total_contrib, const uint32_t *skip, cudaStream_t st,
-                    const int32_t *view_base_dev = nullptr);
+// The consume pass of a view (k_accum.cu): its spill list and its per-Gaussian tables to triples
+// of the log, the tables' weights to the compensated sums, the spilled weights to s_ovf. A view
+// whose spills exceeded the list's capacity is not consumed: its tables are cleared and nothing
+// else changes, so that the view can be composited again with a larger list. Nothing at all when
+// *skip (nullable) is non-zero.
+struct ConsumeArgs {
+    HashEntry *hash;                        // n entries (internal order)
+    int64_t n;
+    int32_t view_base;                      // column of segment 0 of the view
+    const int32_t *view_base_dev;           // nullable: the same, read on the device
+    float *s_hi, *s_lo, *s_ovf;
+    unsigned long long *log_count;          // the triple log
+    unsigned long long log_cap;
+    uint64_t *log_key;
+    float *log_w;
+    uint32_t *overflow;                     // set when the log is full (never reset by a view)
+    const unsigned long long *spill_count;  // the view's spill list
+    unsigned long long spill_cap;
+    const uint64_t *spill_key;
+    const float *spill_w;
+    const unsigned long long *view_contrib; // the view's composited pairs (nullable)
+    unsigned long long *total_contrib;      // their running total
+    const uint32_t *skip;
+};
+void launch_consume(const ConsumeArgs &a, cudaStream_t st);
 void launch_unique_flags(const uint64_t *keys, int64_t Z, uint32_t *flags, cudaStream_t st);
 // keys in the compact layout (launch_repack_keys with to_compact) of columns < 2^col_bits
 void launch_uniques(const uint64_t *keys, const uint32_t *flags, const uint32_t *uidx, int64_t Z, int col_bits,

@@ -59,7 +59,8 @@ class CView(ctypes.Structure):
 class CStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("views", "pairs", "contributions", "triples", "columns",
                                                "last_pairs", "last_contributions", "touched",
-                                               "evaluations", "executed", "resized_views")]
+                                               "evaluations", "executed", "resized_views",
+                                               "recomposited_views")]
 
 
 _lib = None

@@ -12,7 +12,10 @@ float32 summation order of the weight atomics:
 - a rejected view after an accepted one;
 - slag_reset with a view still waiting;
 - the caller's input buffers reused as soon as slag_add_view returns (host and device);
-- views whose pair counts outgrow the estimate (against the oracle)."""
+- views whose pair counts outgrow the estimate (against the oracle);
+- views whose Gaussians reach more segments than their tables hold, beyond the spill list's
+  capacity (composited again, against the oracle);
+- replayed graphs against kernel-by-kernel launches."""
 import math
 
 import numpy as np
@@ -172,6 +175,43 @@ def test_views_outgrowing_the_estimate_are_binned_again(slag):
     relw = np.linalg.norm(w.astype(np.float64) - den) / np.linalg.norm(den)
     assert rel <= 1e-4 and relw <= 1e-4, (rel, relw)
 
+
+
+def test_views_overflowing_the_spill_list_are_composited_again(slag):
+    # per-pixel random segment maps over 64 segments: each Gaussian reaches dozens of segments in
+    # a view, far more than its table's slots, and the spilled sums of one view (at least 370,000
+    # by the oracle's distinct (Gaussian, segment) counts) exceed the spill list's first capacity;
+    # such a view is composited again with a list that holds them, and counted once
+    s = synth.small_scene(43, 12000, 3, 320, 240, 8, dim=128, surfaces=4)
+    base = list(s.views())
+    zv = _zoomed(base[:2], [2.2, 2.2])
+    rng = np.random.default_rng(7)
+    views = [base[2]]
+    for v in zv:
+        seg = rng.integers(0, 64, size=(v.camera.height, v.camera.width)).astype(np.int32)
+        table = rng.standard_normal((64, 128)).astype(np.float32)
+        views.append(synth.View(v.camera, seg, table))
+    lower = [int(np.maximum((O.view_weights(s.gaussians, v)["B"] > 0).sum(1) - 4, 0).sum()) for v in views[1:]]
+    assert min(lower) > 300_000
+    out = {}
+    for graphs in (True, False):
+        with slag.Lifter(s.gaussians, dim=128) as L:
+            L.set_graphs(graphs)
+            for v in views:
+                L.add_view(v.camera, v.seg, v.table)
+            E, w = L.finalize()
+            out[graphs] = (E, w, L.stats())
+    num, den, info = O.lift(s.gaussians, views)
+    Eo = O.normalise(num, den)
+    contrib = sum(c for _, c in info)
+    for graphs, (E, w, st) in out.items():
+        # a view composited twice counts its composited pairs once
+        assert st["recomposited_views"] >= 1, graphs
+        assert st["views"] == len(views), graphs
+        assert abs(st["contributions"] - contrib) <= 1e-4 * contrib, (graphs, st["contributions"], contrib)
+        rel = np.linalg.norm(E.astype(np.float64) - Eo) / np.linalg.norm(Eo)
+        relw = np.linalg.norm(w.astype(np.float64) - den) / np.linalg.norm(den)
+        assert rel <= 1e-4 and relw <= 1e-4, (graphs, rel, relw)
 
 
 def test_graph_replays_match_kernel_launches(slag):
