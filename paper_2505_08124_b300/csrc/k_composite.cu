@@ -16,8 +16,9 @@
 // of its bin's list (a 4x4-tile super-tile) whose tile rectangle holds the
 // tile, taken in list order.
 //   * Producer: fills one of kNB record buffers at a time (a ring) with the hits among
-//     the next 128 candidates of the bin's list (the following 128 are loaded
-//     meanwhile; the list holds Gaussian indices), copying each hit's record
+//     the bin's list, 128 candidates at a time (the following 128 are loaded
+//     meanwhile; the list holds Gaussian indices), as many groups as the buffer's
+//     128 records hold, copying each hit's record
 //     (36 bytes, written by the projection) asynchronously and publishing the
 //     buffer on an mbarrier that completes once the copies have landed, so the
 //     producer never waits for them; it refills a buffer once all consumers
@@ -402,11 +403,21 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
         rc_nx[k] = c < end ? a.prect[c] : make_uint2(0u, 0u);
     }
     bool ok = true, have_slots = false;
-    int it = 0;
-    for (;; ++it) {
+    // batch it is filled in buffer it % kNB; taking a buffer for batch it >= kNB waits until the
+    // consumers have released batch it - kNB and moves that batch's sums out
+    int it = 0, nb = 0;
+    bool held = false;   // batch it has its buffer
+    auto take = [&]() -> bool {
         const int b = it % kNB;
-        // this batch's candidates (Gaussian indices) and their hits; the next batch's loads are
-        // issued now
+        if (it >= kNB) {
+            if (!wait_phase(a, sm, &sm.empty[b], (uint32_t)(it / kNB - 1) & 1u)) return false;
+            if (a.accumulate) drain_sums(a, sm, b, sm.count[b], ns_smem, lane, rr);
+        }
+        held = true;
+        return true;
+    };
+    for (;;) {
+        // the next kBuf candidates and their hits; the loads of the group after them are issued now
         uint32_t g[kPerLane];
         bool hit[kPerLane];
 #pragma unroll
@@ -421,53 +432,85 @@ __device__ void producer(const CompositeArgs &a, Smem &sm, int tile, int tx, int
             r_nx[k] = cn < end ? a.list[cn] : 0u;
             rc_nx[k] = cn < end ? a.prect[cn] : make_uint2(0u, 0u);
         }
-        if (it >= kNB) {
-            // the consumers have released this buffer (its previous batch, it - kNB): move its sums out
-            if (!wait_phase(a, sm, &sm.empty[b], (uint32_t)(it / kNB - 1) & 1u)) { ok = false; break; }
-            if (a.accumulate) drain_sums(a, sm, b, sm.count[b], ns_smem, lane, rr);
-        }
         bool live = trace;
         if (!trace) {
             // the consumers' liveness after the batches they have released
             for (int q = 0; q < kConsumers; ++q) live = live || (*((volatile int32_t *)&sm.warp_live[q]) != 0);
         }
-        if (cursor >= end || !live) {
-            if (lane == 0) sm.count[b] = -1;
-            __syncwarp();
-            publish(sm, b);
-            break;
-        }
-        // stable compaction of the hits (candidate order is (k, lane)); their records are copied
-        // asynchronously
-        int nb = 0;
+        if (cursor >= end || !live) break;
+        uint32_t bal[kPerLane];
+        int gh = 0;
 #pragma unroll
         for (int k = 0; k < kPerLane; ++k) {
-            const uint32_t bal = __ballot_sync(0xffffffffu, hit[k]);
-            const int pos = nb + __popc(bal & lt);
+            bal[k] = __ballot_sync(0xffffffffu, hit[k]);
+            gh += __popc(bal[k]);
+        }
+        cursor += kBuf;
+        if (gh == 0) continue;
+        if (!held && !take()) { ok = false; break; }
+        if (nb + gh > kBuf) {
+            // the batch is as full as the group allows: publish it and fill the next one
+            if (!have_slots) {
+                // the number of slots comes from the consumers' prologue (needed by the drains)
+                if (!wait_phase(a, sm, &sm.ready, 0u)) { ok = false; break; }
+                ns_smem = sm.scalar[1];
+                have_slots = true;
+            }
+            if (lane == 0) sm.count[it % kNB] = nb;
+            __syncwarp();
+            publish(sm, it % kNB);   // complete once the records' copies have landed
+            ++it;
+            nb = 0;
+            held = false;
+            if (!take()) { ok = false; break; }
+        }
+        // stable compaction of the group's hits (candidate order is (k, lane)) after the batch's
+        // records so far; their records are copied asynchronously
+        const int b = it % kNB;
+        int ng = 0;
+#pragma unroll
+        for (int k = 0; k < kPerLane; ++k) {
+            const int pg = ng + __popc(bal[k] & lt);
             if (hit[k]) {
+                const int pos = nb + pg;
                 cp_async16(&sm.q0[b][pos], a.rec_a + g[k]);
                 cp_async16(&sm.q1[b][pos], a.rec_b + g[k]);
                 cp_async4(&sm.qt[b][pos], a.rec_t + g[k]);
                 sm.gid[b][pos] = g[k];
                 if (trace) {
-                    const int64_t at = a.dbg_off[tile] + staged + pos;
+                    const int64_t at = a.dbg_off[tile] + staged + pg;
                     if (at < a.dbg_off[tile + 1]) a.dbg_list[at] = g[k];
                     else atomicOr(a.dbg_bad, 1u);
                 }
             }
-            nb += __popc(bal);
+            ng += __popc(bal[k]);
         }
-        cursor += kBuf;
-        staged += nb;
-        if (!have_slots) {
-            // the number of slots comes from the consumers' prologue (needed by the drains)
-            if (!wait_phase(a, sm, &sm.ready, 0u)) { ok = false; break; }
-            ns_smem = sm.scalar[1];
-            have_slots = true;
+        nb += gh;
+        staged += gh;
+    }
+    if (ok) {
+        // the last batch with records, then the end mark in the batch after it
+        if (nb > 0) {
+            if (!have_slots) {
+                if (!wait_phase(a, sm, &sm.ready, 0u)) ok = false;
+                ns_smem = sm.scalar[1];
+                have_slots = true;
+            }
+            if (ok) {
+                if (lane == 0) sm.count[it % kNB] = nb;
+                __syncwarp();
+                publish(sm, it % kNB);
+                ++it;
+                held = false;
+            }
         }
-        if (lane == 0) sm.count[b] = nb;
-        __syncwarp();
-        publish(sm, b);   // complete once the records' copies have landed
+        if (ok && (held || take())) {
+            if (lane == 0) sm.count[it % kNB] = -1;
+            __syncwarp();
+            publish(sm, it % kNB);
+        } else {
+            ok = false;
+        }
     }
     // the batches still held by the consumers (it - kNB + 1 .. it - 1): their sums once released
     for (int bt = it - kNB + 1 > 0 ? it - kNB + 1 : 0; ok && bt < it; ++bt) {
