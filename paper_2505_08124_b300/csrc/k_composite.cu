@@ -63,6 +63,11 @@ constexpr int kPerLane = 4;                           // candidates per producer
 constexpr int kBuf = 32 * kPerLane;                   // candidates per batch = record capacity of a buffer
 constexpr int kNB = 2;                                // record buffers (a ring)
 constexpr int kSmemSlots = 4;
+// A pixel stops before the Gaussian that would take its transmittance below kTStop. Its T keeps
+// being multiplied by (1 - alpha) afterwards, so it stays below kTStop (a product with a factor
+// in [0.01, 1] does not round above its operand): T >= kTStop is "the pixel is live", and the
+// transmittance chain is one packed FMA per Gaussian.
+constexpr float kTStop = 1e-4f;
 static_assert(kBuf < kRecChunk, "one slot's sums of a buffer must fit in two record chunks");
 constexpr int kWStride = 36;                          // transposition rows: 16-byte aligned, conflict-free
 constexpr uint32_t kBarConsumers = 1;                 // named barrier of the consumer warps
@@ -704,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
         const float *qt = sm.qt[b];
         for (int c = 0; c * 32 < nb; ++c) {
             const float2 T = unpk(PT);
-            const bool alive0 = T.x > 0.f, alive1 = T.y > 0.f;
+            const bool alive0 = T.x >= kTStop, alive1 = T.y >= kTStop;
             if (!__any_sync(0xffffffffu, alive0 || alive1)) break;
             const int nvalid = min(32, nb - c * 32);
             // which of the chunk's Gaussians can reach alpha >= 1/255 inside this warp's pixels: lane
@@ -767,12 +772,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
                     // FL: alpha >= 1/255; NAL = -alpha (0 below the floor)
                     const uint64_t FL = pk(set_ge(e0, kLog2AlphaMin), set_ge(e1, kLog2AlphaMin));
                     const uint64_t NAL = mul2(pk(fmaxf(-0.99f, -fast_exp2(e0)), fmaxf(-0.99f, -fast_exp2(e1))), FL);
-                    // the Gaussian whose (1 - alpha) would take T below 1e-4 stops the pixel (T = 0)
-                    // and contributes nothing: M = 0; alpha = 0 leaves T as it is. Weights are kept
-                    // negated (nw = -w), as the packed products give them.
+                    // the Gaussian whose (1 - alpha) takes T below kTStop stops the pixel and
+                    // contributes nothing (M = 0), nor does any later one; alpha = 0 leaves T as it
+                    // is. Weights are kept negated (nw = -w), as the packed products give them.
                     const uint64_t Tn = fma2(NAL, PT, PT);   // T - alpha T
                     const float2 tn = unpk(Tn);
-                    const uint64_t M = pk(set_ge(tn.x, 1e-4f), set_ge(tn.y, 1e-4f));
+                    const uint64_t M = pk(set_ge(tn.x, kTStop), set_ge(tn.y, kTStop));
                     float2 nw;
                     if (kKernel) {
                         const float lo = q1[c * 32 + cl[i + k]].y;
@@ -782,12 +787,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
                     }
                     if (kDebug) {
                         const float2 Tb = unpk(PT);
-                        Tf0 = (tn.x < 1e-4f && Tb.x > 0.f) ? Tb.x : Tf0;
-                        Tf1 = (tn.y < 1e-4f && Tb.y > 0.f) ? Tb.y : Tf1;
+                        Tf0 = (tn.x < kTStop && Tb.x >= kTStop) ? Tb.x : Tf0;
+                        Tf1 = (tn.y < kTStop && Tb.y >= kTStop) ? Tb.y : Tf1;
                         wsum0 -= nw.x;
                         wsum1 -= nw.y;
                     }
-                    PT = mul2(Tn, M);
+                    PT = Tn;
                     CNT = fma2(FL, M, CNT);
                     wb_warp[(i + k) * kWStride + lane] = fmaf(nw.y, s1, nw.x);
                     if (split1 && nw.y != 0.f) flush_slot(a, sm, b, slot1, c * 32 + cl[i + k], -nw.y);
@@ -795,8 +800,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
             }
             {
                 const float2 Ta = unpk(PT);
-                evp0 = (alive0 && !(Ta.x > 0.f)) ? seen + c * 32 + nvalid : evp0;
-                evp1 = (alive1 && !(Ta.y > 0.f)) ? seen + c * 32 + nvalid : evp1;
+                evp0 = (alive0 && !(Ta.x >= kTStop)) ? seen + c * 32 + nvalid : evp0;
+                evp1 = (alive1 && !(Ta.y >= kTStop)) ? seen + c * 32 + nvalid : evp1;
             }
             __syncwarp();
             // B: lane r = survivor r, sum over this warp's 32 lanes per slot
@@ -836,7 +841,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
         seen += nb;
         {
             const float2 T = unpk(PT);
-            const bool any = __any_sync(0xffffffffu, T.x > 0.f || T.y > 0.f);
+            const bool any = __any_sync(0xffffffffu, T.x >= kTStop || T.y >= kTStop);
             if (lane == 0) sm.warp_live[w] = any ? 1 : 0;
         }
         __syncwarp();
@@ -849,17 +854,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
     const int count0 = (int)cntf.x, count1 = (int)cntf.y;
     if (inside0) {
         const int64_t pi = (int64_t)py0 * W + px0;
-        if (a.dbg_T) a.dbg_T[pi] = T0 > 0.f ? T0 : Tf0;
+        if (a.dbg_T) a.dbg_T[pi] = T0 >= kTStop ? T0 : Tf0;
         if (a.dbg_wsum) a.dbg_wsum[pi] = wsum0;
         if (a.dbg_count) a.dbg_count[pi] = count0;
     }
     if (inside1) {
         const int64_t pi = (int64_t)py1 * W + px1;
-        if (a.dbg_T) a.dbg_T[pi] = T1 > 0.f ? T1 : Tf1;
+        if (a.dbg_T) a.dbg_T[pi] = T1 >= kTStop ? T1 : Tf1;
         if (a.dbg_wsum) a.dbg_wsum[pi] = wsum1;
         if (a.dbg_count) a.dbg_count[pi] = count1;
     }
-    const int ev0 = inside0 ? (T0 > 0.f ? seen : evp0) : 0, ev1 = inside1 ? (T1 > 0.f ? seen : evp1) : 0;
+    const int ev0 = inside0 ? (T0 >= kTStop ? seen : evp0) : 0, ev1 = inside1 ? (T1 >= kTStop ? seen : evp1) : 0;
     unsigned long long cnt = (unsigned long long)(count0 + count1), ev = (unsigned long long)(ev0 + ev1);
     for (int o = 16; o; o >>= 1) {
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
