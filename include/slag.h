@@ -202,8 +202,10 @@ slag_status slag_add_view(slag_ctx *ctx, const slag_camera *cam, const int32_t *
  * Gaussian order; a Gaussian no view touched (sum w = 0) gets the zero
  * vector. out_wsum: n float32 (nullable), the denominator sum w. on_device
  * says where the two outputs live. May be called again after more views.
- * Errors: STATE before any view; CAPACITY when the per-view reduction
- * overflowed its bound in some view; OOM; CUDA. */
+ * Errors: STATE before any view; CAPACITY when the triple log overflowed in
+ * some view (the log is grown ahead of every view to hold what it can append:
+ * 4 triples per Gaussian from its tables plus its spill list, which a view
+ * that outgrows it is composited again with); OOM; CUDA. */
 slag_status slag_finalize(slag_ctx *ctx, float *out_emb, float *out_wsum, int32_t on_device);
 
 /* slag_finalize with asynchronous outputs: the aggregation runs as in

@@ -43,7 +43,7 @@
 //     in flight before it exits.
 // A combine pass (many records in flight per SM) adds the records to the
 // per-view (segment, weight) table of each Gaussian (4 slots per Gaussian;
-// further segments are appended directly as triples).
+// sums of further segments go to the view's spill list).
 #include "slag_internal.cuh"
 #include "tc_util.cuh"
 
