@@ -81,7 +81,7 @@ OPS_PER_EVAL = 18
 # DRAM bytes (read + write) per launch of composite_k from one ncu capture, valid while the kernel
 # source has the recorded SHA-256 (otherwise the roofline reports traffic: null).
 COMPOSITE_TRAFFIC = {"bytes_per_launch": 36.27e6,
-                     "source_sha256": "815e3c931dffead9d1082f3a556f3feb3bd0d2435e319c8e8286311cb5bd6064",
+                     "source_sha256": "e3398ed48afaf888d9606eb7b288e9f7d3f81e2cc31ed0f4efd9739cad3c1d74",
                      "workload": "precision workload, 1920x1080 views 4-6 of the third step of an 8-view run: "
                                  "mean of 3 launches (profiles/composite_k_traffic_precision_1080p.md)"}
 # Nominal TF32 : BF16 dense tensor rate (1.1 : 2.25 PFLOP/s); the float32 path's contraction is a

@@ -675,8 +675,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) composite_k(const Compos
                    YY1d = pk(Y1 * Y1, Y1 * Y1);
     // bounding box of this warp's pixel centres (culling of Gaussians per warp), tile-local
     const float4 wbox = live_box(inside0, inside1, X0, Y0, X1, Y1);   // every lane holds the warp's box
-    // T (both pixels, packed) = 0 marks a pixel that has stopped (or lies outside the image): its
-    // weights are then 0 and every later Gaussian takes it below 1e-4 again, so no flag is needed
+    // T (both pixels, packed) below kTStop marks a pixel that has stopped (T = 0 one outside the
+    // image): every later Gaussian keeps it there, so no flag is needed
     uint64_t PT = pk(inside0 ? 1.f : 0.f, inside1 ? 1.f : 0.f);
     {
         const bool any = __any_sync(0xffffffffu, inside0 || inside1);
