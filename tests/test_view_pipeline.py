@@ -15,6 +15,8 @@ float32 summation order of the weight atomics:
 - views whose pair counts outgrow the estimate (against the oracle);
 - views whose Gaussians reach more segments than their tables hold, beyond the spill list's
   capacity (composited again, against the oracle);
+- degenerate views sized on the device: no visible Gaussian, no segment, one segment, ragged and
+  1x1 images (against the oracle);
 - replayed graphs against kernel-by-kernel launches."""
 import math
 
@@ -208,6 +210,42 @@ def test_views_overflowing_the_spill_list_are_composited_again(slag):
         # a view composited twice counts its composited pairs once
         assert st["recomposited_views"] >= 1, graphs
         assert st["views"] == len(views), graphs
+        assert abs(st["contributions"] - contrib) <= 1e-4 * contrib, (graphs, st["contributions"], contrib)
+        rel = np.linalg.norm(E.astype(np.float64) - Eo) / np.linalg.norm(Eo)
+        relw = np.linalg.norm(w.astype(np.float64) - den) / np.linalg.norm(den)
+        assert rel <= 1e-4 and relw <= 1e-4, (graphs, rel, relw)
+
+
+def test_degenerate_views_sized_on_the_device(slag):
+    # after a first view gives the pair estimate, the second halves are sized on the device (and
+    # replayed from graphs, or launched kernel by kernel): a view facing away from the scene (no
+    # visible Gaussian, no pairs), a view without segments (every id -1), a single segment, a
+    # ragged 17x33 view and a 1x1 view; the sums are the oracle's
+    s = synth.small_scene(45, 4000, 2, 96, 64, 6, dim=128, surfaces=3)
+    base = list(s.views())
+    rng = np.random.default_rng(11)
+    v0 = base[0]
+    away = synth.look_at([3.0, 0.0, 1.0], [6.0, 0.0, 2.0], 96, 64)
+    views = [v0, synth.View(away, v0.seg, v0.table)]
+    views.append(synth.View(base[1].camera, np.full((64, 96), -1, np.int32), base[1].table))
+    views.append(synth.View(base[1].camera, np.zeros((64, 96), np.int32), base[1].table[:1]))
+    for W, H in ((17, 33), (1, 1)):
+        cam = synth.look_at([2.4, 0.8, 0.9], [0.0, 0.0, 0.0], W, H)
+        seg = rng.integers(-1, 3, size=(H, W)).astype(np.int32)
+        views.append(synth.View(cam, seg, rng.standard_normal((3, 128)).astype(np.float32)))
+    views.append(base[1])
+    num, den, info = O.lift(s.gaussians, views)
+    assert info[1] == (0, 0)   # the view facing away: no pairs, no contributions
+    Eo = O.normalise(num, den)
+    for graphs in (True, False):
+        with slag.Lifter(s.gaussians, dim=128) as L:
+            L.set_graphs(graphs)
+            for v in views:
+                L.add_view(v.camera, v.seg, v.table)
+            E, w = L.finalize()
+            st = L.stats()
+        assert st["views"] == len(views) and st["resized_views"] == 0, (graphs, st)
+        contrib = sum(c for _, c in info)
         assert abs(st["contributions"] - contrib) <= 1e-4 * contrib, (graphs, st["contributions"], contrib)
         rel = np.linalg.norm(E.astype(np.float64) - Eo) / np.linalg.norm(Eo)
         relw = np.linalg.norm(w.astype(np.float64) - den) / np.linalg.norm(den)
