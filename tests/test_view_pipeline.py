@@ -17,6 +17,8 @@ float32 summation order of the weight atomics:
   capacity (composited again, against the oracle);
 - degenerate views sized on the device: no visible Gaussian, no segment, one segment, ragged and
   1x1 images (against the oracle);
+- a view with more super-tiles than the single-pass binning takes, between views sized on the
+  device (against the oracle);
 - replayed graphs against kernel-by-kernel launches."""
 import math
 
@@ -250,6 +252,33 @@ def test_degenerate_views_sized_on_the_device(slag):
         rel = np.linalg.norm(E.astype(np.float64) - Eo) / np.linalg.norm(Eo)
         relw = np.linalg.norm(w.astype(np.float64) - den) / np.linalg.norm(den)
         assert rel <= 1e-4 and relw <= 1e-4, (graphs, rel, relw)
+
+
+def test_views_with_more_bins_than_the_single_pass_binning(slag):
+    # a 4096x2176 view has 64 x 34 super-tiles, more than the single-pass binning's 2048 bins: its
+    # second half is sized on the host (pair emission and a two-pass sort), between views sized on
+    # the device; the sums are the oracle's
+    s = synth.small_scene(46, 3000, 1, 96, 64, 4, dim=128, surfaces=3)
+    rng = np.random.default_rng(5)
+    cam = synth.look_at([2.2, 0.9, 0.8], [0.0, 0.0, 0.0], 4096, 2176)
+    blocks = rng.integers(-1, 24, size=(2176 // 64 + 1, 4096 // 64 + 1)).astype(np.int32)
+    seg = np.ascontiguousarray(np.repeat(np.repeat(blocks, 64, 0), 64, 1)[:2176, :4096])
+    big = synth.View(cam, seg, rng.standard_normal((24, 128)).astype(np.float32))
+    small = next(iter(s.views()))
+    views = [small, big, small]
+    parts = {id(v): O.view_weights(s.gaussians, v) for v in (small, big)}
+    num = sum(parts[id(v)]["B"] @ v.table.astype(np.float64) for v in views)
+    den = sum(parts[id(v)]["B"].sum(axis=1) for v in views)
+    Eo = O.normalise(num, den)
+    with slag.Lifter(s.gaussians, dim=128) as L:
+        for v in views:
+            L.add_view(v.camera, v.seg, v.table)
+        E, w = L.finalize()
+        st = L.stats()
+    assert st["pairs"] == sum(parts[id(v)]["P"] for v in views)
+    rel = np.linalg.norm(E.astype(np.float64) - Eo) / np.linalg.norm(Eo)
+    relw = np.linalg.norm(w.astype(np.float64) - den) / np.linalg.norm(den)
+    assert rel <= 1e-4 and relw <= 1e-4, (rel, relw)
 
 
 def test_graph_replays_match_kernel_launches(slag):
