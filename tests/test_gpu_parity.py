@@ -185,6 +185,27 @@ def test_small_scene_parity(slag, seed, mode, empty):
     _compare(E, w, num, den, "small%d" % seed)
 
 
+@pytest.mark.parametrize("dim", [384, 4096])
+def test_embedding_widths(slag, dim):
+    # D = 384 (the contraction in 128-wide passes) and the largest D, 4096 (sixteen 256-wide passes,
+    # 128 K-chunks per query tile): embeddings and top-10 queries against the oracle
+    s = synth.small_scene(16, 3000, 2, 128, 96, 5, dim=dim, surfaces=3)
+    views = list(s.views())
+    rng = np.random.default_rng(8)
+    with slag.Lifter(s.gaussians, dim=dim) as L:
+        for v in views:
+            L.add_view(v.camera, v.seg, v.table)
+        E, w = L.finalize()
+        Q = rng.standard_normal((20, dim)).astype(np.float32)
+        Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+        ids, sc, cnt = L.query_batch(Q, 10)
+    num, den, _ = O.lift(s.gaussians, views, threads=2)
+    _compare(E, w, num, den, "dim%d" % dim)
+    for b in range(Q.shape[0]):
+        _check_topk(ids[b, :cnt[b]], sc[b, :cnt[b]], E.astype(np.float64), w.astype(np.float64),
+                    Q[b].astype(np.float64), 10)
+
+
 def test_constant_features(slag):
     s = synth.small_scene(14, 3000, 3, 96, 80, 7, dim=128, empty_fraction=0.2)
     c = np.random.default_rng(2).standard_normal(128).astype(np.float32)
