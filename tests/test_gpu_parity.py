@@ -206,6 +206,27 @@ def test_embedding_widths(slag, dim):
                     Q[b].astype(np.float64), 10)
 
 
+@pytest.mark.parametrize("n", [1, 2, 129])
+def test_few_gaussians(slag, n):
+    # one Gaussian, two, and one block of 128 plus one (a ragged second block): embeddings against
+    # the oracle, and a top-5 query that can return fewer ids than asked
+    s = synth.small_scene(17, 2000, 2, 96, 64, 4, dim=128, surfaces=2)
+    g = s.gaussians.subset(np.arange(n))
+    views = list(s.views())
+    q = views[0].table[0] / np.linalg.norm(views[0].table[0])
+    with slag.Lifter(g, dim=128) as L:
+        for v in views:
+            L.add_view(v.camera, v.seg, v.table)
+        E, w = L.finalize()
+        ids, sc, cnt = L.query_batch(q[None, :].astype(np.float32), 5)
+    num, den, _ = O.lift(g, views)
+    assert (den > 0).sum() == n
+    _compare(E, w, num, den, "n%d" % n)
+    assert cnt[0] == min(5, n)
+    _check_topk(ids[0, :cnt[0]], sc[0, :cnt[0]], E.astype(np.float64), w.astype(np.float64), q.astype(np.float64),
+                min(5, n))
+
+
 def test_constant_features(slag):
     s = synth.small_scene(14, 3000, 3, 96, 80, 7, dim=128, empty_fraction=0.2)
     c = np.random.default_rng(2).standard_normal(128).astype(np.float32)
