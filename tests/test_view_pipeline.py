@@ -198,13 +198,14 @@ def test_views_overflowing_the_spill_list_are_composited_again(slag):
     lower = [int(np.maximum((O.view_weights(s.gaussians, v)["B"] > 0).sum(1) - 4, 0).sum()) for v in views[1:]]
     assert min(lower) > 300_000
     out = {}
-    for graphs in (True, False):
+    # replayed graphs, kernel-by-kernel launches, and a spilling first view (sized on the host)
+    for case, order in (("graphs", views), ("direct", views), ("first", views[1:] + views[:1])):
         with slag.Lifter(s.gaussians, dim=128) as L:
-            L.set_graphs(graphs)
-            for v in views:
+            L.set_graphs(case == "graphs")
+            for v in order:
                 L.add_view(v.camera, v.seg, v.table)
             E, w = L.finalize()
-            out[graphs] = (E, w, L.stats())
+            out[case] = (E, w, L.stats())
     num, den, info = O.lift(s.gaussians, views)
     Eo = O.normalise(num, den)
     contrib = sum(c for _, c in info)
