@@ -9,10 +9,12 @@
 //   consume the per-view (segment, weight) tables into the triple log.
 //
 // Views are pipelined over kSlots (6) sets of per-view buffers. The front half
-// (projection through binning) runs on one high-priority internal stream, the
-// back half (composite, consume) on the slot's own stream, so that the next
-// view's front half and the start of its composite fill the SMs that a
-// composite's last, longest tiles leave idle. Consumes keep view order (they
+// (projection through binning) runs on the slot's front stream, the back half
+// (composite, consume) on its back stream, so that the next views' front halves
+// and the start of the next composite fill the SMs that a composite's last,
+// longest tiles leave idle. Back streams have the higher priority: a view
+// whose binning is done composites before more front work is scheduled (the
+// same step time at 1920x1080, 1-3% faster on smaller views). Consumes keep view order (they
 // update the compensated per-Gaussian sums without atomics) through an event
 // chain. Every entry point that reads results or reuses buffers first makes
 // the caller's stream wait for all views in flight.
@@ -120,7 +122,7 @@ struct ViewSlot {
     const uint32_t *sgid = nullptr;        // internal ids in depth order (stage A's output)
     CamParams cp{};                        // the view's camera
     int64_t view_base = 0;                 // its first column in the segment-embedding store
-    cudaStream_t front = nullptr;          // the slot's stages A and B (high priority)
+    cudaStream_t front = nullptr;          // the slot's stages A and B (low priority)
     SortScratch scratch;                   // their sorts and scans
     cudaEvent_t ev_front = nullptr;        // the front stream at a join
     cudaStream_t back = nullptr;
@@ -604,8 +606,8 @@ cudaError_t slot_alloc(ViewSlot &vs, int64_t n) {
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&vs.h_dev, vs.h, 0);
     int lo = 0, hi = 0;
     SA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    SA(cudaStreamCreateWithPriority(&vs.back, cudaStreamNonBlocking, lo));
-    SA(cudaStreamCreateWithPriority(&vs.front, cudaStreamNonBlocking, hi));
+    SA(cudaStreamCreateWithPriority(&vs.back, cudaStreamNonBlocking, hi));
+    SA(cudaStreamCreateWithPriority(&vs.front, cudaStreamNonBlocking, lo));
     SA(cudaEventCreateWithFlags(&vs.ev_front, cudaEventDisableTiming));
     SA(scratch_reserve(vs.scratch, n));
     SA(dalloc(&vs.vp_dev, 1));
